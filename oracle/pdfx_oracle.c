@@ -1,0 +1,1015 @@
+/*
+ * CPU oracle for one timestep of the particle path of the non-hybrid PDF method.
+ *
+ * TEST INFRASTRUCTURE ONLY.  Plain FP64 C, one thread, compiled with
+ * -ffp-contract=off.  It is the definition the CUDA library is checked against and
+ * it shares no code with that library.
+ *
+ * Paper passages followed (section / equation / appendix of the paper):
+ *   Sect. 3.1          explicit forward Euler (Euler-Maruyama) in time
+ *   Eq. 7              particle position
+ *   Eq. 10 / Eq. 27    generalised Langevin velocity (prediction form)
+ *   Eq. 11             G_ij and C0 from the elliptic-relaxation tensor
+ *   Eq. 18             dissipation
+ *   Eqs. 19-20         gamma (van Slooten) frequency model and its source
+ *   Eqs. 24-25         IECM mixing and the micromixing time scale
+ *   Eqs. 34-36         two-pass element/node statistics
+ *   Eqs. 37-38, 40     linear triangle shapefunctions
+ *   Eqs. 43-45         inside-element test and area coordinates (Fig. 1)
+ *   Sect. 3.5, App. A  adaptive sort-and-divide binning, conditioning pointers
+ *   Sect. 3.6          neighbour walk, concave-boundary fall-back (Fig. 2)
+ *   Sect. 3.7, App. B  initial particles, particle redistribution
+ *   Eqs. 53-58         wall crossing probability, reflection, no-slip, wall frequency
+ *   Sect. 3.9          six Gaussians per particle per step, plus one uniform for Eq. 55
+ *   Sect. 4.1.2        source disc with psi = 1
+ *
+ * Readings where the paper is silent, ambiguous or garbled are marked "Reading:".
+ */
+#include "pdfx_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define NF 32
+#define NS 13
+#define HOP_LIMIT 64
+#define GAMMA_ATTEMPTS 32
+
+/* Philox purposes (counter word 2). */
+enum { PUR_STEP = 0, PUR_INIT = 1, PUR_WALL_GAMMA = 2, PUR_REDIST = 3, PUR_INIT_GAMMA = 4 };
+
+struct orc_ctx {
+    orc_params p;
+    int nn, ne;
+    double *node_xy;      /* [nn][2] */
+    int32_t *tri;         /* [ne][3] */
+    int8_t *tag;          /* [ne][3] */
+    /* per element, unwrapped in the element's own frame (vertex A at its node) */
+    double *ax, *ay, *bx, *by, *cx, *cy, *area2;   /* b, c relative to A */
+    int32_t *nbr;         /* [ne][3]: neighbour across the edge opposite vertex k, -1 outside */
+    int32_t *ne_off, *ne_list;   /* node -> elements (ascending element id) */
+    /* wall lines: point, inward unit normal (in element frame); type 0 none */
+    int8_t *wall_type;    /* 0 none, 1 no-slip */
+    double *wall_px, *wall_py, *wall_nx, *wall_ny;
+    int8_t *fs_type;      /* 0 none, 2 free-slip */
+    double *fs_px, *fs_py, *fs_nx, *fs_ny;
+    double *fields;       /* [nn][32] */
+    /* particles, indexed by particle id */
+    int np;
+    double *x, *y, *u, *v, *w, *om, *psi;
+    int32_t *elem;
+    uint8_t *cp;
+    uint32_t step;
+    /* statistics */
+    int32_t *count;       /* [ne] */
+    double *emom;         /* [ne][13] */
+    double *nmom;         /* [nn][13] */
+    int G;                /* bins capacity per element = b1 b2 b3 */
+    double *vcce;         /* [ne][G] */
+    int32_t *gbin;        /* [ne][3] */
+    orc_diag diag;
+};
+
+/* ------------------------------------------------------------------------------------ */
+/* Random numbers (Sect. 3.9).  Reading: counter-based Philox4x32-10 replaces the paper's
+ * per-step tables; a particle's draws depend only on (seed, particle id, step, purpose,
+ * block), so they are identical in any execution order.                                 */
+/* ------------------------------------------------------------------------------------ */
+
+/* Philox4x32-10 of Salmon, Moraes, Dror & Shaw (SC'11): ten rounds of two 32x32->64
+ * multiplications with Weyl-sequence key increments between rounds. */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    const uint32_t M0 = 0xD2511F53u, M1 = 0xCD9E8D57u;
+    const uint32_t W0 = 0x9E3779B9u, W1 = 0xBB67AE85u;
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) { k0 += W0; k1 += W1; }
+        uint64_t p0 = (uint64_t)M0 * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)M1 * (uint64_t)c2;
+        uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        uint32_t n0 = hi1 ^ c1 ^ k0;
+        uint32_t n2 = hi0 ^ c3 ^ k1;
+        c0 = n0; c1 = lo1; c2 = n2; c3 = lo0;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* Uniform on the open interval (0, 1): (w + 1/2) 2^-32. */
+double orc_uniform(uint32_t w) { return ((double)w + 0.5) * (1.0 / 4294967296.0); }
+
+/* Box & Muller (1958): two independent standard Gaussians from two uniforms. */
+void orc_box_muller(uint32_t w1, uint32_t w2, double *g1, double *g2)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    double u1 = orc_uniform(w1), u2 = orc_uniform(w2);
+    double r = sqrt(-2.0 * log(u1));
+    double th = two_pi * u2;
+    *g1 = r * cos(th);
+    *g2 = r * sin(th);
+}
+
+static void philox_draw(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t step,
+                        uint32_t purpose, uint32_t block, uint32_t out[4])
+{
+    uint32_t key[2] = {(uint32_t)(seed & 0xffffffffu), (uint32_t)(seed >> 32) ^ instance};
+    uint32_t ctr[4] = {pid, step, purpose, block};
+    orc_philox4x32_10(ctr, key, out);
+}
+
+/* Gamma(shape, scale) by Marsaglia & Tsang (2000) for shape >= 1; attempt j uses Philox
+ * block j.  Each attempt draws one Gaussian (Box-Muller of words 0-1, cosine branch) and
+ * one uniform (word 2).  Reading: at most 32 attempts; if all are rejected the mean
+ * shape*scale is returned and counted. */
+double orc_gamma_draw(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t step,
+                      uint32_t purpose, double shape, double scale, int *exhausted)
+{
+    double d = shape - 1.0 / 3.0;
+    double c = 1.0 / sqrt(9.0 * d);
+    *exhausted = 0;
+    for (uint32_t j = 0; j < GAMMA_ATTEMPTS; ++j) {
+        uint32_t r[4];
+        double xg, dummy;
+        philox_draw(seed, instance, pid, step, purpose, j, r);
+        orc_box_muller(r[0], r[1], &xg, &dummy);
+        double uu = orc_uniform(r[2]);
+        double t = 1.0 + c * xg;
+        if (t <= 0.0) continue;
+        double vv = t * t * t;
+        if (log(uu) < 0.5 * xg * xg + d - d * vv + d * log(vv)) return d * vv * scale;
+    }
+    *exhausted = 1;
+    return shape * scale;
+}
+
+/* Sect. 3.9: the six Gaussians of one particle step and the uniform eta of Eq. 55.
+ * Block 0 -> (xi1, xi2), (xi3, xi4); block 1 -> (xi5, xi6) and eta from word 2. */
+void orc_step_gaussians(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t step,
+                        double xi[6], double *eta)
+{
+    uint32_t r0[4], r1[4];
+    philox_draw(seed, instance, pid, step, PUR_STEP, 0, r0);
+    philox_draw(seed, instance, pid, step, PUR_STEP, 1, r1);
+    orc_box_muller(r0[0], r0[1], &xi[0], &xi[1]);
+    orc_box_muller(r0[2], r0[3], &xi[2], &xi[3]);
+    orc_box_muller(r1[0], r1[1], &xi[4], &xi[5]);
+    *eta = orc_uniform(r1[2]);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Grid preprocessing.                                                                  */
+/* ------------------------------------------------------------------------------------ */
+
+static double min_image(double d, double L)
+{
+    if (L <= 0.0) return d;
+    if (d > 0.5 * L) return d - L;
+    if (d < -0.5 * L) return d + L;
+    return d;
+}
+
+static int elem_has_node(const orc_ctx *c, int e, int n)
+{
+    return c->tri[3 * e] == n || c->tri[3 * e + 1] == n || c->tri[3 * e + 2] == n;
+}
+
+/* Line of edge k of element f (the edge opposite its vertex k), with the unit normal
+ * pointing toward vertex k, i.e. into the domain.  Returned in f's frame. */
+static void edge_line(const orc_ctx *c, int f, int k, double *px, double *py, double *nx, double *ny)
+{
+    double vx[3] = {c->ax[f], c->ax[f] + c->bx[f], c->ax[f] + c->cx[f]};
+    double vy[3] = {c->ay[f], c->ay[f] + c->by[f], c->ay[f] + c->cy[f]};
+    int a = (k + 1) % 3, b = (k + 2) % 3;
+    double tx = vx[b] - vx[a], ty = vy[b] - vy[a];
+    double len = sqrt(tx * tx + ty * ty);
+    double mx = -ty / len, my = tx / len;
+    if ((vx[k] - vx[a]) * mx + (vy[k] - vy[a]) * my < 0.0) { mx = -mx; my = -my; }
+    *px = vx[a]; *py = vy[a]; *nx = mx; *ny = my;
+}
+
+/* Reading of Sect. 3.8 (last paragraph): an element with an edge on a wall uses that
+ * edge's line; an element with only a node on a wall uses the line of the first wall
+ * edge (lowest element id, then lowest local edge) incident to that node. */
+static void find_boundary_line(orc_ctx *c, int e, int type, int8_t *out_type,
+                               double *px, double *py, double *nx, double *ny)
+{
+    *out_type = 0;
+    for (int k = 0; k < 3; ++k)
+        if (c->tag[3 * e + k] == type) {
+            edge_line(c, e, k, px, py, nx, ny);
+            *out_type = (int8_t)type;
+            return;
+        }
+    for (int kv = 0; kv < 3; ++kv) {
+        int n = c->tri[3 * e + kv];
+        for (int i = c->ne_off[n]; i < c->ne_off[n + 1]; ++i) {
+            int f = c->ne_list[i];
+            for (int k = 0; k < 3; ++k) {
+                if (c->tag[3 * f + k] != type) continue;
+                int a = c->tri[3 * f + (k + 1) % 3], b = c->tri[3 * f + (k + 2) % 3];
+                if (a != n && b != n) continue;
+                double qx;
+                edge_line(c, f, k, &qx, py, nx, ny);
+                /* move the point into e's frame */
+                *px = c->ax[e] + min_image(qx - c->ax[e], c->p.period_x);
+                *out_type = (int8_t)type;
+                return;
+            }
+        }
+    }
+}
+
+static int params_valid(const orc_params *p)
+{
+    /* Marsaglia-Tsang needs shape 1/C4 >= 1; bins are 1..16 per component, <= 256 total */
+    if (!(p->C4 > 0.0 && p->C4 <= 1.0)) return 0;
+    for (int l = 0; l < 3; ++l)
+        if (p->bins[l] < 1 || p->bins[l] > 16) return 0;
+    if (p->bins[0] * p->bins[1] * p->bins[2] > 256 || p->min_per_bin < 1) return 0;
+    return 1;
+}
+
+int orc_create(orc_ctx **out, const orc_params *p, int nn, const double *node_xy,
+               int ne, const int32_t *tri, const int8_t *edge_tag)
+{
+    *out = NULL;
+    if (nn <= 0 || ne <= 0 || !params_valid(p)) return -1;
+    orc_ctx *c = (orc_ctx *)calloc(1, sizeof(orc_ctx));
+    c->p = *p;
+    c->nn = nn;
+    c->ne = ne;
+    c->node_xy = (double *)malloc(sizeof(double) * 2 * nn);
+    memcpy(c->node_xy, node_xy, sizeof(double) * 2 * nn);
+    c->tri = (int32_t *)malloc(sizeof(int32_t) * 3 * ne);
+    memcpy(c->tri, tri, sizeof(int32_t) * 3 * ne);
+    c->tag = (int8_t *)malloc(3 * ne);
+    memcpy(c->tag, edge_tag, 3 * ne);
+    double **geo[7] = {&c->ax, &c->ay, &c->bx, &c->by, &c->cx, &c->cy, &c->area2};
+    for (int i = 0; i < 7; ++i) *geo[i] = (double *)malloc(sizeof(double) * ne);
+    for (int e = 0; e < ne; ++e) {
+        int A = tri[3 * e], B = tri[3 * e + 1], C = tri[3 * e + 2];
+        if (A < 0 || B < 0 || C < 0 || A >= nn || B >= nn || C >= nn) { orc_destroy(c); return -2; }
+        c->ax[e] = node_xy[2 * A];
+        c->ay[e] = node_xy[2 * A + 1];
+        c->bx[e] = min_image(node_xy[2 * B] - c->ax[e], p->period_x);
+        c->by[e] = node_xy[2 * B + 1] - c->ay[e];
+        c->cx[e] = min_image(node_xy[2 * C] - c->ax[e], p->period_x);
+        c->cy[e] = node_xy[2 * C + 1] - c->ay[e];
+        /* 2 A_e: twice the signed area, positive for counter-clockwise vertices */
+        c->area2[e] = c->bx[e] * c->cy[e] - c->by[e] * c->cx[e];
+        if (!(c->area2[e] > 0.0)) { orc_destroy(c); return -3; }
+    }
+    /* node -> elements (Sect. 3.3 linked lists), ascending element id */
+    c->ne_off = (int32_t *)calloc(nn + 1, sizeof(int32_t));
+    for (int e = 0; e < ne; ++e)
+        for (int k = 0; k < 3; ++k) c->ne_off[tri[3 * e + k] + 1]++;
+    for (int n = 0; n < nn; ++n) c->ne_off[n + 1] += c->ne_off[n];
+    c->ne_list = (int32_t *)malloc(sizeof(int32_t) * 3 * ne);
+    int32_t *fill = (int32_t *)calloc(nn, sizeof(int32_t));
+    for (int e = 0; e < ne; ++e)
+        for (int k = 0; k < 3; ++k) {
+            int n = tri[3 * e + k];
+            c->ne_list[c->ne_off[n] + fill[n]++] = e;
+        }
+    free(fill);
+    /* elements surrounding elements (Sect. 3.6): neighbour across edge k */
+    c->nbr = (int32_t *)malloc(sizeof(int32_t) * 3 * ne);
+    for (int e = 0; e < ne; ++e)
+        for (int k = 0; k < 3; ++k) {
+            int a = tri[3 * e + (k + 1) % 3], b = tri[3 * e + (k + 2) % 3];
+            int found = -1;
+            for (int i = c->ne_off[a]; i < c->ne_off[a + 1]; ++i) {
+                int f = c->ne_list[i];
+                if (f != e && elem_has_node(c, f, b)) { found = f; break; }
+            }
+            c->nbr[3 * e + k] = found;
+            if ((found < 0) != (edge_tag[3 * e + k] != 0)) { orc_destroy(c); return -4; }
+        }
+    c->wall_type = (int8_t *)calloc(ne, 1);
+    c->fs_type = (int8_t *)calloc(ne, 1);
+    double **wl[8] = {&c->wall_px, &c->wall_py, &c->wall_nx, &c->wall_ny,
+                      &c->fs_px, &c->fs_py, &c->fs_nx, &c->fs_ny};
+    for (int i = 0; i < 8; ++i) *wl[i] = (double *)calloc(ne, sizeof(double));
+    for (int e = 0; e < ne; ++e) {
+        find_boundary_line(c, e, 1, &c->wall_type[e], &c->wall_px[e], &c->wall_py[e],
+                           &c->wall_nx[e], &c->wall_ny[e]);
+        find_boundary_line(c, e, 2, &c->fs_type[e], &c->fs_px[e], &c->fs_py[e],
+                           &c->fs_nx[e], &c->fs_ny[e]);
+    }
+    c->fields = (double *)calloc((size_t)nn * NF, sizeof(double));
+    c->count = (int32_t *)calloc(ne, sizeof(int32_t));
+    c->emom = (double *)calloc((size_t)ne * NS, sizeof(double));
+    c->nmom = (double *)calloc((size_t)nn * NS, sizeof(double));
+    c->G = p->bins[0] * p->bins[1] * p->bins[2];
+    if (c->G < 1 || c->G > 256) { orc_destroy(c); return -5; }
+    c->vcce = (double *)calloc((size_t)ne * c->G, sizeof(double));
+    c->gbin = (int32_t *)calloc((size_t)ne * 3, sizeof(int32_t));
+    *out = c;
+    return 0;
+}
+
+void orc_destroy(orc_ctx *c)
+{
+    if (!c) return;
+    void *ptrs[] = {c->node_xy, c->tri, c->tag, c->ax, c->ay, c->bx, c->by, c->cx, c->cy,
+                    c->area2, c->nbr, c->ne_off, c->ne_list, c->wall_type, c->wall_px,
+                    c->wall_py, c->wall_nx, c->wall_ny, c->fs_type, c->fs_px, c->fs_py,
+                    c->fs_nx, c->fs_ny, c->fields, c->x, c->y, c->u, c->v, c->w, c->om,
+                    c->psi, c->elem, c->cp, c->count, c->emom, c->nmom, c->vcce, c->gbin};
+    for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
+    free(c);
+}
+
+int orc_set_params(orc_ctx *c, const orc_params *p)
+{
+    if (!params_valid(p)) return -1;
+    if (p->bins[0] * p->bins[1] * p->bins[2] != c->G) return -5;
+    c->p = *p;
+    return 0;
+}
+
+int orc_set_fields(orc_ctx *c, const double *fields)
+{
+    memcpy(c->fields, fields, sizeof(double) * (size_t)c->nn * NF);
+    return 0;
+}
+
+int orc_neighbors(const orc_ctx *c, int32_t *nbr)
+{
+    memcpy(nbr, c->nbr, sizeof(int32_t) * 3 * (size_t)c->ne);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Area coordinates and interpolation (Eqs. 37-38, 43-45).                              */
+/* ------------------------------------------------------------------------------------ */
+
+/* Eqs. 44-45: N^A and N^C are half the signed cross products pivoted at vertex B; the
+ * area coordinates are lambda = N / A_e and N^B = A_e - N^A - N^C.  Reading: the paper
+ * prints |.| but calls them signed; the signed z-component is used (vertices counter-
+ * clockwise).  The particle's x is taken as its minimum image relative to vertex A. */
+void orc_lambda(const orc_ctx *c, int e, double x, double y, double lam[3])
+{
+    double dx = min_image(x - c->ax[e], c->p.period_x);
+    double dy = y - c->ay[e];
+    double bx = c->bx[e], by = c->by[e], cx = c->cx[e], cy = c->cy[e];
+    /* (r_C - r_B) x (r_P - r_B) */
+    double nA2 = (cx - bx) * (dy - by) - (cy - by) * (dx - bx);
+    /* (r_P - r_B) x (r_A - r_B), with r_A = 0 */
+    double nC2 = (dx - bx) * (-by) - (dy - by) * (-bx);
+    lam[0] = nA2 / c->area2[e];
+    lam[2] = nC2 / c->area2[e];
+    lam[1] = 1.0 - lam[0] - lam[2];
+}
+
+/* Eq. 43 as a closed test (Reading: the strict inequalities would leave edge points in
+ * no element). */
+static int lambda_inside(const double lam[3])
+{
+    return lam[0] >= 0.0 && lam[1] >= 0.0 && lam[2] >= 0.0;
+}
+
+/* Eq. 37: q(x) = sum_j N^j(x) q_j over the three nodes of the element. */
+void orc_interp(const orc_ctx *c, int e, const double lam[3], double q[32])
+{
+    const double *fa = c->fields + (size_t)NF * c->tri[3 * e];
+    const double *fb = c->fields + (size_t)NF * c->tri[3 * e + 1];
+    const double *fc = c->fields + (size_t)NF * c->tri[3 * e + 2];
+    for (int f = 0; f < NF; ++f) q[f] = lam[0] * fa[f] + lam[1] * fb[f] + lam[2] * fc[f];
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Particle tracking (Sect. 3.6).                                                       */
+/* ------------------------------------------------------------------------------------ */
+
+int orc_brute_locate(const orc_ctx *c, double x, double y)
+{
+    double lam[3];
+    for (int e = 0; e < c->ne; ++e) {
+        orc_lambda(c, e, x, y, lam);
+        if (lambda_inside(lam)) return e;
+    }
+    return -1;
+}
+
+/* Neighbour-to-neighbour walk: if the particle is outside the element, continue in the
+ * neighbour opposite the vertex with the lowest area coordinate.  Reading: equal minima
+ * go to the lowest local vertex; after 64 hops, or when the next guess is outside the
+ * domain (a tagged boundary edge, Fig. 2), search the elements surrounding the nodes of
+ * the old host element in ascending id; if that fails, search all elements (counted as
+ * an error).  Returns -1 if the point lies in no element. */
+int orc_walk(orc_ctx *c, int e0, double x, double y, int *hops)
+{
+    double lam[3];
+    int e = e0;
+    *hops = 0;
+    for (;;) {
+        orc_lambda(c, e, x, y, lam);
+        if (lambda_inside(lam)) return e;
+        if (*hops >= HOP_LIMIT) break;
+        int k = 0;
+        if (lam[1] < lam[k]) k = 1;
+        if (lam[2] < lam[k]) k = 2;
+        int nb = c->nbr[3 * e + k];
+        if (nb < 0) break;
+        e = nb;
+        (*hops)++;
+    }
+    c->diag.walk_fallback++;
+    int best = -1;
+    for (int kv = 0; kv < 3; ++kv) {
+        int n = c->tri[3 * e0 + kv];
+        for (int i = c->ne_off[n]; i < c->ne_off[n + 1]; ++i) {
+            int f = c->ne_list[i];
+            if (best >= 0 && f >= best) continue;
+            orc_lambda(c, f, x, y, lam);
+            if (lambda_inside(lam)) best = f;
+        }
+    }
+    if (best >= 0) return best;
+    c->diag.walk_brute++;
+    return orc_brute_locate(c, x, y);
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Particle advance (Sect. 3.1; Eqs. 7, 27, 19, 24; Sect. 3.8).                         */
+/* ------------------------------------------------------------------------------------ */
+
+static double wrap_x(double x, double L)
+{
+    if (L <= 0.0) return x;
+    if (x < 0.0) x += L;
+    if (x >= L) x -= L;
+    return x;
+}
+
+/* Source disc of Sect. 4.1.2: particles inside get psi = phi_0 = 1. */
+static int in_source(const orc_ctx *c, double x, double y)
+{
+    if (!c->p.source_on) return 0;
+    double dx = min_image(x - c->p.src_x, c->p.period_x);
+    double dy = y - c->p.src_y;
+    return dx * dx + dy * dy <= c->p.src_r * c->p.src_r;
+}
+
+static void advance_particle(orc_ctx *c, int p, double dt)
+{
+    const orc_params *P = &c->p;
+    const int e = c->elem[p];
+    double lam[3], q[NF];
+
+    /* Eqs. 37-38 and 44-45 at X^n (Reading: interp_mode 1 is the element average the
+     * paper uses, Sect. 3.3; mode 0 the shapefunction interpolation). */
+    if (P->interp_mode == 1) {
+        lam[0] = lam[1] = lam[2] = 1.0 / 3.0;
+    } else {
+        orc_lambda(c, e, c->x[p], c->y[p], lam);
+    }
+    orc_interp(c, e, lam, q);
+
+    const double Um[3] = {q[0], q[1], q[2]};
+    const double dP[3] = {q[3], q[4], 0.0};
+    double gradU[3][2];
+    for (int i = 0; i < 3; ++i) { gradU[i][0] = q[5 + 2 * i]; gradU[i][1] = q[6 + 2 * i]; }
+    const double lapU[3] = {q[11], q[12], q[13]};
+    double wp[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) wp[i][j] = q[14 + 3 * i + j];
+    double R[3][3];
+    R[0][0] = q[23]; R[1][1] = q[24]; R[2][2] = q[25];
+    R[0][1] = R[1][0] = q[26];
+    R[0][2] = R[2][0] = q[27];
+    R[1][2] = R[2][1] = q[28];
+    const double Om = q[29];
+    const double om_w = q[30];
+
+    /* k = <u_i u_i>/2 and Eq. 18.  Reading: k and eps are floored at 1e-30 so that a
+     * particle exactly on a wall (k = 0) keeps finite coefficients. */
+    double k = 0.5 * (R[0][0] + R[1][1] + R[2][2]);
+    if (k < 1e-30) k = 1e-30;
+    double eps = Om * (k + P->nu * P->CT * P->CT * Om);
+    if (eps < 1e-30) eps = 1e-30;
+
+    /* Eq. 11 */
+    double G[3][3];
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 3; ++j) G[i][j] = (wp[i][j] - (i == j ? 0.5 * eps : 0.0)) / k;
+    double C0;
+    if (P->c0_mode == 1) {
+        C0 = P->C0;
+    } else {
+        double s = 0.0;
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j) s += wp[i][j] * R[i][j];
+        C0 = -2.0 * s / (3.0 * k * eps);
+    }
+    /* Production P = -<u_i u_j> d<U_i>/dx_j (two space dimensions) and Eq. 20 */
+    double prod = 0.0;
+    for (int i = 0; i < 3; ++i)
+        for (int j = 0; j < 2; ++j) prod -= R[i][j] * gradU[i][j];
+    double Somega = P->Cw2 - P->Cw1 * prod / eps;
+
+    /* Eq. 25, or t_m = 2k / (C_phi eps).  Reading of Eq. 25: d_r = |X^n - x_s|,
+     * U_c = |<U>(X^n)| over three components; U_c = 0 makes the first argument infinite. */
+    double tm;
+    if (P->tm_mode == 1) {
+        tm = 2.0 * k / (P->Cphi * eps);
+    } else {
+        double ddx = min_image(c->x[p] - P->src_x, P->period_x);
+        double ddy = c->y[p] - P->src_y;
+        double dr = sqrt(ddx * ddx + ddy * ddy);
+        double Uc = sqrt(Um[0] * Um[0] + Um[1] * Um[1] + Um[2] * Um[2]);
+        double a1 = (Uc < 1e-300) ? INFINITY
+                    : P->Cs * cbrt(P->src_r * P->src_r / eps) + P->Ct * dr / Uc;
+        double kt = k / eps, kol = P->CT * sqrt(P->nu / eps);
+        double a2 = kt > kol ? kt : kol;
+        tm = a1 < a2 ? a1 : a2;
+    }
+
+    /* Sect. 3.9 draws */
+    double xi[6], eta;
+    orc_step_gaussians(P->seed, P->instance, (uint32_t)p, c->step, xi, &eta);
+    const double sdt = sqrt(dt);
+    const double dWx = sdt * xi[0], dWy = sdt * xi[1];
+    const double dWp[3] = {sdt * xi[2], sdt * xi[3], sdt * xi[4]};
+    const double dWw = sdt * xi[5];
+    const double s2nu = sqrt(2.0 * P->nu);
+
+    const double U0[3] = {c->u[p], c->v[p], c->w[p]};
+    const double X0 = c->x[p], Y0 = c->y[p];
+    const double w0 = c->om[p], psi0 = c->psi[p];
+
+    /* Eq. 27 (Reading: C0 eps < 0 is clamped to 0 under the square root, counted). */
+    double c0e = C0 * eps;
+    if (c0e < 0.0) { c0e = 0.0; c->diag.c0_clamp++; }
+    const double sc0e = sqrt(c0e);
+    double Un[3];
+    for (int i = 0; i < 3; ++i) {
+        double a = U0[i] - dP[i] * dt + 2.0 * P->nu * lapU[i] * dt
+                   + s2nu * (gradU[i][0] * dWx + gradU[i][1] * dWy);
+        double g = 0.0;
+        for (int j = 0; j < 3; ++j) g += G[i][j] * (U0[j] - Um[j]);
+        Un[i] = a + g * dt + sc0e * dWp[i];
+    }
+    /* Eq. 7 with the same dW as Eq. 27 */
+    double Xn = X0 + U0[0] * dt + s2nu * dWx;
+    double Yn = Y0 + U0[1] * dt + s2nu * dWy;
+    /* Eq. 19 (Reading: max(omega, 0) under the square root, then |omega|) */
+    double wpos = w0 > 0.0 ? w0 : 0.0;
+    double wn = w0 - P->C3 * Om * (w0 - Om) * dt - Somega * Om * w0 * dt
+                + sqrt(2.0 * P->C3 * P->C4 * Om * Om * wpos) * dWw;
+    if (wn < 0.0) { wn = -wn; c->diag.omega_reflect++; }
+    /* Eq. 24 with the conditional mean of the particle's bin (Appendix A pointer) */
+    double phic = c->vcce[(size_t)e * c->G + c->cp[p]];
+    double psin = psi0 - (psi0 - phic) * dt / tm;
+
+    /* Sect. 3.8, Eqs. 53-58, only in elements touching a wall (Reading: distances to the
+     * element's wall line; reflect only when behind the wall; psi is not changed). */
+    if (c->wall_type[e] == 1) {
+        double nx = c->wall_nx[e], ny = c->wall_ny[e];
+        double d0 = min_image(X0 - c->wall_px[e], P->period_x) * nx + (Y0 - c->wall_py[e]) * ny;
+        double d1 = min_image(Xn - c->wall_px[e], P->period_x) * nx + (Yn - c->wall_py[e]) * ny;
+        int hit = 0;
+        if (d1 < 0.0) {
+            hit = 1;
+            c->diag.wall_hits_a++;
+        } else {
+            double dd0 = d0 > 0.0 ? d0 : 0.0;
+            double fw = exp(-dd0 * d1 / (P->nu * dt));
+            if (eta < fw) hit = 1;
+        }
+        if (hit) {
+            c->diag.wall_hits++;
+            if (d1 < 0.0) { Xn -= 2.0 * d1 * nx; Yn -= 2.0 * d1 * ny; }
+            Un[0] = Un[1] = Un[2] = 0.0;                         /* Eq. 56 */
+            int ex = 0;
+            double shape = 1.0 / P->C4;                           /* Eq. 58 */
+            wn = orc_gamma_draw(P->seed, P->instance, (uint32_t)p, c->step, PUR_WALL_GAMMA,
+                                shape, P->C4 * om_w, &ex);
+            if (ex) c->diag.gamma_exhausted++;
+        }
+    }
+    /* Free-slip boundary (Sect. 4.2): perfect reflection, normal velocity reversed. */
+    if (c->fs_type[e] == 2) {
+        double nx = c->fs_nx[e], ny = c->fs_ny[e];
+        double d1 = min_image(Xn - c->fs_px[e], P->period_x) * nx + (Yn - c->fs_py[e]) * ny;
+        if (d1 < 0.0) {
+            c->diag.freeslip_hits++;
+            Xn -= 2.0 * d1 * nx;
+            Yn -= 2.0 * d1 * ny;
+            double un = Un[0] * nx + Un[1] * ny;
+            Un[0] -= 2.0 * un * nx;
+            Un[1] -= 2.0 * un * ny;
+        }
+    }
+    Xn = wrap_x(Xn, P->period_x);
+    if (in_source(c, Xn, Yn)) { psin = 1.0; c->diag.source_hits++; }
+
+    /* Sect. 3.6 */
+    int hops;
+    int en = orc_walk(c, e, Xn, Yn, &hops);
+    c->diag.hops_total += hops;
+    c->diag.hop_hist[hops < 7 ? hops : 7]++;
+    if (en < 0) { en = e; c->diag.lost++; }
+
+    c->x[p] = Xn; c->y[p] = Yn;
+    c->u[p] = Un[0]; c->v[p] = Un[1]; c->w[p] = Un[2];
+    c->om[p] = wn; c->psi[p] = psin;
+    c->elem[p] = en;
+}
+
+int orc_advance(orc_ctx *c, double dt)
+{
+    if (!c->x) return -1;
+    for (int p = 0; p < c->np; ++p) advance_particle(c, p, dt);
+    return 0;
+}
+
+void orc_finish_step(orc_ctx *c) { c->step++; }
+
+/* ------------------------------------------------------------------------------------ */
+/* Particle-number control (Sect. 3.7, Appendix B).                                     */
+/* ------------------------------------------------------------------------------------ */
+
+/* The Appendix B loop, literally: find the elements with the fewest and the most
+ * particles; while min < MINNPEL and the two differ, move one particle from the max to
+ * the min element.  Reading: ties go to the lowest element id; the loop also stops when
+ * max - min <= 1, where a move only swaps the two counts and the printed loop would not
+ * terminate. */
+int orc_redistribution_counts(const int32_t *counts, int ne, int minnpel, int32_t *fc)
+{
+    memcpy(fc, counts, sizeof(int32_t) * (size_t)ne);
+    int moves = 0;
+    if (minnpel <= 0) return 0;
+    for (;;) {
+        int mine = 0, maxe = 0;
+        for (int e = 1; e < ne; ++e) {
+            if (fc[e] < fc[mine]) mine = e;
+            if (fc[e] > fc[maxe]) maxe = e;
+        }
+        if (!(fc[mine] < minnpel && fc[maxe] - fc[mine] >= 2)) break;
+        fc[mine]++;
+        fc[maxe]--;
+        moves++;
+    }
+    return moves;
+}
+
+/* Appendix B and its closing paragraph.  Reading of what the paper leaves open:
+ *  - pairing: recipients in ascending element id, each repeated by its gain; donor slots
+ *    in ascending donor id, each donor giving its highest particle ids first; the k-th
+ *    recipient slot receives the k-th donor particle, which keeps its id;
+ *  - the moved particle is placed uniformly in the recipient triangle (Philox purpose 3,
+ *    words 0-1, square-root method) and copies (U, omega, psi) of the recipient's
+ *    resident with rank floor(u * n) in ascending id among its residents before the move
+ *    (word 2); an empty recipient copies from its lowest-id non-empty edge neighbour,
+ *    and with none the particle keeps its own properties;
+ *  - the source disc is re-applied at the new position. */
+int orc_redistribute(orc_ctx *c)
+{
+    const int ne = c->ne;
+    int32_t *cnt = (int32_t *)calloc(ne, sizeof(int32_t));
+    for (int p = 0; p < c->np; ++p) cnt[c->elem[p]]++;
+    int32_t *fin = (int32_t *)malloc(sizeof(int32_t) * ne);
+    int T = orc_redistribution_counts(cnt, ne, c->p.minnpel, fin);
+    if (T == 0) { free(cnt); free(fin); return 0; }
+
+    /* residents of every element, ascending particle id */
+    int32_t *off = (int32_t *)calloc(ne + 1, sizeof(int32_t));
+    for (int e = 0; e < ne; ++e) off[e + 1] = off[e] + cnt[e];
+    int32_t *res = (int32_t *)malloc(sizeof(int32_t) * (c->np > 0 ? c->np : 1));
+    int32_t *fillc = (int32_t *)calloc(ne, sizeof(int32_t));
+    for (int p = 0; p < c->np; ++p) res[off[c->elem[p]] + fillc[c->elem[p]]++] = p;
+    free(fillc);
+
+    int32_t *rslot = (int32_t *)malloc(sizeof(int32_t) * T);
+    int32_t *dpart = (int32_t *)malloc(sizeof(int32_t) * T);
+    int nr = 0, nd = 0;
+    for (int e = 0; e < ne; ++e) {
+        for (int g = 0; g < fin[e] - cnt[e]; ++g) rslot[nr++] = e;
+        for (int l = 0; l < cnt[e] - fin[e]; ++l) dpart[nd++] = res[off[e + 1] - 1 - l];
+    }
+    /* all new values first (from the state before any move), then apply */
+    double (*nv)[7] = malloc(sizeof(double[7]) * T);
+    for (int k = 0; k < T; ++k) {
+        int p = dpart[k], r = rslot[k];
+        uint32_t rw[4];
+        philox_draw(c->p.seed, c->p.instance, (uint32_t)p, c->step, PUR_REDIST, 0, rw);
+        double s = sqrt(orc_uniform(rw[0]));
+        double t = orc_uniform(rw[1]);
+        /* uniform point in a triangle: (1-s) A + s (1-t) B + s t C, Osada et al. */
+        double px = c->ax[r] + s * (1.0 - t) * c->bx[r] + s * t * c->cx[r];
+        double py = c->ay[r] + s * (1.0 - t) * c->by[r] + s * t * c->cy[r];
+        px = wrap_x(px, c->p.period_x);
+        int src = r;
+        if (cnt[r] == 0) {
+            src = -1;
+            for (int k2 = 0; k2 < 3; ++k2) {
+                int nb = c->nbr[3 * r + k2];
+                if (nb >= 0 && cnt[nb] > 0 && (src < 0 || nb < src)) src = nb;
+            }
+        }
+        int q = p;
+        if (src >= 0) {
+            int n = cnt[src];
+            int j = (int)(orc_uniform(rw[2]) * (double)n);
+            if (j >= n) j = n - 1;
+            q = res[off[src] + j];
+        }
+        nv[k][0] = px; nv[k][1] = py;
+        nv[k][2] = c->u[q]; nv[k][3] = c->v[q]; nv[k][4] = c->w[q];
+        nv[k][5] = c->om[q];
+        nv[k][6] = in_source(c, px, py) ? 1.0 : c->psi[q];
+    }
+    for (int k = 0; k < T; ++k) {
+        int p = dpart[k];
+        c->x[p] = nv[k][0]; c->y[p] = nv[k][1];
+        c->u[p] = nv[k][2]; c->v[p] = nv[k][3]; c->w[p] = nv[k][4];
+        c->om[p] = nv[k][5]; c->psi[p] = nv[k][6];
+        c->elem[p] = rslot[k];
+    }
+    c->diag.moves += T;
+    free(nv); free(rslot); free(dpart); free(res); free(off); free(cnt); free(fin);
+    return T;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Statistics (Sect. 3.3, Eqs. 35-36) and conditional means (Sect. 3.5, Appendix A).   */
+/* ------------------------------------------------------------------------------------ */
+
+static const double *g_sort_key;
+
+/* Sort order of Sect. 3.5 at one level: by the velocity component, ties by particle id. */
+static int cmp_by_key(const void *a, const void *b)
+{
+    int32_t pa = *(const int32_t *)a, pb = *(const int32_t *)b;
+    double ka = g_sort_key[pa], kb = g_sort_key[pb];
+    if (ka < kb) return -1;
+    if (ka > kb) return 1;
+    return (pa > pb) - (pa < pb);
+}
+
+/* Effective bins.  Reading of Sect. 3.5 ("stopped at any stage ... at least 2 particles
+ * ... only use two groups"): level l divides each group into
+ * g_l = max(1, min(b_l, floor(N / (g_1 ... g_{l-1} * min_per_bin)))) parts, so every bin
+ * keeps at least min_per_bin particles. */
+static void effective_bins(const orc_params *P, int N, int g[3])
+{
+    int Gp = 1;
+    for (int l = 0; l < 3; ++l) {
+        int cap = N / (Gp * P->min_per_bin);
+        int gl = P->bins[l] < cap ? P->bins[l] : cap;
+        if (gl < 1) gl = 1;
+        g[l] = gl;
+        Gp *= gl;
+    }
+}
+
+int orc_statistics(orc_ctx *c)
+{
+    const int ne = c->ne, nn = c->nn;
+    int32_t *off = (int32_t *)calloc(ne + 1, sizeof(int32_t));
+    memset(c->count, 0, sizeof(int32_t) * ne);
+    for (int p = 0; p < c->np; ++p) c->count[c->elem[p]]++;
+    for (int e = 0; e < ne; ++e) off[e + 1] = off[e] + c->count[e];
+    int32_t *res = (int32_t *)malloc(sizeof(int32_t) * (c->np > 0 ? c->np : 1));
+    int32_t *fillc = (int32_t *)calloc(ne, sizeof(int32_t));
+    for (int p = 0; p < c->np; ++p) res[off[c->elem[p]] + fillc[c->elem[p]]++] = p;
+    free(fillc);
+
+    /* Element moments: first pass means (Eq. 35), second pass central moments (Eq. 36).
+     * Layout: N, <U>, <V>, <W>, <uu>, <vv>, <ww>, <uv>, <uw>, <vw>, <omega>, <phi>, <phi'^2> */
+    for (int e = 0; e < ne; ++e) {
+        double *m = c->emom + (size_t)NS * e;
+        for (int i = 0; i < NS; ++i) m[i] = 0.0;
+        int N = c->count[e];
+        m[0] = (double)N;
+        if (N == 0) continue;
+        double su = 0, sv = 0, sw = 0, so = 0, sp = 0;
+        for (int i = off[e]; i < off[e + 1]; ++i) {
+            int p = res[i];
+            su += c->u[p]; sv += c->v[p]; sw += c->w[p]; so += c->om[p]; sp += c->psi[p];
+        }
+        double mu = su / N, mv = sv / N, mw = sw / N, mo = so / N, mp = sp / N;
+        double suu = 0, svv = 0, sww = 0, suv = 0, suw = 0, svw = 0, spp = 0;
+        for (int i = off[e]; i < off[e + 1]; ++i) {
+            int p = res[i];
+            double du = c->u[p] - mu, dv = c->v[p] - mv, dw = c->w[p] - mw, dp = c->psi[p] - mp;
+            suu += du * du; svv += dv * dv; sww += dw * dw;
+            suv += du * dv; suw += du * dw; svw += dv * dw;
+            spp += dp * dp;
+        }
+        m[1] = mu; m[2] = mv; m[3] = mw;
+        m[4] = suu / N; m[5] = svv / N; m[6] = sww / N;
+        m[7] = suv / N; m[8] = suw / N; m[9] = svw / N;
+        m[10] = mo; m[11] = mp; m[12] = spp / N;
+    }
+    /* Node values: average over the surrounding elements (Sect. 3.3).  Reading: plain
+     * average over the surrounding elements that hold particles; column 0 is the mean
+     * particle count of those elements; a node with none gets zeros. */
+    for (int n = 0; n < nn; ++n) {
+        double *m = c->nmom + (size_t)NS * n;
+        for (int i = 0; i < NS; ++i) m[i] = 0.0;
+        int cntn = 0;
+        for (int i = c->ne_off[n]; i < c->ne_off[n + 1]; ++i) {
+            int e = c->ne_list[i];
+            if (c->count[e] < 1) continue;
+            const double *em = c->emom + (size_t)NS * e;
+            for (int s = 0; s < NS; ++s) m[s] += em[s];
+            cntn++;
+        }
+        if (cntn > 0)
+            for (int s = 0; s < NS; ++s) m[s] /= cntn;
+    }
+    /* Conditional means (Sect. 3.5, Appendix A) */
+    const double *keys[3] = {c->u, c->v, c->w};
+    memset(c->vcce, 0, sizeof(double) * (size_t)ne * c->G);
+    for (int e = 0; e < ne; ++e) {
+        int N = c->count[e];
+        int g[3];
+        effective_bins(&c->p, N, g);
+        c->gbin[3 * e] = g[0]; c->gbin[3 * e + 1] = g[1]; c->gbin[3 * e + 2] = g[2];
+        if (N == 0) continue;
+        int32_t *par = res + off[e];                 /* parid[] of Appendix A */
+        /* sort & divide: level l sorts each group of the previous level */
+        int Gprev = 1;
+        for (int l = 0; l < 3; ++l) {
+            if (g[l] > 1) {
+                g_sort_key = keys[l];
+                int start = 0;
+                while (start < N) {
+                    /* group of position n at the previous level: floor(Gprev n / N) */
+                    int grp = (int)(((long long)Gprev * start) / N);
+                    int end = start;
+                    while (end < N && (int)(((long long)Gprev * end) / N) == grp) end++;
+                    qsort(par + start, (size_t)(end - start), sizeof(int32_t), cmp_by_key);
+                    start = end;
+                }
+            }
+            Gprev *= g[l];
+        }
+        /* Appendix A: i = CNBI * n / npel[e] */
+        const int CNBI = g[0] * g[1] * g[2];
+        int np_bin[256];
+        double *vc = c->vcce + (size_t)e * c->G;
+        for (int i = 0; i < CNBI; ++i) { np_bin[i] = 0; vc[i] = 0.0; }
+        for (int n = 0; n < N; ++n) {
+            int i = (int)(((long long)CNBI * n) / N);
+            np_bin[i] += 1;
+            vc[i] += c->psi[par[n]];
+            c->cp[par[n]] = (uint8_t)i;
+        }
+        for (int i = 0; i < CNBI; ++i) vc[i] = vc[i] / np_bin[i];
+    }
+    free(res);
+    free(off);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Initial particles (Sect. 3.7) and the whole step.                                    */
+/* ------------------------------------------------------------------------------------ */
+
+static void alloc_particles(orc_ctx *c, int np)
+{
+    free(c->x); free(c->y); free(c->u); free(c->v); free(c->w); free(c->om); free(c->psi);
+    free(c->elem); free(c->cp);
+    c->np = np;
+    size_t n = (size_t)(np > 0 ? np : 1);
+    c->x = (double *)calloc(n, sizeof(double));
+    c->y = (double *)calloc(n, sizeof(double));
+    c->u = (double *)calloc(n, sizeof(double));
+    c->v = (double *)calloc(n, sizeof(double));
+    c->w = (double *)calloc(n, sizeof(double));
+    c->om = (double *)calloc(n, sizeof(double));
+    c->psi = (double *)calloc(n, sizeof(double));
+    c->elem = (int32_t *)calloc(n, sizeof(int32_t));
+    c->cp = (uint8_t *)calloc(n, 1);
+}
+
+/* Sect. 3.7: an equal number of particles per element, uniform in the element; velocity
+ * Gaussian about the local mean with variance 2k/3; frequency gamma with the local mean
+ * and variance C4 <omega>^2; psi from the source disc.  Particle id = e * ppe + k.
+ * Draws: purpose 1 block 0 (position words 0-1, Gaussians from words 2-3), block 1
+ * (third Gaussian from words 0-1); gamma attempts on purpose 4. */
+int orc_init_particles(orc_ctx *c, int ppe)
+{
+    if (ppe <= 0) return -1;
+    long long np = (long long)ppe * c->ne;
+    if (np > 2147483647LL) return -1;
+    alloc_particles(c, (int)np);
+    c->step = 0;
+    memset(&c->diag, 0, sizeof(c->diag));
+    for (int e = 0; e < c->ne; ++e)
+        for (int k = 0; k < ppe; ++k) {
+            int p = e * ppe + k;
+            uint32_t r0[4], r1[4];
+            philox_draw(c->p.seed, c->p.instance, (uint32_t)p, 0, PUR_INIT, 0, r0);
+            philox_draw(c->p.seed, c->p.instance, (uint32_t)p, 0, PUR_INIT, 1, r1);
+            double s = sqrt(orc_uniform(r0[0]));
+            double t = orc_uniform(r0[1]);
+            double px = c->ax[e] + s * (1.0 - t) * c->bx[e] + s * t * c->cx[e];
+            double py = c->ay[e] + s * (1.0 - t) * c->by[e] + s * t * c->cy[e];
+            double lam[3], q[NF];
+            if (c->p.interp_mode == 1) lam[0] = lam[1] = lam[2] = 1.0 / 3.0;
+            else orc_lambda(c, e, px, py, lam);
+            orc_interp(c, e, lam, q);
+            double k2 = 0.5 * (q[23] + q[24] + q[25]);
+            if (k2 < 0.0) k2 = 0.0;
+            double sd = sqrt(2.0 * k2 / 3.0);
+            double g0, g1, g2, gdum;
+            orc_box_muller(r0[2], r0[3], &g0, &g1);
+            orc_box_muller(r1[0], r1[1], &g2, &gdum);
+            int ex = 0;
+            double om = orc_gamma_draw(c->p.seed, c->p.instance, (uint32_t)p, 0, PUR_INIT_GAMMA,
+                                       1.0 / c->p.C4, c->p.C4 * q[29], &ex);
+            if (ex) c->diag.gamma_exhausted++;
+            px = wrap_x(px, c->p.period_x);
+            c->x[p] = px; c->y[p] = py;
+            c->u[p] = q[0] + sd * g0;
+            c->v[p] = q[1] + sd * g1;
+            c->w[p] = q[2] + sd * g2;
+            c->om[p] = om;
+            c->psi[p] = in_source(c, px, py) ? 1.0 : 0.0;
+            c->elem[p] = e;
+        }
+    return orc_statistics(c);
+}
+
+int orc_set_particles(orc_ctx *c, int np, const double *x, const double *y, const double *u,
+                      const double *v, const double *w, const double *om, const double *psi,
+                      const int32_t *elem, uint32_t step)
+{
+    if (np < 0) return -1;
+    for (int p = 0; p < np; ++p)
+        if (elem[p] < 0 || elem[p] >= c->ne) return -2;
+    alloc_particles(c, np);
+    memcpy(c->x, x, sizeof(double) * np);
+    memcpy(c->y, y, sizeof(double) * np);
+    memcpy(c->u, u, sizeof(double) * np);
+    memcpy(c->v, v, sizeof(double) * np);
+    memcpy(c->w, w, sizeof(double) * np);
+    memcpy(c->om, om, sizeof(double) * np);
+    memcpy(c->psi, psi, sizeof(double) * np);
+    memcpy(c->elem, elem, sizeof(int32_t) * np);
+    c->step = step;
+    return orc_statistics(c);
+}
+
+int orc_get_particles(const orc_ctx *c, double *x, double *y, double *u, double *v, double *w,
+                      double *om, double *psi, int32_t *elem, uint8_t *cp)
+{
+    size_t n = (size_t)c->np;
+    if (x) memcpy(x, c->x, sizeof(double) * n);
+    if (y) memcpy(y, c->y, sizeof(double) * n);
+    if (u) memcpy(u, c->u, sizeof(double) * n);
+    if (v) memcpy(v, c->v, sizeof(double) * n);
+    if (w) memcpy(w, c->w, sizeof(double) * n);
+    if (om) memcpy(om, c->om, sizeof(double) * n);
+    if (psi) memcpy(psi, c->psi, sizeof(double) * n);
+    if (elem) memcpy(elem, c->elem, sizeof(int32_t) * n);
+    if (cp) memcpy(cp, c->cp, n);
+    return 0;
+}
+
+int orc_num_particles(const orc_ctx *c) { return c->np; }
+uint32_t orc_step_index(const orc_ctx *c) { return c->step; }
+
+/* One timestep (Table 1 order restricted to the particle path): advance and track,
+ * particle-number control, then statistics and conditional means for the next step. */
+int orc_step(orc_ctx *c, double dt)
+{
+    int rc = orc_advance(c, dt);
+    if (rc) return rc;
+    orc_redistribute(c);
+    rc = orc_statistics(c);
+    orc_finish_step(c);
+    return rc;
+}
+
+int orc_get_element_stats(const orc_ctx *c, double *out, int32_t *counts)
+{
+    if (out) memcpy(out, c->emom, sizeof(double) * (size_t)c->ne * NS);
+    if (counts) memcpy(counts, c->count, sizeof(int32_t) * (size_t)c->ne);
+    return 0;
+}
+
+int orc_get_nodal_stats(const orc_ctx *c, double *out)
+{
+    memcpy(out, c->nmom, sizeof(double) * (size_t)c->nn * NS);
+    return 0;
+}
+
+int orc_get_bins(const orc_ctx *c, double *vcce, int32_t *g)
+{
+    if (vcce) memcpy(vcce, c->vcce, sizeof(double) * (size_t)c->ne * c->G);
+    if (g) memcpy(g, c->gbin, sizeof(int32_t) * 3 * (size_t)c->ne);
+    return 0;
+}
+
+int orc_bins_capacity(const orc_ctx *c) { return c->G; }
+void orc_get_diag(const orc_ctx *c, orc_diag *d) { *d = c->diag; }
+void orc_reset_diag(orc_ctx *c) { memset(&c->diag, 0, sizeof(c->diag)); }

@@ -1,0 +1,310 @@
+"""Seeded synthetic inputs: unstructured triangle grids and prescribed nodal fields.
+
+This module produces *input data only* (node coordinates, triangles, edge tags,
+nodal Eulerian fields, model parameters).  It contains none of the particle
+method's arithmetic: no shapefunctions, no stochastic updates, no tracking, no
+statistics.  Both the CUDA library and the CPU oracle consume what it returns.
+
+Workloads (the paper's test cases, Sect. 4.1 and 4.2, rebuilt synthetically
+because its DNS and wind-tunnel data are not part of the method):
+
+* ``channel_grid`` -- the 2-D channel cross-section [0, Lx] x [0, 1], walls at
+  y = 0 and y = 1 (no-slip), periodic in x.  A jittered lattice whose quads are
+  split along the diagonal that passes the local empty-circumcircle test, so the
+  node valence varies like an unstructured Delaunay mesh.  Rows are uniform or
+  geometrically graded toward both walls (first cell at y+ ~ 1).
+* ``channel_fields`` -- prescribed nodal fields for fully developed channel flow
+  at friction Reynolds number Re_tau: Reichardt mean velocity, a smooth
+  turbulent kinetic energy and frequency profile, a realisable Reynolds stress,
+  the mean-pressure gradient of Eq. 63, a local algebraic form for the
+  elliptic-relaxation tensor and the Eq. 58 wall frequency.
+
+Nodal field layout (32 doubles per node):
+  0-2   <U_i>                      3-4   d<P>/dx_j (rho = 1)
+  5-10  d<U_i>/dx_j (i-major, j = x, y)
+  11-13 laplacian <U_i>            14-22 wp_ij (3 x 3 row-major)
+  23-28 <u_i u_j> (xx, yy, zz, xy, xz, yz)
+  29    <omega>                    30    omega_w (Eq. 58 mean at walls)
+  31    reserved (0)
+Edge tags (int8 per element edge k, the edge opposite local vertex k):
+  0 interior, 1 no-slip wall, 2 free-slip boundary.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass
+
+import numpy as np
+
+NF = 32           # nodal field slots
+NSTAT = 13        # statistics per element / node
+
+# Table 4 of the paper (model constants for velocity and frequency).
+TABLE4 = dict(C1=1.85, C2=0.63, C3=5.0, C4=0.25, CT=6.0, CL=0.134, Ceta=72.0,
+              Cv=1.4, gamma5=0.1, Cw1=0.5, Cw2=0.73)
+
+
+@dataclass
+class Grid:
+    node_xy: np.ndarray      # float64 [nn, 2]
+    tri: np.ndarray          # int32 [ne, 3], counter-clockwise (minimum image in x)
+    edge_tag: np.ndarray     # int8 [ne, 3]
+    period_x: float          # 0.0 = not periodic
+
+    @property
+    def nn(self) -> int:
+        return int(self.node_xy.shape[0])
+
+    @property
+    def ne(self) -> int:
+        return int(self.tri.shape[0])
+
+
+def _geometric_rows(ny: int, y1: float) -> np.ndarray:
+    """Node rows on [0, 1] with cell widths y1 * r**min(k, ncell-1-k), symmetric about 0.5."""
+    ncell = ny - 1
+    k = np.arange(ncell)
+    m = np.minimum(k, ncell - 1 - k)
+
+    def total(r: float) -> float:
+        return float(np.sum(y1 * r ** m))
+
+    lo, hi = 1.0, 2.0
+    while total(hi) < 1.0:
+        hi *= 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if total(mid) < 1.0:
+            lo = mid
+        else:
+            hi = mid
+    h = y1 * (0.5 * (lo + hi)) ** m
+    y = np.concatenate([[0.0], np.cumsum(h)])
+    y[-1] = 1.0
+    return y
+
+
+def _incircle(ax, ay, bx, by, cx, cy, dx, dy) -> np.ndarray:
+    """> 0 where d lies inside the circumcircle of the counter-clockwise triangle abc."""
+    adx, ady = ax - dx, ay - dy
+    bdx, bdy = bx - dx, by - dy
+    cdx, cdy = cx - dx, cy - dy
+    ad = adx * adx + ady * ady
+    bd = bdx * bdx + bdy * bdy
+    cd = cdx * cdx + cdy * cdy
+    return (adx * (bdy * cd - bd * cdy) - ady * (bdx * cd - bd * cdx)
+            + ad * (bdx * cdy - bdy * cdx))
+
+
+def channel_grid(nx: int, ny: int, lx: float = 2.0, graded_y1: float | None = None,
+                 jitter_x: float = 0.2, jitter_y: float = 0.1, seed: int = 1) -> Grid:
+    """Periodic-in-x channel grid with nx columns and ny node rows (2 nx (ny-1) triangles).
+
+    Wall rows (y = 0, 1) are jittered in x only, so wall edges lie exactly on the walls.
+    Interior nodes move by up to +-jitter_x * dx in x and +-jitter_y * (smaller adjacent
+    row spacing) in y.  Each quad takes the diagonal that satisfies the empty-circle test.
+    """
+    rng = np.random.default_rng(seed)
+    dx = lx / nx
+    if graded_y1 is None:
+        ys = np.linspace(0.0, 1.0, ny)
+    else:
+        ys = _geometric_rows(ny, graded_y1)
+    xs = np.arange(nx) * dx
+    X = np.repeat(xs[None, :], ny, axis=0).copy()
+    Y = np.repeat(ys[:, None], nx, axis=1).copy()
+    X += rng.uniform(-jitter_x, jitter_x, size=X.shape) * dx
+    dy_loc = np.empty(ny)
+    dy_loc[0] = ys[1] - ys[0]
+    dy_loc[-1] = ys[-1] - ys[-2]
+    dy_loc[1:-1] = np.minimum(ys[1:-1] - ys[:-2], ys[2:] - ys[1:-1])
+    jy = rng.uniform(-jitter_y, jitter_y, size=Y.shape) * dy_loc[:, None]
+    jy[0, :] = 0.0
+    jy[-1, :] = 0.0
+    Y += jy
+    X = np.mod(X, lx)
+    node_xy = np.stack([X.ravel(), Y.ravel()], axis=1).astype(np.float64)
+
+    def nid(j, i):
+        return j * nx + (i % nx)
+
+    # quad (i, j): corners p00=(i,j), p10=(i+1,j), p11=(i+1,j+1), p01=(i,j+1)
+    J, I = np.meshgrid(np.arange(ny - 1), np.arange(nx), indexing="ij")
+    J = J.ravel()
+    I = I.ravel()
+    n00, n10, n11, n01 = nid(J, I), nid(J, I + 1), nid(J + 1, I + 1), nid(J + 1, I)
+
+    def unwrapped(n, ref):
+        x = node_xy[n, 0].copy()
+        d = x - node_xy[ref, 0]
+        x = np.where(d > 0.5 * lx, x - lx, np.where(d < -0.5 * lx, x + lx, x))
+        return x, node_xy[n, 1]
+
+    x00, y00 = unwrapped(n00, n00)
+    x10, y10 = unwrapped(n10, n00)
+    x11, y11 = unwrapped(n11, n00)
+    x01, y01 = unwrapped(n01, n00)
+    # Diagonal p00-p11 gives (p00,p10,p11),(p00,p11,p01); it is Delaunay in the quad iff
+    # p01 is not inside the circumcircle of (p00,p10,p11).
+    use_a = _incircle(x00, y00, x10, y10, x11, y11, x01, y01) <= 0.0
+
+    def area2(ax, ay, bx, by, cx, cy):
+        return (bx - ax) * (cy - ay) - (by - ay) * (cx - ax)
+
+    a_ok = (area2(x00, y00, x10, y10, x11, y11) > 0) & (area2(x00, y00, x11, y11, x01, y01) > 0)
+    b_ok = (area2(x00, y00, x10, y10, x01, y01) > 0) & (area2(x10, y10, x11, y11, x01, y01) > 0)
+    use_a = np.where(a_ok & b_ok, use_a, a_ok)
+    if not np.all(np.where(use_a, a_ok, b_ok)):
+        raise ValueError("jitter too large: a quad admits no valid split")
+
+    t1 = np.where(use_a[:, None], np.stack([n00, n10, n11], 1), np.stack([n00, n10, n01], 1))
+    t2 = np.where(use_a[:, None], np.stack([n00, n11, n01], 1), np.stack([n10, n11, n01], 1))
+    tri = np.empty((2 * t1.shape[0], 3), dtype=np.int32)
+    tri[0::2] = t1
+    tri[1::2] = t2
+
+    # Edge tags: an edge with both ends on the same wall row is a no-slip wall edge.
+    on_bottom = np.zeros(node_xy.shape[0], bool)
+    on_top = np.zeros(node_xy.shape[0], bool)
+    on_bottom[:nx] = True
+    on_top[(ny - 1) * nx:] = True
+    edge_tag = np.zeros(tri.shape, dtype=np.int8)
+    for k in range(3):
+        a = tri[:, (k + 1) % 3]
+        b = tri[:, (k + 2) % 3]
+        wall = (on_bottom[a] & on_bottom[b]) | (on_top[a] & on_top[b])
+        edge_tag[:, k] = np.where(wall, 1, 0)
+    return Grid(node_xy=node_xy, tri=tri, edge_tag=edge_tag, period_x=float(lx))
+
+
+# ----------------------------------------------------------------------------------------
+# Prescribed channel fields.
+# ----------------------------------------------------------------------------------------
+
+def _reichardt(yp):
+    """Reichardt's mean-velocity profile U+(y+) and its first two y+-derivatives."""
+    kap = 0.41
+    a = np.log1p(kap * yp) / kap
+    da = 1.0 / (1.0 + kap * yp)
+    dda = -kap / (1.0 + kap * yp) ** 2
+    e1 = np.exp(-yp / 11.0)
+    e3 = np.exp(-yp / 3.0)
+    b = 7.8 * (1.0 - e1 - (yp / 11.0) * e3)
+    db = 7.8 * (e1 / 11.0 - e3 / 11.0 + (yp / 33.0) * e3)
+    ddb = 7.8 * (-e1 / 121.0 + e3 / 33.0 + e3 / 33.0 - (yp / 99.0) * e3)
+    return a + b, da + db, dda + ddb
+
+
+def channel_fields(grid: Grid, re_tau: float, u_tau: float = 0.05, h: float = 0.5,
+                   params: dict | None = None) -> np.ndarray:
+    """Nodal fields [nn, 32] for statistically stationary channel flow at Re_tau."""
+    c = dict(TABLE4)
+    if params:
+        c.update({k: v for k, v in params.items() if k in c})
+    nu = u_tau * h / re_tau
+    y = grid.node_xy[:, 1]
+    yw = np.minimum(y, 1.0 - y)
+    s = np.where(y < 0.5, 1.0, -1.0)               # d(yw)/dy
+    yp = u_tau * yw / nu
+    iscale = u_tau / nu                            # d(y+)/d(yw)
+
+    up, dup, ddup = _reichardt(yp)
+    U = u_tau * up
+    dUdy = s * u_tau * iscale * dup
+    d2Udy2 = u_tau * iscale ** 2 * ddup
+
+    ek = np.exp(-yp / 10.0)
+    kp = 3.33 * (1.0 - ek) ** 2
+    dkp = 3.33 * 2.0 * (1.0 - ek) * ek / 10.0
+    k = u_tau ** 2 * kp
+    dkdy = s * u_tau ** 2 * iscale * dkp
+    fv = (1.0 - np.exp(-yp / 26.0)) ** 2
+    uv = -s * u_tau ** 2 * (1.0 - yw / h) * fv
+    wp = 0.73 / (yp + 8.1)
+    om = (u_tau ** 2 / nu) * wp
+
+    F = np.zeros((grid.nn, NF), dtype=np.float64)
+    F[:, 0] = U
+    F[:, 3] = -u_tau ** 2 / h                      # driving streamwise pressure gradient
+    F[:, 4] = -(2.0 / 3.0) * dkdy                  # Eq. 63 with <v^2> = 2k/3
+    F[:, 6] = dUdy                                 # dU/dy
+    F[:, 11] = d2Udy2
+    # Elliptic-relaxation tensor: local algebraic (L -> 0) form, isotropic part plus a
+    # production-like part proportional to the mean velocity gradient.
+    grad = np.zeros((grid.nn, 3, 3))
+    grad[:, 0, 1] = dUdy
+    wpij = np.zeros((grid.nn, 3, 3))
+    for i in range(3):
+        wpij[:, i, i] += 0.5 * (1.0 - c["C1"]) * k * om
+    wpij += c["C2"] * k[:, None, None] * grad
+    F[:, 14:23] = wpij.reshape(grid.nn, 9)
+    F[:, 23] = 2.0 * k / 3.0
+    F[:, 24] = 2.0 * k / 3.0
+    F[:, 25] = 2.0 * k / 3.0
+    F[:, 26] = uv
+    F[:, 29] = om
+    # Eq. 58 mean frequency at the wall, (1/C_T) d sqrt(2k)/dy at y = 0 for this k profile.
+    F[:, 30] = (1.0 / c["CT"]) * u_tau * iscale * math.sqrt(2.0 * 3.33) / 10.0
+    return F
+
+
+def channel_nu(re_tau: float, u_tau: float = 0.05, h: float = 0.5) -> float:
+    return u_tau * h / re_tau
+
+
+def uniform_fields(nn: int, U=(0.0, 0.0, 0.0), dP=(0.0, 0.0), grad=None, lap=(0.0, 0.0, 0.0),
+                   wp=None, uu=None, omega=1.0, omega_w=1.0) -> np.ndarray:
+    """Spatially constant nodal fields (homogeneous test flows)."""
+    F = np.zeros((nn, NF), dtype=np.float64)
+    F[:, 0:3] = U
+    F[:, 3:5] = dP
+    if grad is not None:
+        F[:, 5:11] = np.asarray(grad, dtype=np.float64).reshape(6)
+    F[:, 11:14] = lap
+    if wp is not None:
+        F[:, 14:23] = np.asarray(wp, dtype=np.float64).reshape(9)
+    if uu is None:
+        uu = (2.0 / 3.0, 2.0 / 3.0, 2.0 / 3.0, 0.0, 0.0, 0.0)
+    F[:, 23:29] = uu
+    F[:, 29] = omega
+    F[:, 30] = omega_w
+    return F
+
+
+# ----------------------------------------------------------------------------------------
+# Named workloads.
+# ----------------------------------------------------------------------------------------
+
+def workload(name: str) -> dict:
+    """Grid, fields and parameters of a named synthetic workload.
+
+    ``channel_2k``  : 46 x 24 nodes, 2116 triangles, Re_tau 392, 100 particles per element,
+                      dt 1e-4, constant C0 = 3.5 and C_phi = 2 mixing, Philox seed 1.
+    ``channel_50k`` : 200 x 126 nodes graded to y+ = 1 at both walls, 50,000 triangles,
+                      Re_tau 1080, 500 particles per element (25M), Eq. 11 C0 and Eq. 25 t_m.
+    ``channel_tiny``: 8 x 5 nodes, 64 triangles (parity at sizes the oracle finishes fast).
+    """
+    if name == "channel_2k":
+        g = channel_grid(46, 24, jitter_x=0.2, jitter_y=0.1, seed=1)
+        re = 392.0
+        p = dict(c0_mode=1, C0=3.5, tm_mode=1, Cphi=2.0, seed=1, ppe=100, dt=1e-4, steps=10)
+    elif name == "channel_50k":
+        re = 1080.0
+        nu = channel_nu(re)
+        g = channel_grid(200, 126, graded_y1=nu / 0.05, jitter_x=0.2, jitter_y=0.1, seed=2)
+        p = dict(c0_mode=0, C0=0.0, tm_mode=0, Cphi=2.0, seed=2, ppe=500, dt=1e-4, steps=200)
+    elif name == "channel_tiny":
+        g = channel_grid(8, 5, jitter_x=0.2, jitter_y=0.1, seed=3)
+        re = 392.0
+        p = dict(c0_mode=1, C0=3.5, tm_mode=1, Cphi=2.0, seed=3, ppe=40, dt=1e-4, steps=3)
+    else:
+        raise KeyError(name)
+    nu = channel_nu(re)
+    fields = channel_fields(g, re)
+    params = dict(TABLE4)
+    params.update(nu=nu, Cs=0.02, Ct=0.7, src_x=0.5, src_y=0.5, src_r=0.02,
+                  bins=(4, 4, 4), min_per_bin=2, minnpel=max(1, p["ppe"] // 10),
+                  interp_mode=0, period_x=g.period_x)
+    params.update({k: v for k, v in p.items() if k not in ("ppe", "dt", "steps")})
+    return dict(name=name, grid=g, fields=fields, params=params, ppe=p["ppe"], dt=p["dt"],
+                steps=p["steps"], re_tau=re)

@@ -1,0 +1,714 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix (no GPU).
+
+Each test checks the oracle against something other than its own formulas: published
+known answers, closed forms of the stochastic recursions, invariants, textbook
+distributions (scipy), brute force, or the paper's worked example.
+"""
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import stats
+
+import oracle
+from paper_1006_0532_gb300 import synth
+from helpers import base_params, homogeneous_fields
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------------------
+# Random numbers (Sect. 3.9)
+# --------------------------------------------------------------------------------------
+
+def test_philox_known_answers():
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(t, 16) for t in r]
+        assert oracle.philox(v[0:4], v[4:6]) == v[6:10]
+
+
+def test_uniform_open_interval():
+    assert oracle.lib().orc_uniform(0) == 0.5 / 2 ** 32
+    assert oracle.lib().orc_uniform(0xffffffff) == (2 ** 32 - 0.5) / 2 ** 32
+    assert 0.0 < oracle.lib().orc_uniform(0) and oracle.lib().orc_uniform(0xffffffff) < 1.0
+
+
+def _gaussians(n, seed=11):
+    out = []
+    for pid in range(n // 6):
+        xi, _ = oracle.step_gaussians(seed, 0, pid, 3)
+        out.append(xi)
+    return np.concatenate(out)
+
+
+def test_box_muller_standard_normal():
+    g = _gaussians(120000)
+    n = g.size
+    assert abs(g.mean()) < 5 / math.sqrt(n)
+    assert abs(g.var() - 1.0) < 5 * math.sqrt(2.0 / n)
+    assert abs(stats.skew(g)) < 5 * math.sqrt(6.0 / n)
+    assert abs(stats.kurtosis(g)) < 5 * math.sqrt(24.0 / n)
+    assert stats.kstest(g, "norm").pvalue > 1e-3
+    # the six per-particle Gaussians are mutually uncorrelated
+    m = g.reshape(-1, 6)
+    c = np.corrcoef(m.T)
+    assert np.max(np.abs(c - np.eye(6))) < 5 / math.sqrt(m.shape[0])
+
+
+def test_gamma_sampler_distribution():
+    # Eq. 58 / Sect. 3.7: gamma with mean m and variance C4 m^2 is Gamma(1/C4, C4 m).
+    C4, m = 0.25, 3.0
+    n = 40000
+    draws = np.array([oracle.gamma_draw(5, 0, pid, 9, 2, 1.0 / C4, C4 * m)[0] for pid in range(n)])
+    assert abs(draws.mean() - m) < 5 * math.sqrt(C4 * m * m / n)
+    assert abs(draws.var() / (C4 * m * m) - 1.0) < 0.05
+    assert stats.kstest(draws, stats.gamma(a=1.0 / C4, scale=C4 * m).cdf).pvalue > 1e-3
+
+
+# --------------------------------------------------------------------------------------
+# Shapefunctions and tracking (Sect. 3.4, 3.6)
+# --------------------------------------------------------------------------------------
+
+@pytest.fixture(scope="module")
+def w2k():
+    return synth.workload("channel_2k")
+
+
+@pytest.fixture(scope="module")
+def orc2k(w2k):
+    return oracle.Oracle(w2k["grid"], w2k["params"], w2k["fields"])
+
+
+def _unwrapped_vertices(grid, e):
+    tri = grid.tri[e]
+    xy = grid.node_xy[tri].copy()
+    L = grid.period_x
+    for k in (1, 2):
+        d = xy[k, 0] - xy[0, 0]
+        if d > L / 2:
+            xy[k, 0] -= L
+        elif d < -L / 2:
+            xy[k, 0] += L
+    return xy
+
+
+def test_area_coordinates_vertices_and_sum(orc2k, w2k):
+    g = w2k["grid"]
+    rng = np.random.default_rng(0)
+    for e in rng.integers(0, g.ne, 200):
+        xy = _unwrapped_vertices(g, e)
+        for k in range(3):
+            lam = orc2k.lam(e, xy[k, 0] % g.period_x, xy[k, 1])
+            assert np.allclose(lam, np.eye(3)[k], atol=1e-12)
+        r = rng.dirichlet([1, 1, 1])
+        p = r @ xy
+        lam = orc2k.lam(e, p[0] % g.period_x, p[1])
+        assert abs(lam.sum() - 1.0) < 1e-14
+        assert np.allclose(lam, r, atol=1e-11)
+
+
+def test_linear_fields_interpolated_exactly(w2k):
+    g = w2k["grid"]
+    o = oracle.Oracle(g, w2k["params"])
+    # a field linear in y (x is periodic, so use y and constants only)
+    F = np.zeros((g.nn, 32))
+    F[:, 0] = 3.0 * g.node_xy[:, 1] - 1.0
+    F[:, 7] = 2.5
+    o.set_fields(F)
+    rng = np.random.default_rng(1)
+    for e in rng.integers(0, g.ne, 100):
+        xy = _unwrapped_vertices(g, e)
+        p = rng.dirichlet([1, 1, 1]) @ xy
+        q = o.interp(e, o.lam(e, p[0] % g.period_x, p[1]))
+        assert abs(q[0] - (3.0 * p[1] - 1.0)) < 1e-12
+        assert abs(q[7] - 2.5) < 1e-13
+
+
+def test_neighbors_symmetric(orc2k, w2k):
+    nb = orc2k.neighbors()
+    g = w2k["grid"]
+    for e in range(g.ne):
+        for k in range(3):
+            f = nb[e, k]
+            if f < 0:
+                assert g.edge_tag[e, k] != 0
+            else:
+                assert e in nb[f]
+                shared = set(g.tri[e]) & set(g.tri[f])
+                assert len(shared) == 2 and g.tri[e, k] not in shared
+
+
+def test_walk_equals_brute_force(orc2k, w2k):
+    """Sect. 3.6: the neighbour walk finds the element that brute force finds."""
+    g = w2k["grid"]
+    rng = np.random.default_rng(2)
+    hops_seen = []
+    for _ in range(3000):
+        e0 = int(rng.integers(0, g.ne))
+        xy = _unwrapped_vertices(g, e0)
+        c = xy.mean(0)
+        p = c + rng.normal(0, 0.05, 2)          # up to a few elements away, crosses the seam
+        p[1] = np.clip(p[1], 1e-9, 1 - 1e-9)
+        x = p[0] % g.period_x
+        e, hops = orc2k.walk(e0, x, p[1])
+        b = orc2k.brute(x, p[1])
+        assert b >= 0 and e >= 0
+        if e != b:
+            # only a point on a shared edge may be claimed by either element
+            assert orc2k.lam(e, x, p[1]).min() > -1e-12
+            assert orc2k.lam(b, x, p[1]).min() > -1e-12
+        hops_seen.append(hops)
+    assert max(hops_seen) < 64
+
+
+# --------------------------------------------------------------------------------------
+# Stochastic updates: closed forms of the Euler-Maruyama recursions
+# --------------------------------------------------------------------------------------
+
+def _homog_oracle(grid, params, fields):
+    o = oracle.Oracle(grid, params, fields)
+    return o
+
+
+def _middle(st, lo=0.2, hi=0.8):
+    return (st["y"] > lo) & (st["y"] < hi)
+
+
+@pytest.fixture(scope="module")
+def grid_small():
+    return synth.channel_grid(16, 9, seed=4)
+
+
+def test_glm_ornstein_uhlenbeck_transient(grid_small):
+    """Eq. 27 with constant coefficients: U' = (1 - a dt) U - dP dt + b sqrt(dt) xi.
+
+    Mean: m_n = -(dP/a) (1 - r^n); variance: s_n = r^{2n} s_0 + b^2/(a(2 - a dt)) (1 - r^{2n}),
+    r = 1 - a dt, a = (eps/2 - p)/k, b^2 = C0 eps.  (Ornstein-Uhlenbeck under Euler-Maruyama.)
+    """
+    k, Om, p_iso, C0, dt, n = 1.5e-4, 1.0, 0.0, 2.0, 0.05, 40
+    nu = 0.0
+    dPx = -0.01
+    F, eps = homogeneous_fields(grid_small, k, Om, nu, p_iso=p_iso, dP=(dPx, 0.0))
+    P = base_params(nu=nu, c0_mode=1, C0=C0, source_on=0, seed=21)
+    o = _homog_oracle(grid_small, P, F)
+    o.init_particles(400)
+    for _ in range(n):
+        o.step(dt)
+    st = o.get_particles()
+    m = _middle(st)
+    a = (eps / 2 - p_iso) / k
+    b2 = C0 * eps
+    r = 1 - a * dt
+    s0 = 2 * k / 3
+    var_n = r ** (2 * n) * s0 + b2 / (a * (2 - a * dt)) * (1 - r ** (2 * n))
+    mean_n = -(dPx / a) * (1 - r ** n)
+    N = int(m.sum())
+    assert N > 20000
+    for key, mexp in (("u", mean_n), ("v", 0.0), ("w", 0.0)):
+        vals = st[key][m]
+        assert abs(vals.mean() - mexp) < 5 * math.sqrt(var_n / N)
+        assert abs(vals.var() / var_n - 1) < 5 * math.sqrt(2.0 / N)
+
+
+def test_glm_shared_wiener_increment(grid_small):
+    """Eqs. 7 and 27 use the same dW: Cov(dU_x, dY) = 2 nu S dt, Var(dU_x) = 2 nu S^2 dt,
+    E[dU_x] = (-dP_x + 2 nu lap U_x) dt, E[dY] = V dt (one step, G = 0, C0 = 0)."""
+    k, Om, nu, dt, S = 1e-4, 1.0, 1e-3, 1e-2, 3.0
+    lapx, dPx = 0.7, -0.2
+    F, eps = homogeneous_fields(grid_small, k, Om, nu, grad=(0, S, 0, 0, 0, 0), lap=(lapx, 0, 0),
+                                dP=(dPx, 0.0))
+    P = base_params(nu=nu, c0_mode=1, C0=0.0, source_on=0, seed=22)
+    o = _homog_oracle(grid_small, P, F)
+    o.init_particles(300)
+    s0 = o.get_particles()
+    o.step(dt)
+    s1 = o.get_particles()
+    m = _middle(s0, 0.3, 0.7)
+    dU = (s1["u"] - s0["u"])[m]
+    dY = (s1["y"] - s0["y"] - s0["v"] * dt)[m]
+    N = dU.size
+    assert abs(dU.mean() - (-dPx + 2 * nu * lapx) * dt) < 5 * math.sqrt(2 * nu * S * S * dt / N)
+    assert abs(dU.var() / (2 * nu * S * S * dt) - 1) < 5 * math.sqrt(2.0 / N)
+    cov = np.mean((dU - dU.mean()) * (dY - dY.mean()))
+    assert abs(cov / (2 * nu * S * dt) - 1) < 5 * math.sqrt(2.0 / N)
+    assert abs(dY.var() / (2 * nu * dt) - 1) < 5 * math.sqrt(2.0 / N)
+    # v and w get no mean-gradient noise here
+    assert np.allclose(s1["v"][m], s0["v"][m], atol=1e-15)
+
+
+def test_position_viscous_diffusion(grid_small):
+    """Eq. 7 with U = 0: displacement has zero mean and variance 2 nu dt per component."""
+    nu, dt = 2e-4, 1e-2
+    F, _ = homogeneous_fields(grid_small, 1e-12, 1.0, nu)
+    P = base_params(nu=nu, c0_mode=1, C0=0.0, source_on=0, seed=23)
+    o = _homog_oracle(grid_small, P, F)
+    o.init_particles(300)
+    s0 = o.get_particles()
+    s0["u"][:] = 0
+    s0["v"][:] = 0
+    s0["w"][:] = 0
+    o.set_particles(s0, 0)
+    o.step(dt)
+    s1 = o.get_particles()
+    m = _middle(s0, 0.3, 0.7)
+    L = grid_small.period_x
+    dx = ((s1["x"] - s0["x"] + L / 2) % L - L / 2)[m]
+    dy = (s1["y"] - s0["y"])[m]
+    N = dx.size
+    sig2 = 2 * nu * dt
+    for d in (dx, dy):
+        assert abs(d.mean()) < 5 * math.sqrt(sig2 / N)
+        assert abs(d.var() / sig2 - 1) < 5 * math.sqrt(2.0 / N)
+
+
+def test_frequency_cir_stationary_gamma(grid_small):
+    """Eq. 19 with S_omega = 0 and constant <omega> = Om is a CIR process whose stationary
+    law is Gamma(1/C4, C4 Om); under Euler-Maruyama the stationary variance is
+    C4 Om^2 * 2 / (2 - C3 Om dt) and the mean is exactly Om."""
+    Om, dt, C3, C4 = 2.0, 1e-3, 5.0, 0.25
+    F, _ = homogeneous_fields(grid_small, 1e-4, Om, 0.0)
+    P = base_params(nu=0.0, c0_mode=1, C0=0.0, Cw1=0.0, Cw2=0.0, source_on=0, seed=24)
+    o = _homog_oracle(grid_small, P, F)
+    o.init_particles(80)
+    s = o.get_particles()
+    s["om"][:] = Om                      # start from a delta at the mean
+    s["u"][:] = 0
+    s["v"][:] = 0
+    s["w"][:] = 0
+    o.set_particles(s, 0)
+    for _ in range(400):                 # C3 Om t = 4: relaxation e^-4 of the transient
+        o.step(dt)
+    w = o.get_particles()["om"]
+    N = w.size
+    var_em = C4 * Om * Om * 2 / (2 - C3 * Om * dt)
+    trans = math.exp(-2 * C3 * Om * 400 * dt)
+    assert abs(w.mean() - Om) < 5 * math.sqrt(var_em / N)
+    assert abs(w.var() / var_em - 1) < 5 * math.sqrt(2.0 * 3 / N) + trans
+    assert stats.kstest(w, stats.gamma(a=1 / C4, scale=C4 * Om).cdf).pvalue > 1e-4
+
+
+def test_iecm_preserves_bin_means_and_decays_deviations(grid_small):
+    """Eq. 24 with constant t_m: within each conditioning bin of the previous statistics
+    the scalar mean is unchanged and every deviation from it shrinks by 1 - dt/t_m, with
+    1/t_m = C_phi eps / (2k) = C_phi Om / 2 (IEM/IECM mixing rate; nu = 0)."""
+    Om, dt, Cphi = 3.0, 1e-2, 2.0
+    F, _ = homogeneous_fields(grid_small, 1e-6, Om, 0.0)
+    P = base_params(nu=0.0, c0_mode=1, C0=0.0, tm_mode=1, Cphi=Cphi, source_on=0, seed=25,
+                    bins=(3, 2, 2), min_per_bin=3)
+    o = _homog_oracle(grid_small, P, F)
+    o.init_particles(60)
+    s0 = o.get_particles()
+    rng = np.random.default_rng(3)
+    s0["psi"] = rng.uniform(0, 1, s0["x"].size)
+    o.set_particles(s0, 5)
+    s0 = o.get_particles()
+    o.step(dt)
+    s1 = o.get_particles()
+    key = s0["elem"].astype(np.int64) * 256 + s0["cp"]
+    uniq, inv = np.unique(key, return_inverse=True)
+    cnt = np.bincount(inv)
+    mean0 = np.bincount(inv, s0["psi"]) / cnt
+    mean1 = np.bincount(inv, s1["psi"]) / cnt
+    assert np.allclose(mean1, mean0, rtol=0, atol=1e-14)
+    ratio = 1 - dt * Cphi * Om / 2
+    dev0 = s0["psi"] - mean0[inv]
+    dev1 = s1["psi"] - mean0[inv]
+    assert np.allclose(dev1, ratio * dev0, rtol=0, atol=1e-14)
+    # element totals of psi are conserved (Sect. 3.3 statistics, no source, no walls on psi)
+    e0 = np.bincount(s0["elem"], s0["psi"], minlength=grid_small.ne)
+    e1 = np.bincount(s0["elem"], s1["psi"], minlength=grid_small.ne)
+    assert np.allclose(e0, e1, atol=1e-12)
+
+
+def test_eq11_c0_dissipates_energy_at_rate_eps(grid_small):
+    """Eq. 11 (C0 from wp) makes the GLM consistent with dk/dt = -eps in homogeneous
+    turbulence without production, for any wp: per step E[dk] = -eps dt + O(dt^2)."""
+    k, Om, dt = 1.0, 1.0, 0.01
+    F, eps = homogeneous_fields(grid_small, k, Om, 0.0)
+    wp = np.array([[-0.6, 0.25, 0.0], [-0.1, -0.3, 0.05], [0.0, 0.15, -0.2]])   # anisotropic
+    F[:, 14:23] = wp.reshape(9)
+    P = base_params(nu=0.0, c0_mode=0, source_on=0, seed=27)
+    o = _homog_oracle(grid_small, P, F)
+    o.init_particles(800)
+    s0 = o.get_particles()
+    o.step(dt)
+    s1 = o.get_particles()
+    dk = 0.5 * ((s1["u"] ** 2 + s1["v"] ** 2 + s1["w"] ** 2) - (s0["u"] ** 2 + s0["v"] ** 2 + s0["w"] ** 2))
+    sel = _middle(s0, 0.05, 0.95)
+    dk = dk[sel]
+    G = (wp - 0.5 * eps * np.eye(3)) / k
+    Rs = np.cov(np.stack([s0[c][sel] for c in ("u", "v", "w")]))
+    second = 0.5 * dt * dt * np.trace(G @ Rs @ G.T)
+    # sample-covariance correction of the first-order term: tr(G (R_s - R)) dt
+    first = dt * np.trace(G @ (Rs - (2 * k / 3) * np.eye(3)))
+    assert abs(dk.mean() - (-eps * dt + first + second)) < 5 * dk.std() / math.sqrt(dk.size)
+    assert abs(dk.mean() / (-eps * dt) - 1) < 0.1
+
+
+def test_eq20_mean_frequency_source(grid_small):
+    """Eq. 19 averaged with <omega> = Om: E[omega'] = Om (1 - S_omega Om dt), and Eq. 20 makes
+    S_omega = C_w2 - C_w1 P / eps with production P = -<u v> dU/dy (the only shear here)."""
+    Om, dt, S, uv = 2.0, 1e-3, 4.0, -0.1
+    k = 1.0
+    F, eps = homogeneous_fields(grid_small, k, Om, 0.0, grad=(0, S, 0, 0, 0, 0))
+    F[:, 26] = uv
+    C3, Cw1, Cw2 = 5.0, 0.5, 0.73
+    P = base_params(nu=0.0, c0_mode=1, C0=0.0, source_on=0, seed=28, C3=C3, Cw1=Cw1, Cw2=Cw2)
+    o = _homog_oracle(grid_small, P, F)
+    o.init_particles(500)
+    s0 = o.get_particles()
+    s0["om"][:] = Om
+    s0["u"][:] = s0["v"][:] = s0["w"][:] = 0.0
+    o.set_particles(s0, 0)
+    o.step(dt)
+    w1 = o.get_particles()["om"]
+    prod = -uv * S
+    Sw = Cw2 - Cw1 * prod / eps
+    sd = math.sqrt(2 * C3 * 0.25 * Om ** 3 * dt)
+    assert abs(w1.mean() - Om * (1 - Sw * Om * dt)) < 5 * sd / math.sqrt(w1.size)
+    assert abs(w1.std() / sd - 1) < 0.02
+
+
+@pytest.mark.parametrize("case", ["no_mean_flow", "source_term"])
+def test_eq25_micromixing_time_limits(grid_small, case):
+    """Eq. 25 limits: with zero mean velocity the first argument is infinite, so
+    t_m = max(k/eps, C_T sqrt(nu/eps)) = 1/Om for nu = 0; with C_t = 0 and a large k/eps
+    it reduces to t_m = C_s (r0^2/eps)^(1/3).  Checked through the IECM decay ratio."""
+    Om, dt = 3.0, 1e-3
+    if case == "no_mean_flow":
+        k, U, Cs, Ct, r0 = 1e-6, (0.0, 0.0, 0.0), 0.02, 0.7, 0.02
+    else:
+        k, U, Cs, Ct, r0 = 1e4, (1e-3, 0.0, 0.0), 0.5, 0.0, 0.05
+    F, eps = homogeneous_fields(grid_small, k, Om, 0.0, U=U)
+    P = base_params(nu=0.0, c0_mode=1, C0=0.0, tm_mode=0, Cs=Cs, Ct=Ct, src_r=r0, source_on=0,
+                    seed=29, bins=(1, 1, 1), min_per_bin=1, C3=0.0, Cw1=0.0, Cw2=0.0)
+    o = _homog_oracle(grid_small, P, F)
+    o.init_particles(30)
+    s0 = o.get_particles()
+    rng = np.random.default_rng(5)
+    s0["psi"] = rng.uniform(0, 1, s0["x"].size)
+    s0["u"][:] = s0["v"][:] = s0["w"][:] = 0.0
+    o.set_particles(s0, 0)
+    s0 = o.get_particles()
+    o.step(dt)
+    s1 = o.get_particles()
+    mean0 = np.bincount(s0["elem"], s0["psi"]) / np.bincount(s0["elem"])
+    ratio = (s1["psi"] - mean0[s0["elem"]]) / (s0["psi"] - mean0[s0["elem"]])
+    tm = 1.0 / Om if case == "no_mean_flow" else Cs * (r0 * r0 / eps) ** (1.0 / 3.0)
+    assert np.allclose(ratio, 1 - dt / tm, rtol=1e-9)
+
+
+# --------------------------------------------------------------------------------------
+# Walls (Sect. 3.8)
+# --------------------------------------------------------------------------------------
+
+def test_wall_hit_probability_reflection_principle():
+    """Eqs. 53-55: a particle at distance d from the wall with only viscous diffusion hits
+    the wall during dt with probability P(d* < 0) + E[1{d* >= 0} f_w] = 2 Phi(-d/sigma),
+    sigma^2 = 2 nu dt (reflection principle).  Hit particles get U = 0 (Eq. 56) and a
+    gamma frequency with mean omega_w and variance C4 omega_w^2 (Eq. 58)."""
+    g = synth.channel_grid(40, 6, seed=5)
+    nu, dt, omw, C4 = 1e-3, 1e-3, 4.0, 0.25
+    sig = math.sqrt(2 * nu * dt)
+    F, _ = homogeneous_fields(g, 1e-12, 1.0, nu, omega_w=omw)
+    # C3 = C_w1 = C_w2 = 0 freezes Eq. 19, so only the wall condition changes omega
+    P = base_params(nu=nu, c0_mode=1, C0=0.0, C3=0.0, Cw1=0.0, Cw2=0.0, source_on=0, seed=26)
+    o = oracle.Oracle(g, P, F)
+    n = 30000
+    rng = np.random.default_rng(4)
+    for frac in (0.3, 1.0, 2.0):
+        d = frac * sig
+        x = rng.uniform(0, g.period_x, n)
+        y = np.full(n, d)
+        elem = np.array([o.brute(xi, d) for xi in x], dtype=np.int32)
+        st = dict(x=x, y=y, u=np.zeros(n), v=np.zeros(n), w=np.zeros(n), om=np.ones(n),
+                  psi=np.zeros(n), elem=elem)
+        o.set_particles(st, 1)
+        o.reset_diag()
+        o.step(dt)
+        dg = o.diag()
+        s1 = o.get_particles()
+        expected = 2 * stats.norm.cdf(-frac)
+        frac_hit = dg["wall_hits"] / n
+        assert abs(frac_hit - expected) < 5 * math.sqrt(expected * (1 - expected) / n)
+        assert abs(dg["wall_hits_a"] / n - expected / 2) < 5 * math.sqrt(expected / 2 / n)
+        assert s1["y"].min() >= 0.0
+        hit = s1["om"] != 1.0                  # frequency was resampled by the wall condition
+        assert hit.sum() == dg["wall_hits"]
+        assert np.all(s1["u"][hit] == 0) and np.all(s1["v"][hit] == 0)
+        if frac == 0.3:
+            wv = s1["om"][hit]
+            assert stats.kstest(wv, stats.gamma(a=1 / C4, scale=C4 * omw).cdf).pvalue > 1e-3
+
+
+# --------------------------------------------------------------------------------------
+# Binning (Sect. 3.5, Appendix A)
+# --------------------------------------------------------------------------------------
+
+def _bin_setup(counts, bins, mpb, seed=8):
+    g = synth.channel_grid(8, 5, seed=6)
+    F, _ = homogeneous_fields(g, 1e-4, 1.0, 0.0)
+    P = base_params(nu=0.0, bins=bins, min_per_bin=mpb, source_on=0, seed=seed)
+    o = oracle.Oracle(g, P, F)
+    rng = np.random.default_rng(seed)
+    xs, ys, es = [], [], []
+    for e, c in enumerate(counts):
+        xy = _unwrapped_vertices(g, e)
+        for _ in range(c):
+            p = rng.dirichlet([1, 1, 1]) @ xy
+            xs.append(p[0] % g.period_x)
+            ys.append(p[1])
+            es.append(e)
+    n = len(xs)
+    st = dict(x=np.array(xs), y=np.array(ys), u=rng.normal(size=n), v=rng.normal(size=n),
+              w=rng.normal(size=n), om=np.ones(n), psi=rng.uniform(size=n),
+              elem=np.array(es, dtype=np.int32))
+    # a few exact ties, as after no-slip wall hits
+    st["u"][::7] = 0.0
+    o.set_particles(st, 0)
+    return g, o, st
+
+
+def test_binning_worked_example():
+    row = [l.split() for l in open(os.path.join(GOLDEN, "binning_worked_example.txt"))
+           if l.strip() and not l.startswith("#")][0]
+    N, b1, b2, b3, mpb, g1, g2, g3 = map(int, row)
+    counts = [N] + [40] * 63
+    g, o, st = _bin_setup(counts, (b1, b2, b3), mpb)
+    v, gb = o.bins()
+    assert tuple(gb[0]) == (g1, g2, g3)
+    s = o.get_particles()
+    idx = np.where(s["elem"] == 0)[0]
+    order = sorted(idx, key=lambda p: (s["u"][p], p))
+    # two groups of sizes 3 and 2 (Appendix A, i = 2 n / 5), the lower u in group 0
+    assert [int(s["cp"][p]) for p in order] == [0, 0, 0, 1, 1]
+    assert abs(v[0, 0] - s["psi"][order[:3]].mean()) < 1e-15
+    assert abs(v[0, 1] - s["psi"][order[3:]].mean()) < 1e-15
+
+
+def test_binning_uniform_counts_effective_bins():
+    # 5x5x5 bins, at least 2 per bin: 150 -> 5*5*3 = 75, 300 -> 125, 1 -> 1, 9 -> 4*1*1
+    counts = [150, 300, 1, 9, 0] + [20] * 59
+    g, o, _ = _bin_setup(counts, (5, 5, 5), 2)
+    _, gb = o.bins()
+    assert tuple(gb[0]) == (5, 5, 3)
+    assert tuple(gb[1]) == (5, 5, 5)
+    assert tuple(gb[2]) == (1, 1, 1)
+    assert tuple(gb[3]) == (4, 1, 1)
+    assert tuple(gb[4]) == (1, 1, 1)
+
+
+@pytest.mark.parametrize("bins,mpb", [((4, 4, 4), 2), ((3, 2, 5), 3), ((1, 4, 2), 2)])
+def test_binning_characterisation(bins, mpb):
+    """Sect. 3.5: bins are as equal in size as possible (App. A sizes), each holds at least
+    min_per_bin particles, and bins are nested: level-1 groups are ordered by (u, id),
+    inside them level-2 groups by (v, id), inside those the bins by (w, id).  The
+    conditional mean of a bin is the mean scalar of its members."""
+    rng = np.random.default_rng(9)
+    counts = list(rng.integers(0, 130, 64))
+    g, o, _ = _bin_setup(counts, bins, mpb)
+    s = o.get_particles()
+    v, gb = o.bins()
+    for e in range(g.ne):
+        idx = np.where(s["elem"] == e)[0]
+        N = idx.size
+        g1, g2, g3 = gb[e]
+        G = g1 * g2 * g3
+        assert G * mpb <= max(N, mpb)
+        if N == 0:
+            continue
+        cp = s["cp"][idx].astype(int)
+        sizes = np.bincount(cp, minlength=G)
+        assert sizes.size == G
+        expect = np.bincount((G * np.arange(N)) // N, minlength=G)
+        assert np.array_equal(sizes, expect)
+        if N >= mpb:
+            assert sizes.min() >= mpb
+        lvl1, lvl2 = cp // (g2 * g3), cp // g3
+        for a, b in ((lvl1, None), (lvl2, lvl1), (cp, lvl2)):
+            key = {id(lvl1): "u", id(lvl2): "v", id(cp): "w"}[id(a)]
+            for grp in (np.unique(b) if b is not None else [None]):
+                sel = np.ones(N, bool) if grp is None else (b == grp)
+                sub_a = a[sel]
+                vals = s[key][idx][sel]
+                ids = idx[sel]
+                for i in np.unique(sub_a)[:-1]:
+                    lo = max(zip(vals[sub_a == i], ids[sub_a == i]))
+                    hi = min(zip(vals[sub_a > i], ids[sub_a > i]))
+                    assert lo < hi
+        means = np.bincount(cp, s["psi"][idx], minlength=G) / sizes
+        assert np.allclose(v[e, :G], means, rtol=0, atol=1e-15)
+
+
+# --------------------------------------------------------------------------------------
+# Statistics (Sect. 3.3)
+# --------------------------------------------------------------------------------------
+
+def test_element_and_nodal_moments_definition():
+    g, o, st = _bin_setup([50] * 30 + [0] * 2 + [1] + [50] * 31, (2, 2, 2), 2, seed=12)
+    s = o.get_particles()
+    em, cnt = o.element_stats()
+    nm = o.nodal_stats()
+    e = s["elem"]
+    N = np.bincount(e, minlength=g.ne)
+    assert np.array_equal(cnt, N)
+    safe = np.maximum(N, 1)
+    cols = {}
+    for i, k in enumerate(("u", "v", "w")):
+        cols[k] = np.bincount(e, s[k], minlength=g.ne) / safe
+        assert np.allclose(em[:, 1 + i], cols[k], atol=1e-14)
+    pairs = [("u", "u"), ("v", "v"), ("w", "w"), ("u", "v"), ("u", "w"), ("v", "w")]
+    for j, (a, b) in enumerate(pairs):
+        c = np.bincount(e, (s[a] - cols[a][e]) * (s[b] - cols[b][e]), minlength=g.ne) / safe
+        assert np.allclose(em[:, 4 + j], c, atol=1e-14)
+    mp = np.bincount(e, s["psi"], minlength=g.ne) / safe
+    assert np.allclose(em[:, 11], mp, atol=1e-14)
+    assert np.allclose(em[:, 12], np.bincount(e, (s["psi"] - mp[e]) ** 2, minlength=g.ne) / safe,
+                       atol=1e-14)
+    assert em[32, 4] == 0.0 and em[32, 0] == 1.0          # one particle: zero variance
+    # nodes: plain mean over surrounding non-empty elements
+    for n in range(g.nn):
+        es = [k for k in range(g.ne) if n in g.tri[k] and N[k] > 0]
+        if es:
+            assert np.allclose(nm[n], em[es].mean(0), atol=1e-14)
+        else:
+            assert np.all(nm[n] == 0)
+
+
+def test_moments_closed_form_two_values():
+    g = synth.channel_grid(8, 5, seed=6)
+    F, _ = homogeneous_fields(g, 1e-4, 1.0, 0.0)
+    o = oracle.Oracle(g, base_params(nu=0.0, source_on=0), F)
+    xy = _unwrapped_vertices(g, 3).mean(0)
+    n = 4
+    st = dict(x=np.full(n, xy[0] % g.period_x), y=np.full(n, xy[1]), u=np.array([1.0, -1.0, 1.0, -1.0]),
+              v=np.array([2.0, 2.0, 0.0, 0.0]), w=np.zeros(n), om=np.array([1.0, 3.0, 1.0, 3.0]),
+              psi=np.array([0.0, 1.0, 1.0, 0.0]), elem=np.full(n, 3, dtype=np.int32))
+    o.set_particles(st, 0)
+    em, _ = o.element_stats()
+    # N, U, V, W, uu, vv, ww, uv, uw, vw, omega, phi, phi'^2
+    assert np.allclose(em[3], [4, 0, 1, 0, 1, 1, 0, 0, 0, 0, 2, 0.5, 0.25], atol=1e-15)
+
+
+# --------------------------------------------------------------------------------------
+# Particle-number control (Sect. 3.7, Appendix B)
+# --------------------------------------------------------------------------------------
+
+@pytest.mark.parametrize("seed", [0, 1, 2, 3])
+def test_redistribution_counts_properties(seed):
+    rng = np.random.default_rng(seed)
+    ne = 300
+    counts = rng.integers(0, 60, ne).astype(np.int32)
+    counts[rng.integers(0, ne, 20)] = rng.integers(100, 400, 20)
+    minnpel = 25
+    fin, moves = oracle.redistribution_counts(counts, minnpel)
+    assert fin.sum() == counts.sum()
+    deficit = np.maximum(minnpel - counts, 0)
+    # feasible here: min reaches MINNPEL with exactly the deficit moved, one particle each
+    assert fin.min() >= minnpel
+    assert moves == deficit.sum()
+    gain = fin - counts
+    assert np.all(gain[counts >= minnpel] <= 0)          # only deficient elements receive
+    assert np.all(fin[gain > 0] == minnpel)              # ...and only up to the threshold
+    # donors are drained from the top: every donor ends at the same level or one above
+    donors = gain < 0
+    top = fin[donors]
+    assert top.max() - top.min() <= 1
+    assert np.all(counts[~donors & (gain == 0)] <= top.max())
+
+
+def test_redistribution_infeasible_levels_out():
+    counts = np.array([0, 0, 1, 10, 3], dtype=np.int32)
+    fin, moves = oracle.redistribution_counts(counts, 100)
+    assert fin.sum() == counts.sum()
+    assert fin.max() - fin.min() <= 1
+    fin2, moves2 = oracle.redistribution_counts(counts, 0)
+    assert moves2 == 0 and np.array_equal(fin2, counts)
+
+
+def test_redistribution_moves_particles():
+    g = synth.channel_grid(8, 5, seed=6)
+    F, _ = homogeneous_fields(g, 1e-4, 1.0, 0.0)
+    counts = [40] * 64
+    counts[5] = 0
+    counts[9] = 2
+    counts[20] = 140
+    g, o, st = _bin_setup(counts, (2, 2, 2), 2, seed=13)
+    o.set_params(base_params(nu=0.0, bins=(2, 2, 2), min_per_bin=2, source_on=0, seed=13,
+                             minnpel=10, period_x=g.period_x))
+    o.set_fields(F)
+    s0 = o.get_particles()
+    o.advance(1e-9)
+    s_adv = o.get_particles()
+    T = o.redistribute()
+    s1 = o.get_particles()
+    assert T == 18
+    moved = np.where(s1["elem"] != s_adv["elem"])[0]
+    assert moved.size == T
+    # movers come from the donor (the fullest element), highest particle ids first
+    donor_ids = np.where(s_adv["elem"] == 20)[0]
+    assert set(moved) == set(np.sort(donor_ids)[-T:])
+    for p in moved:
+        r = s1["elem"][p]
+        assert r in (5, 9)
+        assert o.brute(s1["x"][p], s1["y"][p]) == r or o.lam(r, s1["x"][p], s1["y"][p]).min() > -1e-12
+        src = r if counts[r] > 0 else None
+        res = np.where(s_adv["elem"] == (src if src is not None else -1))[0]
+        if src is not None:
+            match = (s_adv["u"][res] == s1["u"][p]) & (s_adv["om"][res] == s1["om"][p])
+            assert match.any()
+    fin = np.bincount(s1["elem"], minlength=g.ne)
+    assert fin[5] == 10 and fin[9] == 10
+
+
+# --------------------------------------------------------------------------------------
+# Whole step on the channel workload
+# --------------------------------------------------------------------------------------
+
+def test_step_tracking_and_domain(w2k):
+    o = oracle.Oracle(w2k["grid"], w2k["params"], w2k["fields"])
+    o.init_particles(20)
+    s0 = o.get_particles()
+    n0 = s0["x"].size
+    for _ in range(3):
+        o.step(w2k["dt"])
+    s = o.get_particles()
+    assert s["x"].size == n0
+    assert s["y"].min() >= 0 and s["y"].max() <= 1
+    assert s["x"].min() >= 0 and s["x"].max() < w2k["grid"].period_x
+    rng = np.random.default_rng(5)
+    for p in rng.integers(0, n0, 2000):
+        e = s["elem"][p]
+        assert o.lam(e, s["x"][p], s["y"][p]).min() >= -1e-12
+    d = o.diag()
+    assert d["lost"] == 0 and d["walk_brute"] == 0
+    for k in ("u", "v", "w", "om", "psi"):
+        assert np.all(np.isfinite(s[k]))
+
+
+def test_init_particles_distribution(w2k):
+    o = oracle.Oracle(w2k["grid"], w2k["params"], w2k["fields"])
+    o.init_particles(30)
+    s = o.get_particles()
+    ne = w2k["grid"].ne
+    assert np.array_equal(np.bincount(s["elem"], minlength=ne), np.full(ne, 30))
+    for p in range(0, s["x"].size, 97):
+        assert o.lam(s["elem"][p], s["x"][p], s["y"][p]).min() >= -1e-12
+    # standardised velocity fluctuations about the local mean: N(0,1)
+    z = []
+    for p in range(0, s["x"].size, 3):
+        e = s["elem"][p]
+        q = o.interp(e, o.lam(e, s["x"][p], s["y"][p]))
+        k = 0.5 * (q[23] + q[24] + q[25])
+        z.append((s["u"][p] - q[0]) / math.sqrt(2 * k / 3))
+        z.append(s["om"][p] / q[29])
+    z = np.array(z)
+    zu, zo = z[0::2], z[1::2]
+    assert stats.kstest(zu, "norm").pvalue > 1e-3
+    assert stats.kstest(zo, stats.gamma(a=4, scale=0.25).cdf).pvalue > 1e-3
+    psi_in = (((s["x"] - 0.5) ** 2 + (s["y"] - 0.5) ** 2) <= 0.02 ** 2)
+    assert np.array_equal(s["psi"] == 1.0, psi_in)
