@@ -1,0 +1,319 @@
+"""Benchmark: particle-updates per second of the full particle timestep on GB300.
+
+One step = one pass of the whole particle path (advance and track, particle-number
+control, statistics, conditional-mean binning, nodal averages) over all particles of the
+workload: the 50,000-triangle wall-graded channel at 500 particles per element (25.0M
+particles), synthetic seeded inputs.  The FP32 form (FP32 state and SDE arithmetic, FP64
+statistics) is the headline; the plain FP64 form is measured on the same GPU beside it.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pdfx|reference]
+
+With N > 1 (torchrun), every rank steps its own independent instance (its own Philox
+instance id): weak scaling with no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "particle-updates/sec per full PDF timestep, FP32/batched vs FP64, same GPU"
+UNIT = "particle-updates/s"
+# Algorithmic bytes per particle of the advance kernel (read x,y,u,v,w,omega,psi, elem,
+# cp; write x,y,u,v,w,omega,psi, elem): 4*7+4+1+4*7+4 in FP32, 8*7+4+1+8*7+4 in FP64.
+ADV_BYTES = {1: 65, 0: 121}
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def __enter__(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        return self
+
+    def __exit__(self, *a):
+        if self.p is not None:
+            self.p.terminate()
+            try:
+                self.p.wait(timeout=5)
+            except Exception:
+                self.p.kill()
+
+    def summary(self):
+        try:
+            self.f.flush()
+            rows = [l.strip().split(", ") for l in open(self.f.name) if l.strip()]
+        except Exception:
+            rows = []
+        finally:
+            try:
+                os.unlink(self.f.name)
+            except Exception:
+                pass
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+                for nm, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(nm)
+            except Exception:
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def oracle_sample(workload_name: str, steps: int, ppe: int):
+    """The oracle as it stands (one host thread) on a bounded sample of the workload."""
+    import oracle
+    from paper_1006_0532_gb300 import synth
+
+    w = synth.workload(workload_name)
+    o = oracle.Oracle(w["grid"], w["params"], w["fields"])
+    o.init_particles(ppe)
+    n = o.np_
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step(w["dt"])
+    dt = time.perf_counter() - t0
+    return n, steps, dt, w
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    ppe = args.oracle_ppe
+    from paper_1006_0532_gb300 import synth
+    w = synth.workload(args.workload)
+    import oracle
+    o = oracle.Oracle(w["grid"], w["params"], w["fields"])
+    o.init_particles(ppe)
+    n = o.np_
+    for _ in range(args.warmup):
+        o.step(w["dt"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step(w["dt"])
+    el = time.perf_counter() - t0
+    v = n * args.steps / el
+    sample = "%s grid (%d triangles) at %d particles per element (%d particles), %d steps" % (
+        args.workload, w["grid"].ne, ppe, n, args.steps)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": args.workload, "particles": n,
+                                            "triangles": w["grid"].ne, "ppe": ppe},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def make_ctx(B, w, precision, instance, sort_every):
+    p = dict(w["params"], precision=precision, sort_every=sort_every, instance=instance)
+    c = B.Context(p)
+    c.set_grid(w["grid"])
+    c.set_fields(w["fields"])
+    c.init_particles(w["ppe"])
+    return c
+
+
+def time_form(torch, B, w, precision, args, rank, world, dist, with_clock):
+    """Device time of K steps of one form (inputs resident in HBM)."""
+    c = make_ctx(B, w, precision, rank, args.sort_every)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        c.step(w["dt"])
+    torch.cuda.synchronize()
+    c.set_profiling(True)
+    c.stage_times()
+    l0 = c.kernel_launches
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    sampler = ClockSampler(torch.cuda.current_device()) if with_clock else None
+    if sampler:
+        sampler.__enter__()
+    ev0.record(stream)
+    for _ in range(args.steps):
+        c.step(w["dt"])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.__exit__()
+    ms = ev0.elapsed_time(ev1)
+    launches = c.kernel_launches - l0
+    stage_ms, stage_n = c.stage_times()
+    c.set_profiling(False)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+        if dist.get_rank() != 0:
+            pass
+    err = c.check()
+    diag = c.diag()
+    np_ = c.np_
+    out = dict(ms=ms, launches=launches, stage_ms=stage_ms, stage_n=stage_n, np=np_, err=err,
+               diag=diag, clocks=sampler.summary() if sampler else None)
+    return c, out
+
+
+def e2e_form(torch, B, c, w, args):
+    """Same metric through the C ABI with host buffers: per step, the nodal fields go
+    host -> device from pinned memory, the step runs, the nodal statistics come back."""
+    import numpy as np
+    nn = w["grid"].nn
+    f_host = torch.from_numpy(np.ascontiguousarray(w["fields"])).pin_memory()
+    s_host = torch.empty((nn, 13), dtype=torch.float64).pin_memory()
+    for _ in range(2):
+        c.set_fields(f_host.numpy())
+        c.step(w["dt"])
+        c.nodal_stats(s_host.numpy())
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        c.set_fields(f_host.numpy())
+        c.step(w["dt"])
+        c.nodal_stats(s_host.numpy())
+    el = time.perf_counter() - t0
+    return el, nn * 32 * 8, nn * 13 * 8
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="pdfx", choices=["pdfx", "reference"])
+    ap.add_argument("--workload", default="channel_50k")
+    ap.add_argument("--sort-every", type=int, default=8)
+    ap.add_argument("--oracle-ppe", type=int, default=40)
+    ap.add_argument("--oracle-steps", type=int, default=2)
+    ap.add_argument("--no-f64", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_env()
+
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    from paper_1006_0532_gb300 import _binding as B
+    from paper_1006_0532_gb300 import synth
+    w = synth.workload(args.workload)
+
+    c32, r32 = time_form(torch, B, w, 1, args, rank, world, dist, with_clock=True)
+    e2e_s, h2d, d2h = e2e_form(torch, B, c32, w, args)
+    c32.close()
+    r64 = None
+    if not args.no_f64:
+        c64, r64 = time_form(torch, B, w, 0, args, rank, world, dist, with_clock=False)
+        c64.close()
+    if dist is not None:
+        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    np_ = r32["np"]
+    value = np_ * world * args.steps / (r32["ms"] * 1e-3)
+    peak, peak_kind = peaks()
+    adv_ms = r32["stage_ms"][0] / max(r32["stage_n"][0], 1)
+    achieved = ADV_BYTES[1] * np_ / (adv_ms * 1e-3) / 1e9
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r32["ms"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": args.workload, "triangles": w["grid"].ne, "nodes": w["grid"].nn,
+                   "particles_per_gpu": np_, "ppe": w["ppe"], "dt": w["dt"],
+                   "form": "FP32 state and SDE arithmetic, FP64 statistics",
+                   "l2": "particle state (%.2f GB) larger than L2; grid and fields L2-resident"
+                         % (np_ * 37 / 1e9),
+                   "sort_every": args.sort_every, "parallelism": "independent instance per GPU"},
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": "advance_kernel<float>",
+                     "peak_source": peak_kind, "ms_per_launch": adv_ms},
+        "stages_ms_per_step": {n: r32["stage_ms"][i] / max(r32["stage_n"][i], 1) for i, n in enumerate(
+            ["advance", "plan", "lists", "redistribute", "statistics_binning", "node_average"])},
+        "gpu_launches": r32["launches"],
+        "e2e": {"value": np_ * world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+                "d2h_bytes_per_step": d2h},
+        "clocks": r32["clocks"],
+        "device_errors": r32["err"],
+    }
+    if r64 is not None:
+        v64 = r64["np"] * world * args.steps / (r64["ms"] * 1e-3)
+        line["f64_form"] = {"value": v64, "ms_per_step": r64["ms"] / args.steps,
+                            "stages_ms_per_step": {n: r64["stage_ms"][i] / max(r64["stage_n"][i], 1)
+                                                   for i, n in enumerate(["advance", "plan", "lists",
+                                                                          "redistribute",
+                                                                          "statistics_binning",
+                                                                          "node_average"])},
+                            "device_errors": r64["err"]}
+        line["speedup_f32_vs_f64"] = value / v64
+    if not args.no_cpu:
+        n, st, el, _ = oracle_sample(args.workload, args.oracle_steps, args.oracle_ppe)
+        line["cpu_baseline"] = {"value": n * st / el, "unit": UNIT, "cores": 1, "kind": "oracle",
+                                "sample": "%s grid at %d particles per element (%d particles), %d steps"
+                                          % (args.workload, args.oracle_ppe, n, st)}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,204 @@
+/*
+ * pdfx -- one timestep of the particle path of the non-hybrid PDF method for turbulent
+ * flows on unstructured triangle grids (Bakosi, Franzese & Boybeyi), on one GB300 GPU.
+ *
+ * One call of pdfx_step advances every Lagrangian particle by one explicit Euler-Maruyama
+ * step (Sect. 3.1): it interpolates the nodal Eulerian fields with linear shapefunctions
+ * (Eqs. 37-38), updates position (Eq. 7), velocity (Eq. 27, the generalised Langevin
+ * model with the elliptic-relaxation closure of Eq. 11), turbulent frequency (Eqs. 18-20)
+ * and passive scalar (IECM, Eqs. 24-25), applies the wall conditions (Eqs. 53-58) and the
+ * scalar source (Sect. 4.1.2), tracks the particle to its new element (Sect. 3.6),
+ * redistributes particles to keep every element above a minimum count (Sect. 3.7,
+ * Appendix B), and recomputes the element and nodal statistics (Sect. 3.3, Eqs. 34-36)
+ * and the velocity-conditioned scalar means used by the next step (Sect. 3.5, Appendix A).
+ *
+ * Conventions for every call:
+ *  - Return value: PDFX_OK (0) or a negative PDFX_ERR_* code.  No exception crosses this
+ *    boundary.  pdfx_strerror() names a code.
+ *  - Device work is enqueued on the caller's CUDA stream (a cudaStream_t passed as void*,
+ *    NULL = the legacy default stream) and is asynchronous unless a call says otherwise.
+ *    Problems found on the device (a particle found in no element, an element above the
+ *    per-element capacity, a non-finite state) set a device error word; it is read by
+ *    pdfx_get_diag() and pdfx_check(), which synchronise the stream.
+ *  - Pointers marked "host" are read or written before the call returns.  Pointers marked
+ *    "device" must stay valid until the stream has executed the call.  The caller owns
+ *    every buffer it passes; the library copies what it keeps.
+ *  - Device memory of a context comes from the allocator given to pdfx_create (or
+ *    cudaMalloc when none is given) and is released by pdfx_destroy.
+ *  - A context is used by one host thread at a time.
+ */
+#ifndef PDFX_H
+#define PDFX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PDFX_OK                 0
+#define PDFX_ERR_ARG           -1   /* invalid argument or parameter */
+#define PDFX_ERR_MESH          -2   /* invalid grid: bad index, non-positive area, open edge */
+#define PDFX_ERR_ORDER         -3   /* call made before the state it needs exists */
+#define PDFX_ERR_CUDA          -4   /* a CUDA runtime call failed */
+#define PDFX_ERR_ALLOC         -5   /* device allocation failed */
+#define PDFX_ERR_LOST_PARTICLE -6   /* a particle was found in no element (device word) */
+#define PDFX_ERR_CAPACITY      -7   /* an element exceeded PDFX_MAX_PER_ELEMENT (device word) */
+#define PDFX_ERR_NONFINITE     -8   /* a particle state became NaN or infinite (device word) */
+
+#define PDFX_NF 32                  /* nodal field slots, layout below */
+#define PDFX_NSTAT 13               /* statistics per element or node, layout below */
+#define PDFX_MAX_PER_ELEMENT 4096   /* particles one element may hold for the binning */
+
+/*
+ * Nodal field layout, [nn][32] FP64 (pdfx_set_fields):
+ *   0-2   <U_i>                         3-4   d<P>/dx_j (rho = 1), j = x, y
+ *   5-10  d<U_i>/dx_j, i-major, j = x, y
+ *   11-13 laplacian of <U_i>            14-22 elliptic-relaxation tensor wp_ij, row-major
+ *   23-28 <u_i u_j>: xx, yy, zz, xy, xz, yz
+ *   29    <omega>                       30    omega_w, the Eq. 58 wall frequency mean
+ *   31    unused
+ * Statistics layout, [.][13] FP64: N, <U>, <V>, <W>, <uu>, <vv>, <ww>, <uv>, <uw>, <vw>,
+ *   <omega>, <phi>, <phi'^2>.  For an element N is its particle count; for a node it is
+ *   the mean count of the surrounding elements that hold particles.
+ */
+
+typedef struct pdfx_params {
+    /* Table 4 of the paper */
+    double C1, C2, C3, C4, CT, CL, Ceta, Cv, gamma5, Cw1, Cw2;
+    double nu;                /* kinematic viscosity */
+    int    c0_mode;           /* 0: C0 from Eq. 11; 1: the constant C0 below */
+    double C0;
+    int    tm_mode;           /* 0: t_m from Eq. 25; 1: t_m = 2k / (Cphi eps) */
+    double Cs, Ct, Cphi;      /* Eq. 25 constants (Sect. 4.1.2: 0.02, 0.7) and IEM constant */
+    double src_x, src_y, src_r; /* source disc: particles inside get psi = 1 */
+    int    bins[3];           /* requested conditioning bins per velocity component, 1..16 */
+    int    min_per_bin;       /* fewest particles a conditioning bin may hold (>= 1) */
+    int    minnpel;           /* Appendix B threshold MINNPEL; 0 disables redistribution */
+    int    interp_mode;       /* 0: shapefunctions at the particle; 1: element average */
+    int    source_on;         /* 1: apply the source disc */
+    uint64_t seed;            /* Philox key = (seed low word, seed high word ^ instance) */
+    uint32_t instance;
+    double period_x;          /* period of the x direction; 0 = not periodic */
+    /* GPU form, fixed at pdfx_create */
+    int    precision;         /* 0: FP64 state and arithmetic; 1: FP32 state and SDE
+                                 arithmetic with FP64 statistics and conditional means */
+    int    sort_every;        /* re-order particles by element every this many steps */
+} pdfx_params;
+
+typedef struct pdfx_allocator {
+    void *(*alloc)(size_t bytes, void *user);            /* returns device memory or NULL */
+    void  (*release)(void *ptr, size_t bytes, void *user);
+    void  *user;
+} pdfx_allocator;
+
+/* Particle state by particle id, FP64 values (converted for the FP32 form). */
+typedef struct pdfx_soa {
+    double  *x, *y, *u, *v, *w, *om, *psi;   /* [np] */
+    int32_t *elem;                            /* [np] host element */
+    uint8_t *cp;                              /* [np] conditioning pointer (get only) */
+} pdfx_soa;
+
+typedef struct pdfx_diag {
+    int64_t steps;
+    int64_t hops_total, walk_fallback, walk_brute, lost;
+    int64_t wall_hits, freeslip_hits, omega_reflect, c0_clamp, gamma_exhausted;
+    int64_t moves, source_hits, capacity_overflow, nonfinite;
+    int64_t hop_hist[8];      /* particles that needed 0, 1, ..., 6, 7+ hops */
+    int32_t error;            /* first device error code seen (PDFX_ERR_*), 0 if none */
+} pdfx_diag;
+
+/* Defaults: Table 4 constants, Cs = 0.02, Ct = 0.7 (Sect. 4.1.2), C0 from Eq. 11,
+ * t_m from Eq. 25, (4, 4, 4) bins with at least 2 particles, FP64 form, re-order every 8
+ * steps.  Host: writes *p. */
+void pdfx_default_params(pdfx_params *p);
+
+/* Creates a context.  p: host, copied.  alloc: host, copied, may be NULL (cudaMalloc).
+ * The current CUDA device is the context's device.  PDFX_ERR_ARG for invalid params. */
+int  pdfx_create(const pdfx_params *p, const pdfx_allocator *alloc, void **out_ctx);
+
+/* Releases all device memory of the context (synchronises the device first). */
+void pdfx_destroy(void *ctx);
+
+/* Replaces the model parameters (everything except bins, precision and sort_every, which
+ * are fixed at creation).  Host pointer.  PDFX_ERR_ARG if those differ. */
+int  pdfx_set_params(void *ctx, const pdfx_params *p);
+
+/* Sets the Eulerian grid (Sect. 3.3, Fig. 1): nn nodes node_xy[nn][2] (FP64, host),
+ * ne counter-clockwise triangles tri[ne][3] (int32 node ids, host) and edge tags
+ * edge_tag[ne][3] (int8, host) for the edge opposite local vertex k: 0 interior,
+ * 1 no-slip wall (Sect. 3.8), 2 free-slip boundary (Sect. 4.2).  With period_x > 0, x is
+ * periodic and a triangle may span the seam (its vertices are taken as minimum images).
+ * Builds element geometry (Eq. 40), neighbours across each edge and node-to-element lists
+ * (Sect. 3.6).  Synchronous.  PDFX_ERR_MESH for a bad index, a non-positive area or an
+ * edge that is neither shared nor tagged.  Discards particles. */
+int  pdfx_set_grid(void *ctx, int32_t nn, const double *node_xy, int32_t ne,
+                   const int32_t *tri, const int8_t *edge_tag);
+
+/* Sets the nodal fields [nn][32] (layout above), FP64, host (on_device = 0) or device
+ * (on_device = 1) memory, enqueued on stream.  PDFX_ERR_ORDER before pdfx_set_grid. */
+int  pdfx_set_fields(void *ctx, const double *fields, int on_device, void *stream);
+
+/* Sect. 3.7: ppe particles per element, uniform in the element; velocity Gaussian about
+ * the local mean with variance 2k/3 per component; frequency gamma with the local mean
+ * and variance C4 <omega>^2; psi = 1 inside the source, else 0.  Particle id =
+ * element * ppe + k.  Then computes the statistics and conditional means.  Resets the
+ * step counter to 0.  PDFX_ERR_ORDER without grid and fields. */
+int  pdfx_init_particles(void *ctx, int32_t ppe, void *stream);
+
+/* Replaces the particle state by np particles with ids 0..np-1 (FP64 arrays of s, host
+ * or device per on_device; cp is ignored) and sets the step counter.  Computes the
+ * statistics and conditional means of that state.  Synchronous for host input. */
+int  pdfx_set_particles(void *ctx, int64_t np, const pdfx_soa *s, uint32_t step,
+                        int on_device, void *stream);
+
+/* Writes the particle state by particle id into the caller's arrays of s (any pointer may
+ * be NULL to skip it), host or device memory.  Synchronous for host output. */
+int  pdfx_get_particles(void *ctx, pdfx_soa *s, int on_device, void *stream);
+
+/* Number of particles (0 before initialisation). */
+int64_t pdfx_num_particles(const void *ctx);
+
+/* Step counter (the Philox counter word of the next step). */
+uint32_t pdfx_step_index(const void *ctx);
+
+/* One timestep of fixed size dt > 0 (Table 1 order restricted to the particle path):
+ * advance and track every particle, particle-number control, statistics and conditional
+ * means.  Asynchronous on stream.  PDFX_ERR_ORDER without particles and fields. */
+int  pdfx_step(void *ctx, double dt, void *stream);
+
+/* Nodal statistics [nn][13] and element statistics [ne][13] with counts [ne] of the last
+ * step (or initialisation), into host or device memory.  Synchronous for host output. */
+int  pdfx_get_nodal_stats(void *ctx, double *out, int on_device, void *stream);
+int  pdfx_get_element_stats(void *ctx, double *out, int32_t *counts, int on_device,
+                            void *stream);
+
+/* Conditional scalar means vcce[ne][G] (G = bins[0]*bins[1]*bins[2]; bins past the
+ * element's effective count are 0) and effective bins g[ne][3] (Sect. 3.5, Appendix A). */
+int  pdfx_get_bins(void *ctx, double *vcce, int32_t *g, int on_device, void *stream);
+int  pdfx_bins_capacity(const void *ctx);
+
+/* Diagnostic counters accumulated since creation or the last reset, and the device error
+ * word.  Synchronises stream.  pdfx_check returns the device error word as a code. */
+int  pdfx_get_diag(void *ctx, pdfx_diag *d, void *stream);
+int  pdfx_reset_diag(void *ctx, void *stream);
+int  pdfx_check(void *ctx, void *stream);
+
+/* Per-stage GPU time.  When enabled, each stage of pdfx_step is bracketed by CUDA events
+ * on the step's stream; pdfx_stage_times synchronises and writes, for stage i < n,
+ * ms[i] = accumulated milliseconds and launches[i] = number of timed launches, then
+ * clears them.  Stages: 0 advance, 1 plan, 2 lists, 3 redistribution, 4 statistics and
+ * binning, 5 nodal average.  Returns the number of stages. */
+int  pdfx_set_profiling(void *ctx, int on);
+int  pdfx_stage_times(void *ctx, double *ms, int64_t *launches, int n, void *stream);
+
+/* Number of kernel launches the library issued since creation. */
+int64_t pdfx_kernel_launches(const void *ctx);
+
+const char *pdfx_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -522,8 +522,8 @@ static void advance_particle(orc_ctx *c, int p, double dt)
         double ddy = c->y[p] - P->src_y;
         double dr = sqrt(ddx * ddx + ddy * ddy);
         double Uc = sqrt(Um[0] * Um[0] + Um[1] * Um[1] + Um[2] * Um[2]);
-        double a1 = (Uc < 1e-300) ? INFINITY
-                    : P->Cs * cbrt(P->src_r * P->src_r / eps) + P->Ct * dr / Uc;
+        double a1 = (Uc > 0.0) ? P->Cs * cbrt(P->src_r * P->src_r / eps) + P->Ct * dr / Uc
+                               : INFINITY;
         double kt = k / eps, kol = P->CT * sqrt(P->nu / eps);
         double a2 = kt > kol ? kt : kol;
         tm = a1 < a2 ? a1 : a2;

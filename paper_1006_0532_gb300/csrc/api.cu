@@ -1,0 +1,851 @@
+// C ABI of pdfx: context, grid preprocessing, buffers and the timestep orchestration.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "pdfx_internal.h"
+
+namespace pdfx {
+
+namespace {
+
+int cerr(cudaError_t e) { return e == cudaSuccess ? PDFX_OK : PDFX_ERR_CUDA; }
+#define PDFX_CUDA(call)                          \
+  do {                                           \
+    const cudaError_t e_ = (call);               \
+    if (e_ != cudaSuccess) return PDFX_ERR_CUDA; \
+  } while (0)
+#define PDFX_TRY(call)             \
+  do {                             \
+    const int r_ = (call);         \
+    if (r_ != PDFX_OK) return r_;  \
+  } while (0)
+
+cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+void* dev_alloc(Ctx& c, size_t bytes) {
+  bytes = (bytes + 255) & ~size_t(255);
+  if (bytes == 0) bytes = 256;
+  void* p = nullptr;
+  if (c.has_alloc) {
+    p = c.alloc.alloc(bytes, c.alloc.user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) c.owned.push_back({p, bytes});
+  return p;
+}
+
+void dev_free(Ctx& c, void* p) {
+  if (!p) return;
+  for (size_t i = 0; i < c.owned.size(); ++i) {
+    if (c.owned[i].first == p) {
+      if (c.has_alloc) c.alloc.release(p, c.owned[i].second, c.alloc.user);
+      else cudaFree(p);
+      c.owned.erase(c.owned.begin() + static_cast<long>(i));
+      return;
+    }
+  }
+}
+
+template <typename P>
+int alloc_into(Ctx& c, P*& out, size_t count) {
+  dev_free(c, out);
+  out = static_cast<P*>(dev_alloc(c, sizeof(P) * (count ? count : 1)));
+  return out ? PDFX_OK : PDFX_ERR_ALLOC;
+}
+
+bool params_valid(const pdfx_params& p) {
+  if (!(p.C4 > 0.0 && p.C4 <= 1.0)) return false;        // Marsaglia-Tsang needs shape >= 1
+  for (int l = 0; l < 3; ++l)
+    if (p.bins[l] < 1 || p.bins[l] > 16) return false;
+  if (p.bins[0] * p.bins[1] * p.bins[2] > 256) return false;  // conditioning pointer is 8-bit
+  if (p.min_per_bin < 1 || p.minnpel < 0 || p.minnpel > PDFX_MAX_PER_ELEMENT) return false;
+  if (p.precision != 0 && p.precision != 1) return false;
+  if (p.sort_every < 0 || !(p.nu >= 0.0) || !(p.period_x >= 0.0)) return false;
+  return true;
+}
+
+template <typename T>
+Model<T> model_of(const pdfx_params& p) {
+  Model<T> m;
+  m.C1 = T(p.C1); m.C2 = T(p.C2); m.C3 = T(p.C3); m.C4 = T(p.C4); m.CT = T(p.CT);
+  m.Cw1 = T(p.Cw1); m.Cw2 = T(p.Cw2); m.nu = T(p.nu); m.C0 = T(p.C0); m.Cs = T(p.Cs);
+  m.Ct = T(p.Ct); m.Cphi = T(p.Cphi); m.src_x = T(p.src_x); m.src_y = T(p.src_y);
+  m.src_r = T(p.src_r); m.period_x = T(p.period_x);
+  m.c0_mode = p.c0_mode; m.tm_mode = p.tm_mode; m.interp_mode = p.interp_mode;
+  m.source_on = p.source_on;
+  return m;
+}
+
+inline uint32_t key0(const pdfx_params& p) { return static_cast<uint32_t>(p.seed & 0xffffffffu); }
+inline uint32_t key1(const pdfx_params& p) {
+  return static_cast<uint32_t>(p.seed >> 32) ^ p.instance;
+}
+
+double min_image_h(double d, double L) {
+  if (L > 0.0) {
+    if (d > 0.5 * L) return d - L;
+    if (d < -0.5 * L) return d + L;
+  }
+  return d;
+}
+
+struct HostGeo {
+  std::vector<double> ax, ay, bx, by, cx, cy, area2;
+};
+
+// Boundary line of edge k (opposite vertex k) of element f, normal toward vertex k.
+void edge_line_h(const HostGeo& g, int f, int k, double out[4]) {
+  const double vx[3] = {g.ax[f], g.ax[f] + g.bx[f], g.ax[f] + g.cx[f]};
+  const double vy[3] = {g.ay[f], g.ay[f] + g.by[f], g.ay[f] + g.cy[f]};
+  const int a = (k + 1) % 3, b = (k + 2) % 3;
+  const double tx = vx[b] - vx[a], ty = vy[b] - vy[a];
+  const double len = std::sqrt(tx * tx + ty * ty);
+  double mx = -ty / len, my = tx / len;
+  if ((vx[k] - vx[a]) * mx + (vy[k] - vy[a]) * my < 0.0) { mx = -mx; my = -my; }
+  out[0] = vx[a]; out[1] = vy[a]; out[2] = mx; out[3] = my;
+}
+
+template <typename T>
+Particles<T> carve(void* base, int64_t np) {
+  Particles<T> p;
+  auto* b = static_cast<unsigned char*>(base);
+  const size_t n = static_cast<size_t>(np > 0 ? np : 1);
+  auto step = [&](size_t bytes) { unsigned char* r = b; b += (bytes + 255) & ~size_t(255); return r; };
+  p.x = reinterpret_cast<T*>(step(sizeof(T) * n));
+  p.y = reinterpret_cast<T*>(step(sizeof(T) * n));
+  p.u = reinterpret_cast<T*>(step(sizeof(T) * n));
+  p.v = reinterpret_cast<T*>(step(sizeof(T) * n));
+  p.w = reinterpret_cast<T*>(step(sizeof(T) * n));
+  p.om = reinterpret_cast<T*>(step(sizeof(T) * n));
+  p.psi = reinterpret_cast<T*>(step(sizeof(T) * n));
+  p.pid = reinterpret_cast<uint32_t*>(step(4 * n));
+  p.elem = reinterpret_cast<int32_t*>(step(4 * n));
+  p.cp = reinterpret_cast<uint8_t*>(step(n));
+  return p;
+}
+
+template <typename T>
+size_t particle_bytes(int64_t np) {
+  const size_t n = static_cast<size_t>(np > 0 ? np : 1);
+  auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
+  return 7 * r(sizeof(T) * n) + r(4 * n) + r(4 * n) + r(n);
+}
+
+// ---- profiling ----------------------------------------------------------------------------
+cudaEvent_t take_event(Ctx& c) {
+  if (!c.ev_pool.empty()) {
+    cudaEvent_t e = c.ev_pool.back();
+    c.ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct StageTimer {
+  Ctx& c;
+  int stage;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  StageTimer(Ctx& cc, int st, cudaStream_t ss) : c(cc), stage(st), s(ss) {
+    if (c.profiling) {
+      a = take_event(c);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~StageTimer() {
+    if (c.profiling && a) {
+      cudaEvent_t b = take_event(c);
+      cudaEventRecord(b, s);
+      c.ev_pending.push_back({stage, {a, b}});
+    }
+  }
+};
+
+void collect_times(Ctx& c) {
+  for (auto& pe : c.ev_pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.second.first, pe.second.second) == cudaSuccess) {
+      c.stage_ms[pe.first] += ms;
+      c.stage_n[pe.first] += 1;
+    }
+    c.ev_pool.push_back(pe.second.first);
+    c.ev_pool.push_back(pe.second.second);
+  }
+  c.ev_pending.clear();
+}
+
+// ---- pipeline -------------------------------------------------------------------------------
+template <typename T>
+int ensure_particles(Ctx& c, int64_t np) {
+  const size_t bytes = particle_bytes<T>(np);
+  if (c.pbuf[0] && c.pbuf_bytes >= bytes && c.np == np) return PDFX_OK;
+  for (int b = 0; b < 2; ++b) {
+    dev_free(c, c.pbuf[b]);
+    c.pbuf[b] = dev_alloc(c, bytes);
+    if (!c.pbuf[b]) return PDFX_ERR_ALLOC;
+  }
+  c.pbuf_bytes = bytes;
+  c.np = np;
+  c.cur = 0;
+  const size_t n = static_cast<size_t>(np > 0 ? np : 1);
+  PDFX_TRY(alloc_into(c, c.plan.idx, n));
+  PDFX_TRY(alloc_into(c, c.plan.movers, n));
+  PDFX_TRY(alloc_into(c, c.plan.mrecip, n));
+  PDFX_TRY(alloc_into(c, c.plan.mvals, 7 * n));
+  return PDFX_OK;
+}
+
+// Statistics and conditional means of the current state (after advance or a new state).
+template <typename T>
+int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resort, cudaStream_t s) {
+  Particles<T> p = carve<T>(c.pbuf[c.cur], c.np);
+  if (!counts_ready) {
+    PDFX_CUDA(cudaMemsetAsync(c.plan.cnt, 0, sizeof(int32_t) * c.ne, s));
+    launch_count(p.elem, c.np, c.plan.cnt, s);
+    c.launches++;
+  }
+  {
+    StageTimer t(c, 1, s);
+    launch_plan(c.plan, c.ne, c.prm.minnpel, allow_moves ? 1 : 0, s);
+    c.launches++;
+  }
+  {
+    StageTimer t(c, 2, s);
+    launch_scatter(p.elem, c.np, c.plan, s);
+    c.launches++;
+  }
+  if (allow_moves && c.prm.minnpel > 0) {
+    StageTimer t(c, 3, s);
+    launch_redistribute<T>(p, c.plan, c.ne, c.np, static_cast<const ElemGeo<T>*>(c.geo), c.topo,
+                           T(c.prm.period_x), c.prm.source_on, T(c.prm.src_x), T(c.prm.src_y),
+                           T(c.prm.src_r), c.step, key0(c.prm), key1(c.prm), c.num_sms, c.diag,
+                           c.err, s);
+    c.launches += 3;
+  }
+  const bool resort = force_resort || (c.prm.sort_every > 0 && c.steps_since_sort + 1 >= c.prm.sort_every);
+  {
+    StageTimer t(c, 4, s);
+    StatsArgs<T> a{};
+    a.p = p;
+    a.out = carve<T>(c.pbuf[1 - c.cur], c.np);
+    a.resort = resort ? 1 : 0;
+    a.cnt = c.plan.cnt;
+    a.off = c.plan.off;
+    a.idx = c.plan.idx;
+    a.fin = c.plan.fin;
+    a.foff = c.plan.foff;
+    a.gain = c.plan.gain;
+    a.goff = c.plan.goff;
+    a.movers = c.plan.movers;
+    a.big_list = c.plan.big_list;
+    a.scal = c.plan.scal;
+    a.ne = c.ne;
+    a.np = c.np;
+    a.bins[0] = c.prm.bins[0]; a.bins[1] = c.prm.bins[1]; a.bins[2] = c.prm.bins[2];
+    a.min_per_bin = c.prm.min_per_bin;
+    a.G = c.G;
+    a.emom = c.emom;
+    a.vcce = c.vcce;
+    a.gbin = c.gbin;
+    a.diag = c.diag;
+    a.err = c.err;
+    launch_stats<T>(a, c.num_sms, s);
+    c.launches += 2;
+  }
+  if (resort) {
+    c.cur = 1 - c.cur;
+    c.steps_since_sort = 0;
+  } else {
+    c.steps_since_sort++;
+  }
+  {
+    StageTimer t(c, 5, s);
+    launch_node_average(c.emom, c.ne_off, c.ne_list, c.nn, c.nmom, s);
+    c.launches++;
+  }
+  return cerr(cudaGetLastError());
+}
+
+template <typename T>
+int do_step(Ctx& c, double dt, cudaStream_t s) {
+  Particles<T> p = carve<T>(c.pbuf[c.cur], c.np);
+  PDFX_CUDA(cudaMemsetAsync(c.plan.cnt, 0, sizeof(int32_t) * c.ne, s));
+  {
+    StageTimer t(c, 0, s);
+    AdvanceArgs<T> a{};
+    a.p = p;
+    a.np = c.np;
+    a.geo = static_cast<const ElemGeo<T>*>(c.geo);
+    a.topo = c.topo;
+    a.walls = static_cast<const Line<T>*>(c.walls);
+    a.fslines = static_cast<const Line<T>*>(c.fslines);
+    a.ne_off = c.ne_off;
+    a.ne_list = c.ne_list;
+    a.ne = c.ne;
+    a.fields = static_cast<const T*>(c.fields);
+    a.vcce = c.vcce;
+    a.G = c.G;
+    a.cnt = c.plan.cnt;
+    a.diag = c.diag;
+    a.err = c.err;
+    a.m = model_of<T>(c.prm);
+    a.dt = T(dt);
+    a.step = c.step;
+    a.k0 = key0(c.prm);
+    a.k1 = key1(c.prm);
+    launch_advance<T>(a, c.num_sms, s);
+    c.launches++;
+  }
+  PDFX_TRY(run_statistics<T>(c, true, true, false, s));
+  c.step++;
+  c.steps_done++;
+  return cerr(cudaGetLastError());
+}
+
+template <typename T>
+int do_init(Ctx& c, int32_t ppe, cudaStream_t s) {
+  const int64_t np = static_cast<int64_t>(ppe) * c.ne;
+  PDFX_TRY(ensure_particles<T>(c, np));
+  Particles<T> p = carve<T>(c.pbuf[c.cur], np);
+  launch_init<T>(p, c.ne, ppe, static_cast<const ElemGeo<T>*>(c.geo), c.topo,
+                 static_cast<const T*>(c.fields), model_of<T>(c.prm), key0(c.prm), key1(c.prm),
+                 c.diag, s);
+  c.launches++;
+  c.step = 0;
+  c.steps_since_sort = 0;
+  return run_statistics<T>(c, false, false, false, s);
+}
+
+template <typename T>
+int do_set_particles(Ctx& c, int64_t np, const pdfx_soa* soa, uint32_t step, int on_device,
+                     cudaStream_t s) {
+  PDFX_TRY(ensure_particles<T>(c, np));
+  Particles<T> p = carve<T>(c.pbuf[c.cur], np);
+  const size_t n = static_cast<size_t>(np);
+  double* tmp = nullptr;
+  int32_t* tel = nullptr;
+  const double* src[7] = {soa->x, soa->y, soa->u, soa->v, soa->w, soa->om, soa->psi};
+  const int32_t* el = soa->elem;
+  if (!on_device && np > 0) {
+    tmp = static_cast<double*>(dev_alloc(c, sizeof(double) * 7 * n));
+    tel = static_cast<int32_t*>(dev_alloc(c, sizeof(int32_t) * n));
+    if (!tmp || !tel) { dev_free(c, tmp); dev_free(c, tel); return PDFX_ERR_ALLOC; }
+    for (int k = 0; k < 7; ++k) {
+      PDFX_CUDA(cudaMemcpyAsync(tmp + k * n, src[k], sizeof(double) * n, cudaMemcpyHostToDevice, s));
+      src[k] = tmp + k * n;
+    }
+    PDFX_CUDA(cudaMemcpyAsync(tel, el, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
+    el = tel;
+  }
+  launch_load_state<T>(p, np, src[0], src[1], src[2], src[3], src[4], src[5], src[6], el, s);
+  c.launches++;
+  c.step = step;
+  c.steps_since_sort = 0;
+  const int rc = run_statistics<T>(c, false, false, true, s);
+  if (tmp) {
+    cudaStreamSynchronize(s);
+    dev_free(c, tmp);
+    dev_free(c, tel);
+  }
+  return rc;
+}
+
+template <typename T>
+int do_get_particles(Ctx& c, pdfx_soa* soa, int on_device, cudaStream_t s) {
+  Particles<T> p = carve<T>(c.pbuf[c.cur], c.np);
+  const size_t n = static_cast<size_t>(c.np);
+  if (on_device) {
+    launch_gather_by_pid<T>(p, c.np, soa->x, soa->y, soa->u, soa->v, soa->w, soa->om, soa->psi,
+                            soa->elem, soa->cp, s);
+    c.launches++;
+    return cerr(cudaGetLastError());
+  }
+  if (n == 0) return PDFX_OK;
+  double* tmp = static_cast<double*>(dev_alloc(c, sizeof(double) * 7 * n + 5 * n));
+  if (!tmp) return PDFX_ERR_ALLOC;
+  int32_t* tel = reinterpret_cast<int32_t*>(tmp + 7 * n);
+  uint8_t* tcp = reinterpret_cast<uint8_t*>(tel + n);
+  launch_gather_by_pid<T>(p, c.np, tmp, tmp + n, tmp + 2 * n, tmp + 3 * n, tmp + 4 * n,
+                          tmp + 5 * n, tmp + 6 * n, tel, tcp, s);
+  c.launches++;
+  double* dst[7] = {soa->x, soa->y, soa->u, soa->v, soa->w, soa->om, soa->psi};
+  int rc = PDFX_OK;
+  for (int k = 0; k < 7 && rc == PDFX_OK; ++k)
+    if (dst[k]) rc = cerr(cudaMemcpyAsync(dst[k], tmp + k * n, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  if (rc == PDFX_OK && soa->elem)
+    rc = cerr(cudaMemcpyAsync(soa->elem, tel, sizeof(int32_t) * n, cudaMemcpyDeviceToHost, s));
+  if (rc == PDFX_OK && soa->cp) rc = cerr(cudaMemcpyAsync(soa->cp, tcp, n, cudaMemcpyDeviceToHost, s));
+  if (rc == PDFX_OK) rc = cerr(cudaStreamSynchronize(s));
+  dev_free(c, tmp);
+  return rc;
+}
+
+template <typename T>
+int upload_grid(Ctx& c, const HostGeo& g, const std::vector<ElemTopo>& topo,
+                const std::vector<double>& walls, const std::vector<double>& fsl) {
+  const int32_t ne = c.ne;
+  std::vector<ElemGeo<T>> hg(static_cast<size_t>(ne));
+  for (int32_t e = 0; e < ne; ++e) {
+    hg[e].ax = T(g.ax[e]); hg[e].ay = T(g.ay[e]);
+    hg[e].bx = T(g.bx[e]); hg[e].by = T(g.by[e]);
+    hg[e].cx = T(g.cx[e]); hg[e].cy = T(g.cy[e]);
+    hg[e].inv2a = T(1.0 / g.area2[e]);
+    hg[e].pad = T(0);
+  }
+  dev_free(c, c.geo);
+  c.geo = dev_alloc(c, sizeof(ElemGeo<T>) * ne);
+  if (!c.geo) return PDFX_ERR_ALLOC;
+  PDFX_CUDA(cudaMemcpy(c.geo, hg.data(), sizeof(ElemGeo<T>) * ne, cudaMemcpyHostToDevice));
+  PDFX_TRY(alloc_into(c, c.topo, static_cast<size_t>(ne)));
+  PDFX_CUDA(cudaMemcpy(c.topo, topo.data(), sizeof(ElemTopo) * ne, cudaMemcpyHostToDevice));
+  for (int which = 0; which < 2; ++which) {
+    const std::vector<double>& src = which == 0 ? walls : fsl;
+    void*& dst = which == 0 ? c.walls : c.fslines;
+    const size_t nl = src.size() / 4;
+    std::vector<Line<T>> hl(nl ? nl : 1);
+    for (size_t i = 0; i < nl; ++i) {
+      hl[i].px = T(src[4 * i]); hl[i].py = T(src[4 * i + 1]);
+      hl[i].nx = T(src[4 * i + 2]); hl[i].ny = T(src[4 * i + 3]);
+    }
+    dev_free(c, dst);
+    dst = dev_alloc(c, sizeof(Line<T>) * hl.size());
+    if (!dst) return PDFX_ERR_ALLOC;
+    PDFX_CUDA(cudaMemcpy(dst, hl.data(), sizeof(Line<T>) * hl.size(), cudaMemcpyHostToDevice));
+  }
+  return PDFX_OK;
+}
+
+int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tri, const int8_t* tag) {
+  if (nn <= 0 || ne <= 0 || !xy || !tri || !tag) return PDFX_ERR_ARG;
+  const double L = c.prm.period_x;
+  HostGeo g;
+  for (auto* v : {&g.ax, &g.ay, &g.bx, &g.by, &g.cx, &g.cy, &g.area2}) v->resize(ne);
+  for (int32_t e = 0; e < ne; ++e) {
+    const int A = tri[3 * e], B = tri[3 * e + 1], C = tri[3 * e + 2];
+    if (A < 0 || B < 0 || C < 0 || A >= nn || B >= nn || C >= nn || A == B || B == C || A == C)
+      return PDFX_ERR_MESH;
+    g.ax[e] = xy[2 * A];
+    g.ay[e] = xy[2 * A + 1];
+    g.bx[e] = min_image_h(xy[2 * B] - g.ax[e], L);
+    g.by[e] = xy[2 * B + 1] - g.ay[e];
+    g.cx[e] = min_image_h(xy[2 * C] - g.ax[e], L);
+    g.cy[e] = xy[2 * C + 1] - g.ay[e];
+    g.area2[e] = g.bx[e] * g.cy[e] - g.by[e] * g.cx[e];   // 2 A_e (Eq. 40 denominator)
+    if (!(g.area2[e] > 0.0)) return PDFX_ERR_MESH;
+  }
+  // node -> elements, ascending element id
+  std::vector<int32_t> off(static_cast<size_t>(nn) + 1, 0), lst(3 * static_cast<size_t>(ne));
+  for (int32_t e = 0; e < ne; ++e)
+    for (int k = 0; k < 3; ++k) off[tri[3 * e + k] + 1]++;
+  for (int32_t n = 0; n < nn; ++n) off[n + 1] += off[n];
+  {
+    std::vector<int32_t> fill(off.begin(), off.end() - 1);
+    for (int32_t e = 0; e < ne; ++e)
+      for (int k = 0; k < 3; ++k) lst[fill[tri[3 * e + k]]++] = e;
+  }
+  // neighbours across edges: sort the (min node, max node) edge keys
+  struct EdgeRec { int64_t key; int32_t e; int8_t k; };
+  std::vector<EdgeRec> edges(3 * static_cast<size_t>(ne));
+  for (int32_t e = 0; e < ne; ++e)
+    for (int k = 0; k < 3; ++k) {
+      const int64_t a = tri[3 * e + (k + 1) % 3], b = tri[3 * e + (k + 2) % 3];
+      edges[3 * e + k] = {std::min(a, b) * static_cast<int64_t>(nn) + std::max(a, b), e,
+                          static_cast<int8_t>(k)};
+    }
+  std::sort(edges.begin(), edges.end(), [](const EdgeRec& x, const EdgeRec& y) {
+    return x.key != y.key ? x.key < y.key : (x.e != y.e ? x.e < y.e : x.k < y.k);
+  });
+  std::vector<int32_t> nbr(3 * static_cast<size_t>(ne), -1);
+  for (size_t i = 0; i < edges.size();) {
+    size_t j = i + 1;
+    while (j < edges.size() && edges[j].key == edges[i].key) ++j;
+    if (j - i > 2) return PDFX_ERR_MESH;
+    if (j - i == 2) {
+      nbr[3 * edges[i].e + edges[i].k] = edges[i + 1].e;
+      nbr[3 * edges[i + 1].e + edges[i + 1].k] = edges[i].e;
+    }
+    i = j;
+  }
+  for (int32_t e = 0; e < ne; ++e)
+    for (int k = 0; k < 3; ++k)
+      if ((nbr[3 * e + k] < 0) != (tag[3 * e + k] != 0)) return PDFX_ERR_MESH;
+  // boundary lines (Sect. 3.8 reading): own tagged edge first, else the first tagged edge
+  // (lowest element id, lowest local edge) touching one of the element's nodes
+  std::vector<ElemTopo> topo(static_cast<size_t>(ne));
+  std::vector<double> walls, fsl;
+  for (int32_t e = 0; e < ne; ++e) {
+    ElemTopo& t = topo[e];
+    t.n0 = tri[3 * e]; t.n1 = tri[3 * e + 1]; t.n2 = tri[3 * e + 2];
+    t.nb0 = nbr[3 * e]; t.nb1 = nbr[3 * e + 1]; t.nb2 = nbr[3 * e + 2];
+    t.wall = -1;
+    t.fslip = -1;
+    for (int type = 1; type <= 2; ++type) {
+      double line[4];
+      bool found = false;
+      for (int k = 0; k < 3 && !found; ++k)
+        if (tag[3 * e + k] == type) { edge_line_h(g, e, k, line); found = true; }
+      for (int kv = 0; kv < 3 && !found; ++kv) {
+        const int n = tri[3 * e + kv];
+        for (int32_t i = off[n]; i < off[n + 1] && !found; ++i) {
+          const int f = lst[i];
+          for (int k = 0; k < 3 && !found; ++k) {
+            if (tag[3 * f + k] != type) continue;
+            if (tri[3 * f + (k + 1) % 3] != n && tri[3 * f + (k + 2) % 3] != n) continue;
+            edge_line_h(g, f, k, line);
+            line[0] = g.ax[e] + min_image_h(line[0] - g.ax[e], L);
+            found = true;
+          }
+        }
+      }
+      if (!found) continue;
+      std::vector<double>& dst = type == 1 ? walls : fsl;
+      (type == 1 ? t.wall : t.fslip) = static_cast<int>(dst.size() / 4);
+      dst.insert(dst.end(), line, line + 4);
+    }
+  }
+  c.nn = nn;
+  c.ne = ne;
+  int rc = c.prm.precision == 1 ? upload_grid<float>(c, g, topo, walls, fsl)
+                                : upload_grid<double>(c, g, topo, walls, fsl);
+  if (rc) return rc;
+  PDFX_TRY(alloc_into(c, c.ne_off, off.size()));
+  PDFX_TRY(alloc_into(c, c.ne_list, lst.size()));
+  PDFX_CUDA(cudaMemcpy(c.ne_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice));
+  PDFX_CUDA(cudaMemcpy(c.ne_list, lst.data(), sizeof(int32_t) * lst.size(), cudaMemcpyHostToDevice));
+  c.h_ne_off = off;
+  c.h_ne_list = lst;
+  // per-element and per-node buffers
+  const size_t E = static_cast<size_t>(ne), N = static_cast<size_t>(nn);
+  Plan& pl = c.plan;
+  for (int32_t** b : {&pl.cnt, &pl.cursor, &pl.fin, &pl.gain, &pl.loss, &pl.recips, &pl.donors,
+                      &pl.big_list})
+    PDFX_TRY(alloc_into(c, *b, E));
+  for (int32_t** b : {&pl.off, &pl.foff, &pl.goff, &pl.doff}) PDFX_TRY(alloc_into(c, *b, E + 1));
+  PDFX_TRY(alloc_into(c, pl.scal, 16));
+  PDFX_TRY(alloc_into(c, pl.hist, 2 * (kHistCap + 1)));
+  PDFX_TRY(alloc_into(c, c.emom, E * kNS));
+  PDFX_TRY(alloc_into(c, c.nmom, N * kNS));
+  PDFX_TRY(alloc_into(c, c.vcce, E * c.G));
+  PDFX_TRY(alloc_into(c, c.gbin, E * 3));
+  PDFX_CUDA(cudaMemset(pl.scal, 0, sizeof(int32_t) * 16));
+  PDFX_CUDA(cudaMemset(c.vcce, 0, sizeof(double) * E * c.G));
+  PDFX_CUDA(cudaMemset(c.emom, 0, sizeof(double) * E * kNS));
+  PDFX_CUDA(cudaMemset(c.nmom, 0, sizeof(double) * N * kNS));
+  dev_free(c, c.fields);
+  dev_free(c, c.fields64);
+  c.fields = dev_alloc(c, (c.prm.precision == 1 ? sizeof(float) : sizeof(double)) * N * kNF);
+  c.fields64 = c.prm.precision == 1 ? static_cast<double*>(dev_alloc(c, sizeof(double) * N * kNF)) : nullptr;
+  if (!c.fields || (c.prm.precision == 1 && !c.fields64)) return PDFX_ERR_ALLOC;
+  for (int b = 0; b < 2; ++b) { dev_free(c, c.pbuf[b]); c.pbuf[b] = nullptr; }
+  c.np = 0;
+  c.have_grid = true;
+  c.have_fields = false;
+  return PDFX_OK;
+}
+
+Ctx* as_ctx(void* p) { return static_cast<Ctx*>(p); }
+
+}  // namespace
+}  // namespace pdfx
+
+using namespace pdfx;
+
+extern "C" {
+
+void pdfx_default_params(pdfx_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  // Table 4
+  p->C1 = 1.85; p->C2 = 0.63; p->C3 = 5.0; p->C4 = 0.25; p->CT = 6.0; p->CL = 0.134;
+  p->Ceta = 72.0; p->Cv = 1.4; p->gamma5 = 0.1; p->Cw1 = 0.5; p->Cw2 = 0.73;
+  p->nu = 1e-4;
+  p->c0_mode = 0; p->C0 = 3.5;
+  p->tm_mode = 0; p->Cs = 0.02; p->Ct = 0.7; p->Cphi = 2.0;
+  p->src_x = 0.5; p->src_y = 0.5; p->src_r = 0.02;
+  p->bins[0] = p->bins[1] = p->bins[2] = 4;
+  p->min_per_bin = 2;
+  p->minnpel = 0;
+  p->interp_mode = 0;
+  p->source_on = 1;
+  p->seed = 1;
+  p->instance = 0;
+  p->period_x = 0.0;
+  p->precision = 0;
+  p->sort_every = 8;
+}
+
+int pdfx_create(const pdfx_params* p, const pdfx_allocator* alloc, void** out) {
+  if (!p || !out) return PDFX_ERR_ARG;
+  *out = nullptr;
+  if (!params_valid(*p)) return PDFX_ERR_ARG;
+  Ctx* c = new (std::nothrow) Ctx();
+  if (!c) return PDFX_ERR_ALLOC;
+  c->prm = *p;
+  if (alloc && alloc->alloc && alloc->release) {
+    c->alloc = *alloc;
+    c->has_alloc = true;
+  }
+  c->G = p->bins[0] * p->bins[1] * p->bins[2];
+  if (cudaGetDevice(&c->device) != cudaSuccess ||
+      cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+    delete c;
+    return PDFX_ERR_CUDA;
+  }
+  c->diag = static_cast<unsigned long long*>(dev_alloc(*c, sizeof(unsigned long long) * kDiagCount));
+  c->err = static_cast<int*>(dev_alloc(*c, sizeof(int) * 4));
+  if (!c->diag || !c->err) { pdfx_destroy(c); return PDFX_ERR_ALLOC; }
+  if (cudaMemset(c->diag, 0, sizeof(unsigned long long) * kDiagCount) != cudaSuccess ||
+      cudaMemset(c->err, 0, sizeof(int) * 4) != cudaSuccess) {
+    pdfx_destroy(c);
+    return PDFX_ERR_CUDA;
+  }
+  *out = c;
+  return PDFX_OK;
+}
+
+void pdfx_destroy(void* ctx) {
+  Ctx* c = as_ctx(ctx);
+  if (!c) return;
+  cudaDeviceSynchronize();
+  for (auto& o : c->owned) {
+    if (c->has_alloc) c->alloc.release(o.first, o.second, c->alloc.user);
+    else cudaFree(o.first);
+  }
+  c->owned.clear();
+  for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+  for (auto& pe : c->ev_pending) { cudaEventDestroy(pe.second.first); cudaEventDestroy(pe.second.second); }
+  delete c;
+}
+
+int pdfx_set_params(void* ctx, const pdfx_params* p) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !p || !params_valid(*p)) return PDFX_ERR_ARG;
+  if (p->precision != c->prm.precision || p->sort_every != c->prm.sort_every ||
+      p->bins[0] != c->prm.bins[0] || p->bins[1] != c->prm.bins[1] || p->bins[2] != c->prm.bins[2])
+    return PDFX_ERR_ARG;
+  if (c->have_grid && p->period_x != c->prm.period_x) return PDFX_ERR_ARG;
+  c->prm = *p;
+  return PDFX_OK;
+}
+
+int pdfx_set_grid(void* ctx, int32_t nn, const double* node_xy, int32_t ne, const int32_t* tri,
+                  const int8_t* edge_tag) {
+  Ctx* c = as_ctx(ctx);
+  if (!c) return PDFX_ERR_ARG;
+  if (cudaDeviceSynchronize() != cudaSuccess) return PDFX_ERR_CUDA;
+  return set_grid(*c, nn, node_xy, ne, tri, edge_tag);
+}
+
+int pdfx_set_fields(void* ctx, const double* fields, int on_device, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !fields) return PDFX_ERR_ARG;
+  if (!c->have_grid) return PDFX_ERR_ORDER;
+  const cudaStream_t s = as_stream(stream);
+  const size_t n = static_cast<size_t>(c->nn) * kNF;
+  const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (c->prm.precision == 1) {
+    PDFX_CUDA(cudaMemcpyAsync(c->fields64, fields, sizeof(double) * n, kind, s));
+    launch_convert_fields(c->fields64, static_cast<float*>(c->fields), static_cast<int64_t>(n), s);
+    c->launches++;
+  } else {
+    PDFX_CUDA(cudaMemcpyAsync(c->fields, fields, sizeof(double) * n, kind, s));
+  }
+  c->have_fields = true;
+  return cerr(cudaGetLastError());
+}
+
+int pdfx_init_particles(void* ctx, int32_t ppe, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || ppe <= 0) return PDFX_ERR_ARG;
+  if (!c->have_grid || !c->have_fields) return PDFX_ERR_ORDER;
+  if (static_cast<int64_t>(ppe) * c->ne > 2147483647LL) return PDFX_ERR_ARG;
+  return c->prm.precision == 1 ? do_init<float>(*c, ppe, as_stream(stream))
+                               : do_init<double>(*c, ppe, as_stream(stream));
+}
+
+int pdfx_set_particles(void* ctx, int64_t np, const pdfx_soa* s, uint32_t step, int on_device,
+                       void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !s || np < 0 || np > 2147483647LL) return PDFX_ERR_ARG;
+  if (np > 0 && (!s->x || !s->y || !s->u || !s->v || !s->w || !s->om || !s->psi || !s->elem))
+    return PDFX_ERR_ARG;
+  if (!c->have_grid) return PDFX_ERR_ORDER;
+  if (!on_device)
+    for (int64_t i = 0; i < np; ++i)
+      if (s->elem[i] < 0 || s->elem[i] >= c->ne) return PDFX_ERR_ARG;
+  return c->prm.precision == 1 ? do_set_particles<float>(*c, np, s, step, on_device, as_stream(stream))
+                               : do_set_particles<double>(*c, np, s, step, on_device, as_stream(stream));
+}
+
+int pdfx_get_particles(void* ctx, pdfx_soa* s, int on_device, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !s) return PDFX_ERR_ARG;
+  if (!c->pbuf[0]) return PDFX_ERR_ORDER;
+  return c->prm.precision == 1 ? do_get_particles<float>(*c, s, on_device, as_stream(stream))
+                               : do_get_particles<double>(*c, s, on_device, as_stream(stream));
+}
+
+int64_t pdfx_num_particles(const void* ctx) {
+  const Ctx* c = static_cast<const Ctx*>(ctx);
+  return c ? c->np : 0;
+}
+
+uint32_t pdfx_step_index(const void* ctx) {
+  const Ctx* c = static_cast<const Ctx*>(ctx);
+  return c ? c->step : 0;
+}
+
+int pdfx_step(void* ctx, double dt, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !(dt > 0.0)) return PDFX_ERR_ARG;
+  if (!c->pbuf[0] || !c->have_fields) return PDFX_ERR_ORDER;
+  return c->prm.precision == 1 ? do_step<float>(*c, dt, as_stream(stream))
+                               : do_step<double>(*c, dt, as_stream(stream));
+}
+
+static int copy_out(void* dst, const void* src, size_t bytes, int on_device, cudaStream_t s) {
+  if (!dst) return PDFX_OK;
+  if (on_device) return cerr(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));
+  if (cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) return PDFX_ERR_CUDA;
+  return cerr(cudaStreamSynchronize(s));
+}
+
+int pdfx_get_nodal_stats(void* ctx, double* out, int on_device, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !out) return PDFX_ERR_ARG;
+  if (!c->have_grid) return PDFX_ERR_ORDER;
+  return copy_out(out, c->nmom, sizeof(double) * kNS * c->nn, on_device, as_stream(stream));
+}
+
+int pdfx_get_element_stats(void* ctx, double* out, int32_t* counts, int on_device, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c) return PDFX_ERR_ARG;
+  if (!c->have_grid) return PDFX_ERR_ORDER;
+  const cudaStream_t s = as_stream(stream);
+  PDFX_TRY(copy_out(out, c->emom, sizeof(double) * kNS * c->ne, on_device, s));
+  if (counts) {
+    // counts of the last statistics pass: the element moments' first column
+    std::vector<double> tmp;
+    if (on_device) return PDFX_ERR_ARG;
+    tmp.resize(static_cast<size_t>(kNS) * c->ne);
+    PDFX_TRY(copy_out(tmp.data(), c->emom, sizeof(double) * tmp.size(), 0, s));
+    for (int32_t e = 0; e < c->ne; ++e) counts[e] = static_cast<int32_t>(tmp[kNS * e]);
+  }
+  return PDFX_OK;
+}
+
+int pdfx_get_bins(void* ctx, double* vcce, int32_t* g, int on_device, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c) return PDFX_ERR_ARG;
+  if (!c->have_grid) return PDFX_ERR_ORDER;
+  const cudaStream_t s = as_stream(stream);
+  PDFX_TRY(copy_out(vcce, c->vcce, sizeof(double) * c->G * c->ne, on_device, s));
+  return copy_out(g, c->gbin, sizeof(int32_t) * 3 * c->ne, on_device, s);
+}
+
+int pdfx_bins_capacity(const void* ctx) {
+  const Ctx* c = static_cast<const Ctx*>(ctx);
+  return c ? c->G : 0;
+}
+
+int pdfx_get_diag(void* ctx, pdfx_diag* d, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !d) return PDFX_ERR_ARG;
+  unsigned long long h[kDiagCount];
+  int err = 0;
+  const cudaStream_t s = as_stream(stream);
+  PDFX_CUDA(cudaMemcpyAsync(h, c->diag, sizeof(h), cudaMemcpyDeviceToHost, s));
+  PDFX_CUDA(cudaMemcpyAsync(&err, c->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PDFX_CUDA(cudaStreamSynchronize(s));
+  std::memset(d, 0, sizeof(*d));
+  d->steps = c->steps_done;
+  d->hops_total = static_cast<int64_t>(h[kDiagHops]);
+  d->walk_fallback = static_cast<int64_t>(h[kDiagFallback]);
+  d->walk_brute = static_cast<int64_t>(h[kDiagBrute]);
+  d->lost = static_cast<int64_t>(h[kDiagLost]);
+  d->wall_hits = static_cast<int64_t>(h[kDiagWall]);
+  d->freeslip_hits = static_cast<int64_t>(h[kDiagFreeSlip]);
+  d->omega_reflect = static_cast<int64_t>(h[kDiagOmegaReflect]);
+  d->c0_clamp = static_cast<int64_t>(h[kDiagC0Clamp]);
+  d->gamma_exhausted = static_cast<int64_t>(h[kDiagGammaExhausted]);
+  d->moves = static_cast<int64_t>(h[kDiagMoves]);
+  d->source_hits = static_cast<int64_t>(h[kDiagSource]);
+  d->capacity_overflow = static_cast<int64_t>(h[kDiagCapacity]);
+  d->nonfinite = static_cast<int64_t>(h[kDiagNonFinite]);
+  int64_t moved = 0;
+  for (int b = 1; b < 8; ++b) {
+    d->hop_hist[b] = static_cast<int64_t>(h[kDiagHopHist0 + b]);
+    moved += d->hop_hist[b];
+  }
+  d->hop_hist[0] = c->steps_done * c->np - moved;
+  d->error = err;
+  return PDFX_OK;
+}
+
+int pdfx_reset_diag(void* ctx, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c) return PDFX_ERR_ARG;
+  const cudaStream_t s = as_stream(stream);
+  PDFX_CUDA(cudaMemsetAsync(c->diag, 0, sizeof(unsigned long long) * kDiagCount, s));
+  PDFX_CUDA(cudaMemsetAsync(c->err, 0, sizeof(int), s));
+  c->steps_done = 0;
+  return PDFX_OK;
+}
+
+int pdfx_check(void* ctx, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c) return PDFX_ERR_ARG;
+  int err = 0;
+  const cudaStream_t s = as_stream(stream);
+  PDFX_CUDA(cudaMemcpyAsync(&err, c->err, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PDFX_CUDA(cudaStreamSynchronize(s));
+  return err;
+}
+
+int pdfx_set_profiling(void* ctx, int on) {
+  Ctx* c = as_ctx(ctx);
+  if (!c) return PDFX_ERR_ARG;
+  c->profiling = on != 0;
+  return PDFX_OK;
+}
+
+int pdfx_stage_times(void* ctx, double* ms, int64_t* launches, int n, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c) return PDFX_ERR_ARG;
+  PDFX_CUDA(cudaStreamSynchronize(as_stream(stream)));
+  collect_times(*c);
+  for (int i = 0; i < n && i < Ctx::kStages; ++i) {
+    if (ms) ms[i] = c->stage_ms[i];
+    if (launches) launches[i] = c->stage_n[i];
+  }
+  for (int i = 0; i < Ctx::kStages; ++i) { c->stage_ms[i] = 0; c->stage_n[i] = 0; }
+  return Ctx::kStages;
+}
+
+int64_t pdfx_kernel_launches(const void* ctx) {
+  const Ctx* c = static_cast<const Ctx*>(ctx);
+  return c ? c->launches : 0;
+}
+
+const char* pdfx_strerror(int code) {
+  switch (code) {
+    case PDFX_OK: return "ok";
+    case PDFX_ERR_ARG: return "invalid argument";
+    case PDFX_ERR_MESH: return "invalid grid";
+    case PDFX_ERR_ORDER: return "call made before the state it needs exists";
+    case PDFX_ERR_CUDA: return "CUDA runtime error";
+    case PDFX_ERR_ALLOC: return "device allocation failed";
+    case PDFX_ERR_LOST_PARTICLE: return "a particle was found in no element";
+    case PDFX_ERR_CAPACITY: return "an element exceeded the per-element capacity";
+    case PDFX_ERR_NONFINITE: return "a particle state became non-finite";
+    default: return "unknown error";
+  }
+}
+
+}  // extern "C"

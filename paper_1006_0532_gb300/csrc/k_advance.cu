@@ -1,0 +1,495 @@
+// Particle advance (one thread per particle slot) and particle initialisation.
+//
+// Per particle, in the order of one explicit Euler-Maruyama step (Sect. 3.1):
+//   area coordinates at X^n in the host element (Eqs. 44-45) and interpolation of the 31
+//   nodal fields (Eq. 37); k, eps (Eq. 18), G_ij and C0 (Eq. 11), production and S_omega
+//   (Eq. 20), t_m (Eq. 25); six Gaussians and one uniform (Sect. 3.9); velocity (Eq. 27),
+//   position (Eq. 7), frequency (Eq. 19), scalar (Eq. 24); wall conditions (Eqs. 53-58)
+//   and free-slip reflection; periodic wrap; source disc (Sect. 4.1.2); neighbour walk to
+//   the new host element (Sect. 3.6).  Counts per new element are aggregated per warp.
+#include "pdfx_internal.h"
+
+namespace pdfx {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+
+template <typename T>
+__device__ __forceinline__ bool inside(const ElemGeo<T>& g, T x, T y, T L) {
+  T la, lb, lc;
+  area_coords(g, x, y, L, la, lb, lc);
+  return la >= T(0) && lb >= T(0) && lc >= T(0);
+}
+
+// Sect. 3.6: walk to the neighbour opposite the lowest area coordinate (ties: lowest local
+// vertex); after kHopLimit hops or at a boundary edge, search the elements around the
+// nodes of the old host element (lowest containing id), then all elements.
+template <typename T>
+__device__ int walk(const AdvanceArgs<T>& a, int e0, T x, T y, int& hops, int& fb, int& brute) {
+  const T L = a.m.period_x;
+  int e = e0;
+  hops = 0;
+  for (;;) {
+    const ElemGeo<T> g = a.geo[e];
+    T la, lb, lc;
+    area_coords(g, x, y, L, la, lb, lc);
+    if (la >= T(0) && lb >= T(0) && lc >= T(0)) return e;
+    if (hops >= kHopLimit) break;
+    int k = 0;
+    T mn = la;
+    if (lb < mn) { k = 1; mn = lb; }
+    if (lc < mn) k = 2;
+    const ElemTopo t = a.topo[e];
+    const int nb = k == 0 ? t.nb0 : (k == 1 ? t.nb1 : t.nb2);
+    if (nb < 0) break;
+    e = nb;
+    ++hops;
+  }
+  fb = 1;
+  const ElemTopo t0 = a.topo[e0];
+  int best = -1;
+#pragma unroll
+  for (int kv = 0; kv < 3; ++kv) {
+    const int nd = kv == 0 ? t0.n0 : (kv == 1 ? t0.n1 : t0.n2);
+    for (int i = a.ne_off[nd]; i < a.ne_off[nd + 1]; ++i) {
+      const int f = a.ne_list[i];
+      if (best >= 0 && f >= best) continue;
+      if (inside(a.geo[f], x, y, L)) best = f;
+    }
+  }
+  if (best >= 0) return best;
+  brute = 1;
+  for (int f = 0; f < a.ne; ++f)
+    if (inside(a.geo[f], x, y, L)) return f;
+  return -1;
+}
+
+// q = lambda_A f_A + lambda_B f_B + lambda_C f_C for the 31 used field slots.
+__device__ __forceinline__ void interp_fields(const double* __restrict__ F, int na, int nb, int nc,
+                                              double la, double lb, double lc, double* q) {
+  const double2* A = reinterpret_cast<const double2*>(F + (size_t)kNF * na);
+  const double2* B = reinterpret_cast<const double2*>(F + (size_t)kNF * nb);
+  const double2* C = reinterpret_cast<const double2*>(F + (size_t)kNF * nc);
+#pragma unroll
+  for (int i = 0; i < 16; ++i) {
+    const double2 a = __ldg(A + i), b = __ldg(B + i), c = __ldg(C + i);
+    q[2 * i] = la * a.x + lb * b.x + lc * c.x;
+    q[2 * i + 1] = la * a.y + lb * b.y + lc * c.y;
+  }
+}
+__device__ __forceinline__ void interp_fields(const float* __restrict__ F, int na, int nb, int nc,
+                                              float la, float lb, float lc, float* q) {
+  const float4* A = reinterpret_cast<const float4*>(F + (size_t)kNF * na);
+  const float4* B = reinterpret_cast<const float4*>(F + (size_t)kNF * nb);
+  const float4* C = reinterpret_cast<const float4*>(F + (size_t)kNF * nc);
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const float4 a = __ldg(A + i), b = __ldg(B + i), c = __ldg(C + i);
+    q[4 * i] = la * a.x + lb * b.x + lc * c.x;
+    q[4 * i + 1] = la * a.y + lb * b.y + lc * c.y;
+    q[4 * i + 2] = la * a.z + lb * b.z + lc * c.z;
+    q[4 * i + 3] = la * a.w + lb * b.w + lc * c.w;
+  }
+}
+
+__device__ __forceinline__ double tcbrt(double x) { return cbrt(x); }
+__device__ __forceinline__ float tcbrt(float x) { return cbrtf(x); }
+__device__ __forceinline__ double texp(double x) { return exp(x); }
+__device__ __forceinline__ float texp(float x) { return expf(x); }
+
+template <typename T>
+__device__ __forceinline__ bool finite(T v) { return isfinite(v); }
+
+__device__ __forceinline__ void warp_count(unsigned long long* diag, int slot, int v) {
+  const unsigned s = __reduce_add_sync(kFull, static_cast<unsigned>(v));
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(diag + slot, static_cast<unsigned long long>(s));
+}
+
+template <typename T>
+__global__ void __launch_bounds__(256) advance_kernel(const AdvanceArgs<T> a) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const bool valid = i < a.np;
+  int c_hops = 0, c_fb = 0, c_brute = 0, c_lost = 0, c_wall = 0, c_fs = 0, c_oref = 0,
+      c_c0 = 0, c_gex = 0, c_src = 0, c_nf = 0;
+  int hop_bin = -1;
+  int e_new = -1;
+  if (valid) {
+    const Model<T>& M = a.m;
+    const T L = M.period_x;
+    const int e = a.p.elem[i];
+    const T X0 = a.p.x[i], Y0 = a.p.y[i];
+    const T U0[3] = {a.p.u[i], a.p.v[i], a.p.w[i]};
+    const T w0 = a.p.om[i], psi0 = a.p.psi[i];
+    const uint32_t pid = a.p.pid[i];
+    const int cpi = a.p.cp[i];
+    const ElemGeo<T> g = a.geo[e];
+    const ElemTopo tp = a.topo[e];
+
+    // Eqs. 37-38, 44-45 at X^n (interp_mode 1: element average)
+    T la, lb, lc;
+    if (M.interp_mode == 1) {
+      la = lb = lc = T(1) / T(3);
+    } else {
+      area_coords(g, X0, Y0, L, la, lb, lc);
+    }
+    T q[kNF];
+    interp_fields(a.fields, tp.n0, tp.n1, tp.n2, la, lb, lc, q);
+    const T Um[3] = {q[0], q[1], q[2]};
+    const T dP[3] = {q[3], q[4], T(0)};
+    T R[3][3];
+    R[0][0] = q[23]; R[1][1] = q[24]; R[2][2] = q[25];
+    R[0][1] = R[1][0] = q[26];
+    R[0][2] = R[2][0] = q[27];
+    R[1][2] = R[2][1] = q[28];
+    const T Om = q[29];
+
+    // k and Eq. 18 (floored at 1e-30 so a particle on a wall keeps finite coefficients)
+    T k = T(0.5) * (R[0][0] + R[1][1] + R[2][2]);
+    if (k < T(1e-30)) k = T(1e-30);
+    T eps = Om * (k + M.nu * M.CT * M.CT * Om);
+    if (eps < T(1e-30)) eps = T(1e-30);
+    const T ik = T(1) / k;
+    // Eq. 11
+    T C0;
+    if (M.c0_mode == 1) {
+      C0 = M.C0;
+    } else {
+      T s = T(0);
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) s += q[14 + 3 * r + c] * R[r][c];
+      C0 = T(-2) * s / (T(3) * k * eps);
+    }
+    // production P = -<u_i u_j> d<U_i>/dx_j (x, y) and Eq. 20
+    T prod = T(0);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+      for (int c = 0; c < 2; ++c) prod -= R[r][c] * q[5 + 2 * r + c];
+    const T Somega = M.Cw2 - M.Cw1 * prod / eps;
+    // Eq. 25 or the IEM time scale 2k / (C_phi eps)
+    T tm;
+    if (M.tm_mode == 1) {
+      tm = T(2) * k / (M.Cphi * eps);
+    } else {
+      const T ddx = min_image(X0 - M.src_x, L), ddy = Y0 - M.src_y;
+      const T dr = sqrt(ddx * ddx + ddy * ddy);
+      const T Uc = sqrt(Um[0] * Um[0] + Um[1] * Um[1] + Um[2] * Um[2]);
+      const T kt = k / eps, kol = M.CT * sqrt(M.nu / eps);
+      const T a2 = kt > kol ? kt : kol;
+      if (!(Uc > T(0))) {
+        tm = a2;
+      } else {
+        const T a1 = M.Cs * tcbrt(M.src_r * M.src_r / eps) + M.Ct * dr / Uc;
+        tm = a1 < a2 ? a1 : a2;
+      }
+    }
+
+    // Sect. 3.9: six Gaussians and eta
+    const uint4 r0 = philox(make_uint4(pid, a.step, kPurStep, 0u), a.k0, a.k1);
+    const uint4 r1 = philox(make_uint4(pid, a.step, kPurStep, 1u), a.k0, a.k1);
+    T xi[6];
+    box_muller(r0.x, r0.y, xi[0], xi[1]);
+    box_muller(r0.z, r0.w, xi[2], xi[3]);
+    box_muller(r1.x, r1.y, xi[4], xi[5]);
+    const T eta = uniform01(r1.z, T(0));
+    const T dt = a.dt;
+    const T sdt = sqrt(dt);
+    const T dWx = sdt * xi[0], dWy = sdt * xi[1];
+    const T s2nu = sqrt(T(2) * M.nu);
+
+    // Eq. 27 (C0 eps < 0 is clamped under the root and counted)
+    T c0e = C0 * eps;
+    if (c0e < T(0)) { c0e = T(0); c_c0 = 1; }
+    const T sc0e = sqrt(c0e);
+    T Un[3];
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+      const T base = U0[r] - dP[r] * dt + T(2) * M.nu * q[11 + r] * dt +
+                     s2nu * (q[5 + 2 * r] * dWx + q[6 + 2 * r] * dWy);
+      T gsum = T(0);
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const T Gij = (q[14 + 3 * r + c] - (r == c ? T(0.5) * eps : T(0))) * ik;
+        gsum += Gij * (U0[c] - Um[c]);
+      }
+      Un[r] = base + gsum * dt + sc0e * (sdt * xi[2 + r]);
+    }
+    // Eq. 7 (same dW as Eq. 27)
+    T Xn = X0 + U0[0] * dt + s2nu * dWx;
+    T Yn = Y0 + U0[1] * dt + s2nu * dWy;
+    // Eq. 19, reflected at zero
+    const T wpos = w0 > T(0) ? w0 : T(0);
+    T wn = w0 - M.C3 * Om * (w0 - Om) * dt - Somega * Om * w0 * dt +
+           sqrt(T(2) * M.C3 * M.C4 * Om * Om * wpos) * (sdt * xi[5]);
+    if (wn < T(0)) { wn = -wn; c_oref = 1; }
+    // Eq. 24 with the conditional mean of the particle's bin
+    const T phic = static_cast<T>(a.vcce[(size_t)e * a.G + cpi]);
+    T psin = psi0 - (psi0 - phic) * dt / tm;
+
+    // Sect. 3.8: wall elements only
+    if (tp.wall >= 0) {
+      const Line<T> ln = a.walls[tp.wall];
+      const T d0 = min_image(X0 - ln.px, L) * ln.nx + (Y0 - ln.py) * ln.ny;
+      const T d1 = min_image(Xn - ln.px, L) * ln.nx + (Yn - ln.py) * ln.ny;
+      bool hit;
+      if (d1 < T(0)) {
+        hit = true;
+      } else {
+        const T dd0 = d0 > T(0) ? d0 : T(0);
+        hit = eta < texp(-dd0 * d1 / (M.nu * dt));   // Eqs. 53, 55
+      }
+      if (hit) {
+        c_wall = 1;
+        if (d1 < T(0)) { Xn -= T(2) * d1 * ln.nx; Yn -= T(2) * d1 * ln.ny; }
+        Un[0] = Un[1] = Un[2] = T(0);                  // Eq. 56
+        int ex = 0;                                    // Eq. 58
+        wn = gamma_draw<T>(a.k0, a.k1, pid, a.step, kPurWallGamma, T(1) / M.C4, M.C4 * q[30], &ex);
+        c_gex = ex;
+      }
+    }
+    // free-slip boundary: reflect, reverse the normal velocity
+    if (tp.fslip >= 0) {
+      const Line<T> ln = a.fslines[tp.fslip];
+      const T d1 = min_image(Xn - ln.px, L) * ln.nx + (Yn - ln.py) * ln.ny;
+      if (d1 < T(0)) {
+        c_fs = 1;
+        Xn -= T(2) * d1 * ln.nx;
+        Yn -= T(2) * d1 * ln.ny;
+        const T un = Un[0] * ln.nx + Un[1] * ln.ny;
+        Un[0] -= T(2) * un * ln.nx;
+        Un[1] -= T(2) * un * ln.ny;
+      }
+    }
+    Xn = wrap_period(Xn, L);
+    if (M.source_on) {
+      const T sx = min_image(Xn - M.src_x, L), sy = Yn - M.src_y;
+      if (sx * sx + sy * sy <= M.src_r * M.src_r) { psin = T(1); c_src = 1; }
+    }
+    if (!(finite(Xn) && finite(Yn) && finite(Un[0]) && finite(Un[1]) && finite(Un[2]) &&
+          finite(wn) && finite(psin)))
+      c_nf = 1;
+
+    // Sect. 3.6
+    int hops = 0, fb = 0, brute = 0;
+    e_new = walk(a, e, Xn, Yn, hops, fb, brute);
+    c_hops = hops;
+    c_fb = fb;
+    c_brute = brute;
+    hop_bin = hops < 7 ? hops : 7;
+    if (e_new < 0) { e_new = e; c_lost = 1; }
+
+    a.p.x[i] = Xn;
+    a.p.y[i] = Yn;
+    a.p.u[i] = Un[0];
+    a.p.v[i] = Un[1];
+    a.p.w[i] = Un[2];
+    a.p.om[i] = wn;
+    a.p.psi[i] = psin;
+    a.p.elem[i] = e_new;
+  }
+  // counts per new element, aggregated over the lanes of a warp that share it
+  const unsigned active = __ballot_sync(kFull, valid);
+  if (valid) {
+    const unsigned peers = __match_any_sync(active, e_new);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(a.cnt + e_new, __popc(peers));
+  }
+  warp_count(a.diag, kDiagHops, c_hops);
+  if (__any_sync(kFull, c_fb | c_brute | c_lost | c_nf | c_gex | c_c0)) {
+    warp_count(a.diag, kDiagFallback, c_fb);
+    warp_count(a.diag, kDiagBrute, c_brute);
+    warp_count(a.diag, kDiagLost, c_lost);
+    warp_count(a.diag, kDiagNonFinite, c_nf);
+    warp_count(a.diag, kDiagGammaExhausted, c_gex);
+    warp_count(a.diag, kDiagC0Clamp, c_c0);
+  }
+  if (__any_sync(kFull, c_lost) && (threadIdx.x & 31) == 0) atomicCAS(a.err, 0, PDFX_ERR_LOST_PARTICLE);
+  if (__any_sync(kFull, c_nf) && (threadIdx.x & 31) == 0) atomicCAS(a.err, 0, PDFX_ERR_NONFINITE);
+  if (__any_sync(kFull, c_wall | c_fs | c_oref | c_src)) {
+    warp_count(a.diag, kDiagWall, c_wall);
+    warp_count(a.diag, kDiagFreeSlip, c_fs);
+    warp_count(a.diag, kDiagOmegaReflect, c_oref);
+    warp_count(a.diag, kDiagSource, c_src);
+  }
+  if (__any_sync(kFull, hop_bin > 0)) {
+#pragma unroll
+    for (int b = 1; b < 8; ++b) warp_count(a.diag, kDiagHopHist0 + b, hop_bin == b);
+  }
+}
+
+// Sect. 3.7: particle id e * ppe + k, uniform in element e (square-root method of Osada
+// et al.), velocity N(<U>, 2k/3 I), frequency Gamma(1/C4, C4 <omega>), scalar from the
+// source disc.
+template <typename T>
+__global__ void init_kernel(Particles<T> p, int32_t ne, int32_t ppe, const ElemGeo<T>* geo,
+                            const ElemTopo* topo, const T* fields, Model<T> m, uint32_t k0,
+                            uint32_t k1, unsigned long long* diag) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t np = static_cast<int64_t>(ne) * ppe;
+  int c_gex = 0;
+  if (i < np) {
+    const int e = static_cast<int>(i / ppe);
+    const uint32_t pid = static_cast<uint32_t>(i);
+    const uint4 r0 = philox(make_uint4(pid, 0u, kPurInit, 0u), k0, k1);
+    const uint4 r1 = philox(make_uint4(pid, 0u, kPurInit, 1u), k0, k1);
+    const ElemGeo<T> g = geo[e];
+    const ElemTopo tp = topo[e];
+    const T s = sqrt(uniform01(r0.x, T(0)));
+    const T t = uniform01(r0.y, T(0));
+    T px = g.ax + s * (T(1) - t) * g.bx + s * t * g.cx;
+    const T py = g.ay + s * (T(1) - t) * g.by + s * t * g.cy;
+    T la, lb, lc;
+    if (m.interp_mode == 1) {
+      la = lb = lc = T(1) / T(3);
+    } else {
+      area_coords(g, px, py, m.period_x, la, lb, lc);
+    }
+    T q[kNF];
+    interp_fields(fields, tp.n0, tp.n1, tp.n2, la, lb, lc, q);
+    T k2 = T(0.5) * (q[23] + q[24] + q[25]);
+    if (k2 < T(0)) k2 = T(0);
+    const T sd = sqrt(T(2) * k2 / T(3));
+    T g0, g1, g2, gd;
+    box_muller(r0.z, r0.w, g0, g1);
+    box_muller(r1.x, r1.y, g2, gd);
+    int ex = 0;
+    const T om = gamma_draw<T>(k0, k1, pid, 0u, kPurInitGamma, T(1) / m.C4, m.C4 * q[29], &ex);
+    c_gex = ex;
+    px = wrap_period(px, m.period_x);
+    bool src = false;
+    if (m.source_on) {
+      const T sx = min_image(px - m.src_x, m.period_x), sy = py - m.src_y;
+      src = sx * sx + sy * sy <= m.src_r * m.src_r;
+    }
+    p.x[i] = px;
+    p.y[i] = py;
+    p.u[i] = q[0] + sd * g0;
+    p.v[i] = q[1] + sd * g1;
+    p.w[i] = q[2] + sd * g2;
+    p.om[i] = om;
+    p.psi[i] = src ? T(1) : T(0);
+    p.pid[i] = pid;
+    p.elem[i] = e;
+    p.cp[i] = 0;
+  }
+  warp_count(diag, kDiagGammaExhausted, c_gex);
+}
+
+__global__ void count_kernel(const int32_t* __restrict__ elem, int64_t np, int32_t* cnt) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const bool valid = i < np;
+  const int e = valid ? elem[i] : -1;
+  const unsigned active = __ballot_sync(kFull, valid);
+  if (valid) {
+    const unsigned peers = __match_any_sync(active, e);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cnt + e, __popc(peers));
+  }
+}
+
+template <typename T>
+__global__ void gather_by_pid_kernel(Particles<T> p, int64_t np, double* x, double* y, double* u,
+                                     double* v, double* w, double* om, double* psi,
+                                     int32_t* elem, uint8_t* cp) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const uint32_t id = p.pid[i];
+  if (x) x[id] = p.x[i];
+  if (y) y[id] = p.y[i];
+  if (u) u[id] = p.u[i];
+  if (v) v[id] = p.v[i];
+  if (w) w[id] = p.w[i];
+  if (om) om[id] = p.om[i];
+  if (psi) psi[id] = p.psi[i];
+  if (elem) elem[id] = p.elem[i];
+  if (cp) cp[id] = p.cp[i];
+}
+
+template <typename T>
+__global__ void load_state_kernel(Particles<T> p, int64_t np, const double* x, const double* y,
+                                  const double* u, const double* v, const double* w,
+                                  const double* om, const double* psi, const int32_t* elem) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  p.x[i] = static_cast<T>(x[i]);
+  p.y[i] = static_cast<T>(y[i]);
+  p.u[i] = static_cast<T>(u[i]);
+  p.v[i] = static_cast<T>(v[i]);
+  p.w[i] = static_cast<T>(w[i]);
+  p.om[i] = static_cast<T>(om[i]);
+  p.psi[i] = static_cast<T>(psi[i]);
+  p.elem[i] = elem[i];
+  p.pid[i] = static_cast<uint32_t>(i);
+  p.cp[i] = 0;
+}
+
+__global__ void convert_fields_kernel(const double* in, float* out, int64_t n) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = static_cast<float>(in[i]);
+}
+
+inline unsigned blocks_for(int64_t n, int threads) {
+  return static_cast<unsigned>((n + threads - 1) / threads);
+}
+
+}  // namespace
+
+template <typename T>
+void launch_advance(const AdvanceArgs<T>& a, int, cudaStream_t s) {
+  if (a.np <= 0) return;
+  advance_kernel<T><<<blocks_for(a.np, 256), 256, 0, s>>>(a);
+}
+
+template <typename T>
+void launch_init(Particles<T> p, int32_t ne, int32_t ppe, const ElemGeo<T>* geo,
+                 const ElemTopo* topo, const T* fields, Model<T> m, uint32_t k0, uint32_t k1,
+                 unsigned long long* diag, cudaStream_t s) {
+  const int64_t np = static_cast<int64_t>(ne) * ppe;
+  if (np <= 0) return;
+  init_kernel<T><<<blocks_for(np, 256), 256, 0, s>>>(p, ne, ppe, geo, topo, fields, m, k0, k1, diag);
+}
+
+void launch_count(const int32_t* elem, int64_t np, int32_t* cnt, cudaStream_t s) {
+  if (np <= 0) return;
+  count_kernel<<<blocks_for(np, 256), 256, 0, s>>>(elem, np, cnt);
+}
+
+template <typename T>
+void launch_gather_by_pid(Particles<T> p, int64_t np, double* x, double* y, double* u, double* v,
+                          double* w, double* om, double* psi, int32_t* elem, uint8_t* cp,
+                          cudaStream_t s) {
+  if (np <= 0) return;
+  gather_by_pid_kernel<T><<<blocks_for(np, 256), 256, 0, s>>>(p, np, x, y, u, v, w, om, psi, elem, cp);
+}
+
+template <typename T>
+void launch_load_state(Particles<T> p, int64_t np, const double* x, const double* y,
+                       const double* u, const double* v, const double* w, const double* om,
+                       const double* psi, const int32_t* elem, cudaStream_t s) {
+  if (np <= 0) return;
+  load_state_kernel<T><<<blocks_for(np, 256), 256, 0, s>>>(p, np, x, y, u, v, w, om, psi, elem);
+}
+
+void launch_convert_fields(const double* in, float* out, int64_t n, cudaStream_t s) {
+  if (n <= 0) return;
+  convert_fields_kernel<<<blocks_for(n, 256), 256, 0, s>>>(in, out, n);
+}
+
+#define PDFX_INSTANTIATE(T)                                                                    \
+  template void launch_advance<T>(const AdvanceArgs<T>&, int, cudaStream_t);                   \
+  template void launch_init<T>(Particles<T>, int32_t, int32_t, const ElemGeo<T>*,              \
+                               const ElemTopo*, const T*, Model<T>, uint32_t, uint32_t,        \
+                               unsigned long long*, cudaStream_t);                             \
+  template void launch_gather_by_pid<T>(Particles<T>, int64_t, double*, double*, double*,      \
+                                        double*, double*, double*, double*, int32_t*,          \
+                                        uint8_t*, cudaStream_t);                               \
+  template void launch_load_state<T>(Particles<T>, int64_t, const double*, const double*,      \
+                                     const double*, const double*, const double*,              \
+                                     const double*, const double*, const int32_t*,             \
+                                     cudaStream_t);
+PDFX_INSTANTIATE(double)
+PDFX_INSTANTIATE(float)
+#undef PDFX_INSTANTIATE
+
+}  // namespace pdfx

@@ -1,0 +1,735 @@
+// Statistics pipeline after the particle advance:
+//   plan         counts -> list offsets; Appendix B particle-number control in closed form
+//   scatter      element lists of particle slots
+//   redistribute donor selection, new values of moved particles, commit
+//   stats        per element: two-pass moments (Eqs. 35-36), adaptive sort-and-divide
+//                binning and conditional means (Sect. 3.5, Appendix A), optional re-order
+//   node average nodal statistics = mean over the surrounding non-empty elements (Sect. 3.3)
+#include "pdfx_internal.h"
+
+namespace pdfx {
+
+namespace {
+
+constexpr unsigned kFull = 0xffffffffu;
+constexpr int kPlanThreads = 1024;
+
+// ---------------------------------------------------------------------------------------
+// Block-wide exclusive scan (deterministic).
+// ---------------------------------------------------------------------------------------
+template <typename V>
+__device__ V block_exclusive_scan(V v, V* tmp /* [32] */, V& total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  V x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const V y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) tmp[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    V t = lane < nw ? tmp[lane] : V(0);
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const V y = __shfl_up_sync(kFull, t, o);
+      if (lane >= o) t += y;
+    }
+    tmp[lane] = t;
+  }
+  __syncthreads();
+  const V before = (wid > 0 ? tmp[wid - 1] : V(0)) + x - v;
+  total = tmp[nw - 1];
+  __syncthreads();
+  return before;
+}
+
+// ---------------------------------------------------------------------------------------
+// Plan: one block.  Writes off / cursor (exclusive scan of counts), the big-element list,
+// and, when particles must move, the Appendix B final counts in closed form.
+//
+// The Appendix B loop moves one particle at a time from the fullest element (lowest id on
+// ties) to the emptiest (lowest id on ties) while min < MINNPEL and max - min >= 2.  A
+// receiving element never becomes the fullest while the loop runs, nor a giving element
+// the emptiest, so after t moves the receiving side is "water-filled" from below and the
+// giving side drained from the top:
+//   min_t = max{L : D(L) <= t},  D(L) = sum_e max(0, L - c_e)
+//   max_t = min{H : S(H) <= t},  S(H) = sum_e max(0, c_e - H)
+// and the loop stops at T = min{t : min_t >= MINNPEL or max_t - min_t <= 1}.  The extra
+// units at the final levels go to (come from) the lowest element ids, exactly as the
+// loop's tie-breaking picks them.
+// ---------------------------------------------------------------------------------------
+struct PlanShared {
+  int32_t tmp32[32];
+  int64_t tmp64[32];
+  int32_t vmin[32], vmax[32];
+  int32_t carry[8];
+  int64_t Tm, L, H, r, rp, cmin, cmax;
+  int need;
+};
+
+__device__ int64_t D_of(const int64_t* P0, const int64_t* P1, int64_t L, int64_t cmax) {
+  // sum over c < L of h[c] (L - c), counts clipped at kHistCap
+  if (L <= 0) return 0;
+  int64_t x = L - 1;
+  if (x > cmax) x = cmax;
+  return L * P0[x] - P1[x];
+}
+__device__ int64_t S_of(const int64_t* P0, const int64_t* P1, int64_t H, int64_t cmax) {
+  if (H >= cmax) return 0;
+  const int64_t a0 = P0[cmax] - (H >= 0 ? P0[H] : 0);
+  const int64_t a1 = P1[cmax] - (H >= 0 ? P1[H] : 0);
+  return a1 - H * a0;
+}
+
+__global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne, int minnpel,
+                                                             int allow_moves) {
+  __shared__ PlanShared sh;
+  __shared__ int32_t hist[kHistCap + 1];
+  const int tid = threadIdx.x;
+  // pass 1: offsets of the element lists, min / max, big elements (no moves)
+  int32_t carry = 0, lmin = 0x7fffffff, lmax = -1;
+  if (tid == 0) pl.scal[3] = 0;
+  __syncthreads();
+  for (int32_t base = 0; base < ne; base += kPlanThreads) {
+    const int32_t e = base + tid;
+    const int32_t c = e < ne ? pl.cnt[e] : 0;
+    int32_t tot;
+    const int32_t ex = block_exclusive_scan<int32_t>(c, sh.tmp32, tot);
+    if (e < ne) {
+      pl.off[e] = carry + ex;
+      pl.foff[e] = carry + ex;
+      pl.cursor[e] = carry + ex;
+      lmin = min(lmin, c);
+      lmax = max(lmax, c);
+      if (c > kSmallCap) pl.big_list[atomicAdd(pl.scal + 3, 1)] = e;
+    }
+    carry += tot;
+  }
+  if (tid == 0) { pl.off[ne] = carry; pl.foff[ne] = carry; }
+  for (int o = 16; o > 0; o >>= 1) {
+    lmin = min(lmin, __shfl_xor_sync(kFull, lmin, o));
+    lmax = max(lmax, __shfl_xor_sync(kFull, lmax, o));
+  }
+  if ((tid & 31) == 0) { sh.vmin[tid >> 5] = lmin; sh.vmax[tid >> 5] = lmax; }
+  __syncthreads();
+  if (tid == 0) {
+    int32_t a = 0x7fffffff, b = -1;
+    for (int w = 0; w < kPlanThreads / 32; ++w) { a = min(a, sh.vmin[w]); b = max(b, sh.vmax[w]); }
+    sh.cmin = a;
+    sh.cmax = b;
+    sh.need = allow_moves && minnpel > 0 && a < minnpel && (b - a) >= 2;
+    pl.scal[4] = a;
+    pl.scal[5] = b;
+    if (!sh.need) { pl.scal[0] = 0; pl.scal[1] = 0; pl.scal[2] = 0; }
+  }
+  __syncthreads();
+  if (!sh.need) return;
+
+  // pass 2: histogram of counts and its prefix sums P0[c] = #{c_e <= c}, P1[c] = sum c_e
+  for (int i = tid; i <= kHistCap; i += kPlanThreads) hist[i] = 0;
+  __syncthreads();
+  for (int32_t e = tid; e < ne; e += kPlanThreads) atomicAdd(&hist[min(pl.cnt[e], kHistCap)], 1);
+  __syncthreads();
+  int64_t* P0 = pl.hist;
+  int64_t* P1 = pl.hist + (kHistCap + 1);
+  {
+    int64_t c0 = 0, c1 = 0;
+    for (int base = 0; base <= kHistCap; base += kPlanThreads) {
+      const int i = base + tid;
+      const int64_t h = i <= kHistCap ? hist[i] : 0;
+      int64_t t0, t1;
+      const int64_t e0 = block_exclusive_scan<int64_t>(h, sh.tmp64, t0);
+      const int64_t e1 = block_exclusive_scan<int64_t>(h * i, sh.tmp64, t1);
+      if (i <= kHistCap) { P0[i] = c0 + e0 + h; P1[i] = c1 + e1 + h * i; }
+      c0 += t0;
+      c1 += t1;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    const int64_t cmin = sh.cmin, cmax = sh.cmax < kHistCap ? sh.cmax : kHistCap;
+    auto min_level = [&](int64_t t) {   // max{L in [cmin, minnpel] : D(L) <= t}
+      int64_t lo = cmin, hi = minnpel;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi + 1) / 2;
+        if (D_of(P0, P1, mid, cmax) <= t) lo = mid; else hi = mid - 1;
+      }
+      return lo;
+    };
+    auto max_level = [&](int64_t t) {   // min{H in [cmin, cmax] : S(H) <= t}
+      int64_t lo = cmin, hi = cmax;
+      while (lo < hi) {
+        const int64_t mid = (lo + hi) / 2;
+        if (S_of(P0, P1, mid, cmax) <= t) hi = mid; else lo = mid + 1;
+      }
+      return lo;
+    };
+    int64_t lo = 0, hi = D_of(P0, P1, minnpel, cmax);
+    while (lo < hi) {                   // first t at which the loop stops
+      const int64_t mid = (lo + hi) / 2;
+      const int64_t Lm = min_level(mid), Hm = max_level(mid);
+      if (Lm >= minnpel || Hm - Lm <= 1) hi = mid; else lo = mid + 1;
+    }
+    const int64_t T = lo;
+    sh.Tm = T;
+    sh.L = min_level(T);
+    sh.H = max_level(T);
+    sh.r = T - D_of(P0, P1, sh.L, cmax);
+    sh.rp = T - S_of(P0, P1, sh.H, cmax);
+    pl.scal[0] = static_cast<int32_t>(T);
+    pl.scal[3] = 0;
+  }
+  __syncthreads();
+  // pass 3: gains, losses, final counts, offsets and the recipient / donor / big lists
+  const int64_t L = sh.L, H = sh.H, r = sh.r, rp = sh.rp;
+  int32_t cRankL = 0, cRankH = 0, cG = 0, cD = 0, cF = 0, cNR = 0, cND = 0;
+  for (int32_t base = 0; base < ne; base += kPlanThreads) {
+    const int32_t e = base + tid;
+    const int32_t c = e < ne ? pl.cnt[e] : 0;
+    const int32_t atL = (e < ne && c <= L) ? 1 : 0;
+    const int32_t atH = (e < ne && c >= H) ? 1 : 0;
+    int32_t tot;
+    const int32_t rankL = cRankL + block_exclusive_scan<int32_t>(atL, sh.tmp32, tot);
+    cRankL += tot;
+    const int32_t rankH = cRankH + block_exclusive_scan<int32_t>(atH, sh.tmp32, tot);
+    cRankH += tot;
+    int32_t g = 0, l = 0;
+    if (e < ne) {
+      if (c < L) g += static_cast<int32_t>(L - c);
+      if (atL && rankL < r) g += 1;
+      if (c > H) l += static_cast<int32_t>(c - H);
+      if (atH && rankH < rp) l += 1;
+    }
+    const int32_t f = c + g - l;
+    const int32_t go = cG + block_exclusive_scan<int32_t>(g, sh.tmp32, tot);
+    cG += tot;
+    const int32_t dof = cD + block_exclusive_scan<int32_t>(l, sh.tmp32, tot);
+    cD += tot;
+    const int32_t fo = cF + block_exclusive_scan<int32_t>(e < ne ? f : 0, sh.tmp32, tot);
+    cF += tot;
+    const int32_t ri = cNR + block_exclusive_scan<int32_t>(g > 0 ? 1 : 0, sh.tmp32, tot);
+    cNR += tot;
+    const int32_t di = cND + block_exclusive_scan<int32_t>(l > 0 ? 1 : 0, sh.tmp32, tot);
+    cND += tot;
+    if (e < ne) {
+      pl.gain[e] = g;
+      pl.loss[e] = l;
+      pl.goff[e] = go;
+      pl.doff[e] = dof;
+      pl.fin[e] = f;
+      pl.foff[e] = fo;
+      if (g > 0) pl.recips[ri] = e;
+      if (l > 0) pl.donors[di] = e;
+      if (f > kSmallCap) pl.big_list[atomicAdd(pl.scal + 3, 1)] = e;
+    }
+  }
+  if (tid == 0) {
+    pl.goff[ne] = cG;
+    pl.doff[ne] = cD;
+    pl.foff[ne] = cF;
+    pl.scal[1] = cNR;
+    pl.scal[2] = cND;
+  }
+}
+
+// Element lists: idx[off[e] .. off[e] + cnt[e]) holds the slots of the particles in e.
+__global__ void scatter_kernel(const int32_t* __restrict__ elem, int64_t np, int32_t* cursor,
+                               int32_t* idx) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const bool valid = i < np;
+  const int e = valid ? elem[i] : -1;
+  const unsigned active = __ballot_sync(kFull, valid);
+  if (!valid) return;
+  const unsigned peers = __match_any_sync(active, e);
+  const int lane = threadIdx.x & 31;
+  const int leader = __ffs(peers) - 1;
+  int base = 0;
+  if (lane == leader) base = atomicAdd(cursor + e, __popc(peers));
+  base = __shfl_sync(peers, base, leader);
+  idx[base + __popc(peers & ((1u << lane) - 1u))] = static_cast<int32_t>(i);
+}
+
+// ---------------------------------------------------------------------------------------
+// Redistribution (Appendix B; reading: donors give their highest particle ids; a moved
+// particle keeps its id, lands uniformly in the recipient and copies (U, omega, psi) of the
+// recipient's resident of rank floor(u n) in ascending id, or of the lowest-id non-empty
+// edge neighbour's when the recipient is empty; the source disc is re-applied).
+// ---------------------------------------------------------------------------------------
+constexpr int kRedistThreads = 256;
+constexpr int kRedistCap = 4096;   // = PDFX_MAX_PER_ELEMENT
+
+template <typename T>
+__global__ void __launch_bounds__(kRedistThreads) select_donors_kernel(Particles<T> p, Plan pl) {
+  __shared__ uint32_t spid[kRedistCap];
+  __shared__ int32_t sslot[kRedistCap];
+  const int32_t ndon = pl.scal[0] > 0 ? pl.scal[2] : 0;
+  for (int32_t d = blockIdx.x; d < ndon; d += gridDim.x) {
+    const int32_t e = pl.donors[d];
+    const int32_t n = min(pl.cnt[e], kRedistCap);
+    const int32_t o = pl.off[e];
+    const int32_t l = pl.loss[e];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const int32_t s = pl.idx[o + j];
+      sslot[j] = s;
+      spid[j] = p.pid[s];
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const uint32_t me = spid[j];
+      int rank = 0;   // particles with a higher id
+      for (int m = 0; m < n; ++m) rank += spid[m] > me;
+      if (rank < l) pl.movers[pl.doff[e] + rank] = sslot[j];
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kRedistThreads) apply_moves_kernel(
+    Particles<T> p, Plan pl, int64_t np, const ElemGeo<T>* geo, const ElemTopo* topo, T period_x,
+    int source_on, T sx, T sy, T sr, uint32_t step, uint32_t k0, uint32_t k1) {
+  extern __shared__ __align__(16) unsigned char dyn[];
+  uint32_t* spid = reinterpret_cast<uint32_t*>(dyn);
+  int32_t* sslot = reinterpret_cast<int32_t*>(dyn + 4 * kRedistCap);
+  int32_t* sorted = reinterpret_cast<int32_t*>(dyn + 8 * kRedistCap);
+  const int32_t nrec = pl.scal[0] > 0 ? pl.scal[1] : 0;
+  for (int32_t ri = blockIdx.x; ri < nrec; ri += gridDim.x) {
+    const int32_t r = pl.recips[ri];
+    int32_t src = r;
+    if (pl.cnt[r] == 0) {
+      const ElemTopo t = topo[r];
+      const int nbs[3] = {t.nb0, t.nb1, t.nb2};
+      src = -1;
+      for (int k = 0; k < 3; ++k)
+        if (nbs[k] >= 0 && pl.cnt[nbs[k]] > 0 && (src < 0 || nbs[k] < src)) src = nbs[k];
+    }
+    const int32_t n = src >= 0 ? min(pl.cnt[src], kRedistCap) : 0;
+    if (n > 0) {
+      const int32_t o = pl.off[src];
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int32_t s = pl.idx[o + j];
+        sslot[j] = s;
+        spid[j] = p.pid[s];
+      }
+      __syncthreads();
+      for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const uint32_t me = spid[j];
+        int rank = 0;
+        for (int m = 0; m < n; ++m) rank += spid[m] < me;
+        sorted[rank] = sslot[j];
+      }
+      __syncthreads();
+    }
+    const ElemGeo<T> g = geo[r];
+    const int32_t g0 = pl.goff[r], gn = pl.gain[r];
+    for (int j = threadIdx.x; j < gn; j += blockDim.x) {
+      const int32_t k = g0 + j;
+      const int32_t q = pl.movers[k];
+      if (q < 0 || q >= np) { pl.mrecip[k] = -1; continue; }
+      const uint32_t pid = p.pid[q];
+      const uint4 rw = philox(make_uint4(pid, step, kPurRedist, 0u), k0, k1);
+      const T s = sqrt(uniform01(rw.x, T(0)));
+      const T t = uniform01(rw.y, T(0));
+      T px = g.ax + s * (T(1) - t) * g.bx + s * t * g.cx;
+      const T py = g.ay + s * (T(1) - t) * g.by + s * t * g.cy;
+      px = wrap_period(px, period_x);
+      int32_t from = q;
+      if (n > 0) {
+        const double uu = uniform01(rw.z, 0.0);   // rank choice in double in both forms
+        int jj = static_cast<int>(uu * static_cast<double>(n));
+        if (jj >= n) jj = n - 1;
+        from = sorted[jj];
+      }
+      double* mv = pl.mvals + static_cast<size_t>(k) * 7;
+      mv[0] = static_cast<double>(px);
+      mv[1] = static_cast<double>(py);
+      mv[2] = static_cast<double>(p.u[from]);
+      mv[3] = static_cast<double>(p.v[from]);
+      mv[4] = static_cast<double>(p.w[from]);
+      mv[5] = static_cast<double>(p.om[from]);
+      bool insrc = false;
+      if (source_on) {
+        const T ddx = min_image(px - sx, period_x), ddy = py - sy;
+        insrc = ddx * ddx + ddy * ddy <= sr * sr;
+      }
+      mv[6] = insrc ? 1.0 : static_cast<double>(p.psi[from]);
+      pl.mrecip[k] = r;
+    }
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void commit_moves_kernel(Particles<T> p, Plan pl, int64_t np, int32_t ne,
+                                    unsigned long long* diag, int* err) {
+  const int32_t T_moves = pl.scal[0];
+  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < T_moves; k += gridDim.x * blockDim.x) {
+    const int32_t q = pl.movers[k];
+    const int32_t r = pl.mrecip[k];
+    if (q < 0 || q >= np || r < 0 || r >= ne) {   // an inconsistent move table is an error
+      atomicCAS(err, 0, PDFX_ERR_CAPACITY);
+      continue;
+    }
+    const double* mv = pl.mvals + static_cast<size_t>(k) * 7;
+    p.x[q] = static_cast<T>(mv[0]);
+    p.y[q] = static_cast<T>(mv[1]);
+    p.u[q] = static_cast<T>(mv[2]);
+    p.v[q] = static_cast<T>(mv[3]);
+    p.w[q] = static_cast<T>(mv[4]);
+    p.om[q] = static_cast<T>(mv[5]);
+    p.psi[q] = static_cast<T>(mv[6]);
+    p.elem[q] = r;
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0 && T_moves > 0)
+    atomicAdd(diag + kDiagMoves, static_cast<unsigned long long>(T_moves));
+}
+
+// ---------------------------------------------------------------------------------------
+// Per-element statistics and conditional means.
+// ---------------------------------------------------------------------------------------
+constexpr int kStatsThreads = 256;
+
+template <typename T>
+struct StatsSmem {
+  T* u; T* v; T* w; T* om; T* psi;
+  uint32_t* pid;
+  int32_t* slot;
+  uint16_t* perm;
+  uint8_t* grp;
+};
+
+template <typename T>
+__device__ __forceinline__ bool key_less(const StatsSmem<T>& s, const T* key, int a, int b, int N) {
+  if (a >= N) return false;        // padding sorts last
+  if (b >= N) return true;
+  if (s.grp[a] != s.grp[b]) return s.grp[a] < s.grp[b];
+  const T ka = key[a], kb = key[b];
+  if (ka < kb) return true;
+  if (kb < ka) return false;
+  return s.pid[a] < s.pid[b];
+}
+
+// Bitonic sort of perm[0, P) (P a power of two) by (group, key, particle id).
+template <typename T>
+__device__ void bitonic_sort(const StatsSmem<T>& s, const T* key, int N, int P) {
+  for (int k = 2; k <= P; k <<= 1) {
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      for (int q = threadIdx.x; q < P / 2; q += blockDim.x) {
+        const int lo = 2 * j * (q / j) + (q % j);
+        const int hi = lo + j;
+        const bool up = (lo & k) == 0;
+        const int a = s.perm[lo], b = s.perm[hi];
+        const bool swap = up ? key_less(s, key, b, a, N) : key_less(s, key, a, b, N);
+        if (swap) { s.perm[lo] = b; s.perm[hi] = a; }
+      }
+      __syncthreads();
+    }
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  return v;
+}
+
+// Deterministic block sums of NV values (fixed reduction order).
+template <int NV>
+__device__ void block_sums(double (&v)[NV], double* red /* [32 * NV] */) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    const double s = warp_sum(v[k]);
+    if (lane == 0) red[wid * NV + k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x < NV) {
+    double s = 0.0;
+    for (int w = 0; w < nw; ++w) s += red[w * NV + threadIdx.x];
+    red[32 * NV + threadIdx.x] = s;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = red[32 * NV + k];
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void process_element(const StatsArgs<T>& a, int e, int N, int cap, unsigned char* raw,
+                                int moves) {
+  __shared__ double red[32 * 8 + 8];
+  __shared__ int sh_n;
+  // smem carve-up for cap entries
+  StatsSmem<T> s;
+  unsigned char* ptr = raw;
+  auto take = [&](size_t bytes) { unsigned char* r = ptr; ptr += (bytes + 15) & ~size_t(15); return r; };
+  s.u = reinterpret_cast<T*>(take(sizeof(T) * cap));
+  s.v = reinterpret_cast<T*>(take(sizeof(T) * cap));
+  s.w = reinterpret_cast<T*>(take(sizeof(T) * cap));
+  s.om = reinterpret_cast<T*>(take(sizeof(T) * cap));
+  s.psi = reinterpret_cast<T*>(take(sizeof(T) * cap));
+  s.pid = reinterpret_cast<uint32_t*>(take(sizeof(uint32_t) * cap));
+  s.slot = reinterpret_cast<int32_t*>(take(sizeof(int32_t) * cap));
+  s.perm = reinterpret_cast<uint16_t*>(take(sizeof(uint16_t) * cap));
+  s.grp = reinterpret_cast<uint8_t*>(take(cap));
+
+  const int tid = threadIdx.x;
+  if (tid == 0) sh_n = 0;
+  __syncthreads();
+  // gather the element's particles: its list minus those moved out, plus those moved in
+  const int32_t o = a.off[e], c = a.cnt[e];
+  for (int j = tid; j < c; j += blockDim.x) {
+    const int32_t q = a.idx[o + j];
+    if (moves && a.p.elem[q] != e) continue;
+    const int at = atomicAdd(&sh_n, 1);
+    if (at < cap) s.slot[at] = q;
+  }
+  if (moves) {
+    const int32_t gn = a.gain[e], g0 = a.goff[e];
+    for (int j = tid; j < gn; j += blockDim.x) {
+      const int32_t q = a.movers[g0 + j];
+      if (q < 0 || q >= a.np) continue;
+      const int at = atomicAdd(&sh_n, 1);
+      if (at < cap) s.slot[at] = q;
+    }
+  }
+  __syncthreads();
+  const int n = min(min(sh_n, cap), N);
+  if (tid == 0 && sh_n != N) atomicCAS(a.err, 0, PDFX_ERR_CAPACITY);
+  for (int j = tid; j < n; j += blockDim.x) {
+    const int32_t q = s.slot[j];
+    s.u[j] = a.p.u[q];
+    s.v[j] = a.p.v[q];
+    s.w[j] = a.p.w[q];
+    s.om[j] = a.p.om[q];
+    s.psi[j] = a.p.psi[q];
+    s.pid[j] = a.p.pid[q];
+    s.grp[j] = 0;
+  }
+  int P = 1;
+  while (P < n) P <<= 1;
+  for (int j = tid; j < P; j += blockDim.x) s.perm[j] = static_cast<uint16_t>(j);
+  __syncthreads();
+
+  // effective bins (Sect. 3.5 reading): g_l = max(1, min(b_l, n / (g_1..g_{l-1} min_per_bin)))
+  int g[3];
+  {
+    int Gp = 1;
+    for (int l = 0; l < 3; ++l) {
+      int cap_l = n / (Gp * a.min_per_bin);
+      int gl = a.bins[l] < cap_l ? a.bins[l] : cap_l;
+      if (gl < 1) gl = 1;
+      g[l] = gl;
+      Gp *= gl;
+    }
+  }
+  // level 1: sort by (u, id)
+  if (n > 1) bitonic_sort(s, s.u, n, P);
+
+  // moments in sorted order (deterministic): means, then central moments
+  {
+    double m[5] = {0, 0, 0, 0, 0};
+    for (int j = tid; j < n; j += blockDim.x) {
+      const int q = s.perm[j];
+      m[0] += static_cast<double>(s.u[q]);
+      m[1] += static_cast<double>(s.v[q]);
+      m[2] += static_cast<double>(s.w[q]);
+      m[3] += static_cast<double>(s.om[q]);
+      m[4] += static_cast<double>(s.psi[q]);
+    }
+    block_sums<5>(m, red);
+    const double inv = n > 0 ? 1.0 / n : 0.0;
+    const double mu = m[0] * inv, mv = m[1] * inv, mw = m[2] * inv, mo = m[3] * inv, mp = m[4] * inv;
+    double c2[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int j = tid; j < n; j += blockDim.x) {
+      const int q = s.perm[j];
+      const double du = static_cast<double>(s.u[q]) - mu, dv = static_cast<double>(s.v[q]) - mv,
+                   dw = static_cast<double>(s.w[q]) - mw, dp = static_cast<double>(s.psi[q]) - mp;
+      c2[0] += du * du; c2[1] += dv * dv; c2[2] += dw * dw;
+      c2[3] += du * dv; c2[4] += du * dw; c2[5] += dv * dw;
+      c2[6] += dp * dp;
+    }
+    block_sums<7>(c2, red);
+    if (tid == 0) {
+      double* em = a.emom + static_cast<size_t>(kNS) * e;
+      em[0] = static_cast<double>(n);
+      em[1] = mu; em[2] = mv; em[3] = mw;
+      for (int k = 0; k < 6; ++k) em[4 + k] = c2[k] * inv;
+      em[10] = mo; em[11] = mp; em[12] = c2[6] * inv;
+      a.gbin[3 * e] = g[0];
+      a.gbin[3 * e + 1] = g[1];
+      a.gbin[3 * e + 2] = g[2];
+    }
+  }
+  // levels 2 and 3: sort each group of the previous level by (v, id), then (w, id)
+  {
+    int Gprev = g[0];
+    const T* keys[2] = {s.v, s.w};
+    for (int l = 1; l < 3; ++l) {
+      if (g[l] > 1) {
+        for (int j = tid; j < n; j += blockDim.x)
+          s.grp[s.perm[j]] = static_cast<uint8_t>((static_cast<int64_t>(Gprev) * j) / n);
+        __syncthreads();
+        bitonic_sort(s, keys[l - 1], n, P);
+      }
+      Gprev *= g[l];
+    }
+  }
+  // Appendix A: bin i = G n / N, conditional means, conditioning pointers
+  const int G = g[0] * g[1] * g[2];
+  double* vc = a.vcce + static_cast<size_t>(a.G) * e;
+  for (int i = tid; i < a.G; i += blockDim.x) {
+    if (i < G && n > 0) {
+      const int lo = static_cast<int>((static_cast<int64_t>(i) * n + G - 1) / G);
+      const int hi = static_cast<int>((static_cast<int64_t>(i + 1) * n + G - 1) / G);
+      double sum = 0.0;
+      for (int j = lo; j < hi; ++j) sum += static_cast<double>(s.psi[s.perm[j]]);
+      vc[i] = sum / (hi - lo);
+    } else {
+      vc[i] = 0.0;
+    }
+  }
+  if (a.resort) {
+    const int32_t fo = a.foff[e];
+    for (int j = tid; j < n; j += blockDim.x) {
+      const int q = s.perm[j];
+      const int32_t d = fo + j;
+      if (d >= a.np) break;
+      const int32_t src = s.slot[q];
+      a.out.x[d] = a.p.x[src];
+      a.out.y[d] = a.p.y[src];
+      a.out.u[d] = s.u[q];
+      a.out.v[d] = s.v[q];
+      a.out.w[d] = s.w[q];
+      a.out.om[d] = s.om[q];
+      a.out.psi[d] = s.psi[q];
+      a.out.pid[d] = s.pid[q];
+      a.out.elem[d] = e;
+      a.out.cp[d] = static_cast<uint8_t>((static_cast<int64_t>(G) * j) / n);
+    }
+  } else {
+    for (int j = tid; j < n; j += blockDim.x)
+      a.p.cp[s.slot[s.perm[j]]] = static_cast<uint8_t>((static_cast<int64_t>(G) * j) / n);
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kStatsThreads) stats_small_kernel(const StatsArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  const int moves = a.scal[0] > 0;
+  const int e = blockIdx.x;
+  if (e >= a.ne) return;
+  const int N = moves ? a.fin[e] : a.cnt[e];
+  if (N > kSmallCap) return;      // handled by the large-element kernel
+  process_element(a, e, N, kSmallCap, raw, moves);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kStatsThreads) stats_big_kernel(const StatsArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char raw[];
+  const int moves = a.scal[0] > 0;
+  const int nbig = a.scal[3];
+  for (int b = blockIdx.x; b < nbig; b += gridDim.x) {
+    const int e = a.big_list[b];
+    const int N = moves ? a.fin[e] : a.cnt[e];
+    if (N > kBigCap) {
+      if (threadIdx.x == 0) {
+        atomicAdd(a.diag + kDiagCapacity, 1ull);
+        atomicCAS(a.err, 0, PDFX_ERR_CAPACITY);
+      }
+      continue;
+    }
+    process_element(a, e, N, kBigCap, raw, moves);
+  }
+}
+
+template <typename T>
+size_t stats_smem_bytes(int cap) {
+  auto r = [](size_t b) { return (b + 15) & ~size_t(15); };
+  return 5 * r(sizeof(T) * cap) + r(4 * cap) + r(4 * cap) + r(2 * cap) + r(cap);
+}
+
+__global__ void node_average_kernel(const double* __restrict__ emom, const int32_t* __restrict__ ne_off,
+                                    const int32_t* __restrict__ ne_list, int32_t nn, double* nmom) {
+  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  double acc[kNS];
+#pragma unroll
+  for (int s = 0; s < kNS; ++s) acc[s] = 0.0;
+  int c = 0;
+  for (int i = ne_off[n]; i < ne_off[n + 1]; ++i) {
+    const double* em = emom + static_cast<size_t>(kNS) * ne_list[i];
+    if (em[0] < 1.0) continue;
+#pragma unroll
+    for (int s = 0; s < kNS; ++s) acc[s] += em[s];
+    ++c;
+  }
+  double* out = nmom + static_cast<size_t>(kNS) * n;
+#pragma unroll
+  for (int s = 0; s < kNS; ++s) out[s] = c > 0 ? acc[s] / c : 0.0;
+}
+
+}  // namespace
+
+void launch_plan(Plan& pl, int32_t ne, int minnpel, int allow_moves, cudaStream_t s) {
+  plan_kernel<<<1, kPlanThreads, 0, s>>>(pl, ne, minnpel, allow_moves);
+}
+
+void launch_scatter(const int32_t* elem, int64_t np, Plan& pl, cudaStream_t s) {
+  if (np <= 0) return;
+  scatter_kernel<<<static_cast<unsigned>((np + 255) / 256), 256, 0, s>>>(elem, np, pl.cursor, pl.idx);
+}
+
+template <typename T>
+void launch_redistribute(Particles<T> p, Plan& pl, int32_t ne, int64_t np, const ElemGeo<T>* geo,
+                         const ElemTopo* topo, T period_x, int source_on, T sx, T sy, T sr,
+                         uint32_t step, uint32_t k0, uint32_t k1, int num_sms,
+                         unsigned long long* diag, int* err, cudaStream_t s) {
+  const unsigned grid = static_cast<unsigned>(num_sms > 0 ? num_sms : 1);
+  static bool configured = false;
+  const size_t apply_smem = 12 * static_cast<size_t>(kRedistCap);
+  if (!configured) {
+    cudaFuncSetAttribute(apply_moves_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(apply_smem));
+    configured = true;
+  }
+  select_donors_kernel<T><<<grid, kRedistThreads, 0, s>>>(p, pl);
+  apply_moves_kernel<T><<<grid, kRedistThreads, apply_smem, s>>>(p, pl, np, geo, topo, period_x,
+                                                                  source_on, sx, sy, sr, step, k0, k1);
+  commit_moves_kernel<T><<<grid, 256, 0, s>>>(p, pl, np, ne, diag, err);
+}
+
+template <typename T>
+void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s) {
+  static bool configured = false;
+  const size_t small = stats_smem_bytes<T>(kSmallCap), big = stats_smem_bytes<T>(kBigCap);
+  static_assert(5 * 8 * kBigCap + 11 * kBigCap <= 227 * 1024, "large-element tile exceeds shared memory");
+  if (!configured) {
+    cudaFuncSetAttribute(stats_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(small));
+    cudaFuncSetAttribute(stats_big_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         static_cast<int>(big));
+    configured = true;
+  }
+  if (a.ne > 0) stats_small_kernel<T><<<a.ne, kStatsThreads, small, s>>>(a);
+  stats_big_kernel<T><<<static_cast<unsigned>(num_sms > 0 ? num_sms : 1), kStatsThreads, big, s>>>(a);
+}
+
+void launch_node_average(const double* emom, const int32_t* ne_off, const int32_t* ne_list,
+                         int32_t nn, double* nmom, cudaStream_t s) {
+  if (nn <= 0) return;
+  node_average_kernel<<<(nn + 127) / 128, 128, 0, s>>>(emom, ne_off, ne_list, nn, nmom);
+}
+
+#define PDFX_INSTANTIATE(T)                                                                    \
+  template void launch_redistribute<T>(Particles<T>, Plan&, int32_t, int64_t, const ElemGeo<T>*, \
+                                       const ElemTopo*, T, int, T, T, T, uint32_t, uint32_t,   \
+                                       uint32_t, int, unsigned long long*, int*, cudaStream_t); \
+  template void launch_stats<T>(const StatsArgs<T>&, int, cudaStream_t);
+PDFX_INSTANTIATE(double)
+PDFX_INSTANTIATE(float)
+#undef PDFX_INSTANTIATE
+
+}  // namespace pdfx

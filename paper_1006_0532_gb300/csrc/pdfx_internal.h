@@ -1,0 +1,193 @@
+// Host-side context of one pdfx instance and the kernel launch interface.
+#pragma once
+
+#include <cstdint>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/pdfx.h"
+#include "pdfx_device.cuh"
+
+namespace pdfx {
+
+// Model constants in the working precision, passed by value to the advance kernel.
+template <typename T>
+struct Model {
+  T C1, C2, C3, C4, CT, Cw1, Cw2, nu, C0, Cs, Ct, Cphi, src_x, src_y, src_r, period_x;
+  int c0_mode, tm_mode, interp_mode, source_on;
+};
+
+// Particle storage (structure of arrays) in the working precision.
+template <typename T>
+struct Particles {
+  T *x = nullptr, *y = nullptr, *u = nullptr, *v = nullptr, *w = nullptr, *om = nullptr,
+    *psi = nullptr;
+  uint32_t* pid = nullptr;
+  int32_t* elem = nullptr;
+  uint8_t* cp = nullptr;
+};
+
+// Arguments of the advance kernel (Eqs. 7, 27, 19, 24; Sect. 3.8; Sect. 3.6).
+template <typename T>
+struct AdvanceArgs {
+  Particles<T> p;
+  int64_t np;
+  const ElemGeo<T>* geo;
+  const ElemTopo* topo;
+  const Line<T>* walls;
+  const Line<T>* fslines;
+  const int32_t* ne_off;
+  const int32_t* ne_list;
+  int32_t ne;
+  const T* fields;
+  const double* vcce;
+  int G;
+  int32_t* cnt;
+  unsigned long long* diag;
+  int* err;
+  Model<T> m;
+  T dt;
+  uint32_t step, k0, k1;
+};
+
+// Arguments of the statistics / conditional-mean kernels.
+template <typename T>
+struct StatsArgs {
+  Particles<T> p;       // current state
+  Particles<T> out;     // re-ordered state (written when resort != 0)
+  int resort;
+  const int32_t* cnt;   // particles per element after advance (list segment sizes)
+  const int32_t* off;   // list offsets
+  const int32_t* idx;   // element lists of particle slots (-1 = moved out)
+  const int32_t* fin;   // final counts after redistribution
+  const int32_t* foff;  // exclusive scan of fin
+  const int32_t* gain;  // particles received per element
+  const int32_t* goff;  // offsets into movers of received particles
+  const int32_t* movers;
+  const int32_t* big_list;
+  const int32_t* scal;  // plan scalars: 0 moves, 3 number of large elements
+  int32_t ne;
+  int64_t np;
+  int bins[3];
+  int min_per_bin;
+  int G;
+  double* emom;
+  double* vcce;
+  int32_t* gbin;
+  unsigned long long* diag;
+  int* err;
+};
+
+// Scratch of the statistics pipeline (device).
+struct Plan {
+  int32_t* cnt = nullptr;      // [ne]
+  int32_t* off = nullptr;      // [ne + 1]
+  int32_t* cursor = nullptr;   // [ne]
+  int32_t* fin = nullptr;      // [ne]
+  int32_t* foff = nullptr;     // [ne + 1]
+  int32_t* gain = nullptr;     // [ne]
+  int32_t* goff = nullptr;     // [ne + 1]
+  int32_t* loss = nullptr;     // [ne]
+  int32_t* doff = nullptr;     // [ne + 1]
+  int32_t* recips = nullptr;   // [ne] elements that receive
+  int32_t* donors = nullptr;   // [ne] elements that give
+  int32_t* big_list = nullptr; // [ne] elements above the small binning capacity
+  int32_t* scal = nullptr;     // [16]: 0 T, 1 n_recips, 2 n_donors, 3 n_big, 4 min, 5 max
+  int64_t* hist = nullptr;     // [2 (kHistCap + 1)] prefix sums for the closed form
+  int32_t* idx = nullptr;      // [np] element lists
+  int32_t* movers = nullptr;   // [np] particle slots that move (by move index)
+  int32_t* mrecip = nullptr;   // [np] recipient element per move
+  double* mvals = nullptr;     // [np][7] new values per move
+};
+
+constexpr int kHistCap = 8192;      // counts above this are clipped for the closed form
+constexpr int kSmallCap = 1024;     // binning capacity of the per-element kernel
+constexpr int kBigCap = 4096;       // binning capacity of the large-element kernel
+
+struct Ctx {
+  pdfx_params prm{};
+  pdfx_allocator alloc{};
+  bool has_alloc = false;
+  int device = 0;
+  int num_sms = 0;
+  // grid
+  int32_t nn = 0, ne = 0;
+  void* geo = nullptr;          // ElemGeo<T>[ne]
+  ElemTopo* topo = nullptr;     // [ne]
+  void* walls = nullptr;        // Line<T>[n_walls]
+  void* fslines = nullptr;      // Line<T>[n_fs]
+  int32_t* ne_off = nullptr;    // [nn + 1]
+  int32_t* ne_list = nullptr;   // [3 ne]
+  std::vector<int32_t> h_ne_off, h_ne_list;
+  bool have_grid = false;
+  // fields
+  void* fields = nullptr;       // T[nn][32]
+  double* fields64 = nullptr;   // staging for the FP32 conversion
+  bool have_fields = false;
+  // particles (double buffered for re-ordering)
+  int64_t np = 0;
+  int cur = 0;
+  void* pbuf[2] = {nullptr, nullptr};  // one allocation per buffer
+  size_t pbuf_bytes = 0;
+  uint32_t step = 0;
+  int steps_since_sort = 0;
+  // statistics
+  Plan plan;
+  double* emom = nullptr;       // [ne][13]
+  double* nmom = nullptr;       // [nn][13]
+  double* vcce = nullptr;       // [ne][G]
+  int32_t* gbin = nullptr;      // [ne][3]
+  int G = 1;
+  // diagnostics
+  unsigned long long* diag = nullptr;  // [kDiagCount]
+  int* err = nullptr;
+  int64_t steps_done = 0;
+  int64_t launches = 0;
+  // profiling
+  bool profiling = false;
+  static constexpr int kStages = 6;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
+  double stage_ms[kStages] = {0};
+  int64_t stage_n[kStages] = {0};
+  // allocations to release
+  std::vector<std::pair<void*, size_t>> owned;
+};
+
+template <typename T>
+Particles<T> particles_of(Ctx& c, int which);
+
+// Kernel launchers (defined in the .cu files).
+template <typename T>
+void launch_advance(const AdvanceArgs<T>& a, int num_sms, cudaStream_t s);
+template <typename T>
+void launch_init(Particles<T> p, int32_t ne, int32_t ppe, const ElemGeo<T>* geo,
+                 const ElemTopo* topo, const T* fields, Model<T> m, uint32_t k0, uint32_t k1,
+                 unsigned long long* diag, cudaStream_t s);
+void launch_count(const int32_t* elem, int64_t np, int32_t* cnt, cudaStream_t s);
+void launch_plan(Plan& pl, int32_t ne, int minnpel, int allow_moves, cudaStream_t s);
+void launch_scatter(const int32_t* elem, int64_t np, Plan& pl, cudaStream_t s);
+template <typename T>
+void launch_redistribute(Particles<T> p, Plan& pl, int32_t ne, int64_t np, const ElemGeo<T>* geo,
+                         const ElemTopo* topo, T period_x, int source_on, T sx, T sy, T sr,
+                         uint32_t step, uint32_t k0, uint32_t k1, int num_sms,
+                         unsigned long long* diag, int* err, cudaStream_t s);
+template <typename T>
+void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s);
+void launch_node_average(const double* emom, const int32_t* ne_off, const int32_t* ne_list,
+                         int32_t nn, double* nmom, cudaStream_t s);
+template <typename T>
+void launch_gather_by_pid(Particles<T> p, int64_t np, double* x, double* y, double* u, double* v,
+                          double* w, double* om, double* psi, int32_t* elem, uint8_t* cp,
+                          cudaStream_t s);
+template <typename T>
+void launch_load_state(Particles<T> p, int64_t np, const double* x, const double* y,
+                       const double* u, const double* v, const double* w, const double* om,
+                       const double* psi, const int32_t* elem, cudaStream_t s);
+void launch_convert_fields(const double* in, float* out, int64_t n, cudaStream_t s);
+template <typename T>
+void launch_check_finite(Particles<T> p, int64_t np, unsigned long long* diag, int* err,
+                         cudaStream_t s);
+
+}  // namespace pdfx

@@ -1,0 +1,308 @@
+"""CUDA path vs the CPU oracle, element by element, from the same seeded inputs.
+
+Tolerances (relative, with a per-quantity scale floor so values near zero compare on an
+absolute scale):  FP64 form: particle states 1e-12, statistics 1e-10, element indices,
+conditioning pointers and effective bins bit-exact.  FP32 form: states 1e-5, statistics
+1e-6; particles whose element or wall decision sits within the FP32 rounding band of a
+threshold are exempt, counted and bounded.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_1006_0532_gb300 import synth
+from helpers import STATE_KEYS, base_params, homogeneous_fields, period_diff
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1006_0532_gb300 import _binding as B  # noqa: E402
+
+
+def gpu_ctx(grid, params, fields, precision=0, sort_every=4):
+    p = dict(params)
+    p.setdefault("period_x", grid.period_x)
+    p.update(precision=precision, sort_every=sort_every)
+    c = B.Context(p)
+    c.set_grid(grid)
+    c.set_fields(fields)
+    return c
+
+
+def scale_of(a):
+    s = float(np.sqrt(np.mean(np.square(a)))) if a.size else 1.0
+    return s if s > 0 else 1.0
+
+
+def compare_state(g, o, L, tol, skip=None):
+    """Max relative error over particles (skip: boolean mask of exempt particles)."""
+    worst = {}
+    for k in STATE_KEYS:
+        a, b = g[k], o[k]
+        if k == "x":
+            d = np.abs(period_diff(a, b, L))
+        else:
+            d = np.abs(a - b)
+        r = d / np.maximum(np.abs(b), scale_of(b))
+        if skip is not None:
+            r = r[~skip]
+        worst[k] = float(r.max()) if r.size else 0.0
+    bad = {k: v for k, v in worst.items() if v > tol}
+    assert not bad, bad
+    return worst
+
+
+def compare_stats(a, b, tol, rows=None):
+    if rows is not None:
+        a, b = a[rows], b[rows]
+    sc = np.array([scale_of(b[:, j]) for j in range(b.shape[1])])
+    r = np.abs(a - b) / np.maximum(np.abs(b), sc[None, :])
+    assert r.max() <= tol, (float(r.max()), np.unravel_index(np.argmax(r), r.shape))
+    return float(r.max())
+
+
+def both(name, ppe=None, precision=0, **over):
+    w = synth.workload(name)
+    params = dict(w["params"])
+    params.update(over)
+    g = w["grid"]
+    o = oracle.Oracle(g, params, w["fields"])
+    c = gpu_ctx(g, params, w["fields"], precision=precision)
+    return w, g, o, c, (ppe or w["ppe"])
+
+
+# ----------------------------------------------------------------------------------------
+# FP64 form
+# ----------------------------------------------------------------------------------------
+
+def test_init_matches_oracle_f64():
+    w, g, o, c, ppe = both("channel_2k", ppe=25)
+    o.init_particles(ppe)
+    c.init_particles(ppe)
+    so, sg = o.get_particles(), c.get_particles()
+    assert np.array_equal(sg["elem"], so["elem"])
+    compare_state(sg, so, g.period_x, 1e-12)
+    assert np.array_equal(sg["cp"], so["cp"])
+    vo, go = o.bins()
+    vg, gg = c.bins()
+    assert np.array_equal(gg, go)
+    compare_stats(vg, vo, 1e-12)
+    eo, co = o.element_stats()
+    eg, cg = c.element_stats()
+    assert np.array_equal(cg, co)
+    compare_stats(eg, eo, 1e-10)
+    compare_stats(c.nodal_stats(), o.nodal_stats(), 1e-10)
+
+
+@pytest.mark.parametrize("name,steps", [("channel_tiny", 3), ("channel_2k", 10)])
+def test_steps_match_oracle_f64(name, steps):
+    """The plain FP64 workload: 211,600 particles on 2116 triangles, 10 steps."""
+    w, g, o, c, ppe = both(name)
+    o.init_particles(ppe)
+    c.init_particles(ppe)
+    for _ in range(steps):
+        o.step(w["dt"])
+        c.step(w["dt"])
+    so, sg = o.get_particles(), c.get_particles()
+    # element indices bit-exact except for particles on a shared edge (either element)
+    diff = sg["elem"] != so["elem"]
+    for p in np.where(diff)[0]:
+        assert o.lam(sg["elem"][p], sg["x"][p], sg["y"][p]).min() > -1e-12
+    assert diff.sum() <= 2
+    compare_state(sg, so, g.period_x, 1e-12)
+    if diff.sum() == 0:
+        assert np.array_equal(sg["cp"], so["cp"])
+        vo, go = o.bins()
+        vg, gg = c.bins()
+        assert np.array_equal(gg, go)
+        compare_stats(vg, vo, 1e-10)
+        eo, co = o.element_stats()
+        eg, cg = c.element_stats()
+        assert np.array_equal(cg, co)
+        compare_stats(eg, eo, 1e-10)
+        compare_stats(c.nodal_stats(), o.nodal_stats(), 1e-10)
+    dg, do = c.diag(), o.diag()
+    assert dg["error"] == 0 and dg["lost"] == 0
+    assert dg["wall_hits"] == do["wall_hits"]
+    assert dg["hops_total"] == do["hops_total"]
+
+
+def _imbalanced_state(g, counts, seed):
+    rng = np.random.default_rng(seed)
+    xs, ys, es = [], [], []
+    for e, n in enumerate(counts):
+        tri = g.tri[e]
+        xy = g.node_xy[tri].copy()
+        for k in (1, 2):
+            d = xy[k, 0] - xy[0, 0]
+            if d > g.period_x / 2:
+                xy[k, 0] -= g.period_x
+            elif d < -g.period_x / 2:
+                xy[k, 0] += g.period_x
+        w = rng.dirichlet([1, 1, 1], size=n)
+        p = w @ xy
+        xs.append(p[:, 0] % g.period_x)
+        ys.append(p[:, 1])
+        es.append(np.full(n, e, dtype=np.int32))
+    x, y, e = np.concatenate(xs), np.concatenate(ys), np.concatenate(es)
+    n = x.size
+    return dict(x=x, y=y, u=0.9 + 0.05 * rng.normal(size=n), v=0.05 * rng.normal(size=n),
+                w=0.05 * rng.normal(size=n), om=rng.gamma(4, 0.25 * 3.0, size=n),
+                psi=rng.uniform(size=n), elem=e)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_redistribution_matches_oracle_f64(seed):
+    """Appendix B with MINNPEL above some counts: final counts, movers, their new states."""
+    w = synth.workload("channel_tiny")
+    g = w["grid"]
+    rng = np.random.default_rng(100 + seed)
+    counts = rng.integers(20, 80, g.ne)
+    counts[rng.integers(0, g.ne, 6)] = rng.integers(0, 6, 6)     # includes empty elements
+    counts[rng.integers(0, g.ne, 3)] = rng.integers(150, 300, 3)
+    st = _imbalanced_state(g, counts, seed)
+    params = dict(w["params"], minnpel=15)
+    o = oracle.Oracle(g, params, w["fields"])
+    c = gpu_ctx(g, params, w["fields"])
+    o.set_particles(st, 7)
+    c.set_particles(st, 7)
+    o.step(w["dt"])
+    c.step(w["dt"])
+    so, sg = o.get_particles(), c.get_particles()
+    assert np.array_equal(sg["elem"], so["elem"])
+    compare_state(sg, so, g.period_x, 1e-12)
+    assert c.diag()["moves"] == o.diag()["moves"] > 0
+    eo, co = o.element_stats()
+    eg, cg = c.element_stats()
+    assert np.array_equal(cg, co)
+    assert cg.min() >= 15
+    compare_stats(eg, eo, 1e-10)
+    assert np.array_equal(sg["cp"], so["cp"])
+    compare_stats(c.nodal_stats(), o.nodal_stats(), 1e-10)
+
+
+def test_large_element_path_and_empty_elements():
+    """Elements above the 1024-particle binning tile go through the large-element kernel."""
+    w = synth.workload("channel_tiny")
+    g = w["grid"]
+    counts = np.full(g.ne, 30)
+    counts[3] = 1500
+    counts[10] = 3000
+    counts[11] = 0
+    counts[12] = 1
+    st = _imbalanced_state(g, counts, 5)
+    o = oracle.Oracle(g, w["params"], w["fields"])
+    c = gpu_ctx(g, w["params"], w["fields"])
+    o.set_particles(st, 0)
+    c.set_particles(st, 0)
+    for _ in range(2):
+        o.step(w["dt"])
+        c.step(w["dt"])
+    so, sg = o.get_particles(), c.get_particles()
+    assert np.array_equal(sg["elem"], so["elem"])
+    assert np.array_equal(sg["cp"], so["cp"])
+    compare_state(sg, so, g.period_x, 1e-12)
+    eo, _ = o.element_stats()
+    eg, _ = c.element_stats()
+    compare_stats(eg, eo, 1e-10)
+    vo, go = o.bins()
+    vg, gg = c.bins()
+    assert np.array_equal(gg, go)
+    compare_stats(vg, vo, 1e-10)
+
+
+def test_empty_state():
+    w = synth.workload("channel_tiny")
+    g = w["grid"]
+    c = gpu_ctx(g, w["params"], w["fields"])
+    e = np.zeros(0)
+    c.set_particles(dict(x=e, y=e, u=e, v=e, w=e, om=e, psi=e, elem=np.zeros(0, np.int32)), 0)
+    c.step(w["dt"])
+    em, cnt = c.element_stats()
+    assert cnt.sum() == 0 and np.all(em == 0)
+    assert c.check() == 0
+
+
+def test_capacity_error_is_reported():
+    w = synth.workload("channel_tiny")
+    g = w["grid"]
+    counts = np.full(g.ne, 5)
+    counts[0] = 5000                       # above PDFX_MAX_PER_ELEMENT
+    st = _imbalanced_state(g, counts, 6)
+    c = gpu_ctx(g, w["params"], w["fields"])
+    c.set_particles(st, 0)
+    assert c.check() == -7
+
+
+def test_homogeneous_ou_statistics_gpu():
+    """The OU closed form (Eq. 27) holds for the GPU path too (FP64 form)."""
+    g = synth.channel_grid(16, 9, seed=4)
+    k, Om, C0, dt, n = 1.5e-4, 1.0, 2.0, 0.05, 40
+    F, eps = homogeneous_fields(g, k, Om, 0.0, p_iso=0.0, dP=(-0.01, 0.0))
+    P = base_params(nu=0.0, c0_mode=1, C0=C0, source_on=0, seed=21)
+    c = gpu_ctx(g, P, F)
+    c.init_particles(400)
+    for _ in range(n):
+        c.step(dt)
+    st = c.get_particles()
+    m = (st["y"] > 0.2) & (st["y"] < 0.8)
+    a = (eps / 2) / k
+    r = 1 - a * dt
+    var_n = r ** (2 * n) * (2 * k / 3) + C0 * eps / (a * (2 - a * dt)) * (1 - r ** (2 * n))
+    N = int(m.sum())
+    for key in ("u", "v", "w"):
+        assert abs(st[key][m].var() / var_n - 1) < 5 * math.sqrt(2.0 / N)
+
+
+# ----------------------------------------------------------------------------------------
+# FP32 form
+# ----------------------------------------------------------------------------------------
+
+def _round32(st):
+    out = dict(st)
+    for k in STATE_KEYS:
+        out[k] = st[k].astype(np.float32).astype(np.float64)
+    return out
+
+
+def test_one_step_f32_matches_oracle():
+    w = synth.workload("channel_2k")
+    g = w["grid"]
+    params = dict(w["params"])
+    F32 = w["fields"].astype(np.float32).astype(np.float64)
+    o = oracle.Oracle(g, params, F32)
+    o.init_particles(w["ppe"])
+    s0 = _round32(o.get_particles())
+    # geometry is rounded to FP32 on the GPU; keep particles clear of element edges there
+    o.set_particles(s0, 0)
+    c = gpu_ctx(g, params, F32, precision=1)
+    c.set_particles(s0, 0)
+    # initial statistics from identical FP32 values: exact pointers, FP64-level moments
+    sg0 = c.get_particles()
+    assert np.array_equal(sg0["cp"], o.get_particles()["cp"])
+    compare_stats(c.element_stats()[0], o.element_stats()[0], 1e-12)
+    o.step(w["dt"])
+    c.step(w["dt"])
+    so, sg = o.get_particles(), c.get_particles()
+    # exemptions: element choice within the FP32 band of an edge
+    diff = sg["elem"] != so["elem"]
+    for p in np.where(diff)[0]:
+        assert o.lam(sg["elem"][p], so["x"][p], so["y"][p]).min() > -1e-5
+    assert diff.sum() <= 20
+    worst = compare_state(sg, so, g.period_x, 1e-5, skip=diff)
+    # nodal moments away from exempt particles
+    bad_e = np.unique(np.concatenate([sg["elem"][diff], so["elem"][diff]]))
+    eg, cg = c.element_stats()
+    eo, co = o.element_stats()
+    good_e = np.setdiff1d(np.arange(g.ne), bad_e)
+    assert np.array_equal(cg[good_e], co[good_e])
+    compare_stats(eg, eo, 1e-6, rows=good_e)
+    bad_n = np.unique(g.tri[bad_e].ravel()) if bad_e.size else np.zeros(0, int)
+    good_n = np.setdiff1d(np.arange(g.nn), bad_n)
+    compare_stats(c.nodal_stats(), o.nodal_stats(), 1e-6, rows=good_n)
+    assert c.check() == 0
