@@ -57,7 +57,7 @@ class ClockSampler:
     def __enter__(self):
         try:
             self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
-                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                       "--format=csv,noheader,nounits", "-lms", "20"],
                                       stdout=self.f, stderr=subprocess.DEVNULL)
         except Exception:
             self.p = None
@@ -226,7 +226,7 @@ def e2e_form(torch, B, c, w, args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="pdfx", choices=["pdfx", "reference"])
     ap.add_argument("--workload", default="channel_50k")
@@ -294,6 +294,8 @@ def main():
                 "d2h_bytes_per_step": d2h},
         "clocks": r32["clocks"],
         "device_errors": r32["err"],
+        "diag": {k: r32["diag"][k] for k in ("hops_total", "walk_fallback", "walk_brute", "lost",
+                                              "wall_hits", "moves", "capacity_overflow", "nonfinite")},
     }
     if r64 is not None:
         v64 = r64["np"] * world * args.steps / (r64["ms"] * 1e-3)
@@ -303,7 +305,10 @@ def main():
                                                                           "redistribute",
                                                                           "statistics_binning",
                                                                           "node_average"])},
-                            "device_errors": r64["err"]}
+                            "device_errors": r64["err"],
+                            "diag": {k: r64["diag"][k] for k in ("hops_total", "walk_fallback",
+                                                                  "walk_brute", "lost", "wall_hits",
+                                                                  "moves")}}
         line["speedup_f32_vs_f64"] = value / v64
     if not args.no_cpu:
         n, st, el, _ = oracle_sample(args.workload, args.oracle_steps, args.oracle_ppe)

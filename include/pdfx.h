@@ -107,6 +107,8 @@ typedef struct pdfx_diag {
     int64_t moves, source_hits, capacity_overflow, nonfinite;
     int64_t hop_hist[8];      /* particles that needed 0, 1, ..., 6, 7+ hops */
     int32_t error;            /* first device error code seen (PDFX_ERR_*), 0 if none */
+    int32_t lost_records;     /* entries of lost[] in use */
+    double  lost_xy[4][4];    /* first lost particles: x, y, old element, particle id */
 } pdfx_diag;
 
 /* Defaults: Table 4 constants, Cs = 0.02, Ct = 0.7 (Sect. 4.1.2), C0 from Eq. 11,

@@ -45,8 +45,10 @@ struct orc_ctx {
     double *node_xy;      /* [nn][2] */
     int32_t *tri;         /* [ne][3] */
     int8_t *tag;          /* [ne][3] */
-    /* per element, unwrapped in the element's own frame (vertex A at its node) */
-    double *ax, *ay, *bx, *by, *cx, *cy, *area2;   /* b, c relative to A */
+    /* per element: vertices unwrapped across a periodic seam into vertex A's image
+     * (vx, vy [ne][3]), edge vectors B - A and C - A, and twice the signed area */
+    double *vx, *vy;
+    double *ax, *ay, *bx, *by, *cx, *cy, *area2;
     int32_t *nbr;         /* [ne][3]: neighbour across the edge opposite vertex k, -1 outside */
     int32_t *ne_off, *ne_list;   /* node -> elements (ascending element id) */
     /* wall lines: point, inward unit normal (in element frame); type 0 none */
@@ -180,8 +182,7 @@ static int elem_has_node(const orc_ctx *c, int e, int n)
  * pointing toward vertex k, i.e. into the domain.  Returned in f's frame. */
 static void edge_line(const orc_ctx *c, int f, int k, double *px, double *py, double *nx, double *ny)
 {
-    double vx[3] = {c->ax[f], c->ax[f] + c->bx[f], c->ax[f] + c->cx[f]};
-    double vy[3] = {c->ay[f], c->ay[f] + c->by[f], c->ay[f] + c->cy[f]};
+    const double *vx = c->vx + 3 * f, *vy = c->vy + 3 * f;
     int a = (k + 1) % 3, b = (k + 2) % 3;
     double tx = vx[b] - vx[a], ty = vy[b] - vy[a];
     double len = sqrt(tx * tx + ty * ty);
@@ -249,15 +250,29 @@ int orc_create(orc_ctx **out, const orc_params *p, int nn, const double *node_xy
     memcpy(c->tag, edge_tag, 3 * ne);
     double **geo[7] = {&c->ax, &c->ay, &c->bx, &c->by, &c->cx, &c->cy, &c->area2};
     for (int i = 0; i < 7; ++i) *geo[i] = (double *)malloc(sizeof(double) * ne);
+    c->vx = (double *)malloc(sizeof(double) * 3 * ne);
+    c->vy = (double *)malloc(sizeof(double) * 3 * ne);
     for (int e = 0; e < ne; ++e) {
         int A = tri[3 * e], B = tri[3 * e + 1], C = tri[3 * e + 2];
         if (A < 0 || B < 0 || C < 0 || A >= nn || B >= nn || C >= nn) { orc_destroy(c); return -2; }
+        const int n3[3] = {A, B, C};
+        for (int k = 0; k < 3; ++k) {
+            double x = node_xy[2 * n3[k]];
+            /* the image of the node nearest to vertex A (periodic in x) */
+            if (p->period_x > 0.0 && k > 0) {
+                double d = x - node_xy[2 * A];
+                if (d > 0.5 * p->period_x) x -= p->period_x;
+                else if (d < -0.5 * p->period_x) x += p->period_x;
+            }
+            c->vx[3 * e + k] = x;
+            c->vy[3 * e + k] = node_xy[2 * n3[k] + 1];
+        }
         c->ax[e] = node_xy[2 * A];
         c->ay[e] = node_xy[2 * A + 1];
-        c->bx[e] = min_image(node_xy[2 * B] - c->ax[e], p->period_x);
-        c->by[e] = node_xy[2 * B + 1] - c->ay[e];
-        c->cx[e] = min_image(node_xy[2 * C] - c->ax[e], p->period_x);
-        c->cy[e] = node_xy[2 * C + 1] - c->ay[e];
+        c->bx[e] = min_image(node_xy[2 * B] - node_xy[2 * A], p->period_x);
+        c->by[e] = node_xy[2 * B + 1] - node_xy[2 * A + 1];
+        c->cx[e] = min_image(node_xy[2 * C] - node_xy[2 * A], p->period_x);
+        c->cy[e] = node_xy[2 * C + 1] - node_xy[2 * A + 1];
         /* 2 A_e: twice the signed area, positive for counter-clockwise vertices */
         c->area2[e] = c->bx[e] * c->cy[e] - c->by[e] * c->cx[e];
         if (!(c->area2[e] > 0.0)) { orc_destroy(c); return -3; }
@@ -314,7 +329,7 @@ int orc_create(orc_ctx **out, const orc_params *p, int nn, const double *node_xy
 void orc_destroy(orc_ctx *c)
 {
     if (!c) return;
-    void *ptrs[] = {c->node_xy, c->tri, c->tag, c->ax, c->ay, c->bx, c->by, c->cx, c->cy,
+    void *ptrs[] = {c->node_xy, c->tri, c->tag, c->vx, c->vy, c->ax, c->ay, c->bx, c->by, c->cx, c->cy,
                     c->area2, c->nbr, c->ne_off, c->ne_list, c->wall_type, c->wall_px,
                     c->wall_py, c->wall_nx, c->wall_ny, c->fs_type, c->fs_px, c->fs_py,
                     c->fs_nx, c->fs_ny, c->fields, c->x, c->y, c->u, c->v, c->w, c->om,
@@ -347,26 +362,41 @@ int orc_neighbors(const orc_ctx *c, int32_t *nbr)
 /* Area coordinates and interpolation (Eqs. 37-38, 43-45).                              */
 /* ------------------------------------------------------------------------------------ */
 
-/* Eqs. 44-45: N^A and N^C are half the signed cross products pivoted at vertex B; the
- * area coordinates are lambda = N / A_e and N^B = A_e - N^A - N^C.  Reading: the paper
- * prints |.| but calls them signed; the signed z-component is used (vertices counter-
- * clockwise).  The particle's x is taken as its minimum image relative to vertex A. */
-void orc_lambda(const orc_ctx *c, int e, double x, double y, double lam[3])
+/* Eqs. 44-45 and Fig. 1: the area coordinate of a vertex is half the signed cross product
+ * of the edge opposite that vertex with the vector from one end of that edge to the
+ * particle, over A_e (N^A from (r_C - r_B) x (r_P - r_B), Eq. 44; N^C from
+ * (r_P - r_B) x (r_A - r_B), Eq. 45; N^B likewise).  Readings: the paper prints |.| but
+ * calls the values signed, so the signed z-component is used (counter-clockwise
+ * vertices); every N^k is formed by the same construction (N^B is not taken as
+ * A_e - N^A - N^C, the same number in exact arithmetic); and each edge is pivoted at its
+ * lower-numbered node, with node x taken as the minimum image, so the two elements
+ * sharing an edge evaluate it with the same rounding and opposite signs: every point of
+ * the domain lies in at least one element (Eq. 43 closed).  area_cross returns 2 N^k. */
+static double edge_cross(const orc_ctx *c, int a, int b, double x, double y)
 {
-    double dx = min_image(x - c->ax[e], c->p.period_x);
-    double dy = y - c->ay[e];
-    double bx = c->bx[e], by = c->by[e], cx = c->cx[e], cy = c->cy[e];
-    /* (r_C - r_B) x (r_P - r_B) */
-    double nA2 = (cx - bx) * (dy - by) - (cy - by) * (dx - bx);
-    /* (r_P - r_B) x (r_A - r_B), with r_A = 0 */
-    double nC2 = (dx - bx) * (-by) - (dy - by) * (-bx);
-    lam[0] = nA2 / c->area2[e];
-    lam[2] = nC2 / c->area2[e];
-    lam[1] = 1.0 - lam[0] - lam[2];
+    const double *xy = c->node_xy;
+    double sign = 1.0;
+    if (a > b) { int t = a; a = b; b = t; sign = -1.0; }
+    double ex = min_image(xy[2 * b] - xy[2 * a], c->p.period_x), ey = xy[2 * b + 1] - xy[2 * a + 1];
+    double px = min_image(x - xy[2 * a], c->p.period_x), py = y - xy[2 * a + 1];
+    return sign * (ex * py - ey * px);
 }
 
-/* Eq. 43 as a closed test (Reading: the strict inequalities would leave edge points in
- * no element). */
+static void area_cross(const orc_ctx *c, int e, double x, double y, double N2[3])
+{
+    const int32_t *t = c->tri + 3 * e;
+    for (int k = 0; k < 3; ++k) N2[k] = edge_cross(c, t[(k + 1) % 3], t[(k + 2) % 3], x, y);
+}
+
+void orc_lambda(const orc_ctx *c, int e, double x, double y, double lam[3])
+{
+    double N2[3];
+    area_cross(c, e, x, y, N2);
+    for (int k = 0; k < 3; ++k) lam[k] = N2[k] / c->area2[e];
+}
+
+/* Eq. 43 as a closed test on the signed areas (Reading: the strict inequalities would
+ * leave edge points in no element). */
 static int lambda_inside(const double lam[3])
 {
     return lam[0] >= 0.0 && lam[1] >= 0.0 && lam[2] >= 0.0;
@@ -387,10 +417,10 @@ void orc_interp(const orc_ctx *c, int e, const double lam[3], double q[32])
 
 int orc_brute_locate(const orc_ctx *c, double x, double y)
 {
-    double lam[3];
+    double N2[3];
     for (int e = 0; e < c->ne; ++e) {
-        orc_lambda(c, e, x, y, lam);
-        if (lambda_inside(lam)) return e;
+        area_cross(c, e, x, y, N2);
+        if (lambda_inside(N2)) return e;
     }
     return -1;
 }
@@ -403,11 +433,11 @@ int orc_brute_locate(const orc_ctx *c, double x, double y)
  * an error).  Returns -1 if the point lies in no element. */
 int orc_walk(orc_ctx *c, int e0, double x, double y, int *hops)
 {
-    double lam[3];
+    double lam[3];   /* 2 N^k: same signs and order as the area coordinates */
     int e = e0;
     *hops = 0;
     for (;;) {
-        orc_lambda(c, e, x, y, lam);
+        area_cross(c, e, x, y, lam);
         if (lambda_inside(lam)) return e;
         if (*hops >= HOP_LIMIT) break;
         int k = 0;
@@ -425,7 +455,7 @@ int orc_walk(orc_ctx *c, int e0, double x, double y, int *hops)
         for (int i = c->ne_off[n]; i < c->ne_off[n + 1]; ++i) {
             int f = c->ne_list[i];
             if (best >= 0 && f >= best) continue;
-            orc_lambda(c, f, x, y, lam);
+            area_cross(c, f, x, y, lam);
             if (lambda_inside(lam)) best = f;
         }
     }

@@ -61,7 +61,9 @@ DIAG_NAMES = ("steps", "hops_total", "walk_fallback", "walk_brute", "lost", "wal
 
 class Diag(C.Structure):
     _fields_ = [(n, C.c_int64) for n in DIAG_NAMES] + [("hop_hist", C.c_int64 * 8),
-                                                        ("error", C.c_int32)]
+                                                        ("error", C.c_int32),
+                                                        ("lost_records", C.c_int32),
+                                                        ("lost_xy", C.c_double * 16)]
 
 
 def library_path() -> str:
@@ -286,6 +288,7 @@ class Context:
         out = {n: int(getattr(d, n)) for n in DIAG_NAMES}
         out["hop_hist"] = [int(v) for v in d.hop_hist]
         out["error"] = int(d.error)
+        out["lost_records"] = [list(d.lost_xy[4 * i:4 * i + 4]) for i in range(d.lost_records)]
         return out
 
     def reset_diag(self, stream=None):

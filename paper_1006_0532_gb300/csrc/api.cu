@@ -94,13 +94,15 @@ double min_image_h(double d, double L) {
 }
 
 struct HostGeo {
-  std::vector<double> ax, ay, bx, by, cx, cy, area2;
+  std::vector<double> vx, vy;   // [ne][3] vertices, unwrapped toward vertex A
+  std::vector<double> nx;       // [ne][3] node x as given (canonical image)
+  std::vector<double> ax, area2;
 };
 
 // Boundary line of edge k (opposite vertex k) of element f, normal toward vertex k.
 void edge_line_h(const HostGeo& g, int f, int k, double out[4]) {
-  const double vx[3] = {g.ax[f], g.ax[f] + g.bx[f], g.ax[f] + g.cx[f]};
-  const double vy[3] = {g.ay[f], g.ay[f] + g.by[f], g.ay[f] + g.cy[f]};
+  const double* vx = g.vx.data() + 3 * f;
+  const double* vy = g.vy.data() + 3 * f;
   const int a = (k + 1) % 3, b = (k + 2) % 3;
   const double tx = vx[b] - vx[a], ty = vy[b] - vy[a];
   const double len = std::sqrt(tx * tx + ty * ty);
@@ -294,6 +296,10 @@ int do_step(Ctx& c, double dt, cudaStream_t s) {
     a.cnt = c.plan.cnt;
     a.diag = c.diag;
     a.err = c.err;
+    a.brute_list = c.brute_list;
+    a.brute_count = c.err + 1;
+    a.brute_cap = kBruteCap;
+    a.lost_rec = c.lost_rec;
     a.m = model_of<T>(c.prm);
     a.dt = T(dt);
     a.step = c.step;
@@ -392,9 +398,9 @@ int upload_grid(Ctx& c, const HostGeo& g, const std::vector<ElemTopo>& topo,
   const int32_t ne = c.ne;
   std::vector<ElemGeo<T>> hg(static_cast<size_t>(ne));
   for (int32_t e = 0; e < ne; ++e) {
-    hg[e].ax = T(g.ax[e]); hg[e].ay = T(g.ay[e]);
-    hg[e].bx = T(g.bx[e]); hg[e].by = T(g.by[e]);
-    hg[e].cx = T(g.cx[e]); hg[e].cy = T(g.cy[e]);
+    hg[e].x0 = T(g.nx[3 * e]); hg[e].y0 = T(g.vy[3 * e]);
+    hg[e].x1 = T(g.nx[3 * e + 1]); hg[e].y1 = T(g.vy[3 * e + 1]);
+    hg[e].x2 = T(g.nx[3 * e + 2]); hg[e].y2 = T(g.vy[3 * e + 2]);
     hg[e].inv2a = T(1.0 / g.area2[e]);
     hg[e].pad = T(0);
   }
@@ -425,18 +431,31 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
   if (nn <= 0 || ne <= 0 || !xy || !tri || !tag) return PDFX_ERR_ARG;
   const double L = c.prm.period_x;
   HostGeo g;
-  for (auto* v : {&g.ax, &g.ay, &g.bx, &g.by, &g.cx, &g.cy, &g.area2}) v->resize(ne);
+  g.vx.resize(3 * static_cast<size_t>(ne));
+  g.vy.resize(3 * static_cast<size_t>(ne));
+  g.nx.resize(3 * static_cast<size_t>(ne));
+  g.ax.resize(ne);
+  g.area2.resize(ne);
   for (int32_t e = 0; e < ne; ++e) {
     const int A = tri[3 * e], B = tri[3 * e + 1], C = tri[3 * e + 2];
     if (A < 0 || B < 0 || C < 0 || A >= nn || B >= nn || C >= nn || A == B || B == C || A == C)
       return PDFX_ERR_MESH;
-    g.ax[e] = xy[2 * A];
-    g.ay[e] = xy[2 * A + 1];
-    g.bx[e] = min_image_h(xy[2 * B] - g.ax[e], L);
-    g.by[e] = xy[2 * B + 1] - g.ay[e];
-    g.cx[e] = min_image_h(xy[2 * C] - g.ax[e], L);
-    g.cy[e] = xy[2 * C + 1] - g.ay[e];
-    g.area2[e] = g.bx[e] * g.cy[e] - g.by[e] * g.cx[e];   // 2 A_e (Eq. 40 denominator)
+    const int n3[3] = {A, B, C};
+    for (int k = 0; k < 3; ++k) {
+      double x = xy[2 * n3[k]];
+      if (L > 0.0 && k > 0) {   // the image nearest vertex A
+        const double d = x - xy[2 * A];
+        if (d > 0.5 * L) x -= L;
+        else if (d < -0.5 * L) x += L;
+      }
+      g.vx[3 * e + k] = x;
+      g.vy[3 * e + k] = xy[2 * n3[k] + 1];
+      g.nx[3 * e + k] = xy[2 * n3[k]];
+    }
+    g.ax[e] = g.vx[3 * e];
+    const double bx = min_image_h(xy[2 * B] - xy[2 * A], L), by = xy[2 * B + 1] - xy[2 * A + 1];
+    const double cx = min_image_h(xy[2 * C] - xy[2 * A], L), cy = xy[2 * C + 1] - xy[2 * A + 1];
+    g.area2[e] = bx * cy - by * cx;   // 2 A_e (Eq. 40 denominator)
     if (!(g.area2[e] > 0.0)) return PDFX_ERR_MESH;
   }
   // node -> elements, ascending element id
@@ -599,7 +618,9 @@ int pdfx_create(const pdfx_params* p, const pdfx_allocator* alloc, void** out) {
   }
   c->diag = static_cast<unsigned long long*>(dev_alloc(*c, sizeof(unsigned long long) * kDiagCount));
   c->err = static_cast<int*>(dev_alloc(*c, sizeof(int) * 4));
-  if (!c->diag || !c->err) { pdfx_destroy(c); return PDFX_ERR_ALLOC; }
+  c->brute_list = static_cast<int32_t*>(dev_alloc(*c, sizeof(int32_t) * kBruteCap));
+  c->lost_rec = static_cast<double*>(dev_alloc(*c, sizeof(double) * 4 * kLostRecords));
+  if (!c->diag || !c->err || !c->brute_list || !c->lost_rec) { pdfx_destroy(c); return PDFX_ERR_ALLOC; }
   if (cudaMemset(c->diag, 0, sizeof(unsigned long long) * kDiagCount) != cudaSuccess ||
       cudaMemset(c->err, 0, sizeof(int) * 4) != cudaSuccess) {
     pdfx_destroy(c);
@@ -785,6 +806,11 @@ int pdfx_get_diag(void* ctx, pdfx_diag* d, void* stream) {
   }
   d->hop_hist[0] = c->steps_done * c->np - moved;
   d->error = err;
+  const int nrec = static_cast<int>(h[kDiagLostRecord] < kLostRecords ? h[kDiagLostRecord] : kLostRecords);
+  if (nrec > 0) {
+    PDFX_CUDA(cudaMemcpy(d->lost_xy, c->lost_rec, sizeof(double) * 4 * nrec, cudaMemcpyDeviceToHost));
+  }
+  d->lost_records = nrec;
   return PDFX_OK;
 }
 

@@ -16,10 +16,10 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 
 template <typename T>
-__device__ __forceinline__ bool inside(const ElemGeo<T>& g, T x, T y, T L) {
-  T la, lb, lc;
-  area_coords(g, x, y, L, la, lb, lc);
-  return la >= T(0) && lb >= T(0) && lc >= T(0);
+__device__ __forceinline__ bool inside(const ElemGeo<T>& g, const ElemTopo& t, T x, T y, T L) {
+  T na, nb, nc;
+  area_cross(g, t.n0, t.n1, t.n2, x, y, L, na, nb, nc);
+  return na >= T(0) && nb >= T(0) && nc >= T(0);
 }
 
 // Sect. 3.6: walk to the neighbour opposite the lowest area coordinate (ties: lowest local
@@ -32,15 +32,15 @@ __device__ int walk(const AdvanceArgs<T>& a, int e0, T x, T y, int& hops, int& f
   hops = 0;
   for (;;) {
     const ElemGeo<T> g = a.geo[e];
-    T la, lb, lc;
-    area_coords(g, x, y, L, la, lb, lc);
+    const ElemTopo t = a.topo[e];
+    T la, lb, lc;   // 2 N^k: signs and order of the area coordinates
+    area_cross(g, t.n0, t.n1, t.n2, x, y, L, la, lb, lc);
     if (la >= T(0) && lb >= T(0) && lc >= T(0)) return e;
     if (hops >= kHopLimit) break;
     int k = 0;
     T mn = la;
     if (lb < mn) { k = 1; mn = lb; }
     if (lc < mn) k = 2;
-    const ElemTopo t = a.topo[e];
     const int nb = k == 0 ? t.nb0 : (k == 1 ? t.nb1 : t.nb2);
     if (nb < 0) break;
     e = nb;
@@ -55,13 +55,11 @@ __device__ int walk(const AdvanceArgs<T>& a, int e0, T x, T y, int& hops, int& f
     for (int i = a.ne_off[nd]; i < a.ne_off[nd + 1]; ++i) {
       const int f = a.ne_list[i];
       if (best >= 0 && f >= best) continue;
-      if (inside(a.geo[f], x, y, L)) best = f;
+      if (inside(a.geo[f], a.topo[f], x, y, L)) best = f;
     }
   }
   if (best >= 0) return best;
-  brute = 1;
-  for (int f = 0; f < a.ne; ++f)
-    if (inside(a.geo[f], x, y, L)) return f;
+  brute = 1;       // searched over all elements by brute_search_kernel
   return -1;
 }
 
@@ -131,7 +129,7 @@ __global__ void __launch_bounds__(256) advance_kernel(const AdvanceArgs<T> a) {
     if (M.interp_mode == 1) {
       la = lb = lc = T(1) / T(3);
     } else {
-      area_coords(g, X0, Y0, L, la, lb, lc);
+      area_coords(g, tp.n0, tp.n1, tp.n2, X0, Y0, L, la, lb, lc);
     }
     T q[kNF];
     interp_fields(a.fields, tp.n0, tp.n1, tp.n2, la, lb, lc, q);
@@ -279,7 +277,13 @@ __global__ void __launch_bounds__(256) advance_kernel(const AdvanceArgs<T> a) {
     c_fb = fb;
     c_brute = brute;
     hop_bin = hops < 7 ? hops : 7;
-    if (e_new < 0) { e_new = e; c_lost = 1; }
+    if (e_new < 0) {
+      // counted in the old element for now; the brute-force kernel moves it (or flags it)
+      e_new = e;
+      const int at = atomicAdd(a.brute_count, 1);
+      if (at < a.brute_cap) a.brute_list[at] = static_cast<int32_t>(i);
+      else c_lost = 1;
+    }
 
     a.p.x[i] = Xn;
     a.p.y[i] = Yn;
@@ -319,6 +323,48 @@ __global__ void __launch_bounds__(256) advance_kernel(const AdvanceArgs<T> a) {
   }
 }
 
+// Last resort of Sect. 3.6 for particles neither the walk nor the fall-back located: one
+// block per particle tests every element; the lowest containing id wins.  The particle's
+// count moves from its old element to the found one; a particle in no element is flagged.
+template <typename T>
+__global__ void __launch_bounds__(256) brute_search_kernel(AdvanceArgs<T> a) {
+  __shared__ int best_s[8];
+  const int n = min(*a.brute_count, a.brute_cap);
+  for (int j = blockIdx.x; j < n; j += gridDim.x) {
+    const int32_t i = a.brute_list[j];
+    const T x = a.p.x[i], y = a.p.y[i];
+    int best = 0x7fffffff;
+    for (int f = threadIdx.x; f < a.ne; f += blockDim.x)
+      if (f < best && inside(a.geo[f], a.topo[f], x, y, a.m.period_x)) best = f;
+    for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(kFull, best, o));
+    if ((threadIdx.x & 31) == 0) best_s[threadIdx.x >> 5] = best;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int w = 1; w < (blockDim.x >> 5); ++w) best = min(best, best_s[w]);
+      const int32_t e0 = a.p.elem[i];
+      if (best < a.ne) {
+        if (best != e0) {
+          atomicSub(a.cnt + e0, 1);
+          atomicAdd(a.cnt + best, 1);
+          a.p.elem[i] = best;
+        }
+      } else {
+        atomicAdd(a.diag + kDiagLost, 1ull);
+        atomicCAS(a.err, 0, PDFX_ERR_LOST_PARTICLE);
+        const unsigned long long k = atomicAdd(a.diag + kDiagLostRecord, 1ull);
+        if (k < kLostRecords) {
+          double* rec = a.lost_rec + 4 * k;
+          rec[0] = static_cast<double>(x);
+          rec[1] = static_cast<double>(y);
+          rec[2] = static_cast<double>(e0);
+          rec[3] = static_cast<double>(a.p.pid[i]);
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Sect. 3.7: particle id e * ppe + k, uniform in element e (square-root method of Osada
 // et al.), velocity N(<U>, 2k/3 I), frequency Gamma(1/C4, C4 <omega>), scalar from the
 // source disc.
@@ -338,13 +384,13 @@ __global__ void init_kernel(Particles<T> p, int32_t ne, int32_t ppe, const ElemG
     const ElemTopo tp = topo[e];
     const T s = sqrt(uniform01(r0.x, T(0)));
     const T t = uniform01(r0.y, T(0));
-    T px = g.ax + s * (T(1) - t) * g.bx + s * t * g.cx;
-    const T py = g.ay + s * (T(1) - t) * g.by + s * t * g.cy;
+    T px, py;
+    triangle_point(g, s, t, m.period_x, px, py);
     T la, lb, lc;
     if (m.interp_mode == 1) {
       la = lb = lc = T(1) / T(3);
     } else {
-      area_coords(g, px, py, m.period_x, la, lb, lc);
+      area_coords(g, tp.n0, tp.n1, tp.n2, px, py, m.period_x, la, lb, lc);
     }
     T q[kNF];
     interp_fields(fields, tp.n0, tp.n1, tp.n2, la, lb, lc, q);
@@ -436,9 +482,11 @@ inline unsigned blocks_for(int64_t n, int threads) {
 }  // namespace
 
 template <typename T>
-void launch_advance(const AdvanceArgs<T>& a, int, cudaStream_t s) {
+void launch_advance(const AdvanceArgs<T>& a, int num_sms, cudaStream_t s) {
   if (a.np <= 0) return;
+  cudaMemsetAsync(a.brute_count, 0, sizeof(int), s);
   advance_kernel<T><<<blocks_for(a.np, 256), 256, 0, s>>>(a);
+  brute_search_kernel<T><<<static_cast<unsigned>(num_sms > 0 ? num_sms : 1), 256, 0, s>>>(a);
 }
 
 template <typename T>

@@ -331,8 +331,8 @@ __global__ void __launch_bounds__(kRedistThreads) apply_moves_kernel(
       const uint4 rw = philox(make_uint4(pid, step, kPurRedist, 0u), k0, k1);
       const T s = sqrt(uniform01(rw.x, T(0)));
       const T t = uniform01(rw.y, T(0));
-      T px = g.ax + s * (T(1) - t) * g.bx + s * t * g.cx;
-      const T py = g.ay + s * (T(1) - t) * g.by + s * t * g.cy;
+      T px, py;
+      triangle_point(g, s, t, period_x, px, py);
       px = wrap_period(px, period_x);
       int32_t from = q;
       if (n > 0) {

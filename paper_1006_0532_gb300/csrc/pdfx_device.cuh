@@ -20,14 +20,17 @@ enum Purpose : uint32_t { kPurStep = 0, kPurInit = 1, kPurWallGamma = 2, kPurRed
 enum Diag : int {
   kDiagHops = 0, kDiagFallback, kDiagBrute, kDiagLost, kDiagWall, kDiagFreeSlip,
   kDiagOmegaReflect, kDiagC0Clamp, kDiagGammaExhausted, kDiagMoves, kDiagSource,
-  kDiagCapacity, kDiagNonFinite, kDiagHopHist0, kDiagCount = kDiagHopHist0 + 8
+  kDiagCapacity, kDiagNonFinite, kDiagHopHist0, kDiagLostRecord = kDiagHopHist0 + 8,
+  kDiagCount
 };
+constexpr int kLostRecords = 4;    // (x, y, old element, particle id) of the first lost particles
+constexpr int kBruteCap = 4096;    // particles per step that may need the brute-force search
 
-// Per-element geometry in the element's own frame: vertex A at its node, B and C as
-// offsets from A (minimum image across a periodic seam), and 1 / (2 A_e).
+// Per-element geometry: the coordinates of the three nodes (x in [0, period)) and
+// 1 / (2 A_e).
 template <typename T>
 struct __align__(sizeof(T) * 8) ElemGeo {
-  T ax, ay, bx, by, cx, cy, inv2a, pad;
+  T x0, y0, x1, y1, x2, y2, inv2a, pad;
 };
 
 // Per-element topology: node ids, neighbour across the edge opposite each vertex (-1 =
@@ -133,18 +136,52 @@ __device__ __forceinline__ T wrap_period(T x, T L) {
   return x;
 }
 
-// Area coordinates (Eqs. 44-45): N^A and N^C are half the signed cross products pivoted
-// at vertex B, lambda = N / A_e, and lambda_B = 1 - lambda_A - lambda_C.
+// Separately rounded products (no fused multiply-add).  Every evaluation of an edge's
+// cross product then rounds identically, whichever element and slot it is computed for,
+// so the two elements sharing an edge always see exactly opposite values (a point on the
+// edge is in both), and the FP64 form matches host arithmetic bit for bit.
+__device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ float xmul(float a, float b) { return __fmul_rn(a, b); }
+
+// (r_b - r_a) x (r_P - r_a) for the edge a -> b (minimum image in x).
 template <typename T>
-__device__ __forceinline__ void area_coords(const ElemGeo<T>& g, T x, T y, T L, T& la, T& lb,
-                                            T& lc) {
-  const T dx = min_image(x - g.ax, L);
-  const T dy = y - g.ay;
-  const T nA2 = (g.cx - g.bx) * (dy - g.by) - (g.cy - g.by) * (dx - g.bx);
-  const T nC2 = (dx - g.bx) * (-g.by) - (dy - g.by) * (-g.bx);
-  la = nA2 * g.inv2a;
-  lc = nC2 * g.inv2a;
-  lb = T(1) - la - lc;
+__device__ __forceinline__ T edge_cross(T xa, T ya, T xb, T yb, T x, T y, T L) {
+  return xmul(min_image(xb - xa, L), y - ya) - xmul(yb - ya, min_image(x - xa, L));
+}
+
+// Twice the signed areas N^A, N^B, N^C (Eqs. 44-45, Fig. 1): for each vertex, the cross
+// product of the opposite edge with the vector from one end of that edge to the particle.
+// Each edge is pivoted at its lower-numbered node, so the two elements sharing an edge
+// evaluate it with identical rounding and opposite signs (watertight point location).
+template <typename T>
+__device__ __forceinline__ void area_cross(const ElemGeo<T>& g, int na, int nb, int nc, T x, T y,
+                                           T L, T& n0, T& n1, T& n2) {
+  // edge opposite A: B -> C
+  n0 = nb < nc ? edge_cross(g.x1, g.y1, g.x2, g.y2, x, y, L)
+               : -edge_cross(g.x2, g.y2, g.x1, g.y1, x, y, L);
+  // edge opposite B: C -> A
+  n1 = nc < na ? edge_cross(g.x2, g.y2, g.x0, g.y0, x, y, L)
+               : -edge_cross(g.x0, g.y0, g.x2, g.y2, x, y, L);
+  // edge opposite C: A -> B
+  n2 = na < nb ? edge_cross(g.x0, g.y0, g.x1, g.y1, x, y, L)
+               : -edge_cross(g.x1, g.y1, g.x0, g.y0, x, y, L);
+}
+
+// Area coordinates lambda_k = N^k / A_e (Eqs. 37-38 shapefunction values at the particle).
+template <typename T>
+__device__ __forceinline__ void area_coords(const ElemGeo<T>& g, int na, int nb, int nc, T x, T y,
+                                            T L, T& la, T& lb, T& lc) {
+  area_cross(g, na, nb, nc, x, y, L, la, lb, lc);
+  la *= g.inv2a;
+  lb *= g.inv2a;
+  lc *= g.inv2a;
+}
+
+// Point in the triangle with weights (1 - s) A + s (1 - t) B + s t C (Osada et al.).
+template <typename T>
+__device__ __forceinline__ void triangle_point(const ElemGeo<T>& g, T s, T t, T L, T& px, T& py) {
+  px = g.x0 + s * (T(1) - t) * min_image(g.x1 - g.x0, L) + s * t * min_image(g.x2 - g.x0, L);
+  py = g.y0 + s * (T(1) - t) * (g.y1 - g.y0) + s * t * (g.y2 - g.y0);
 }
 
 }  // namespace pdfx

@@ -46,6 +46,10 @@ struct AdvanceArgs {
   int32_t* cnt;
   unsigned long long* diag;
   int* err;
+  int32_t* brute_list;   // slots that need the brute-force search
+  int* brute_count;
+  int brute_cap;
+  double* lost_rec;      // [kLostRecords][4]
   Model<T> m;
   T dt;
   uint32_t step, k0, k1;
@@ -141,7 +145,9 @@ struct Ctx {
   int G = 1;
   // diagnostics
   unsigned long long* diag = nullptr;  // [kDiagCount]
-  int* err = nullptr;
+  int* err = nullptr;                  // [0] error word, [1] brute-force list length
+  int32_t* brute_list = nullptr;       // [kBruteCap]
+  double* lost_rec = nullptr;          // [kLostRecords][4]
   int64_t steps_done = 0;
   int64_t launches = 0;
   // profiling
