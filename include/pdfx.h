@@ -50,6 +50,7 @@ extern "C" {
 #define PDFX_NF 32                  /* nodal field slots, layout below */
 #define PDFX_NSTAT 13               /* statistics per element or node, layout below */
 #define PDFX_MAX_PER_ELEMENT 4096   /* particles one element may hold for the binning */
+#define PDFX_MAX_PARTICLES (1 << 28) /* particles per context (ids fit the binning sort keys) */
 
 /*
  * Nodal field layout, [nn][32] FP64 (pdfx_set_fields):
@@ -146,7 +147,8 @@ int  pdfx_set_fields(void *ctx, const double *fields, int on_device, void *strea
  * the local mean with variance 2k/3 per component; frequency gamma with the local mean
  * and variance C4 <omega>^2; psi = 1 inside the source, else 0.  Particle id =
  * element * ppe + k.  Then computes the statistics and conditional means.  Resets the
- * step counter to 0.  PDFX_ERR_ORDER without grid and fields. */
+ * step counter to 0.  PDFX_ERR_ORDER without grid and fields; PDFX_ERR_ARG if ppe * ne
+ * reaches PDFX_MAX_PARTICLES. */
 int  pdfx_init_particles(void *ctx, int32_t ppe, void *stream);
 
 /* Replaces the particle state by np particles with ids 0..np-1 (FP64 arrays of s, host

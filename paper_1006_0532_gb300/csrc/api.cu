@@ -685,7 +685,7 @@ int pdfx_init_particles(void* ctx, int32_t ppe, void* stream) {
   Ctx* c = as_ctx(ctx);
   if (!c || ppe <= 0) return PDFX_ERR_ARG;
   if (!c->have_grid || !c->have_fields) return PDFX_ERR_ORDER;
-  if (static_cast<int64_t>(ppe) * c->ne > 2147483647LL) return PDFX_ERR_ARG;
+  if (static_cast<int64_t>(ppe) * c->ne >= kMaxParticles) return PDFX_ERR_ARG;
   return c->prm.precision == 1 ? do_init<float>(*c, ppe, as_stream(stream))
                                : do_init<double>(*c, ppe, as_stream(stream));
 }
@@ -693,7 +693,7 @@ int pdfx_init_particles(void* ctx, int32_t ppe, void* stream) {
 int pdfx_set_particles(void* ctx, int64_t np, const pdfx_soa* s, uint32_t step, int on_device,
                        void* stream) {
   Ctx* c = as_ctx(ctx);
-  if (!c || !s || np < 0 || np > 2147483647LL) return PDFX_ERR_ARG;
+  if (!c || !s || np < 0 || np >= kMaxParticles) return PDFX_ERR_ARG;
   if (np > 0 && (!s->x || !s->y || !s->u || !s->v || !s->w || !s->om || !s->psi || !s->elem))
     return PDFX_ERR_ARG;
   if (!c->have_grid) return PDFX_ERR_ORDER;

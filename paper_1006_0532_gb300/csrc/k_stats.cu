@@ -713,7 +713,7 @@ void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s) {
                          static_cast<int>(big));
     configured = true;
   }
-  if (a.ne > 0) stats_small_kernel<T><<<a.ne, kStatsThreads, small, s>>>(a);
+  launch_stats_warp<T>(a, s);
   stats_big_kernel<T><<<static_cast<unsigned>(num_sms > 0 ? num_sms : 1), kStatsThreads, big, s>>>(a);
 }
 

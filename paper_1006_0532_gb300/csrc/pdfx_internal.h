@@ -106,7 +106,8 @@ struct Plan {
 };
 
 constexpr int kHistCap = 8192;      // counts above this are clipped for the closed form
-constexpr int kSmallCap = 1024;     // binning capacity of the per-element kernel
+constexpr int kSmallCap = 1024;     // binning capacity of the warp-per-element kernel
+constexpr int64_t kMaxParticles = int64_t(1) << 28;   // particle ids fit the 28-bit sort key field
 constexpr int kBigCap = 4096;       // binning capacity of the large-element kernel
 
 struct Ctx {
@@ -181,6 +182,8 @@ void launch_redistribute(Particles<T> p, Plan& pl, int32_t ne, int64_t np, const
                          unsigned long long* diag, int* err, cudaStream_t s);
 template <typename T>
 void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s);
+template <typename T>
+void launch_stats_warp(const StatsArgs<T>& a, cudaStream_t s);
 void launch_node_average(const double* emom, const int32_t* ne_off, const int32_t* ne_list,
                          int32_t nn, double* nmom, cudaStream_t s);
 template <typename T>
