@@ -197,6 +197,31 @@ int  pdfx_check(void *ctx, void *stream);
 int  pdfx_set_profiling(void *ctx, int on);
 int  pdfx_stage_times(void *ctx, double *ms, int64_t *launches, int n, void *stream);
 
+/* Element statistics, conditional means and nodal statistics of a caller's particle
+ * state, computed without allocating device memory.  The paper has no counterpart: this
+ * is a service for callers that cannot allocate while they run (an application whose own
+ * pool owns all device memory, a service that must keep its footprint fixed, a loop that
+ * cannot take the device-wide synchronisation cudaMalloc may cause).
+ *   ctx: a context with a grid (its bins, min_per_bin and node lists are used).
+ *   np particles indexed by particle id; u, v, w, om, psi [np] FP64 and elem [np] int32,
+ *   device memory, read only.  np <= PDFX_NOALLOC_MAX_PARTICLES and the grid's element
+ *   count <= PDFX_NOALLOC_MAX_ELEMENTS, else PDFX_ERR_ARG.
+ *   Outputs, device memory written on stream: emom [ne][13], vcce [ne][G], gbin [ne][3],
+ *   cp [np] (conditioning pointers), nmom [nn][13] (may be NULL to skip).
+ * The results equal those the context computes for the same state (pdfx_set_particles
+ * followed by pdfx_get_element_stats / pdfx_get_bins / pdfx_get_nodal_stats), in FP64.
+ * Scratch is one fixed device array of the library (about 10 MB) that every GPU loading
+ * the library reserves until exit; the first call on a device looks up its address with
+ * cudaGetSymbolAddress, so make that first call before any stream capture.  Every call
+ * reuses the same array: calls that overlap on the GPU (other streams, other host
+ * threads, other contexts) race and must be serialised by the caller.  Asynchronous. */
+#define PDFX_NOALLOC_MAX_PARTICLES (1 << 20)
+#define PDFX_NOALLOC_MAX_ELEMENTS (1 << 16)
+int  pdfx_element_stats_noalloc(void *ctx, int64_t np, const double *u, const double *v,
+                                const double *w, const double *om, const double *psi,
+                                const int32_t *elem, double *emom, double *vcce, int32_t *gbin,
+                                uint8_t *cp, double *nmom, void *stream);
+
 /* Number of kernel launches the library issued since creation. */
 int64_t pdfx_kernel_launches(const void *ctx);
 

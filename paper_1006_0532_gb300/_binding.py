@@ -103,6 +103,7 @@ def lib():
                 "pdfx_set_profiling": (C.c_int, [vp, C.c_int]),
                 "pdfx_stage_times": (C.c_int, [vp, C.POINTER(dp), C.POINTER(i64), C.c_int, vp]),
                 "pdfx_kernel_launches": (i64, [vp]),
+                "pdfx_element_stats_noalloc": (C.c_int, [vp, i64] + [vp] * 11 + [vp]),
                 "pdfx_strerror": (C.c_char_p, [C.c_int]),
             }
             for name, (res, args) in sig.items():
@@ -307,6 +308,16 @@ class Context:
         if k < 0:
             raise PdfxError(k, "pdfx_stage_times")
         return [float(ms[i]) for i in range(k)], [int(n[i]) for i in range(k)]
+
+    def element_stats_noalloc(self, st: dict, emom, vcce, gbin, cp, nmom=None, stream=None):
+        """Statistics of a device particle state (torch tensors by particle id) into the
+        given device outputs, with no device allocation (pdfx_element_stats_noalloc)."""
+        n = int(st["u"].shape[0])
+        args = [_ptr(st[k]) for k in ("u", "v", "w", "om", "psi", "elem")]
+        self._check(lib().pdfx_element_stats_noalloc(self.h, n, *args, _ptr(emom), _ptr(vcce),
+                                                      _ptr(gbin), _ptr(cp), _ptr(nmom),
+                                                      _stream(stream)),
+                    "pdfx_element_stats_noalloc")
 
     @property
     def kernel_launches(self) -> int:
