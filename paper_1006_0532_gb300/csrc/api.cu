@@ -75,6 +75,9 @@ Model<T> model_of(const pdfx_params& p) {
   m.Cw1 = T(p.Cw1); m.Cw2 = T(p.Cw2); m.nu = T(p.nu); m.C0 = T(p.C0); m.Cs = T(p.Cs);
   m.Ct = T(p.Ct); m.Cphi = T(p.Cphi); m.src_x = T(p.src_x); m.src_y = T(p.src_y);
   m.src_r = T(p.src_r); m.period_x = T(p.period_x);
+  m.nuCT2 = T(p.nu * p.CT * p.CT);
+  m.s2nu = T(std::sqrt(2.0 * p.nu));
+  m.cs_r2 = T(p.Cs * std::cbrt(p.src_r * p.src_r));
   m.c0_mode = p.c0_mode; m.tm_mode = p.tm_mode; m.interp_mode = p.interp_mode;
   m.source_on = p.source_on;
   return m;
@@ -302,6 +305,7 @@ int do_step(Ctx& c, double dt, cudaStream_t s) {
     a.lost_rec = c.lost_rec;
     a.m = model_of<T>(c.prm);
     a.dt = T(dt);
+    a.sdt = T(std::sqrt(dt));
     a.step = c.step;
     a.k0 = key0(c.prm);
     a.k1 = key1(c.prm);

@@ -104,8 +104,9 @@ __device__ __forceinline__ void warp_count(unsigned long long* diag, int slot, i
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(diag + slot, static_cast<unsigned long long>(s));
 }
 
+// FP32: 4 blocks of 256 per SM (64 registers); FP64: 2 blocks.
 template <typename T>
-__global__ void __launch_bounds__(256) advance_kernel(const AdvanceArgs<T> a) {
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(const AdvanceArgs<T> a) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool valid = i < a.np;
   int c_hops = 0, c_fb = 0, c_brute = 0, c_lost = 0, c_wall = 0, c_fs = 0, c_oref = 0,
@@ -145,9 +146,9 @@ __global__ void __launch_bounds__(256) advance_kernel(const AdvanceArgs<T> a) {
     // k and Eq. 18 (floored at 1e-30 so a particle on a wall keeps finite coefficients)
     T k = T(0.5) * (R[0][0] + R[1][1] + R[2][2]);
     if (k < T(1e-30)) k = T(1e-30);
-    T eps = Om * (k + M.nu * M.CT * M.CT * Om);
+    T eps = Om * (k + M.nuCT2 * Om);
     if (eps < T(1e-30)) eps = T(1e-30);
-    const T ik = T(1) / k;
+    const T ik = T(1) / k, ieps = T(1) / eps;
     // Eq. 11
     T C0;
     if (M.c0_mode == 1) {
@@ -158,7 +159,7 @@ __global__ void __launch_bounds__(256) advance_kernel(const AdvanceArgs<T> a) {
       for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c) s += q[14 + 3 * r + c] * R[r][c];
-      C0 = T(-2) * s / (T(3) * k * eps);
+      C0 = T(-2) / T(3) * s * ik * ieps;
     }
     // production P = -<u_i u_j> d<U_i>/dx_j (x, y) and Eq. 20
     T prod = T(0);
@@ -166,23 +167,22 @@ __global__ void __launch_bounds__(256) advance_kernel(const AdvanceArgs<T> a) {
     for (int r = 0; r < 3; ++r)
 #pragma unroll
       for (int c = 0; c < 2; ++c) prod -= R[r][c] * q[5 + 2 * r + c];
-    const T Somega = M.Cw2 - M.Cw1 * prod / eps;
-    // Eq. 25 or the IEM time scale 2k / (C_phi eps)
-    T tm;
+    const T Somega = M.Cw2 - M.Cw1 * prod * ieps;
+    // 1 / t_m: Eq. 25, or the IEM time scale t_m = 2k / (C_phi eps)
+    T itm;
     if (M.tm_mode == 1) {
-      tm = T(2) * k / (M.Cphi * eps);
+      itm = T(0.5) * M.Cphi * eps * ik;
     } else {
-      const T ddx = min_image(X0 - M.src_x, L), ddy = Y0 - M.src_y;
-      const T dr = sqrt(ddx * ddx + ddy * ddy);
-      const T Uc = sqrt(Um[0] * Um[0] + Um[1] * Um[1] + Um[2] * Um[2]);
-      const T kt = k / eps, kol = M.CT * sqrt(M.nu / eps);
+      const T kt = k * ieps, kol = M.CT * sqrt(M.nu * ieps);
       const T a2 = kt > kol ? kt : kol;
-      if (!(Uc > T(0))) {
-        tm = a2;
-      } else {
-        const T a1 = M.Cs * tcbrt(M.src_r * M.src_r / eps) + M.Ct * dr / Uc;
+      const T ddx = min_image(X0 - M.src_x, L), ddy = Y0 - M.src_y;
+      const T Uc2 = Um[0] * Um[0] + Um[1] * Um[1] + Um[2] * Um[2];
+      T tm = a2;
+      if (Uc2 > T(0)) {
+        const T a1 = M.cs_r2 * tcbrt(ieps) + M.Ct * sqrt((ddx * ddx + ddy * ddy) / Uc2);
         tm = a1 < a2 ? a1 : a2;
       }
+      itm = T(1) / tm;
     }
 
     // Sect. 3.9: six Gaussians and eta
@@ -194,26 +194,25 @@ __global__ void __launch_bounds__(256) advance_kernel(const AdvanceArgs<T> a) {
     box_muller(r1.x, r1.y, xi[4], xi[5]);
     const T eta = uniform01(r1.z, T(0));
     const T dt = a.dt;
-    const T sdt = sqrt(dt);
+    const T sdt = a.sdt;
     const T dWx = sdt * xi[0], dWy = sdt * xi[1];
-    const T s2nu = sqrt(T(2) * M.nu);
+    const T s2nu = M.s2nu;
 
-    // Eq. 27 (C0 eps < 0 is clamped under the root and counted)
+    // Eq. 27 (C0 eps < 0 is clamped under the root and counted);
+    // G_ij (U_j - <U_j>) = (wp_ij (U_j - <U_j>) - eps/2 (U_i - <U_i>)) / k  (Eq. 11)
     T c0e = C0 * eps;
     if (c0e < T(0)) { c0e = T(0); c_c0 = 1; }
-    const T sc0e = sqrt(c0e);
+    const T sc0e = sqrt(c0e) * sdt;
+    const T dU[3] = {U0[0] - Um[0], U0[1] - Um[1], U0[2] - Um[2]};
     T Un[3];
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
       const T base = U0[r] - dP[r] * dt + T(2) * M.nu * q[11 + r] * dt +
                      s2nu * (q[5 + 2 * r] * dWx + q[6 + 2 * r] * dWy);
-      T gsum = T(0);
+      T gsum = -T(0.5) * eps * dU[r];
 #pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        const T Gij = (q[14 + 3 * r + c] - (r == c ? T(0.5) * eps : T(0))) * ik;
-        gsum += Gij * (U0[c] - Um[c]);
-      }
-      Un[r] = base + gsum * dt + sc0e * (sdt * xi[2 + r]);
+      for (int c = 0; c < 3; ++c) gsum += q[14 + 3 * r + c] * dU[c];
+      Un[r] = base + gsum * ik * dt + sc0e * xi[2 + r];
     }
     // Eq. 7 (same dW as Eq. 27)
     T Xn = X0 + U0[0] * dt + s2nu * dWx;
@@ -225,7 +224,7 @@ __global__ void __launch_bounds__(256) advance_kernel(const AdvanceArgs<T> a) {
     if (wn < T(0)) { wn = -wn; c_oref = 1; }
     // Eq. 24 with the conditional mean of the particle's bin
     const T phic = static_cast<T>(a.vcce[(size_t)e * a.G + cpi]);
-    T psin = psi0 - (psi0 - phic) * dt / tm;
+    T psin = psi0 - (psi0 - phic) * dt * itm;
 
     // Sect. 3.8: wall elements only
     if (tp.wall >= 0) {
@@ -266,9 +265,8 @@ __global__ void __launch_bounds__(256) advance_kernel(const AdvanceArgs<T> a) {
       const T sx = min_image(Xn - M.src_x, L), sy = Yn - M.src_y;
       if (sx * sx + sy * sy <= M.src_r * M.src_r) { psin = T(1); c_src = 1; }
     }
-    if (!(finite(Xn) && finite(Yn) && finite(Un[0]) && finite(Un[1]) && finite(Un[2]) &&
-          finite(wn) && finite(psin)))
-      c_nf = 1;
+    // a sum of finite terms of this size is finite; a NaN or infinity anywhere is not
+    if (!finite(Xn + Yn + Un[0] + Un[1] + Un[2] + wn + psin)) c_nf = 1;
 
     // Sect. 3.6
     int hops = 0, fb = 0, brute = 0;

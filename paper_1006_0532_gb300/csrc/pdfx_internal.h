@@ -15,6 +15,9 @@ namespace pdfx {
 template <typename T>
 struct Model {
   T C1, C2, C3, C4, CT, Cw1, Cw2, nu, C0, Cs, Ct, Cphi, src_x, src_y, src_r, period_x;
+  T nuCT2;      // nu C_T^2 (Eq. 18)
+  T s2nu;       // sqrt(2 nu) (Eqs. 7, 27)
+  T cs_r2;      // C_s r0^(2/3) (Eq. 25)
   int c0_mode, tm_mode, interp_mode, source_on;
 };
 
@@ -51,7 +54,7 @@ struct AdvanceArgs {
   int brute_cap;
   double* lost_rec;      // [kLostRecords][4]
   Model<T> m;
-  T dt;
+  T dt, sdt;    // time step and its square root
   uint32_t step, k0, k1;
 };
 
@@ -183,7 +186,7 @@ void launch_redistribute(Particles<T> p, Plan& pl, int32_t ne, int64_t np, const
 template <typename T>
 void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s);
 template <typename T>
-void launch_stats_warp(const StatsArgs<T>& a, cudaStream_t s);
+void launch_stats_warp(const StatsArgs<T>& a, cudaStream_t s);   // k_bins_f32.cu / k_bins_f64.cu
 void launch_node_average(const double* emom, const int32_t* ne_off, const int32_t* ne_list,
                          int32_t nn, double* nmom, cudaStream_t s);
 template <typename T>
