@@ -235,6 +235,8 @@ def main():
     ap.add_argument("--oracle-steps", type=int, default=2)
     ap.add_argument("--no-f64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--ppe", type=int, default=None,
+                    help="particles per element (default: the workload's own)")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()
@@ -251,7 +253,7 @@ def main():
         dist.init_process_group("nccl")
     from paper_1006_0532_gb300 import _binding as B
     from paper_1006_0532_gb300 import synth
-    w = synth.workload(args.workload)
+    w = synth.workload(args.workload, args.ppe)
 
     c32, r32 = time_form(torch, B, w, 1, args, rank, world, dist, with_clock=True)
     e2e_s, h2d, d2h = e2e_form(torch, B, c32, w, args)

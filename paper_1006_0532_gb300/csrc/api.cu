@@ -249,6 +249,7 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
     a.goff = c.plan.goff;
     a.movers = c.plan.movers;
     a.big_list = c.plan.big_list;
+    a.tiles = c.plan.tiles;
     a.scal = c.plan.scal;
     a.ne = c.ne;
     a.np = c.np;
@@ -547,7 +548,7 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
   const size_t E = static_cast<size_t>(ne), N = static_cast<size_t>(nn);
   Plan& pl = c.plan;
   for (int32_t** b : {&pl.cnt, &pl.cursor, &pl.fin, &pl.gain, &pl.loss, &pl.recips, &pl.donors,
-                      &pl.big_list})
+                      &pl.big_list, &pl.tiles})
     PDFX_TRY(alloc_into(c, *b, E));
   for (int32_t** b : {&pl.off, &pl.foff, &pl.goff, &pl.doff}) PDFX_TRY(alloc_into(c, *b, E + 1));
   PDFX_TRY(alloc_into(c, pl.scal, 16));

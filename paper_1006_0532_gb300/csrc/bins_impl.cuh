@@ -1,5 +1,6 @@
-// Per-element statistics and conditional means, one thread block per element of up to 1024
-// particles (larger elements go through the block kernel in k_stats.cu).
+// Per-element statistics and conditional means for elements of up to 1024 particles, one
+// thread block per element (persistent blocks walk the plan's element lists of two size
+// classes; larger elements go through the block kernel in k_stats.cu).
 //
 // Sect. 3.5 / Appendix A: the element's particles are sorted by (u, id); the level-1 groups
 // (positions with equal floor(g1 p / N)) are sorted by (v, id), the level-2 groups by
@@ -11,8 +12,11 @@
 // key), so the ranks are a permutation and the new order is written by scatter.
 // Sect. 3.3, Eqs. 35-36: element means, then central moments about them, summed by one
 // warp in the final order (deterministic); the FP32 form accumulates compensated FP32 per
-// lane and combines lanes as FP32 value/error pairs, the FP64 form sums in FP64.
+// lane and combines lanes as FP32 value/error pairs, the FP64 form sums in FP64.  The 13
+// outputs are then formed in FP64 one per lane.
 #pragma once
+#include <initializer_list>
+
 #include "pdfx_internal.h"
 
 namespace pdfx {
@@ -108,8 +112,8 @@ __device__ __forceinline__ int count_below(const Arr& s, int base, const K& k) {
   return pos + (kless(s.get(base + pos), k) ? 1 : 0);
 }
 
-// Compensated (Kahan) accumulation for the FP32 form; plain for FP64.  warp_total() sums
-// the 32 lanes' accumulators (every lane gets the same value).
+// Compensated (Kahan) accumulation for the FP32 form; plain for FP64.  warp_pair() sums
+// the 32 lanes' accumulators into a value/error pair (every lane gets the same pair).
 template <typename T>
 struct Acc;
 template <>
@@ -121,8 +125,9 @@ struct Acc<float> {
     c = (t - s) - y;
     s = t;
   }
+  __device__ __forceinline__ float value() const { return s - c; }
   // value/error pairs: an exact two-sum of the leading parts, errors added, renormalised
-  __device__ __forceinline__ double warp_total() const {
+  __device__ __forceinline__ void warp_pair(float& hv, float& lv) const {
     float h = s, l = -c;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -134,23 +139,47 @@ struct Acc<float> {
       h = sh + lo;
       l = lo - (h - sh);
     }
-    return static_cast<double>(h) + static_cast<double>(l);
+    hv = h;
+    lv = l;
   }
 };
 template <>
 struct Acc<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double x) { s += x; }
-  __device__ __forceinline__ double warp_total() const {
+  __device__ __forceinline__ double value() const { return s; }
+  __device__ __forceinline__ void warp_pair(double& hv, double& lv) const {
     double v = s;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
-    return v;
+    hv = v;
+    lv = 0.0;
   }
 };
 
+// First position of group g of G over n positions: ceil(g n / G) (g n < 2^18 here).
 __device__ __forceinline__ int group_start(int g, int n, int G) {
-  return static_cast<int>((static_cast<int64_t>(g) * n + G - 1) / G);
+  return static_cast<int>((static_cast<unsigned>(g * n) + static_cast<unsigned>(G - 1)) /
+                          static_cast<unsigned>(G));
+}
+
+// Moment outputs, one per lane: em[c] = X + Y/N - (Z/N)(W/N), X a shift value, Y a sum of
+// d or of a product of d, Z and W sums of d; four bits per lane, 15 = term absent.
+// Sums 0..4: d of u, v, w, omega, psi; 5..11: uu, vv, ww, uv, uw, vw, psi psi.
+// Outputs: 0 N, 1-3 means of u, v, w, 4-6 variances, 7-9 <uv>, <uw>, <vw>, 10 mean omega,
+// 11 mean psi, 12 variance of psi.
+constexpr uint64_t pack13(std::initializer_list<int> v) {
+  uint64_t r = 0;
+  int i = 0;
+  for (int x : v) r |= static_cast<uint64_t>(x & 15) << (4 * i++);
+  return r;
+}
+constexpr uint64_t kMomX = pack13({15, 0, 1, 2, 15, 15, 15, 15, 15, 15, 3, 4, 15});
+constexpr uint64_t kMomY = pack13({15, 0, 1, 2, 5, 6, 7, 8, 9, 10, 3, 4, 11});
+constexpr uint64_t kMomZ = pack13({15, 15, 15, 15, 0, 1, 2, 0, 0, 1, 15, 15, 4});
+constexpr uint64_t kMomW = pack13({15, 15, 15, 15, 0, 1, 2, 1, 2, 2, 15, 15, 4});
+__device__ __forceinline__ int mom_nib(uint64_t tab, int c) {
+  return static_cast<int>((tab >> (4 * c)) & 15u);
 }
 
 // Shared tile of one element.  Chunk tables are needed only when groups exceed 32
@@ -164,20 +193,15 @@ struct Tile {
   int32_t spay[kChunks * 32];       // their slots
   int32_t gfc[CAP / 32 + 1];        // first chunk of each group
   uint8_t cg[kChunks];              // group of each chunk
+  T mh[12], ml[12], msh[5];         // moment sums (value/error pairs) and shift values
   int n_gathered;
 };
 
-// Elements with lo < N <= hi (hi <= CAP), one block of THREADS each.
+// One element of N <= CAP particles (list size after redistribution) by a block of THREADS.
 template <typename T, int CAP, int THREADS>
-__global__ void __launch_bounds__(THREADS) stats_tile_kernel(const StatsArgs<T> a, int lo, int hi) {
+__device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int N, int moves) {
   using K = typename KeyOf<T>::type;
   constexpr int W = THREADS / 32;
-  __shared__ Tile<T, CAP> t;
-  const int e = blockIdx.x;
-  if (e >= a.ne) return;
-  const int moves = a.scal[0] > 0;
-  const int N = moves ? a.fin[e] : a.cnt[e];
-  if (N <= lo || N > hi) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned below = (1u << lane) - 1u;
 
@@ -323,51 +347,54 @@ __global__ void __launch_bounds__(THREADS) stats_tile_kernel(const StatsArgs<T> 
       const int32_t q0 = cur[0];
       sh[0] = a.p.u[q0]; sh[1] = a.p.v[q0]; sh[2] = a.p.w[q0]; sh[3] = a.p.om[q0]; sh[4] = a.p.psi[q0];
     }
-    Acc<T> s1[5], s2[7];
+    Acc<T> m[12];
     for (int p = lane; p < n; p += 32) {
       const int32_t q = cur[p];
       const T du = a.p.u[q] - sh[0], dv = a.p.v[q] - sh[1], dw = a.p.w[q] - sh[2];
       const T dom = a.p.om[q] - sh[3], dp = a.p.psi[q] - sh[4];
-      s1[0].add(du); s1[1].add(dv); s1[2].add(dw); s1[3].add(dom); s1[4].add(dp);
-      s2[0].add(du * du); s2[1].add(dv * dv); s2[2].add(dw * dw);
-      s2[3].add(du * dv); s2[4].add(du * dw); s2[5].add(dv * dw);
-      s2[6].add(dp * dp);
+      m[0].add(du); m[1].add(dv); m[2].add(dw); m[3].add(dom); m[4].add(dp);
+      m[5].add(du * du); m[6].add(dv * dv); m[7].add(dw * dw);
+      m[8].add(du * dv); m[9].add(du * dw); m[10].add(dv * dw);
+      m[11].add(dp * dp);
     }
-    const double inv = n > 0 ? 1.0 / n : 0.0;
-    double d1[5], d2[7];
 #pragma unroll
-    for (int c = 0; c < 5; ++c) d1[c] = s1[c].warp_total() * inv;
-#pragma unroll
-    for (int c = 0; c < 7; ++c) d2[c] = s2[c].warp_total() * inv;
-    if (lane == 0) {
-      double* em = a.emom + static_cast<size_t>(kNS) * e;
-      em[0] = static_cast<double>(n);
-      em[1] = static_cast<double>(sh[0]) + d1[0];
-      em[2] = static_cast<double>(sh[1]) + d1[1];
-      em[3] = static_cast<double>(sh[2]) + d1[2];
-      em[4] = d2[0] - d1[0] * d1[0]; em[5] = d2[1] - d1[1] * d1[1]; em[6] = d2[2] - d1[2] * d1[2];
-      em[7] = d2[3] - d1[0] * d1[1]; em[8] = d2[4] - d1[0] * d1[2]; em[9] = d2[5] - d1[1] * d1[2];
-      em[10] = static_cast<double>(sh[3]) + d1[3];
-      em[11] = static_cast<double>(sh[4]) + d1[4];
-      em[12] = d2[6] - d1[4] * d1[4];
-      if (n == 0) for (int c = 1; c < kNS; ++c) em[c] = 0.0;
-      a.gbin[3 * e] = g[0];
-      a.gbin[3 * e + 1] = g[1];
-      a.gbin[3 * e + 2] = g[2];
+    for (int c = 0; c < 12; ++c) {
+      T h, l;
+      m[c].warp_pair(h, l);
+      if (lane == c) { t.mh[c] = h; t.ml[c] = l; }
     }
+    if (lane < 5)
+      t.msh[lane] = lane == 0 ? sh[0] : lane == 1 ? sh[1] : lane == 2 ? sh[2] : lane == 3 ? sh[3] : sh[4];
+    __syncwarp();
+    if (lane < kNS) {
+      const double inv = n > 0 ? 1.0 / n : 0.0;
+      const int ix = mom_nib(kMomX, lane), iy = mom_nib(kMomY, lane);
+      const int iz = mom_nib(kMomZ, lane), iw = mom_nib(kMomW, lane);
+      double v = ix < 15 ? static_cast<double>(t.msh[ix]) : 0.0;
+      if (iy < 15) v += (static_cast<double>(t.mh[iy]) + static_cast<double>(t.ml[iy])) * inv;
+      if (iz < 15) {
+        const double z = (static_cast<double>(t.mh[iz]) + static_cast<double>(t.ml[iz])) * inv;
+        const double w = (static_cast<double>(t.mh[iw]) + static_cast<double>(t.ml[iw])) * inv;
+        v -= z * w;
+      }
+      if (lane == 0) v = static_cast<double>(n);
+      else if (n == 0) v = 0.0;
+      a.emom[static_cast<size_t>(kNS) * e + lane] = v;
+    }
+    if (lane < 3) a.gbin[3 * e + lane] = lane == 0 ? g[0] : lane == 1 ? g[1] : g[2];
   }
 
   // Appendix A bins: conditional scalar means over the final order's bins
   double* vc = a.vcce + static_cast<size_t>(a.G) * e;
   for (int i = threadIdx.x; i < a.G; i += THREADS) {
-    double mval = 0.0;
+    T mval = T(0);
     if (i < G && n > 0) {
       const int b0 = group_start(i, n, G), b1 = group_start(i + 1, n, G);
-      double sum = 0.0;
-      for (int p = b0; p < b1; ++p) sum += static_cast<double>(a.p.psi[cur[p]]);
-      mval = sum / (b1 - b0);
+      Acc<T> sum;
+      for (int p = b0; p < b1; ++p) sum.add(a.p.psi[cur[p]]);
+      mval = sum.value() / static_cast<T>(b1 - b0);
     }
-    vc[i] = mval;
+    vc[i] = static_cast<double>(mval);
   }
   // conditioning pointers (and the element-ordered copy of the state every few steps)
   if (a.resort) {
@@ -385,23 +412,42 @@ __global__ void __launch_bounds__(THREADS) stats_tile_kernel(const StatsArgs<T> 
       a.out.psi[d] = a.p.psi[q];
       a.out.pid[d] = a.p.pid[q];
       a.out.elem[d] = e;
-      a.out.cp[d] = static_cast<uint8_t>((static_cast<int64_t>(G) * p) / n);
+      a.out.cp[d] = static_cast<uint8_t>(static_cast<unsigned>(G * p) / static_cast<unsigned>(n));
     }
   } else {
     for (int p = threadIdx.x; p < n; p += THREADS)
-      a.p.cp[cur[p]] = static_cast<uint8_t>((static_cast<int64_t>(G) * p) / n);
+      a.p.cp[cur[p]] = static_cast<uint8_t>(static_cast<unsigned>(G * p) / static_cast<unsigned>(n));
   }
+}
+
+// One block per entry of one size class of the plan's tile lists: the elements of up to
+// kTileSplit particles (FRONT) or of kTileSplit + 1 .. kSmallCap (the back of the list).  The
+// grid covers every element; blocks past the class count return at once.  The register cap
+// keeps 1536 threads resident per SM in the FP32 form, 1024 in the FP64 form.
+template <typename T, int CAP, int THREADS, bool FRONT>
+__global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1536 : 1024) / THREADS)
+    stats_tile_kernel(const StatsArgs<T> a) {
+  __shared__ Tile<T, CAP> t;
+  const int count = FRONT ? a.scal[6] : a.scal[7];
+  const int b = blockIdx.x;
+  if (b >= count) return;
+  const int moves = a.scal[0] > 0;
+  const int e = FRONT ? a.tiles[b] : a.tiles[a.ne - 1 - b];
+  const int N = moves ? a.fin[e] : a.cnt[e];
+  element_tile<T, CAP, THREADS>(a, t, e, min(N, CAP), moves);
 }
 
 }  // namespace
 
 template <typename T>
-void launch_stats_warp_impl(const StatsArgs<T>& a, cudaStream_t s) {
+void launch_stats_tiles_impl(const StatsArgs<T>& a, int num_sms, cudaStream_t s) {
   if (a.ne <= 0) return;
-  static_assert(kSmallCap == 1024, "tile classes cover the small-element capacity");
+  static_assert(kSmallCap == 1024 && kTileSplit == 512, "tile classes cover the small-element capacity");
   // elements of up to 512 particles (4 warps), then 513..1024 (8 warps)
-  stats_tile_kernel<T, 512, 128><<<static_cast<unsigned>(a.ne), 128, 0, s>>>(a, -1, 512);
-  stats_tile_kernel<T, 1024, 256><<<static_cast<unsigned>(a.ne), 256, 0, s>>>(a, 512, 1024);
+  (void)num_sms;
+  const unsigned grid = static_cast<unsigned>(a.ne);
+  stats_tile_kernel<T, 512, 128, true><<<grid, 128, 0, s>>>(a);
+  stats_tile_kernel<T, 1024, 256, false><<<grid, 256, 0, s>>>(a);
 }
 
 }  // namespace pdfx

@@ -4,8 +4,8 @@
 namespace pdfx {
 
 template <>
-void launch_stats_warp<float>(const StatsArgs<float>& a, cudaStream_t s) {
-  launch_stats_warp_impl<float>(a, s);
+void launch_stats_tiles<float>(const StatsArgs<float>& a, int num_sms, cudaStream_t s) {
+  launch_stats_tiles_impl<float>(a, num_sms, s);
 }
 
 }  // namespace pdfx

@@ -4,8 +4,8 @@
 namespace pdfx {
 
 template <>
-void launch_stats_warp<double>(const StatsArgs<double>& a, cudaStream_t s) {
-  launch_stats_warp_impl<double>(a, s);
+void launch_stats_tiles<double>(const StatsArgs<double>& a, int num_sms, cudaStream_t s) {
+  launch_stats_tiles_impl<double>(a, num_sms, s);
 }
 
 }  // namespace pdfx

@@ -82,20 +82,40 @@ __device__ int64_t S_of(const int64_t* P0, const int64_t* P1, int64_t H, int64_t
   return a1 - H * a0;
 }
 
+// Tile-class lists for the statistics kernels: elements of up to kTileSplit particles from
+// the front of pl.tiles, of up to kSmallCap from the back, in element order.  The class
+// flags ride in bits 32-47 and 48-63 of a count's block scan (counts sum below 2^28 and a
+// block holds kPlanThreads elements, so the fields never carry into each other).
+__device__ __forceinline__ int64_t tile_class_bits(bool valid, int32_t c) {
+  if (!valid || c > kSmallCap) return 0;
+  return c <= kTileSplit ? (int64_t(1) << 32) : (int64_t(1) << 48);
+}
+__device__ __forceinline__ void place_tile_class(Plan& pl, bool valid, int32_t c, int32_t e,
+                                                 int32_t ne, int64_t ex, int64_t tot, int32_t& tA,
+                                                 int32_t& tB) {
+  const int64_t bits = tile_class_bits(valid, c);
+  if (bits == (int64_t(1) << 32)) pl.tiles[tA + static_cast<int32_t>((ex >> 32) & 0xffff)] = e;
+  else if (bits != 0) pl.tiles[ne - 1 - (tB + static_cast<int32_t>(ex >> 48))] = e;
+  tA += static_cast<int32_t>((tot >> 32) & 0xffff);
+  tB += static_cast<int32_t>(tot >> 48);
+}
+
 __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne, int minnpel,
                                                              int allow_moves) {
   __shared__ PlanShared sh;
   __shared__ int32_t hist[kHistCap + 1];
   const int tid = threadIdx.x;
   // pass 1: offsets of the element lists, min / max, big elements (no moves)
-  int32_t carry = 0, lmin = 0x7fffffff, lmax = -1;
+  int32_t carry = 0, lmin = 0x7fffffff, lmax = -1, tA = 0, tB = 0;
   if (tid == 0) pl.scal[3] = 0;
   __syncthreads();
   for (int32_t base = 0; base < ne; base += kPlanThreads) {
     const int32_t e = base + tid;
     const int32_t c = e < ne ? pl.cnt[e] : 0;
-    int32_t tot;
-    const int32_t ex = block_exclusive_scan<int32_t>(c, sh.tmp32, tot);
+    int64_t ptot;
+    const int64_t pex = block_exclusive_scan<int64_t>(c | tile_class_bits(e < ne, c), sh.tmp64, ptot);
+    const int32_t ex = static_cast<int32_t>(pex & 0xffffffff), tot = static_cast<int32_t>(ptot & 0xffffffff);
+    place_tile_class(pl, e < ne, c, e, ne, pex, ptot, tA, tB);
     if (e < ne) {
       pl.off[e] = carry + ex;
       pl.foff[e] = carry + ex;
@@ -106,7 +126,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne,
     }
     carry += tot;
   }
-  if (tid == 0) { pl.off[ne] = carry; pl.foff[ne] = carry; }
+  if (tid == 0) { pl.off[ne] = carry; pl.foff[ne] = carry; pl.scal[6] = tA; pl.scal[7] = tB; }
   for (int o = 16; o > 0; o >>= 1) {
     lmin = min(lmin, __shfl_xor_sync(kFull, lmin, o));
     lmax = max(lmax, __shfl_xor_sync(kFull, lmax, o));
@@ -184,6 +204,8 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne,
   // pass 3: gains, losses, final counts, offsets and the recipient / donor / big lists
   const int64_t L = sh.L, H = sh.H, r = sh.r, rp = sh.rp;
   int32_t cRankL = 0, cRankH = 0, cG = 0, cD = 0, cF = 0, cNR = 0, cND = 0;
+  tA = 0;
+  tB = 0;
   for (int32_t base = 0; base < ne; base += kPlanThreads) {
     const int32_t e = base + tid;
     const int32_t c = e < ne ? pl.cnt[e] : 0;
@@ -206,8 +228,12 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne,
     cG += tot;
     const int32_t dof = cD + block_exclusive_scan<int32_t>(l, sh.tmp32, tot);
     cD += tot;
-    const int32_t fo = cF + block_exclusive_scan<int32_t>(e < ne ? f : 0, sh.tmp32, tot);
-    cF += tot;
+    int64_t ptot;
+    const int64_t pex = block_exclusive_scan<int64_t>((e < ne ? f : 0) | tile_class_bits(e < ne, f),
+                                                      sh.tmp64, ptot);
+    const int32_t fo = cF + static_cast<int32_t>(pex & 0xffffffff);
+    cF += static_cast<int32_t>(ptot & 0xffffffff);
+    place_tile_class(pl, e < ne, f, e, ne, pex, ptot, tA, tB);
     const int32_t ri = cNR + block_exclusive_scan<int32_t>(g > 0 ? 1 : 0, sh.tmp32, tot);
     cNR += tot;
     const int32_t di = cND + block_exclusive_scan<int32_t>(l > 0 ? 1 : 0, sh.tmp32, tot);
@@ -225,6 +251,8 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne,
     }
   }
   if (tid == 0) {
+    pl.scal[6] = tA;
+    pl.scal[7] = tB;
     pl.goff[ne] = cG;
     pl.doff[ne] = cD;
     pl.foff[ne] = cF;
@@ -713,7 +741,7 @@ void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s) {
                          static_cast<int>(big));
     configured = true;
   }
-  launch_stats_warp<T>(a, s);
+  launch_stats_tiles<T>(a, num_sms, s);
   stats_big_kernel<T><<<static_cast<unsigned>(num_sms > 0 ? num_sms : 1), kStatsThreads, big, s>>>(a);
 }
 

@@ -21,8 +21,9 @@ constexpr size_t kNaP = static_cast<size_t>(kNaMaxParticles);
 constexpr size_t kNaE = static_cast<size_t>(kNaMaxElements) + 1;
 
 // Layout (int32 words): element lists [P], particle ids [P], counts [E], list offsets [E],
-// final offsets [E], cursors [E], large-element list [E], plan scalars [16].
-constexpr size_t kNaWords = 2 * kNaP + 5 * kNaE + 16;
+// final offsets [E], cursors [E], large-element list [E], tile-class lists [E], plan
+// scalars [16].
+constexpr size_t kNaWords = 2 * kNaP + 6 * kNaE + 16;
 constexpr size_t kNaBytes = ((4 * kNaWords + 255) / 256) * 256;
 static_assert(kNaMaxParticles == PDFX_NOALLOC_MAX_PARTICLES, "header limit");
 static_assert(kNaMaxElements == PDFX_NOALLOC_MAX_ELEMENTS, "header limit");
@@ -76,7 +77,8 @@ int element_stats_noalloc(Ctx& c, int64_t np, const double* u, const double* v, 
   pl.foff = per_e + 2 * kNaE;
   pl.cursor = per_e + 3 * kNaE;
   pl.big_list = per_e + 4 * kNaE;
-  pl.scal = per_e + 5 * kNaE;
+  pl.tiles = per_e + 5 * kNaE;
+  pl.scal = per_e + 6 * kNaE;
   pl.idx = idx;
   // without particle moves the plan touches only the arrays above; the rest alias the final
   // offsets so that no pointer leaves the scratch
@@ -112,6 +114,7 @@ int element_stats_noalloc(Ctx& c, int64_t np, const double* u, const double* v, 
   a.goff = pl.goff;
   a.movers = pl.movers;
   a.big_list = pl.big_list;
+  a.tiles = pl.tiles;
   a.scal = pl.scal;
   a.ne = c.ne;
   a.np = np;

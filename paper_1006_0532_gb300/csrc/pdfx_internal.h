@@ -73,6 +73,7 @@ struct StatsArgs {
   const int32_t* goff;  // offsets into movers of received particles
   const int32_t* movers;
   const int32_t* big_list;
+  const int32_t* tiles;  // tile-class element lists (scal 6 from the front, scal 7 from the back)
   const int32_t* scal;  // plan scalars: 0 moves, 3 number of large elements
   int32_t ne;
   int64_t np;
@@ -100,6 +101,8 @@ struct Plan {
   int32_t* recips = nullptr;   // [ne] elements that receive
   int32_t* donors = nullptr;   // [ne] elements that give
   int32_t* big_list = nullptr; // [ne] elements above the small binning capacity
+  int32_t* tiles = nullptr;    // [ne] elements of up to kTileSplit particles from the front,
+                               // up to kSmallCap from the back
   int32_t* scal = nullptr;     // [16]: 0 T, 1 n_recips, 2 n_donors, 3 n_big, 4 min, 5 max
   int64_t* hist = nullptr;     // [2 (kHistCap + 1)] prefix sums for the closed form
   int32_t* idx = nullptr;      // [np] element lists
@@ -109,7 +112,8 @@ struct Plan {
 };
 
 constexpr int kHistCap = 8192;      // counts above this are clipped for the closed form
-constexpr int kSmallCap = 1024;     // binning capacity of the warp-per-element kernel
+constexpr int kSmallCap = 1024;     // binning capacity of the block-per-element tile kernels
+constexpr int kTileSplit = 512;     // tile classes: up to 512 particles, then up to kSmallCap
 constexpr int64_t kMaxParticles = int64_t(1) << 28;   // particle ids fit the 28-bit sort key field
 constexpr int kBigCap = 4096;       // binning capacity of the large-element kernel
 
@@ -186,7 +190,7 @@ void launch_redistribute(Particles<T> p, Plan& pl, int32_t ne, int64_t np, const
 template <typename T>
 void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s);
 template <typename T>
-void launch_stats_warp(const StatsArgs<T>& a, cudaStream_t s);   // k_bins_f32.cu / k_bins_f64.cu
+void launch_stats_tiles(const StatsArgs<T>& a, int num_sms, cudaStream_t s);   // k_bins_f32.cu / k_bins_f64.cu
 void launch_node_average(const double* emom, const int32_t* ne_off, const int32_t* ne_list,
                          int32_t nn, double* nmom, cudaStream_t s);
 template <typename T>

@@ -275,8 +275,9 @@ def uniform_fields(nn: int, U=(0.0, 0.0, 0.0), dP=(0.0, 0.0), grad=None, lap=(0.
 # Named workloads.
 # ----------------------------------------------------------------------------------------
 
-def workload(name: str) -> dict:
-    """Grid, fields and parameters of a named synthetic workload.
+def workload(name: str, ppe: int | None = None) -> dict:
+    """Grid, fields and parameters of a named synthetic workload (``ppe`` overrides the
+    particles per element, and with it the particle-number floor of one tenth of it).
 
     ``channel_2k``  : 46 x 24 nodes, 2116 triangles, Re_tau 392, 100 particles per element,
                       dt 1e-4, constant C0 = 3.5 and C_phi = 2 mixing, Philox seed 1.
@@ -299,6 +300,8 @@ def workload(name: str) -> dict:
         p = dict(c0_mode=1, C0=3.5, tm_mode=1, Cphi=2.0, seed=3, ppe=40, dt=1e-4, steps=3)
     else:
         raise KeyError(name)
+    if ppe is not None:
+        p["ppe"] = int(ppe)
     nu = channel_nu(re)
     fields = channel_fields(g, re)
     params = dict(TABLE4)

@@ -297,6 +297,11 @@ def test_one_step_f32_matches_oracle():
     sg0 = c.get_particles()
     assert np.array_equal(sg0["cp"], o.get_particles()["cp"])
     compare_stats(c.element_stats()[0], o.element_stats()[0], 1e-6)
+    # conditional means: FP32 sums of FP32 values over bins of a few particles
+    vo, go = o.bins()
+    vg, gg = c.bins()
+    assert np.array_equal(gg, go)
+    compare_stats(vg, vo, 1e-6, stats_layout=False)
     o.step(w["dt"])
     c.step(w["dt"])
     so, sg = o.get_particles(), c.get_particles()
@@ -313,6 +318,10 @@ def test_one_step_f32_matches_oracle():
     good_e = np.setdiff1d(np.arange(g.ne), bad_e)
     assert np.array_equal(cg[good_e], co[good_e])
     compare_stats(eg, eo, 1e-6, rows=good_e)
+    vo, go = o.bins()
+    vg, gg = c.bins()
+    assert np.array_equal(gg[good_e], go[good_e])
+    compare_stats(vg, vo, 1e-6, rows=good_e, stats_layout=False)
     bad_n = np.unique(g.tri[bad_e].ravel()) if bad_e.size else np.zeros(0, int)
     good_n = np.setdiff1d(np.arange(g.nn), bad_n)
     compare_stats(c.nodal_stats(), o.nodal_stats(), 1e-6, rows=good_n)
