@@ -27,9 +27,17 @@ sys.path.insert(0, ROOT)
 
 METRIC = "particle-updates/sec per full PDF timestep, FP32/batched vs FP64, same GPU"
 UNIT = "particle-updates/s"
-# Algorithmic bytes per particle of the advance kernel (read x,y,u,v,w,omega,psi, elem,
-# cp; write x,y,u,v,w,omega,psi, elem): 4*7+4+1+4*7+4 in FP32, 8*7+4+1+8*7+4 in FP64.
+# Algorithmic bytes per particle-update (keys: 1 FP32 form, 0 FP64 form).
+# advance (pass 1): read x, y, u, v, w, omega, psi, elem, cp; write x, y, u, v, w, omega,
+#   psi, elem: 4*7+4+1+4*7+4 in FP32, 8*7+4+1+8*7+4 in FP64.
+# binning (pass 2): read u, v, w, psi, elem; write cp: 4*4+4+1, 8*4+4+1.
 ADV_BYTES = {1: 65, 0: 121}
+BIN_BYTES = {1: 21, 0: 37}
+# DRAM bytes per particle measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
+# for the current kernels, FP32 form: profiles/advance_kernel_channel_50k_ppe100_f32.md and
+# profiles/stats_tile_kernel_channel_50k_ppe500_f32.md.  None once a kernel changes.
+TRAFFIC_PER_PARTICLE = {"advance": 64.6, "statistics_binning": 40.2}
+STAGES = ["advance", "plan", "lists", "redistribute", "statistics_binning", "node_average"]
 
 
 def peaks():
@@ -274,8 +282,15 @@ def main():
     np_ = r32["np"]
     value = np_ * world * args.steps / (r32["ms"] * 1e-3)
     peak, peak_kind = peaks()
-    adv_ms = r32["stage_ms"][0] / max(r32["stage_n"][0], 1)
-    achieved = ADV_BYTES[1] * np_ / (adv_ms * 1e-3) / 1e9
+    stage = {n: r32["stage_ms"][i] / max(r32["stage_n"][i], 1) for i, n in enumerate(STAGES)}
+    # roofline of the dominant kernel (by time per step): binning or advance
+    dom = "statistics_binning" if stage["statistics_binning"] >= stage["advance"] else "advance"
+    per_p = BIN_BYTES[1] if dom == "statistics_binning" else ADV_BYTES[1]
+    dom_ms = stage[dom]
+    achieved = per_p * np_ / (dom_ms * 1e-3) / 1e9
+    traffic = TRAFFIC_PER_PARTICLE.get(dom)
+    step_bytes = ADV_BYTES[1] + BIN_BYTES[1]
+    step_achieved = step_bytes * np_ * args.steps / (r32["ms"] * 1e-3) / 1e9
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r32["ms"] / args.steps, "higher_is_better": True,
@@ -287,10 +302,15 @@ def main():
                          % (np_ * 37 / 1e9),
                    "sort_every": args.sort_every, "parallelism": "independent instance per GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": "advance_kernel<float>",
-                     "peak_source": peak_kind, "ms_per_launch": adv_ms},
-        "stages_ms_per_step": {n: r32["stage_ms"][i] / max(r32["stage_n"][i], 1) for i, n in enumerate(
-            ["advance", "plan", "lists", "redistribute", "statistics_binning", "node_average"])},
+                     "frac": achieved / peak,
+                     "traffic": traffic * np_ if traffic is not None else None,
+                     "kernel": ("stats_tile_kernel<float> (2 size-class launches per step)"
+                                if dom == "statistics_binning" else "advance_kernel<float>"),
+                     "algorithmic_bytes_per_particle": per_p, "peak_source": peak_kind,
+                     "ms_per_step": dom_ms},
+        "step_roofline": {"bytes_per_update": step_bytes, "achieved": step_achieved,
+                          "peak": peak, "unit": "GB/s", "frac": step_achieved / peak},
+        "stages_ms_per_step": stage,
         "gpu_launches": r32["launches"],
         "e2e": {"value": np_ * world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
