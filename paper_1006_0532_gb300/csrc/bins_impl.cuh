@@ -8,8 +8,12 @@
 // group is cut into chunks of 32 consecutive positions, a warp sorts a chunk in registers
 // (bitonic network, one key per lane), and a key's rank in its group is its rank in its
 // chunk plus, for every other chunk of the group, the number of smaller keys found by a
-// binary search of that sorted chunk.  Keys are distinct (the particle id is part of the
-// key), so the ranks are a permutation and the new order is written by scatter.
+// binary search of that sorted chunk.  Exact keys are distinct (the particle id is part of
+// the key), so the ranks are a permutation and the new order is written by scatter.  A
+// level first runs on the value bits alone (32-bit keys in the FP32 form, 64-bit in the
+// FP64 form); ties are detected exactly (equal neighbours in a sorted chunk, an equal key
+// at the end of a search), and an element with a tie at that level runs it again with the
+// exact (value, id) keys, which rewrites every position.
 // Sect. 3.3, Eqs. 35-36: element means, then central moments about them, summed by one
 // warp in the final order (deterministic); the FP32 form accumulates compensated FP32 per
 // lane and combines lanes as FP32 value/error pairs, the FP64 form sums in FP64.  The 13
@@ -38,7 +42,10 @@ __device__ __forceinline__ uint64_t ord_bits(double x) {
   return (b & 0x8000000000000000ull) ? ~b : (b | 0x8000000000000000ull);
 }
 
-struct K64 {   // FP32 form: value (32 bits) << 28 | id (28 bits)
+struct K32 {   // FP32 form, value bits
+  uint32_t k;
+};
+struct K64 {   // FP32 form: value (32 bits) << 28 | id (28 bits); FP64 form: value bits
   uint64_t k;
 };
 struct K96 {   // FP64 form: value, id
@@ -46,31 +53,64 @@ struct K96 {   // FP64 form: value, id
   uint32_t lo;
 };
 
+__device__ __forceinline__ bool kless(const K32& a, const K32& b) { return a.k < b.k; }
 __device__ __forceinline__ bool kless(const K64& a, const K64& b) { return a.k < b.k; }
 __device__ __forceinline__ bool kless(const K96& a, const K96& b) {
   return (a.hi < b.hi) | ((a.hi == b.hi) & (a.lo < b.lo));
 }
+__device__ __forceinline__ bool keq(const K32& a, const K32& b) { return a.k == b.k; }
+__device__ __forceinline__ bool keq(const K64& a, const K64& b) { return a.k == b.k; }
+__device__ __forceinline__ bool keq(const K96& a, const K96& b) { return (a.hi == b.hi) & (a.lo == b.lo); }
+__device__ __forceinline__ K32 ksel(bool c, const K32& a, const K32& b) { return {c ? a.k : b.k}; }
 __device__ __forceinline__ K64 ksel(bool c, const K64& a, const K64& b) { return {c ? a.k : b.k}; }
 __device__ __forceinline__ K96 ksel(bool c, const K96& a, const K96& b) {
   return {c ? a.hi : b.hi, c ? a.lo : b.lo};
 }
+__device__ __forceinline__ K32 kshfl(const K32& a, int m) { return {__shfl_xor_sync(kFull, a.k, m)}; }
 __device__ __forceinline__ K64 kshfl(const K64& a, int m) { return {__shfl_xor_sync(kFull, a.k, m)}; }
 __device__ __forceinline__ K96 kshfl(const K96& a, int m) {
   return {__shfl_xor_sync(kFull, a.hi, m), __shfl_xor_sync(kFull, a.lo, m)};
 }
-__device__ __forceinline__ K64 make_key(float v, uint32_t pid) {
-  return {(static_cast<uint64_t>(ord_bits(v)) << 28) | (pid & 0x0fffffffu)};
+__device__ __forceinline__ K32 kdown(const K32& a) { return {__shfl_down_sync(kFull, a.k, 1)}; }
+__device__ __forceinline__ K64 kdown(const K64& a) { return {__shfl_down_sync(kFull, a.k, 1)}; }
+__device__ __forceinline__ K96 kdown(const K96& a) {
+  return {__shfl_down_sync(kFull, a.hi, 1), __shfl_down_sync(kFull, a.lo, 1)};
 }
-__device__ __forceinline__ K96 make_key(double v, uint32_t pid) { return {ord_bits(v), pid}; }
+__device__ __forceinline__ void pad_key(K32& k) { k.k = ~0u; }
 __device__ __forceinline__ void pad_key(K64& k) { k.k = ~0ull; }
 __device__ __forceinline__ void pad_key(K96& k) { k.hi = ~0ull; k.lo = ~0u; }
 
-template <typename T> struct KeyOf;
-template <> struct KeyOf<float> { using type = K64; };
-template <> struct KeyOf<double> { using type = K96; };
+// Key of a particle at one level: value bits only (fast pass) or (value, id) (exact pass).
+template <typename T, bool EXACT> struct KeyPolicy;
+template <> struct KeyPolicy<float, false> {
+  using K = K32;
+  __device__ __forceinline__ static K make(float v, const uint32_t*, int32_t) { return {ord_bits(v)}; }
+};
+template <> struct KeyPolicy<float, true> {
+  using K = K64;
+  __device__ __forceinline__ static K make(float v, const uint32_t* pid, int32_t q) {
+    return {(static_cast<uint64_t>(ord_bits(v)) << 28) | (pid[q] & 0x0fffffffu)};
+  }
+};
+template <> struct KeyPolicy<double, false> {
+  using K = K64;
+  __device__ __forceinline__ static K make(double v, const uint32_t*, int32_t) { return {ord_bits(v)}; }
+};
+template <> struct KeyPolicy<double, true> {
+  using K = K96;
+  __device__ __forceinline__ static K make(double v, const uint32_t* pid, int32_t q) {
+    return {ord_bits(v), pid[q]};
+  }
+};
 
 // Sorted chunk keys in shared memory.
 template <typename K, int N> struct KeyArr;
+template <int N>
+struct KeyArr<K32, N> {
+  uint32_t k[N];
+  __device__ __forceinline__ K32 get(int i) const { return {k[i]}; }
+  __device__ __forceinline__ void set(int i, const K32& v) { k[i] = v.k; }
+};
 template <int N>
 struct KeyArr<K64, N> {
   uint64_t k[N];
@@ -86,7 +126,8 @@ struct KeyArr<K96, N> {
 };
 
 // Ascending bitonic sort of one key (and its payload) per lane.  Padding keys are the
-// maximum and compare equal to each other only, so they end in the top lanes.
+// maximum and sort above every real key (ties with them only matter for the fast pass,
+// whose tie test looks at real lanes only).
 template <typename K>
 __device__ __forceinline__ void warp_sort32(K& k, int32_t& v, int lane) {
 #pragma unroll
@@ -103,13 +144,17 @@ __device__ __forceinline__ void warp_sort32(K& k, int32_t& v, int lane) {
   }
 }
 
-// Number of keys below k in a sorted, padded chunk of 32 keys starting at base.
+// Number of keys below k in a sorted, padded chunk of 32 keys starting at base; eq tells
+// whether the chunk holds a key equal to k (the first key not below k is the last one read).
 template <typename Arr, typename K>
-__device__ __forceinline__ int count_below(const Arr& s, int base, const K& k) {
+__device__ __forceinline__ int count_below(const Arr& s, int base, const K& k, bool& eq) {
   int pos = 0;
 #pragma unroll
   for (int st = 16; st >= 1; st >>= 1) pos += kless(s.get(base + pos + st - 1), k) ? st : 0;
-  return pos + (kless(s.get(base + pos), k) ? 1 : 0);
+  const K v = s.get(base + pos);
+  const bool lt = kless(v, k);
+  eq = !lt && keq(v, k);
+  return pos + (lt ? 1 : 0);
 }
 
 // Compensated (Kahan) accumulation for the FP32 form; plain for FP64.  warp_pair() sums
@@ -189,24 +234,105 @@ struct Tile {
   static constexpr int kChunks = 2 * CAP / 32;
   int32_t ord[CAP];                 // particle slots in the current order
   int32_t nord[CAP];                // the next level's order
-  KeyArr<typename KeyOf<T>::type, kChunks * 32> sk;   // sorted chunks (padded to 32)
+  union {                           // sorted chunks (padded to 32), fast or exact keys
+    KeyArr<typename KeyPolicy<T, false>::K, kChunks * 32> fast;
+    KeyArr<typename KeyPolicy<T, true>::K, kChunks * 32> exact;
+  } sk;
   int32_t spay[kChunks * 32];       // their slots
+  int tie[3];                       // a tie was found at level l (fast pass)
   int32_t gfc[CAP / 32 + 1];        // first chunk of each group
   uint8_t cg[kChunks];              // group of each chunk
   T mh[12], ml[12], msh[5];         // moment sums (value/error pairs) and shift values
   int n_gathered;
 };
 
+// One sorting level: the groups of the current order (Gprev groups over n positions, the
+// largest of M) are each ordered by the level's key into nxt.  With M <= 32 a group is one
+// warp sort; otherwise chunks of 32 (tables t.gfc, t.cg) are sorted, then ranked across the
+// group's chunks.  The fast pass (EXACT false) sets *tie when two real keys of a group are
+// equal; its ranks never leave the group, so nxt stays within bounds either way.
+template <typename T, int CAP, int THREADS, bool EXACT, typename Arr>
+__device__ void sort_level(const StatsArgs<T>& a, Tile<T, CAP>& t, Arr& sk, const int32_t* cur,
+                           int32_t* nxt, const T* val, int n, int Gprev, int M, int* tie) {
+  using P = KeyPolicy<T, EXACT>;
+  using K = typename P::K;
+  constexpr int W = THREADS / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  bool found = false;
+  if (M <= 32) {
+    for (int c = warp; c < Gprev; c += W) {
+      const int gs = group_start(c, n, Gprev), len = group_start(c + 1, n, Gprev) - gs;
+      K k;
+      int32_t q = -1;
+      if (lane < len) {
+        q = cur[gs + lane];
+        k = P::make(val[q], a.p.pid, q);
+      } else {
+        pad_key(k);
+      }
+      warp_sort32(k, q, lane);
+      if (!EXACT) {
+        const K nk = kdown(k);   // every lane takes part in the shuffle
+        found |= (lane + 1 < len) && keq(k, nk);
+      }
+      if (lane < len) nxt[gs + lane] = q;
+    }
+  } else {
+    const int nchunks = t.gfc[Gprev];
+    for (int c = warp; c < nchunks; c += W) {
+      const int gi = t.cg[c];
+      const int gs = group_start(gi, n, Gprev), ge = group_start(gi + 1, n, Gprev);
+      const int cs = gs + 32 * (c - t.gfc[gi]), len = min(32, ge - cs);
+      K k;
+      int32_t q = -1;
+      if (lane < len) {
+        q = cur[cs + lane];
+        k = P::make(val[q], a.p.pid, q);
+      } else {
+        pad_key(k);
+      }
+      warp_sort32(k, q, lane);
+      if (!EXACT) {
+        const K nk = kdown(k);   // every lane takes part in the shuffle
+        found |= (lane + 1 < len) && keq(k, nk);
+      }
+      sk.set(c * 32 + lane, k);
+      t.spay[c * 32 + lane] = q;
+    }
+    __syncthreads();
+    for (int c = warp; c < nchunks; c += W) {
+      const int gi = t.cg[c];
+      const int gs = group_start(gi, n, Gprev), ge = group_start(gi + 1, n, Gprev);
+      const int c0 = t.gfc[gi], c1 = t.gfc[gi + 1];
+      const int cs = gs + 32 * (c - c0), len = min(32, ge - cs);
+      const K k = sk.get(c * 32 + lane);
+      int r = lane;
+      bool eq_any = false;
+      for (int c2 = c0; c2 < c1; ++c2) {
+        if (c2 == c) continue;
+        bool eq;
+        r += count_below(sk, c2 * 32, k, eq);
+        eq_any |= eq;
+      }
+      if (!EXACT) found |= eq_any && lane < len;
+      if (lane < len) nxt[gs + r] = t.spay[c * 32 + lane];
+    }
+  }
+  if (!EXACT) {
+    const bool any = __any_sync(kFull, found);   // every lane takes part
+    if (any && lane == 0) *tie = 1;
+  }
+}
+
 // One element of N <= CAP particles (list size after redistribution) by a block of THREADS.
 template <typename T, int CAP, int THREADS>
 __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int N, int moves) {
-  using K = typename KeyOf<T>::type;
-  constexpr int W = THREADS / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned below = (1u << lane) - 1u;
 
   // gather: the element's list minus particles moved out, plus those moved in
   if (threadIdx.x == 0) t.n_gathered = 0;
+  if (threadIdx.x < 3) t.tie[threadIdx.x] = 0;
   __syncthreads();
   {
     const int32_t o = a.off[e], c = a.cnt[e];
@@ -267,70 +393,29 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int 
       if (l > 0 && g[l] <= 1) continue;
       const T* val = l == 0 ? a.p.u : (l == 1 ? a.p.v : a.p.w);
       const int M = (n + Gprev - 1) / Gprev;   // largest group
-      if (M <= 32) {
-        // every group is one chunk: the warp sort is the whole level
-        for (int c = warp; c < Gprev; c += W) {
-          const int gs = group_start(c, n, Gprev), len = group_start(c + 1, n, Gprev) - gs;
-          K k;
-          int32_t q = -1;
-          if (lane < len) {
-            q = cur[gs + lane];
-            k = make_key(val[q], a.p.pid[q]);
-          } else {
-            pad_key(k);
-          }
-          warp_sort32(k, q, lane);
-          if (lane < len) nxt[gs + lane] = q;
-        }
-      } else {
+      if (M > 32 && warp == 0) {
         // chunk tables: Gprev < n / 32 <= CAP / 32 <= 32 groups, one lane each
-        if (warp == 0) {
-          int nch = 0;
-          if (lane < Gprev) nch = (group_start(lane + 1, n, Gprev) - group_start(lane, n, Gprev) + 31) >> 5;
-          int incl = nch;
+        int nch = 0;
+        if (lane < Gprev) nch = (group_start(lane + 1, n, Gprev) - group_start(lane, n, Gprev) + 31) >> 5;
+        int incl = nch;
 #pragma unroll
-          for (int o = 1; o < 32; o <<= 1) {
-            const int y = __shfl_up_sync(kFull, incl, o);
-            if (lane >= o) incl += y;
-          }
-          if (lane < Gprev) {
-            t.gfc[lane] = incl - nch;
-            for (int j = 0; j < nch; ++j) t.cg[incl - nch + j] = static_cast<uint8_t>(lane);
-          }
-          if (lane == Gprev - 1) t.gfc[Gprev] = incl;
+        for (int o = 1; o < 32; o <<= 1) {
+          const int y = __shfl_up_sync(kFull, incl, o);
+          if (lane >= o) incl += y;
         }
-        __syncthreads();
-        const int nchunks = t.gfc[Gprev];
-        for (int c = warp; c < nchunks; c += W) {
-          const int gi = t.cg[c];
-          const int gs = group_start(gi, n, Gprev), ge = group_start(gi + 1, n, Gprev);
-          const int cs = gs + 32 * (c - t.gfc[gi]), len = min(32, ge - cs);
-          K k;
-          int32_t q = -1;
-          if (lane < len) {
-            q = cur[cs + lane];
-            k = make_key(val[q], a.p.pid[q]);
-          } else {
-            pad_key(k);
-          }
-          warp_sort32(k, q, lane);
-          t.sk.set(c * 32 + lane, k);
-          t.spay[c * 32 + lane] = q;
+        if (lane < Gprev) {
+          t.gfc[lane] = incl - nch;
+          for (int j = 0; j < nch; ++j) t.cg[incl - nch + j] = static_cast<uint8_t>(lane);
         }
-        __syncthreads();
-        for (int c = warp; c < nchunks; c += W) {
-          const int gi = t.cg[c];
-          const int gs = group_start(gi, n, Gprev), ge = group_start(gi + 1, n, Gprev);
-          const int c0 = t.gfc[gi], c1 = t.gfc[gi + 1];
-          const int cs = gs + 32 * (c - c0), len = min(32, ge - cs);
-          const K k = t.sk.get(c * 32 + lane);
-          int r = lane;
-          for (int c2 = c0; c2 < c1; ++c2)
-            if (c2 != c) r += count_below(t.sk, c2 * 32, k);
-          if (lane < len) nxt[gs + r] = t.spay[c * 32 + lane];
-        }
+        if (lane == Gprev - 1) t.gfc[Gprev] = incl;
       }
       __syncthreads();
+      sort_level<T, CAP, THREADS, false>(a, t, t.sk.fast, cur, nxt, val, n, Gprev, M, &t.tie[l]);
+      __syncthreads();
+      if (t.tie[l]) {
+        sort_level<T, CAP, THREADS, true>(a, t, t.sk.exact, cur, nxt, val, n, Gprev, M, nullptr);
+        __syncthreads();
+      }
       int32_t* tmp = cur;
       cur = nxt;
       nxt = tmp;
