@@ -202,10 +202,17 @@ struct Acc<double> {
   }
 };
 
-// First position of group g of G over n positions: ceil(g n / G) (g n < 2^18 here).
-__device__ __forceinline__ int group_start(int g, int n, int G) {
-  return static_cast<int>((static_cast<unsigned>(g * n) + static_cast<unsigned>(G - 1)) /
-                          static_cast<unsigned>(G));
+// floor(x / d) for 0 <= x < 2^18 + 2^8 and 1 <= d <= 1024 with inv = 1/d in FP32: the
+// quotient is at most 1025, so the two roundings of (x + 1/2) inv err by at most
+// 1025 * 2^-23 < 2^-12 < 1/(2d), the distance from (x + 1/2)/d to the nearest integer.
+__device__ __forceinline__ int fdiv(int x, float inv) {
+  return __float2int_rz((static_cast<float>(x) + 0.5f) * inv);
+}
+
+// First position of group g of G over n positions: ceil(g n / G) = floor((g n + G - 1) / G)
+// (g <= G <= 256, n <= 1024), invG = 1/G.
+__device__ __forceinline__ int group_start(int g, int n, int G, float invG) {
+  return fdiv(g * n + G - 1, invG);
 }
 
 // Moment outputs, one per lane: em[c] = X + Y/N - (Z/N)(W/N), X a shift value, Y a sum of
@@ -253,7 +260,8 @@ struct Tile {
 // equal; its ranks never leave the group, so nxt stays within bounds either way.
 template <typename T, int CAP, int THREADS, bool EXACT, typename Arr>
 __device__ void sort_level(const StatsArgs<T>& a, Tile<T, CAP>& t, Arr& sk, const int32_t* cur,
-                           int32_t* nxt, const T* val, int n, int Gprev, int M, int* tie) {
+                           int32_t* nxt, const T* val, int n, int Gprev, int M, float invG,
+                           int* tie) {
   using P = KeyPolicy<T, EXACT>;
   using K = typename P::K;
   constexpr int W = THREADS / 32;
@@ -261,7 +269,7 @@ __device__ void sort_level(const StatsArgs<T>& a, Tile<T, CAP>& t, Arr& sk, cons
   bool found = false;
   if (M <= 32) {
     for (int c = warp; c < Gprev; c += W) {
-      const int gs = group_start(c, n, Gprev), len = group_start(c + 1, n, Gprev) - gs;
+      const int gs = group_start(c, n, Gprev, invG), len = group_start(c + 1, n, Gprev, invG) - gs;
       K k;
       int32_t q = -1;
       if (lane < len) {
@@ -281,7 +289,7 @@ __device__ void sort_level(const StatsArgs<T>& a, Tile<T, CAP>& t, Arr& sk, cons
     const int nchunks = t.gfc[Gprev];
     for (int c = warp; c < nchunks; c += W) {
       const int gi = t.cg[c];
-      const int gs = group_start(gi, n, Gprev), ge = group_start(gi + 1, n, Gprev);
+      const int gs = group_start(gi, n, Gprev, invG), ge = group_start(gi + 1, n, Gprev, invG);
       const int cs = gs + 32 * (c - t.gfc[gi]), len = min(32, ge - cs);
       K k;
       int32_t q = -1;
@@ -302,7 +310,7 @@ __device__ void sort_level(const StatsArgs<T>& a, Tile<T, CAP>& t, Arr& sk, cons
     __syncthreads();
     for (int c = warp; c < nchunks; c += W) {
       const int gi = t.cg[c];
-      const int gs = group_start(gi, n, Gprev), ge = group_start(gi + 1, n, Gprev);
+      const int gs = group_start(gi, n, Gprev, invG), ge = group_start(gi + 1, n, Gprev, invG);
       const int c0 = t.gfc[gi], c1 = t.gfc[gi + 1];
       const int cs = gs + 32 * (c - c0), len = min(32, ge - cs);
       const K k = sk.get(c * 32 + lane);
@@ -393,10 +401,11 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int 
       if (l > 0 && g[l] <= 1) continue;
       const T* val = l == 0 ? a.p.u : (l == 1 ? a.p.v : a.p.w);
       const int M = (n + Gprev - 1) / Gprev;   // largest group
+      const float invG = 1.0f / static_cast<float>(Gprev);
       if (M > 32 && warp == 0) {
         // chunk tables: Gprev < n / 32 <= CAP / 32 <= 32 groups, one lane each
         int nch = 0;
-        if (lane < Gprev) nch = (group_start(lane + 1, n, Gprev) - group_start(lane, n, Gprev) + 31) >> 5;
+        if (lane < Gprev) nch = (group_start(lane + 1, n, Gprev, invG) - group_start(lane, n, Gprev, invG) + 31) >> 5;
         int incl = nch;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
@@ -410,10 +419,10 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int 
         if (lane == Gprev - 1) t.gfc[Gprev] = incl;
       }
       __syncthreads();
-      sort_level<T, CAP, THREADS, false>(a, t, t.sk.fast, cur, nxt, val, n, Gprev, M, &t.tie[l]);
+      sort_level<T, CAP, THREADS, false>(a, t, t.sk.fast, cur, nxt, val, n, Gprev, M, invG, &t.tie[l]);
       __syncthreads();
       if (t.tie[l]) {
-        sort_level<T, CAP, THREADS, true>(a, t, t.sk.exact, cur, nxt, val, n, Gprev, M, nullptr);
+        sort_level<T, CAP, THREADS, true>(a, t, t.sk.exact, cur, nxt, val, n, Gprev, M, invG, nullptr);
         __syncthreads();
       }
       int32_t* tmp = cur;
@@ -471,10 +480,11 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int 
 
   // Appendix A bins: conditional scalar means over the final order's bins
   double* vc = a.vcce + static_cast<size_t>(a.G) * e;
+  const float invGb = 1.0f / static_cast<float>(G);
   for (int i = threadIdx.x; i < a.G; i += THREADS) {
     T mval = T(0);
     if (i < G && n > 0) {
-      const int b0 = group_start(i, n, G), b1 = group_start(i + 1, n, G);
+      const int b0 = group_start(i, n, G, invGb), b1 = group_start(i + 1, n, G, invGb);
       Acc<T> sum;
       for (int p = b0; p < b1; ++p) sum.add(a.p.psi[cur[p]]);
       mval = sum.value() / static_cast<T>(b1 - b0);
@@ -482,6 +492,7 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int 
     vc[i] = static_cast<double>(mval);
   }
   // conditioning pointers (and the element-ordered copy of the state every few steps)
+  const float inv_n = n > 0 ? 1.0f / static_cast<float>(n) : 0.0f;
   if (a.resort) {
     const int32_t fo = a.foff[e];
     for (int p = threadIdx.x; p < n; p += THREADS) {
@@ -497,11 +508,10 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int 
       a.out.psi[d] = a.p.psi[q];
       a.out.pid[d] = a.p.pid[q];
       a.out.elem[d] = e;
-      a.out.cp[d] = static_cast<uint8_t>(static_cast<unsigned>(G * p) / static_cast<unsigned>(n));
+      a.out.cp[d] = static_cast<uint8_t>(fdiv(G * p, inv_n));
     }
   } else {
-    for (int p = threadIdx.x; p < n; p += THREADS)
-      a.p.cp[cur[p]] = static_cast<uint8_t>(static_cast<unsigned>(G * p) / static_cast<unsigned>(n));
+    for (int p = threadIdx.x; p < n; p += THREADS) a.p.cp[cur[p]] = static_cast<uint8_t>(fdiv(G * p, inv_n));
   }
 }
 
