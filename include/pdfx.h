@@ -125,8 +125,28 @@ int  pdfx_create(const pdfx_params *p, const pdfx_allocator *alloc, void **out_c
 void pdfx_destroy(void *ctx);
 
 /* Replaces the model parameters (everything except bins, precision and sort_every, which
- * are fixed at creation).  Host pointer.  PDFX_ERR_ARG if those differ. */
+ * are fixed at creation).  Host pointer.  PDFX_ERR_ARG if those differ, and for a batch of
+ * more than one instance (its parameters come from pdfx_set_instances). */
 int  pdfx_set_params(void *ctx, const pdfx_params *p);
+
+/* Batches of independent instances (the paper has no counterpart: each instance is one run
+ * of the method on its own grid, and a batch steps them all with one launch per stage).
+ * Call before pdfx_set_grid.  n instances; p[n] their parameters (host, copied): each may
+ * have its own constants, seed, instance number, source, period_x and MINNPEL, while
+ * precision, sort_every, bins and min_per_bin must equal the context's (else
+ * PDFX_ERR_ARG).  elem_first[n + 1] (host): instance k owns the elements elem_first[k] ..
+ * elem_first[k + 1] - 1 of the union grid that pdfx_set_grid receives next (elem_first[0]
+ * = 0, increasing, elem_first[n] = its ne; the instances may share no edge and no node,
+ * else pdfx_set_grid returns PDFX_ERR_MESH).  Fields are the union's nodal fields; particle
+ * ids restart at 0 in every instance, and particle arrays are ordered by (instance, id).
+ * Statistics are those of the union (element and node ranges of each instance).  With n =
+ * 1 the context becomes a single instance with parameters p[0].  Discards the grid, fields
+ * and particles.  Synchronous. */
+int  pdfx_set_instances(void *ctx, int32_t n, const pdfx_params *p, const int32_t *elem_first);
+
+/* Number of instances (1 for a single grid); writes elem_first[K + 1] and part_first[K + 1]
+ * (first particle slot of each instance) where the pointers are not NULL. */
+int  pdfx_instance_ranges(const void *ctx, int32_t *elem_first, int64_t *part_first);
 
 /* Sets the Eulerian grid (Sect. 3.3, Fig. 1): nn nodes node_xy[nn][2] (FP64, host),
  * ne counter-clockwise triangles tri[ne][3] (int32 node ids, host) and edge tags
@@ -151,8 +171,15 @@ int  pdfx_set_fields(void *ctx, const double *fields, int on_device, void *strea
  * reaches PDFX_MAX_PARTICLES. */
 int  pdfx_init_particles(void *ctx, int32_t ppe, void *stream);
 
+/* As pdfx_init_particles with ppe[k] particles per element in instance k (host array of
+ * K entries); instance k's ids are 0 .. ppe[k] ne_k - 1.  PDFX_ERR_ARG if an instance
+ * reaches PDFX_MAX_PARTICLES or the batch reaches 2^31 - 1 particles. */
+int  pdfx_init_particles_batch(void *ctx, const int32_t *ppe, void *stream);
+
 /* Replaces the particle state by np particles with ids 0..np-1 (FP64 arrays of s, host
- * or device per on_device; cp is ignored) and sets the step counter.  Computes the
+ * or device per on_device; cp is ignored) and sets the step counter.  In a batch, host
+ * arrays only, ordered by instance (ids restart at 0 in each instance; PDFX_ERR_ARG
+ * otherwise).  Computes the
  * statistics and conditional means of that state.  Synchronous for host input. */
 int  pdfx_set_particles(void *ctx, int64_t np, const pdfx_soa *s, uint32_t step,
                         int on_device, void *stream);

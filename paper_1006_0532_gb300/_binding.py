@@ -93,6 +93,9 @@ def lib():
                 "pdfx_num_particles": (i64, [vp]),
                 "pdfx_step_index": (u32, [vp]),
                 "pdfx_step": (C.c_int, [vp, dp, vp]),
+                "pdfx_set_instances": (C.c_int, [vp, i32, C.POINTER(Params), vp]),
+                "pdfx_instance_ranges": (C.c_int, [vp, vp, vp]),
+                "pdfx_init_particles_batch": (C.c_int, [vp, vp, vp]),
                 "pdfx_get_nodal_stats": (C.c_int, [vp, vp, C.c_int, vp]),
                 "pdfx_get_element_stats": (C.c_int, [vp, vp, vp, C.c_int, vp]),
                 "pdfx_get_bins": (C.c_int, [vp, vp, vp, C.c_int, vp]),
@@ -195,6 +198,26 @@ class Context:
         p = make_params(params)
         self._check(lib().pdfx_set_params(self.h, C.byref(p)), "pdfx_set_params")
         self.params = p
+
+    def set_instances(self, params_list, elem_first):
+        """Batch of independent instances (call before set_grid with the union grid)."""
+        n = len(params_list)
+        arr = (Params * n)(*[make_params(p) for p in params_list])
+        ef = np.ascontiguousarray(elem_first, dtype=np.int32)
+        self._check(lib().pdfx_set_instances(self.h, n, arr, ef.ctypes.data), "pdfx_set_instances")
+
+    def instance_ranges(self):
+        """(elem_first[K + 1], part_first[K + 1]) of the instances."""
+        k = int(lib().pdfx_instance_ranges(self.h, None, None))
+        ef = np.zeros(k + 1, dtype=np.int32)
+        pf = np.zeros(k + 1, dtype=np.int64)
+        lib().pdfx_instance_ranges(self.h, ef.ctypes.data, pf.ctypes.data)
+        return ef, pf
+
+    def init_particles_batch(self, ppe, stream=None):
+        arr = np.ascontiguousarray(ppe, dtype=np.int32)
+        self._check(lib().pdfx_init_particles_batch(self.h, arr.ctypes.data, _stream(stream)),
+                    "pdfx_init_particles_batch")
 
     def set_grid(self, grid):
         xy = np.ascontiguousarray(grid.node_xy, dtype=np.float64)

@@ -88,6 +88,47 @@ inline uint32_t key1(const pdfx_params& p) {
   return static_cast<uint32_t>(p.seed >> 32) ^ p.instance;
 }
 
+// Parameters of instance k (the context's own for a single grid).
+const pdfx_params& inst_params(const Ctx& c, int k) { return c.K > 1 ? c.iprm[k] : c.prm; }
+
+// Instance k of element e (host).
+int inst_of_element(const Ctx& c, int32_t e) {
+  if (c.K <= 1) return 0;
+  return static_cast<int>(std::upper_bound(c.h_ielem.begin(), c.h_ielem.end(), e) - c.h_ielem.begin()) - 1;
+}
+
+// Device table of the instances (model, Philox key, element and particle ranges).
+template <typename T>
+int upload_inst(Ctx& c) {
+  const int K = c.K;
+  std::vector<InstDev<T>> h(static_cast<size_t>(K));
+  for (int k = 0; k < K; ++k) {
+    const pdfx_params& p = inst_params(c, k);
+    h[k].m = model_of<T>(p);
+    h[k].k0 = key0(p);
+    h[k].k1 = key1(p);
+    h[k].e0 = c.h_ielem[k];
+    h[k].e1 = c.h_ielem[k + 1];
+    h[k].p0 = c.h_ip0[k];
+    h[k].np = c.h_ip0[k + 1] - c.h_ip0[k];
+    h[k].ppe = c.h_ippe.empty() ? 0 : c.h_ippe[k];
+    h[k].minnpel = p.minnpel;
+  }
+  if (c.inst_cap < K || !c.inst) {
+    dev_free(c, c.inst);
+    c.inst = dev_alloc(c, sizeof(InstDev<double>) * static_cast<size_t>(K));
+    if (!c.inst) return PDFX_ERR_ALLOC;
+    c.inst_cap = K;
+  }
+  PDFX_CUDA(cudaMemcpy(c.inst, h.data(), sizeof(InstDev<T>) * K, cudaMemcpyHostToDevice));
+  if (K > 1) PDFX_CUDA(cudaMemcpy(c.ip0, c.h_ip0.data(), sizeof(int64_t) * (K + 1), cudaMemcpyHostToDevice));
+  return PDFX_OK;
+}
+
+int upload_inst_any(Ctx& c) {
+  return c.prm.precision == 1 ? upload_inst<float>(c) : upload_inst<double>(c);
+}
+
 double min_image_h(double d, double L) {
   if (L > 0.0) {
     if (d > 0.5 * L) return d - L;
@@ -217,7 +258,7 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
   }
   {
     StageTimer t(c, 1, s);
-    launch_plan(c.plan, c.ne, c.prm.minnpel, allow_moves ? 1 : 0, s);
+    launch_plan(c.plan, c.ne, c.K, c.prm.minnpel, allow_moves ? 1 : 0, s);
     c.launches++;
   }
   {
@@ -225,12 +266,13 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
     launch_scatter(p.elem, c.np, c.plan, s);
     c.launches++;
   }
-  if (allow_moves && c.prm.minnpel > 0) {
+  bool any_minnpel = false;
+  for (int k = 0; k < c.K; ++k) any_minnpel |= inst_params(c, k).minnpel > 0;
+  if (allow_moves && any_minnpel) {
     StageTimer t(c, 3, s);
-    launch_redistribute<T>(p, c.plan, c.ne, c.np, static_cast<const ElemGeo<T>*>(c.geo), c.topo,
-                           T(c.prm.period_x), c.prm.source_on, T(c.prm.src_x), T(c.prm.src_y),
-                           T(c.prm.src_r), c.step, key0(c.prm), key1(c.prm), c.num_sms, c.diag,
-                           c.err, s);
+    launch_redistribute<T>(p, c.plan, c.K, static_cast<const InstDev<T>*>(c.inst), c.ne, c.np,
+                           static_cast<const ElemGeo<T>*>(c.geo), c.topo, c.step, c.num_sms,
+                           c.diag, c.err, s);
     c.launches += 3;
   }
   const bool resort = force_resort || (c.prm.sort_every > 0 && c.steps_since_sort + 1 >= c.prm.sort_every);
@@ -250,6 +292,9 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
     a.movers = c.plan.movers;
     a.big_list = c.plan.big_list;
     a.tiles = c.plan.tiles;
+    a.einst = c.K > 1 ? c.einst : nullptr;
+    a.ielem = c.K > 1 ? c.ielem : nullptr;
+    a.K = c.K;
     a.scal = c.plan.scal;
     a.ne = c.ne;
     a.np = c.np;
@@ -310,6 +355,8 @@ int do_step(Ctx& c, double dt, cudaStream_t s) {
     a.step = c.step;
     a.k0 = key0(c.prm);
     a.k1 = key1(c.prm);
+    a.inst = c.K > 1 ? static_cast<const InstDev<T>*>(c.inst) : nullptr;
+    a.einst = c.K > 1 ? c.einst : nullptr;
     launch_advance<T>(a, c.num_sms, s);
     c.launches++;
   }
@@ -320,13 +367,23 @@ int do_step(Ctx& c, double dt, cudaStream_t s) {
 }
 
 template <typename T>
-int do_init(Ctx& c, int32_t ppe, cudaStream_t s) {
-  const int64_t np = static_cast<int64_t>(ppe) * c.ne;
+int do_init(Ctx& c, const int32_t* ppe, cudaStream_t s) {
+  c.h_ippe.assign(ppe, ppe + c.K);
+  c.h_ip0.assign(static_cast<size_t>(c.K) + 1, 0);
+  for (int k = 0; k < c.K; ++k)
+    c.h_ip0[k + 1] = c.h_ip0[k] + static_cast<int64_t>(ppe[k]) * (c.h_ielem[k + 1] - c.h_ielem[k]);
+  const int64_t np = c.h_ip0[c.K];
   PDFX_TRY(ensure_particles<T>(c, np));
+  PDFX_TRY(upload_inst<T>(c));
   Particles<T> p = carve<T>(c.pbuf[c.cur], np);
-  launch_init<T>(p, c.ne, ppe, static_cast<const ElemGeo<T>*>(c.geo), c.topo,
-                 static_cast<const T*>(c.fields), model_of<T>(c.prm), key0(c.prm), key1(c.prm),
-                 c.diag, s);
+  if (c.K > 1)
+    launch_init_batch<T>(p, np, c.K, static_cast<const InstDev<T>*>(c.inst), c.ip0,
+                         static_cast<const ElemGeo<T>*>(c.geo), c.topo,
+                         static_cast<const T*>(c.fields), c.diag, s);
+  else
+    launch_init<T>(p, c.ne, ppe[0], static_cast<const ElemGeo<T>*>(c.geo), c.topo,
+                   static_cast<const T*>(c.fields), model_of<T>(c.prm), key0(c.prm), key1(c.prm),
+                   c.diag, s);
   c.launches++;
   c.step = 0;
   c.steps_since_sort = 0;
@@ -337,6 +394,7 @@ template <typename T>
 int do_set_particles(Ctx& c, int64_t np, const pdfx_soa* soa, uint32_t step, int on_device,
                      cudaStream_t s) {
   PDFX_TRY(ensure_particles<T>(c, np));
+  PDFX_TRY(upload_inst<T>(c));
   Particles<T> p = carve<T>(c.pbuf[c.cur], np);
   const size_t n = static_cast<size_t>(np);
   double* tmp = nullptr;
@@ -354,7 +412,8 @@ int do_set_particles(Ctx& c, int64_t np, const pdfx_soa* soa, uint32_t step, int
     PDFX_CUDA(cudaMemcpyAsync(tel, el, sizeof(int32_t) * n, cudaMemcpyHostToDevice, s));
     el = tel;
   }
-  launch_load_state<T>(p, np, src[0], src[1], src[2], src[3], src[4], src[5], src[6], el, s);
+  launch_load_state<T>(p, np, c.K > 1 ? c.einst : nullptr, c.K > 1 ? c.ip0 : nullptr, src[0],
+                       src[1], src[2], src[3], src[4], src[5], src[6], el, s);
   c.launches++;
   c.step = step;
   c.steps_since_sort = 0;
@@ -372,8 +431,9 @@ int do_get_particles(Ctx& c, pdfx_soa* soa, int on_device, cudaStream_t s) {
   Particles<T> p = carve<T>(c.pbuf[c.cur], c.np);
   const size_t n = static_cast<size_t>(c.np);
   if (on_device) {
-    launch_gather_by_pid<T>(p, c.np, soa->x, soa->y, soa->u, soa->v, soa->w, soa->om, soa->psi,
-                            soa->elem, soa->cp, s);
+    launch_gather_by_pid<T>(p, c.np, c.K > 1 ? c.einst : nullptr, c.K > 1 ? c.ip0 : nullptr,
+                            soa->x, soa->y, soa->u, soa->v, soa->w, soa->om, soa->psi, soa->elem,
+                            soa->cp, s);
     c.launches++;
     return cerr(cudaGetLastError());
   }
@@ -382,8 +442,9 @@ int do_get_particles(Ctx& c, pdfx_soa* soa, int on_device, cudaStream_t s) {
   if (!tmp) return PDFX_ERR_ALLOC;
   int32_t* tel = reinterpret_cast<int32_t*>(tmp + 7 * n);
   uint8_t* tcp = reinterpret_cast<uint8_t*>(tel + n);
-  launch_gather_by_pid<T>(p, c.np, tmp, tmp + n, tmp + 2 * n, tmp + 3 * n, tmp + 4 * n,
-                          tmp + 5 * n, tmp + 6 * n, tel, tcp, s);
+  launch_gather_by_pid<T>(p, c.np, c.K > 1 ? c.einst : nullptr, c.K > 1 ? c.ip0 : nullptr, tmp,
+                          tmp + n, tmp + 2 * n, tmp + 3 * n, tmp + 4 * n, tmp + 5 * n, tmp + 6 * n,
+                          tel, tcp, s);
   c.launches++;
   double* dst[7] = {soa->x, soa->y, soa->u, soa->v, soa->w, soa->om, soa->psi};
   int rc = PDFX_OK;
@@ -434,7 +495,12 @@ int upload_grid(Ctx& c, const HostGeo& g, const std::vector<ElemTopo>& topo,
 
 int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tri, const int8_t* tag) {
   if (nn <= 0 || ne <= 0 || !xy || !tri || !tag) return PDFX_ERR_ARG;
-  const double L = c.prm.period_x;
+  if (c.K > 1 && c.h_ielem.back() != ne) return PDFX_ERR_ARG;
+  if (c.K <= 1) c.h_ielem = {0, ne};
+  std::vector<int32_t> hinst(static_cast<size_t>(ne), 0);   // instance of each element
+  for (int k = 0; k < c.K; ++k)
+    for (int32_t e = c.h_ielem[k]; e < c.h_ielem[k + 1]; ++e) hinst[e] = k;
+  auto period_of = [&](int32_t e) { return inst_params(c, hinst[e]).period_x; };
   HostGeo g;
   g.vx.resize(3 * static_cast<size_t>(ne));
   g.vy.resize(3 * static_cast<size_t>(ne));
@@ -442,6 +508,7 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
   g.ax.resize(ne);
   g.area2.resize(ne);
   for (int32_t e = 0; e < ne; ++e) {
+    const double L = period_of(e);
     const int A = tri[3 * e], B = tri[3 * e + 1], C = tri[3 * e + 2];
     if (A < 0 || B < 0 || C < 0 || A >= nn || B >= nn || C >= nn || A == B || B == C || A == C)
       return PDFX_ERR_MESH;
@@ -499,6 +566,19 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
   for (int32_t e = 0; e < ne; ++e)
     for (int k = 0; k < 3; ++k)
       if ((nbr[3 * e + k] < 0) != (tag[3 * e + k] != 0)) return PDFX_ERR_MESH;
+  if (c.K > 1) {
+    // the instances of a batch share no edge and no node
+    for (int32_t e = 0; e < ne; ++e)
+      for (int k = 0; k < 3; ++k)
+        if (nbr[3 * e + k] >= 0 && hinst[nbr[3 * e + k]] != hinst[e]) return PDFX_ERR_MESH;
+    std::vector<int32_t> owner(static_cast<size_t>(nn), -1);
+    for (int32_t e = 0; e < ne; ++e)
+      for (int k = 0; k < 3; ++k) {
+        int32_t& o = owner[tri[3 * e + k]];
+        if (o >= 0 && o != hinst[e]) return PDFX_ERR_MESH;
+        o = hinst[e];
+      }
+  }
   // boundary lines (Sect. 3.8 reading): own tagged edge first, else the first tagged edge
   // (lowest element id, lowest local edge) touching one of the element's nodes
   std::vector<ElemTopo> topo(static_cast<size_t>(ne));
@@ -522,7 +602,7 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
             if (tag[3 * f + k] != type) continue;
             if (tri[3 * f + (k + 1) % 3] != n && tri[3 * f + (k + 2) % 3] != n) continue;
             edge_line_h(g, f, k, line);
-            line[0] = g.ax[e] + min_image_h(line[0] - g.ax[e], L);
+            line[0] = g.ax[e] + min_image_h(line[0] - g.ax[e], period_of(e));
             found = true;
           }
         }
@@ -551,13 +631,32 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
                       &pl.big_list, &pl.tiles})
     PDFX_TRY(alloc_into(c, *b, E));
   for (int32_t** b : {&pl.off, &pl.foff, &pl.goff, &pl.doff}) PDFX_TRY(alloc_into(c, *b, E + 1));
-  PDFX_TRY(alloc_into(c, pl.scal, 16));
-  PDFX_TRY(alloc_into(c, pl.hist, 2 * (kHistCap + 1)));
+  const int K = c.K;
+  PDFX_TRY(alloc_into(c, pl.scal, 16 * static_cast<size_t>(K)));
+  PDFX_TRY(alloc_into(c, pl.hist, static_cast<size_t>(K) * 2 * (kHistCap + 1)));
+  if (K > 1) {
+    PDFX_TRY(alloc_into(c, c.einst, E));
+    PDFX_TRY(alloc_into(c, c.ielem, static_cast<size_t>(K) + 1));
+    PDFX_TRY(alloc_into(c, c.ip0, static_cast<size_t>(K) + 1));
+    PDFX_TRY(alloc_into(c, c.iminnpel, static_cast<size_t>(K)));
+    std::vector<int32_t> mn(static_cast<size_t>(K));
+    for (int k = 0; k < K; ++k) mn[k] = c.iprm[k].minnpel;
+    PDFX_CUDA(cudaMemcpy(c.einst, hinst.data(), sizeof(int32_t) * E, cudaMemcpyHostToDevice));
+    PDFX_CUDA(cudaMemcpy(c.ielem, c.h_ielem.data(), sizeof(int32_t) * (K + 1), cudaMemcpyHostToDevice));
+    PDFX_CUDA(cudaMemcpy(c.iminnpel, mn.data(), sizeof(int32_t) * K, cudaMemcpyHostToDevice));
+    pl.ielem = c.ielem;
+    pl.ip0 = c.ip0;
+    pl.iminnpel = c.iminnpel;
+  } else {
+    pl.ielem = nullptr;
+    pl.ip0 = nullptr;
+    pl.iminnpel = nullptr;
+  }
   PDFX_TRY(alloc_into(c, c.emom, E * kNS));
   PDFX_TRY(alloc_into(c, c.nmom, N * kNS));
   PDFX_TRY(alloc_into(c, c.vcce, E * c.G));
   PDFX_TRY(alloc_into(c, c.gbin, E * 3));
-  PDFX_CUDA(cudaMemset(pl.scal, 0, sizeof(int32_t) * 16));
+  PDFX_CUDA(cudaMemset(pl.scal, 0, sizeof(int32_t) * 16 * K));
   PDFX_CUDA(cudaMemset(c.vcce, 0, sizeof(double) * E * c.G));
   PDFX_CUDA(cudaMemset(c.emom, 0, sizeof(double) * E * kNS));
   PDFX_CUDA(cudaMemset(c.nmom, 0, sizeof(double) * N * kNS));
@@ -656,8 +755,46 @@ int pdfx_set_params(void* ctx, const pdfx_params* p) {
       p->bins[0] != c->prm.bins[0] || p->bins[1] != c->prm.bins[1] || p->bins[2] != c->prm.bins[2])
     return PDFX_ERR_ARG;
   if (c->have_grid && p->period_x != c->prm.period_x) return PDFX_ERR_ARG;
+  if (c->K > 1) return PDFX_ERR_ARG;   // a batch takes its parameters from pdfx_set_instances
   c->prm = *p;
+  if (c->np > 0) return upload_inst_any(*c);
   return PDFX_OK;
+}
+
+int pdfx_set_instances(void* ctx, int32_t n, const pdfx_params* p, const int32_t* elem_first) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || n < 1 || !p || !elem_first || elem_first[0] != 0) return PDFX_ERR_ARG;
+  for (int32_t k = 0; k < n; ++k) {
+    if (elem_first[k + 1] <= elem_first[k] || !params_valid(p[k])) return PDFX_ERR_ARG;
+    if (p[k].precision != c->prm.precision || p[k].sort_every != c->prm.sort_every ||
+        p[k].bins[0] != c->prm.bins[0] || p[k].bins[1] != c->prm.bins[1] ||
+        p[k].bins[2] != c->prm.bins[2] || p[k].min_per_bin != c->prm.min_per_bin)
+      return PDFX_ERR_ARG;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) return PDFX_ERR_CUDA;
+  if (n == 1) {
+    c->K = 1;
+    c->iprm.clear();
+    c->prm = p[0];
+  } else {
+    c->K = n;
+    c->iprm.assign(p, p + n);
+  }
+  c->h_ielem.assign(elem_first, elem_first + n + 1);
+  c->h_ippe.clear();
+  for (int b = 0; b < 2; ++b) { dev_free(*c, c->pbuf[b]); c->pbuf[b] = nullptr; }
+  c->np = 0;
+  c->have_grid = false;
+  c->have_fields = false;
+  return PDFX_OK;
+}
+
+int pdfx_instance_ranges(const void* ctx, int32_t* elem_first, int64_t* part_first) {
+  const Ctx* c = static_cast<const Ctx*>(ctx);
+  if (!c) return PDFX_ERR_ARG;
+  if (elem_first) for (int k = 0; k <= c->K && k < static_cast<int>(c->h_ielem.size()); ++k) elem_first[k] = c->h_ielem[k];
+  if (part_first) for (int k = 0; k <= c->K && k < static_cast<int>(c->h_ip0.size()); ++k) part_first[k] = c->h_ip0[k];
+  return c->K;
 }
 
 int pdfx_set_grid(void* ctx, int32_t nn, const double* node_xy, int32_t ne, const int32_t* tri,
@@ -686,25 +823,56 @@ int pdfx_set_fields(void* ctx, const double* fields, int on_device, void* stream
   return cerr(cudaGetLastError());
 }
 
+int pdfx_init_particles_batch(void* ctx, const int32_t* ppe, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !ppe) return PDFX_ERR_ARG;
+  if (!c->have_grid || !c->have_fields) return PDFX_ERR_ORDER;
+  int64_t total = 0;
+  for (int k = 0; k < c->K; ++k) {
+    const int64_t nk = static_cast<int64_t>(ppe[k]) * (c->h_ielem[k + 1] - c->h_ielem[k]);
+    if (ppe[k] <= 0 || nk >= kMaxParticles) return PDFX_ERR_ARG;
+    total += nk;
+  }
+  if (total > kMaxSlots) return PDFX_ERR_ARG;
+  return c->prm.precision == 1 ? do_init<float>(*c, ppe, as_stream(stream))
+                               : do_init<double>(*c, ppe, as_stream(stream));
+}
+
 int pdfx_init_particles(void* ctx, int32_t ppe, void* stream) {
   Ctx* c = as_ctx(ctx);
   if (!c || ppe <= 0) return PDFX_ERR_ARG;
-  if (!c->have_grid || !c->have_fields) return PDFX_ERR_ORDER;
-  if (static_cast<int64_t>(ppe) * c->ne >= kMaxParticles) return PDFX_ERR_ARG;
-  return c->prm.precision == 1 ? do_init<float>(*c, ppe, as_stream(stream))
-                               : do_init<double>(*c, ppe, as_stream(stream));
+  const std::vector<int32_t> all(static_cast<size_t>(c->K), ppe);
+  return pdfx_init_particles_batch(ctx, all.data(), stream);
 }
 
 int pdfx_set_particles(void* ctx, int64_t np, const pdfx_soa* s, uint32_t step, int on_device,
                        void* stream) {
   Ctx* c = as_ctx(ctx);
-  if (!c || !s || np < 0 || np >= kMaxParticles) return PDFX_ERR_ARG;
+  if (!c || !s || np < 0 || np > kMaxSlots || (c->K <= 1 && np >= kMaxParticles)) return PDFX_ERR_ARG;
   if (np > 0 && (!s->x || !s->y || !s->u || !s->v || !s->w || !s->om || !s->psi || !s->elem))
     return PDFX_ERR_ARG;
   if (!c->have_grid) return PDFX_ERR_ORDER;
   if (!on_device)
     for (int64_t i = 0; i < np; ++i)
       if (s->elem[i] < 0 || s->elem[i] >= c->ne) return PDFX_ERR_ARG;
+  if (c->K > 1) {
+    // a batch state is given instance by instance (ids restart at each instance)
+    if (on_device) return PDFX_ERR_ARG;
+    c->h_ip0.assign(static_cast<size_t>(c->K) + 1, 0);
+    int prev = 0;
+    for (int64_t i = 0; i < np; ++i) {
+      const int k = inst_of_element(*c, s->elem[i]);
+      if (k < prev) return PDFX_ERR_ARG;
+      prev = k;
+      c->h_ip0[k + 1]++;
+    }
+    for (int k = 0; k < c->K; ++k) {
+      if (c->h_ip0[k + 1] >= kMaxParticles) return PDFX_ERR_ARG;
+      c->h_ip0[k + 1] += c->h_ip0[k];
+    }
+  } else {
+    c->h_ip0 = {0, np};
+  }
   return c->prm.precision == 1 ? do_set_particles<float>(*c, np, s, step, on_device, as_stream(stream))
                                : do_set_particles<double>(*c, np, s, step, on_device, as_stream(stream));
 }

@@ -516,18 +516,22 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int 
 }
 
 // One block per entry of one size class of the plan's tile lists: the elements of up to
-// kTileSplit particles (FRONT) or of kTileSplit + 1 .. kSmallCap (the back of the list).  The
-// grid covers every element; blocks past the class count return at once.  The register cap
+// kTileSplit particles (FRONT) or of kTileSplit + 1 .. kSmallCap (the back of each
+// instance's list).  The grid covers every element; blocks past the class count return.  The register cap
 // keeps 1536 threads resident per SM in the FP32 form, 1024 in the FP64 form.
 template <typename T, int CAP, int THREADS, bool FRONT>
 __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1536 : 1024) / THREADS)
     stats_tile_kernel(const StatsArgs<T> a) {
   __shared__ Tile<T, CAP> t;
-  const int count = FRONT ? a.scal[6] : a.scal[7];
+  // block b is entry b of the tile list; the list of instance k fills its element range
+  // [eb, ee): the first class from the front, the second from the back
   const int b = blockIdx.x;
-  if (b >= count) return;
-  const int moves = a.scal[0] > 0;
-  const int e = FRONT ? a.tiles[b] : a.tiles[a.ne - 1 - b];
+  const int inst = a.einst ? a.einst[b] : 0;
+  const int eb = a.einst ? a.ielem[inst] : 0, ee = a.einst ? a.ielem[inst + 1] : a.ne;
+  const int32_t* sc = a.scal + 16 * inst;
+  if (FRONT ? (b - eb >= sc[6]) : (ee - 1 - b >= sc[7])) return;
+  const int moves = sc[0] > 0;
+  const int e = a.tiles[b];
   const int N = moves ? a.fin[e] : a.cnt[e];
   element_tile<T, CAP, THREADS>(a, t, e, min(N, CAP), moves);
 }

@@ -26,8 +26,7 @@ __device__ __forceinline__ bool inside(const ElemGeo<T>& g, const ElemTopo& t, T
 // vertex); after kHopLimit hops or at a boundary edge, search the elements around the
 // nodes of the old host element (lowest containing id), then all elements.
 template <typename T>
-__device__ int walk(const AdvanceArgs<T>& a, int e0, T x, T y, int& hops, int& fb, int& brute) {
-  const T L = a.m.period_x;
+__device__ int walk(const AdvanceArgs<T>& a, int e0, T x, T y, T L, int& hops, int& fb, int& brute) {
   int e = e0;
   hops = 0;
   for (;;) {
@@ -104,8 +103,9 @@ __device__ __forceinline__ void warp_count(unsigned long long* diag, int slot, i
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(diag + slot, static_cast<unsigned long long>(s));
 }
 
-// FP32: 4 blocks of 256 per SM (64 registers); FP64: 2 blocks.
-template <typename T>
+// FP32: 4 blocks of 256 per SM (64 registers); FP64: 2 blocks.  BATCH: model constants and
+// Philox key of the particle's instance (that of its element) instead of a.m, a.k0, a.k1.
+template <typename T, bool BATCH>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(const AdvanceArgs<T> a) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool valid = i < a.np;
@@ -114,9 +114,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
   int hop_bin = -1;
   int e_new = -1;
   if (valid) {
-    const Model<T>& M = a.m;
-    const T L = M.period_x;
     const int e = a.p.elem[i];
+    const int ki = BATCH ? a.einst[e] : 0;
+    const Model<T>& M = BATCH ? a.inst[ki].m : a.m;
+    const uint32_t k0 = BATCH ? a.inst[ki].k0 : a.k0, k1 = BATCH ? a.inst[ki].k1 : a.k1;
+    const T L = M.period_x;
     const T X0 = a.p.x[i], Y0 = a.p.y[i];
     const T U0[3] = {a.p.u[i], a.p.v[i], a.p.w[i]};
     const T w0 = a.p.om[i], psi0 = a.p.psi[i];
@@ -186,8 +188,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
     }
 
     // Sect. 3.9: six Gaussians and eta
-    const uint4 r0 = philox(make_uint4(pid, a.step, kPurStep, 0u), a.k0, a.k1);
-    const uint4 r1 = philox(make_uint4(pid, a.step, kPurStep, 1u), a.k0, a.k1);
+    const uint4 r0 = philox(make_uint4(pid, a.step, kPurStep, 0u), k0, k1);
+    const uint4 r1 = philox(make_uint4(pid, a.step, kPurStep, 1u), k0, k1);
     T xi[6];
     box_muller(r0.x, r0.y, xi[0], xi[1]);
     box_muller(r0.z, r0.w, xi[2], xi[3]);
@@ -243,7 +245,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
         if (d1 < T(0)) { Xn -= T(2) * d1 * ln.nx; Yn -= T(2) * d1 * ln.ny; }
         Un[0] = Un[1] = Un[2] = T(0);                  // Eq. 56
         int ex = 0;                                    // Eq. 58
-        wn = gamma_draw<T>(a.k0, a.k1, pid, a.step, kPurWallGamma, T(1) / M.C4, M.C4 * q[30], &ex);
+        wn = gamma_draw<T>(k0, k1, pid, a.step, kPurWallGamma, T(1) / M.C4, M.C4 * q[30], &ex);
         c_gex = ex;
       }
     }
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
 
     // Sect. 3.6
     int hops = 0, fb = 0, brute = 0;
-    e_new = walk(a, e, Xn, Yn, hops, fb, brute);
+    e_new = walk(a, e, Xn, Yn, L, hops, fb, brute);
     c_hops = hops;
     c_fb = fb;
     c_brute = brute;
@@ -322,25 +324,29 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
 }
 
 // Last resort of Sect. 3.6 for particles neither the walk nor the fall-back located: one
-// block per particle tests every element; the lowest containing id wins.  The particle's
-// count moves from its old element to the found one; a particle in no element is flagged.
-template <typename T>
+// block per particle tests every element (of the particle's instance); the lowest
+// containing id wins.  The particle's count moves from its old element to the found one; a
+// particle in no element is flagged.
+template <typename T, bool BATCH>
 __global__ void __launch_bounds__(256) brute_search_kernel(AdvanceArgs<T> a) {
   __shared__ int best_s[8];
   const int n = min(*a.brute_count, a.brute_cap);
   for (int j = blockIdx.x; j < n; j += gridDim.x) {
     const int32_t i = a.brute_list[j];
     const T x = a.p.x[i], y = a.p.y[i];
+    const int ki = BATCH ? a.einst[a.p.elem[i]] : 0;
+    const int f0 = BATCH ? a.inst[ki].e0 : 0, f1 = BATCH ? a.inst[ki].e1 : a.ne;
+    const T L = BATCH ? a.inst[ki].m.period_x : a.m.period_x;
     int best = 0x7fffffff;
-    for (int f = threadIdx.x; f < a.ne; f += blockDim.x)
-      if (f < best && inside(a.geo[f], a.topo[f], x, y, a.m.period_x)) best = f;
+    for (int f = f0 + threadIdx.x; f < f1; f += blockDim.x)
+      if (f < best && inside(a.geo[f], a.topo[f], x, y, L)) best = f;
     for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(kFull, best, o));
     if ((threadIdx.x & 31) == 0) best_s[threadIdx.x >> 5] = best;
     __syncthreads();
     if (threadIdx.x == 0) {
       for (int w = 1; w < (blockDim.x >> 5); ++w) best = min(best, best_s[w]);
       const int32_t e0 = a.p.elem[i];
-      if (best < a.ne) {
+      if (best < f1) {
         if (best != e0) {
           atomicSub(a.cnt + e0, 1);
           atomicAdd(a.cnt + best, 1);
@@ -367,15 +373,12 @@ __global__ void __launch_bounds__(256) brute_search_kernel(AdvanceArgs<T> a) {
 // et al.), velocity N(<U>, 2k/3 I), frequency Gamma(1/C4, C4 <omega>), scalar from the
 // source disc.
 template <typename T>
-__global__ void init_kernel(Particles<T> p, int32_t ne, int32_t ppe, const ElemGeo<T>* geo,
-                            const ElemTopo* topo, const T* fields, Model<T> m, uint32_t k0,
-                            uint32_t k1, unsigned long long* diag) {
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int64_t np = static_cast<int64_t>(ne) * ppe;
+__device__ __forceinline__ int init_one(Particles<T> p, int64_t i, int e, uint32_t pid,
+                                        const ElemGeo<T>* geo, const ElemTopo* topo,
+                                        const T* fields, const Model<T>& m, uint32_t k0,
+                                        uint32_t k1) {
   int c_gex = 0;
-  if (i < np) {
-    const int e = static_cast<int>(i / ppe);
-    const uint32_t pid = static_cast<uint32_t>(i);
+  {
     const uint4 r0 = philox(make_uint4(pid, 0u, kPurInit, 0u), k0, k1);
     const uint4 r1 = philox(make_uint4(pid, 0u, kPurInit, 1u), k0, k1);
     const ElemGeo<T> g = geo[e];
@@ -418,6 +421,41 @@ __global__ void init_kernel(Particles<T> p, int32_t ne, int32_t ppe, const ElemG
     p.elem[i] = e;
     p.cp[i] = 0;
   }
+  return c_gex;
+}
+
+template <typename T>
+__global__ void init_kernel(Particles<T> p, int32_t ne, int32_t ppe, const ElemGeo<T>* geo,
+                            const ElemTopo* topo, const T* fields, Model<T> m, uint32_t k0,
+                            uint32_t k1, unsigned long long* diag) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const int64_t np = static_cast<int64_t>(ne) * ppe;
+  int c_gex = 0;
+  if (i < np)
+    c_gex = init_one(p, i, static_cast<int>(i / ppe), static_cast<uint32_t>(i), geo, topo, fields,
+                     m, k0, k1);
+  warp_count(diag, kDiagGammaExhausted, c_gex);
+}
+
+// Batches: slot i belongs to the instance k with p0_k <= i < p0_{k+1}; id i - p0_k, element
+// e0_k + (i - p0_k) / ppe_k (the numbering of a run of that instance alone).
+template <typename T>
+__global__ void init_batch_kernel(Particles<T> p, int64_t np, int K, const InstDev<T>* inst,
+                                  const int64_t* ip0, const ElemGeo<T>* geo, const ElemTopo* topo,
+                                  const T* fields, unsigned long long* diag) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  int c_gex = 0;
+  if (i < np) {
+    int lo = 0, hi = K - 1;   // largest k with ip0[k] <= i
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (ip0[mid] <= i) lo = mid; else hi = mid - 1;
+    }
+    const InstDev<T>& I = inst[lo];
+    const int64_t loc = i - I.p0;
+    c_gex = init_one(p, i, I.e0 + static_cast<int>(loc / I.ppe), static_cast<uint32_t>(loc), geo,
+                     topo, fields, I.m, I.k0, I.k1);
+  }
   warp_count(diag, kDiagGammaExhausted, c_gex);
 }
 
@@ -433,12 +471,13 @@ __global__ void count_kernel(const int32_t* __restrict__ elem, int64_t np, int32
 }
 
 template <typename T>
-__global__ void gather_by_pid_kernel(Particles<T> p, int64_t np, double* x, double* y, double* u,
+__global__ void gather_by_pid_kernel(Particles<T> p, int64_t np, const int32_t* einst,
+                                     const int64_t* ip0, double* x, double* y, double* u,
                                      double* v, double* w, double* om, double* psi,
                                      int32_t* elem, uint8_t* cp) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= np) return;
-  const uint32_t id = p.pid[i];
+  const int64_t id = (einst ? ip0[einst[p.elem[i]]] : 0) + p.pid[i];
   if (x) x[id] = p.x[i];
   if (y) y[id] = p.y[i];
   if (u) u[id] = p.u[i];
@@ -451,7 +490,8 @@ __global__ void gather_by_pid_kernel(Particles<T> p, int64_t np, double* x, doub
 }
 
 template <typename T>
-__global__ void load_state_kernel(Particles<T> p, int64_t np, const double* x, const double* y,
+__global__ void load_state_kernel(Particles<T> p, int64_t np, const int32_t* einst,
+                                  const int64_t* ip0, const double* x, const double* y,
                                   const double* u, const double* v, const double* w,
                                   const double* om, const double* psi, const int32_t* elem) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -464,7 +504,7 @@ __global__ void load_state_kernel(Particles<T> p, int64_t np, const double* x, c
   p.om[i] = static_cast<T>(om[i]);
   p.psi[i] = static_cast<T>(psi[i]);
   p.elem[i] = elem[i];
-  p.pid[i] = static_cast<uint32_t>(i);
+  p.pid[i] = static_cast<uint32_t>(i - (einst ? ip0[einst[elem[i]]] : 0));
   p.cp[i] = 0;
 }
 
@@ -483,8 +523,14 @@ template <typename T>
 void launch_advance(const AdvanceArgs<T>& a, int num_sms, cudaStream_t s) {
   if (a.np <= 0) return;
   cudaMemsetAsync(a.brute_count, 0, sizeof(int), s);
-  advance_kernel<T><<<blocks_for(a.np, 256), 256, 0, s>>>(a);
-  brute_search_kernel<T><<<static_cast<unsigned>(num_sms > 0 ? num_sms : 1), 256, 0, s>>>(a);
+  const unsigned bgrid = static_cast<unsigned>(num_sms > 0 ? num_sms : 1);
+  if (a.einst) {
+    advance_kernel<T, true><<<blocks_for(a.np, 256), 256, 0, s>>>(a);
+    brute_search_kernel<T, true><<<bgrid, 256, 0, s>>>(a);
+  } else {
+    advance_kernel<T, false><<<blocks_for(a.np, 256), 256, 0, s>>>(a);
+    brute_search_kernel<T, false><<<bgrid, 256, 0, s>>>(a);
+  }
 }
 
 template <typename T>
@@ -496,25 +542,36 @@ void launch_init(Particles<T> p, int32_t ne, int32_t ppe, const ElemGeo<T>* geo,
   init_kernel<T><<<blocks_for(np, 256), 256, 0, s>>>(p, ne, ppe, geo, topo, fields, m, k0, k1, diag);
 }
 
+template <typename T>
+void launch_init_batch(Particles<T> p, int64_t np, int K, const InstDev<T>* inst,
+                       const int64_t* ip0, const ElemGeo<T>* geo, const ElemTopo* topo,
+                       const T* fields, unsigned long long* diag, cudaStream_t s) {
+  if (np <= 0) return;
+  init_batch_kernel<T><<<blocks_for(np, 256), 256, 0, s>>>(p, np, K, inst, ip0, geo, topo, fields, diag);
+}
+
 void launch_count(const int32_t* elem, int64_t np, int32_t* cnt, cudaStream_t s) {
   if (np <= 0) return;
   count_kernel<<<blocks_for(np, 256), 256, 0, s>>>(elem, np, cnt);
 }
 
 template <typename T>
-void launch_gather_by_pid(Particles<T> p, int64_t np, double* x, double* y, double* u, double* v,
-                          double* w, double* om, double* psi, int32_t* elem, uint8_t* cp,
-                          cudaStream_t s) {
+void launch_gather_by_pid(Particles<T> p, int64_t np, const int32_t* einst, const int64_t* ip0,
+                          double* x, double* y, double* u, double* v, double* w, double* om,
+                          double* psi, int32_t* elem, uint8_t* cp, cudaStream_t s) {
   if (np <= 0) return;
-  gather_by_pid_kernel<T><<<blocks_for(np, 256), 256, 0, s>>>(p, np, x, y, u, v, w, om, psi, elem, cp);
+  gather_by_pid_kernel<T><<<blocks_for(np, 256), 256, 0, s>>>(p, np, einst, ip0, x, y, u, v, w, om,
+                                                              psi, elem, cp);
 }
 
 template <typename T>
-void launch_load_state(Particles<T> p, int64_t np, const double* x, const double* y,
-                       const double* u, const double* v, const double* w, const double* om,
-                       const double* psi, const int32_t* elem, cudaStream_t s) {
+void launch_load_state(Particles<T> p, int64_t np, const int32_t* einst, const int64_t* ip0,
+                       const double* x, const double* y, const double* u, const double* v,
+                       const double* w, const double* om, const double* psi, const int32_t* elem,
+                       cudaStream_t s) {
   if (np <= 0) return;
-  load_state_kernel<T><<<blocks_for(np, 256), 256, 0, s>>>(p, np, x, y, u, v, w, om, psi, elem);
+  load_state_kernel<T><<<blocks_for(np, 256), 256, 0, s>>>(p, np, einst, ip0, x, y, u, v, w, om,
+                                                           psi, elem);
 }
 
 void launch_convert_fields(const double* in, float* out, int64_t n, cudaStream_t s) {
@@ -527,13 +584,16 @@ void launch_convert_fields(const double* in, float* out, int64_t n, cudaStream_t
   template void launch_init<T>(Particles<T>, int32_t, int32_t, const ElemGeo<T>*,              \
                                const ElemTopo*, const T*, Model<T>, uint32_t, uint32_t,        \
                                unsigned long long*, cudaStream_t);                             \
-  template void launch_gather_by_pid<T>(Particles<T>, int64_t, double*, double*, double*,      \
-                                        double*, double*, double*, double*, int32_t*,          \
-                                        uint8_t*, cudaStream_t);                               \
-  template void launch_load_state<T>(Particles<T>, int64_t, const double*, const double*,      \
+  template void launch_init_batch<T>(Particles<T>, int64_t, int, const InstDev<T>*,            \
+                                     const int64_t*, const ElemGeo<T>*, const ElemTopo*,       \
+                                     const T*, unsigned long long*, cudaStream_t);             \
+  template void launch_gather_by_pid<T>(Particles<T>, int64_t, const int32_t*, const int64_t*, \
+                                        double*, double*, double*, double*, double*, double*,  \
+                                        double*, int32_t*, uint8_t*, cudaStream_t);            \
+  template void launch_load_state<T>(Particles<T>, int64_t, const int32_t*, const int64_t*,    \
                                      const double*, const double*, const double*,              \
-                                     const double*, const double*, const int32_t*,             \
-                                     cudaStream_t);
+                                     const double*, const double*, const double*,              \
+                                     const double*, const int32_t*, cudaStream_t);
 PDFX_INSTANTIATE(double)
 PDFX_INSTANTIATE(float)
 #undef PDFX_INSTANTIATE

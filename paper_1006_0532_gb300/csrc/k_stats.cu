@@ -91,42 +91,55 @@ __device__ __forceinline__ int64_t tile_class_bits(bool valid, int32_t c) {
   return c <= kTileSplit ? (int64_t(1) << 32) : (int64_t(1) << 48);
 }
 __device__ __forceinline__ void place_tile_class(Plan& pl, bool valid, int32_t c, int32_t e,
-                                                 int32_t ne, int64_t ex, int64_t tot, int32_t& tA,
-                                                 int32_t& tB) {
+                                                 int32_t eb, int32_t ee, int64_t ex, int64_t tot,
+                                                 int32_t& tA, int32_t& tB) {
   const int64_t bits = tile_class_bits(valid, c);
-  if (bits == (int64_t(1) << 32)) pl.tiles[tA + static_cast<int32_t>((ex >> 32) & 0xffff)] = e;
-  else if (bits != 0) pl.tiles[ne - 1 - (tB + static_cast<int32_t>(ex >> 48))] = e;
+  if (bits == (int64_t(1) << 32)) pl.tiles[eb + tA + static_cast<int32_t>((ex >> 32) & 0xffff)] = e;
+  else if (bits != 0) pl.tiles[ee - 1 - (tB + static_cast<int32_t>(ex >> 48))] = e;
   tA += static_cast<int32_t>((tot >> 32) & 0xffff);
   tB += static_cast<int32_t>(tot >> 48);
 }
 
-__global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne, int minnpel,
+// One block per instance: elements [eb, ee) of the union grid, particle slots from p0.
+__global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne_all, int minnpel_one,
                                                              int allow_moves) {
   __shared__ PlanShared sh;
   __shared__ int32_t hist[kHistCap + 1];
   const int tid = threadIdx.x;
+  const int inst = blockIdx.x;
+  const bool last = inst == static_cast<int>(gridDim.x) - 1;
+  const int32_t eb = pl.ielem ? pl.ielem[inst] : 0, ee = pl.ielem ? pl.ielem[inst + 1] : ne_all;
+  const int32_t ne = ee - eb;
+  const int32_t p0 = pl.ip0 ? static_cast<int32_t>(pl.ip0[inst]) : 0;
+  const int minnpel = pl.iminnpel ? pl.iminnpel[inst] : minnpel_one;
+  int32_t* scal = pl.scal + 16 * inst;
   // pass 1: offsets of the element lists, min / max, big elements (no moves)
-  int32_t carry = 0, lmin = 0x7fffffff, lmax = -1, tA = 0, tB = 0;
-  if (tid == 0) pl.scal[3] = 0;
+  int32_t carry = p0, lmin = 0x7fffffff, lmax = -1, tA = 0, tB = 0;
+  if (tid == 0) scal[3] = 0;
   __syncthreads();
   for (int32_t base = 0; base < ne; base += kPlanThreads) {
-    const int32_t e = base + tid;
-    const int32_t c = e < ne ? pl.cnt[e] : 0;
+    const bool valid = base + tid < ne;
+    const int32_t e = eb + base + tid;
+    const int32_t c = valid ? pl.cnt[e] : 0;
     int64_t ptot;
-    const int64_t pex = block_exclusive_scan<int64_t>(c | tile_class_bits(e < ne, c), sh.tmp64, ptot);
+    const int64_t pex = block_exclusive_scan<int64_t>(c | tile_class_bits(valid, c), sh.tmp64, ptot);
     const int32_t ex = static_cast<int32_t>(pex & 0xffffffff), tot = static_cast<int32_t>(ptot & 0xffffffff);
-    place_tile_class(pl, e < ne, c, e, ne, pex, ptot, tA, tB);
-    if (e < ne) {
+    place_tile_class(pl, valid, c, e, eb, ee, pex, ptot, tA, tB);
+    if (valid) {
       pl.off[e] = carry + ex;
       pl.foff[e] = carry + ex;
       pl.cursor[e] = carry + ex;
       lmin = min(lmin, c);
       lmax = max(lmax, c);
-      if (c > kSmallCap) pl.big_list[atomicAdd(pl.scal + 3, 1)] = e;
+      if (c > kSmallCap) pl.big_list[eb + atomicAdd(scal + 3, 1)] = e;
     }
     carry += tot;
   }
-  if (tid == 0) { pl.off[ne] = carry; pl.foff[ne] = carry; pl.scal[6] = tA; pl.scal[7] = tB; }
+  if (tid == 0) {
+    if (last) { pl.off[ee] = carry; pl.foff[ee] = carry; }
+    scal[6] = tA;
+    scal[7] = tB;
+  }
   for (int o = 16; o > 0; o >>= 1) {
     lmin = min(lmin, __shfl_xor_sync(kFull, lmin, o));
     lmax = max(lmax, __shfl_xor_sync(kFull, lmax, o));
@@ -139,9 +152,9 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne,
     sh.cmin = a;
     sh.cmax = b;
     sh.need = allow_moves && minnpel > 0 && a < minnpel && (b - a) >= 2;
-    pl.scal[4] = a;
-    pl.scal[5] = b;
-    if (!sh.need) { pl.scal[0] = 0; pl.scal[1] = 0; pl.scal[2] = 0; }
+    scal[4] = a;
+    scal[5] = b;
+    if (!sh.need) { scal[0] = 0; scal[1] = 0; scal[2] = 0; }
   }
   __syncthreads();
   if (!sh.need) return;
@@ -149,10 +162,10 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne,
   // pass 2: histogram of counts and its prefix sums P0[c] = #{c_e <= c}, P1[c] = sum c_e
   for (int i = tid; i <= kHistCap; i += kPlanThreads) hist[i] = 0;
   __syncthreads();
-  for (int32_t e = tid; e < ne; e += kPlanThreads) atomicAdd(&hist[min(pl.cnt[e], kHistCap)], 1);
+  for (int32_t e = eb + tid; e < ee; e += kPlanThreads) atomicAdd(&hist[min(pl.cnt[e], kHistCap)], 1);
   __syncthreads();
-  int64_t* P0 = pl.hist;
-  int64_t* P1 = pl.hist + (kHistCap + 1);
+  int64_t* P0 = pl.hist + static_cast<size_t>(inst) * 2 * (kHistCap + 1);
+  int64_t* P1 = P0 + (kHistCap + 1);
   {
     int64_t c0 = 0, c1 = 0;
     for (int base = 0; base <= kHistCap; base += kPlanThreads) {
@@ -197,27 +210,28 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne,
     sh.H = max_level(T);
     sh.r = T - D_of(P0, P1, sh.L, cmax);
     sh.rp = T - S_of(P0, P1, sh.H, cmax);
-    pl.scal[0] = static_cast<int32_t>(T);
-    pl.scal[3] = 0;
+    scal[0] = static_cast<int32_t>(T);
+    scal[3] = 0;
   }
   __syncthreads();
   // pass 3: gains, losses, final counts, offsets and the recipient / donor / big lists
   const int64_t L = sh.L, H = sh.H, r = sh.r, rp = sh.rp;
-  int32_t cRankL = 0, cRankH = 0, cG = 0, cD = 0, cF = 0, cNR = 0, cND = 0;
+  int32_t cRankL = 0, cRankH = 0, cG = p0, cD = p0, cF = p0, cNR = 0, cND = 0;
   tA = 0;
   tB = 0;
   for (int32_t base = 0; base < ne; base += kPlanThreads) {
-    const int32_t e = base + tid;
-    const int32_t c = e < ne ? pl.cnt[e] : 0;
-    const int32_t atL = (e < ne && c <= L) ? 1 : 0;
-    const int32_t atH = (e < ne && c >= H) ? 1 : 0;
+    const bool valid = base + tid < ne;
+    const int32_t e = eb + base + tid;
+    const int32_t c = valid ? pl.cnt[e] : 0;
+    const int32_t atL = (valid && c <= L) ? 1 : 0;
+    const int32_t atH = (valid && c >= H) ? 1 : 0;
     int32_t tot;
     const int32_t rankL = cRankL + block_exclusive_scan<int32_t>(atL, sh.tmp32, tot);
     cRankL += tot;
     const int32_t rankH = cRankH + block_exclusive_scan<int32_t>(atH, sh.tmp32, tot);
     cRankH += tot;
     int32_t g = 0, l = 0;
-    if (e < ne) {
+    if (valid) {
       if (c < L) g += static_cast<int32_t>(L - c);
       if (atL && rankL < r) g += 1;
       if (c > H) l += static_cast<int32_t>(c - H);
@@ -229,35 +243,37 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne,
     const int32_t dof = cD + block_exclusive_scan<int32_t>(l, sh.tmp32, tot);
     cD += tot;
     int64_t ptot;
-    const int64_t pex = block_exclusive_scan<int64_t>((e < ne ? f : 0) | tile_class_bits(e < ne, f),
+    const int64_t pex = block_exclusive_scan<int64_t>((valid ? f : 0) | tile_class_bits(valid, f),
                                                       sh.tmp64, ptot);
     const int32_t fo = cF + static_cast<int32_t>(pex & 0xffffffff);
     cF += static_cast<int32_t>(ptot & 0xffffffff);
-    place_tile_class(pl, e < ne, f, e, ne, pex, ptot, tA, tB);
+    place_tile_class(pl, valid, f, e, eb, ee, pex, ptot, tA, tB);
     const int32_t ri = cNR + block_exclusive_scan<int32_t>(g > 0 ? 1 : 0, sh.tmp32, tot);
     cNR += tot;
     const int32_t di = cND + block_exclusive_scan<int32_t>(l > 0 ? 1 : 0, sh.tmp32, tot);
     cND += tot;
-    if (e < ne) {
+    if (valid) {
       pl.gain[e] = g;
       pl.loss[e] = l;
       pl.goff[e] = go;
       pl.doff[e] = dof;
       pl.fin[e] = f;
       pl.foff[e] = fo;
-      if (g > 0) pl.recips[ri] = e;
-      if (l > 0) pl.donors[di] = e;
-      if (f > kSmallCap) pl.big_list[atomicAdd(pl.scal + 3, 1)] = e;
+      if (g > 0) pl.recips[eb + ri] = e;
+      if (l > 0) pl.donors[eb + di] = e;
+      if (f > kSmallCap) pl.big_list[eb + atomicAdd(scal + 3, 1)] = e;
     }
   }
   if (tid == 0) {
-    pl.scal[6] = tA;
-    pl.scal[7] = tB;
-    pl.goff[ne] = cG;
-    pl.doff[ne] = cD;
-    pl.foff[ne] = cF;
-    pl.scal[1] = cNR;
-    pl.scal[2] = cND;
+    scal[6] = tA;
+    scal[7] = tB;
+    if (last) {
+      pl.goff[ee] = cG;
+      pl.doff[ee] = cD;
+      pl.foff[ee] = cF;
+    }
+    scal[1] = cNR;
+    scal[2] = cND;
   }
 }
 
@@ -287,13 +303,17 @@ __global__ void scatter_kernel(const int32_t* __restrict__ elem, int64_t np, int
 constexpr int kRedistThreads = 256;
 constexpr int kRedistCap = 4096;   // = PDFX_MAX_PER_ELEMENT
 
+// Every instance in turn (its lists live in its element range, its moves in its slots).
 template <typename T>
-__global__ void __launch_bounds__(kRedistThreads) select_donors_kernel(Particles<T> p, Plan pl) {
+__global__ void __launch_bounds__(kRedistThreads) select_donors_kernel(Particles<T> p, Plan pl, int K) {
   __shared__ uint32_t spid[kRedistCap];
   __shared__ int32_t sslot[kRedistCap];
-  const int32_t ndon = pl.scal[0] > 0 ? pl.scal[2] : 0;
+  for (int inst = 0; inst < K; ++inst) {
+  const int32_t* sc = pl.scal + 16 * inst;
+  const int32_t eb = pl.ielem ? pl.ielem[inst] : 0;
+  const int32_t ndon = sc[0] > 0 ? sc[2] : 0;
   for (int32_t d = blockIdx.x; d < ndon; d += gridDim.x) {
-    const int32_t e = pl.donors[d];
+    const int32_t e = pl.donors[eb + d];
     const int32_t n = min(pl.cnt[e], kRedistCap);
     const int32_t o = pl.off[e];
     const int32_t l = pl.loss[e];
@@ -311,19 +331,27 @@ __global__ void __launch_bounds__(kRedistThreads) select_donors_kernel(Particles
     }
     __syncthreads();
   }
+  }
 }
 
 template <typename T>
 __global__ void __launch_bounds__(kRedistThreads) apply_moves_kernel(
-    Particles<T> p, Plan pl, int64_t np, const ElemGeo<T>* geo, const ElemTopo* topo, T period_x,
-    int source_on, T sx, T sy, T sr, uint32_t step, uint32_t k0, uint32_t k1) {
+    Particles<T> p, Plan pl, int K, const InstDev<T>* inst_tab, int64_t np, const ElemGeo<T>* geo,
+    const ElemTopo* topo, uint32_t step) {
   extern __shared__ __align__(16) unsigned char dyn[];
   uint32_t* spid = reinterpret_cast<uint32_t*>(dyn);
   int32_t* sslot = reinterpret_cast<int32_t*>(dyn + 4 * kRedistCap);
   int32_t* sorted = reinterpret_cast<int32_t*>(dyn + 8 * kRedistCap);
-  const int32_t nrec = pl.scal[0] > 0 ? pl.scal[1] : 0;
+  for (int inst = 0; inst < K; ++inst) {
+  const int32_t* sc = pl.scal + 16 * inst;
+  const int32_t eb = pl.ielem ? pl.ielem[inst] : 0;
+  const int32_t nrec = sc[0] > 0 ? sc[1] : 0;
+  const Model<T>& mi = inst_tab[inst].m;
+  const T period_x = mi.period_x, sx = mi.src_x, sy = mi.src_y, sr = mi.src_r;
+  const int source_on = mi.source_on;
+  const uint32_t k0 = inst_tab[inst].k0, k1 = inst_tab[inst].k1;
   for (int32_t ri = blockIdx.x; ri < nrec; ri += gridDim.x) {
-    const int32_t r = pl.recips[ri];
+    const int32_t r = pl.recips[eb + ri];
     int32_t src = r;
     if (pl.cnt[r] == 0) {
       const ElemTopo t = topo[r];
@@ -386,13 +414,17 @@ __global__ void __launch_bounds__(kRedistThreads) apply_moves_kernel(
     }
     __syncthreads();
   }
+  }
 }
 
 template <typename T>
-__global__ void commit_moves_kernel(Particles<T> p, Plan pl, int64_t np, int32_t ne,
+__global__ void commit_moves_kernel(Particles<T> p, Plan pl, int K, int64_t np, int32_t ne,
                                     unsigned long long* diag, int* err) {
-  const int32_t T_moves = pl.scal[0];
-  for (int32_t k = blockIdx.x * blockDim.x + threadIdx.x; k < T_moves; k += gridDim.x * blockDim.x) {
+  for (int inst = 0; inst < K; ++inst) {
+  const int32_t T_moves = pl.scal[16 * inst];
+  const int32_t p0 = pl.ip0 ? static_cast<int32_t>(pl.ip0[inst]) : 0;
+  for (int32_t j = blockIdx.x * blockDim.x + threadIdx.x; j < T_moves; j += gridDim.x * blockDim.x) {
+    const int32_t k = p0 + j;
     const int32_t q = pl.movers[k];
     const int32_t r = pl.mrecip[k];
     if (q < 0 || q >= np || r < 0 || r >= ne) {   // an inconsistent move table is an error
@@ -411,6 +443,7 @@ __global__ void commit_moves_kernel(Particles<T> p, Plan pl, int64_t np, int32_t
   }
   if (blockIdx.x == 0 && threadIdx.x == 0 && T_moves > 0)
     atomicAdd(diag + kDiagMoves, static_cast<unsigned long long>(T_moves));
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -644,23 +677,15 @@ __device__ void process_element(const StatsArgs<T>& a, int e, int N, int cap, un
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kStatsThreads) stats_small_kernel(const StatsArgs<T> a) {
-  extern __shared__ __align__(16) unsigned char raw[];
-  const int moves = a.scal[0] > 0;
-  const int e = blockIdx.x;
-  if (e >= a.ne) return;
-  const int N = moves ? a.fin[e] : a.cnt[e];
-  if (N > kSmallCap) return;      // handled by the large-element kernel
-  process_element(a, e, N, kSmallCap, raw, moves);
-}
-
-template <typename T>
 __global__ void __launch_bounds__(kStatsThreads) stats_big_kernel(const StatsArgs<T> a) {
   extern __shared__ __align__(16) unsigned char raw[];
-  const int moves = a.scal[0] > 0;
-  const int nbig = a.scal[3];
+  for (int inst = 0; inst < a.K; ++inst) {
+  const int32_t* sc = a.scal + 16 * inst;
+  const int eb = a.ielem ? a.ielem[inst] : 0;
+  const int moves = sc[0] > 0;
+  const int nbig = sc[3];
   for (int b = blockIdx.x; b < nbig; b += gridDim.x) {
-    const int e = a.big_list[b];
+    const int e = a.big_list[eb + b];
     const int N = moves ? a.fin[e] : a.cnt[e];
     if (N > kBigCap) {
       if (threadIdx.x == 0) {
@@ -670,6 +695,7 @@ __global__ void __launch_bounds__(kStatsThreads) stats_big_kernel(const StatsArg
       continue;
     }
     process_element(a, e, N, kBigCap, raw, moves);
+  }
   }
 }
 
@@ -701,8 +727,8 @@ __global__ void node_average_kernel(const double* __restrict__ emom, const int32
 
 }  // namespace
 
-void launch_plan(Plan& pl, int32_t ne, int minnpel, int allow_moves, cudaStream_t s) {
-  plan_kernel<<<1, kPlanThreads, 0, s>>>(pl, ne, minnpel, allow_moves);
+void launch_plan(Plan& pl, int32_t ne, int K, int minnpel, int allow_moves, cudaStream_t s) {
+  plan_kernel<<<static_cast<unsigned>(K > 0 ? K : 1), kPlanThreads, 0, s>>>(pl, ne, minnpel, allow_moves);
 }
 
 void launch_scatter(const int32_t* elem, int64_t np, Plan& pl, cudaStream_t s) {
@@ -711,10 +737,9 @@ void launch_scatter(const int32_t* elem, int64_t np, Plan& pl, cudaStream_t s) {
 }
 
 template <typename T>
-void launch_redistribute(Particles<T> p, Plan& pl, int32_t ne, int64_t np, const ElemGeo<T>* geo,
-                         const ElemTopo* topo, T period_x, int source_on, T sx, T sy, T sr,
-                         uint32_t step, uint32_t k0, uint32_t k1, int num_sms,
-                         unsigned long long* diag, int* err, cudaStream_t s) {
+void launch_redistribute(Particles<T> p, Plan& pl, int K, const InstDev<T>* inst, int32_t ne,
+                         int64_t np, const ElemGeo<T>* geo, const ElemTopo* topo, uint32_t step,
+                         int num_sms, unsigned long long* diag, int* err, cudaStream_t s) {
   const unsigned grid = static_cast<unsigned>(num_sms > 0 ? num_sms : 1);
   static bool configured = false;
   const size_t apply_smem = 12 * static_cast<size_t>(kRedistCap);
@@ -723,20 +748,17 @@ void launch_redistribute(Particles<T> p, Plan& pl, int32_t ne, int64_t np, const
                          static_cast<int>(apply_smem));
     configured = true;
   }
-  select_donors_kernel<T><<<grid, kRedistThreads, 0, s>>>(p, pl);
-  apply_moves_kernel<T><<<grid, kRedistThreads, apply_smem, s>>>(p, pl, np, geo, topo, period_x,
-                                                                  source_on, sx, sy, sr, step, k0, k1);
-  commit_moves_kernel<T><<<grid, 256, 0, s>>>(p, pl, np, ne, diag, err);
+  select_donors_kernel<T><<<grid, kRedistThreads, 0, s>>>(p, pl, K);
+  apply_moves_kernel<T><<<grid, kRedistThreads, apply_smem, s>>>(p, pl, K, inst, np, geo, topo, step);
+  commit_moves_kernel<T><<<grid, 256, 0, s>>>(p, pl, K, np, ne, diag, err);
 }
 
 template <typename T>
 void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s) {
   static bool configured = false;
-  const size_t small = stats_smem_bytes<T>(kSmallCap), big = stats_smem_bytes<T>(kBigCap);
+  const size_t big = stats_smem_bytes<T>(kBigCap);
   static_assert(5 * 8 * kBigCap + 11 * kBigCap <= 227 * 1024, "large-element tile exceeds shared memory");
   if (!configured) {
-    cudaFuncSetAttribute(stats_small_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         static_cast<int>(small));
     cudaFuncSetAttribute(stats_big_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(big));
     configured = true;
@@ -752,9 +774,9 @@ void launch_node_average(const double* emom, const int32_t* ne_off, const int32_
 }
 
 #define PDFX_INSTANTIATE(T)                                                                    \
-  template void launch_redistribute<T>(Particles<T>, Plan&, int32_t, int64_t, const ElemGeo<T>*, \
-                                       const ElemTopo*, T, int, T, T, T, uint32_t, uint32_t,   \
-                                       uint32_t, int, unsigned long long*, int*, cudaStream_t); \
+  template void launch_redistribute<T>(Particles<T>, Plan&, int, const InstDev<T>*, int32_t,   \
+                                       int64_t, const ElemGeo<T>*, const ElemTopo*, uint32_t,  \
+                                       int, unsigned long long*, int*, cudaStream_t);          \
   template void launch_stats<T>(const StatsArgs<T>&, int, cudaStream_t);
 PDFX_INSTANTIATE(double)
 PDFX_INSTANTIATE(float)

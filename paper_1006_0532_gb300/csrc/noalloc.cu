@@ -93,7 +93,7 @@ int element_stats_noalloc(Ctx& c, int64_t np, const double* u, const double* v, 
     iota_kernel<<<static_cast<unsigned>((np + 255) / 256), 256, 0, s>>>(pid, np);
     launch_count(elem, np, pl.cnt, s);
   }
-  launch_plan(pl, c.ne, 0, 0, s);
+  launch_plan(pl, c.ne, 1, 0, 0, s);
   launch_scatter(elem, np, pl, s);
   StatsArgs<double> a{};
   a.p.u = const_cast<double*>(u);
@@ -115,6 +115,9 @@ int element_stats_noalloc(Ctx& c, int64_t np, const double* u, const double* v, 
   a.movers = pl.movers;
   a.big_list = pl.big_list;
   a.tiles = pl.tiles;
+  a.einst = nullptr;   // the whole grid as one instance
+  a.ielem = nullptr;
+  a.K = 1;
   a.scal = pl.scal;
   a.ne = c.ne;
   a.np = np;

@@ -21,6 +21,17 @@ struct Model {
   int c0_mode, tm_mode, interp_mode, source_on;
 };
 
+// One instance of a batch (a grid of the union, its particles and its parameters).  A
+// context without instances is a batch of one.
+template <typename T>
+struct InstDev {
+  Model<T> m;
+  uint32_t k0, k1;       // Philox key (seed, instance)
+  int32_t e0, e1;        // element range in the union grid
+  int64_t p0, np;        // particle slot range
+  int32_t ppe, minnpel;
+};
+
 // Particle storage (structure of arrays) in the working precision.
 template <typename T>
 struct Particles {
@@ -56,6 +67,9 @@ struct AdvanceArgs {
   Model<T> m;
   T dt, sdt;    // time step and its square root
   uint32_t step, k0, k1;
+  // batches: per-instance parameters (m, k0, k1 above are unused) and element -> instance
+  const InstDev<T>* inst;
+  const int32_t* einst;
 };
 
 // Arguments of the statistics / conditional-mean kernels.
@@ -74,6 +88,9 @@ struct StatsArgs {
   const int32_t* movers;
   const int32_t* big_list;
   const int32_t* tiles;  // tile-class element lists (scal 6 from the front, scal 7 from the back)
+  const int32_t* einst;  // element -> instance (nullptr: one instance)
+  const int32_t* ielem;  // [K + 1] first element of each instance
+  int K;                 // instances (plan scalars scal[16 k ...] per instance)
   const int32_t* scal;  // plan scalars: 0 moves, 3 number of large elements
   int32_t ne;
   int64_t np;
@@ -103,8 +120,13 @@ struct Plan {
   int32_t* big_list = nullptr; // [ne] elements above the small binning capacity
   int32_t* tiles = nullptr;    // [ne] elements of up to kTileSplit particles from the front,
                                // up to kSmallCap from the back
-  int32_t* scal = nullptr;     // [16]: 0 T, 1 n_recips, 2 n_donors, 3 n_big, 4 min, 5 max
-  int64_t* hist = nullptr;     // [2 (kHistCap + 1)] prefix sums for the closed form
+  int32_t* scal = nullptr;     // [16 K]: per instance 0 T, 1 n_recips, 2 n_donors, 3 n_big,
+                               // 4 min, 5 max, 6 / 7 tile-class counts; lists of instance k
+                               // live in its element range, its moves in its slot range
+  const int32_t* ielem = nullptr;    // [K + 1] first element of each instance (nullptr: one)
+  const int64_t* ip0 = nullptr;      // [K + 1] first particle slot of each instance
+  const int32_t* iminnpel = nullptr; // [K] MINNPEL of each instance
+  int64_t* hist = nullptr;     // [K][2 (kHistCap + 1)] prefix sums for the closed form
   int32_t* idx = nullptr;      // [np] element lists
   int32_t* movers = nullptr;   // [np] particle slots that move (by move index)
   int32_t* mrecip = nullptr;   // [np] recipient element per move
@@ -115,6 +137,7 @@ constexpr int kHistCap = 8192;      // counts above this are clipped for the clo
 constexpr int kSmallCap = 1024;     // binning capacity of the block-per-element tile kernels
 constexpr int kTileSplit = 512;     // tile classes: up to 512 particles, then up to kSmallCap
 constexpr int64_t kMaxParticles = int64_t(1) << 28;   // particle ids fit the 28-bit sort key field
+constexpr int64_t kMaxSlots = (int64_t(1) << 31) - 1;  // particle slots of a batch (int32 lists)
 constexpr int kBigCap = 4096;       // binning capacity of the large-element kernel
 
 struct Ctx {
@@ -144,6 +167,19 @@ struct Ctx {
   size_t pbuf_bytes = 0;
   uint32_t step = 0;
   int steps_since_sort = 0;
+  // instances of a batch (K = 1: the whole grid)
+  int K = 1;
+  std::vector<pdfx_params> iprm;        // [K] parameters (K > 1 only)
+  std::vector<int32_t> h_ielem;         // [K + 1]
+  std::vector<int64_t> h_ip0;           // [K + 1]
+  std::vector<int32_t> h_ippe;          // [K]
+  std::vector<int32_t> h_nb;            // [3 ne] neighbours (host copy for batch checks)
+  int32_t* einst = nullptr;             // [ne] (K > 1 only)
+  int32_t* ielem = nullptr;             // [K + 1]
+  int64_t* ip0 = nullptr;               // [K + 1]
+  int32_t* iminnpel = nullptr;          // [K]
+  void* inst = nullptr;                 // InstDev<T>[K]
+  int inst_cap = 0;                     // capacity of the instance tables
   // statistics
   Plan plan;
   double* emom = nullptr;       // [ne][13]
@@ -179,28 +215,35 @@ template <typename T>
 void launch_init(Particles<T> p, int32_t ne, int32_t ppe, const ElemGeo<T>* geo,
                  const ElemTopo* topo, const T* fields, Model<T> m, uint32_t k0, uint32_t k1,
                  unsigned long long* diag, cudaStream_t s);
+// Batches: every instance k gets ppe_k particles per element in slots [p0_k, p0_k + np_k).
+template <typename T>
+void launch_init_batch(Particles<T> p, int64_t np, int K, const InstDev<T>* inst,
+                       const int64_t* ip0, const ElemGeo<T>* geo, const ElemTopo* topo,
+                       const T* fields, unsigned long long* diag, cudaStream_t s);
 void launch_count(const int32_t* elem, int64_t np, int32_t* cnt, cudaStream_t s);
-void launch_plan(Plan& pl, int32_t ne, int minnpel, int allow_moves, cudaStream_t s);
+void launch_plan(Plan& pl, int32_t ne, int K, int minnpel, int allow_moves, cudaStream_t s);
 void launch_scatter(const int32_t* elem, int64_t np, Plan& pl, cudaStream_t s);
 template <typename T>
-void launch_redistribute(Particles<T> p, Plan& pl, int32_t ne, int64_t np, const ElemGeo<T>* geo,
-                         const ElemTopo* topo, T period_x, int source_on, T sx, T sy, T sr,
-                         uint32_t step, uint32_t k0, uint32_t k1, int num_sms,
-                         unsigned long long* diag, int* err, cudaStream_t s);
+void launch_redistribute(Particles<T> p, Plan& pl, int K, const InstDev<T>* inst, int32_t ne,
+                         int64_t np, const ElemGeo<T>* geo, const ElemTopo* topo, uint32_t step,
+                         int num_sms, unsigned long long* diag, int* err, cudaStream_t s);
 template <typename T>
 void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s);
 template <typename T>
 void launch_stats_tiles(const StatsArgs<T>& a, int num_sms, cudaStream_t s);   // k_bins_f32.cu / k_bins_f64.cu
 void launch_node_average(const double* emom, const int32_t* ne_off, const int32_t* ne_list,
                          int32_t nn, double* nmom, cudaStream_t s);
+// Particle order of the caller's arrays: by (instance, id), i.e. index p0_k + id (einst and
+// ip0 nullptr: one instance, index = id).
 template <typename T>
-void launch_gather_by_pid(Particles<T> p, int64_t np, double* x, double* y, double* u, double* v,
-                          double* w, double* om, double* psi, int32_t* elem, uint8_t* cp,
-                          cudaStream_t s);
+void launch_gather_by_pid(Particles<T> p, int64_t np, const int32_t* einst, const int64_t* ip0,
+                          double* x, double* y, double* u, double* v, double* w, double* om,
+                          double* psi, int32_t* elem, uint8_t* cp, cudaStream_t s);
 template <typename T>
-void launch_load_state(Particles<T> p, int64_t np, const double* x, const double* y,
-                       const double* u, const double* v, const double* w, const double* om,
-                       const double* psi, const int32_t* elem, cudaStream_t s);
+void launch_load_state(Particles<T> p, int64_t np, const int32_t* einst, const int64_t* ip0,
+                       const double* x, const double* y, const double* u, const double* v,
+                       const double* w, const double* om, const double* psi, const int32_t* elem,
+                       cudaStream_t s);
 void launch_convert_fields(const double* in, float* out, int64_t n, cudaStream_t s);
 template <typename T>
 void launch_check_finite(Particles<T> p, int64_t np, unsigned long long* diag, int* err,

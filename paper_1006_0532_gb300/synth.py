@@ -311,3 +311,69 @@ def workload(name: str, ppe: int | None = None) -> dict:
     params.update({k: v for k, v in p.items() if k not in ("ppe", "dt", "steps")})
     return dict(name=name, grid=g, fields=fields, params=params, ppe=p["ppe"], dt=p["dt"],
                 steps=p["steps"], re_tau=re)
+
+
+# ----------------------------------------------------------------------------------------
+# Batches of independent instances (inputs of one batched context).
+# ----------------------------------------------------------------------------------------
+
+def channel_instance(n_tri: int, re_tau: float, seed: int, ppe: int, src=(0.5, 0.5),
+                     philox_seed: int = 1, instance: int = 0) -> dict:
+    """A jittered channel grid of about n_tri triangles (cells about square on [0, 2] x
+    [0, 1]), its fields, and the parameters of one instance (C0 from Eq. 11, t_m from
+    Eq. 25, MINNPEL = ppe / 10)."""
+    rows = max(2, int(round(math.sqrt(n_tri / 4.0))))
+    g = channel_grid(2 * rows, rows + 1, jitter_x=0.2, jitter_y=0.1, seed=seed)
+    nu = channel_nu(re_tau)
+    params = dict(TABLE4)
+    params.update(nu=nu, Cs=0.02, Ct=0.7, src_x=float(src[0]), src_y=float(src[1]), src_r=0.02,
+                  bins=(4, 4, 4), min_per_bin=2, minnpel=max(1, ppe // 10), interp_mode=0,
+                  period_x=g.period_x, c0_mode=0, C0=0.0, tm_mode=0, Cphi=2.0,
+                  seed=int(philox_seed), instance=int(instance), source_on=1)
+    return dict(grid=g, fields=channel_fields(g, re_tau), params=params, ppe=int(ppe))
+
+
+def union(instances: list[dict]):
+    """Disjoint union of the instances' grids and fields: (grid, fields, elem_first,
+    node_first); element and node ids of instance k are offset by elem_first[k] and
+    node_first[k]."""
+    xy, tri, tag, fl = [], [], [], []
+    ef, nf = [0], [0]
+    for it in instances:
+        g = it["grid"]
+        xy.append(g.node_xy)
+        tri.append(g.tri + nf[-1])
+        tag.append(g.edge_tag)
+        fl.append(it["fields"])
+        ef.append(ef[-1] + g.ne)
+        nf.append(nf[-1] + g.nn)
+    grid = Grid(np.concatenate(xy), np.concatenate(tri).astype(np.int32),
+                np.concatenate(tag).astype(np.int8), instances[0]["grid"].period_x)
+    return grid, np.concatenate(fl), np.array(ef, dtype=np.int32), np.array(nf, dtype=np.int64)
+
+
+def ensemble(n_inst: int = 64, tri_lo: float = 1000.0, tri_hi: float = 60000.0,
+             ppe_lo: int = 50, ppe_hi: int = 500, total_lo: float = 2.7e8,
+             total_hi: float = 3.3e8, key: int = 5) -> list[dict]:
+    """The ensemble of independent channel instances: triangle counts log-uniform in
+    [tri_lo, tri_hi], particles per element uniform in [ppe_lo, ppe_hi], redrawn with the
+    next key until the particle total lies in [total_lo, total_hi]; source position and
+    Philox seed (1000 + k) per instance."""
+    while True:
+        rng = np.random.default_rng(key)
+        u = rng.random(n_inst)
+        v = rng.random(n_inst)
+        w = rng.random(n_inst)
+        tris = np.round(np.exp(np.log(tri_lo) + u * np.log(tri_hi / tri_lo))).astype(int)
+        ppes = (ppe_lo + np.floor(w * (ppe_hi - ppe_lo + 1))).astype(int)
+        rows = np.maximum(2, np.round(np.sqrt(tris / 4.0))).astype(int)
+        total = float(np.sum(4 * rows * rows * ppes))
+        if total_lo <= total <= total_hi:
+            break
+        key += 1
+    out = []
+    for k in range(n_inst):
+        src = (0.25 + 1.5 * u[k], 0.2 + 0.6 * v[k])
+        out.append(channel_instance(int(tris[k]), 392.0, seed=100 + k, ppe=int(ppes[k]), src=src,
+                                    philox_seed=1000 + k, instance=k))
+    return out

@@ -1,0 +1,92 @@
+"""Batched form: instances stepped together in one context must give, bit for bit, what each
+instance gives alone (same grid, fields, parameters, seed and instance number)."""
+import numpy as np
+import pytest
+
+from paper_1006_0532_gb300 import synth
+from helpers import STATE_KEYS
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+from paper_1006_0532_gb300 import _binding as B  # noqa: E402
+
+
+def _instances():
+    spec = [(120, 11, 30, (0.6, 0.4), 7), (300, 12, 20, (1.2, 0.5), 8), (200, 13, 40, (0.3, 0.7), 9)]
+    out = []
+    for k, (tri, seed, ppe, src, ps) in enumerate(spec):
+        it = synth.channel_instance(tri, 392.0, seed=seed, ppe=ppe, src=src, philox_seed=ps, instance=k)
+        it["params"]["minnpel"] = ppe - 1          # particle-number control fires (Appendix B)
+        out.append(it)
+    return out
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_batch_matches_instances_run_alone(precision):
+    ins = _instances()
+    g, F, ef, nf = synth.union(ins)
+    P = [dict(it["params"], precision=precision, sort_every=4) for it in ins]
+    b = B.Context(P[0])
+    b.set_instances(P, ef)
+    b.set_grid(g)
+    b.set_fields(F)
+    b.init_particles_batch([it["ppe"] for it in ins])
+    alone = []
+    for it, p in zip(ins, P):
+        c = B.Context(p)
+        c.set_grid(it["grid"])
+        c.set_fields(it["fields"])
+        c.init_particles(it["ppe"])
+        alone.append(c)
+    dt = 2e-3
+    for _ in range(7):
+        b.step(dt)
+        for c in alone:
+            c.step(dt)
+    ef2, pf = b.instance_ranges()
+    assert np.array_equal(ef2, ef)
+    sb = b.get_particles()
+    eb, cb = b.element_stats()
+    nb = b.nodal_stats()
+    vb, gb = b.bins()
+    moves = 0
+    for k, c in enumerate(alone):
+        sa = c.get_particles()
+        sl = slice(int(pf[k]), int(pf[k + 1]))
+        assert pf[k + 1] - pf[k] == sa["x"].shape[0]
+        for key in STATE_KEYS:
+            assert np.array_equal(sb[key][sl], sa[key]), key
+        assert np.array_equal(sb["elem"][sl] - ef[k], sa["elem"])
+        assert np.array_equal(sb["cp"][sl], sa["cp"])
+        ea, ca = c.element_stats()
+        es = slice(int(ef[k]), int(ef[k + 1]))
+        assert np.array_equal(cb[es], ca)
+        assert np.array_equal(eb[es], ea)
+        assert np.array_equal(nb[int(nf[k]):int(nf[k + 1])], c.nodal_stats())
+        va, ga = c.bins()
+        assert np.array_equal(vb[es], va)
+        assert np.array_equal(gb[es], ga)
+        moves += c.diag()["moves"]
+        assert c.check() == 0
+    assert moves > 0
+    assert b.diag()["moves"] == moves
+    assert b.check() == 0
+
+
+def test_batch_rejects_mismatched_or_connected_instances():
+    ins = _instances()
+    g, F, ef, nf = synth.union(ins)
+    P = [dict(it["params"]) for it in ins]
+    b = B.Context(P[0])
+    bad = [dict(P[0]), dict(P[1], bins=(2, 2, 2)), dict(P[2])]
+    with pytest.raises(B.PdfxError):
+        b.set_instances(bad, ef)
+    with pytest.raises(B.PdfxError):
+        b.set_instances(P, np.array([0, 5, 5, g.ne], dtype=np.int32))
+    # element ranges that cut an instance's grid in two leave shared edges: a mesh error
+    b.set_instances(P, np.array([0, ef[1] // 2, ef[2], g.ne], dtype=np.int32))
+    with pytest.raises(B.PdfxError):
+        b.set_grid(g)
