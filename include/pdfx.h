@@ -199,6 +199,14 @@ uint32_t pdfx_step_index(const void *ctx);
  * means.  Asynchronous on stream.  PDFX_ERR_ORDER without particles and fields. */
 int  pdfx_step(void *ctx, double dt, void *stream);
 
+/* nsteps calls of pdfx_step with the same dt.  With use_graph != 0 the steps of whole
+ * re-order cycles (2 sort_every steps, or 1 without re-ordering) are replayed from a CUDA
+ * graph captured on the first such call (steps before the next cycle start and after the
+ * last whole cycle run as plain launches); the results are those of plain steps.  The
+ * graph is rebuilt after a change of dt, grid, instances, parameters or particle state.
+ * Capture runs on a stream of the library's own; the graph is launched on stream. */
+int  pdfx_step_many(void *ctx, double dt, int32_t nsteps, int use_graph, void *stream);
+
 /* Nodal statistics [nn][13] and element statistics [ne][13] with counts [ne] of the last
  * step (or initialisation), into host or device memory.  Synchronous for host output. */
 int  pdfx_get_nodal_stats(void *ctx, double *out, int on_device, void *stream);

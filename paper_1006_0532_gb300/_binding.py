@@ -94,6 +94,7 @@ def lib():
                 "pdfx_step_index": (u32, [vp]),
                 "pdfx_step": (C.c_int, [vp, dp, vp]),
                 "pdfx_set_instances": (C.c_int, [vp, i32, C.POINTER(Params), vp]),
+                "pdfx_step_many": (C.c_int, [vp, dp, i32, C.c_int, vp]),
                 "pdfx_instance_ranges": (C.c_int, [vp, vp, vp]),
                 "pdfx_init_particles_batch": (C.c_int, [vp, vp, vp]),
                 "pdfx_get_nodal_stats": (C.c_int, [vp, vp, C.c_int, vp]),
@@ -283,6 +284,10 @@ class Context:
 
     def step(self, dt: float, stream=None):
         self._check(lib().pdfx_step(self.h, float(dt), _stream(stream)), "pdfx_step")
+
+    def step_many(self, dt: float, nsteps: int, use_graph: bool = True, stream=None):
+        self._check(lib().pdfx_step_many(self.h, float(dt), int(nsteps), int(bool(use_graph)),
+                                         _stream(stream)), "pdfx_step_many")
 
     def nodal_stats(self, out=None, stream=None):
         if out is None:

@@ -271,7 +271,7 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
   if (allow_moves && any_minnpel) {
     StageTimer t(c, 3, s);
     launch_redistribute<T>(p, c.plan, c.K, static_cast<const InstDev<T>*>(c.inst), c.ne, c.np,
-                           static_cast<const ElemGeo<T>*>(c.geo), c.topo, c.step, c.num_sms,
+                           static_cast<const ElemGeo<T>*>(c.geo), c.topo, c.dstep, c.num_sms,
                            c.diag, c.err, s);
     c.launches += 3;
   }
@@ -304,6 +304,7 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
     a.emom = c.emom;
     a.vcce = c.vcce;
     a.gbin = c.gbin;
+    a.step_inc = allow_moves ? c.dstep : nullptr;   // only a step advances the counter
     a.diag = c.diag;
     a.err = c.err;
     launch_stats<T>(a, c.num_sms, s);
@@ -352,7 +353,7 @@ int do_step(Ctx& c, double dt, cudaStream_t s) {
     a.m = model_of<T>(c.prm);
     a.dt = T(dt);
     a.sdt = T(std::sqrt(dt));
-    a.step = c.step;
+    a.stepc = c.dstep;
     a.k0 = key0(c.prm);
     a.k1 = key1(c.prm);
     a.inst = c.K > 1 ? static_cast<const InstDev<T>*>(c.inst) : nullptr;
@@ -386,6 +387,7 @@ int do_init(Ctx& c, const int32_t* ppe, cudaStream_t s) {
                    c.diag, s);
   c.launches++;
   c.step = 0;
+  PDFX_CUDA(cudaMemsetAsync(c.dstep, 0, sizeof(uint32_t), s));
   c.steps_since_sort = 0;
   return run_statistics<T>(c, false, false, false, s);
 }
@@ -416,6 +418,7 @@ int do_set_particles(Ctx& c, int64_t np, const pdfx_soa* soa, uint32_t step, int
                        src[1], src[2], src[3], src[4], src[5], src[6], el, s);
   c.launches++;
   c.step = step;
+  PDFX_CUDA(cudaMemcpyAsync(c.dstep, &step, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
   c.steps_since_sort = 0;
   const int rc = run_statistics<T>(c, false, false, true, s);
   if (tmp) {
@@ -672,6 +675,76 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
   return PDFX_OK;
 }
 
+// A captured cycle of steps bakes in dt, the grid, the particle storage and the model
+// parameters: any change of those drops it.
+void drop_graph(Ctx& c) {
+  if (c.gexec) cudaGraphExecDestroy(c.gexec);
+  c.gexec = nullptr;
+  c.g_steps = 0;
+}
+
+template <typename T>
+int capture_cycle(Ctx& c, double dt, int nsteps) {
+  drop_graph(c);
+  if (!c.gstream && cudaStreamCreateWithFlags(&c.gstream, cudaStreamNonBlocking) != cudaSuccess)
+    return PDFX_ERR_CUDA;
+  // host bookkeeping is replayed after capture: keep the state of the cycle's start
+  const uint32_t step0 = c.step;
+  const int64_t done0 = c.steps_done, launches0 = c.launches;
+  const int cur0 = c.cur, since0 = c.steps_since_sort;
+  const bool prof = c.profiling;
+  c.profiling = false;
+  PDFX_CUDA(cudaStreamBeginCapture(c.gstream, cudaStreamCaptureModeThreadLocal));
+  int rc = PDFX_OK;
+  for (int k = 0; k < nsteps && rc == PDFX_OK; ++k) rc = do_step<T>(c, dt, c.gstream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(c.gstream, &g);
+  c.profiling = prof;
+  const int64_t launches1 = c.launches;
+  c.step = step0;
+  c.steps_done = done0;
+  c.launches = launches0;
+  if (rc != PDFX_OK || ec != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    c.cur = cur0;
+    c.steps_since_sort = since0;
+    return rc != PDFX_OK ? rc : PDFX_ERR_CUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&c.gexec, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) { c.gexec = nullptr; return PDFX_ERR_CUDA; }
+  if (c.cur != cur0 || c.steps_since_sort != since0) { drop_graph(c); return PDFX_ERR_ORDER; }
+  c.g_dt = dt;
+  c.g_steps = nsteps;
+  c.g_buf = c.pbuf[0];
+  c.g_np = c.np;
+  c.g_launches = launches1 - launches0;
+  return PDFX_OK;
+}
+
+template <typename T>
+int do_step_many(Ctx& c, double dt, int32_t nsteps, int use_graph, cudaStream_t s) {
+  const int cycle = c.prm.sort_every > 0 ? 2 * c.prm.sort_every : 1;
+  int32_t left = nsteps;
+  if (use_graph) {
+    // eager steps up to the start of a re-order cycle, then whole cycles from the graph
+    while (left > 0 && c.steps_since_sort != 0) { PDFX_TRY(do_step<T>(c, dt, s)); --left; }
+    if (left >= cycle) {
+      if (!c.gexec || c.g_dt != dt || c.g_steps != cycle || c.g_buf != c.pbuf[0] || c.g_np != c.np)
+        PDFX_TRY(capture_cycle<T>(c, dt, cycle));
+      while (left >= cycle) {
+        PDFX_CUDA(cudaGraphLaunch(c.gexec, s));
+        c.step += static_cast<uint32_t>(cycle);
+        c.steps_done += cycle;
+        c.launches += c.g_launches;
+        left -= cycle;
+      }
+    }
+  }
+  for (; left > 0; --left) PDFX_TRY(do_step<T>(c, dt, s));
+  return cerr(cudaGetLastError());
+}
+
 Ctx* as_ctx(void* p) { return static_cast<Ctx*>(p); }
 
 }  // namespace
@@ -724,9 +797,14 @@ int pdfx_create(const pdfx_params* p, const pdfx_allocator* alloc, void** out) {
   c->err = static_cast<int*>(dev_alloc(*c, sizeof(int) * 4));
   c->brute_list = static_cast<int32_t*>(dev_alloc(*c, sizeof(int32_t) * kBruteCap));
   c->lost_rec = static_cast<double*>(dev_alloc(*c, sizeof(double) * 4 * kLostRecords));
-  if (!c->diag || !c->err || !c->brute_list || !c->lost_rec) { pdfx_destroy(c); return PDFX_ERR_ALLOC; }
+  c->dstep = static_cast<uint32_t*>(dev_alloc(*c, sizeof(uint32_t)));
+  if (!c->diag || !c->err || !c->brute_list || !c->lost_rec || !c->dstep) {
+    pdfx_destroy(c);
+    return PDFX_ERR_ALLOC;
+  }
   if (cudaMemset(c->diag, 0, sizeof(unsigned long long) * kDiagCount) != cudaSuccess ||
-      cudaMemset(c->err, 0, sizeof(int) * 4) != cudaSuccess) {
+      cudaMemset(c->err, 0, sizeof(int) * 4) != cudaSuccess ||
+      cudaMemset(c->dstep, 0, sizeof(uint32_t)) != cudaSuccess) {
     pdfx_destroy(c);
     return PDFX_ERR_CUDA;
   }
@@ -738,6 +816,8 @@ void pdfx_destroy(void* ctx) {
   Ctx* c = as_ctx(ctx);
   if (!c) return;
   cudaDeviceSynchronize();
+  if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  if (c->gstream) cudaStreamDestroy(c->gstream);
   for (auto& o : c->owned) {
     if (c->has_alloc) c->alloc.release(o.first, o.second, c->alloc.user);
     else cudaFree(o.first);
@@ -757,6 +837,7 @@ int pdfx_set_params(void* ctx, const pdfx_params* p) {
   if (c->have_grid && p->period_x != c->prm.period_x) return PDFX_ERR_ARG;
   if (c->K > 1) return PDFX_ERR_ARG;   // a batch takes its parameters from pdfx_set_instances
   c->prm = *p;
+  drop_graph(*c);
   if (c->np > 0) return upload_inst_any(*c);
   return PDFX_OK;
 }
@@ -772,6 +853,7 @@ int pdfx_set_instances(void* ctx, int32_t n, const pdfx_params* p, const int32_t
       return PDFX_ERR_ARG;
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return PDFX_ERR_CUDA;
+  drop_graph(*c);
   if (n == 1) {
     c->K = 1;
     c->iprm.clear();
@@ -802,6 +884,7 @@ int pdfx_set_grid(void* ctx, int32_t nn, const double* node_xy, int32_t ne, cons
   Ctx* c = as_ctx(ctx);
   if (!c) return PDFX_ERR_ARG;
   if (cudaDeviceSynchronize() != cudaSuccess) return PDFX_ERR_CUDA;
+  drop_graph(*c);
   return set_grid(*c, nn, node_xy, ne, tri, edge_tag);
 }
 
@@ -834,6 +917,7 @@ int pdfx_init_particles_batch(void* ctx, const int32_t* ppe, void* stream) {
     total += nk;
   }
   if (total > kMaxSlots) return PDFX_ERR_ARG;
+  drop_graph(*c);
   return c->prm.precision == 1 ? do_init<float>(*c, ppe, as_stream(stream))
                                : do_init<double>(*c, ppe, as_stream(stream));
 }
@@ -873,6 +957,7 @@ int pdfx_set_particles(void* ctx, int64_t np, const pdfx_soa* s, uint32_t step, 
   } else {
     c->h_ip0 = {0, np};
   }
+  drop_graph(*c);
   return c->prm.precision == 1 ? do_set_particles<float>(*c, np, s, step, on_device, as_stream(stream))
                                : do_set_particles<double>(*c, np, s, step, on_device, as_stream(stream));
 }
@@ -893,6 +978,14 @@ int64_t pdfx_num_particles(const void* ctx) {
 uint32_t pdfx_step_index(const void* ctx) {
   const Ctx* c = static_cast<const Ctx*>(ctx);
   return c ? c->step : 0;
+}
+
+int pdfx_step_many(void* ctx, double dt, int32_t nsteps, int use_graph, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !(dt > 0.0) || nsteps < 0) return PDFX_ERR_ARG;
+  if (!c->pbuf[0] || !c->have_fields) return PDFX_ERR_ORDER;
+  return c->prm.precision == 1 ? do_step_many<float>(*c, dt, nsteps, use_graph, as_stream(stream))
+                               : do_step_many<double>(*c, dt, nsteps, use_graph, as_stream(stream));
 }
 
 int pdfx_step(void* ctx, double dt, void* stream) {

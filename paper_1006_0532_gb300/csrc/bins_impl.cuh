@@ -526,6 +526,7 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1536 : 1024) / THRE
   // block b is entry b of the tile list; the list of instance k fills its element range
   // [eb, ee): the first class from the front, the second from the back
   const int b = blockIdx.x;
+  if (FRONT && b == 0 && threadIdx.x == 0 && a.step_inc) atomicAdd(a.step_inc, 1u);
   const int inst = a.einst ? a.einst[b] : 0;
   const int eb = a.einst ? a.ielem[inst] : 0, ee = a.einst ? a.ielem[inst + 1] : a.ne;
   const int32_t* sc = a.scal + 16 * inst;

@@ -188,8 +188,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
     }
 
     // Sect. 3.9: six Gaussians and eta
-    const uint4 r0 = philox(make_uint4(pid, a.step, kPurStep, 0u), k0, k1);
-    const uint4 r1 = philox(make_uint4(pid, a.step, kPurStep, 1u), k0, k1);
+    const uint32_t step = *a.stepc;
+    const uint4 r0 = philox(make_uint4(pid, step, kPurStep, 0u), k0, k1);
+    const uint4 r1 = philox(make_uint4(pid, step, kPurStep, 1u), k0, k1);
     T xi[6];
     box_muller(r0.x, r0.y, xi[0], xi[1]);
     box_muller(r0.z, r0.w, xi[2], xi[3]);
@@ -245,7 +246,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
         if (d1 < T(0)) { Xn -= T(2) * d1 * ln.nx; Yn -= T(2) * d1 * ln.ny; }
         Un[0] = Un[1] = Un[2] = T(0);                  // Eq. 56
         int ex = 0;                                    // Eq. 58
-        wn = gamma_draw<T>(k0, k1, pid, a.step, kPurWallGamma, T(1) / M.C4, M.C4 * q[30], &ex);
+        wn = gamma_draw<T>(k0, k1, pid, step, kPurWallGamma, T(1) / M.C4, M.C4 * q[30], &ex);
         c_gex = ex;
       }
     }

@@ -337,7 +337,8 @@ __global__ void __launch_bounds__(kRedistThreads) select_donors_kernel(Particles
 template <typename T>
 __global__ void __launch_bounds__(kRedistThreads) apply_moves_kernel(
     Particles<T> p, Plan pl, int K, const InstDev<T>* inst_tab, int64_t np, const ElemGeo<T>* geo,
-    const ElemTopo* topo, uint32_t step) {
+    const ElemTopo* topo, const uint32_t* stepc) {
+  const uint32_t step = *stepc;
   extern __shared__ __align__(16) unsigned char dyn[];
   uint32_t* spid = reinterpret_cast<uint32_t*>(dyn);
   int32_t* sslot = reinterpret_cast<int32_t*>(dyn + 4 * kRedistCap);
@@ -738,7 +739,7 @@ void launch_scatter(const int32_t* elem, int64_t np, Plan& pl, cudaStream_t s) {
 
 template <typename T>
 void launch_redistribute(Particles<T> p, Plan& pl, int K, const InstDev<T>* inst, int32_t ne,
-                         int64_t np, const ElemGeo<T>* geo, const ElemTopo* topo, uint32_t step,
+                         int64_t np, const ElemGeo<T>* geo, const ElemTopo* topo, const uint32_t* stepc,
                          int num_sms, unsigned long long* diag, int* err, cudaStream_t s) {
   const unsigned grid = static_cast<unsigned>(num_sms > 0 ? num_sms : 1);
   static bool configured = false;
@@ -749,7 +750,7 @@ void launch_redistribute(Particles<T> p, Plan& pl, int K, const InstDev<T>* inst
     configured = true;
   }
   select_donors_kernel<T><<<grid, kRedistThreads, 0, s>>>(p, pl, K);
-  apply_moves_kernel<T><<<grid, kRedistThreads, apply_smem, s>>>(p, pl, K, inst, np, geo, topo, step);
+  apply_moves_kernel<T><<<grid, kRedistThreads, apply_smem, s>>>(p, pl, K, inst, np, geo, topo, stepc);
   commit_moves_kernel<T><<<grid, 256, 0, s>>>(p, pl, K, np, ne, diag, err);
 }
 
@@ -775,7 +776,8 @@ void launch_node_average(const double* emom, const int32_t* ne_off, const int32_
 
 #define PDFX_INSTANTIATE(T)                                                                    \
   template void launch_redistribute<T>(Particles<T>, Plan&, int, const InstDev<T>*, int32_t,   \
-                                       int64_t, const ElemGeo<T>*, const ElemTopo*, uint32_t,  \
+                                       int64_t, const ElemGeo<T>*, const ElemTopo*,            \
+                                       const uint32_t*,                                        \
                                        int, unsigned long long*, int*, cudaStream_t);          \
   template void launch_stats<T>(const StatsArgs<T>&, int, cudaStream_t);
 PDFX_INSTANTIATE(double)

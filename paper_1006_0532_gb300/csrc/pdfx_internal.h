@@ -66,7 +66,8 @@ struct AdvanceArgs {
   double* lost_rec;      // [kLostRecords][4]
   Model<T> m;
   T dt, sdt;    // time step and its square root
-  uint32_t step, k0, k1;
+  const uint32_t* stepc;   // step counter (Philox counter word) in device memory
+  uint32_t k0, k1;
   // batches: per-instance parameters (m, k0, k1 above are unused) and element -> instance
   const InstDev<T>* inst;
   const int32_t* einst;
@@ -100,6 +101,7 @@ struct StatsArgs {
   double* emom;
   double* vcce;
   int32_t* gbin;
+  uint32_t* step_inc;    // stepping: the step counter, advanced once after this step's reads
   unsigned long long* diag;
   int* err;
 };
@@ -165,8 +167,17 @@ struct Ctx {
   int cur = 0;
   void* pbuf[2] = {nullptr, nullptr};  // one allocation per buffer
   size_t pbuf_bytes = 0;
-  uint32_t step = 0;
+  uint32_t step = 0;             // host mirror of the device step counter
   int steps_since_sort = 0;
+  uint32_t* dstep = nullptr;     // device step counter (read by the kernels of a step)
+  // CUDA graph of a cycle of steps (2 sort_every steps, so the buffer roles repeat)
+  cudaStream_t gstream = nullptr;
+  cudaGraphExec_t gexec = nullptr;
+  double g_dt = 0.0;
+  int g_steps = 0;
+  const void* g_buf = nullptr;
+  int64_t g_np = -1;
+  int64_t g_launches = 0;
   // instances of a batch (K = 1: the whole grid)
   int K = 1;
   std::vector<pdfx_params> iprm;        // [K] parameters (K > 1 only)
@@ -225,7 +236,7 @@ void launch_plan(Plan& pl, int32_t ne, int K, int minnpel, int allow_moves, cuda
 void launch_scatter(const int32_t* elem, int64_t np, Plan& pl, cudaStream_t s);
 template <typename T>
 void launch_redistribute(Particles<T> p, Plan& pl, int K, const InstDev<T>* inst, int32_t ne,
-                         int64_t np, const ElemGeo<T>* geo, const ElemTopo* topo, uint32_t step,
+                         int64_t np, const ElemGeo<T>* geo, const ElemTopo* topo, const uint32_t* stepc,
                          int num_sms, unsigned long long* diag, int* err, cudaStream_t s);
 template <typename T>
 void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s);

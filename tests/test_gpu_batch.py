@@ -90,3 +90,60 @@ def test_batch_rejects_mismatched_or_connected_instances():
     b.set_instances(P, np.array([0, ef[1] // 2, ef[2], g.ne], dtype=np.int32))
     with pytest.raises(B.PdfxError):
         b.set_grid(g)
+
+
+def _single(it, precision, sort_every):
+    c = B.Context(dict(it["params"], precision=precision, sort_every=sort_every))
+    c.set_grid(it["grid"])
+    c.set_fields(it["fields"])
+    c.init_particles(it["ppe"])
+    return c
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_graph_replay_equals_plain_steps(precision):
+    """Re-order cycles replayed from a CUDA graph give the plain steps' results (11 steps
+    with a cycle of 4: one plain step after a first plain one, two cycles, a remainder)."""
+    it = _instances()[1]
+    a = _single(it, precision, 2)
+    b = _single(it, precision, 2)
+    dt = 2e-3
+    a.step(dt)
+    b.step(dt)
+    for _ in range(11):
+        a.step(dt)
+    b.step_many(dt, 11, use_graph=True)
+    assert a.step_index == b.step_index == 12
+    sa, sb = a.get_particles(), b.get_particles()
+    for key in STATE_KEYS + ("elem", "cp"):
+        assert np.array_equal(sa[key], sb[key]), key
+    assert np.array_equal(a.element_stats()[0], b.element_stats()[0])
+    assert np.array_equal(a.nodal_stats(), b.nodal_stats())
+    assert a.diag()["moves"] == b.diag()["moves"]
+    # a further plain step continues from the replayed state
+    a.step(dt)
+    b.step(dt)
+    assert np.array_equal(a.get_particles()["x"], b.get_particles()["x"])
+    assert b.check() == 0
+
+
+def test_batch_graph_equals_instances_run_alone():
+    ins = _instances()
+    g, F, ef, nf = synth.union(ins)
+    P = [dict(it["params"], precision=1, sort_every=2) for it in ins]
+    b = B.Context(P[0])
+    b.set_instances(P, ef)
+    b.set_grid(g)
+    b.set_fields(F)
+    b.init_particles_batch([it["ppe"] for it in ins])
+    b.step_many(2e-3, 9, use_graph=True)
+    _, pf = b.instance_ranges()
+    sb = b.get_particles()
+    for k, it in enumerate(ins):
+        c = _single(it, 1, 2)
+        for _ in range(9):
+            c.step(2e-3)
+        sa = c.get_particles()
+        sl = slice(int(pf[k]), int(pf[k + 1]))
+        for key in STATE_KEYS:
+            assert np.array_equal(sb[key][sl], sa[key]), key
