@@ -231,6 +231,75 @@ def e2e_form(torch, B, c, w, args):
     return el, nn * 32 * 8, nn * 13 * 8
 
 
+def batched_form(torch, B, synth, args):
+    """The ensemble of independent instances (64 channel grids of 1k-57k triangles at 50-500
+    particles per element, about 287M particles, FP32 state): one context stepping all of
+    them with one launch per stage, whole re-order cycles replayed from a CUDA graph; then
+    the same instances as 64 contexts stepped one after the other."""
+    ins = synth.ensemble(args.batch_instances)
+    g, F, ef, nf = synth.union(ins)
+    P = [dict(it["params"], precision=1, sort_every=args.sort_every) for it in ins]
+    ppe = [it["ppe"] for it in ins]
+    dt = 1e-4
+    cycle = 2 * args.sort_every
+    steps = max(cycle, (args.batch_steps // cycle) * cycle)
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    b = B.Context(P[0])
+    b.set_instances(P, ef)
+    b.set_grid(g)
+    b.set_fields(F)
+    b.init_particles_batch(ppe)
+    npart = b.np_
+    b.step_many(dt, cycle, use_graph=True)            # warm-up, includes the capture
+    l0 = b.kernel_launches
+    ms_b = timed(lambda: b.step_many(dt, steps, use_graph=True))
+    launches_b = b.kernel_launches - l0
+    err_b = b.check()
+    b.close()
+    del b
+    torch.cuda.empty_cache()
+
+    ctxs = []
+    for it, p in zip(ins, P):
+        c = B.Context(p)
+        c.set_grid(it["grid"])
+        c.set_fields(it["fields"])
+        c.init_particles(it["ppe"])
+        ctxs.append(c)
+    for c in ctxs:
+        c.step(dt)
+
+    def one_by_one():
+        for _ in range(steps):
+            for c in ctxs:
+                c.step(dt)
+
+    ms_1 = timed(one_by_one)
+    err_1 = max(c.check() for c in ctxs)
+    for c in ctxs:
+        c.close()
+    torch.cuda.empty_cache()
+    v_b = npart * steps / (ms_b * 1e-3)
+    v_1 = npart * steps / (ms_1 * 1e-3)
+    return {"value": v_b, "unit": UNIT, "ms_per_step": ms_b / steps, "steps": steps,
+            "instances": len(ins), "particles": npart, "triangles": int(g.ne),
+            "ppe_range": [min(ppe), max(ppe)], "dtype": "f32", "graph_cycle_steps": cycle,
+            "gpu_launches": launches_b, "device_errors": err_b,
+            "one_by_one": {"value": v_1, "ms_per_step": ms_1 / steps, "device_errors": err_1},
+            "speedup_vs_one_by_one": v_b / v_1}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -243,6 +312,9 @@ def main():
     ap.add_argument("--oracle-steps", type=int, default=2)
     ap.add_argument("--no-f64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--batch-instances", type=int, default=64)
+    ap.add_argument("--batch-steps", type=int, default=16)
     ap.add_argument("--ppe", type=int, default=None,
                     help="particles per element (default: the workload's own)")
     args = ap.parse_args()
@@ -270,6 +342,9 @@ def main():
     if not args.no_f64:
         c64, r64 = time_form(torch, B, w, 0, args, rank, world, dist, with_clock=False)
         c64.close()
+    rb = None
+    if not args.no_batch:
+        rb = batched_form(torch, B, synth, args)
     if dist is not None:
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -332,6 +407,10 @@ def main():
                                                                   "walk_brute", "lost", "wall_hits",
                                                                   "moves")}}
         line["speedup_f32_vs_f64"] = value / v64
+    if rb is not None:
+        line["batched_form"] = rb
+        if r64 is not None:
+            line["speedup_batched_vs_f64"] = rb["value"] / v64
     if not args.no_cpu:
         n, st, el, _ = oracle_sample(args.workload, args.oracle_steps, args.oracle_ppe)
         line["cpu_baseline"] = {"value": n * st / el, "unit": UNIT, "cores": 1, "kind": "oracle",
