@@ -174,6 +174,7 @@ def time_form(torch, B, w, precision, args, rank, world, dist, with_clock):
     for _ in range(args.warmup):
         c.step(w["dt"])
     torch.cuda.synchronize()
+    tuned = c.autotune(w["dt"]) if not args.no_autotune else None
     c.set_profiling(True)
     c.stage_times()
     l0 = c.kernel_launches
@@ -206,7 +207,8 @@ def time_form(torch, B, w, precision, args, rank, world, dist, with_clock):
     diag = c.diag()
     np_ = c.np_
     out = dict(ms=ms, launches=launches, stage_ms=stage_ms, stage_n=stage_n, np=np_, err=err,
-               diag=diag, clocks=sampler.summary() if sampler else None)
+               diag=diag, clocks=sampler.summary() if sampler else None, tuned=tuned,
+               nodal=c.nodal_stats())
     return c, out
 
 
@@ -231,6 +233,29 @@ def e2e_form(torch, B, c, w, args):
     return el, nn * 32 * 8, nn * 13 * 8
 
 
+STAT_NAMES = ["N", "U", "V", "W", "uu", "vv", "ww", "uv", "uw", "vw", "omega", "psi", "psi2"]
+
+
+def precision_study(n32, n64):
+    """Relative error per nodal statistic of the FP32 form against the FP64 form after the
+    same steps from the same seeds (floor: the column RMS; covariances also sqrt(<ii><jj>))."""
+    import numpy as np
+    pairs = {7: (4, 5), 8: (4, 6), 9: (5, 6)}
+    out = {}
+    for j, name in enumerate(STAT_NAMES):
+        if j == 0:
+            continue
+        b = n64[:, j]
+        rms = float(np.sqrt(np.mean(b * b))) or 1.0
+        den = np.maximum(np.abs(b), rms)
+        if j in pairs:
+            den = np.maximum(den, np.sqrt(np.abs(n64[:, pairs[j][0]] * n64[:, pairs[j][1]])))
+        r = np.abs(n32[:, j] - b) / den
+        out[name] = {"max": float(r.max()), "rms": float(np.sqrt(np.mean(r * r))),
+                     "p99": float(np.percentile(r, 99))}
+    return out
+
+
 def batched_form(torch, B, synth, args):
     """The ensemble of independent instances (64 channel grids of 1k-57k triangles at 50-500
     particles per element, about 287M particles, FP32 state): one context stepping all of
@@ -241,8 +266,6 @@ def batched_form(torch, B, synth, args):
     P = [dict(it["params"], precision=1, sort_every=args.sort_every) for it in ins]
     ppe = [it["ppe"] for it in ins]
     dt = 1e-4
-    cycle = 2 * args.sort_every
-    steps = max(cycle, (args.batch_steps // cycle) * cycle)
     stream = torch.cuda.current_stream()
 
     def timed(fn):
@@ -261,6 +284,10 @@ def batched_form(torch, B, synth, args):
     b.set_fields(F)
     b.init_particles_batch(ppe)
     npart = b.np_
+    b.step(dt)
+    tuned = b.autotune(dt) if not args.no_autotune else None
+    cycle = 2 * (tuned["sort_every"] if tuned else args.sort_every)
+    steps = max(cycle, (args.batch_steps // cycle) * cycle)
     b.step_many(dt, cycle, use_graph=True)            # warm-up, includes the capture
     l0 = b.kernel_launches
     ms_b = timed(lambda: b.step_many(dt, steps, use_graph=True))
@@ -295,7 +322,7 @@ def batched_form(torch, B, synth, args):
     return {"value": v_b, "unit": UNIT, "ms_per_step": ms_b / steps, "steps": steps,
             "instances": len(ins), "particles": npart, "triangles": int(g.ne),
             "ppe_range": [min(ppe), max(ppe)], "dtype": "f32", "graph_cycle_steps": cycle,
-            "gpu_launches": launches_b, "device_errors": err_b,
+            "gpu_launches": launches_b, "device_errors": err_b, "tuned": tuned,
             "one_by_one": {"value": v_1, "ms_per_step": ms_1 / steps, "device_errors": err_1},
             "speedup_vs_one_by_one": v_b / v_1}
 
@@ -313,6 +340,7 @@ def main():
     ap.add_argument("--no-f64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=16)
     ap.add_argument("--ppe", type=int, default=None,
@@ -375,7 +403,10 @@ def main():
                    "form": "FP32 state and SDE arithmetic, FP64 statistics",
                    "l2": "particle state (%.2f GB) larger than L2; grid and fields L2-resident"
                          % (np_ * 37 / 1e9),
-                   "sort_every": args.sort_every, "parallelism": "independent instance per GPU"},
+                   "sort_every": (r32["tuned"] or {}).get("sort_every", args.sort_every),
+                   "advance_block": (r32["tuned"] or {}).get("adv_block", 256),
+                   "autotuned": r32["tuned"] is not None,
+                   "parallelism": "independent instance per GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": traffic * np_ if traffic is not None else None,
@@ -407,6 +438,10 @@ def main():
                                                                   "walk_brute", "lost", "wall_hits",
                                                                   "moves")}}
         line["speedup_f32_vs_f64"] = value / v64
+        line["precision_study"] = {
+            "what": "nodal statistics of the FP32 form vs the FP64 form after the same %d steps "
+                    "from the same seeds (relative error, floor = column RMS)" % (args.warmup + args.steps),
+            "errors": precision_study(r32["nodal"], r64["nodal"])}
     if rb is not None:
         line["batched_form"] = rb
         if r64 is not None:

@@ -207,6 +207,15 @@ int  pdfx_step(void *ctx, double dt, void *stream);
  * Capture runs on a stream of the library's own; the graph is launched on stream. */
 int  pdfx_step_many(void *ctx, double dt, int32_t nsteps, int use_graph, void *stream);
 
+/* Picks the launch shapes that do not change any result: the advance kernel's block size
+ * (128 or 256 threads) and the re-order period sort_every (4, 8 or 16 steps; results do
+ * not depend on the slots' order).  Each candidate runs one re-order cycle of dt steps from
+ * a snapshot of the current state, which is restored afterwards (particles, statistics,
+ * step counter and diagnostics as before the call).  Writes the choice to adv_block and
+ * sort_every where not NULL.  Needs temporary device memory of one particle buffer plus
+ * the statistics.  Synchronous on stream. */
+int  pdfx_autotune(void *ctx, double dt, int32_t *adv_block, int32_t *sort_every, void *stream);
+
 /* Nodal statistics [nn][13] and element statistics [ne][13] with counts [ne] of the last
  * step (or initialisation), into host or device memory.  Synchronous for host output. */
 int  pdfx_get_nodal_stats(void *ctx, double *out, int on_device, void *stream);

@@ -95,6 +95,7 @@ def lib():
                 "pdfx_step": (C.c_int, [vp, dp, vp]),
                 "pdfx_set_instances": (C.c_int, [vp, i32, C.POINTER(Params), vp]),
                 "pdfx_step_many": (C.c_int, [vp, dp, i32, C.c_int, vp]),
+                "pdfx_autotune": (C.c_int, [vp, dp, vp, vp, vp]),
                 "pdfx_instance_ranges": (C.c_int, [vp, vp, vp]),
                 "pdfx_init_particles_batch": (C.c_int, [vp, vp, vp]),
                 "pdfx_get_nodal_stats": (C.c_int, [vp, vp, C.c_int, vp]),
@@ -284,6 +285,12 @@ class Context:
 
     def step(self, dt: float, stream=None):
         self._check(lib().pdfx_step(self.h, float(dt), _stream(stream)), "pdfx_step")
+
+    def autotune(self, dt: float, stream=None) -> dict:
+        blk, se = C.c_int32(0), C.c_int32(0)
+        self._check(lib().pdfx_autotune(self.h, float(dt), C.byref(blk), C.byref(se),
+                                        _stream(stream)), "pdfx_autotune")
+        return {"adv_block": int(blk.value), "sort_every": int(se.value)}
 
     def step_many(self, dt: float, nsteps: int, use_graph: bool = True, stream=None):
         self._check(lib().pdfx_step_many(self.h, float(dt), int(nsteps), int(bool(use_graph)),

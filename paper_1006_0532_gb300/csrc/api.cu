@@ -358,7 +358,7 @@ int do_step(Ctx& c, double dt, cudaStream_t s) {
     a.k1 = key1(c.prm);
     a.inst = c.K > 1 ? static_cast<const InstDev<T>*>(c.inst) : nullptr;
     a.einst = c.K > 1 ? c.einst : nullptr;
-    launch_advance<T>(a, c.num_sms, s);
+    launch_advance<T>(a, c.num_sms, c.adv_block, s);
     c.launches++;
   }
   PDFX_TRY(run_statistics<T>(c, true, true, false, s));
@@ -745,6 +745,98 @@ int do_step_many(Ctx& c, double dt, int32_t nsteps, int use_graph, cudaStream_t 
   return cerr(cudaGetLastError());
 }
 
+// Launch shapes that leave every result unchanged: the advance kernel's block size (each
+// particle is independent) and the re-order period (no result depends on the slots'
+// order: every ordering decision of the method goes through particle ids).  Each candidate
+// runs one re-order cycle from the same snapshot of the state; the state, counters and
+// diagnostics are restored afterwards.
+template <typename T>
+int do_autotune(Ctx& c, double dt, cudaStream_t s, int32_t* best_block, int32_t* best_se) {
+  const size_t pb = c.pbuf_bytes;
+  const size_t vb = sizeof(double) * static_cast<size_t>(c.ne) * c.G;
+  const size_t eb = sizeof(double) * static_cast<size_t>(c.ne) * kNS;
+  const size_t nb = sizeof(double) * static_cast<size_t>(c.nn) * kNS;
+  const size_t gb = sizeof(int32_t) * static_cast<size_t>(c.ne) * 3;
+  const size_t db = sizeof(unsigned long long) * kDiagCount;
+  const size_t rb = sizeof(double) * 4 * kLostRecords;
+  unsigned char* snap = static_cast<unsigned char*>(dev_alloc(c, pb + vb + eb + nb + gb + db + rb + 16));
+  if (!snap) return PDFX_ERR_ALLOC;
+  struct Piece { void* dev; size_t bytes; };
+  const Piece pieces[] = {{c.pbuf[c.cur], pb}, {c.vcce, vb}, {c.emom, eb}, {c.nmom, nb},
+                          {c.gbin, gb}, {c.diag, db}, {c.lost_rec, rb}, {c.err, 16}};
+  size_t off = 0;
+  for (const Piece& q : pieces) {
+    PDFX_CUDA(cudaMemcpyAsync(snap + off, q.dev, q.bytes, cudaMemcpyDeviceToDevice, s));
+    off += q.bytes;
+  }
+  const int cur0 = c.cur, since0 = c.steps_since_sort, block0 = c.adv_block;
+  const int se0 = c.prm.sort_every;
+  const uint32_t step0 = c.step;
+  const int64_t done0 = c.steps_done, launches0 = c.launches;
+  const bool prof0 = c.profiling;
+  c.profiling = false;
+  auto restore = [&]() -> int {
+    c.cur = cur0;
+    size_t o = 0;
+    const Piece back[] = {{c.pbuf[cur0], pb}, {c.vcce, vb}, {c.emom, eb}, {c.nmom, nb},
+                          {c.gbin, gb}, {c.diag, db}, {c.lost_rec, rb}, {c.err, 16}};
+    for (const Piece& q : back) {
+      PDFX_CUDA(cudaMemcpyAsync(q.dev, snap + o, q.bytes, cudaMemcpyDeviceToDevice, s));
+      o += q.bytes;
+    }
+    c.steps_since_sort = since0;
+    c.step = step0;
+    c.steps_done = done0;
+    c.launches = launches0;
+    PDFX_CUDA(cudaMemcpyAsync(c.dstep, &step0, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    return cerr(cudaStreamSynchronize(s));
+  };
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) {
+    dev_free(c, snap);
+    return PDFX_ERR_CUDA;
+  }
+  const int blocks[] = {128, 256};
+  const int periods[] = {4, 8, 16};
+  double best = 1e300;
+  int bb = block0, bs = se0;
+  int rc = PDFX_OK;
+  for (int blk : blocks) {
+    for (int se : periods) {
+      if (rc != PDFX_OK) break;
+      rc = restore();
+      if (rc != PDFX_OK) break;
+      c.adv_block = blk;
+      c.prm.sort_every = se;
+      rc = do_step<T>(c, dt, s);                    // warm-up
+      const int n = 2 * se;
+      if (rc == PDFX_OK) rc = cerr(cudaEventRecord(e0, s));
+      for (int k = 0; k < n && rc == PDFX_OK; ++k) rc = do_step<T>(c, dt, s);
+      if (rc == PDFX_OK) rc = cerr(cudaEventRecord(e1, s));
+      if (rc == PDFX_OK) rc = cerr(cudaEventSynchronize(e1));
+      float ms = 0.0f;
+      if (rc == PDFX_OK) rc = cerr(cudaEventElapsedTime(&ms, e0, e1));
+      if (rc == PDFX_OK && ms / n < best) { best = ms / n; bb = blk; bs = se; }
+    }
+  }
+  const int rr = restore();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  dev_free(c, snap);
+  c.profiling = prof0;
+  if (rc != PDFX_OK || rr != PDFX_OK) {
+    c.adv_block = block0;
+    c.prm.sort_every = se0;
+    return rc != PDFX_OK ? rc : rr;
+  }
+  c.adv_block = bb;
+  c.prm.sort_every = bs;
+  drop_graph(c);
+  if (best_block) *best_block = bb;
+  if (best_se) *best_se = bs;
+  return PDFX_OK;
+}
+
 Ctx* as_ctx(void* p) { return static_cast<Ctx*>(p); }
 
 }  // namespace
@@ -986,6 +1078,14 @@ int pdfx_step_many(void* ctx, double dt, int32_t nsteps, int use_graph, void* st
   if (!c->pbuf[0] || !c->have_fields) return PDFX_ERR_ORDER;
   return c->prm.precision == 1 ? do_step_many<float>(*c, dt, nsteps, use_graph, as_stream(stream))
                                : do_step_many<double>(*c, dt, nsteps, use_graph, as_stream(stream));
+}
+
+int pdfx_autotune(void* ctx, double dt, int32_t* adv_block, int32_t* sort_every, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !(dt > 0.0)) return PDFX_ERR_ARG;
+  if (!c->pbuf[0] || !c->have_fields || c->np <= 0) return PDFX_ERR_ORDER;
+  return c->prm.precision == 1 ? do_autotune<float>(*c, dt, as_stream(stream), adv_block, sort_every)
+                               : do_autotune<double>(*c, dt, as_stream(stream), adv_block, sort_every);
 }
 
 int pdfx_step(void* ctx, double dt, void* stream) {

@@ -521,15 +521,15 @@ inline unsigned blocks_for(int64_t n, int threads) {
 }  // namespace
 
 template <typename T>
-void launch_advance(const AdvanceArgs<T>& a, int num_sms, cudaStream_t s) {
+void launch_advance(const AdvanceArgs<T>& a, int num_sms, int block, cudaStream_t s) {
   if (a.np <= 0) return;
   cudaMemsetAsync(a.brute_count, 0, sizeof(int), s);
   const unsigned bgrid = static_cast<unsigned>(num_sms > 0 ? num_sms : 1);
   if (a.einst) {
-    advance_kernel<T, true><<<blocks_for(a.np, 256), 256, 0, s>>>(a);
+    advance_kernel<T, true><<<blocks_for(a.np, block), block, 0, s>>>(a);
     brute_search_kernel<T, true><<<bgrid, 256, 0, s>>>(a);
   } else {
-    advance_kernel<T, false><<<blocks_for(a.np, 256), 256, 0, s>>>(a);
+    advance_kernel<T, false><<<blocks_for(a.np, block), block, 0, s>>>(a);
     brute_search_kernel<T, false><<<bgrid, 256, 0, s>>>(a);
   }
 }
@@ -581,7 +581,7 @@ void launch_convert_fields(const double* in, float* out, int64_t n, cudaStream_t
 }
 
 #define PDFX_INSTANTIATE(T)                                                                    \
-  template void launch_advance<T>(const AdvanceArgs<T>&, int, cudaStream_t);                   \
+  template void launch_advance<T>(const AdvanceArgs<T>&, int, int, cudaStream_t);              \
   template void launch_init<T>(Particles<T>, int32_t, int32_t, const ElemGeo<T>*,              \
                                const ElemTopo*, const T*, Model<T>, uint32_t, uint32_t,        \
                                unsigned long long*, cudaStream_t);                             \

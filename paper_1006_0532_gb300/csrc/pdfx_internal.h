@@ -178,6 +178,8 @@ struct Ctx {
   const void* g_buf = nullptr;
   int64_t g_np = -1;
   int64_t g_launches = 0;
+  // launch shapes (pdfx_autotune)
+  int adv_block = 256;
   // instances of a batch (K = 1: the whole grid)
   int K = 1;
   std::vector<pdfx_params> iprm;        // [K] parameters (K > 1 only)
@@ -221,7 +223,7 @@ Particles<T> particles_of(Ctx& c, int which);
 
 // Kernel launchers (defined in the .cu files).
 template <typename T>
-void launch_advance(const AdvanceArgs<T>& a, int num_sms, cudaStream_t s);
+void launch_advance(const AdvanceArgs<T>& a, int num_sms, int block, cudaStream_t s);   // block <= 256
 template <typename T>
 void launch_init(Particles<T> p, int32_t ne, int32_t ppe, const ElemGeo<T>* geo,
                  const ElemTopo* topo, const T* fields, Model<T> m, uint32_t k0, uint32_t k1,

@@ -147,3 +147,29 @@ def test_batch_graph_equals_instances_run_alone():
         sl = slice(int(pf[k]), int(pf[k + 1]))
         for key in STATE_KEYS:
             assert np.array_equal(sb[key][sl], sa[key]), key
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_autotune_changes_no_result(precision):
+    """The tuned launch shapes (advance block size, re-order period) leave every result as
+    it was, and tuning leaves the state where it found it."""
+    it = _instances()[2]
+    a = _single(it, precision, 8)
+    b = _single(it, precision, 8)
+    dt = 2e-3
+    for c in (a, b):
+        c.step(dt)
+    x_before = b.get_particles()["x"]
+    tuned = b.autotune(dt)
+    assert tuned["adv_block"] in (128, 256) and tuned["sort_every"] in (4, 8, 16)
+    assert b.step_index == a.step_index
+    assert np.array_equal(b.get_particles()["x"], x_before)
+    assert b.diag()["steps"] == a.diag()["steps"]
+    for _ in range(10):
+        a.step(dt)
+    b.step_many(dt, 10, use_graph=True)
+    sa, sb = a.get_particles(), b.get_particles()
+    for key in STATE_KEYS + ("elem", "cp"):
+        assert np.array_equal(sa[key], sb[key]), key
+    assert np.array_equal(a.nodal_stats(), b.nodal_stats())
+    assert a.diag()["moves"] == b.diag()["moves"]
