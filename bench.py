@@ -256,6 +256,41 @@ def precision_study(n32, n64):
     return out
 
 
+def canyon_form(torch, B, synth, args):
+    """The street canyon (cavity [1.5, 2.5] x [0, 1] under a periodic channel [0, 4] x
+    [1, 2], 200,000 triangles graded to the walls and cavity corners, 100 particles per
+    element, FP32 state): autotuned, whole re-order cycles replayed from a CUDA graph."""
+    w = synth.canyon_workload("canyon_200k")
+    c = B.Context(dict(w["params"], precision=1, sort_every=args.sort_every))
+    c.set_grid(w["grid"])
+    c.set_fields(w["fields"])
+    c.init_particles(w["ppe"])
+    dt = w["dt"]
+    c.step(dt)
+    tuned = c.autotune(dt) if not args.no_autotune else None
+    cycle = 2 * (tuned["sort_every"] if tuned else args.sort_every)
+    steps = max(cycle, (args.steps // cycle) * cycle)
+    c.step_many(dt, cycle, use_graph=True)
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    c.step_many(dt, steps, use_graph=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    npart = c.np_
+    d = c.diag()
+    out = {"value": npart * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
+           "steps": steps, "particles": npart, "triangles": int(w["grid"].ne), "ppe": w["ppe"],
+           "dtype": "f32", "tuned": tuned, "device_errors": c.check(),
+           "diag": {k: d[k] for k in ("wall_hits", "freeslip_hits", "moves", "lost", "walk_brute")}}
+    c.close()
+    torch.cuda.empty_cache()
+    return out
+
+
 def batched_form(torch, B, synth, args):
     """The ensemble of independent instances (64 channel grids of 1k-57k triangles at 50-500
     particles per element, about 287M particles, FP32 state): one context stepping all of
@@ -340,6 +375,7 @@ def main():
     ap.add_argument("--no-f64", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-batch", action="store_true")
+    ap.add_argument("--no-canyon", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=16)
@@ -373,6 +409,9 @@ def main():
     rb = None
     if not args.no_batch:
         rb = batched_form(torch, B, synth, args)
+    rc = None
+    if not args.no_canyon:
+        rc = canyon_form(torch, B, synth, args)
     if dist is not None:
         t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -442,6 +481,8 @@ def main():
             "what": "nodal statistics of the FP32 form vs the FP64 form after the same %d steps "
                     "from the same seeds (relative error, floor = column RMS)" % (args.warmup + args.steps),
             "errors": precision_study(r32["nodal"], r64["nodal"])}
+    if rc is not None:
+        line["street_canyon"] = rc
     if rb is not None:
         line["batched_form"] = rb
         if r64 is not None:

@@ -51,9 +51,9 @@ struct orc_ctx {
     double *ax, *ay, *bx, *by, *cx, *cy, *area2;
     int32_t *nbr;         /* [ne][3]: neighbour across the edge opposite vertex k, -1 outside */
     int32_t *ne_off, *ne_list;   /* node -> elements (ascending element id) */
-    /* wall lines: point, inward unit normal (in element frame); type 0 none */
-    int8_t *wall_type;    /* 0 none, 1 no-slip */
-    double *wall_px, *wall_py, *wall_nx, *wall_ny;
+    /* boundary lines: point, inward unit normal (in element frame) */
+    int8_t *wall_type;    /* number of no-slip lines of the element (0, 1 or 2) */
+    double *wall_px, *wall_py, *wall_nx, *wall_ny;   /* [ne][2] */
     int8_t *fs_type;      /* 0 none, 2 free-slip */
     double *fs_px, *fs_py, *fs_nx, *fs_ny;
     double *fields;       /* [nn][32] */
@@ -149,8 +149,10 @@ double orc_gamma_draw(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t s
 
 /* Sect. 3.9: the six Gaussians of one particle step and the uniform eta of Eq. 55.
  * Block 0 -> (xi1, xi2), (xi3, xi4); block 1 -> (xi5, xi6) and eta from word 2. */
-void orc_step_gaussians(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t step,
-                        double xi[6], double *eta)
+/* The step's draws: six Gaussians, eta (word 2 of block 1) for the first wall line of the
+ * element and eta2 (word 3) for a second one. */
+static void step_draws(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t step,
+                       double xi[6], double *eta, double *eta2)
 {
     uint32_t r0[4], r1[4];
     philox_draw(seed, instance, pid, step, PUR_STEP, 0, r0);
@@ -159,6 +161,14 @@ void orc_step_gaussians(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t
     orc_box_muller(r0[2], r0[3], &xi[2], &xi[3]);
     orc_box_muller(r1[0], r1[1], &xi[4], &xi[5]);
     *eta = orc_uniform(r1[2]);
+    *eta2 = orc_uniform(r1[3]);
+}
+
+void orc_step_gaussians(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t step,
+                        double xi[6], double *eta)
+{
+    double eta2;
+    step_draws(seed, instance, pid, step, xi, eta, &eta2);
 }
 
 /* ------------------------------------------------------------------------------------ */
@@ -191,36 +201,61 @@ static void edge_line(const orc_ctx *c, int f, int k, double *px, double *py, do
     *px = vx[a]; *py = vy[a]; *nx = mx; *ny = my;
 }
 
-/* Reading of Sect. 3.8 (last paragraph): an element with an edge on a wall uses that
- * edge's line; an element with only a node on a wall uses the line of the first wall
- * edge (lowest element id, then lowest local edge) incident to that node. */
-static void find_boundary_line(orc_ctx *c, int e, int type, int8_t *out_type,
+/* Reading of Sect. 3.8 (last paragraph), extended to corners: an element's boundary lines
+ * of a type are, in this order, its own edges of that type (local edge order), then the
+ * edges of that type incident to one of its nodes (nodes in local order, elements in
+ * ascending id, edges in local order) whose line, oriented into the fluid by the edge's
+ * own element, has the element's centroid strictly in front; a line equal to one already
+ * taken is skipped; at most max_lines lines.  Returns the number found; line j is written
+ * to px[j], py[j] (in e's frame), nx[j], ny[j]. */
+static int same_line(double px, double py, double nx, double ny,
+                     double qx, double qy, double mx, double my)
+{
+    if (nx * mx + ny * my < 1.0 - 1e-9) return 0;
+    double d = (qx - px) * nx + (qy - py) * ny;
+    return fabs(d) <= 1e-9 * (1.0 + fabs(px) + fabs(py));
+}
+
+static int find_boundary_lines(orc_ctx *c, int e, int type, int max_lines,
                                double *px, double *py, double *nx, double *ny)
 {
-    *out_type = 0;
-    for (int k = 0; k < 3; ++k)
-        if (c->tag[3 * e + k] == type) {
-            edge_line(c, e, k, px, py, nx, ny);
-            *out_type = (int8_t)type;
-            return;
-        }
-    for (int kv = 0; kv < 3; ++kv) {
+    int n_found = 0;
+    for (int k = 0; k < 3 && n_found < max_lines; ++k) {
+        if (c->tag[3 * e + k] != type) continue;
+        double qx, qy, mx, my;
+        edge_line(c, e, k, &qx, &qy, &mx, &my);
+        int dup = 0;
+        for (int j = 0; j < n_found; ++j)
+            dup |= same_line(px[j], py[j], nx[j], ny[j], qx, qy, mx, my);
+        if (dup) continue;
+        px[n_found] = qx; py[n_found] = qy; nx[n_found] = mx; ny[n_found] = my;
+        ++n_found;
+    }
+    /* centroid in e's frame (b, c are offsets from vertex A) */
+    const double gx = c->ax[e] + (c->bx[e] + c->cx[e]) / 3.0;
+    const double gy = c->ay[e] + (c->by[e] + c->cy[e]) / 3.0;
+    for (int kv = 0; kv < 3 && n_found < max_lines; ++kv) {
         int n = c->tri[3 * e + kv];
-        for (int i = c->ne_off[n]; i < c->ne_off[n + 1]; ++i) {
+        for (int i = c->ne_off[n]; i < c->ne_off[n + 1] && n_found < max_lines; ++i) {
             int f = c->ne_list[i];
-            for (int k = 0; k < 3; ++k) {
+            for (int k = 0; k < 3 && n_found < max_lines; ++k) {
                 if (c->tag[3 * f + k] != type) continue;
                 int a = c->tri[3 * f + (k + 1) % 3], b = c->tri[3 * f + (k + 2) % 3];
                 if (a != n && b != n) continue;
-                double qx;
-                edge_line(c, f, k, &qx, py, nx, ny);
-                /* move the point into e's frame */
-                *px = c->ax[e] + min_image(qx - c->ax[e], c->p.period_x);
-                *out_type = (int8_t)type;
-                return;
+                double qx, qy, mx, my;
+                edge_line(c, f, k, &qx, &qy, &mx, &my);
+                qx = c->ax[e] + min_image(qx - c->ax[e], c->p.period_x);   /* e's frame */
+                if ((gx - qx) * mx + (gy - qy) * my <= 0.0) continue;       /* not in front */
+                int dup = 0;
+                for (int j = 0; j < n_found; ++j)
+                    dup |= same_line(px[j], py[j], nx[j], ny[j], qx, qy, mx, my);
+                if (dup) continue;
+                px[n_found] = qx; py[n_found] = qy; nx[n_found] = mx; ny[n_found] = my;
+                ++n_found;
             }
         }
     }
+    return n_found;
 }
 
 static int params_valid(const orc_params *p)
@@ -305,14 +340,16 @@ int orc_create(orc_ctx **out, const orc_params *p, int nn, const double *node_xy
         }
     c->wall_type = (int8_t *)calloc(ne, 1);
     c->fs_type = (int8_t *)calloc(ne, 1);
-    double **wl[8] = {&c->wall_px, &c->wall_py, &c->wall_nx, &c->wall_ny,
-                      &c->fs_px, &c->fs_py, &c->fs_nx, &c->fs_ny};
-    for (int i = 0; i < 8; ++i) *wl[i] = (double *)calloc(ne, sizeof(double));
+    double **wl[4] = {&c->wall_px, &c->wall_py, &c->wall_nx, &c->wall_ny};
+    for (int i = 0; i < 4; ++i) *wl[i] = (double *)calloc(2 * (size_t)ne, sizeof(double));
+    double **fl[4] = {&c->fs_px, &c->fs_py, &c->fs_nx, &c->fs_ny};
+    for (int i = 0; i < 4; ++i) *fl[i] = (double *)calloc(ne, sizeof(double));
     for (int e = 0; e < ne; ++e) {
-        find_boundary_line(c, e, 1, &c->wall_type[e], &c->wall_px[e], &c->wall_py[e],
-                           &c->wall_nx[e], &c->wall_ny[e]);
-        find_boundary_line(c, e, 2, &c->fs_type[e], &c->fs_px[e], &c->fs_py[e],
-                           &c->fs_nx[e], &c->fs_ny[e]);
+        c->wall_type[e] = (int8_t)find_boundary_lines(c, e, 1, 2, c->wall_px + 2 * e,
+                                                       c->wall_py + 2 * e, c->wall_nx + 2 * e,
+                                                       c->wall_ny + 2 * e);
+        c->fs_type[e] = (int8_t)(2 * find_boundary_lines(c, e, 2, 1, c->fs_px + e, c->fs_py + e,
+                                                          c->fs_nx + e, c->fs_ny + e));
     }
     c->fields = (double *)calloc((size_t)nn * NF, sizeof(double));
     c->count = (int32_t *)calloc(ne, sizeof(int32_t));
@@ -560,8 +597,8 @@ static void advance_particle(orc_ctx *c, int p, double dt)
     }
 
     /* Sect. 3.9 draws */
-    double xi[6], eta;
-    orc_step_gaussians(P->seed, P->instance, (uint32_t)p, c->step, xi, &eta);
+    double xi[6], eta, eta2;
+    step_draws(P->seed, P->instance, (uint32_t)p, c->step, xi, &eta, &eta2);
     const double sdt = sqrt(dt);
     const double dWx = sdt * xi[0], dWy = sdt * xi[1];
     const double dWp[3] = {sdt * xi[2], sdt * xi[3], sdt * xi[4]};
@@ -596,12 +633,16 @@ static void advance_particle(orc_ctx *c, int p, double dt)
     double phic = c->vcce[(size_t)e * c->G + c->cp[p]];
     double psin = psi0 - (psi0 - phic) * dt / tm;
 
-    /* Sect. 3.8, Eqs. 53-58, only in elements touching a wall (Reading: distances to the
-     * element's wall line; reflect only when behind the wall; psi is not changed). */
-    if (c->wall_type[e] == 1) {
-        double nx = c->wall_nx[e], ny = c->wall_ny[e];
-        double d0 = min_image(X0 - c->wall_px[e], P->period_x) * nx + (Y0 - c->wall_py[e]) * ny;
-        double d1 = min_image(Xn - c->wall_px[e], P->period_x) * nx + (Yn - c->wall_py[e]) * ny;
+    /* Sect. 3.8, Eqs. 53-58, only in elements touching a wall (Reading: distances to each of
+     * the element's wall lines in turn, the second from the position after the first's
+     * reflection, with its own uniform; reflect only when behind a line; a hit on either
+     * sets U = 0 and draws omega once; psi is not changed). */
+    int any_hit = 0;
+    for (int j = 0; j < c->wall_type[e]; ++j) {
+        const double nx = c->wall_nx[2 * e + j], ny = c->wall_ny[2 * e + j];
+        const double lx = c->wall_px[2 * e + j], ly = c->wall_py[2 * e + j];
+        double d0 = min_image(X0 - lx, P->period_x) * nx + (Y0 - ly) * ny;
+        double d1 = min_image(Xn - lx, P->period_x) * nx + (Yn - ly) * ny;
         int hit = 0;
         if (d1 < 0.0) {
             hit = 1;
@@ -609,18 +650,21 @@ static void advance_particle(orc_ctx *c, int p, double dt)
         } else {
             double dd0 = d0 > 0.0 ? d0 : 0.0;
             double fw = exp(-dd0 * d1 / (P->nu * dt));
-            if (eta < fw) hit = 1;
+            if ((j == 0 ? eta : eta2) < fw) hit = 1;
         }
         if (hit) {
-            c->diag.wall_hits++;
+            any_hit = 1;
             if (d1 < 0.0) { Xn -= 2.0 * d1 * nx; Yn -= 2.0 * d1 * ny; }
-            Un[0] = Un[1] = Un[2] = 0.0;                         /* Eq. 56 */
-            int ex = 0;
-            double shape = 1.0 / P->C4;                           /* Eq. 58 */
-            wn = orc_gamma_draw(P->seed, P->instance, (uint32_t)p, c->step, PUR_WALL_GAMMA,
-                                shape, P->C4 * om_w, &ex);
-            if (ex) c->diag.gamma_exhausted++;
         }
+    }
+    if (any_hit) {
+        c->diag.wall_hits++;
+        Un[0] = Un[1] = Un[2] = 0.0;                             /* Eq. 56 */
+        int ex = 0;
+        double shape = 1.0 / P->C4;                               /* Eq. 58 */
+        wn = orc_gamma_draw(P->seed, P->instance, (uint32_t)p, c->step, PUR_WALL_GAMMA,
+                            shape, P->C4 * om_w, &ex);
+        if (ex) c->diag.gamma_exhausted++;
     }
     /* Free-slip boundary (Sect. 4.2): perfect reflection, normal velocity reversed. */
     if (c->fs_type[e] == 2) {

@@ -336,6 +336,7 @@ int do_step(Ctx& c, double dt, cudaStream_t s) {
     a.geo = static_cast<const ElemGeo<T>*>(c.geo);
     a.topo = c.topo;
     a.walls = static_cast<const Line<T>*>(c.walls);
+    a.wall2 = c.wall2;
     a.fslines = static_cast<const Line<T>*>(c.fslines);
     a.ne_off = c.ne_off;
     a.ne_list = c.ne_list;
@@ -582,38 +583,66 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
         o = hinst[e];
       }
   }
-  // boundary lines (Sect. 3.8 reading): own tagged edge first, else the first tagged edge
-  // (lowest element id, lowest local edge) touching one of the element's nodes
+  // boundary lines (Sect. 3.8 reading, extended to corners): the element's own edges of the
+  // type (local order), then edges of the type incident to one of its nodes (nodes in local
+  // order, elements ascending, edges in local order) whose line, oriented into the fluid by
+  // the edge's own element, has the element's centroid strictly in front; lines equal to
+  // one already taken are skipped; at most two no-slip lines and one free-slip line
   std::vector<ElemTopo> topo(static_cast<size_t>(ne));
   std::vector<double> walls, fsl;
+  std::vector<int32_t> wall2(static_cast<size_t>(ne), -1);
+  auto same_line = [](const double* p, const double* q) {
+    if (p[2] * q[2] + p[3] * q[3] < 1.0 - 1e-9) return false;
+    const double d = (q[0] - p[0]) * p[2] + (q[1] - p[1]) * p[3];
+    return std::fabs(d) <= 1e-9 * (1.0 + std::fabs(p[0]) + std::fabs(p[1]));
+  };
   for (int32_t e = 0; e < ne; ++e) {
     ElemTopo& t = topo[e];
     t.n0 = tri[3 * e]; t.n1 = tri[3 * e + 1]; t.n2 = tri[3 * e + 2];
     t.nb0 = nbr[3 * e]; t.nb1 = nbr[3 * e + 1]; t.nb2 = nbr[3 * e + 2];
     t.wall = -1;
     t.fslip = -1;
+    const double gx = (g.vx[3 * e] + g.vx[3 * e + 1] + g.vx[3 * e + 2]) / 3.0;
+    const double gy = (g.vy[3 * e] + g.vy[3 * e + 1] + g.vy[3 * e + 2]) / 3.0;
     for (int type = 1; type <= 2; ++type) {
-      double line[4];
-      bool found = false;
-      for (int k = 0; k < 3 && !found; ++k)
-        if (tag[3 * e + k] == type) { edge_line_h(g, e, k, line); found = true; }
-      for (int kv = 0; kv < 3 && !found; ++kv) {
+      const int max_lines = type == 1 ? 2 : 1;
+      double found[2][4];
+      int nf = 0;
+      auto take = [&](const double* line) {
+        for (int j = 0; j < nf; ++j)
+          if (same_line(found[j], line)) return;
+        for (int q = 0; q < 4; ++q) found[nf][q] = line[q];
+        ++nf;
+      };
+      for (int k = 0; k < 3 && nf < max_lines; ++k)
+        if (tag[3 * e + k] == type) {
+          double line[4];
+          edge_line_h(g, e, k, line);
+          take(line);
+        }
+      for (int kv = 0; kv < 3 && nf < max_lines; ++kv) {
         const int n = tri[3 * e + kv];
-        for (int32_t i = off[n]; i < off[n + 1] && !found; ++i) {
+        for (int32_t i = off[n]; i < off[n + 1] && nf < max_lines; ++i) {
           const int f = lst[i];
-          for (int k = 0; k < 3 && !found; ++k) {
+          for (int k = 0; k < 3 && nf < max_lines; ++k) {
             if (tag[3 * f + k] != type) continue;
             if (tri[3 * f + (k + 1) % 3] != n && tri[3 * f + (k + 2) % 3] != n) continue;
+            double line[4];
             edge_line_h(g, f, k, line);
             line[0] = g.ax[e] + min_image_h(line[0] - g.ax[e], period_of(e));
-            found = true;
+            if ((gx - line[0]) * line[2] + (gy - line[1]) * line[3] <= 0.0) continue;
+            take(line);
           }
         }
       }
-      if (!found) continue;
       std::vector<double>& dst = type == 1 ? walls : fsl;
-      (type == 1 ? t.wall : t.fslip) = static_cast<int>(dst.size() / 4);
-      dst.insert(dst.end(), line, line + 4);
+      for (int j = 0; j < nf; ++j) {
+        const int idx = static_cast<int>(dst.size() / 4);
+        if (type == 2) t.fslip = idx;
+        else if (j == 0) t.wall = idx;
+        else wall2[e] = idx;
+        dst.insert(dst.end(), found[j], found[j] + 4);
+      }
     }
   }
   c.nn = nn;
@@ -621,6 +650,8 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
   int rc = c.prm.precision == 1 ? upload_grid<float>(c, g, topo, walls, fsl)
                                 : upload_grid<double>(c, g, topo, walls, fsl);
   if (rc) return rc;
+  PDFX_TRY(alloc_into(c, c.wall2, wall2.size()));
+  PDFX_CUDA(cudaMemcpy(c.wall2, wall2.data(), sizeof(int32_t) * wall2.size(), cudaMemcpyHostToDevice));
   PDFX_TRY(alloc_into(c, c.ne_off, off.size()));
   PDFX_TRY(alloc_into(c, c.ne_list, lst.size()));
   PDFX_CUDA(cudaMemcpy(c.ne_off, off.data(), sizeof(int32_t) * off.size(), cudaMemcpyHostToDevice));

@@ -195,7 +195,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
     box_muller(r0.x, r0.y, xi[0], xi[1]);
     box_muller(r0.z, r0.w, xi[2], xi[3]);
     box_muller(r1.x, r1.y, xi[4], xi[5]);
-    const T eta = uniform01(r1.z, T(0));
+    const T eta = uniform01(r1.z, T(0));     // first wall line
+    const T eta2 = uniform01(r1.w, T(0));    // second wall line (a corner element)
     const T dt = a.dt;
     const T sdt = a.sdt;
     const T dWx = sdt * xi[0], dWy = sdt * xi[1];
@@ -229,21 +230,31 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
     const T phic = static_cast<T>(a.vcce[(size_t)e * a.G + cpi]);
     T psin = psi0 - (psi0 - phic) * dt * itm;
 
-    // Sect. 3.8: wall elements only
+    // Sect. 3.8: wall elements only; each wall line in turn (a corner element has two),
+    // the second from the position after the first's reflection
     if (tp.wall >= 0) {
-      const Line<T> ln = a.walls[tp.wall];
-      const T d0 = min_image(X0 - ln.px, L) * ln.nx + (Y0 - ln.py) * ln.ny;
-      const T d1 = min_image(Xn - ln.px, L) * ln.nx + (Yn - ln.py) * ln.ny;
-      bool hit;
-      if (d1 < T(0)) {
-        hit = true;
-      } else {
-        const T dd0 = d0 > T(0) ? d0 : T(0);
-        hit = eta < texp(-dd0 * d1 / (M.nu * dt));   // Eqs. 53, 55
+      const int lines[2] = {tp.wall, a.wall2[e]};
+      bool any_hit = false;
+#pragma unroll
+      for (int j = 0; j < 2; ++j) {
+        if (lines[j] < 0) break;
+        const Line<T> ln = a.walls[lines[j]];
+        const T d0 = min_image(X0 - ln.px, L) * ln.nx + (Y0 - ln.py) * ln.ny;
+        const T d1 = min_image(Xn - ln.px, L) * ln.nx + (Yn - ln.py) * ln.ny;
+        bool hit;
+        if (d1 < T(0)) {
+          hit = true;
+        } else {
+          const T dd0 = d0 > T(0) ? d0 : T(0);
+          hit = (j == 0 ? eta : eta2) < texp(-dd0 * d1 / (M.nu * dt));   // Eqs. 53, 55
+        }
+        if (hit) {
+          any_hit = true;
+          if (d1 < T(0)) { Xn -= T(2) * d1 * ln.nx; Yn -= T(2) * d1 * ln.ny; }
+        }
       }
-      if (hit) {
+      if (any_hit) {
         c_wall = 1;
-        if (d1 < T(0)) { Xn -= T(2) * d1 * ln.nx; Yn -= T(2) * d1 * ln.ny; }
         Un[0] = Un[1] = Un[2] = T(0);                  // Eq. 56
         int ex = 0;                                    // Eq. 58
         wn = gamma_draw<T>(k0, k1, pid, step, kPurWallGamma, T(1) / M.C4, M.C4 * q[30], &ex);

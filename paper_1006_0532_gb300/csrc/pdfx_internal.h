@@ -50,6 +50,7 @@ struct AdvanceArgs {
   const ElemGeo<T>* geo;
   const ElemTopo* topo;
   const Line<T>* walls;
+  const int32_t* wall2;    // [ne] second no-slip line of the element (a corner), -1 none
   const Line<T>* fslines;
   const int32_t* ne_off;
   const int32_t* ne_list;
@@ -152,6 +153,7 @@ struct Ctx {
   int32_t nn = 0, ne = 0;
   void* geo = nullptr;          // ElemGeo<T>[ne]
   ElemTopo* topo = nullptr;     // [ne]
+  int32_t* wall2 = nullptr;     // [ne] second no-slip line index (-1 none)
   void* walls = nullptr;        // Line<T>[n_walls]
   void* fslines = nullptr;      // Line<T>[n_fs]
   int32_t* ne_off = nullptr;    // [nn + 1]

@@ -377,3 +377,285 @@ def ensemble(n_inst: int = 64, tri_lo: float = 1000.0, tri_hi: float = 60000.0,
         out.append(channel_instance(int(tris[k]), 392.0, seed=100 + k, ppe=int(ppes[k]), src=src,
                                     philox_seed=1000 + k, instance=k))
     return out
+
+
+# ----------------------------------------------------------------------------------------
+# Street canyon: a periodic channel [0, 4] x [1, 2] over a cavity [1.5, 2.5] x [0, 1].
+# ----------------------------------------------------------------------------------------
+
+def _graded(n: int, length: float, h0: float, both: bool) -> np.ndarray:
+    """n cells on [0, length]: geometric widths from h0 at the start (and, with both, at the
+    end too), growth ratio solved so the widths sum to length."""
+    k = np.arange(n)
+    m = np.minimum(k, n - 1 - k) if both else k
+
+    def total(r: float) -> float:
+        return float(np.sum(h0 * r ** m))
+
+    if total(1.0) >= length:                        # uniform cells already fit
+        return np.linspace(0.0, length, n + 1)
+    lo, hi = 1.0, 2.0
+    while total(hi) < length:
+        hi *= 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if total(mid) < length:
+            lo = mid
+        else:
+            hi = mid
+    w = h0 * (0.5 * (lo + hi)) ** m
+    x = np.concatenate([[0.0], np.cumsum(w)])
+    x *= length / x[-1]
+    return x
+
+
+def canyon_grid(nc: int, no: int, ny: int, mc: int, h0: float, jitter_x: float = 0.2,
+                jitter_y: float = 0.1, seed: int = 1) -> Grid:
+    """Street-canyon grid.  The upper block has nc + no node columns (periodic in x with
+    period 4): nc cells across the cavity opening [1.5, 2.5] and no cells over [2.5, 5.5]
+    (wrapping to 1.5), both graded toward x = 1.5 and 2.5; ny cells in y over [1, 2]
+    graded toward the floor y = 1.  The cavity has the opening's nc cells in x and mc cells
+    in y over [0, 1], graded toward all its walls; its top node row is the upper block's
+    floor row.  Edge tags: free-slip (2) at y = 2; no-slip (1) on the floor outside the
+    opening, on the cavity's side walls and on its bottom.  Nodes on boundaries and on the
+    floor row move only along their line; corners stay put."""
+    rng = np.random.default_rng(seed)
+    L = 4.0
+    xc = 1.5 + _graded(nc, 1.0, h0, True)                  # opening, both ends refined
+    xo = 2.5 + _graded(no, 3.0, h0, True)[1:-1]            # outer part, wraps to 1.5
+    xs = np.concatenate([xc, xo])                          # nx = nc + no columns
+    nx = xs.shape[0]
+    yu = 1.0 + _graded(ny, 1.0, h0, False)                  # upper rows, refined at the floor
+    yc = _graded(mc, 1.0, h0, True)[:-1]                    # cavity rows below y = 1
+    # upper block nodes
+    XU = np.repeat(xs[None, :], ny + 1, axis=0)
+    YU = np.repeat(yu[:, None], nx, axis=1)
+    # cavity nodes (rows below the floor row), columns of the opening
+    XC = np.repeat(xc[None, :], mc, axis=0)
+    YC = np.repeat(yc[:, None], nc + 1, axis=1)
+
+    def local(v):
+        d = np.empty_like(v)
+        d[0] = v[1] - v[0]
+        d[-1] = v[-1] - v[-2]
+        d[1:-1] = np.minimum(v[1:-1] - v[:-2], v[2:] - v[1:-1])
+        return d
+
+    dxu = np.minimum(np.abs(np.diff(np.concatenate([xs, [xs[0] + L]]))),
+                     np.abs(np.diff(np.concatenate([[xs[-1] - L], xs]))))
+    dyu, dxc, dyc = local(yu), local(xc), local(np.concatenate([yc, [1.0]]))[:-1]
+    jxu = rng.uniform(-jitter_x, jitter_x, XU.shape) * dxu[None, :]
+    jyu = rng.uniform(-jitter_y, jitter_y, YU.shape) * dyu[:, None]
+    jxc = rng.uniform(-jitter_x, jitter_x, XC.shape) * dxc[None, :]
+    jyc = rng.uniform(-jitter_y, jitter_y, YC.shape) * dyc[:, None]
+    jyu[0, :] = 0.0                 # floor row
+    jyu[-1, :] = 0.0                # top
+    jxu[:, 0] = 0.0                 # x = 1.5 and 2.5 lines stay straight in the upper block's
+    jxu[:, nc] = 0.0                # floor row (corners) ...
+    jxu[1:, 0] = rng.uniform(-jitter_x, jitter_x, ny) * dxu[0]     # ... but move above it
+    jxu[1:, nc] = rng.uniform(-jitter_x, jitter_x, ny) * dxu[nc]
+    jxc[:, 0] = 0.0                 # cavity side walls
+    jxc[:, -1] = 0.0
+    jyc[0, :] = 0.0                 # cavity bottom
+    XU = np.mod(XU + jxu, L)
+    YU = YU + jyu
+    XC = XC + jxc
+    YC = YC + jyc
+    nu_nodes = (ny + 1) * nx
+    node_xy = np.concatenate([np.stack([XU.ravel(), YU.ravel()], 1),
+                              np.stack([XC.ravel(), YC.ravel()], 1)]).astype(np.float64)
+
+    def uid(j, i):
+        return j * nx + (i % nx)
+
+    def cid(j, i):   # cavity row j (mc = the floor row of the upper block)
+        return np.where(j >= mc, uid(0, i), nu_nodes + np.minimum(j, mc - 1) * (nc + 1) + i)
+
+    quads = []
+    J, I = np.meshgrid(np.arange(ny), np.arange(nx), indexing="ij")
+    J, I = J.ravel(), I.ravel()
+    quads.append(np.stack([uid(J, I), uid(J, I + 1), uid(J + 1, I + 1), uid(J + 1, I)], 1))
+    J, I = np.meshgrid(np.arange(mc), np.arange(nc), indexing="ij")
+    J, I = J.ravel(), I.ravel()
+    quads.append(np.stack([cid(J, I), cid(J, I + 1), cid(J + 1, I + 1), cid(J + 1, I)], 1))
+    q = np.concatenate(quads)
+    n00, n10, n11, n01 = q[:, 0], q[:, 1], q[:, 2], q[:, 3]
+
+    def unwrapped(n, ref):
+        x = node_xy[n, 0].copy()
+        d = x - node_xy[ref, 0]
+        x = np.where(d > 0.5 * L, x - L, np.where(d < -0.5 * L, x + L, x))
+        return x, node_xy[n, 1]
+
+    x00, y00 = unwrapped(n00, n00)
+    x10, y10 = unwrapped(n10, n00)
+    x11, y11 = unwrapped(n11, n00)
+    x01, y01 = unwrapped(n01, n00)
+    use_a = _incircle(x00, y00, x10, y10, x11, y11, x01, y01) <= 0.0
+
+    def area2(ax, ay, bx, by, cx, cy):
+        return (bx - ax) * (cy - ay) - (by - ay) * (cx - ax)
+
+    # nodes on the solid boundary (walls and the free-slip top): no triangle may have all
+    # three there (near a corner that would make a triangle with no interior node)
+    nn = node_xy.shape[0]
+    bnd = np.zeros(nn, bool)
+    bnd[:nx] = True                                  # floor row (walls, corners, opening)
+    bnd[ny * nx:(ny + 1) * nx] = True                # top
+    cav_ids = np.arange(nu_nodes, nn)
+    cc = (cav_ids - nu_nodes) % (nc + 1)
+    cr = (cav_ids - nu_nodes) // (nc + 1)
+    bnd[cav_ids[(cc == 0) | (cc == nc) | (cr == 0)]] = True
+    a_allb = (bnd[n00] & bnd[n10] & bnd[n11]) | (bnd[n00] & bnd[n11] & bnd[n01])
+    b_allb = (bnd[n00] & bnd[n10] & bnd[n01]) | (bnd[n10] & bnd[n11] & bnd[n01])
+    a_ok = (area2(x00, y00, x10, y10, x11, y11) > 0) & (area2(x00, y00, x11, y11, x01, y01) > 0)
+    b_ok = (area2(x00, y00, x10, y10, x01, y01) > 0) & (area2(x10, y10, x11, y11, x01, y01) > 0)
+    a_good, b_good = a_ok & ~a_allb, b_ok & ~b_allb
+    use_a = np.where(a_good & b_good, use_a, np.where(a_good, True, np.where(b_good, False, a_ok)))
+    if not np.all(np.where(use_a, a_ok, b_ok)):
+        raise ValueError("jitter too large: a quad admits no valid split")
+    t1 = np.where(use_a[:, None], np.stack([n00, n10, n11], 1), np.stack([n00, n10, n01], 1))
+    t2 = np.where(use_a[:, None], np.stack([n00, n11, n01], 1), np.stack([n10, n11, n01], 1))
+    tri = np.empty((2 * t1.shape[0], 3), dtype=np.int32)
+    tri[0::2] = t1
+    tri[1::2] = t2
+
+    # boundary classes of the nodes
+    ids = np.arange(nn)
+    col = np.full(nn, -1)
+    col[:nu_nodes] = ids[:nu_nodes] % nx
+    row_u = np.full(nn, -1)
+    row_u[:nu_nodes] = ids[:nu_nodes] // nx
+    ccol = np.full(nn, -1)
+    crow = np.full(nn, -1)
+    ccol[nu_nodes:] = (ids[nu_nodes:] - nu_nodes) % (nc + 1)
+    crow[nu_nodes:] = (ids[nu_nodes:] - nu_nodes) // (nc + 1)
+    top = row_u == ny
+    floor = row_u == 0
+    in_open = floor & (col >= 0) & (col <= nc)             # floor nodes over the opening
+    left = (ccol == 0) | (floor & (col == 0))
+    right = (ccol == nc) | (floor & (col == nc))
+    bottom = crow == 0
+    edge_tag = np.zeros(tri.shape, dtype=np.int8)
+    for k in range(3):
+        a = tri[:, (k + 1) % 3]
+        b = tri[:, (k + 2) % 3]
+        fs = top[a] & top[b]
+        floor_wall = floor[a] & floor[b] & ~(in_open[a] & in_open[b])
+        cav_wall = ((left[a] & left[b]) | (right[a] & right[b]) | (bottom[a] & bottom[b])) & \
+            ((a >= nu_nodes) | (b >= nu_nodes))
+        edge_tag[:, k] = np.where(fs, 2, np.where(floor_wall | cav_wall, 1, 0))
+    return Grid(node_xy=node_xy, tri=tri, edge_tag=edge_tag, period_x=L)
+
+
+def canyon_fields(grid: Grid, nu: float, u_tau: float = 0.05, umax_cav: float = 0.3,
+                  params: dict | None = None) -> np.ndarray:
+    """Nodal fields [nn, 32] of the street canyon.  Above the floor (y >= 1): the
+    half-channel profiles of channel_fields with wall distance y - 1 and height 1 (total
+    shear stress falling linearly to zero at the free-slip top).  In the cavity: the vortex
+    of streamfunction A sin^2(pi (x - 1.5)) sin^2(pi y) with max |U| = umax_cav, k and omega
+    of the near-wall forms (half the channel's) in the distance to the nearest cavity wall,
+    isotropic stresses, no mean-pressure gradient.  k and omega use the distance to the
+    nearest solid wall everywhere (over the opening: to its corners), so they vanish on
+    walls only.  Derivatives are analytic."""
+    c = dict(TABLE4)
+    if params:
+        c.update({k: v for k, v in params.items() if k in c})
+    x = grid.node_xy[:, 0]
+    y = grid.node_xy[:, 1]
+    F = np.zeros((grid.nn, NF), dtype=np.float64)
+    iscale = u_tau / nu
+    up_m = y >= 1.0
+    cav = ~up_m
+    # distance to the nearest solid wall (the floor outside the opening, the cavity walls;
+    # over the opening the nearest of its two corners) and its y-derivative
+    xm = np.mod(x, 4.0)
+    over = (xm > 1.5) & (xm < 2.5)
+    dcorner = np.sqrt(np.minimum((xm - 1.5) ** 2, (xm - 2.5) ** 2) + (y - 1.0) ** 2)
+    dw_up = np.where(over, dcorner, np.maximum(y - 1.0, 0.0))
+    ddw_dy = np.where(over, (y - 1.0) / np.maximum(dcorner, 1e-300), 1.0)
+    xi = x - 1.5
+    dw_cav = np.maximum(np.minimum(np.minimum(xi, 1.0 - xi), y), 0.0)
+    dw = np.where(up_m, dw_up, dw_cav)
+    dp_ = iscale * dw
+    ek = np.exp(-dp_ / 10.0)
+    kp = 3.33 * (1.0 - ek) ** 2
+    dkp = 3.33 * 2.0 * (1.0 - ek) * ek / 10.0
+    k_w = u_tau ** 2 * kp
+    om_w = (u_tau ** 2 / nu) * 0.73 / (dp_ + 8.1)
+    # upper part: half-channel mean velocity in y - 1
+    yw = np.maximum(y - 1.0, 0.0)
+    yp = iscale * yw
+    upv, dup, ddup = _reichardt(yp)
+    fv = (1.0 - np.exp(-dp_ / 26.0)) ** 2
+    F[up_m, 0] = (u_tau * upv)[up_m]
+    F[up_m, 3] = -u_tau ** 2 / 1.0
+    F[up_m, 4] = (-(2.0 / 3.0) * u_tau ** 2 * iscale * dkp * ddw_dy)[up_m]
+    F[up_m, 6] = (u_tau * iscale * dup)[up_m]
+    F[up_m, 11] = (u_tau * iscale ** 2 * ddup)[up_m]
+    F[up_m, 23] = F[up_m, 24] = F[up_m, 25] = (2.0 * k_w / 3.0)[up_m]
+    F[up_m, 26] = (-u_tau ** 2 * (1.0 - yw) * fv)[up_m]
+    F[up_m, 29] = om_w[up_m]
+    # cavity vortex
+    A = umax_cav / math.pi
+    xi = x - 1.5
+    s2x, s2y = np.sin(2 * math.pi * xi), np.sin(2 * math.pi * y)
+    c2x, c2y = np.cos(2 * math.pi * xi), np.cos(2 * math.pi * y)
+    sx2, sy2 = np.sin(math.pi * xi) ** 2, np.sin(math.pi * y) ** 2
+    pi = math.pi
+    U = A * pi * sx2 * s2y
+    V = -A * pi * s2x * sy2
+    dUdx = A * pi ** 2 * s2x * s2y
+    dUdy = 2 * A * pi ** 2 * sx2 * c2y
+    dVdx = -2 * A * pi ** 2 * c2x * sy2
+    dVdy = -dUdx
+    lapU = 2 * A * pi ** 3 * c2x * s2y - 4 * pi ** 2 * U
+    lapV = -4 * pi ** 2 * V - 2 * A * pi ** 3 * s2x * c2y
+    k_ref = 0.5 * 3.33 * u_tau ** 2                 # cavity: half the channel's outer k
+    k_c = 0.5 * k_w
+    om_c = 0.5 * om_w
+    F[cav, 0], F[cav, 1] = U[cav], V[cav]
+    F[cav, 5], F[cav, 6], F[cav, 7], F[cav, 8] = dUdx[cav], dUdy[cav], dVdx[cav], dVdy[cav]
+    F[cav, 11], F[cav, 12] = lapU[cav], lapV[cav]
+    F[cav, 23] = F[cav, 24] = F[cav, 25] = (2.0 * k_c / 3.0)[cav]
+    F[cav, 29] = om_c[cav]
+    # elliptic-relaxation tensor (local algebraic form) from the fields above
+    k_all = 0.5 * (F[:, 23] + F[:, 24] + F[:, 25])
+    grad = np.zeros((grid.nn, 3, 3))
+    grad[:, 0, 0], grad[:, 0, 1] = F[:, 5], F[:, 6]
+    grad[:, 1, 0], grad[:, 1, 1] = F[:, 7], F[:, 8]
+    wpij = np.zeros((grid.nn, 3, 3))
+    for i in range(3):
+        wpij[:, i, i] += 0.5 * (1.0 - c["C1"]) * k_all * F[:, 29]
+    wpij += c["C2"] * k_all[:, None, None] * grad
+    F[:, 14:23] = wpij.reshape(grid.nn, 9)
+    # Eq. 58 wall frequency: (1/C_T) d sqrt(2k)/dn at the wall for these k profiles
+    F[:, 30] = np.where(up_m, (1.0 / c["CT"]) * u_tau * iscale * math.sqrt(2.0 * 3.33) / 10.0,
+                        (1.0 / c["CT"]) * math.sqrt(2.0 * k_ref) * iscale / 10.0)
+    return F
+
+
+def canyon_workload(name: str, ppe: int | None = None) -> dict:
+    """``canyon_2k``: about 2,000 triangles, 20 particles per element, FP64 parity size.
+    ``canyon_200k``: about 200,000 triangles graded to y+ = 1 at the floor and the cavity
+    walls and corners, 100 particles per element (about 20M).  Re_0 = 12,000 (U_max = 1,
+    H = 1, nu = 1/12,000); source disc of radius 0.01 at (2.0, 0.5); Eq. 11 C0, Eq. 25 t_m;
+    MINNPEL = ppe / 10; dt = 1e-4."""
+    nu = 1.0 / 12000.0
+    if name == "canyon_2k":
+        g = canyon_grid(16, 48, 12, 12, h0=0.02, seed=4)
+        p = dict(ppe=20, seed=4, src_r=0.05)
+    elif name == "canyon_200k":
+        g = canyon_grid(160, 480, 125, 125, h0=nu / 0.05, seed=5)
+        p = dict(ppe=100, seed=5, src_r=0.01)
+    else:
+        raise KeyError(name)
+    if ppe is not None:
+        p["ppe"] = int(ppe)
+    params = dict(TABLE4)
+    params.update(nu=nu, Cs=0.02, Ct=0.7, src_x=2.0, src_y=0.5, src_r=p["src_r"],
+                  bins=(4, 4, 4), min_per_bin=2, minnpel=max(1, p["ppe"] // 10),
+                  interp_mode=0, period_x=g.period_x, c0_mode=0, C0=0.0, tm_mode=0, Cphi=2.0,
+                  seed=p["seed"], source_on=1)
+    return dict(name=name, grid=g, fields=canyon_fields(g, nu), params=params, ppe=p["ppe"],
+                dt=1e-4, steps=3)
