@@ -158,8 +158,24 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def max_over_ranks(torch, dist, x: float) -> float:
+    """The largest value over the ranks (the job's time is its slowest rank's); a CUDA tensor
+    under NCCL, a host tensor under gloo."""
+    if dist is None:
+        return x
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], device=dev, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def rank_params(params: dict, rank: int, precision: int, sort_every: int) -> dict:
+    """Each rank steps its own instance: the Philox instance number is the rank."""
+    return dict(params, precision=precision, sort_every=sort_every, instance=int(rank))
+
+
 def make_ctx(B, w, precision, instance, sort_every):
-    p = dict(w["params"], precision=precision, sort_every=sort_every, instance=instance)
+    p = rank_params(w["params"], instance, precision, sort_every)
     c = B.Context(p)
     c.set_grid(w["grid"])
     c.set_fields(w["fields"])
@@ -197,12 +213,7 @@ def time_form(torch, B, w, precision, args, rank, world, dist, with_clock):
     launches = c.kernel_launches - l0
     stage_ms, stage_n = c.stage_times()
     c.set_profiling(False)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-        if dist.get_rank() != 0:
-            pass
+    ms = max_over_ranks(torch, dist, ms)
     err = c.check()
     diag = c.diag()
     np_ = c.np_
@@ -412,10 +423,7 @@ def main():
     rc = None
     if not args.no_canyon:
         rc = canyon_form(torch, B, synth, args)
-    if dist is not None:
-        t = torch.tensor([e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    e2e_s = max_over_ranks(torch, dist, e2e_s)
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
