@@ -104,6 +104,10 @@ def lib():
             L.orc_interp.argtypes = [C.c_void_p, C.c_int, dp, dp]
             L.orc_neighbors.argtypes = [C.c_void_p, ip]
             L.orc_init_particles.argtypes = [C.c_void_p, C.c_int]
+            L.orc_init_elements.argtypes = [C.c_void_p, C.c_int, C.c_int, ip]
+            L.orc_set_particles_ids.argtypes = ([C.c_void_p, C.c_int] + [dp] * 7 +
+                                                [ip, C.POINTER(C.c_uint32), C.c_uint32])
+            L.orc_get_pids.argtypes = [C.c_void_p, C.POINTER(C.c_uint32)]
             L.orc_set_particles.argtypes = [C.c_void_p, C.c_int] + [dp] * 7 + [ip, C.c_uint32]
             L.orc_get_particles.argtypes = [C.c_void_p] + [dp] * 7 + [ip, C.POINTER(C.c_uint8)]
             L.orc_num_particles.argtypes = [C.c_void_p]
@@ -241,13 +245,32 @@ class Oracle:
         if rc:
             raise ValueError("orc_init_particles failed: %d" % rc)
 
-    def set_particles(self, st: dict, step: int):
+    def init_elements(self, ppe, elems):
+        """The particles of a ppe-per-element initialisation in the listed elements only
+        (same ids and draws as the full initialisation)."""
+        el = np.ascontiguousarray(np.sort(np.asarray(elems)), dtype=np.int32)
+        rc = lib().orc_init_elements(self.h, int(ppe), int(el.shape[0]), _ip(el))
+        if rc:
+            raise ValueError("orc_init_elements failed: %d" % rc)
+
+    def set_particles(self, st: dict, step: int, pid=None):
+        """State arrays (ids 0..n-1, or the strictly ascending ids pid)."""
         n = int(st["x"].shape[0])
         arrs = [np.ascontiguousarray(st[k], dtype=np.float64) for k in ("x", "y", "u", "v", "w", "om", "psi")]
         el = np.ascontiguousarray(st["elem"], dtype=np.int32)
-        rc = lib().orc_set_particles(self.h, n, *[_dp(a) for a in arrs], _ip(el), int(step))
+        if pid is None:
+            rc = lib().orc_set_particles(self.h, n, *[_dp(a) for a in arrs], _ip(el), int(step))
+        else:
+            ids = np.ascontiguousarray(pid, dtype=np.uint32)
+            rc = lib().orc_set_particles_ids(self.h, n, *[_dp(a) for a in arrs], _ip(el),
+                                             ids.ctypes.data_as(C.POINTER(C.c_uint32)), int(step))
         if rc:
             raise ValueError("orc_set_particles failed: %d" % rc)
+
+    def pids(self):
+        out = np.zeros(self.np_, dtype=np.uint32)
+        lib().orc_get_pids(self.h, out.ctypes.data_as(C.POINTER(C.c_uint32)))
+        return out
 
     @property
     def np_(self):

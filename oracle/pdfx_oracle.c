@@ -62,6 +62,7 @@ struct orc_ctx {
     double *x, *y, *u, *v, *w, *om, *psi;
     int32_t *elem;
     uint8_t *cp;
+    uint32_t *pid;        /* particle ids (ascending), NULL: the index is the id */
     uint32_t step;
     /* statistics */
     int32_t *count;       /* [ne] */
@@ -174,6 +175,9 @@ void orc_step_gaussians(uint64_t seed, uint32_t instance, uint32_t pid, uint32_t
 /* ------------------------------------------------------------------------------------ */
 /* Grid preprocessing.                                                                  */
 /* ------------------------------------------------------------------------------------ */
+
+/* Id of the particle at index p (the Philox counter word). */
+static uint32_t pid_of(const orc_ctx *c, int p) { return c->pid ? c->pid[p] : (uint32_t)p; }
 
 static double min_image(double d, double L)
 {
@@ -370,7 +374,8 @@ void orc_destroy(orc_ctx *c)
                     c->area2, c->nbr, c->ne_off, c->ne_list, c->wall_type, c->wall_px,
                     c->wall_py, c->wall_nx, c->wall_ny, c->fs_type, c->fs_px, c->fs_py,
                     c->fs_nx, c->fs_ny, c->fields, c->x, c->y, c->u, c->v, c->w, c->om,
-                    c->psi, c->elem, c->cp, c->count, c->emom, c->nmom, c->vcce, c->gbin};
+                    c->psi, c->elem, c->cp, c->count, c->emom, c->nmom, c->vcce, c->gbin,
+                    c->pid};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(c);
 }
@@ -598,7 +603,7 @@ static void advance_particle(orc_ctx *c, int p, double dt)
 
     /* Sect. 3.9 draws */
     double xi[6], eta, eta2;
-    step_draws(P->seed, P->instance, (uint32_t)p, c->step, xi, &eta, &eta2);
+    step_draws(P->seed, P->instance, pid_of(c, p), c->step, xi, &eta, &eta2);
     const double sdt = sqrt(dt);
     const double dWx = sdt * xi[0], dWy = sdt * xi[1];
     const double dWp[3] = {sdt * xi[2], sdt * xi[3], sdt * xi[4]};
@@ -662,7 +667,7 @@ static void advance_particle(orc_ctx *c, int p, double dt)
         Un[0] = Un[1] = Un[2] = 0.0;                             /* Eq. 56 */
         int ex = 0;
         double shape = 1.0 / P->C4;                               /* Eq. 58 */
-        wn = orc_gamma_draw(P->seed, P->instance, (uint32_t)p, c->step, PUR_WALL_GAMMA,
+        wn = orc_gamma_draw(P->seed, P->instance, pid_of(c, p), c->step, PUR_WALL_GAMMA,
                             shape, P->C4 * om_w, &ex);
         if (ex) c->diag.gamma_exhausted++;
     }
@@ -771,7 +776,7 @@ int orc_redistribute(orc_ctx *c)
     for (int k = 0; k < T; ++k) {
         int p = dpart[k], r = rslot[k];
         uint32_t rw[4];
-        philox_draw(c->p.seed, c->p.instance, (uint32_t)p, c->step, PUR_REDIST, 0, rw);
+        philox_draw(c->p.seed, c->p.instance, pid_of(c, p), c->step, PUR_REDIST, 0, rw);
         double s = sqrt(orc_uniform(rw[0]));
         double t = orc_uniform(rw[1]);
         /* uniform point in a triangle: (1-s) A + s (1-t) B + s t C, Osada et al. */
@@ -950,7 +955,8 @@ int orc_statistics(orc_ctx *c)
 static void alloc_particles(orc_ctx *c, int np)
 {
     free(c->x); free(c->y); free(c->u); free(c->v); free(c->w); free(c->om); free(c->psi);
-    free(c->elem); free(c->cp);
+    free(c->elem); free(c->cp); free(c->pid);
+    c->pid = NULL;
     c->np = np;
     size_t n = (size_t)(np > 0 ? np : 1);
     c->x = (double *)calloc(n, sizeof(double));
@@ -969,6 +975,40 @@ static void alloc_particles(orc_ctx *c, int np)
  * and variance C4 <omega>^2; psi from the source disc.  Particle id = e * ppe + k.
  * Draws: purpose 1 block 0 (position words 0-1, Gaussians from words 2-3), block 1
  * (third Gaussian from words 0-1); gamma attempts on purpose 4. */
+/* Sect. 3.7 initial state of the particle at index p, element e, id id. */
+static void init_one(orc_ctx *c, int p, int e, uint32_t id)
+{
+    uint32_t r0[4], r1[4];
+    philox_draw(c->p.seed, c->p.instance, id, 0, PUR_INIT, 0, r0);
+    philox_draw(c->p.seed, c->p.instance, id, 0, PUR_INIT, 1, r1);
+    double s = sqrt(orc_uniform(r0[0]));
+    double t = orc_uniform(r0[1]);
+    double px = c->ax[e] + s * (1.0 - t) * c->bx[e] + s * t * c->cx[e];
+    double py = c->ay[e] + s * (1.0 - t) * c->by[e] + s * t * c->cy[e];
+    double lam[3], q[NF];
+    if (c->p.interp_mode == 1) lam[0] = lam[1] = lam[2] = 1.0 / 3.0;
+    else orc_lambda(c, e, px, py, lam);
+    orc_interp(c, e, lam, q);
+    double k2 = 0.5 * (q[23] + q[24] + q[25]);
+    if (k2 < 0.0) k2 = 0.0;
+    double sd = sqrt(2.0 * k2 / 3.0);
+    double g0, g1, g2, gdum;
+    orc_box_muller(r0[2], r0[3], &g0, &g1);
+    orc_box_muller(r1[0], r1[1], &g2, &gdum);
+    int ex = 0;
+    double om = orc_gamma_draw(c->p.seed, c->p.instance, id, 0, PUR_INIT_GAMMA,
+                               1.0 / c->p.C4, c->p.C4 * q[29], &ex);
+    if (ex) c->diag.gamma_exhausted++;
+    px = wrap_x(px, c->p.period_x);
+    c->x[p] = px; c->y[p] = py;
+    c->u[p] = q[0] + sd * g0;
+    c->v[p] = q[1] + sd * g1;
+    c->w[p] = q[2] + sd * g2;
+    c->om[p] = om;
+    c->psi[p] = in_source(c, px, py) ? 1.0 : 0.0;
+    c->elem[p] = e;
+}
+
 int orc_init_particles(orc_ctx *c, int ppe)
 {
     if (ppe <= 0) return -1;
@@ -978,39 +1018,50 @@ int orc_init_particles(orc_ctx *c, int ppe)
     c->step = 0;
     memset(&c->diag, 0, sizeof(c->diag));
     for (int e = 0; e < c->ne; ++e)
+        for (int k = 0; k < ppe; ++k) init_one(c, e * ppe + k, e, (uint32_t)(e * ppe + k));
+    return orc_statistics(c);
+}
+
+/* The particles of a run initialised with ppe per element, for the listed elements only
+ * (ascending): the same ids (e * ppe + k) and draws, so the oracle can follow a sample of a
+ * run too large for it. */
+int orc_init_elements(orc_ctx *c, int ppe, int n, const int32_t *elems)
+{
+    if (ppe <= 0 || n < 0) return -1;
+    for (int i = 0; i < n; ++i)
+        if (elems[i] < 0 || elems[i] >= c->ne || (i > 0 && elems[i] <= elems[i - 1])) return -2;
+    if ((long long)ppe * c->ne > 4294967295LL) return -1;
+    alloc_particles(c, n * ppe);
+    c->pid = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(n * ppe > 0 ? n * ppe : 1));
+    c->step = 0;
+    memset(&c->diag, 0, sizeof(c->diag));
+    for (int i = 0; i < n; ++i)
         for (int k = 0; k < ppe; ++k) {
-            int p = e * ppe + k;
-            uint32_t r0[4], r1[4];
-            philox_draw(c->p.seed, c->p.instance, (uint32_t)p, 0, PUR_INIT, 0, r0);
-            philox_draw(c->p.seed, c->p.instance, (uint32_t)p, 0, PUR_INIT, 1, r1);
-            double s = sqrt(orc_uniform(r0[0]));
-            double t = orc_uniform(r0[1]);
-            double px = c->ax[e] + s * (1.0 - t) * c->bx[e] + s * t * c->cx[e];
-            double py = c->ay[e] + s * (1.0 - t) * c->by[e] + s * t * c->cy[e];
-            double lam[3], q[NF];
-            if (c->p.interp_mode == 1) lam[0] = lam[1] = lam[2] = 1.0 / 3.0;
-            else orc_lambda(c, e, px, py, lam);
-            orc_interp(c, e, lam, q);
-            double k2 = 0.5 * (q[23] + q[24] + q[25]);
-            if (k2 < 0.0) k2 = 0.0;
-            double sd = sqrt(2.0 * k2 / 3.0);
-            double g0, g1, g2, gdum;
-            orc_box_muller(r0[2], r0[3], &g0, &g1);
-            orc_box_muller(r1[0], r1[1], &g2, &gdum);
-            int ex = 0;
-            double om = orc_gamma_draw(c->p.seed, c->p.instance, (uint32_t)p, 0, PUR_INIT_GAMMA,
-                                       1.0 / c->p.C4, c->p.C4 * q[29], &ex);
-            if (ex) c->diag.gamma_exhausted++;
-            px = wrap_x(px, c->p.period_x);
-            c->x[p] = px; c->y[p] = py;
-            c->u[p] = q[0] + sd * g0;
-            c->v[p] = q[1] + sd * g1;
-            c->w[p] = q[2] + sd * g2;
-            c->om[p] = om;
-            c->psi[p] = in_source(c, px, py) ? 1.0 : 0.0;
-            c->elem[p] = e;
+            const int p = i * ppe + k;
+            c->pid[p] = (uint32_t)elems[i] * (uint32_t)ppe + (uint32_t)k;
+            init_one(c, p, elems[i], c->pid[p]);
         }
     return orc_statistics(c);
+}
+
+/* As orc_set_particles with explicit, strictly ascending particle ids. */
+int orc_set_particles_ids(orc_ctx *c, int np, const double *x, const double *y, const double *u,
+                          const double *v, const double *w, const double *om, const double *psi,
+                          const int32_t *elem, const uint32_t *pid, uint32_t step)
+{
+    for (int p = 1; p < np; ++p)
+        if (pid[p] <= pid[p - 1]) return -3;
+    int rc = orc_set_particles(c, np, x, y, u, v, w, om, psi, elem, step);
+    if (rc) return rc;
+    c->pid = (uint32_t *)malloc(sizeof(uint32_t) * (size_t)(np > 0 ? np : 1));
+    memcpy(c->pid, pid, sizeof(uint32_t) * (size_t)np);
+    return orc_statistics(c);
+}
+
+int orc_get_pids(const orc_ctx *c, uint32_t *out)
+{
+    for (int p = 0; p < c->np; ++p) out[p] = pid_of(c, p);
+    return 0;
 }
 
 int orc_set_particles(orc_ctx *c, int np, const double *x, const double *y, const double *u,

@@ -70,6 +70,11 @@ int  orc_neighbors(const orc_ctx *c, int32_t *nbr /* [ne][3] */);
 
 /* Particles (stored by particle id). */
 int  orc_init_particles(orc_ctx *c, int ppe);
+int  orc_init_elements(orc_ctx *c, int ppe, int n, const int32_t *elems);
+int  orc_set_particles_ids(orc_ctx *c, int np, const double *x, const double *y, const double *u,
+                           const double *v, const double *w, const double *om, const double *psi,
+                           const int32_t *elem, const uint32_t *pid, uint32_t step);
+int  orc_get_pids(const orc_ctx *c, uint32_t *out);
 int  orc_set_particles(orc_ctx *c, int np, const double *x, const double *y, const double *u,
                        const double *v, const double *w, const double *om, const double *psi,
                        const int32_t *elem, uint32_t step);

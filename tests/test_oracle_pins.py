@@ -712,3 +712,38 @@ def test_init_particles_distribution(w2k):
     assert stats.kstest(zo, stats.gamma(a=4, scale=0.25).cdf).pvalue > 1e-3
     psi_in = (((s["x"] - 0.5) ** 2 + (s["y"] - 0.5) ** 2) <= 0.02 ** 2)
     assert np.array_equal(s["psi"] == 1.0, psi_in)
+
+
+def test_element_subset_initialisation_matches_the_full_one():
+    """orc_init_elements gives the listed elements' particles of a full initialisation (same
+    ids, same draws), and a step of a subset given with its ids moves those particles as the
+    full run does (the oracle following a sample of a run too large for it)."""
+    w = synth.workload("channel_tiny")
+    g = w["grid"]
+    P = dict(w["params"], minnpel=0)
+    full = oracle.Oracle(g, P, w["fields"])
+    full.init_particles(30)
+    sf = full.get_particles()
+    elems = [3, 17, 40, 41, 63]
+    sub = oracle.Oracle(g, P, w["fields"])
+    sub.init_elements(30, elems)
+    ss = sub.get_particles()
+    ids = sub.pids()
+    assert np.array_equal(ids, np.concatenate([np.arange(e * 30, e * 30 + 30) for e in elems]))
+    for k in ("x", "y", "u", "v", "w", "om", "psi", "elem", "cp"):
+        assert np.array_equal(ss[k], sf[k][ids]), k
+    eo, _ = full.element_stats()
+    es, _ = sub.element_stats()
+    assert np.array_equal(es[elems], eo[elems])
+    full.step(w["dt"])
+    sub.step(w["dt"])
+    sf, ss = full.get_particles(), sub.get_particles()
+    for k in ("x", "y", "u", "v", "w", "om", "psi", "elem"):
+        assert np.array_equal(ss[k], sf[k][ids]), k
+    # the same subset given as a state with its ids
+    sub2 = oracle.Oracle(g, P, w["fields"])
+    st0 = oracle.Oracle(g, P, w["fields"])
+    st0.init_elements(30, elems)
+    sub2.set_particles(st0.get_particles(), 0, pid=st0.pids())
+    sub2.step(w["dt"])
+    assert np.array_equal(sub2.get_particles()["x"], ss["x"])
