@@ -174,8 +174,8 @@ def rank_params(params: dict, rank: int, precision: int, sort_every: int) -> dic
     return dict(params, precision=precision, sort_every=sort_every, instance=int(rank))
 
 
-def make_ctx(B, w, precision, instance, sort_every):
-    p = rank_params(w["params"], instance, precision, sort_every)
+def make_ctx(B, w, precision, instance, sort_every, extra=None):
+    p = dict(rank_params(w["params"], instance, precision, sort_every), **(extra or {}))
     c = B.Context(p)
     c.set_grid(w["grid"])
     c.set_fields(w["fields"])
@@ -183,9 +183,9 @@ def make_ctx(B, w, precision, instance, sort_every):
     return c
 
 
-def time_form(torch, B, w, precision, args, rank, world, dist, with_clock):
+def time_form(torch, B, w, precision, args, rank, world, dist, with_clock, extra=None):
     """Device time of K steps of one form (inputs resident in HBM)."""
-    c = make_ctx(B, w, precision, rank, args.sort_every)
+    c = make_ctx(B, w, precision, rank, args.sort_every, extra)
     stream = torch.cuda.current_stream()
     for _ in range(args.warmup):
         c.step(w["dt"])
@@ -413,10 +413,14 @@ def main():
     c32, r32 = time_form(torch, B, w, 1, args, rank, world, dist, with_clock=True)
     e2e_s, h2d, d2h = e2e_form(torch, B, c32, w, args)
     c32.close()
-    r64 = None
+    r64 = rb64 = None
     if not args.no_f64:
         c64, r64 = time_form(torch, B, w, 0, args, rank, world, dist, with_clock=False)
         c64.close()
+        # the FP32 form with FP64 accumulation of moments and conditional means
+        cb, rb64 = time_form(torch, B, w, 1, args, rank, world, dist, with_clock=False,
+                             extra={"acc64": 1})
+        cb.close()
     rb = None
     if not args.no_batch:
         rb = batched_form(torch, B, synth, args)
@@ -485,10 +489,17 @@ def main():
                                                                   "walk_brute", "lost", "wall_hits",
                                                                   "moves")}}
         line["speedup_f32_vs_f64"] = value / v64
+        vB = rb64["np"] * world * args.steps / (rb64["ms"] * 1e-3)
         line["precision_study"] = {
-            "what": "nodal statistics of the FP32 form vs the FP64 form after the same %d steps "
-                    "from the same seeds (relative error, floor = column RMS)" % (args.warmup + args.steps),
-            "errors": precision_study(r32["nodal"], r64["nodal"])}
+            "what": "nodal statistics against the FP64 form (A) after the same %d steps from the "
+                    "same seeds (relative error, floor = column RMS)" % (args.warmup + args.steps),
+            "forms": {
+                "A_fp64": {"value": v64, "unit": UNIT},
+                "B_fp32_sde_fp64_accumulation": {"value": vB, "unit": UNIT,
+                                                 "errors": precision_study(rb64["nodal"], r64["nodal"])},
+                "C_fp32_sde_compensated_fp32_accumulation": {
+                    "value": value, "unit": UNIT,
+                    "errors": precision_study(r32["nodal"], r64["nodal"])}}}
     if rc is not None:
         line["street_canyon"] = rc
     if rb is not None:

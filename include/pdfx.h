@@ -86,6 +86,8 @@ typedef struct pdfx_params {
     int    precision;         /* 0: FP64 state and arithmetic; 1: FP32 state and SDE
                                  arithmetic with FP64 statistics and conditional means */
     int    sort_every;        /* re-order particles by element every this many steps */
+    int    acc64;             /* FP32 form: 1 accumulates element moments and conditional
+                                 means in FP64, 0 (default) in compensated FP32 */
 } pdfx_params;
 
 typedef struct pdfx_allocator {
@@ -124,8 +126,8 @@ int  pdfx_create(const pdfx_params *p, const pdfx_allocator *alloc, void **out_c
 /* Releases all device memory of the context (synchronises the device first). */
 void pdfx_destroy(void *ctx);
 
-/* Replaces the model parameters (everything except bins, precision and sort_every, which
- * are fixed at creation).  Host pointer.  PDFX_ERR_ARG if those differ, and for a batch of
+/* Replaces the model parameters (everything except bins, precision, sort_every and acc64,
+ * which are fixed at creation).  Host pointer.  PDFX_ERR_ARG if those differ, and for a batch of
  * more than one instance (its parameters come from pdfx_set_instances). */
 int  pdfx_set_params(void *ctx, const pdfx_params *p);
 
@@ -133,7 +135,7 @@ int  pdfx_set_params(void *ctx, const pdfx_params *p);
  * of the method on its own grid, and a batch steps them all with one launch per stage).
  * Call before pdfx_set_grid.  n instances; p[n] their parameters (host, copied): each may
  * have its own constants, seed, instance number, source, period_x and MINNPEL, while
- * precision, sort_every, bins and min_per_bin must equal the context's (else
+ * precision, sort_every, acc64, bins and min_per_bin must equal the context's (else
  * PDFX_ERR_ARG).  elem_first[n + 1] (host): instance k owns the elements elem_first[k] ..
  * elem_first[k + 1] - 1 of the union grid that pdfx_set_grid receives next (elem_first[0]
  * = 0, increasing, elem_first[n] = its ne; the instances may share no edge and no node,

@@ -38,7 +38,7 @@ class Params(C.Structure):
         ("bins", C.c_int * 3), ("min_per_bin", C.c_int), ("minnpel", C.c_int),
         ("interp_mode", C.c_int), ("source_on", C.c_int),
         ("seed", C.c_uint64), ("instance", C.c_uint32), ("period_x", C.c_double),
-        ("precision", C.c_int), ("sort_every", C.c_int),
+        ("precision", C.c_int), ("sort_every", C.c_int), ("acc64", C.c_int),
     ]
 
 

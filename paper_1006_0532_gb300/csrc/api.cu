@@ -65,6 +65,7 @@ bool params_valid(const pdfx_params& p) {
   if (p.min_per_bin < 1 || p.minnpel < 0 || p.minnpel > PDFX_MAX_PER_ELEMENT) return false;
   if (p.precision != 0 && p.precision != 1) return false;
   if (p.sort_every < 0 || !(p.nu >= 0.0) || !(p.period_x >= 0.0)) return false;
+  if (p.acc64 != 0 && p.acc64 != 1) return false;
   return true;
 }
 
@@ -305,6 +306,7 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
     a.vcce = c.vcce;
     a.gbin = c.gbin;
     a.step_inc = allow_moves ? c.dstep : nullptr;   // only a step advances the counter
+    a.acc64 = c.prm.acc64;
     a.diag = c.diag;
     a.err = c.err;
     launch_stats<T>(a, c.num_sms, s);
@@ -955,6 +957,7 @@ int pdfx_set_params(void* ctx, const pdfx_params* p) {
   Ctx* c = as_ctx(ctx);
   if (!c || !p || !params_valid(*p)) return PDFX_ERR_ARG;
   if (p->precision != c->prm.precision || p->sort_every != c->prm.sort_every ||
+      p->acc64 != c->prm.acc64 ||
       p->bins[0] != c->prm.bins[0] || p->bins[1] != c->prm.bins[1] || p->bins[2] != c->prm.bins[2])
     return PDFX_ERR_ARG;
   if (c->have_grid && p->period_x != c->prm.period_x) return PDFX_ERR_ARG;
@@ -972,7 +975,8 @@ int pdfx_set_instances(void* ctx, int32_t n, const pdfx_params* p, const int32_t
     if (elem_first[k + 1] <= elem_first[k] || !params_valid(p[k])) return PDFX_ERR_ARG;
     if (p[k].precision != c->prm.precision || p[k].sort_every != c->prm.sort_every ||
         p[k].bins[0] != c->prm.bins[0] || p[k].bins[1] != c->prm.bins[1] ||
-        p[k].bins[2] != c->prm.bins[2] || p[k].min_per_bin != c->prm.min_per_bin)
+        p[k].bins[2] != c->prm.bins[2] || p[k].min_per_bin != c->prm.min_per_bin ||
+        p[k].acc64 != c->prm.acc64)
       return PDFX_ERR_ARG;
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return PDFX_ERR_CUDA;

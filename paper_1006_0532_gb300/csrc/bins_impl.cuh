@@ -249,7 +249,7 @@ struct Tile {
   int tie[3];                       // a tie was found at level l (fast pass)
   int32_t gfc[CAP / 32 + 1];        // first chunk of each group
   uint8_t cg[kChunks];              // group of each chunk
-  T mh[12], ml[12], msh[5];         // moment sums (value/error pairs) and shift values
+  double mh[12], ml[12], msh[5];    // moment sums (value/error pairs) and shift values
   int n_gathered;
 };
 
@@ -330,6 +330,57 @@ __device__ void sort_level(const StatsArgs<T>& a, Tile<T, CAP>& t, Arr& sk, cons
     const bool any = __any_sync(kFull, found);   // every lane takes part
     if (any && lane == 0) *tie = 1;
   }
+}
+
+// Sect. 3.3, Eqs. 35-36, by warp 0 in the order cur: sums of d = x - x_0 and of products of
+// d in precision A, x_0 the first particle of the order; mean = x_0 + S1/N, central =
+// S2/N - (S1/N)^2; lanes combine as value/error pairs (FP32) or in FP64, then the 13
+// outputs are formed in FP64, one per lane.
+template <typename A, typename T, int CAP>
+__device__ void element_moments(const StatsArgs<T>& a, Tile<T, CAP>& t, const int32_t* cur, int n,
+                                int e, const int (&g)[3]) {
+  const int lane = threadIdx.x & 31;
+  A sh[5] = {A(0), A(0), A(0), A(0), A(0)};
+  if (n > 0) {
+    const int32_t q0 = cur[0];
+    sh[0] = A(a.p.u[q0]); sh[1] = A(a.p.v[q0]); sh[2] = A(a.p.w[q0]);
+    sh[3] = A(a.p.om[q0]); sh[4] = A(a.p.psi[q0]);
+  }
+  Acc<A> m[12];
+  for (int p = lane; p < n; p += 32) {
+    const int32_t q = cur[p];
+    const A du = A(a.p.u[q]) - sh[0], dv = A(a.p.v[q]) - sh[1], dw = A(a.p.w[q]) - sh[2];
+    const A dom = A(a.p.om[q]) - sh[3], dp = A(a.p.psi[q]) - sh[4];
+    m[0].add(du); m[1].add(dv); m[2].add(dw); m[3].add(dom); m[4].add(dp);
+    m[5].add(du * du); m[6].add(dv * dv); m[7].add(dw * dw);
+    m[8].add(du * dv); m[9].add(du * dw); m[10].add(dv * dw);
+    m[11].add(dp * dp);
+  }
+#pragma unroll
+  for (int c = 0; c < 12; ++c) {
+    A h, l;
+    m[c].warp_pair(h, l);
+    if (lane == c) { t.mh[c] = h; t.ml[c] = l; }
+  }
+  if (lane < 5)
+    t.msh[lane] = lane == 0 ? sh[0] : lane == 1 ? sh[1] : lane == 2 ? sh[2] : lane == 3 ? sh[3] : sh[4];
+  __syncwarp();
+  if (lane < kNS) {
+    const double inv = n > 0 ? 1.0 / n : 0.0;
+    const int ix = mom_nib(kMomX, lane), iy = mom_nib(kMomY, lane);
+    const int iz = mom_nib(kMomZ, lane), iw = mom_nib(kMomW, lane);
+    double v = ix < 15 ? t.msh[ix] : 0.0;
+    if (iy < 15) v += (t.mh[iy] + t.ml[iy]) * inv;
+    if (iz < 15) {
+      const double z = (t.mh[iz] + t.ml[iz]) * inv;
+      const double w = (t.mh[iw] + t.ml[iw]) * inv;
+      v -= z * w;
+    }
+    if (lane == 0) v = static_cast<double>(n);
+    else if (n == 0) v = 0.0;
+    a.emom[static_cast<size_t>(kNS) * e + lane] = v;
+  }
+  if (lane < 3) a.gbin[3 * e + lane] = lane == 0 ? g[0] : lane == 1 ? g[1] : g[2];
 }
 
 // One element of N <= CAP particles (list size after redistribution) by a block of THREADS.
@@ -433,63 +484,31 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int 
   }
   const int G = g[0] * g[1] * g[2];
 
-  // moments (warp 0) in the final order: sums of d = x - x_0 and of products of d, x_0 the
-  // first particle of the order; mean = x_0 + S1/N, central = S2/N - (S1/N)^2
+  // moments (warp 0) in the final order, accumulated in the state precision (FP32 form:
+  // compensated) or, with acc64 in the FP32 form, in FP64
   if (warp == 0) {
-    T sh[5] = {T(0), T(0), T(0), T(0), T(0)};
-    if (n > 0) {
-      const int32_t q0 = cur[0];
-      sh[0] = a.p.u[q0]; sh[1] = a.p.v[q0]; sh[2] = a.p.w[q0]; sh[3] = a.p.om[q0]; sh[4] = a.p.psi[q0];
-    }
-    Acc<T> m[12];
-    for (int p = lane; p < n; p += 32) {
-      const int32_t q = cur[p];
-      const T du = a.p.u[q] - sh[0], dv = a.p.v[q] - sh[1], dw = a.p.w[q] - sh[2];
-      const T dom = a.p.om[q] - sh[3], dp = a.p.psi[q] - sh[4];
-      m[0].add(du); m[1].add(dv); m[2].add(dw); m[3].add(dom); m[4].add(dp);
-      m[5].add(du * du); m[6].add(dv * dv); m[7].add(dw * dw);
-      m[8].add(du * dv); m[9].add(du * dw); m[10].add(dv * dw);
-      m[11].add(dp * dp);
-    }
-#pragma unroll
-    for (int c = 0; c < 12; ++c) {
-      T h, l;
-      m[c].warp_pair(h, l);
-      if (lane == c) { t.mh[c] = h; t.ml[c] = l; }
-    }
-    if (lane < 5)
-      t.msh[lane] = lane == 0 ? sh[0] : lane == 1 ? sh[1] : lane == 2 ? sh[2] : lane == 3 ? sh[3] : sh[4];
-    __syncwarp();
-    if (lane < kNS) {
-      const double inv = n > 0 ? 1.0 / n : 0.0;
-      const int ix = mom_nib(kMomX, lane), iy = mom_nib(kMomY, lane);
-      const int iz = mom_nib(kMomZ, lane), iw = mom_nib(kMomW, lane);
-      double v = ix < 15 ? static_cast<double>(t.msh[ix]) : 0.0;
-      if (iy < 15) v += (static_cast<double>(t.mh[iy]) + static_cast<double>(t.ml[iy])) * inv;
-      if (iz < 15) {
-        const double z = (static_cast<double>(t.mh[iz]) + static_cast<double>(t.ml[iz])) * inv;
-        const double w = (static_cast<double>(t.mh[iw]) + static_cast<double>(t.ml[iw])) * inv;
-        v -= z * w;
-      }
-      if (lane == 0) v = static_cast<double>(n);
-      else if (n == 0) v = 0.0;
-      a.emom[static_cast<size_t>(kNS) * e + lane] = v;
-    }
-    if (lane < 3) a.gbin[3 * e + lane] = lane == 0 ? g[0] : lane == 1 ? g[1] : g[2];
+    if (sizeof(T) == 4 && a.acc64) element_moments<double>(a, t, cur, n, e, g);
+    else element_moments<T>(a, t, cur, n, e, g);
   }
 
   // Appendix A bins: conditional scalar means over the final order's bins
   double* vc = a.vcce + static_cast<size_t>(a.G) * e;
   const float invGb = 1.0f / static_cast<float>(G);
   for (int i = threadIdx.x; i < a.G; i += THREADS) {
-    T mval = T(0);
+    double mval = 0.0;
     if (i < G && n > 0) {
       const int b0 = group_start(i, n, G, invGb), b1 = group_start(i + 1, n, G, invGb);
-      Acc<T> sum;
-      for (int p = b0; p < b1; ++p) sum.add(a.p.psi[cur[p]]);
-      mval = sum.value() / static_cast<T>(b1 - b0);
+      if (sizeof(T) == 4 && a.acc64) {
+        double sum = 0.0;
+        for (int p = b0; p < b1; ++p) sum += static_cast<double>(a.p.psi[cur[p]]);
+        mval = sum / static_cast<double>(b1 - b0);
+      } else {
+        Acc<T> sum;
+        for (int p = b0; p < b1; ++p) sum.add(a.p.psi[cur[p]]);
+        mval = static_cast<double>(sum.value() / static_cast<T>(b1 - b0));
+      }
     }
-    vc[i] = static_cast<double>(mval);
+    vc[i] = mval;
   }
   // conditioning pointers (and the element-ordered copy of the state every few steps)
   const float inv_n = n > 0 ? 1.0f / static_cast<float>(n) : 0.0f;

@@ -103,6 +103,7 @@ struct StatsArgs {
   double* vcce;
   int32_t* gbin;
   uint32_t* step_inc;    // stepping: the step counter, advanced once after this step's reads
+  int acc64;             // FP32 form: accumulate moments and conditional means in FP64
   unsigned long long* diag;
   int* err;
 };

@@ -280,10 +280,13 @@ def _round32(st):
     return out
 
 
-def test_one_step_f32_matches_oracle():
+@pytest.mark.parametrize("acc64", [0, 1])
+def test_one_step_f32_matches_oracle(acc64):
+    """FP32 form (acc64 = 0: compensated FP32 accumulation of moments and conditional
+    means; acc64 = 1: FP64 accumulation) against the FP64 oracle."""
     w = synth.workload("channel_2k")
     g = w["grid"]
-    params = dict(w["params"])
+    params = dict(w["params"], acc64=acc64)
     F32 = w["fields"].astype(np.float32).astype(np.float64)
     o = oracle.Oracle(g, params, F32)
     o.init_particles(w["ppe"])
