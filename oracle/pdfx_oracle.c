@@ -63,6 +63,7 @@ struct orc_ctx {
     int32_t *elem;
     uint8_t *cp;
     uint32_t *pid;        /* particle ids (ascending), NULL: the index is the id */
+    double *uphi;         /* [ne][3] element <u_a phi'> (Fox's projection, Eq. 66) */
     uint32_t step;
     /* statistics */
     int32_t *count;       /* [ne] */
@@ -269,6 +270,8 @@ static int params_valid(const orc_params *p)
     for (int l = 0; l < 3; ++l)
         if (p->bins[l] < 1 || p->bins[l] > 16) return 0;
     if (p->bins[0] * p->bins[1] * p->bins[2] > 256 || p->min_per_bin < 1) return 0;
+    if (p->cond_mode != 0 && p->cond_mode != 1) return 0;
+    if (p->cond_mode == 1 && (p->fox_bins < 1 || p->fox_bins > 256)) return 0;
     return 1;
 }
 
@@ -358,8 +361,9 @@ int orc_create(orc_ctx **out, const orc_params *p, int nn, const double *node_xy
     c->fields = (double *)calloc((size_t)nn * NF, sizeof(double));
     c->count = (int32_t *)calloc(ne, sizeof(int32_t));
     c->emom = (double *)calloc((size_t)ne * NS, sizeof(double));
+    c->uphi = (double *)calloc((size_t)ne * 3, sizeof(double));
     c->nmom = (double *)calloc((size_t)nn * NS, sizeof(double));
-    c->G = p->bins[0] * p->bins[1] * p->bins[2];
+    c->G = p->cond_mode == 1 ? p->fox_bins : p->bins[0] * p->bins[1] * p->bins[2];
     if (c->G < 1 || c->G > 256) { orc_destroy(c); return -5; }
     c->vcce = (double *)calloc((size_t)ne * c->G, sizeof(double));
     c->gbin = (int32_t *)calloc((size_t)ne * 3, sizeof(int32_t));
@@ -375,7 +379,7 @@ void orc_destroy(orc_ctx *c)
                     c->wall_py, c->wall_nx, c->wall_ny, c->fs_type, c->fs_px, c->fs_py,
                     c->fs_nx, c->fs_ny, c->fields, c->x, c->y, c->u, c->v, c->w, c->om,
                     c->psi, c->elem, c->cp, c->count, c->emom, c->nmom, c->vcce, c->gbin,
-                    c->pid};
+                    c->pid, c->uphi};
     for (size_t i = 0; i < sizeof(ptrs) / sizeof(ptrs[0]); ++i) free(ptrs[i]);
     free(c);
 }
@@ -847,6 +851,76 @@ static void effective_bins(const orc_params *P, int N, int g[3])
     }
 }
 
+/* Fox's projection (Eqs. 64-66).  Per element: rho_a = <u_a phi'> / (s_a s_phi) and
+ * rho_ab = <u_a u_b> / (s_a s_b) from the element's central moments (s the standard
+ * deviations); alpha solves rho_ab alpha_b = rho_a (Cramer's rule); alpha = 0 when s_phi,
+ * an s_a or the determinant vanishes (|det| <= 1e-12).  Reading of Eq. 64: the projected
+ * velocity of a particle is U_rho = sum_a alpha_a (U_a - <U_a>) / s_a (the normalised
+ * fluctuations the correlations refer to).  The element's particles are ordered by
+ * (U_rho, id) and divided into N_c = max(1, min(fox_bins, N / min_per_bin)) equal
+ * intervals, position n in interval floor(N_c n / N); the conditional mean of an interval
+ * is its mean psi. */
+static void fox_alpha(const double *m, const double *uphi, double alpha_over_s[3])
+{
+    alpha_over_s[0] = alpha_over_s[1] = alpha_over_s[2] = 0.0;
+    const double var[3] = {m[4], m[5], m[6]}, vphi = m[12];
+    if (!(vphi > 0.0) || !(var[0] > 0.0) || !(var[1] > 0.0) || !(var[2] > 0.0)) return;
+    const double s[3] = {sqrt(var[0]), sqrt(var[1]), sqrt(var[2])}, sphi = sqrt(vphi);
+    const double cuv = m[7], cuw = m[8], cvw = m[9];
+    const double A[3][3] = {{1.0, cuv / (s[0] * s[1]), cuw / (s[0] * s[2])},
+                            {cuv / (s[0] * s[1]), 1.0, cvw / (s[1] * s[2])},
+                            {cuw / (s[0] * s[2]), cvw / (s[1] * s[2]), 1.0}};
+    const double b[3] = {uphi[0] / (s[0] * sphi), uphi[1] / (s[1] * sphi), uphi[2] / (s[2] * sphi)};
+    const double det = A[0][0] * (A[1][1] * A[2][2] - A[1][2] * A[2][1])
+                     - A[0][1] * (A[1][0] * A[2][2] - A[1][2] * A[2][0])
+                     + A[0][2] * (A[1][0] * A[2][1] - A[1][1] * A[2][0]);
+    if (!(fabs(det) > 1e-12)) return;
+    for (int i = 0; i < 3; ++i) {
+        double M[3][3];
+        for (int r = 0; r < 3; ++r)
+            for (int col = 0; col < 3; ++col) M[r][col] = col == i ? b[r] : A[r][col];
+        const double di = M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1])
+                        - M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0])
+                        + M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+        alpha_over_s[i] = (di / det) / s[i];
+    }
+}
+
+static void fox_conditional_means(orc_ctx *c, const int32_t *off, int32_t *res)
+{
+    double *key = (double *)malloc(sizeof(double) * (size_t)(c->np > 0 ? c->np : 1));
+    for (int e = 0; e < c->ne; ++e) {
+        const int N = c->count[e];
+        const double *m = c->emom + (size_t)NS * e;
+        int Nc = c->p.fox_bins;
+        int cap = N / c->p.min_per_bin;
+        if (cap < Nc) Nc = cap;
+        if (Nc < 1) Nc = 1;
+        c->gbin[3 * e] = Nc; c->gbin[3 * e + 1] = 1; c->gbin[3 * e + 2] = 1;
+        if (N == 0) continue;
+        double f[3];
+        fox_alpha(m, c->uphi + 3 * e, f);
+        int32_t *par = res + off[e];
+        for (int n = 0; n < N; ++n) {
+            const int p = par[n];
+            key[p] = f[0] * (c->u[p] - m[1]) + f[1] * (c->v[p] - m[2]) + f[2] * (c->w[p] - m[3]);
+        }
+        g_sort_key = key;
+        qsort(par, (size_t)N, sizeof(int32_t), cmp_by_key);
+        double *vc = c->vcce + (size_t)e * c->G;
+        int np_bin[256];
+        for (int i = 0; i < Nc; ++i) { np_bin[i] = 0; vc[i] = 0.0; }
+        for (int n = 0; n < N; ++n) {
+            const int i = (int)(((long long)Nc * n) / N);
+            np_bin[i] += 1;
+            vc[i] += c->psi[par[n]];
+            c->cp[par[n]] = (uint8_t)i;
+        }
+        for (int i = 0; i < Nc; ++i) vc[i] = vc[i] / np_bin[i];
+    }
+    free(key);
+}
+
 int orc_statistics(orc_ctx *c)
 {
     const int ne = c->ne, nn = c->nn;
@@ -874,13 +948,16 @@ int orc_statistics(orc_ctx *c)
         }
         double mu = su / N, mv = sv / N, mw = sw / N, mo = so / N, mp = sp / N;
         double suu = 0, svv = 0, sww = 0, suv = 0, suw = 0, svw = 0, spp = 0;
+        double sup = 0, svp = 0, swp = 0;
         for (int i = off[e]; i < off[e + 1]; ++i) {
             int p = res[i];
             double du = c->u[p] - mu, dv = c->v[p] - mv, dw = c->w[p] - mw, dp = c->psi[p] - mp;
             suu += du * du; svv += dv * dv; sww += dw * dw;
             suv += du * dv; suw += du * dw; svw += dv * dw;
             spp += dp * dp;
+            sup += du * dp; svp += dv * dp; swp += dw * dp;
         }
+        c->uphi[3 * e] = sup / N; c->uphi[3 * e + 1] = svp / N; c->uphi[3 * e + 2] = swp / N;
         m[1] = mu; m[2] = mv; m[3] = mw;
         m[4] = suu / N; m[5] = svv / N; m[6] = sww / N;
         m[7] = suv / N; m[8] = suw / N; m[9] = svw / N;
@@ -906,6 +983,12 @@ int orc_statistics(orc_ctx *c)
     /* Conditional means (Sect. 3.5, Appendix A) */
     const double *keys[3] = {c->u, c->v, c->w};
     memset(c->vcce, 0, sizeof(double) * (size_t)ne * c->G);
+    if (c->p.cond_mode == 1) {
+        fox_conditional_means(c, off, res);
+        free(res);
+        free(off);
+        return 0;
+    }
     for (int e = 0; e < ne; ++e) {
         int N = c->count[e];
         int g[3];

@@ -34,6 +34,9 @@ typedef struct orc_params {
     uint64_t seed;             /* Philox key = (seed_lo, seed_hi ^ instance) */
     uint32_t instance;
     double period_x;           /* 0 = not periodic */
+    int    cond_mode;          /* 0: hierarchical bins (Sect. 3.5, Appendix A); 1: Fox's
+                                  projection (Eqs. 64-66) with fox_bins intervals */
+    int    fox_bins;
 } orc_params;
 
 typedef struct orc_diag {

@@ -747,3 +747,63 @@ def test_element_subset_initialisation_matches_the_full_one():
     sub2.set_particles(st0.get_particles(), 0, pid=st0.pids())
     sub2.step(w["dt"])
     assert np.array_equal(sub2.get_particles()["x"], ss["x"])
+
+
+def _element_state(g, elems, n_per, rng, psi_fn):
+    """Particles at random points of the given elements, Gaussian velocities, psi = psi_fn."""
+    xs, ys, es = [], [], []
+    for e in elems:
+        xy = g.node_xy[g.tri[e]].copy()
+        for k in (1, 2):
+            d = xy[k, 0] - xy[0, 0]
+            if g.period_x > 0 and abs(d) > g.period_x / 2:
+                xy[k, 0] -= np.sign(d) * g.period_x
+        lam = rng.dirichlet([2, 2, 2], size=n_per)
+        p = lam @ xy
+        xs.append(np.mod(p[:, 0], g.period_x) if g.period_x > 0 else p[:, 0])
+        ys.append(p[:, 1])
+        es.append(np.full(n_per, e, dtype=np.int32))
+    n = n_per * len(elems)
+    u, v, w = rng.normal(1.0, 0.3, n), rng.normal(0.0, 0.2, n), rng.normal(0.0, 0.25, n)
+    return dict(x=np.concatenate(xs), y=np.concatenate(ys), u=u, v=v, w=w,
+                om=np.full(n, 1.0), psi=psi_fn(u, v, w), elem=np.concatenate(es))
+
+
+def test_fox_projection_orders_by_the_scalar_when_it_is_linear_in_velocity():
+    """Eqs. 64-66: if phi' = c . u' exactly, alpha_a / s_a = c_a / s_phi, so the projected
+    velocity is phi' / s_phi and the N_c conditional means are the means of the quantile
+    groups of psi (sorted psi cut into N_c equal intervals)."""
+    w = synth.workload("channel_tiny")
+    g = w["grid"]
+    rng = np.random.default_rng(41)
+    elems = [5, 20, 33]
+    st = _element_state(g, elems, 60, rng, lambda u, v, w_: 0.3 + 0.5 * u - 0.2 * v + 0.1 * w_)
+    P = dict(w["params"], cond_mode=1, fox_bins=5, min_per_bin=2)
+    o = oracle.Oracle(g, P, w["fields"])
+    o.set_particles(st, 0)
+    vc, gb = o.bins()
+    for e in elems:
+        psi = np.sort(st["psi"][st["elem"] == e])
+        n = psi.shape[0]
+        assert tuple(gb[e]) == (5, 1, 1)
+        for i in range(5):
+            lo, hi = -(-i * n // 5), -(-(i + 1) * n // 5)
+            assert abs(vc[e, i] - psi[lo:hi].mean()) <= 1e-12
+        assert np.all(np.diff(vc[e, :5]) > 0)
+
+
+def test_fox_projection_degenerates_to_id_order_without_scalar_variance():
+    """psi constant: s_phi = 0, alpha = 0, every particle has U_rho = 0 and the intervals
+    follow particle ids; conditional means equal the constant."""
+    w = synth.workload("channel_tiny")
+    g = w["grid"]
+    rng = np.random.default_rng(42)
+    st = _element_state(g, [7], 40, rng, lambda u, v, w_: np.full(u.shape, 0.25))
+    P = dict(w["params"], cond_mode=1, fox_bins=4, min_per_bin=2)
+    o = oracle.Oracle(g, P, w["fields"])
+    o.set_particles(st, 0)
+    vc, gb = o.bins()
+    assert tuple(gb[7]) == (4, 1, 1)
+    assert np.all(vc[7, :4] == 0.25)
+    cp = o.get_particles()["cp"]
+    assert np.array_equal(cp, (4 * np.arange(40)) // 40)
