@@ -388,6 +388,7 @@ def main():
     ap.add_argument("--no-batch", action="store_true")
     ap.add_argument("--no-canyon", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
+    ap.add_argument("--no-fox", action="store_true")
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=16)
     ap.add_argument("--ppe", type=int, default=None,
@@ -421,6 +422,17 @@ def main():
         cb, rb64 = time_form(torch, B, w, 1, args, rank, world, dist, with_clock=False,
                              extra={"acc64": 1})
         cb.close()
+    rf = None
+    if not args.no_fox:
+        # Fox's projection conditioning (Eqs. 64-66) in place of the hierarchical bins, as
+        # many intervals as the hierarchical form has bins
+        nbins = 1
+        for b in w["params"]["bins"]:
+            nbins *= b
+        cf, rf = time_form(torch, B, w, 1, args, rank, world, dist, with_clock=False,
+                           extra={"cond_mode": 1, "fox_bins": nbins})
+        cf.close()
+        rf["fox_bins"] = nbins
     rb = None
     if not args.no_batch:
         rb = batched_form(torch, B, synth, args)
@@ -500,6 +512,15 @@ def main():
                 "C_fp32_sde_compensated_fp32_accumulation": {
                     "value": value, "unit": UNIT,
                     "errors": precision_study(r32["nodal"], r64["nodal"])}}}
+    if rf is not None:
+        vF = rf["np"] * world * args.steps / (rf["ms"] * 1e-3)
+        line["fox_form"] = {
+            "what": "FP32 form with Fox's projection conditioning (Eqs. 64-66), N_c = %d "
+                    "intervals, in place of the hierarchical bins" % rf["fox_bins"],
+            "value": vF, "unit": UNIT, "ms_per_step": rf["ms"] / args.steps,
+            "stages_ms_per_step": {n: rf["stage_ms"][i] / max(rf["stage_n"][i], 1)
+                                   for i, n in enumerate(STAGES)},
+            "vs_hierarchical": vF / value, "device_errors": rf["err"]}
     if rc is not None:
         line["street_canyon"] = rc
     if rb is not None:

@@ -88,6 +88,10 @@ typedef struct pdfx_params {
     int    sort_every;        /* re-order particles by element every this many steps */
     int    acc64;             /* FP32 form: 1 accumulates element moments and conditional
                                  means in FP64, 0 (default) in compensated FP32 */
+    int    cond_mode;         /* velocity conditioning of the scalar mean: 0 hierarchical
+                                 bins (Sect. 3.5, Appendix A); 1 Fox's projection (Eqs.
+                                 64-66) onto fox_bins intervals of the projected velocity */
+    int    fox_bins;          /* 1..256 (cond_mode 1) */
 } pdfx_params;
 
 typedef struct pdfx_allocator {
@@ -126,8 +130,8 @@ int  pdfx_create(const pdfx_params *p, const pdfx_allocator *alloc, void **out_c
 /* Releases all device memory of the context (synchronises the device first). */
 void pdfx_destroy(void *ctx);
 
-/* Replaces the model parameters (everything except bins, precision, sort_every and acc64,
- * which are fixed at creation).  Host pointer.  PDFX_ERR_ARG if those differ, and for a batch of
+/* Replaces the model parameters (everything except bins, precision, sort_every, acc64,
+ * cond_mode and fox_bins, which are fixed at creation).  Host pointer.  PDFX_ERR_ARG if those differ, and for a batch of
  * more than one instance (its parameters come from pdfx_set_instances). */
 int  pdfx_set_params(void *ctx, const pdfx_params *p);
 
@@ -135,7 +139,8 @@ int  pdfx_set_params(void *ctx, const pdfx_params *p);
  * of the method on its own grid, and a batch steps them all with one launch per stage).
  * Call before pdfx_set_grid.  n instances; p[n] their parameters (host, copied): each may
  * have its own constants, seed, instance number, source, period_x and MINNPEL, while
- * precision, sort_every, acc64, bins and min_per_bin must equal the context's (else
+ * precision, sort_every, acc64, bins, min_per_bin, cond_mode and fox_bins must equal the
+ * context's (else
  * PDFX_ERR_ARG).  elem_first[n + 1] (host): instance k owns the elements elem_first[k] ..
  * elem_first[k + 1] - 1 of the union grid that pdfx_set_grid receives next (elem_first[0]
  * = 0, increasing, elem_first[n] = its ne; the instances may share no edge and no node,

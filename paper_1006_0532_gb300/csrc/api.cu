@@ -66,6 +66,8 @@ bool params_valid(const pdfx_params& p) {
   if (p.precision != 0 && p.precision != 1) return false;
   if (p.sort_every < 0 || !(p.nu >= 0.0) || !(p.period_x >= 0.0)) return false;
   if (p.acc64 != 0 && p.acc64 != 1) return false;
+  if (p.cond_mode != 0 && p.cond_mode != 1) return false;
+  if (p.cond_mode == 1 && (p.fox_bins < 1 || p.fox_bins > 256)) return false;
   return true;
 }
 
@@ -307,6 +309,8 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
     a.gbin = c.gbin;
     a.step_inc = allow_moves ? c.dstep : nullptr;   // only a step advances the counter
     a.acc64 = c.prm.acc64;
+    a.cond_mode = c.prm.cond_mode;
+    a.fox_bins = c.prm.fox_bins;
     a.diag = c.diag;
     a.err = c.err;
     launch_stats<T>(a, c.num_sms, s);
@@ -890,6 +894,8 @@ void pdfx_default_params(pdfx_params* p) {
   p->tm_mode = 0; p->Cs = 0.02; p->Ct = 0.7; p->Cphi = 2.0;
   p->src_x = 0.5; p->src_y = 0.5; p->src_r = 0.02;
   p->bins[0] = p->bins[1] = p->bins[2] = 4;
+  p->cond_mode = 0;
+  p->fox_bins = 5;
   p->min_per_bin = 2;
   p->minnpel = 0;
   p->interp_mode = 0;
@@ -912,7 +918,7 @@ int pdfx_create(const pdfx_params* p, const pdfx_allocator* alloc, void** out) {
     c->alloc = *alloc;
     c->has_alloc = true;
   }
-  c->G = p->bins[0] * p->bins[1] * p->bins[2];
+  c->G = p->cond_mode == 1 ? p->fox_bins : p->bins[0] * p->bins[1] * p->bins[2];
   if (cudaGetDevice(&c->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
     delete c;
@@ -957,7 +963,8 @@ int pdfx_set_params(void* ctx, const pdfx_params* p) {
   Ctx* c = as_ctx(ctx);
   if (!c || !p || !params_valid(*p)) return PDFX_ERR_ARG;
   if (p->precision != c->prm.precision || p->sort_every != c->prm.sort_every ||
-      p->acc64 != c->prm.acc64 ||
+      p->acc64 != c->prm.acc64 || p->cond_mode != c->prm.cond_mode ||
+      (p->cond_mode == 1 && p->fox_bins != c->prm.fox_bins) ||
       p->bins[0] != c->prm.bins[0] || p->bins[1] != c->prm.bins[1] || p->bins[2] != c->prm.bins[2])
     return PDFX_ERR_ARG;
   if (c->have_grid && p->period_x != c->prm.period_x) return PDFX_ERR_ARG;
@@ -976,7 +983,8 @@ int pdfx_set_instances(void* ctx, int32_t n, const pdfx_params* p, const int32_t
     if (p[k].precision != c->prm.precision || p[k].sort_every != c->prm.sort_every ||
         p[k].bins[0] != c->prm.bins[0] || p[k].bins[1] != c->prm.bins[1] ||
         p[k].bins[2] != c->prm.bins[2] || p[k].min_per_bin != c->prm.min_per_bin ||
-        p[k].acc64 != c->prm.acc64)
+        p[k].acc64 != c->prm.acc64 || p[k].cond_mode != c->prm.cond_mode ||
+        (p[k].cond_mode == 1 && p[k].fox_bins != c->prm.fox_bins))
       return PDFX_ERR_ARG;
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return PDFX_ERR_CUDA;

@@ -234,6 +234,13 @@ __device__ __forceinline__ int mom_nib(uint64_t tab, int c) {
   return static_cast<int>((tab >> (4 * c)) & 15u);
 }
 
+// Source of Fox's projected velocity (Eq. 64): factors f_a, means <U_a>, component arrays.
+template <typename T>
+struct ProjSrc {
+  double f[3], m[3];
+  const T* c[3];
+};
+
 // Shared tile of one element.  Chunk tables are needed only when groups exceed 32
 // positions: then there are fewer than CAP/32 groups and fewer than 2 CAP/32 chunks.
 template <typename T, int CAP>
@@ -249,7 +256,10 @@ struct Tile {
   int tie[3];                       // a tie was found at level l (fast pass)
   int32_t gfc[CAP / 32 + 1];        // first chunk of each group
   uint8_t cg[kChunks];              // group of each chunk
-  double mh[12], ml[12], msh[5];    // moment sums (value/error pairs) and shift values
+  double mh[15], ml[15], msh[5];    // moment sums (value/error pairs) and shift values
+  double em[kNS];                   // the element's statistics (Fox's projection needs them)
+  double fox[6];                    // projection factors f_a and means <U_a> (Eqs. 64-66)
+  ProjSrc<T> proj;                  // the projected velocity's source (Fox's projection)
   int n_gathered;
 };
 
@@ -258,9 +268,9 @@ struct Tile {
 // warp sort; otherwise chunks of 32 (tables t.gfc, t.cg) are sorted, then ranked across the
 // group's chunks.  The fast pass (EXACT false) sets *tie when two real keys of a group are
 // equal; its ranks never leave the group, so nxt stays within bounds either way.
-template <typename T, int CAP, int THREADS, bool EXACT, typename Arr>
+template <typename T, int CAP, int THREADS, bool EXACT, typename Arr, typename ValFn>
 __device__ void sort_level(const StatsArgs<T>& a, Tile<T, CAP>& t, Arr& sk, const int32_t* cur,
-                           int32_t* nxt, const T* val, int n, int Gprev, int M, float invG,
+                           int32_t* nxt, const ValFn& val, int n, int Gprev, int M, float invG,
                            int* tie) {
   using P = KeyPolicy<T, EXACT>;
   using K = typename P::K;
@@ -274,7 +284,7 @@ __device__ void sort_level(const StatsArgs<T>& a, Tile<T, CAP>& t, Arr& sk, cons
       int32_t q = -1;
       if (lane < len) {
         q = cur[gs + lane];
-        k = P::make(val[q], a.p.pid, q);
+        k = P::make(val(q), a.p.pid, q);
       } else {
         pad_key(k);
       }
@@ -295,7 +305,7 @@ __device__ void sort_level(const StatsArgs<T>& a, Tile<T, CAP>& t, Arr& sk, cons
       int32_t q = -1;
       if (lane < len) {
         q = cur[cs + lane];
-        k = P::make(val[q], a.p.pid, q);
+        k = P::make(val(q), a.p.pid, q);
       } else {
         pad_key(k);
       }
@@ -332,32 +342,53 @@ __device__ void sort_level(const StatsArgs<T>& a, Tile<T, CAP>& t, Arr& sk, cons
   }
 }
 
+// Key value of a particle at one level: a velocity component (val), or Fox's projected
+// velocity sum_a f_a (U_a - <U_a>) (Eq. 64, computed in FP64, rounded to the state
+// precision) from the factors, means and component arrays in shared memory (proj).
+template <typename T>
+struct KeySrc {
+  const T* val;
+  const ProjSrc<T>* proj;   // nullptr: val
+  __device__ __forceinline__ T operator()(int32_t q) const {
+    if (!proj) return val[q];
+    return static_cast<T>(proj->f[0] * (static_cast<double>(proj->c[0][q]) - proj->m[0]) +
+                          proj->f[1] * (static_cast<double>(proj->c[1][q]) - proj->m[1]) +
+                          proj->f[2] * (static_cast<double>(proj->c[2][q]) - proj->m[2]));
+  }
+};
+
 // Sect. 3.3, Eqs. 35-36, by warp 0 in the order cur: sums of d = x - x_0 and of products of
 // d in precision A, x_0 the first particle of the order; mean = x_0 + S1/N, central =
 // S2/N - (S1/N)^2; lanes combine as value/error pairs (FP32) or in FP64, then the 13
-// outputs are formed in FP64, one per lane.
-template <typename A, typename T, int CAP>
-__device__ void element_moments(const StatsArgs<T>& a, Tile<T, CAP>& t, const int32_t* cur, int n,
-                                int e, const int (&g)[3]) {
+// outputs are formed in FP64, one per lane.  Inlined: as an out-of-line call it measured
+// slower (its spills and the call outweigh the spills it saves in the sorting loops).
+template <typename A, bool FOX, typename T, int CAP>
+__device__ __forceinline__ void element_moments(const T* __restrict__ pu, const T* __restrict__ pv,
+                                             const T* __restrict__ pw, const T* __restrict__ pom,
+                                             const T* __restrict__ ppsi, double* emom_e,
+                                             int32_t* gbin_e, Tile<T, CAP>& t, const int32_t* cur,
+                                             int n, int g0, int g1, int g2) {
+  constexpr int NSUM = FOX ? 15 : 12;
   const int lane = threadIdx.x & 31;
   A sh[5] = {A(0), A(0), A(0), A(0), A(0)};
   if (n > 0) {
     const int32_t q0 = cur[0];
-    sh[0] = A(a.p.u[q0]); sh[1] = A(a.p.v[q0]); sh[2] = A(a.p.w[q0]);
-    sh[3] = A(a.p.om[q0]); sh[4] = A(a.p.psi[q0]);
+    sh[0] = A(pu[q0]); sh[1] = A(pv[q0]); sh[2] = A(pw[q0]);
+    sh[3] = A(pom[q0]); sh[4] = A(ppsi[q0]);
   }
-  Acc<A> m[12];
+  Acc<A> m[NSUM];
   for (int p = lane; p < n; p += 32) {
     const int32_t q = cur[p];
-    const A du = A(a.p.u[q]) - sh[0], dv = A(a.p.v[q]) - sh[1], dw = A(a.p.w[q]) - sh[2];
-    const A dom = A(a.p.om[q]) - sh[3], dp = A(a.p.psi[q]) - sh[4];
+    const A du = A(pu[q]) - sh[0], dv = A(pv[q]) - sh[1], dw = A(pw[q]) - sh[2];
+    const A dom = A(pom[q]) - sh[3], dp = A(ppsi[q]) - sh[4];
     m[0].add(du); m[1].add(dv); m[2].add(dw); m[3].add(dom); m[4].add(dp);
     m[5].add(du * du); m[6].add(dv * dv); m[7].add(dw * dw);
     m[8].add(du * dv); m[9].add(du * dw); m[10].add(dv * dw);
     m[11].add(dp * dp);
+    if (FOX) { m[12 % NSUM].add(du * dp); m[13 % NSUM].add(dv * dp); m[14 % NSUM].add(dw * dp); }
   }
 #pragma unroll
-  for (int c = 0; c < 12; ++c) {
+  for (int c = 0; c < NSUM; ++c) {
     A h, l;
     m[c].warp_pair(h, l);
     if (lane == c) { t.mh[c] = h; t.ml[c] = l; }
@@ -378,13 +409,43 @@ __device__ void element_moments(const StatsArgs<T>& a, Tile<T, CAP>& t, const in
     }
     if (lane == 0) v = static_cast<double>(n);
     else if (n == 0) v = 0.0;
-    a.emom[static_cast<size_t>(kNS) * e + lane] = v;
+    emom_e[lane] = v;
+    if (FOX) t.em[lane] = v;
   }
-  if (lane < 3) a.gbin[3 * e + lane] = lane == 0 ? g[0] : lane == 1 ? g[1] : g[2];
+  if (lane < 3) gbin_e[lane] = lane == 0 ? g0 : lane == 1 ? g1 : g2;
+  if (FOX) {
+    __syncwarp();
+    if (lane == 0) {
+      // <u_a phi'> = S(d_a d_phi)/N - (S d_a/N)(S d_phi/N); then Eqs. 65-66
+      const double inv = n > 0 ? 1.0 / n : 0.0;
+      const double sp = (t.mh[4] + t.ml[4]) * inv;
+      double uphi[3], f[3];
+      for (int k = 0; k < 3; ++k)
+        uphi[k] = (t.mh[12 + k] + t.ml[12 + k]) * inv - (t.mh[k] + t.ml[k]) * inv * sp;
+      fox_factors(t.em, uphi, f);
+      for (int k = 0; k < 3; ++k) { t.fox[k] = f[k]; t.fox[3 + k] = t.em[1 + k]; }
+    }
+  }
+}
+
+// Moments in the state precision (FP32 form: compensated) or, with acc64 in the FP32
+// form, in FP64.
+template <bool FOX, typename T, int CAP>
+__device__ __forceinline__ void element_moments_of(const StatsArgs<T>& a, Tile<T, CAP>& t,
+                                                   const int32_t* cur, int n, int e,
+                                                   const int (&g)[3]) {
+  double* const emom_e = a.emom + static_cast<size_t>(kNS) * e;
+  int32_t* const gbin_e = a.gbin + 3 * e;
+  if (sizeof(T) == 4 && a.acc64)
+    element_moments<double, FOX>(a.p.u, a.p.v, a.p.w, a.p.om, a.p.psi, emom_e, gbin_e, t, cur, n,
+                                 g[0], g[1], g[2]);
+  else
+    element_moments<T, FOX>(a.p.u, a.p.v, a.p.w, a.p.om, a.p.psi, emom_e, gbin_e, t, cur, n,
+                            g[0], g[1], g[2]);
 }
 
 // One element of N <= CAP particles (list size after redistribution) by a block of THREADS.
-template <typename T, int CAP, int THREADS>
+template <typename T, int CAP, int THREADS, bool FOX>
 __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int N, int moves) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned below = (1u << lane) - 1u;
@@ -429,9 +490,16 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int 
   if (n != N && threadIdx.x == 0) atomicCAS(a.err, 0, PDFX_ERR_CAPACITY);
   n = min(min(n, N), CAP);
 
-  // effective bins (reading of Sect. 3.5): g_l = max(1, min(b_l, n / (g_1..g_{l-1} min_per_bin)))
+  // effective bins (reading of Sect. 3.5): g_l = max(1, min(b_l, n / (g_1..g_{l-1} min_per_bin)));
+  // Fox's projection: max(1, min(fox_bins, n / min_per_bin)) intervals
+  constexpr bool fox = FOX;   // Fox's projection (cond_mode 1) or hierarchical bins
   int g[3];
-  {
+  if (fox) {
+    int nc = n / a.min_per_bin;
+    if (a.fox_bins < nc) nc = a.fox_bins;
+    g[0] = nc < 1 ? 1 : nc;
+    g[1] = g[2] = 1;
+  } else {
     int Gp = 1;
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
@@ -445,50 +513,74 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int 
 
   int32_t* cur = t.ord;
   int32_t* nxt = t.nord;
-  int Gprev = 1;
-  if (n > 0) {
-#pragma unroll 1
-    for (int l = 0; l < 3; ++l) {
-      if (l > 0 && g[l] <= 1) continue;
-      const T* val = l == 0 ? a.p.u : (l == 1 ? a.p.v : a.p.w);
-      const int M = (n + Gprev - 1) / Gprev;   // largest group
-      const float invG = 1.0f / static_cast<float>(Gprev);
-      if (M > 32 && warp == 0) {
-        // chunk tables: Gprev < n / 32 <= CAP / 32 <= 32 groups, one lane each
-        int nch = 0;
-        if (lane < Gprev) nch = (group_start(lane + 1, n, Gprev, invG) - group_start(lane, n, Gprev, invG) + 31) >> 5;
-        int incl = nch;
+  // one sorting level over Gprev groups of the current order, keys from val(q)
+  auto run_level = [&](const KeySrc<T>& val, int Gprev, int ti) {
+    const int M = (n + Gprev - 1) / Gprev;   // largest group
+    const float invG = 1.0f / static_cast<float>(Gprev);
+    if (M > 32 && warp == 0) {
+      // chunk tables: Gprev < n / 32 <= CAP / 32 <= 32 groups, one lane each
+      int nch = 0;
+      if (lane < Gprev) nch = (group_start(lane + 1, n, Gprev, invG) - group_start(lane, n, Gprev, invG) + 31) >> 5;
+      int incl = nch;
 #pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-          const int y = __shfl_up_sync(kFull, incl, o);
-          if (lane >= o) incl += y;
-        }
-        if (lane < Gprev) {
-          t.gfc[lane] = incl - nch;
-          for (int j = 0; j < nch; ++j) t.cg[incl - nch + j] = static_cast<uint8_t>(lane);
-        }
-        if (lane == Gprev - 1) t.gfc[Gprev] = incl;
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(kFull, incl, o);
+        if (lane >= o) incl += y;
       }
+      if (lane < Gprev) {
+        t.gfc[lane] = incl - nch;
+        for (int j = 0; j < nch; ++j) t.cg[incl - nch + j] = static_cast<uint8_t>(lane);
+      }
+      if (lane == Gprev - 1) t.gfc[Gprev] = incl;
+    }
+    __syncthreads();
+    sort_level<T, CAP, THREADS, false>(a, t, t.sk.fast, cur, nxt, val, n, Gprev, M, invG, &t.tie[ti]);
+    __syncthreads();
+    if (t.tie[ti]) {
+      sort_level<T, CAP, THREADS, true>(a, t, t.sk.exact, cur, nxt, val, n, Gprev, M, invG, nullptr);
       __syncthreads();
-      sort_level<T, CAP, THREADS, false>(a, t, t.sk.fast, cur, nxt, val, n, Gprev, M, invG, &t.tie[l]);
-      __syncthreads();
-      if (t.tie[l]) {
-        sort_level<T, CAP, THREADS, true>(a, t, t.sk.exact, cur, nxt, val, n, Gprev, M, invG, nullptr);
+    }
+    int32_t* tmp = cur;
+    cur = nxt;
+    nxt = tmp;
+  };
+  if (n > 0) {
+    KeySrc<T> src{a.p.u, nullptr};
+    // hierarchical: levels by u, v, w; Fox's projection (Eqs. 64-66): the (u, id) order for
+    // the moments, then the order of the projected velocity
+    const int levels = fox ? 2 : 3;
+    int Gprev = 1;
+#pragma unroll 1
+    for (int l = 0; l < levels; ++l) {
+      if (!fox && l > 0 && g[l] <= 1) continue;
+      if constexpr (FOX) {
+        if (l == 1) {
+        if (warp == 0) {
+          element_moments_of<true>(a, t, cur, n, e, g);
+        }
+        if (threadIdx.x < 3) {
+          const int k = threadIdx.x;
+          t.proj.f[k] = t.fox[k];
+          t.proj.m[k] = t.fox[3 + k];
+          t.proj.c[k] = k == 0 ? a.p.u : (k == 1 ? a.p.v : a.p.w);
+        }
         __syncthreads();
+        src.proj = &t.proj;
+        }
+      } else {
+        src.val = l == 0 ? a.p.u : (l == 1 ? a.p.v : a.p.w);
       }
-      int32_t* tmp = cur;
-      cur = nxt;
-      nxt = tmp;
-      Gprev *= g[l];
+      run_level(src, fox ? 1 : Gprev, l);
+      if (!fox) Gprev *= g[l];
     }
   }
   const int G = g[0] * g[1] * g[2];
 
   // moments (warp 0) in the final order, accumulated in the state precision (FP32 form:
-  // compensated) or, with acc64 in the FP32 form, in FP64
-  if (warp == 0) {
-    if (sizeof(T) == 4 && a.acc64) element_moments<double>(a, t, cur, n, e, g);
-    else element_moments<T>(a, t, cur, n, e, g);
+  // compensated) or, with acc64 in the FP32 form, in FP64 (Fox's projection: done above;
+  // an empty element still writes its zeros and bins)
+  if (warp == 0 && (!fox || n == 0)) {
+    element_moments_of<false>(a, t, cur, n, e, g);
   }
 
   // Appendix A bins: conditional scalar means over the final order's bins
@@ -538,7 +630,7 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int 
 // kTileSplit particles (FRONT) or of kTileSplit + 1 .. kSmallCap (the back of each
 // instance's list).  The grid covers every element; blocks past the class count return.  The register cap
 // keeps 1536 threads resident per SM in the FP32 form, 1024 in the FP64 form.
-template <typename T, int CAP, int THREADS, bool FRONT>
+template <typename T, int CAP, int THREADS, bool FRONT, bool FOX>
 __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1536 : 1024) / THREADS)
     stats_tile_kernel(const StatsArgs<T> a) {
   __shared__ Tile<T, CAP> t;
@@ -553,7 +645,7 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1536 : 1024) / THRE
   const int moves = sc[0] > 0;
   const int e = a.tiles[b];
   const int N = moves ? a.fin[e] : a.cnt[e];
-  element_tile<T, CAP, THREADS>(a, t, e, min(N, CAP), moves);
+  element_tile<T, CAP, THREADS, FOX>(a, t, e, min(N, CAP), moves);
 }
 
 }  // namespace
@@ -565,8 +657,13 @@ void launch_stats_tiles_impl(const StatsArgs<T>& a, int num_sms, cudaStream_t s)
   // elements of up to 512 particles (4 warps), then 513..1024 (8 warps)
   (void)num_sms;
   const unsigned grid = static_cast<unsigned>(a.ne);
-  stats_tile_kernel<T, 512, 128, true><<<grid, 128, 0, s>>>(a);
-  stats_tile_kernel<T, 1024, 256, false><<<grid, 256, 0, s>>>(a);
+  if (a.cond_mode == 1) {
+    stats_tile_kernel<T, 512, 128, true, true><<<grid, 128, 0, s>>>(a);
+    stats_tile_kernel<T, 1024, 256, false, true><<<grid, 256, 0, s>>>(a);
+  } else {
+    stats_tile_kernel<T, 512, 128, true, false><<<grid, 128, 0, s>>>(a);
+    stats_tile_kernel<T, 1024, 256, false, false><<<grid, 256, 0, s>>>(a);
+  }
 }
 
 }  // namespace pdfx

@@ -520,7 +520,7 @@ __device__ void block_sums(double (&v)[NV], double* red /* [32 * NV] */) {
 template <typename T>
 __device__ void process_element(const StatsArgs<T>& a, int e, int N, int cap, unsigned char* raw,
                                 int moves) {
-  __shared__ double red[32 * 8 + 8];
+  __shared__ double red[32 * 10 + 10];
   __shared__ int sh_n;
   // smem carve-up for cap entries
   StatsSmem<T> s;
@@ -574,9 +574,16 @@ __device__ void process_element(const StatsArgs<T>& a, int e, int N, int cap, un
   for (int j = tid; j < P; j += blockDim.x) s.perm[j] = static_cast<uint16_t>(j);
   __syncthreads();
 
-  // effective bins (Sect. 3.5 reading): g_l = max(1, min(b_l, n / (g_1..g_{l-1} min_per_bin)))
+  // effective bins (Sect. 3.5 reading): g_l = max(1, min(b_l, n / (g_1..g_{l-1} min_per_bin)));
+  // Fox's projection (Eqs. 64-66): max(1, min(fox_bins, n / min_per_bin)) intervals
+  const bool fox = a.cond_mode == 1;
   int g[3];
-  {
+  if (fox) {
+    int nc = n / a.min_per_bin;
+    if (a.fox_bins < nc) nc = a.fox_bins;
+    g[0] = nc < 1 ? 1 : nc;
+    g[1] = g[2] = 1;
+  } else {
     int Gp = 1;
     for (int l = 0; l < 3; ++l) {
       int cap_l = n / (Gp * a.min_per_bin);
@@ -603,7 +610,7 @@ __device__ void process_element(const StatsArgs<T>& a, int e, int N, int cap, un
     block_sums<5>(m, red);
     const double inv = n > 0 ? 1.0 / n : 0.0;
     const double mu = m[0] * inv, mv = m[1] * inv, mw = m[2] * inv, mo = m[3] * inv, mp = m[4] * inv;
-    double c2[7] = {0, 0, 0, 0, 0, 0, 0};
+    double c2[10] = {0, 0, 0, 0, 0, 0, 0, 0, 0, 0};
     for (int j = tid; j < n; j += blockDim.x) {
       const int q = s.perm[j];
       const double du = static_cast<double>(s.u[q]) - mu, dv = static_cast<double>(s.v[q]) - mv,
@@ -611,8 +618,10 @@ __device__ void process_element(const StatsArgs<T>& a, int e, int N, int cap, un
       c2[0] += du * du; c2[1] += dv * dv; c2[2] += dw * dw;
       c2[3] += du * dv; c2[4] += du * dw; c2[5] += dv * dw;
       c2[6] += dp * dp;
+      c2[7] += du * dp; c2[8] += dv * dp; c2[9] += dw * dp;
     }
-    block_sums<7>(c2, red);
+    block_sums<10>(c2, red);
+    __shared__ double fox_f[3], fox_m[3];
     if (tid == 0) {
       double* em = a.emom + static_cast<size_t>(kNS) * e;
       em[0] = static_cast<double>(n);
@@ -622,10 +631,31 @@ __device__ void process_element(const StatsArgs<T>& a, int e, int N, int cap, un
       a.gbin[3 * e] = g[0];
       a.gbin[3 * e + 1] = g[1];
       a.gbin[3 * e + 2] = g[2];
+      if (fox) {
+        double loc[kNS], uphi[3];
+        for (int k = 0; k < kNS; ++k) loc[k] = em[k];
+        for (int k = 0; k < 3; ++k) uphi[k] = c2[7 + k] * inv;
+        fox_factors(loc, uphi, fox_f);
+        fox_m[0] = mu; fox_m[1] = mv; fox_m[2] = mw;
+      }
+    }
+    __syncthreads();
+    if (fox && n > 1) {
+      // Eq. 64: sort once more, one group, by the projected velocity.  Its key takes the
+      // place of omega, whose moments are done; omega is copied out from the particle
+      // arrays, which this kernel does not write.
+      for (int j = tid; j < n; j += blockDim.x) {
+        s.om[j] = static_cast<T>(fox_f[0] * (static_cast<double>(s.u[j]) - fox_m[0]) +
+                                 fox_f[1] * (static_cast<double>(s.v[j]) - fox_m[1]) +
+                                 fox_f[2] * (static_cast<double>(s.w[j]) - fox_m[2]));
+        s.grp[j] = 0;
+      }
+      __syncthreads();
+      bitonic_sort(s, s.om, n, P);
     }
   }
   // levels 2 and 3: sort each group of the previous level by (v, id), then (w, id)
-  {
+  if (!fox) {
     int Gprev = g[0];
     const T* keys[2] = {s.v, s.w};
     for (int l = 1; l < 3; ++l) {
@@ -664,7 +694,7 @@ __device__ void process_element(const StatsArgs<T>& a, int e, int N, int cap, un
       a.out.u[d] = s.u[q];
       a.out.v[d] = s.v[q];
       a.out.w[d] = s.w[q];
-      a.out.om[d] = s.om[q];
+      a.out.om[d] = a.p.om[src];
       a.out.psi[d] = s.psi[q];
       a.out.pid[d] = s.pid[q];
       a.out.elem[d] = e;

@@ -186,3 +186,37 @@ __device__ __forceinline__ void triangle_point(const ElemGeo<T>& g, T s, T t, T 
 }
 
 }  // namespace pdfx
+
+namespace pdfx {
+
+// Fox's projection (Eqs. 64-66): from the element's moments em (layout of the element
+// statistics: 4-6 variances, 7-9 <uv>, <uw>, <vw>, 12 scalar variance) and its scalar-
+// velocity covariances uphi[3], the factors f_a = alpha_a / s_a of the projected velocity
+// U_rho = sum_a f_a (U_a - <U_a>), alpha solving rho_ab alpha_b = rho_a by Cramer's rule;
+// all zero when the scalar or a velocity component has no variance or |det| <= 1e-12.
+__host__ __device__ inline void fox_factors(const double* em, const double* uphi, double f[3]) {
+  f[0] = f[1] = f[2] = 0.0;
+  const double var0 = em[4], var1 = em[5], var2 = em[6], vphi = em[12];
+  if (!(vphi > 0.0) || !(var0 > 0.0) || !(var1 > 0.0) || !(var2 > 0.0)) return;
+  const double s[3] = {sqrt(var0), sqrt(var1), sqrt(var2)}, sphi = sqrt(vphi);
+  const double cuv = em[7], cuw = em[8], cvw = em[9];
+  const double A[3][3] = {{1.0, cuv / (s[0] * s[1]), cuw / (s[0] * s[2])},
+                          {cuv / (s[0] * s[1]), 1.0, cvw / (s[1] * s[2])},
+                          {cuw / (s[0] * s[2]), cvw / (s[1] * s[2]), 1.0}};
+  const double b[3] = {uphi[0] / (s[0] * sphi), uphi[1] / (s[1] * sphi), uphi[2] / (s[2] * sphi)};
+  auto det3 = [](const double M[3][3]) {
+    return M[0][0] * (M[1][1] * M[2][2] - M[1][2] * M[2][1]) -
+           M[0][1] * (M[1][0] * M[2][2] - M[1][2] * M[2][0]) +
+           M[0][2] * (M[1][0] * M[2][1] - M[1][1] * M[2][0]);
+  };
+  const double det = det3(A);
+  if (!(fabs(det) > 1e-12)) return;
+  for (int i = 0; i < 3; ++i) {
+    double M[3][3];
+    for (int r = 0; r < 3; ++r)
+      for (int c = 0; c < 3; ++c) M[r][c] = c == i ? b[r] : A[r][c];
+    f[i] = (det3(M) / det) / s[i];
+  }
+}
+
+}  // namespace pdfx

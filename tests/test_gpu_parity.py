@@ -389,3 +389,99 @@ def test_street_canyon_steps_match_oracle_f64():
     assert dg["wall_hits"] == do["wall_hits"] and dg["wall_hits"] > 0
     assert dg["freeslip_hits"] == do["freeslip_hits"] and dg["freeslip_hits"] > 0
     assert dg["moves"] == do["moves"] and dg["moves"] > 0
+
+
+# ----------------------------------------------------------------------------------------
+# Fox's projection conditioning (Eqs. 64-66)
+# ----------------------------------------------------------------------------------------
+
+def _fox(params, nc=5):
+    return dict(params, cond_mode=1, fox_bins=nc)
+
+
+def test_fox_projection_steps_match_oracle_f64():
+    """Conditioning on the projected velocity of Eq. 64 instead of the hierarchical
+    velocity bins: pointers, effective bins (N_c, 1, 1), conditional means and the states
+    they feed through Eq. 24, 10 steps on 2116 triangles (FP64 form)."""
+    w = synth.workload("channel_2k")
+    g = w["grid"]
+    params = _fox(w["params"])
+    o = oracle.Oracle(g, params, w["fields"])
+    c = gpu_ctx(g, params, w["fields"])
+    o.init_particles(w["ppe"])
+    c.init_particles(w["ppe"])
+    assert np.array_equal(c.get_particles()["cp"], o.get_particles()["cp"])
+    vo, go = o.bins()
+    vg, gg = c.bins()
+    assert np.array_equal(gg, go)
+    assert np.all(gg[:, 1:] == 1) and gg[:, 0].max() == 5
+    compare_stats(vg, vo, 1e-10, stats_layout=False)
+    for _ in range(10):
+        o.step(w["dt"])
+        c.step(w["dt"])
+    so, sg = o.get_particles(), c.get_particles()
+    diff = sg["elem"] != so["elem"]
+    for p in np.where(diff)[0]:
+        assert o.lam(sg["elem"][p], sg["x"][p], sg["y"][p]).min() > -1e-12
+    assert diff.sum() <= 2
+    compare_state(sg, so, g.period_x, 1e-12)
+    if diff.sum() == 0:
+        assert np.array_equal(sg["cp"], so["cp"])
+        vo, go = o.bins()
+        vg, gg = c.bins()
+        assert np.array_equal(gg, go)
+        compare_stats(vg, vo, 1e-10, stats_layout=False)
+    assert c.check() == 0
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fox_projection_large_and_degenerate_elements(precision):
+    """Fox mode through the large-element kernel (1500 and 3000 particles), near-empty
+    elements (N_c = 1) and elements whose scalar is constant (s_phi = 0: alpha = 0, every
+    projected key ties and the particle id orders them)."""
+    w = synth.workload("channel_tiny")
+    g = w["grid"]
+    counts = np.full(g.ne, 40)
+    counts[3] = 1500
+    counts[10] = 3000
+    counts[11] = 0
+    counts[12] = 1
+    counts[13] = 7
+    st = _round32(_imbalanced_state(g, counts, 8))
+    # a scalar correlated with u (nonzero alpha), zero in a few elements (a zero mean and
+    # variance are exact on both sides, however the sums are ordered)
+    st["psi"] = np.clip(0.5 + 4.0 * (st["u"] - 0.9) + 0.1 * st["v"], 0.0, 1.0)
+    for e in (5, 6, 10):
+        st["psi"][st["elem"] == e] = 0.0
+    st = _round32(st)
+    params = _fox(w["params"], nc=8)
+    o = oracle.Oracle(g, params, w["fields"])
+    c = gpu_ctx(g, params, w["fields"], precision=precision)
+    o.set_particles(st, 0)
+    c.set_particles(st, 0)
+    cg, co = c.get_particles()["cp"], o.get_particles()["cp"]
+    vo, go = o.bins()
+    vg, gg = c.bins()
+    assert np.array_equal(gg, go)
+    assert gg[11, 0] == 1 and gg[12, 0] == 1 and gg[3, 0] == 8
+    if precision == 0:
+        assert np.array_equal(cg, co)
+        compare_stats(vg, vo, 1e-10, stats_layout=False)
+    else:
+        # FP32 keys: a pair of particles straddling an interval boundary may swap when
+        # their projected velocities agree to FP32 rounding; such swaps move one interval
+        tie_e = np.isin(st["elem"], (5, 6, 10, 11, 12))
+        assert np.array_equal(cg[tie_e], co[tie_e])
+        d = cg != co
+        assert np.all(np.abs(cg[d].astype(int) - co[d].astype(int)) == 1)
+        assert d.sum() <= 4
+        rows = np.setdiff1d(np.arange(g.ne), np.unique(st["elem"][d]))
+        compare_stats(vg, vo, 1e-6, rows=rows, stats_layout=False)
+    # the degenerate elements are ordered by particle id alone
+    for e in (5, 6, 10):
+        sel = np.where(st["elem"] == e)[0]
+        n, nc = sel.size, go[e, 0]
+        pids = o.pids()[sel]
+        rank = np.argsort(np.argsort(pids, kind="stable"), kind="stable")
+        assert np.array_equal(co[sel], (nc * rank) // n)
+    assert c.check() == 0
