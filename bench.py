@@ -244,6 +244,69 @@ def e2e_form(torch, B, c, w, args):
     return el, nn * 32 * 8, nn * 13 * 8
 
 
+def element_areas(grid):
+    """Triangle areas (x differences taken as minimum images on a periodic grid)."""
+    import numpy as np
+    xy = grid.node_xy[grid.tri]
+    d1 = xy[:, 1] - xy[:, 0]
+    d2 = xy[:, 2] - xy[:, 0]
+    if grid.period_x > 0:
+        L = grid.period_x
+        for d in (d1, d2):
+            d[:, 0] -= L * np.round(d[:, 0] / L)
+    return 0.5 * np.abs(d1[:, 0] * d2[:, 1] - d1[:, 1] * d2[:, 0])
+
+
+def redistribution_study(torch, B, synth, args):
+    """Sect. 3.7, Figs. 4-6: the simplified model of Eqs. 46-47 (alpha = 0.5) on the
+    stretched 1,536-triangle grid, FP32 form, for 50 to 800 initial particles per element
+    with MINNPEL = ppe / 10 (Eq. 51), and at 200 without particle-number control.  Per case:
+    the relative error of the kinetic energy, Eq. 52, delta = (k_c - k_a) / k_a with k_a =
+    3/2 and k_c half the area-weighted spatial average of the element variances, at t = 1,
+    2 and 4; the particles moved per step; and the throughput of the steps."""
+    import numpy as np
+    out = {"what": "Eq. 52 delta at t = 1, 2, 4 (dt 0.01, 400 steps), FP32 form",
+           "cases": {}}
+    for ppe, redist in [(200, False), (50, True), (100, True), (200, True), (400, True),
+                        (800, True)]:
+        w = synth.redistribution_workload("redist_1k", ppe=ppe)
+        p = dict(w["params"], precision=1, sort_every=args.sort_every)
+        if not redist:
+            p["minnpel"] = 0
+        c = B.Context(p)
+        c.set_grid(w["grid"])
+        c.set_fields(w["fields"])
+        c.init_particles(ppe)
+        A = element_areas(w["grid"])
+        dt, blk = w["dt"], 20
+        deltas, moves_prev, ms = {}, 0, 0.0
+        stream = torch.cuda.current_stream()
+        for b in range(400 // blk):
+            ev0 = torch.cuda.Event(enable_timing=True)
+            ev1 = torch.cuda.Event(enable_timing=True)
+            ev0.record(stream)
+            for _ in range(blk):
+                c.step(dt)
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            ms += ev0.elapsed_time(ev1)
+            t = round((b + 1) * blk * dt, 6)
+            if t in (1.0, 2.0, 4.0):
+                em, _ = c.element_stats()
+                kc = 0.5 * float(np.sum(A * (em[:, 4] + em[:, 5] + em[:, 6])) / np.sum(A))
+                deltas["t=%g" % t] = (kc - 1.5) / 1.5
+        d = c.diag()
+        _, cnt = c.element_stats()
+        key = "ppe%d_%s" % (ppe, "minnpel%d" % p["minnpel"] if redist else "no_redistribution")
+        out["cases"][key] = {"delta": deltas, "moves_per_step": d["moves"] / 400.0,
+                             "min_count": int(cnt.min()), "empty_elements": int((cnt == 0).sum()),
+                             "lost": d["lost"], "device_errors": c.check(),
+                             "particles": c.np_,
+                             "value": c.np_ * 400 / (ms * 1e-3), "unit": UNIT}
+        c.close()
+    return out
+
+
 STAT_NAMES = ["N", "U", "V", "W", "uu", "vv", "ww", "uv", "uw", "vw", "omega", "psi", "psi2"]
 
 
@@ -389,6 +452,7 @@ def main():
     ap.add_argument("--no-canyon", action="store_true")
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-fox", action="store_true")
+    ap.add_argument("--no-redist", action="store_true")
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=16)
     ap.add_argument("--ppe", type=int, default=None,
@@ -436,6 +500,9 @@ def main():
     rb = None
     if not args.no_batch:
         rb = batched_form(torch, B, synth, args)
+    rr = None
+    if not args.no_redist and rank == 0:
+        rr = redistribution_study(torch, B, synth, args)
     rc = None
     if not args.no_canyon:
         rc = canyon_form(torch, B, synth, args)
@@ -512,6 +579,8 @@ def main():
                 "C_fp32_sde_compensated_fp32_accumulation": {
                     "value": value, "unit": UNIT,
                     "errors": precision_study(r32["nodal"], r64["nodal"])}}}
+    if rr is not None:
+        line["redistribution_error"] = rr
     if rf is not None:
         vF = rf["np"] * world * args.steps / (rf["ms"] * 1e-3)
         line["fox_form"] = {

@@ -92,6 +92,14 @@ typedef struct pdfx_params {
                                  bins (Sect. 3.5, Appendix A); 1 Fox's projection (Eqs.
                                  64-66) onto fox_bins intervals of the projected velocity */
     int    fox_bins;          /* 1..256 (cond_mode 1) */
+    int    model;             /* particle model: 0 the full model (Eqs. 7, 19, 24, 27, walls
+                                 of Sect. 3.8); 1 the simplified model of Eqs. 46-47 used to
+                                 measure the particle-redistribution error (Sect. 3.7): the
+                                 velocity relaxes to alpha times the particles' own nodal
+                                 mean velocity of the previous statistics pass, the position
+                                 moves with the velocity, omega and psi are kept; the grid may
+                                 have free-slip boundaries but no no-slip walls */
+    double alpha;             /* Eq. 47 (model 1), finite */
 } pdfx_params;
 
 typedef struct pdfx_allocator {

@@ -47,7 +47,7 @@ class Params(C.Structure):
         ("bins", C.c_int * 3), ("min_per_bin", C.c_int), ("minnpel", C.c_int),
         ("interp_mode", C.c_int), ("source_on", C.c_int),
         ("seed", C.c_uint64), ("instance", C.c_uint32), ("period_x", C.c_double),
-        ("cond_mode", C.c_int), ("fox_bins", C.c_int),
+        ("cond_mode", C.c_int), ("fox_bins", C.c_int), ("model", C.c_int), ("alpha", C.c_double),
     ]
 
 
@@ -62,7 +62,7 @@ _DEFAULTS = dict(C1=1.85, C2=0.63, C3=5.0, C4=0.25, CT=6.0, CL=0.134, Ceta=72.0,
                  gamma5=0.1, Cw1=0.5, Cw2=0.73, nu=1e-4, c0_mode=0, C0=0.0, tm_mode=0,
                  Cs=0.02, Ct=0.7, Cphi=2.0, src_x=0.5, src_y=0.5, src_r=0.02, bins=(4, 4, 4),
                  min_per_bin=2, minnpel=0, interp_mode=0, source_on=1, seed=1, instance=0,
-                 period_x=0.0, cond_mode=0, fox_bins=5)
+                 period_x=0.0, cond_mode=0, fox_bins=5, model=0, alpha=0.5)
 
 
 def make_params(d: dict) -> Params:

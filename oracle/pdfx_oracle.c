@@ -272,6 +272,8 @@ static int params_valid(const orc_params *p)
     if (p->bins[0] * p->bins[1] * p->bins[2] > 256 || p->min_per_bin < 1) return 0;
     if (p->cond_mode != 0 && p->cond_mode != 1) return 0;
     if (p->cond_mode == 1 && (p->fox_bins < 1 || p->fox_bins > 256)) return 0;
+    if (p->model != 0 && p->model != 1) return 0;
+    if (!isfinite(p->alpha)) return 0;
     return 1;
 }
 
@@ -531,6 +533,9 @@ static int in_source(const orc_ctx *c, double x, double y)
     return dx * dx + dy * dy <= c->p.src_r * c->p.src_r;
 }
 
+static void finish_particle(orc_ctx *c, int p, int e, double Xn, double Yn, double Un[3],
+                            double wn, double psin);
+
 static void advance_particle(orc_ctx *c, int p, double dt)
 {
     const orc_params *P = &c->p;
@@ -675,28 +680,96 @@ static void advance_particle(orc_ctx *c, int p, double dt)
                             shape, P->C4 * om_w, &ex);
         if (ex) c->diag.gamma_exhausted++;
     }
-    /* Free-slip boundary (Sect. 4.2): perfect reflection, normal velocity reversed. */
-    if (c->fs_type[e] == 2) {
-        double nx = c->fs_nx[e], ny = c->fs_ny[e];
-        double d1 = min_image(Xn - c->fs_px[e], P->period_x) * nx + (Yn - c->fs_py[e]) * ny;
-        if (d1 < 0.0) {
-            c->diag.freeslip_hits++;
-            Xn -= 2.0 * d1 * nx;
-            Yn -= 2.0 * d1 * ny;
-            double un = Un[0] * nx + Un[1] * ny;
-            Un[0] -= 2.0 * un * nx;
-            Un[1] -= 2.0 * un * ny;
+    finish_particle(c, p, e, Xn, Yn, Un, wn, psin);
+}
+
+/* Free-slip reflection (Sect. 4.2): a point behind the boundary line (point px, py, inward
+ * unit normal nx, ny) is mirrored across it and the normal velocity reversed; returns 1 if
+ * it was behind. */
+static int reflect_free_slip(double px, double py, double nx, double ny, double L, double *x,
+                             double *y, double U[3])
+{
+    const double d = min_image(*x - px, L) * nx + (*y - py) * ny;
+    if (!(d < 0.0)) return 0;
+    *x -= 2.0 * d * nx;
+    *y -= 2.0 * d * ny;
+    const double un = U[0] * nx + U[1] * ny;
+    U[0] -= 2.0 * un * nx;
+    U[1] -= 2.0 * un * ny;
+    return 1;
+}
+
+/* The walk of a particle update (Sect. 3.6 as orc_walk).  Reading: when the edge the walk
+ * would cross is a free-slip boundary edge, the particle has passed the boundary beyond its
+ * start element; it is reflected across that edge's own line (Sect. 4.2) and the walk goes
+ * on from the same element, each reflection counting as a hop.  At any other boundary edge,
+ * after HOP_LIMIT hops, or when the point is not strictly behind the free-slip line, the
+ * fall-back and brute force of orc_walk follow. */
+static int walk_particle(orc_ctx *c, int e0, double *x, double *y, double U[3], int *hops,
+                         int *refl)
+{
+    double lam[3];
+    int e = e0;
+    *hops = 0;
+    for (;;) {
+        area_cross(c, e, *x, *y, lam);
+        if (lambda_inside(lam)) return e;
+        if (*hops >= HOP_LIMIT) break;
+        int k = 0;
+        if (lam[1] < lam[k]) k = 1;
+        if (lam[2] < lam[k]) k = 2;
+        int nb = c->nbr[3 * e + k];
+        if (nb < 0) {
+            if (c->tag[3 * e + k] != 2) break;
+            double px, py, nx, ny;
+            edge_line(c, e, k, &px, &py, &nx, &ny);
+            if (!reflect_free_slip(px, py, nx, ny, c->p.period_x, x, y, U)) break;
+            *refl = 1;
+            (*hops)++;
+            continue;
+        }
+        e = nb;
+        (*hops)++;
+    }
+    c->diag.walk_fallback++;
+    int best = -1;
+    for (int kv = 0; kv < 3; ++kv) {
+        int n = c->tri[3 * e0 + kv];
+        for (int i = c->ne_off[n]; i < c->ne_off[n + 1]; ++i) {
+            int f = c->ne_list[i];
+            if (best >= 0 && f >= best) continue;
+            area_cross(c, f, *x, *y, lam);
+            if (lambda_inside(lam)) best = f;
         }
     }
+    if (best >= 0) return best;
+    c->diag.walk_brute++;
+    return orc_brute_locate(c, *x, *y);
+}
+
+/* The end of one particle update in either model: free-slip boundary of the start element
+ * (Sect. 4.2: perfect reflection, normal velocity reversed), periodic wrap, neighbour walk
+ * (Sect. 3.6, with the reflections of walk_particle), source disc, and the store of the new
+ * state.  A particle reflected at all counts once as a free-slip hit. */
+static void finish_particle(orc_ctx *c, int p, int e, double Xn, double Yn, double Un[3],
+                            double wn, double psin)
+{
+    const orc_params *P = &c->p;
+    int refl = 0;
+    if (c->fs_type[e] == 2)
+        refl = reflect_free_slip(c->fs_px[e], c->fs_py[e], c->fs_nx[e], c->fs_ny[e],
+                                 P->period_x, &Xn, &Yn, Un);
     Xn = wrap_x(Xn, P->period_x);
-    if (in_source(c, Xn, Yn)) { psin = 1.0; c->diag.source_hits++; }
 
     /* Sect. 3.6 */
-    int hops;
-    int en = orc_walk(c, e, Xn, Yn, &hops);
+    int hops, wrefl = 0;
+    int en = walk_particle(c, e, &Xn, &Yn, Un, &hops, &wrefl);
     c->diag.hops_total += hops;
     c->diag.hop_hist[hops < 7 ? hops : 7]++;
     if (en < 0) { en = e; c->diag.lost++; }
+    if (wrefl) Xn = wrap_x(Xn, P->period_x);
+    if (refl || wrefl) c->diag.freeslip_hits++;
+    if (in_source(c, Xn, Yn)) { psin = 1.0; c->diag.source_hits++; }
 
     c->x[p] = Xn; c->y[p] = Yn;
     c->u[p] = Un[0]; c->v[p] = Un[1]; c->w[p] = Un[2];
@@ -704,9 +777,48 @@ static void advance_particle(orc_ctx *c, int p, double dt)
     c->elem[p] = en;
 }
 
+/* Eqs. 46-47, the simplified model of the particle-redistribution test (Sect. 3.7):
+ *   dX_i = U_i dt,   dU_i = -(U_i - alpha <U_i>) dt + sqrt(2) dW_i.
+ * Reading: <U_i> is the particles' own mean velocity, the nodal means of the previous
+ * statistics pass interpolated at X^n like every Eulerian statistic at a particle (Sect.
+ * 3.3; interp_mode 1: element average); explicit Euler-Maruyama with both right-hand sides
+ * at time n; dW_i = sqrt(dt) xi_i with xi_1..3 the first three Gaussians of the step's draws;
+ * omega and psi are not changed; the domain has free-slip boundaries and no no-slip walls. */
+static void advance_particle_simple(orc_ctx *c, int p, double dt)
+{
+    const orc_params *P = &c->p;
+    const int e = c->elem[p];
+    double lam[3];
+    if (P->interp_mode == 1) {
+        lam[0] = lam[1] = lam[2] = 1.0 / 3.0;
+    } else {
+        orc_lambda(c, e, c->x[p], c->y[p], lam);
+    }
+    double Um[3];
+    for (int i = 0; i < 3; ++i) {
+        Um[i] = 0.0;
+        for (int k = 0; k < 3; ++k) Um[i] += lam[k] * c->nmom[(size_t)NS * c->tri[3 * e + k] + 1 + i];
+    }
+    double xi[6], eta, eta2;
+    step_draws(P->seed, P->instance, pid_of(c, p), c->step, xi, &eta, &eta2);
+    const double U0[3] = {c->u[p], c->v[p], c->w[p]};
+    double Un[3];
+    for (int i = 0; i < 3; ++i)
+        Un[i] = U0[i] - (U0[i] - P->alpha * Um[i]) * dt + sqrt(2.0 * dt) * xi[i];   /* Eq. 47 */
+    const double Xn = c->x[p] + U0[0] * dt;                                         /* Eq. 46 */
+    const double Yn = c->y[p] + U0[1] * dt;
+    finish_particle(c, p, e, Xn, Yn, Un, c->om[p], c->psi[p]);
+}
+
 int orc_advance(orc_ctx *c, double dt)
 {
     if (!c->x) return -1;
+    if (c->p.model == 1) {
+        for (int e = 0; e < c->ne; ++e)
+            if (c->wall_type[e] > 0) return -2;      /* Eqs. 46-47 define no wall treatment */
+        for (int p = 0; p < c->np; ++p) advance_particle_simple(c, p, dt);
+        return 0;
+    }
     for (int p = 0; p < c->np; ++p) advance_particle(c, p, dt);
     return 0;
 }

@@ -37,6 +37,9 @@ typedef struct orc_params {
     int    cond_mode;          /* 0: hierarchical bins (Sect. 3.5, Appendix A); 1: Fox's
                                   projection (Eqs. 64-66) with fox_bins intervals */
     int    fox_bins;
+    int    model;              /* 0: the full model; 1: the simplified model of Eqs. 46-47
+                                  (particle-redistribution test, Sect. 3.7; no no-slip walls) */
+    double alpha;              /* Eq. 47 */
 } orc_params;
 
 typedef struct orc_diag {

@@ -39,7 +39,7 @@ class Params(C.Structure):
         ("interp_mode", C.c_int), ("source_on", C.c_int),
         ("seed", C.c_uint64), ("instance", C.c_uint32), ("period_x", C.c_double),
         ("precision", C.c_int), ("sort_every", C.c_int), ("acc64", C.c_int),
-        ("cond_mode", C.c_int), ("fox_bins", C.c_int),
+        ("cond_mode", C.c_int), ("fox_bins", C.c_int), ("model", C.c_int), ("alpha", C.c_double),
     ]
 
 

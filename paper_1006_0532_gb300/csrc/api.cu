@@ -68,6 +68,8 @@ bool params_valid(const pdfx_params& p) {
   if (p.acc64 != 0 && p.acc64 != 1) return false;
   if (p.cond_mode != 0 && p.cond_mode != 1) return false;
   if (p.cond_mode == 1 && (p.fox_bins < 1 || p.fox_bins > 256)) return false;
+  if (p.model != 0 && p.model != 1) return false;
+  if (!std::isfinite(p.alpha)) return false;
   return true;
 }
 
@@ -83,6 +85,8 @@ Model<T> model_of(const pdfx_params& p) {
   m.cs_r2 = T(p.Cs * std::cbrt(p.src_r * p.src_r));
   m.c0_mode = p.c0_mode; m.tm_mode = p.tm_mode; m.interp_mode = p.interp_mode;
   m.source_on = p.source_on;
+  m.model = p.model;
+  m.alpha = T(p.alpha);
   return m;
 }
 
@@ -344,12 +348,14 @@ int do_step(Ctx& c, double dt, cudaStream_t s) {
     a.walls = static_cast<const Line<T>*>(c.walls);
     a.wall2 = c.wall2;
     a.fslines = static_cast<const Line<T>*>(c.fslines);
+    a.fsedges = static_cast<const Line<T>*>(c.fsedges);
     a.ne_off = c.ne_off;
     a.ne_list = c.ne_list;
     a.ne = c.ne;
     a.fields = static_cast<const T*>(c.fields);
     a.vcce = c.vcce;
     a.G = c.G;
+    a.nmom = c.nmom;
     a.cnt = c.plan.cnt;
     a.diag = c.diag;
     a.err = c.err;
@@ -470,7 +476,8 @@ int do_get_particles(Ctx& c, pdfx_soa* soa, int on_device, cudaStream_t s) {
 
 template <typename T>
 int upload_grid(Ctx& c, const HostGeo& g, const std::vector<ElemTopo>& topo,
-                const std::vector<double>& walls, const std::vector<double>& fsl) {
+                const std::vector<double>& walls, const std::vector<double>& fsl,
+                const std::vector<double>& fse) {
   const int32_t ne = c.ne;
   std::vector<ElemGeo<T>> hg(static_cast<size_t>(ne));
   for (int32_t e = 0; e < ne; ++e) {
@@ -486,10 +493,11 @@ int upload_grid(Ctx& c, const HostGeo& g, const std::vector<ElemTopo>& topo,
   PDFX_CUDA(cudaMemcpy(c.geo, hg.data(), sizeof(ElemGeo<T>) * ne, cudaMemcpyHostToDevice));
   PDFX_TRY(alloc_into(c, c.topo, static_cast<size_t>(ne)));
   PDFX_CUDA(cudaMemcpy(c.topo, topo.data(), sizeof(ElemTopo) * ne, cudaMemcpyHostToDevice));
-  for (int which = 0; which < 2; ++which) {
-    const std::vector<double>& src = which == 0 ? walls : fsl;
-    void*& dst = which == 0 ? c.walls : c.fslines;
+  for (int which = 0; which < 3; ++which) {
+    const std::vector<double>& src = which == 0 ? walls : (which == 1 ? fsl : fse);
+    void*& dst = which == 0 ? c.walls : (which == 1 ? c.fslines : c.fsedges);
     const size_t nl = src.size() / 4;
+    if (which == 0) c.n_wall_lines = static_cast<int>(nl);
     std::vector<Line<T>> hl(nl ? nl : 1);
     for (size_t i = 0; i < nl; ++i) {
       hl[i].px = T(src[4 * i]); hl[i].py = T(src[4 * i + 1]);
@@ -595,7 +603,7 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
   // the edge's own element, has the element's centroid strictly in front; lines equal to
   // one already taken are skipped; at most two no-slip lines and one free-slip line
   std::vector<ElemTopo> topo(static_cast<size_t>(ne));
-  std::vector<double> walls, fsl;
+  std::vector<double> walls, fsl, fse;
   std::vector<int32_t> wall2(static_cast<size_t>(ne), -1);
   auto same_line = [](const double* p, const double* q) {
     if (p[2] * q[2] + p[3] * q[3] < 1.0 - 1e-9) return false;
@@ -606,6 +614,15 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
     ElemTopo& t = topo[e];
     t.n0 = tri[3 * e]; t.n1 = tri[3 * e + 1]; t.n2 = tri[3 * e + 2];
     t.nb0 = nbr[3 * e]; t.nb1 = nbr[3 * e + 1]; t.nb2 = nbr[3 * e + 2];
+    // a free-slip boundary edge reflects the walk (Sect. 4.2): -2 - (its line's index)
+    for (int k = 0; k < 3; ++k) {
+      if (nbr[3 * e + k] >= 0 || tag[3 * e + k] != 2) continue;
+      double line[4];
+      edge_line_h(g, e, k, line);
+      const int j = static_cast<int>(fse.size() / 4);
+      fse.insert(fse.end(), line, line + 4);
+      (k == 0 ? t.nb0 : (k == 1 ? t.nb1 : t.nb2)) = -2 - j;
+    }
     t.wall = -1;
     t.fslip = -1;
     const double gx = (g.vx[3 * e] + g.vx[3 * e + 1] + g.vx[3 * e + 2]) / 3.0;
@@ -653,8 +670,8 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
   }
   c.nn = nn;
   c.ne = ne;
-  int rc = c.prm.precision == 1 ? upload_grid<float>(c, g, topo, walls, fsl)
-                                : upload_grid<double>(c, g, topo, walls, fsl);
+  int rc = c.prm.precision == 1 ? upload_grid<float>(c, g, topo, walls, fsl, fse)
+                                : upload_grid<double>(c, g, topo, walls, fsl, fse);
   if (rc) return rc;
   PDFX_TRY(alloc_into(c, c.wall2, wall2.size()));
   PDFX_CUDA(cudaMemcpy(c.wall2, wall2.data(), sizeof(int32_t) * wall2.size(), cudaMemcpyHostToDevice));
@@ -876,6 +893,10 @@ int do_autotune(Ctx& c, double dt, cudaStream_t s, int32_t* best_block, int32_t*
 
 Ctx* as_ctx(void* p) { return static_cast<Ctx*>(p); }
 
+// The simplified model of Eqs. 46-47 has no wall treatment: its grid may not have no-slip
+// walls (free-slip boundaries and a periodic direction only).
+bool model_fits_grid(const Ctx& c) { return c.prm.model != 1 || c.n_wall_lines == 0; }
+
 }  // namespace
 }  // namespace pdfx
 
@@ -896,6 +917,8 @@ void pdfx_default_params(pdfx_params* p) {
   p->bins[0] = p->bins[1] = p->bins[2] = 4;
   p->cond_mode = 0;
   p->fox_bins = 5;
+  p->model = 0;
+  p->alpha = 0.5;
   p->min_per_bin = 2;
   p->minnpel = 0;
   p->interp_mode = 0;
@@ -964,7 +987,7 @@ int pdfx_set_params(void* ctx, const pdfx_params* p) {
   if (!c || !p || !params_valid(*p)) return PDFX_ERR_ARG;
   if (p->precision != c->prm.precision || p->sort_every != c->prm.sort_every ||
       p->acc64 != c->prm.acc64 || p->cond_mode != c->prm.cond_mode ||
-      (p->cond_mode == 1 && p->fox_bins != c->prm.fox_bins) ||
+      (p->cond_mode == 1 && p->fox_bins != c->prm.fox_bins) || p->model != c->prm.model ||
       p->bins[0] != c->prm.bins[0] || p->bins[1] != c->prm.bins[1] || p->bins[2] != c->prm.bins[2])
     return PDFX_ERR_ARG;
   if (c->have_grid && p->period_x != c->prm.period_x) return PDFX_ERR_ARG;
@@ -984,7 +1007,7 @@ int pdfx_set_instances(void* ctx, int32_t n, const pdfx_params* p, const int32_t
         p[k].bins[0] != c->prm.bins[0] || p[k].bins[1] != c->prm.bins[1] ||
         p[k].bins[2] != c->prm.bins[2] || p[k].min_per_bin != c->prm.min_per_bin ||
         p[k].acc64 != c->prm.acc64 || p[k].cond_mode != c->prm.cond_mode ||
-        (p[k].cond_mode == 1 && p[k].fox_bins != c->prm.fox_bins))
+        (p[k].cond_mode == 1 && p[k].fox_bins != c->prm.fox_bins) || p[k].model != c->prm.model)
       return PDFX_ERR_ARG;
   }
   if (cudaDeviceSynchronize() != cudaSuccess) return PDFX_ERR_CUDA;
@@ -1117,7 +1140,7 @@ uint32_t pdfx_step_index(const void* ctx) {
 
 int pdfx_step_many(void* ctx, double dt, int32_t nsteps, int use_graph, void* stream) {
   Ctx* c = as_ctx(ctx);
-  if (!c || !(dt > 0.0) || nsteps < 0) return PDFX_ERR_ARG;
+  if (!c || !(dt > 0.0) || nsteps < 0 || !model_fits_grid(*c)) return PDFX_ERR_ARG;
   if (!c->pbuf[0] || !c->have_fields) return PDFX_ERR_ORDER;
   return c->prm.precision == 1 ? do_step_many<float>(*c, dt, nsteps, use_graph, as_stream(stream))
                                : do_step_many<double>(*c, dt, nsteps, use_graph, as_stream(stream));
@@ -1125,7 +1148,7 @@ int pdfx_step_many(void* ctx, double dt, int32_t nsteps, int use_graph, void* st
 
 int pdfx_autotune(void* ctx, double dt, int32_t* adv_block, int32_t* sort_every, void* stream) {
   Ctx* c = as_ctx(ctx);
-  if (!c || !(dt > 0.0)) return PDFX_ERR_ARG;
+  if (!c || !(dt > 0.0) || !model_fits_grid(*c)) return PDFX_ERR_ARG;
   if (!c->pbuf[0] || !c->have_fields || c->np <= 0) return PDFX_ERR_ORDER;
   return c->prm.precision == 1 ? do_autotune<float>(*c, dt, as_stream(stream), adv_block, sort_every)
                                : do_autotune<double>(*c, dt, as_stream(stream), adv_block, sort_every);
@@ -1133,7 +1156,7 @@ int pdfx_autotune(void* ctx, double dt, int32_t* adv_block, int32_t* sort_every,
 
 int pdfx_step(void* ctx, double dt, void* stream) {
   Ctx* c = as_ctx(ctx);
-  if (!c || !(dt > 0.0)) return PDFX_ERR_ARG;
+  if (!c || !(dt > 0.0) || !model_fits_grid(*c)) return PDFX_ERR_ARG;
   if (!c->pbuf[0] || !c->have_fields) return PDFX_ERR_ORDER;
   return c->prm.precision == 1 ? do_step<float>(*c, dt, as_stream(stream))
                                : do_step<double>(*c, dt, as_stream(stream));

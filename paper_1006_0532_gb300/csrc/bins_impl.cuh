@@ -263,11 +263,33 @@ struct Tile {
   int n_gathered;
 };
 
+// Number of keys below k in the sorted run s[base, base + len), len <= R <= RMAX (powers of
+// two); eq tells whether the run holds a key equal to k.
+template <int RMAX, typename Arr, typename K>
+__device__ __forceinline__ int run_count_below(const Arr& s, int base, int len, int R, const K& k,
+                                               bool& eq) {
+  int pos = 0;
+#pragma unroll
+  for (int st = RMAX; st >= 1; st >>= 1) {
+    if (st > R) continue;
+    const int np = pos + st;
+    if (np <= len && kless(s.get(base + np - 1), k)) pos = np;
+  }
+  eq = pos < len && keq(s.get(base + pos), k);
+  return pos;
+}
+
 // One sorting level: the groups of the current order (Gprev groups over n positions, the
 // largest of M) are each ordered by the level's key into nxt.  With M <= 32 a group is one
-// warp sort; otherwise chunks of 32 (tables t.gfc, t.cg) are sorted, then ranked across the
-// group's chunks.  The fast pass (EXACT false) sets *tie when two real keys of a group are
-// equal; its ranks never leave the group, so nxt stays within bounds either way.
+// warp sort; otherwise chunks of 32 (tables t.gfc, t.cg) are sorted first.  Up to 4 chunks
+// per group, a key's rank is its chunk rank plus its count in every other chunk; beyond
+// that, sorted runs (32, 64, 128, ... positions of a group) are merged pairwise, a key's
+// place in the merged run being its place in its own run plus its count in the partner
+// run, with the keys at their group positions in one half of sk and spay and written to
+// the other half (n <= CAP positions each), the last round into nxt.  The fast pass (EXACT
+// false) sets *tie when two real keys of a group are equal; until the first round in which
+// two equal keys meet the runs are exact, so that round's search finds the tie.  Its places
+// never leave the group or run pair, so every index stays within bounds either way.
 template <typename T, int CAP, int THREADS, bool EXACT, typename Arr, typename ValFn>
 __device__ void sort_level(const StatsArgs<T>& a, Tile<T, CAP>& t, Arr& sk, const int32_t* cur,
                            int32_t* nxt, const ValFn& val, int n, int Gprev, int M, float invG,
@@ -294,6 +316,60 @@ __device__ void sort_level(const StatsArgs<T>& a, Tile<T, CAP>& t, Arr& sk, cons
         found |= (lane + 1 < len) && keq(k, nk);
       }
       if (lane < len) nxt[gs + lane] = q;
+    }
+  } else if (M > 256) {
+    const int nchunks = t.gfc[Gprev];
+    for (int c = warp; c < nchunks; c += W) {
+      const int gi = t.cg[c];
+      const int gs = group_start(gi, n, Gprev, invG), ge = group_start(gi + 1, n, Gprev, invG);
+      const int cs = gs + 32 * (c - t.gfc[gi]), len = min(32, ge - cs);
+      K k;
+      int32_t q = -1;
+      if (lane < len) {
+        q = cur[cs + lane];
+        k = P::make(val(q), a.p.pid, q);
+      } else {
+        pad_key(k);
+      }
+      warp_sort32(k, q, lane);
+      if (!EXACT) {
+        const K nk = kdown(k);   // every lane takes part in the shuffle
+        found |= (lane + 1 < len) && keq(k, nk);
+      }
+      if (lane < len) {
+        sk.set(cs + lane, k);
+        t.spay[cs + lane] = q;
+      }
+    }
+    __syncthreads();
+    int src = 0;
+    for (int lgR = 5; (1 << lgR) < M; ++lgR) {
+      const int R = 1 << lgR;
+      const bool last = 2 * R >= M;
+      const int dst = CAP - src;
+      for (int c = warp; c < nchunks; c += W) {
+        const int gi = t.cg[c];
+        const int gs = group_start(gi, n, Gprev, invG), ge = group_start(gi + 1, n, Gprev, invG);
+        const int li = 32 * (c - t.gfc[gi]) + lane;    // position in the group
+        if (li < ge - gs) {
+          const int m = li >> lgR, ps = (m ^ 1) << lgR;   // own run, partner run start
+          const int plen = min(R, ge - gs - ps);        // <= 0: no partner
+          const K k = sk.get(src + gs + li);
+          bool eq = false;
+          const int cnt = plen > 0 ? run_count_below<CAP / 2>(sk, src + gs + ps, plen, R, k, eq) : 0;
+          if (!EXACT) found |= eq;
+          const int np = ((m & ~1) << lgR) + (li - (m << lgR)) + cnt;
+          const int32_t q = t.spay[src + gs + li];
+          if (last) {
+            nxt[gs + np] = q;
+          } else {
+            sk.set(dst + gs + np, k);
+            t.spay[dst + gs + np] = q;
+          }
+        }
+      }
+      __syncthreads();
+      src = dst;
     }
   } else {
     const int nchunks = t.gfc[Gprev];

@@ -23,10 +23,15 @@ __device__ __forceinline__ bool inside(const ElemGeo<T>& g, const ElemTopo& t, T
 }
 
 // Sect. 3.6: walk to the neighbour opposite the lowest area coordinate (ties: lowest local
-// vertex); after kHopLimit hops or at a boundary edge, search the elements around the
-// nodes of the old host element (lowest containing id), then all elements.
+// vertex).  Across a free-slip boundary edge (Sect. 4.2) the particle is reflected across
+// that edge's line, its normal velocity reversed (*refl set), and the walk goes on from the
+// same element; each reflection counts as a hop.  After kHopLimit hops, at any other
+// boundary edge, or when the point is not strictly behind the free-slip line, search the
+// elements around the nodes of the old host element (lowest containing id), then all
+// elements.
 template <typename T>
-__device__ int walk(const AdvanceArgs<T>& a, int e0, T x, T y, T L, int& hops, int& fb, int& brute) {
+__device__ int walk(const AdvanceArgs<T>& a, int e0, T& x, T& y, T (&U)[3], T L, int& hops,
+                    int& fb, int& brute, int& refl) {
   int e = e0;
   hops = 0;
   for (;;) {
@@ -41,7 +46,20 @@ __device__ int walk(const AdvanceArgs<T>& a, int e0, T x, T y, T L, int& hops, i
     if (lb < mn) { k = 1; mn = lb; }
     if (lc < mn) k = 2;
     const int nb = k == 0 ? t.nb0 : (k == 1 ? t.nb1 : t.nb2);
-    if (nb < 0) break;
+    if (nb < 0) {
+      if (nb == -1) break;
+      const Line<T> ln = a.fsedges[-2 - nb];
+      const T d = min_image(x - ln.px, L) * ln.nx + (y - ln.py) * ln.ny;
+      if (!(d < T(0))) break;
+      x -= T(2) * d * ln.nx;
+      y -= T(2) * d * ln.ny;
+      const T un = U[0] * ln.nx + U[1] * ln.ny;
+      U[0] -= T(2) * un * ln.nx;
+      U[1] -= T(2) * un * ln.ny;
+      refl = 1;
+      ++hops;
+      continue;
+    }
     e = nb;
     ++hops;
   }
@@ -103,15 +121,112 @@ __device__ __forceinline__ void warp_count(unsigned long long* diag, int slot, i
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(diag + slot, static_cast<unsigned long long>(s));
 }
 
+// Per-particle event flags of one update, summed per warp into the diagnostics.
+struct StepFlags {
+  int hops = 0, fb = 0, brute = 0, lost = 0, wall = 0, fs = 0, oref = 0, c0 = 0, gex = 0,
+      src = 0, nf = 0;
+  int hop_bin = -1;
+};
+
+// The end of one particle update, common to both models: free-slip reflection with reversal
+// of the normal velocity (Sect. 4.2), periodic wrap, finiteness, neighbour walk to the new
+// host element (Sect. 3.6, with the reflections of a particle that crosses a free-slip edge
+// further on), source disc (Sect. 4.1.2) and the store of the new state.  Returns the new
+// element.
+template <typename T>
+__device__ __forceinline__ int finish_update(const AdvanceArgs<T>& a, const Model<T>& M, int64_t i,
+                                             int e, const ElemTopo& tp, T Xn, T Yn, T (&Un)[3],
+                                             T wn, T psin, StepFlags& f) {
+  const T L = M.period_x;
+  if (tp.fslip >= 0) {
+    const Line<T> ln = a.fslines[tp.fslip];
+    const T d1 = min_image(Xn - ln.px, L) * ln.nx + (Yn - ln.py) * ln.ny;
+    if (d1 < T(0)) {
+      f.fs = 1;
+      Xn -= T(2) * d1 * ln.nx;
+      Yn -= T(2) * d1 * ln.ny;
+      const T un = Un[0] * ln.nx + Un[1] * ln.ny;
+      Un[0] -= T(2) * un * ln.nx;
+      Un[1] -= T(2) * un * ln.ny;
+    }
+  }
+  Xn = wrap_period(Xn, L);
+  // a sum of finite terms of this size is finite; a NaN or infinity anywhere is not
+  if (!finite(Xn + Yn + Un[0] + Un[1] + Un[2] + wn + psin)) f.nf = 1;
+
+  int hops = 0, fb = 0, brute = 0, refl = 0;
+  int e_new = walk(a, e, Xn, Yn, Un, L, hops, fb, brute, refl);
+  f.hops = hops;
+  f.fb = fb;
+  f.brute = brute;
+  f.hop_bin = hops < 7 ? hops : 7;
+  if (refl) {
+    f.fs = 1;
+    Xn = wrap_period(Xn, L);
+  }
+  if (M.source_on) {
+    const T sx = min_image(Xn - M.src_x, L), sy = Yn - M.src_y;
+    if (sx * sx + sy * sy <= M.src_r * M.src_r) { psin = T(1); f.src = 1; }
+  }
+  if (e_new < 0) {
+    // counted in the old element for now; the brute-force kernel moves it (or flags it)
+    e_new = e;
+    const int at = atomicAdd(a.brute_count, 1);
+    if (at < a.brute_cap) a.brute_list[at] = static_cast<int32_t>(i);
+    else f.lost = 1;
+  }
+
+  a.p.x[i] = Xn;
+  a.p.y[i] = Yn;
+  a.p.u[i] = Un[0];
+  a.p.v[i] = Un[1];
+  a.p.w[i] = Un[2];
+  a.p.om[i] = wn;
+  a.p.psi[i] = psin;
+  a.p.elem[i] = e_new;
+  return e_new;
+}
+
+// Counts per new element, aggregated over the lanes of a warp that share it, and the
+// diagnostics counters and error word.  Every lane of the warp takes part.
+template <typename T>
+__device__ __forceinline__ void count_update(const AdvanceArgs<T>& a, bool valid, int e_new,
+                                             const StepFlags& f) {
+  const unsigned active = __ballot_sync(kFull, valid);
+  if (valid) {
+    const unsigned peers = __match_any_sync(active, e_new);
+    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(a.cnt + e_new, __popc(peers));
+  }
+  warp_count(a.diag, kDiagHops, f.hops);
+  if (__any_sync(kFull, f.fb | f.brute | f.lost | f.nf | f.gex | f.c0)) {
+    warp_count(a.diag, kDiagFallback, f.fb);
+    warp_count(a.diag, kDiagBrute, f.brute);
+    warp_count(a.diag, kDiagLost, f.lost);
+    warp_count(a.diag, kDiagNonFinite, f.nf);
+    warp_count(a.diag, kDiagGammaExhausted, f.gex);
+    warp_count(a.diag, kDiagC0Clamp, f.c0);
+  }
+  if (__any_sync(kFull, f.lost) && (threadIdx.x & 31) == 0) atomicCAS(a.err, 0, PDFX_ERR_LOST_PARTICLE);
+  if (__any_sync(kFull, f.nf) && (threadIdx.x & 31) == 0) atomicCAS(a.err, 0, PDFX_ERR_NONFINITE);
+  if (__any_sync(kFull, f.wall | f.fs | f.oref | f.src)) {
+    warp_count(a.diag, kDiagWall, f.wall);
+    warp_count(a.diag, kDiagFreeSlip, f.fs);
+    warp_count(a.diag, kDiagOmegaReflect, f.oref);
+    warp_count(a.diag, kDiagSource, f.src);
+  }
+  if (__any_sync(kFull, f.hop_bin > 0)) {
+#pragma unroll
+    for (int b = 1; b < 8; ++b) warp_count(a.diag, kDiagHopHist0 + b, f.hop_bin == b);
+  }
+}
+
 // FP32: 4 blocks of 256 per SM (64 registers); FP64: 2 blocks.  BATCH: model constants and
 // Philox key of the particle's instance (that of its element) instead of a.m, a.k0, a.k1.
 template <typename T, bool BATCH>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(const AdvanceArgs<T> a) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool valid = i < a.np;
-  int c_hops = 0, c_fb = 0, c_brute = 0, c_lost = 0, c_wall = 0, c_fs = 0, c_oref = 0,
-      c_c0 = 0, c_gex = 0, c_src = 0, c_nf = 0;
-  int hop_bin = -1;
+  StepFlags f;
   int e_new = -1;
   if (valid) {
     const int e = a.p.elem[i];
@@ -205,7 +320,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
     // Eq. 27 (C0 eps < 0 is clamped under the root and counted);
     // G_ij (U_j - <U_j>) = (wp_ij (U_j - <U_j>) - eps/2 (U_i - <U_i>)) / k  (Eq. 11)
     T c0e = C0 * eps;
-    if (c0e < T(0)) { c0e = T(0); c_c0 = 1; }
+    if (c0e < T(0)) { c0e = T(0); f.c0 = 1; }
     const T sc0e = sqrt(c0e) * sdt;
     const T dU[3] = {U0[0] - Um[0], U0[1] - Um[1], U0[2] - Um[2]};
     T Un[3];
@@ -225,7 +340,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
     const T wpos = w0 > T(0) ? w0 : T(0);
     T wn = w0 - M.C3 * Om * (w0 - Om) * dt - Somega * Om * w0 * dt +
            sqrt(T(2) * M.C3 * M.C4 * Om * Om * wpos) * (sdt * xi[5]);
-    if (wn < T(0)) { wn = -wn; c_oref = 1; }
+    if (wn < T(0)) { wn = -wn; f.oref = 1; }
     // Eq. 24 with the conditional mean of the particle's bin
     const T phic = static_cast<T>(a.vcce[(size_t)e * a.G + cpi]);
     T psin = psi0 - (psi0 - phic) * dt * itm;
@@ -254,85 +369,64 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
         }
       }
       if (any_hit) {
-        c_wall = 1;
+        f.wall = 1;
         Un[0] = Un[1] = Un[2] = T(0);                  // Eq. 56
         int ex = 0;                                    // Eq. 58
         wn = gamma_draw<T>(k0, k1, pid, step, kPurWallGamma, T(1) / M.C4, M.C4 * q[30], &ex);
-        c_gex = ex;
+        f.gex = ex;
       }
     }
-    // free-slip boundary: reflect, reverse the normal velocity
-    if (tp.fslip >= 0) {
-      const Line<T> ln = a.fslines[tp.fslip];
-      const T d1 = min_image(Xn - ln.px, L) * ln.nx + (Yn - ln.py) * ln.ny;
-      if (d1 < T(0)) {
-        c_fs = 1;
-        Xn -= T(2) * d1 * ln.nx;
-        Yn -= T(2) * d1 * ln.ny;
-        const T un = Un[0] * ln.nx + Un[1] * ln.ny;
-        Un[0] -= T(2) * un * ln.nx;
-        Un[1] -= T(2) * un * ln.ny;
-      }
-    }
-    Xn = wrap_period(Xn, L);
-    if (M.source_on) {
-      const T sx = min_image(Xn - M.src_x, L), sy = Yn - M.src_y;
-      if (sx * sx + sy * sy <= M.src_r * M.src_r) { psin = T(1); c_src = 1; }
-    }
-    // a sum of finite terms of this size is finite; a NaN or infinity anywhere is not
-    if (!finite(Xn + Yn + Un[0] + Un[1] + Un[2] + wn + psin)) c_nf = 1;
-
-    // Sect. 3.6
-    int hops = 0, fb = 0, brute = 0;
-    e_new = walk(a, e, Xn, Yn, L, hops, fb, brute);
-    c_hops = hops;
-    c_fb = fb;
-    c_brute = brute;
-    hop_bin = hops < 7 ? hops : 7;
-    if (e_new < 0) {
-      // counted in the old element for now; the brute-force kernel moves it (or flags it)
-      e_new = e;
-      const int at = atomicAdd(a.brute_count, 1);
-      if (at < a.brute_cap) a.brute_list[at] = static_cast<int32_t>(i);
-      else c_lost = 1;
-    }
-
-    a.p.x[i] = Xn;
-    a.p.y[i] = Yn;
-    a.p.u[i] = Un[0];
-    a.p.v[i] = Un[1];
-    a.p.w[i] = Un[2];
-    a.p.om[i] = wn;
-    a.p.psi[i] = psin;
-    a.p.elem[i] = e_new;
+    e_new = finish_update(a, M, i, e, tp, Xn, Yn, Un, wn, psin, f);
   }
-  // counts per new element, aggregated over the lanes of a warp that share it
-  const unsigned active = __ballot_sync(kFull, valid);
+  count_update(a, valid, e_new, f);
+}
+
+// Eqs. 46-47 (model 1), the particle-redistribution test of Sect. 3.7: one thread per
+// particle slot.  The mean velocity is the particles' own, the nodal means of the previous
+// statistics pass interpolated at X^n (Eq. 37; interp_mode 1: element average);
+// U^{n+1} = U - (U - alpha <U>) dt + sqrt(2 dt) xi (xi the first three Gaussians of the
+// step's first Philox block), X^{n+1} = X + U dt; omega and psi are kept.  The grid has no
+// no-slip walls; free-slip reflection, wrap, source and walk as in the full model.
+template <typename T, bool BATCH>
+__global__ void __launch_bounds__(256) simple_advance_kernel(const AdvanceArgs<T> a) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  const bool valid = i < a.np;
+  StepFlags f;
+  int e_new = -1;
   if (valid) {
-    const unsigned peers = __match_any_sync(active, e_new);
-    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(a.cnt + e_new, __popc(peers));
-  }
-  warp_count(a.diag, kDiagHops, c_hops);
-  if (__any_sync(kFull, c_fb | c_brute | c_lost | c_nf | c_gex | c_c0)) {
-    warp_count(a.diag, kDiagFallback, c_fb);
-    warp_count(a.diag, kDiagBrute, c_brute);
-    warp_count(a.diag, kDiagLost, c_lost);
-    warp_count(a.diag, kDiagNonFinite, c_nf);
-    warp_count(a.diag, kDiagGammaExhausted, c_gex);
-    warp_count(a.diag, kDiagC0Clamp, c_c0);
-  }
-  if (__any_sync(kFull, c_lost) && (threadIdx.x & 31) == 0) atomicCAS(a.err, 0, PDFX_ERR_LOST_PARTICLE);
-  if (__any_sync(kFull, c_nf) && (threadIdx.x & 31) == 0) atomicCAS(a.err, 0, PDFX_ERR_NONFINITE);
-  if (__any_sync(kFull, c_wall | c_fs | c_oref | c_src)) {
-    warp_count(a.diag, kDiagWall, c_wall);
-    warp_count(a.diag, kDiagFreeSlip, c_fs);
-    warp_count(a.diag, kDiagOmegaReflect, c_oref);
-    warp_count(a.diag, kDiagSource, c_src);
-  }
-  if (__any_sync(kFull, hop_bin > 0)) {
+    const int e = a.p.elem[i];
+    const int ki = BATCH ? a.einst[e] : 0;
+    const Model<T>& M = BATCH ? a.inst[ki].m : a.m;
+    const uint32_t k0 = BATCH ? a.inst[ki].k0 : a.k0, k1 = BATCH ? a.inst[ki].k1 : a.k1;
+    const T X0 = a.p.x[i], Y0 = a.p.y[i];
+    const T U0[3] = {a.p.u[i], a.p.v[i], a.p.w[i]};
+    const ElemTopo tp = a.topo[e];
+    T la, lb, lc;
+    if (M.interp_mode == 1) {
+      la = lb = lc = T(1) / T(3);
+    } else {
+      area_coords(a.geo[e], tp.n0, tp.n1, tp.n2, X0, Y0, M.period_x, la, lb, lc);
+    }
+    const double* m0 = a.nmom + static_cast<size_t>(kNS) * tp.n0;
+    const double* m1 = a.nmom + static_cast<size_t>(kNS) * tp.n1;
+    const double* m2 = a.nmom + static_cast<size_t>(kNS) * tp.n2;
+    const uint4 r0 = philox(make_uint4(a.p.pid[i], *a.stepc, kPurStep, 0u), k0, k1);
+    T xi[4];
+    box_muller(r0.x, r0.y, xi[0], xi[1]);
+    box_muller(r0.z, r0.w, xi[2], xi[3]);
+    const T dt = a.dt;
+    const T s2dt = sqrt(T(2) * dt);
+    T Un[3];
 #pragma unroll
-    for (int b = 1; b < 8; ++b) warp_count(a.diag, kDiagHopHist0 + b, hop_bin == b);
+    for (int r = 0; r < 3; ++r) {
+      const T Um = la * T(m0[1 + r]) + lb * T(m1[1 + r]) + lc * T(m2[1 + r]);
+      Un[r] = U0[r] - (U0[r] - M.alpha * Um) * dt + s2dt * xi[r];
+    }
+    const T Xn = X0 + U0[0] * dt;
+    const T Yn = Y0 + U0[1] * dt;
+    e_new = finish_update(a, M, i, e, tp, Xn, Yn, Un, a.p.om[i], a.p.psi[i], f);
   }
+  count_update(a, valid, e_new, f);
 }
 
 // Last resort of Sect. 3.6 for particles neither the walk nor the fall-back located: one
@@ -536,11 +630,14 @@ void launch_advance(const AdvanceArgs<T>& a, int num_sms, int block, cudaStream_
   if (a.np <= 0) return;
   cudaMemsetAsync(a.brute_count, 0, sizeof(int), s);
   const unsigned bgrid = static_cast<unsigned>(num_sms > 0 ? num_sms : 1);
+  const unsigned grid = blocks_for(a.np, block);
   if (a.einst) {
-    advance_kernel<T, true><<<blocks_for(a.np, block), block, 0, s>>>(a);
+    if (a.m.model == 1) simple_advance_kernel<T, true><<<grid, block, 0, s>>>(a);
+    else advance_kernel<T, true><<<grid, block, 0, s>>>(a);
     brute_search_kernel<T, true><<<bgrid, 256, 0, s>>>(a);
   } else {
-    advance_kernel<T, false><<<blocks_for(a.np, block), block, 0, s>>>(a);
+    if (a.m.model == 1) simple_advance_kernel<T, false><<<grid, block, 0, s>>>(a);
+    else advance_kernel<T, false><<<grid, block, 0, s>>>(a);
     brute_search_kernel<T, false><<<bgrid, 256, 0, s>>>(a);
   }
 }

@@ -33,8 +33,9 @@ struct __align__(sizeof(T) * 8) ElemGeo {
   T x0, y0, x1, y1, x2, y2, inv2a, pad;
 };
 
-// Per-element topology: node ids, neighbour across the edge opposite each vertex (-1 =
-// boundary), index into the no-slip and free-slip line tables (-1 = none).
+// Per-element topology: node ids, neighbour across the edge opposite each vertex (-1 = a
+// boundary edge; -2 - j = a free-slip boundary edge whose own line is entry j of the
+// free-slip edge table), index into the no-slip and free-slip line tables (-1 = none).
 struct __align__(16) ElemTopo {
   int n0, n1, n2, wall;
   int nb0, nb1, nb2, fslip;

@@ -19,6 +19,8 @@ struct Model {
   T s2nu;       // sqrt(2 nu) (Eqs. 7, 27)
   T cs_r2;      // C_s r0^(2/3) (Eq. 25)
   int c0_mode, tm_mode, interp_mode, source_on;
+  int model;    // 0 full model; 1 Eqs. 46-47
+  T alpha;      // Eq. 47
 };
 
 // One instance of a batch (a grid of the union, its particles and its parameters).  A
@@ -52,12 +54,14 @@ struct AdvanceArgs {
   const Line<T>* walls;
   const int32_t* wall2;    // [ne] second no-slip line of the element (a corner), -1 none
   const Line<T>* fslines;
+  const Line<T>* fsedges;  // lines of the free-slip boundary edges (topology -2 - j)
   const int32_t* ne_off;
   const int32_t* ne_list;
   int32_t ne;
   const T* fields;
   const double* vcce;
   int G;
+  const double* nmom;      // [nn][13] nodal statistics of the previous pass (model 1)
   int32_t* cnt;
   unsigned long long* diag;
   int* err;
@@ -158,6 +162,8 @@ struct Ctx {
   ElemTopo* topo = nullptr;     // [ne]
   int32_t* wall2 = nullptr;     // [ne] second no-slip line index (-1 none)
   void* walls = nullptr;        // Line<T>[n_walls]
+  void* fsedges = nullptr;      // Line<T>[]: each free-slip boundary edge's own line
+  int n_wall_lines = 0;         // no-slip wall lines of the grid
   void* fslines = nullptr;      // Line<T>[n_fs]
   int32_t* ne_off = nullptr;    // [nn + 1]
   int32_t* ne_list = nullptr;   // [3 ne]

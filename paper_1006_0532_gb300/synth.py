@@ -313,6 +313,43 @@ def workload(name: str, ppe: int | None = None) -> dict:
                 steps=p["steps"], re_tau=re)
 
 
+def redistribution_workload(name: str, ppe: int | None = None, ratio: int = 10) -> dict:
+    """The particle-redistribution test of Sect. 3.7 (Fig. 3): the simplified model of
+    Eqs. 46-47 (``model = 1``, alpha = 0.5) on a rectangle [0, 1] x [0, 1], periodic in x,
+    with free-slip boundaries at y = 0 and y = 1 and rows graded geometrically toward both
+    (the stretching that empties the thin cells unless particle-number control refills
+    them).  Equal particles per element at the start; velocities N(0, 1) per component
+    (Eq. 48: zero mean field, <u_i u_j> = delta_ij); MINNPEL = ppe / ratio (Eq. 51: the
+    ratio is held fixed across particle numbers); no scalar source.
+
+    ``redist_1k``  : 24 columns x 33 node rows, first row 2e-3 high, 1536 triangles,
+                     200 particles per element (Fig. 4 uses 50 to 800), dt 0.01.
+    ``redist_tiny``: 8 columns x 7 node rows, first row 0.02 high, 96 triangles, 40 per
+                     element (parity at sizes the oracle finishes fast).
+    """
+    if name == "redist_1k":
+        g = channel_grid(24, 33, lx=1.0, graded_y1=2e-3, jitter_x=0.2, jitter_y=0.1, seed=7)
+        p = dict(seed=7, ppe=200, dt=0.01, steps=400)
+    elif name == "redist_tiny":
+        g = channel_grid(8, 7, lx=1.0, graded_y1=0.02, jitter_x=0.2, jitter_y=0.1, seed=8)
+        p = dict(seed=8, ppe=40, dt=0.01, steps=20)
+    else:
+        raise KeyError(name)
+    if ppe is not None:
+        p["ppe"] = int(ppe)
+    # the channel walls become free-slip boundaries
+    tag = np.where(g.edge_tag == 1, 2, g.edge_tag).astype(np.int8)
+    g = Grid(node_xy=g.node_xy, tri=g.tri, edge_tag=tag, period_x=g.period_x)
+    fields = uniform_fields(g.nn, U=(0.0, 0.0, 0.0), uu=(1.0, 1.0, 1.0, 0.0, 0.0, 0.0),
+                            omega=1.0, omega_w=1.0)
+    params = dict(TABLE4)
+    params.update(model=1, alpha=0.5, nu=0.0, source_on=0, bins=(4, 4, 4), min_per_bin=2,
+                  minnpel=max(1, p["ppe"] // ratio), interp_mode=0, period_x=g.period_x,
+                  seed=p["seed"])
+    return dict(name=name, grid=g, fields=fields, params=params, ppe=p["ppe"], dt=p["dt"],
+                steps=p["steps"])
+
+
 # ----------------------------------------------------------------------------------------
 # Batches of independent instances (inputs of one batched context).
 # ----------------------------------------------------------------------------------------

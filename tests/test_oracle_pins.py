@@ -807,3 +807,77 @@ def test_fox_projection_degenerates_to_id_order_without_scalar_variance():
     assert np.all(vc[7, :4] == 0.25)
     cp = o.get_particles()["cp"]
     assert np.array_equal(cp, (4 * np.arange(40)) // 40)
+
+
+# ----------------------------------------------------------------------------------------
+# The simplified model of the particle-redistribution test (Sect. 3.7, Eqs. 46-52)
+# ----------------------------------------------------------------------------------------
+
+def _redist_run(ppe, alpha, steps, U0=(0.0, 0.0, 0.0), minnpel=0, seed=31):
+    w = synth.redistribution_workload("redist_tiny", ppe=ppe)
+    g = w["grid"]
+    P = dict(w["params"], alpha=alpha, minnpel=minnpel, seed=seed)
+    F = synth.uniform_fields(g.nn, U=U0, uu=(1.0, 1.0, 1.0, 0.0, 0.0, 0.0))
+    o = oracle.Oracle(g, P, F)
+    o.init_particles(ppe)
+    return w, g, o
+
+
+@pytest.mark.parametrize("alpha", [0.5, 0.0])
+def test_simplified_model_mean_and_variance_closed_forms(alpha):
+    """Eqs. 46-49 under Euler-Maruyama: the ensemble mean obeys Eq. 49,
+    m_n = m_0 (1 - (1 - alpha) dt)^n (the interpolated nodal mean is the ensemble mean of a
+    homogeneous field), and each component's fluctuation is the discrete OU process
+    var_n = r^(2n) var_0 + 2 dt (1 - r^(2n)) / (1 - r^2), r = 1 - dt, whatever alpha is
+    (alpha <U> is common to all particles; free-slip reflection only flips the sign of v)."""
+    ppe, n = 400, 60
+    w, g, o = _redist_run(ppe, alpha, n, U0=(1.0, 0.0, 0.5))
+    dt = w["dt"]
+    st0 = o.get_particles()
+    m0 = np.array([st0[k].mean() for k in ("u", "w")])
+    v0 = np.array([st0[k].var() for k in ("u", "v", "w")])
+    for _ in range(n):
+        o.step(dt)
+    st = o.get_particles()
+    N = st["u"].size
+    assert o.diag()["freeslip_hits"] > 0
+    m = np.array([st[k].mean() for k in ("u", "w")])
+    decay = (1.0 - (1.0 - alpha) * dt) ** n
+    # statistical error of a mean of N unit-variance samples, plus the noise the per-step
+    # increments add (at most sqrt(1/N))
+    assert np.all(np.abs(m - m0 * decay) < 6.0 * math.sqrt(2.0 / N)), (m, m0 * decay)
+    r = 1.0 - dt
+    var = np.array([st[k].var() for k in ("u", "v", "w")])
+    var_n = r ** (2 * n) * v0 + 2.0 * dt * (1.0 - r ** (2 * n)) / (1.0 - r * r)
+    assert np.all(np.abs(var / var_n - 1.0) < 6.0 * math.sqrt(2.0 / N)), (var, var_n)
+
+
+def test_simplified_model_with_redistribution_keeps_counts_and_variance():
+    """Sect. 3.7 with particle-number control on the stretched grid (MINNPEL = ppe / 10,
+    Eq. 51): particles are moved, no element stays below MINNPEL, and the ensemble variance
+    stays on the discrete OU steady approach toward 2 / (2 - dt) (the paper's analytic
+    steady state <u_i u_j> = delta_ij up to the Euler-Maruyama factor) within the
+    statistical error plus the perturbation the copied velocities bring."""
+    ppe, n = 200, 80
+    w, g, o = _redist_run(ppe, 0.5, n, minnpel=20)
+    dt = w["dt"]
+    v0 = np.array([o.get_particles()[k].var() for k in ("u", "v", "w")])
+    for _ in range(n):
+        o.step(dt)
+        _, cnt = o.element_stats()
+        assert cnt.min() >= 20
+    assert o.diag()["moves"] > 0
+    st = o.get_particles()
+    N = st["u"].size
+    r = 1.0 - dt
+    var = np.array([st[k].var() for k in ("u", "v", "w")])
+    var_n = r ** (2 * n) * v0 + 2.0 * dt * (1.0 - r ** (2 * n)) / (1.0 - r * r)
+    assert np.all(np.abs(var / var_n - 1.0) < 8.0 * math.sqrt(2.0 / N)), (var, var_n)
+
+
+def test_simplified_model_rejects_no_slip_walls():
+    w = synth.workload("channel_tiny")
+    o = oracle.Oracle(w["grid"], dict(w["params"], model=1), w["fields"])
+    o.init_particles(5)
+    with pytest.raises(Exception):
+        o.step(1e-3)
