@@ -211,7 +211,8 @@ uint32_t pdfx_step_index(const void *ctx);
 
 /* One timestep of fixed size dt > 0 (Table 1 order restricted to the particle path):
  * advance and track every particle, particle-number control, statistics and conditional
- * means.  Asynchronous on stream.  PDFX_ERR_ORDER without particles and fields. */
+ * means.  Asynchronous on stream.  PDFX_ERR_ORDER without particles and fields;
+ * PDFX_ERR_ARG for model 1 on a grid with no-slip walls (Eqs. 46-47 define none). */
 int  pdfx_step(void *ctx, double dt, void *stream);
 
 /* nsteps calls of pdfx_step with the same dt.  With use_graph != 0 the steps of whole
