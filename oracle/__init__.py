@@ -122,6 +122,7 @@ def lib():
             L.orc_get_element_stats.argtypes = [C.c_void_p, dp, ip]
             L.orc_get_nodal_stats.argtypes = [C.c_void_p, dp]
             L.orc_get_bins.argtypes = [C.c_void_p, dp, ip]
+            L.orc_scalar_stats.argtypes = [C.c_void_p, C.c_int, ip, C.c_int, ip, dp, dp, dp, dp]
             L.orc_get_diag.argtypes = [C.c_void_p, C.POINTER(Diag)]
             L.orc_reset_diag.argtypes = [C.c_void_p]
             L.orc_redistribution_counts.argtypes = [ip, C.c_int, C.c_int, ip]
@@ -316,6 +317,21 @@ class Oracle:
     def nodal_stats(self):
         out = np.zeros((self.nn, NS))
         lib().orc_get_nodal_stats(self.h, _dp(out))
+        return out
+
+    def scalar_stats(self, elems, nb: int = 200) -> dict:
+        """Scalar statistics of probe elements (Sect. 4.1.2, Eqs. 67-69): per element the
+        bin counts, Eq. 68's phi~, the conditional diffusion and dissipation per unit 1/t_m
+        over nb equal bins of [0, 1], and <phi>, <phi'^2>, <phi'^3>, <phi'^4>, min, max."""
+        el = np.ascontiguousarray(elems, dtype=np.int32)
+        n = int(el.size)
+        out = dict(count=np.zeros((n, nb), np.int32), phit=np.zeros((n, nb)),
+                   cdiff=np.zeros((n, nb)), cdiss=np.zeros((n, nb)), mom=np.zeros((n, 6)))
+        rc = lib().orc_scalar_stats(self.h, n, _ip(el), int(nb), _ip(out["count"]),
+                                    _dp(out["phit"]), _dp(out["cdiff"]), _dp(out["cdiss"]),
+                                    _dp(out["mom"]))
+        if rc:
+            raise RuntimeError("orc_scalar_stats failed (%d)" % rc)
         return out
 
     def bins(self):

@@ -1331,5 +1331,84 @@ int orc_get_bins(const orc_ctx *c, double *vcce, int32_t *g)
 }
 
 int orc_bins_capacity(const orc_ctx *c) { return c->G; }
+
+/* Scalar statistics of the particles of each probe element e = elems[j] (Sect. 4.1.2,
+ * Figs. 12-15), with the state's conditioning pointers and conditional means:
+ *   bin of psi: b = floor(psi nb) clamped to 0..nb-1 (nb equal bins of [0, 1], dpsi = 1/nb);
+ *   count[j][b]  particles in bin b;
+ *   phit[j][b]   Eq. 68: the mean of <phi|V> (the particle's conditional mean) over the
+ *                particles of bin b (Reading: the integral over the conditional PDF is the
+ *                bin average, as the paper computes it);
+ *   cdiff[j][b]  t_m <Gamma lap phi | psi>: under IECM (Eq. 24) the conditional diffusion
+ *                is the conditional mean of (<phi|V> - psi) / t_m; per unit 1/t_m (Reading:
+ *                t_m is a local constant; the paper shows these curves normalised by the mean
+ *                dissipation, where it cancels);
+ *   cdiss[j][b]  t_m <2 Gamma (grad phi)^2 | psi> by Eq. 67 at the bin centre, with f~ the
+ *                empirical PDF: the integral up to psi is (1/N) sum over particles below it
+ *                of (psi_p - phit(psi_p)), which over whole bins is (1/N) sum (psi_p - c_p)
+ *                (c_p the particle's <phi|V>, whose bin average phit is); half of bin b is
+ *                counted; divided by f~ = count / (N dpsi); 0 for an empty bin;
+ *   mom[j][0..5] <phi>, <phi'^2>, <phi'^3>, <phi'^4> (1/N central moments), psi_min, psi_max
+ *                (zeros for an empty element).                                            */
+int orc_scalar_stats(const orc_ctx *c, int n, const int32_t *elems, int nb, int32_t *count,
+                     double *phit, double *cdiff, double *cdiss, double *mom)
+{
+    if (n < 0 || nb < 1 || !c->x) return -1;
+    const double dpsi = 1.0 / nb;
+    double *sc = (double *)calloc((size_t)nb, sizeof(double));
+    double *sd = (double *)calloc((size_t)nb, sizeof(double));
+    for (int j = 0; j < n; ++j) {
+        const int e = elems[j];
+        if (e < 0 || e >= c->ne) { free(sc); free(sd); return -1; }
+        int32_t *cnt = count + (size_t)j * nb;
+        for (int b = 0; b < nb; ++b) { cnt[b] = 0; sc[b] = 0.0; sd[b] = 0.0; }
+        int N = 0;
+        double s1 = 0.0, lo = 0.0, hi = 0.0;
+        for (int p = 0; p < c->np; ++p) {
+            if (c->elem[p] != e) continue;
+            const double psi = c->psi[p];
+            const double cp = c->vcce[(size_t)e * c->G + c->cp[p]];
+            int b = (int)floor(psi * nb);
+            if (b < 0) b = 0;
+            if (b > nb - 1) b = nb - 1;
+            cnt[b]++;
+            sc[b] += cp;
+            sd[b] += psi - cp;
+            if (N == 0 || psi < lo) lo = psi;
+            if (N == 0 || psi > hi) hi = psi;
+            s1 += psi;
+            N++;
+        }
+        double *m = mom + (size_t)j * 6;
+        for (int k = 0; k < 6; ++k) m[k] = 0.0;
+        if (N > 0) {
+            const double mean = s1 / N;
+            double s2 = 0.0, s3 = 0.0, s4 = 0.0;
+            for (int p = 0; p < c->np; ++p) {
+                if (c->elem[p] != e) continue;
+                const double d = c->psi[p] - mean;
+                s2 += d * d;
+                s3 += d * d * d;
+                s4 += d * d * d * d;
+            }
+            m[0] = mean; m[1] = s2 / N; m[2] = s3 / N; m[3] = s4 / N; m[4] = lo; m[5] = hi;
+        }
+        double cum = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            const size_t o = (size_t)j * nb + b;
+            if (cnt[b] > 0) {
+                phit[o] = sc[b] / cnt[b];
+                cdiff[o] = -sd[b] / cnt[b];
+                cdiss[o] = -2.0 * dpsi * (cum + 0.5 * sd[b]) / cnt[b];
+            } else {
+                phit[o] = cdiff[o] = cdiss[o] = 0.0;
+            }
+            cum += sd[b];
+        }
+    }
+    free(sc);
+    free(sd);
+    return 0;
+}
 void orc_get_diag(const orc_ctx *c, orc_diag *d) { *d = c->diag; }
 void orc_reset_diag(orc_ctx *c) { memset(&c->diag, 0, sizeof(c->diag)); }

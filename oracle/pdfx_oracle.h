@@ -101,6 +101,10 @@ int  orc_get_element_stats(const orc_ctx *c, double *out /* [ne][13] */, int32_t
 int  orc_get_nodal_stats(const orc_ctx *c, double *out /* [nn][13] */);
 int  orc_get_bins(const orc_ctx *c, double *vcce /* [ne][G] */, int32_t *g /* [ne][3] */);
 int  orc_bins_capacity(const orc_ctx *c);
+
+/* Scalar statistics of probe elements (Sect. 4.1.2, Eqs. 67-69): see pdfx_oracle.c. */
+int  orc_scalar_stats(const orc_ctx *c, int n, const int32_t *elems, int nb, int32_t *count,
+                      double *phit, double *cdiff, double *cdiss, double *mom);
 void orc_get_diag(const orc_ctx *c, orc_diag *d);
 void orc_reset_diag(orc_ctx *c);
 int  orc_redistribution_counts(const int32_t *counts, int ne, int minnpel, int32_t *final_counts);

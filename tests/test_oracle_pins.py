@@ -881,3 +881,63 @@ def test_simplified_model_rejects_no_slip_walls():
     o.init_particles(5)
     with pytest.raises(Exception):
         o.step(1e-3)
+
+
+# ----------------------------------------------------------------------------------------
+# Scalar post-processing (Sect. 4.1.2, Eqs. 67-69)
+# ----------------------------------------------------------------------------------------
+
+def test_scalar_stats_iem_uniform_closed_forms():
+    """With one conditioning bin (IEM: <phi|V> = <phi> = 1/2) and psi evenly spaced on
+    [0, 1], Eq. 67 gives t_m <2 Gamma (grad phi)^2 | psi> = psi (1 - psi); on the empirical
+    PDF at bin centres the integral is low by dpsi^2 / 8, so the result is psi (1 - psi) -
+    dpsi^2 / 4 exactly.  Eq. 68 gives 1/2, the conditional diffusion 1/2 - psi, and the mean
+    dissipation (Eq. 67 integrated over psi) is 2 <phi'^2>.  Moments are those of the
+    discrete uniform distribution; an empty element gives zeros."""
+    w = synth.workload("channel_tiny")
+    g = w["grid"]
+    nb, m = 20, 10
+    N = nb * m
+    st = _element_state(g, [9], N, np.random.default_rng(5), lambda u, v, w_: np.zeros(u.shape))
+    st["psi"] = (np.arange(N) + 0.5) / N
+    P = dict(w["params"], bins=(1, 1, 1), min_per_bin=1)
+    o = oracle.Oracle(g, P, w["fields"])
+    o.set_particles(st, 0)
+    s = o.scalar_stats([9, 10], nb)
+    dpsi = 1.0 / nb
+    centre = (np.arange(nb) + 0.5) * dpsi
+    assert np.array_equal(s["count"][0], np.full(nb, m))
+    assert np.all(s["count"][1] == 0) and np.all(s["mom"][1] == 0) and np.all(s["cdiss"][1] == 0)
+    np.testing.assert_allclose(s["phit"][0], 0.5, atol=1e-14)
+    np.testing.assert_allclose(s["cdiff"][0], 0.5 - centre, atol=1e-14)
+    np.testing.assert_allclose(s["cdiss"][0], centre * (1 - centre) - dpsi ** 2 / 4, atol=1e-13)
+    mean, m2, m3, m4, lo, hi = s["mom"][0]
+    assert abs(mean - 0.5) < 1e-15 and lo == st["psi"][0] and hi == st["psi"][-1]
+    assert abs(m2 - (N * N - 1) / (12.0 * N * N)) < 1e-15
+    assert abs(m3) < 1e-15
+    assert abs(m4 - (N * N - 1) * (3.0 * N * N - 7) / (240.0 * N ** 4)) < 1e-15
+    chi = float(np.sum(s["cdiss"][0] * s["count"][0])) / N
+    assert abs(chi - 2.0 * m2) < dpsi ** 2
+
+
+def test_scalar_stats_conditional_means_balance_on_a_real_state():
+    """After IECM steps with a source (channel_tiny), the conditional means are bin means
+    (Appendix A), so over an element sum_p (psi_p - <phi|V>_p) = 0: the Eq. 67 integral
+    reaches zero at psi = 1 (sum over bins of count * conditional diffusion), and Eq. 68's
+    phi~ weighted by the counts returns <phi>."""
+    w = synth.workload("channel_tiny")
+    o = oracle.Oracle(w["grid"], w["params"], w["fields"])
+    o.init_particles(60)
+    for _ in range(5):
+        o.step(w["dt"])
+    em, cnt = o.element_stats()
+    elems = np.arange(w["grid"].ne)
+    s = o.scalar_stats(elems, 50)
+    N = s["count"].sum(axis=1)
+    assert np.array_equal(N, cnt)
+    bal = np.sum(s["cdiff"] * s["count"], axis=1)
+    assert np.all(np.abs(bal) <= 1e-12 * np.maximum(N, 1))
+    mean_from_phit = np.sum(s["phit"] * s["count"], axis=1) / np.maximum(N, 1)
+    np.testing.assert_allclose(mean_from_phit[N > 0], em[N > 0, 11], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(s["mom"][N > 0, 0], em[N > 0, 11], rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(s["mom"][N > 0, 1], em[N > 0, 12], rtol=1e-9, atol=1e-14)
