@@ -307,6 +307,26 @@ def redistribution_study(torch, B, synth, args):
     return out
 
 
+def scalar_post(torch, c, w):
+    """Scalar post-processing of Sect. 4.1.2 (Eqs. 67-69) through the C ABI with host
+    outputs: the wall time of one call for 64 probe elements at 200 psi bins (the paper's
+    point PDFs and conditional curves) and for every element at 50 bins."""
+    import numpy as np
+    ne = w["grid"].ne
+    res = {}
+    for name, elems, nb in (("probes64_bins200", np.linspace(0, ne - 1, 64).astype(np.int32), 200),
+                            ("all_elements_bins50", np.arange(ne, dtype=np.int32), 50)):
+        c.scalar_stats(elems, nb)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(3):
+            c.scalar_stats(elems, nb)
+        el = (time.perf_counter() - t0) / 3
+        res[name] = {"ms_per_call": el * 1e3, "probes": int(elems.size), "bins": nb,
+                     "particles": c.np_}
+    return res
+
+
 STAT_NAMES = ["N", "U", "V", "W", "uu", "vv", "ww", "uv", "uw", "vw", "omega", "psi", "psi2"]
 
 
@@ -477,6 +497,7 @@ def main():
 
     c32, r32 = time_form(torch, B, w, 1, args, rank, world, dist, with_clock=True)
     e2e_s, h2d, d2h = e2e_form(torch, B, c32, w, args)
+    rs = scalar_post(torch, c32, w) if rank == 0 else None
     c32.close()
     r64 = rb64 = None
     if not args.no_f64:
@@ -581,6 +602,8 @@ def main():
                     "errors": precision_study(r32["nodal"], r64["nodal"])}}}
     if rr is not None:
         line["redistribution_error"] = rr
+    if rs is not None:
+        line["scalar_statistics"] = rs
     if rf is not None:
         vF = rf["np"] * world * args.steps / (rf["ms"] * 1e-3)
         line["fox_form"] = {

@@ -50,6 +50,7 @@ extern "C" {
 #define PDFX_NF 32                  /* nodal field slots, layout below */
 #define PDFX_NSTAT 13               /* statistics per element or node, layout below */
 #define PDFX_MAX_PER_ELEMENT 4096   /* particles one element may hold for the binning */
+#define PDFX_MAX_SCALAR_BINS 4096  /* psi bins of pdfx_scalar_stats */
 #define PDFX_MAX_PARTICLES (1 << 28) /* particles per context (ids fit the binning sort keys) */
 
 /*
@@ -242,6 +243,29 @@ int  pdfx_get_element_stats(void *ctx, double *out, int32_t *counts, int on_devi
  * element's effective count are 0) and effective bins g[ne][3] (Sect. 3.5, Appendix A). */
 int  pdfx_get_bins(void *ctx, double *vcce, int32_t *g, int on_device, void *stream);
 int  pdfx_bins_capacity(const void *ctx);
+
+/* Scalar statistics of n probe elements (Sect. 4.1.2, Figs. 12-15; Eqs. 67-69), from the
+ * current particles and the conditioning pointers and conditional means of the last
+ * statistics pass.  elems[n]: distinct element ids (host array).  The scalar sample space
+ * [0, 1] is cut into nb (1..PDFX_MAX_SCALAR_BINS) equal bins, dpsi = 1/nb; a particle's bin
+ * is floor(psi nb) clamped to 0..nb-1.  Outputs, row-major per probe, any may be NULL:
+ *   count[n][nb]  particles per bin (the empirical PDF is count / (N dpsi));
+ *   phit[n][nb]   Eq. 68: the bin average of the particles' conditional means <phi|V>;
+ *   cdiff[n][nb]  t_m <Gamma lap phi | psi>: the bin average of <phi|V> - psi (IECM, Eq.
+ *                 24), per unit 1/t_m;
+ *   cdiss[n][nb]  t_m <2 Gamma (grad phi)^2 | psi> by Eq. 67 at the bin centre on the
+ *                 empirical PDF: -2 dpsi (S_<b + S_b / 2) / count_b, S the sums of
+ *                 psi - <phi|V> over the bins below b and over b; per unit 1/t_m;
+ *   mom[n][6]     <phi>, <phi'^2>, <phi'^3>, <phi'^4> (1/N central moments), min and max
+ *                 of psi.
+ * Empty bins and elements give zeros.  The sums are fixed point (2^-46 and, for the
+ * moments, 2^-40 resolution per term), so results do not depend on the order the GPU meets
+ * the particles; they assume psi within [-1, 2].  Host outputs (on_device 0) are complete
+ * on return; device outputs are ready on stream.  PDFX_ERR_ARG for a bad or repeated
+ * element id or nb; PDFX_ERR_ORDER before particles exist. */
+int  pdfx_scalar_stats(void *ctx, int32_t n, const int32_t *elems, int32_t nb, int32_t *count,
+                       double *phit, double *cdiff, double *cdiss, double *mom, int on_device,
+                       void *stream);
 
 /* Diagnostic counters accumulated since creation or the last reset, and the device error
  * word.  Synchronises stream.  pdfx_check returns the device error word as a code. */

@@ -103,6 +103,7 @@ def lib():
                 "pdfx_get_element_stats": (C.c_int, [vp, vp, vp, C.c_int, vp]),
                 "pdfx_get_bins": (C.c_int, [vp, vp, vp, C.c_int, vp]),
                 "pdfx_bins_capacity": (C.c_int, [vp]),
+                "pdfx_scalar_stats": (C.c_int, [vp, i32, vp, i32, vp, vp, vp, vp, vp, C.c_int, vp]),
                 "pdfx_get_diag": (C.c_int, [vp, C.POINTER(Diag), vp]),
                 "pdfx_reset_diag": (C.c_int, [vp, vp]),
                 "pdfx_check": (C.c_int, [vp, vp]),
@@ -318,6 +319,22 @@ class Context:
         self._check(lib().pdfx_get_bins(self.h, v.ctypes.data, g.ctypes.data, 0, _stream(stream)),
                     "pdfx_get_bins")
         return v, g
+
+    def scalar_stats(self, elems, nb: int = 200, stream=None) -> dict:
+        """Scalar statistics of probe elements (pdfx_scalar_stats): per element the psi bin
+        counts, Eq. 68's phi~, the conditional diffusion and Eq. 67's conditional
+        dissipation per unit 1/t_m over nb bins of [0, 1], and <phi>, <phi'^2>, <phi'^3>,
+        <phi'^4>, min and max of psi."""
+        el = np.ascontiguousarray(elems, dtype=np.int32)
+        n = int(el.size)
+        out = dict(count=np.zeros((n, nb), np.int32), phit=np.zeros((n, nb)),
+                   cdiff=np.zeros((n, nb)), cdiss=np.zeros((n, nb)), mom=np.zeros((n, 6)))
+        self._check(lib().pdfx_scalar_stats(self.h, n, el.ctypes.data, int(nb),
+                                            out["count"].ctypes.data, out["phit"].ctypes.data,
+                                            out["cdiff"].ctypes.data, out["cdiss"].ctypes.data,
+                                            out["mom"].ctypes.data, 0, _stream(stream)),
+                    "pdfx_scalar_stats")
+        return out
 
     def diag(self, stream=None) -> dict:
         d = Diag()

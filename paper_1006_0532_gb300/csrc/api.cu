@@ -1202,6 +1202,70 @@ int pdfx_get_bins(void* ctx, double* vcce, int32_t* g, int on_device, void* stre
   return copy_out(g, c->gbin, sizeof(int32_t) * 3 * c->ne, on_device, s);
 }
 
+int pdfx_scalar_stats(void* ctx, int32_t n, const int32_t* elems, int32_t nb, int32_t* count,
+                      double* phit, double* cdiff, double* cdiss, double* mom, int on_device,
+                      void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || n < 1 || !elems || nb < 1 || nb > PDFX_MAX_SCALAR_BINS) return PDFX_ERR_ARG;
+  if (!c->pbuf[0] || !c->have_grid) return PDFX_ERR_ORDER;
+  std::vector<int32_t> probe(static_cast<size_t>(c->ne), -1);
+  for (int32_t j = 0; j < n; ++j) {
+    if (elems[j] < 0 || elems[j] >= c->ne || probe[elems[j]] >= 0) return PDFX_ERR_ARG;
+    probe[elems[j]] = j;
+  }
+  const cudaStream_t s = as_stream(stream);
+  const size_t B = static_cast<size_t>(n) * nb, N = static_cast<size_t>(n), E = probe.size();
+  // one scratch block: the probe map, the accumulators, the outputs
+  const size_t bytes = 4 * E + 4 * B + 8 * 2 * B + 4 * N + 8 * 6 * N + 4 * B + 8 * 3 * B +
+                       8 * 6 * N + 16 * 16;
+  auto* base = static_cast<unsigned char*>(dev_alloc(*c, bytes));
+  if (!base) return PDFX_ERR_ALLOC;
+  unsigned char* ptr = base;
+  auto take = [&](size_t b) { unsigned char* r = ptr; ptr += (b + 15) & ~size_t(15); return r; };
+  auto* dprobe = reinterpret_cast<int32_t*>(take(4 * E));
+  ScalarAcc acc;
+  acc.count = reinterpret_cast<int32_t*>(take(4 * B));
+  acc.sc = reinterpret_cast<unsigned long long*>(take(8 * B));
+  acc.sd = reinterpret_cast<unsigned long long*>(take(8 * B));
+  acc.n = reinterpret_cast<int32_t*>(take(4 * N));
+  acc.s1 = reinterpret_cast<unsigned long long*>(take(8 * N));
+  acc.m = reinterpret_cast<unsigned long long*>(take(8 * 3 * N));
+  acc.lo = reinterpret_cast<unsigned long long*>(take(8 * N));
+  acc.hi = reinterpret_cast<unsigned long long*>(take(8 * N));
+  ScalarOut out;
+  out.count = reinterpret_cast<int32_t*>(take(4 * B));
+  out.phit = reinterpret_cast<double*>(take(8 * B));
+  out.cdiff = reinterpret_cast<double*>(take(8 * B));
+  out.cdiss = reinterpret_cast<double*>(take(8 * B));
+  out.mom = reinterpret_cast<double*>(take(8 * 6 * N));
+  int rc = PDFX_OK;
+  auto run = [&]() -> int {
+    PDFX_CUDA(cudaMemcpyAsync(dprobe, probe.data(), 4 * E, cudaMemcpyHostToDevice, s));
+    PDFX_CUDA(cudaMemsetAsync(acc.count, 0, static_cast<size_t>(reinterpret_cast<unsigned char*>(acc.lo) -
+                                                                reinterpret_cast<unsigned char*>(acc.count)), s));
+    PDFX_CUDA(cudaMemsetAsync(acc.lo, 0xff, 8 * N, s));
+    PDFX_CUDA(cudaMemsetAsync(acc.hi, 0, 8 * N, s));
+    if (c->prm.precision == 1)
+      launch_scalar_stats<float>(carve<float>(c->pbuf[c->cur], c->np), c->np, dprobe, c->vcce, c->G,
+                                 n, nb, acc, out, c->num_sms, s);
+    else
+      launch_scalar_stats<double>(carve<double>(c->pbuf[c->cur], c->np), c->np, dprobe, c->vcce,
+                                  c->G, n, nb, acc, out, c->num_sms, s);
+    c->launches += 3;
+    PDFX_CUDA(cudaGetLastError());
+    PDFX_TRY(copy_out(count, out.count, 4 * B, on_device, s));
+    PDFX_TRY(copy_out(phit, out.phit, 8 * B, on_device, s));
+    PDFX_TRY(copy_out(cdiff, out.cdiff, 8 * B, on_device, s));
+    PDFX_TRY(copy_out(cdiss, out.cdiss, 8 * B, on_device, s));
+    PDFX_TRY(copy_out(mom, out.mom, 8 * 6 * N, on_device, s));
+    return cerr(cudaStreamSynchronize(s));
+  };
+  rc = run();
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == PDFX_OK) rc = PDFX_ERR_CUDA;
+  dev_free(*c, base);
+  return rc;
+}
+
 int pdfx_bins_capacity(const void* ctx) {
   const Ctx* c = static_cast<const Ctx*>(ctx);
   return c ? c->G : 0;

@@ -257,6 +257,31 @@ template <typename T>
 void launch_stats_tiles(const StatsArgs<T>& a, int num_sms, cudaStream_t s);   // k_bins_f32.cu / k_bins_f64.cu
 void launch_node_average(const double* emom, const int32_t* ne_off, const int32_t* ne_list,
                          int32_t nn, double* nmom, cudaStream_t s);
+
+// Accumulators of the scalar statistics of n probe elements over nb psi bins (fixed-point
+// sums in two's complement; lo and hi hold order-preserving images of doubles).
+struct ScalarAcc {
+  int32_t* count;              // [n][nb] particles per bin
+  unsigned long long* sc;      // [n][nb] sums of <phi|V>
+  unsigned long long* sd;      // [n][nb] sums of psi - <phi|V>
+  int32_t* n;                  // [n] particles per element
+  unsigned long long* s1;      // [n] sums of psi
+  unsigned long long* m;       // [n][3] sums of (psi - <phi>)^2, ^3, ^4
+  unsigned long long* lo;      // [n] minimum of psi
+  unsigned long long* hi;      // [n] maximum of psi
+};
+struct ScalarOut {
+  int32_t* count;              // [n][nb]
+  double* phit;                // [n][nb] Eq. 68
+  double* cdiff;               // [n][nb] t_m <Gamma lap phi | psi>
+  double* cdiss;               // [n][nb] t_m <2 Gamma (grad phi)^2 | psi>, Eq. 67
+  double* mom;                 // [n][6] <phi>, <phi'^2>, <phi'^3>, <phi'^4>, min, max
+};
+// probe: [ne] index of the element among the probes, -1 for the others.
+template <typename T>
+void launch_scalar_stats(const Particles<T>& p, int64_t np, const int32_t* probe, const double* vcce,
+                         int G, int n, int nb, const ScalarAcc& acc, const ScalarOut& out,
+                         int num_sms, cudaStream_t s);   // k_scalar.cu
 // Particle order of the caller's arrays: by (instance, id), i.e. index p0_k + id (einst and
 // ip0 nullptr: one instance, index = id).
 template <typename T>
