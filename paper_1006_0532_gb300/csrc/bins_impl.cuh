@@ -241,10 +241,21 @@ struct ProjSrc {
   const T* c[3];
 };
 
+// Members only Fox's projection uses: an empty base of the hierarchical kernels' tile.
+template <typename T, bool FOX>
+struct TileFox {};
+template <typename T>
+struct TileFox<T, true> {
+  double mhx[3], mlx[3];            // sums of d_a d_phi (value/error pairs), Eq. 66
+  double em[kNS];                   // the element's statistics
+  double fox[6];                    // projection factors f_a and means <U_a> (Eqs. 64-66)
+  ProjSrc<T> proj;                  // the projected velocity's source
+};
+
 // Shared tile of one element.  Chunk tables are needed only when groups exceed 32
 // positions: then there are fewer than CAP/32 groups and fewer than 2 CAP/32 chunks.
-template <typename T, int CAP>
-struct Tile {
+template <typename T, int CAP, bool FOX>
+struct Tile : TileFox<T, FOX> {
   static constexpr int kChunks = 2 * CAP / 32;
   int32_t ord[CAP];                 // particle slots in the current order
   int32_t nord[CAP];                // the next level's order
@@ -256,10 +267,7 @@ struct Tile {
   int tie[3];                       // a tie was found at level l (fast pass)
   int32_t gfc[CAP / 32 + 1];        // first chunk of each group
   uint8_t cg[kChunks];              // group of each chunk
-  double mh[15], ml[15], msh[5];    // moment sums (value/error pairs) and shift values
-  double em[kNS];                   // the element's statistics (Fox's projection needs them)
-  double fox[6];                    // projection factors f_a and means <U_a> (Eqs. 64-66)
-  ProjSrc<T> proj;                  // the projected velocity's source (Fox's projection)
+  double mh[12], ml[12], msh[5];    // moment sums (value/error pairs) and shift values
   int n_gathered;
 };
 
@@ -281,17 +289,19 @@ __device__ __forceinline__ int run_count_below(const Arr& s, int base, int len, 
 
 // One sorting level: the groups of the current order (Gprev groups over n positions, the
 // largest of M) are each ordered by the level's key into nxt.  With M <= 32 a group is one
-// warp sort; otherwise chunks of 32 (tables t.gfc, t.cg) are sorted first.  Up to 4 chunks
-// per group, a key's rank is its chunk rank plus its count in every other chunk; beyond
-// that, sorted runs (32, 64, 128, ... positions of a group) are merged pairwise, a key's
+// warp sort; otherwise chunks of 32 (tables t.gfc, t.cg) are sorted first.  A key's rank
+// is its chunk rank plus its count in every other chunk of its group; with MERGE, in groups
+// above 256 positions sorted runs (32, 64, 128, ... positions of a group) are merged
+// pairwise instead (measured faster only where two whole-element levels are ranked), a key's
 // place in the merged run being its place in its own run plus its count in the partner
 // run, with the keys at their group positions in one half of sk and spay and written to
 // the other half (n <= CAP positions each), the last round into nxt.  The fast pass (EXACT
 // false) sets *tie when two real keys of a group are equal; until the first round in which
 // two equal keys meet the runs are exact, so that round's search finds the tie.  Its places
 // never leave the group or run pair, so every index stays within bounds either way.
-template <typename T, int CAP, int THREADS, bool EXACT, typename Arr, typename ValFn>
-__device__ void sort_level(const StatsArgs<T>& a, Tile<T, CAP>& t, Arr& sk, const int32_t* cur,
+template <typename T, int CAP, int THREADS, bool EXACT, bool MERGE, bool FOX, typename Arr,
+          typename ValFn>
+__device__ void sort_level(const StatsArgs<T>& a, Tile<T, CAP, FOX>& t, Arr& sk, const int32_t* cur,
                            int32_t* nxt, const ValFn& val, int n, int Gprev, int M, float invG,
                            int* tie) {
   using P = KeyPolicy<T, EXACT>;
@@ -317,7 +327,7 @@ __device__ void sort_level(const StatsArgs<T>& a, Tile<T, CAP>& t, Arr& sk, cons
       }
       if (lane < len) nxt[gs + lane] = q;
     }
-  } else if (M > 256) {
+  } else if (MERGE && M > 256) {
     const int nchunks = t.gfc[Gprev];
     for (int c = warp; c < nchunks; c += W) {
       const int gi = t.cg[c];
@@ -418,18 +428,21 @@ __device__ void sort_level(const StatsArgs<T>& a, Tile<T, CAP>& t, Arr& sk, cons
   }
 }
 
-// Key value of a particle at one level: a velocity component (val), or Fox's projected
-// velocity sum_a f_a (U_a - <U_a>) (Eq. 64, computed in FP64, rounded to the state
-// precision) from the factors, means and component arrays in shared memory (proj).
+// Key value of a particle at one level: a velocity component, or Fox's projected velocity
+// sum_a f_a (U_a - <U_a>) (Eq. 64, formed in FP64 and rounded to the state precision) from
+// the factors, means and component arrays in shared memory.
 template <typename T>
-struct KeySrc {
-  const T* val;
-  const ProjSrc<T>* proj;   // nullptr: val
+struct ArrVal {
+  const T* v;
+  __device__ __forceinline__ T operator()(int32_t q) const { return v[q]; }
+};
+template <typename T>
+struct ProjVal {
+  const ProjSrc<T>* s;
   __device__ __forceinline__ T operator()(int32_t q) const {
-    if (!proj) return val[q];
-    return static_cast<T>(proj->f[0] * (static_cast<double>(proj->c[0][q]) - proj->m[0]) +
-                          proj->f[1] * (static_cast<double>(proj->c[1][q]) - proj->m[1]) +
-                          proj->f[2] * (static_cast<double>(proj->c[2][q]) - proj->m[2]));
+    return static_cast<T>(s->f[0] * (static_cast<double>(s->c[0][q]) - s->m[0]) +
+                          s->f[1] * (static_cast<double>(s->c[1][q]) - s->m[1]) +
+                          s->f[2] * (static_cast<double>(s->c[2][q]) - s->m[2]));
   }
 };
 
@@ -438,13 +451,13 @@ struct KeySrc {
 // S2/N - (S1/N)^2; lanes combine as value/error pairs (FP32) or in FP64, then the 13
 // outputs are formed in FP64, one per lane.  Inlined: as an out-of-line call it measured
 // slower (its spills and the call outweigh the spills it saves in the sorting loops).
+// FOX: also the sums of d_a d_phi, then <u_a phi'> and the factors of Eqs. 65-66.
 template <typename A, bool FOX, typename T, int CAP>
 __device__ __forceinline__ void element_moments(const T* __restrict__ pu, const T* __restrict__ pv,
-                                             const T* __restrict__ pw, const T* __restrict__ pom,
-                                             const T* __restrict__ ppsi, double* emom_e,
-                                             int32_t* gbin_e, Tile<T, CAP>& t, const int32_t* cur,
-                                             int n, int g0, int g1, int g2) {
-  constexpr int NSUM = FOX ? 15 : 12;
+                                                const T* __restrict__ pw, const T* __restrict__ pom,
+                                                const T* __restrict__ ppsi, double* emom_e,
+                                                int32_t* gbin_e, Tile<T, CAP, FOX>& t,
+                                                const int32_t* cur, int n, int g0, int g1, int g2) {
   const int lane = threadIdx.x & 31;
   A sh[5] = {A(0), A(0), A(0), A(0), A(0)};
   if (n > 0) {
@@ -452,7 +465,8 @@ __device__ __forceinline__ void element_moments(const T* __restrict__ pu, const 
     sh[0] = A(pu[q0]); sh[1] = A(pv[q0]); sh[2] = A(pw[q0]);
     sh[3] = A(pom[q0]); sh[4] = A(ppsi[q0]);
   }
-  Acc<A> m[NSUM];
+  Acc<A> m[12];
+  Acc<A> mx[3];   // FOX only
   for (int p = lane; p < n; p += 32) {
     const int32_t q = cur[p];
     const A du = A(pu[q]) - sh[0], dv = A(pv[q]) - sh[1], dw = A(pw[q]) - sh[2];
@@ -461,13 +475,21 @@ __device__ __forceinline__ void element_moments(const T* __restrict__ pu, const 
     m[5].add(du * du); m[6].add(dv * dv); m[7].add(dw * dw);
     m[8].add(du * dv); m[9].add(du * dw); m[10].add(dv * dw);
     m[11].add(dp * dp);
-    if (FOX) { m[12 % NSUM].add(du * dp); m[13 % NSUM].add(dv * dp); m[14 % NSUM].add(dw * dp); }
+    if constexpr (FOX) { mx[0].add(du * dp); mx[1].add(dv * dp); mx[2].add(dw * dp); }
   }
 #pragma unroll
-  for (int c = 0; c < NSUM; ++c) {
+  for (int c = 0; c < 12; ++c) {
     A h, l;
     m[c].warp_pair(h, l);
     if (lane == c) { t.mh[c] = h; t.ml[c] = l; }
+  }
+  if constexpr (FOX) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      A h, l;
+      mx[c].warp_pair(h, l);
+      if (lane == c) { t.mhx[c] = h; t.mlx[c] = l; }
+    }
   }
   if (lane < 5)
     t.msh[lane] = lane == 0 ? sh[0] : lane == 1 ? sh[1] : lane == 2 ? sh[2] : lane == 3 ? sh[3] : sh[4];
@@ -486,10 +508,10 @@ __device__ __forceinline__ void element_moments(const T* __restrict__ pu, const 
     if (lane == 0) v = static_cast<double>(n);
     else if (n == 0) v = 0.0;
     emom_e[lane] = v;
-    if (FOX) t.em[lane] = v;
+    if constexpr (FOX) t.em[lane] = v;
   }
   if (lane < 3) gbin_e[lane] = lane == 0 ? g0 : lane == 1 ? g1 : g2;
-  if (FOX) {
+  if constexpr (FOX) {
     __syncwarp();
     if (lane == 0) {
       // <u_a phi'> = S(d_a d_phi)/N - (S d_a/N)(S d_phi/N); then Eqs. 65-66
@@ -497,7 +519,7 @@ __device__ __forceinline__ void element_moments(const T* __restrict__ pu, const 
       const double sp = (t.mh[4] + t.ml[4]) * inv;
       double uphi[3], f[3];
       for (int k = 0; k < 3; ++k)
-        uphi[k] = (t.mh[12 + k] + t.ml[12 + k]) * inv - (t.mh[k] + t.ml[k]) * inv * sp;
+        uphi[k] = (t.mhx[k] + t.mlx[k]) * inv - (t.mh[k] + t.ml[k]) * inv * sp;
       fox_factors(t.em, uphi, f);
       for (int k = 0; k < 3; ++k) { t.fox[k] = f[k]; t.fox[3 + k] = t.em[1 + k]; }
     }
@@ -506,8 +528,8 @@ __device__ __forceinline__ void element_moments(const T* __restrict__ pu, const 
 
 // Moments in the state precision (FP32 form: compensated) or, with acc64 in the FP32
 // form, in FP64.
-template <bool FOX, typename T, int CAP>
-__device__ __forceinline__ void element_moments_of(const StatsArgs<T>& a, Tile<T, CAP>& t,
+template <typename T, int CAP, bool FOX>
+__device__ __forceinline__ void element_moments_of(const StatsArgs<T>& a, Tile<T, CAP, FOX>& t,
                                                    const int32_t* cur, int n, int e,
                                                    const int (&g)[3]) {
   double* const emom_e = a.emom + static_cast<size_t>(kNS) * e;
@@ -520,9 +542,29 @@ __device__ __forceinline__ void element_moments_of(const StatsArgs<T>& a, Tile<T
                             g[0], g[1], g[2]);
 }
 
+// Chunk tables of one level (warp 0): the first chunk of each of the Gprev groups over n
+// positions (Gprev < n / 32 <= CAP / 32 <= 32 groups, one lane each) and the group of each
+// chunk.
+template <typename T, int CAP, bool FOX>
+__device__ __forceinline__ void chunk_tables(Tile<T, CAP, FOX>& t, int n, int Gprev, float invG, int lane) {
+  int nch = 0;
+  if (lane < Gprev) nch = (group_start(lane + 1, n, Gprev, invG) - group_start(lane, n, Gprev, invG) + 31) >> 5;
+  int incl = nch;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane < Gprev) {
+    t.gfc[lane] = incl - nch;
+    for (int j = 0; j < nch; ++j) t.cg[incl - nch + j] = static_cast<uint8_t>(lane);
+  }
+  if (lane == Gprev - 1) t.gfc[Gprev] = incl;
+}
+
 // One element of N <= CAP particles (list size after redistribution) by a block of THREADS.
 template <typename T, int CAP, int THREADS, bool FOX>
-__device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int N, int moves) {
+__device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP, FOX>& t, int e, int N, int moves) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const unsigned below = (1u << lane) - 1u;
 
@@ -568,9 +610,8 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int 
 
   // effective bins (reading of Sect. 3.5): g_l = max(1, min(b_l, n / (g_1..g_{l-1} min_per_bin)));
   // Fox's projection: max(1, min(fox_bins, n / min_per_bin)) intervals
-  constexpr bool fox = FOX;   // Fox's projection (cond_mode 1) or hierarchical bins
   int g[3];
-  if (fox) {
+  if constexpr (FOX) {
     int nc = n / a.min_per_bin;
     if (a.fox_bins < nc) nc = a.fox_bins;
     g[0] = nc < 1 ? 1 : nc;
@@ -589,75 +630,67 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int 
 
   int32_t* cur = t.ord;
   int32_t* nxt = t.nord;
-  // one sorting level over Gprev groups of the current order, keys from val(q)
-  auto run_level = [&](const KeySrc<T>& val, int Gprev, int ti) {
-    const int M = (n + Gprev - 1) / Gprev;   // largest group
-    const float invG = 1.0f / static_cast<float>(Gprev);
-    if (M > 32 && warp == 0) {
-      // chunk tables: Gprev < n / 32 <= CAP / 32 <= 32 groups, one lane each
-      int nch = 0;
-      if (lane < Gprev) nch = (group_start(lane + 1, n, Gprev, invG) - group_start(lane, n, Gprev, invG) + 31) >> 5;
-      int incl = nch;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(kFull, incl, o);
-        if (lane >= o) incl += y;
-      }
-      if (lane < Gprev) {
-        t.gfc[lane] = incl - nch;
-        for (int j = 0; j < nch; ++j) t.cg[incl - nch + j] = static_cast<uint8_t>(lane);
-      }
-      if (lane == Gprev - 1) t.gfc[Gprev] = incl;
-    }
-    __syncthreads();
-    sort_level<T, CAP, THREADS, false>(a, t, t.sk.fast, cur, nxt, val, n, Gprev, M, invG, &t.tie[ti]);
-    __syncthreads();
-    if (t.tie[ti]) {
-      sort_level<T, CAP, THREADS, true>(a, t, t.sk.exact, cur, nxt, val, n, Gprev, M, invG, nullptr);
-      __syncthreads();
-    }
-    int32_t* tmp = cur;
-    cur = nxt;
-    nxt = tmp;
-  };
-  if (n > 0) {
-    KeySrc<T> src{a.p.u, nullptr};
-    // hierarchical: levels by u, v, w; Fox's projection (Eqs. 64-66): the (u, id) order for
-    // the moments, then the order of the projected velocity
-    const int levels = fox ? 2 : 3;
+  if constexpr (!FOX) {
+    // levels by (u, id), (v, id), (w, id) within the groups of the previous level
     int Gprev = 1;
+    if (n > 0) {
 #pragma unroll 1
-    for (int l = 0; l < levels; ++l) {
-      if (!fox && l > 0 && g[l] <= 1) continue;
-      if constexpr (FOX) {
-        if (l == 1) {
-        if (warp == 0) {
-          element_moments_of<true>(a, t, cur, n, e, g);
-        }
-        if (threadIdx.x < 3) {
-          const int k = threadIdx.x;
-          t.proj.f[k] = t.fox[k];
-          t.proj.m[k] = t.fox[3 + k];
-          t.proj.c[k] = k == 0 ? a.p.u : (k == 1 ? a.p.v : a.p.w);
-        }
+      for (int l = 0; l < 3; ++l) {
+        if (l > 0 && g[l] <= 1) continue;
+        const ArrVal<T> val{l == 0 ? a.p.u : (l == 1 ? a.p.v : a.p.w)};
+        const int M = (n + Gprev - 1) / Gprev;   // largest group
+        const float invG = 1.0f / static_cast<float>(Gprev);
+        if (M > 32 && warp == 0) chunk_tables(t, n, Gprev, invG, lane);
         __syncthreads();
-        src.proj = &t.proj;
+        sort_level<T, CAP, THREADS, false, false>(a, t, t.sk.fast, cur, nxt, val, n, Gprev, M, invG,
+                                                  &t.tie[l]);
+        __syncthreads();
+        if (t.tie[l]) {
+          sort_level<T, CAP, THREADS, true, false>(a, t, t.sk.exact, cur, nxt, val, n, Gprev, M,
+                                                   invG, nullptr);
+          __syncthreads();
         }
-      } else {
-        src.val = l == 0 ? a.p.u : (l == 1 ? a.p.v : a.p.w);
+        int32_t* tmp = cur;
+        cur = nxt;
+        nxt = tmp;
+        Gprev *= g[l];
       }
-      run_level(src, fox ? 1 : Gprev, l);
-      if (!fox) Gprev *= g[l];
+    }
+    // moments (warp 0) in the final order
+    if (warp == 0) element_moments_of(a, t, cur, n, e, g);
+  } else {
+    // Fox's projection (Eqs. 64-66): the (u, id) order fixes the order of the moment sums;
+    // the moments give the factors; then one level over the whole element by U_rho
+    auto whole_level = [&](const auto& val, int ti) {
+      const float invG = 1.0f;
+      if (n > 32 && warp == 0) chunk_tables(t, n, 1, invG, lane);
+      __syncthreads();
+      sort_level<T, CAP, THREADS, false, true>(a, t, t.sk.fast, cur, nxt, val, n, 1, n, invG,
+                                               &t.tie[ti]);
+      __syncthreads();
+      if (t.tie[ti]) {
+        sort_level<T, CAP, THREADS, true, true>(a, t, t.sk.exact, cur, nxt, val, n, 1, n, invG,
+                                                nullptr);
+        __syncthreads();
+      }
+      int32_t* tmp = cur;
+      cur = nxt;
+      nxt = tmp;
+    };
+    if (n > 0) whole_level(ArrVal<T>{a.p.u}, 0);
+    if (warp == 0) element_moments_of(a, t, cur, n, e, g);   // an empty element writes zeros
+    if (n > 0) {
+      if (threadIdx.x < 3) {
+        const int k = threadIdx.x;
+        t.proj.f[k] = t.fox[k];
+        t.proj.m[k] = t.fox[3 + k];
+        t.proj.c[k] = k == 0 ? a.p.u : (k == 1 ? a.p.v : a.p.w);
+      }
+      __syncthreads();
+      whole_level(ProjVal<T>{&t.proj}, 1);
     }
   }
   const int G = g[0] * g[1] * g[2];
-
-  // moments (warp 0) in the final order, accumulated in the state precision (FP32 form:
-  // compensated) or, with acc64 in the FP32 form, in FP64 (Fox's projection: done above;
-  // an empty element still writes its zeros and bins)
-  if (warp == 0 && (!fox || n == 0)) {
-    element_moments_of<false>(a, t, cur, n, e, g);
-  }
 
   // Appendix A bins: conditional scalar means over the final order's bins
   double* vc = a.vcce + static_cast<size_t>(a.G) * e;
@@ -709,7 +742,7 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP>& t, int e, int 
 template <typename T, int CAP, int THREADS, bool FRONT, bool FOX>
 __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1536 : 1024) / THREADS)
     stats_tile_kernel(const StatsArgs<T> a) {
-  __shared__ Tile<T, CAP> t;
+  __shared__ Tile<T, CAP, FOX> t;
   // block b is entry b of the tile list; the list of instance k fills its element range
   // [eb, ee): the first class from the front, the second from the back
   const int b = blockIdx.x;
