@@ -216,6 +216,13 @@ uint32_t pdfx_step_index(const void *ctx);
  * PDFX_ERR_ARG for model 1 on a grid with no-slip walls (Eqs. 46-47 define none). */
 int  pdfx_step(void *ctx, double dt, void *stream);
 
+/* One timestep of each of n independent contexts (distinct, each with its own grid,
+ * parameters and particles), in array order on one stream: the same work and results as n
+ * calls of pdfx_step.  A set of instances stepped with one launch per stage is a single
+ * context made by pdfx_set_instances.  Stops at the first failing context and returns its
+ * code; PDFX_ERR_ARG for n < 1, a NULL or repeated context. */
+int  pdfx_batch_step(void *const *ctxs, int32_t n, double dt, void *stream);
+
 /* nsteps calls of pdfx_step with the same dt.  With use_graph != 0 the steps of whole
  * re-order cycles (2 sort_every steps, or 1 without re-ordering) are replayed from a CUDA
  * graph captured on the first such call (steps before the next cycle start and after the

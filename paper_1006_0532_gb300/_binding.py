@@ -94,6 +94,7 @@ def lib():
                 "pdfx_num_particles": (i64, [vp]),
                 "pdfx_step_index": (u32, [vp]),
                 "pdfx_step": (C.c_int, [vp, dp, vp]),
+                "pdfx_batch_step": (C.c_int, [vp, i32, dp, vp]),
                 "pdfx_set_instances": (C.c_int, [vp, i32, C.POINTER(Params), vp]),
                 "pdfx_step_many": (C.c_int, [vp, dp, i32, C.c_int, vp]),
                 "pdfx_autotune": (C.c_int, [vp, dp, vp, vp, vp]),
@@ -147,6 +148,14 @@ def _stream(stream):
         return C.c_void_p(stream if isinstance(stream, int) else stream.cuda_stream)
     import torch
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def batch_step(contexts, dt: float, stream=None):
+    """One step of each of several independent contexts on one stream (pdfx_batch_step)."""
+    hs = (C.c_void_p * len(contexts))(*[c.h for c in contexts])
+    rc = lib().pdfx_batch_step(hs, len(contexts), float(dt), _stream(stream))
+    if rc != 0:
+        raise PdfxError(rc, "pdfx_batch_step")
 
 
 class Context:

@@ -1162,6 +1162,20 @@ int pdfx_step(void* ctx, double dt, void* stream) {
                                : do_step<double>(*c, dt, as_stream(stream));
 }
 
+int pdfx_batch_step(void* const* ctxs, int32_t n, double dt, void* stream) {
+  if (!ctxs || n < 1) return PDFX_ERR_ARG;
+  for (int32_t i = 0; i < n; ++i) {
+    if (!ctxs[i]) return PDFX_ERR_ARG;
+    for (int32_t j = 0; j < i; ++j)
+      if (ctxs[j] == ctxs[i]) return PDFX_ERR_ARG;
+  }
+  for (int32_t i = 0; i < n; ++i) {
+    const int rc = pdfx_step(ctxs[i], dt, stream);
+    if (rc != PDFX_OK) return rc;
+  }
+  return PDFX_OK;
+}
+
 static int copy_out(void* dst, const void* src, size_t bytes, int on_device, cudaStream_t s) {
   if (!dst) return PDFX_OK;
   if (on_device) return cerr(cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDeviceToDevice, s));

@@ -1,6 +1,6 @@
 // Per-element statistics and conditional means for elements of up to 1024 particles, one
-// thread block per element (persistent blocks walk the plan's element lists of two size
-// classes; larger elements go through the block kernel in k_stats.cu).
+// thread block per entry of the plan's tile lists (two size classes, launched one after the
+// other; larger elements go through the block kernel in k_stats.cu).
 //
 // Sect. 3.5 / Appendix A: the element's particles are sorted by (u, id); the level-1 groups
 // (positions with equal floor(g1 p / N)) are sorted by (v, id), the level-2 groups by
@@ -18,6 +18,11 @@
 // warp in the final order (deterministic); the FP32 form accumulates compensated FP32 per
 // lane and combines lanes as FP32 value/error pairs, the FP64 form sums in FP64.  The 13
 // outputs are then formed in FP64 one per lane.
+// Fox's projection (Eqs. 64-66, cond_mode 1) is a compile-time variant of the kernel: the
+// (u, id) order fixes the order of the moment sums, the moments give the projection
+// factors, and one more level orders the whole element by the projected velocity (pairwise
+// merge rounds of sorted runs rank these whole-element levels).  The hierarchical variant
+// carries none of its members or code.
 #pragma once
 #include <initializer_list>
 

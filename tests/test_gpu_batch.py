@@ -173,3 +173,24 @@ def test_autotune_changes_no_result(precision):
         assert np.array_equal(sa[key], sb[key]), key
     assert np.array_equal(a.nodal_stats(), b.nodal_stats())
     assert a.diag()["moves"] == b.diag()["moves"]
+
+
+def test_batch_step_of_separate_contexts_equals_single_steps():
+    """pdfx_batch_step over three separate contexts gives, bit for bit, what pdfx_step gives
+    each of them; a repeated context is refused."""
+    ins = _instances()
+    a = [_single(it, 1, 4) for it in ins]
+    b = [_single(it, 1, 4) for it in ins]
+    dt = 2e-3
+    for _ in range(5):
+        B.batch_step(a, dt)
+        for c in b:
+            c.step(dt)
+    for ca, cb in zip(a, b):
+        sa, sb = ca.get_particles(), cb.get_particles()
+        for key in STATE_KEYS + ("elem", "cp"):
+            assert np.array_equal(sa[key], sb[key]), key
+        assert np.array_equal(ca.nodal_stats(), cb.nodal_stats())
+        assert ca.check() == 0
+    with pytest.raises(B.PdfxError):
+        B.batch_step([a[0], a[1], a[0]], dt)
