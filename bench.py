@@ -36,7 +36,7 @@ BIN_BYTES = {1: 21, 0: 37}
 # DRAM bytes per particle measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
 # for the current kernels, FP32 form: profiles/advance_kernel_channel_50k_ppe100_f32.md and
 # profiles/stats_tile_kernel_channel_50k_ppe500_f32.md.  None once a kernel changes.
-TRAFFIC_PER_PARTICLE = {"advance": 64.4, "statistics_binning": 35.0}
+TRAFFIC_PER_PARTICLE = {"advance": 64.4, "statistics_binning": 35.9}
 STAGES = ["advance", "plan", "lists", "redistribute", "statistics_binning", "node_average"]
 
 
