@@ -37,6 +37,10 @@ BIN_BYTES = {1: 21, 0: 37}
 # for the current kernels, FP32 form: profiles/advance_kernel_channel_50k_ppe100_f32.md and
 # profiles/stats_tile_kernel_channel_50k_ppe500_f32.md.  None once a kernel changes.
 TRAFFIC_PER_PARTICLE = {"advance": 64.4, "statistics_binning": 35.9}
+# What bounds each kernel instead of HBM, from the same ncu captures.
+LIMITER = {"advance": "instruction issue (issue active 66%, long-scoreboard stalls; DRAM 15% of peak)",
+           "statistics_binning": "integer ALU issue (ALU pipe 74%, issue active 74% in the <= 512 class; "
+                                 "DRAM 6% of peak)"}
 STAGES = ["advance", "plan", "lists", "redistribute", "statistics_binning", "node_average"]
 
 
@@ -563,7 +567,8 @@ def main():
                      "kernel": ("stats_tile_kernel<float> (2 size-class launches per step)"
                                 if dom == "statistics_binning" else "advance_kernel<float>"),
                      "algorithmic_bytes_per_particle": per_p, "peak_source": peak_kind,
-                     "ms_per_step": dom_ms},
+                     "ms_per_step": dom_ms,
+                     "limiter": LIMITER.get(dom)},
         "step_roofline": {"bytes_per_update": step_bytes, "achieved": step_achieved,
                           "peak": peak, "unit": "GB/s", "frac": step_achieved / peak},
         "stages_ms_per_step": stage,
