@@ -390,8 +390,9 @@ def canyon_form(torch, B, synth, args):
 
 
 def batched_form(torch, B, synth, args):
-    """The ensemble of independent instances (64 channel grids of 1k-57k triangles at 50-500
-    particles per element, about 287M particles, FP32 state): one context stepping all of
+    """The ensemble of independent instances (32 channel and 32 street-canyon grids of 1k-57k
+    triangles at 50-500 particles per element, about 288M particles, FP32 state): one
+    context stepping all of
     them with one launch per stage, whole re-order cycles replayed from a CUDA graph; then
     the same instances as 64 contexts stepped one after the other."""
     ins = synth.ensemble(args.batch_instances)

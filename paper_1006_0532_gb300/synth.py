@@ -389,13 +389,36 @@ def union(instances: list[dict]):
     return grid, np.concatenate(fl), np.array(ef, dtype=np.int32), np.array(nf, dtype=np.int64)
 
 
+def canyon_scale(n_tri: int) -> int:
+    """Scale k of a street-canyon grid of about n_tri triangles (canyon_instance: 120 k^2)."""
+    return max(3, int(round(math.sqrt(n_tri / 120.0))))
+
+
+def canyon_instance(n_tri: int, seed: int, ppe: int, src=(2.0, 0.5), philox_seed: int = 1,
+                    instance: int = 0) -> dict:
+    """A street-canyon grid of 120 k^2 triangles (k = canyon_scale(n_tri): 4k cavity columns,
+    12k channel columns, 3k rows in the channel and in the cavity, first rows 0.08/k high),
+    its fields at Re_0 = 12,000, and the parameters of one instance (C0 from Eq. 11, t_m from
+    Eq. 25, MINNPEL = ppe / 10, source disc of radius 0.02)."""
+    k = canyon_scale(n_tri)
+    g = canyon_grid(4 * k, 12 * k, 3 * k, 3 * k, h0=0.08 / k, seed=seed)
+    nu = 1.0 / 12000.0
+    params = dict(TABLE4)
+    params.update(nu=nu, Cs=0.02, Ct=0.7, src_x=float(src[0]), src_y=float(src[1]), src_r=0.02,
+                  bins=(4, 4, 4), min_per_bin=2, minnpel=max(1, ppe // 10), interp_mode=0,
+                  period_x=g.period_x, c0_mode=0, C0=0.0, tm_mode=0, Cphi=2.0,
+                  seed=int(philox_seed), instance=int(instance), source_on=1)
+    return dict(grid=g, fields=canyon_fields(g, nu), params=params, ppe=int(ppe))
+
+
 def ensemble(n_inst: int = 64, tri_lo: float = 1000.0, tri_hi: float = 60000.0,
              ppe_lo: int = 50, ppe_hi: int = 500, total_lo: float = 2.7e8,
              total_hi: float = 3.3e8, key: int = 5) -> list[dict]:
-    """The ensemble of independent channel instances: triangle counts log-uniform in
-    [tri_lo, tri_hi], particles per element uniform in [ppe_lo, ppe_hi], redrawn with the
-    next key until the particle total lies in [total_lo, total_hi]; source position and
-    Philox seed (1000 + k) per instance."""
+    """The ensemble of independent instances, channel grids at even k and street-canyon
+    grids at odd k: triangle counts log-uniform in [tri_lo, tri_hi], particles per element
+    uniform in [ppe_lo, ppe_hi], redrawn with the next key until the particle total lies in
+    [total_lo, total_hi]; source position (channel: x 0.25..1.75, y 0.2..0.8; cavity:
+    x 1.6..2.4, y 0.1..0.9) and Philox seed (1000 + k) per instance."""
     while True:
         rng = np.random.default_rng(key)
         u = rng.random(n_inst)
@@ -404,15 +427,22 @@ def ensemble(n_inst: int = 64, tri_lo: float = 1000.0, tri_hi: float = 60000.0,
         tris = np.round(np.exp(np.log(tri_lo) + u * np.log(tri_hi / tri_lo))).astype(int)
         ppes = (ppe_lo + np.floor(w * (ppe_hi - ppe_lo + 1))).astype(int)
         rows = np.maximum(2, np.round(np.sqrt(tris / 4.0))).astype(int)
-        total = float(np.sum(4 * rows * rows * ppes))
+        ks = np.array([canyon_scale(int(t)) for t in tris])
+        ne = np.where(np.arange(n_inst) % 2 == 0, 4 * rows * rows, 120 * ks * ks)
+        total = float(np.sum(ne * ppes))
         if total_lo <= total <= total_hi:
             break
         key += 1
     out = []
     for k in range(n_inst):
-        src = (0.25 + 1.5 * u[k], 0.2 + 0.6 * v[k])
-        out.append(channel_instance(int(tris[k]), 392.0, seed=100 + k, ppe=int(ppes[k]), src=src,
-                                    philox_seed=1000 + k, instance=k))
+        if k % 2 == 0:
+            src = (0.25 + 1.5 * u[k], 0.2 + 0.6 * v[k])
+            out.append(channel_instance(int(tris[k]), 392.0, seed=100 + k, ppe=int(ppes[k]),
+                                        src=src, philox_seed=1000 + k, instance=k))
+        else:
+            src = (1.6 + 0.8 * u[k], 0.1 + 0.8 * v[k])
+            out.append(canyon_instance(int(tris[k]), seed=100 + k, ppe=int(ppes[k]), src=src,
+                                       philox_seed=1000 + k, instance=k))
     return out
 
 

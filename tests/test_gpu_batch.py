@@ -24,9 +24,24 @@ def _instances():
     return out
 
 
+def _mixed_instances():
+    """Channel, street canyon (walls, corners, free-slip top; period 4 against 2), channel."""
+    out = [synth.channel_instance(120, 392.0, seed=21, ppe=30, src=(0.6, 0.4), philox_seed=5,
+                                  instance=0),
+           synth.canyon_instance(1080, seed=22, ppe=20, src=(2.0, 0.5), philox_seed=6, instance=1),
+           synth.channel_instance(200, 392.0, seed=23, ppe=25, src=(0.3, 0.7), philox_seed=7,
+                                  instance=2)]
+    for it in out:
+        it["params"]["minnpel"] = it["ppe"] - 1
+    return out
+
+
 @pytest.mark.parametrize("precision", [0, 1])
-def test_batch_matches_instances_run_alone(precision):
-    ins = _instances()
+@pytest.mark.parametrize("mixed", [False, True])
+def test_batch_matches_instances_run_alone(precision, mixed):
+    """Channel instances, and a mix of channel and street-canyon instances (the ensemble's
+    two kinds), stepped as one batch give each instance's results run alone bit for bit."""
+    ins = _mixed_instances() if mixed else _instances()
     g, F, ef, nf = synth.union(ins)
     P = [dict(it["params"], precision=precision, sort_every=4) for it in ins]
     b = B.Context(P[0])
@@ -41,7 +56,7 @@ def test_batch_matches_instances_run_alone(precision):
         c.set_fields(it["fields"])
         c.init_particles(it["ppe"])
         alone.append(c)
-    dt = 2e-3
+    dt = 1e-3 if mixed else 2e-3
     for _ in range(7):
         b.step(dt)
         for c in alone:
