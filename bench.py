@@ -477,6 +477,7 @@ def main():
     ap.add_argument("--no-autotune", action="store_true")
     ap.add_argument("--no-fox", action="store_true")
     ap.add_argument("--no-redist", action="store_true")
+    ap.add_argument("--no-sweep", action="store_true")
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=16)
     ap.add_argument("--ppe", type=int, default=None,
@@ -511,6 +512,12 @@ def main():
         cb, rb64 = time_form(torch, B, w, 1, args, rank, world, dist, with_clock=False,
                              extra={"acc64": 1})
         cb.close()
+    rs8 = None
+    if not args.no_sweep:
+        # the (2, 2, 2) point of the bins sweep: 8 conditioning bins instead of 64
+        cs8, rs8 = time_form(torch, B, w, 1, args, rank, world, dist, with_clock=False,
+                             extra={"bins": (2, 2, 2)})
+        cs8.close()
     rf = None
     if not args.no_fox:
         # Fox's projection conditioning (Eqs. 64-66) in place of the hierarchical bins, as
@@ -571,8 +578,15 @@ def main():
                      "ms_per_step": dom_ms,
                      "limiter": LIMITER.get(dom)},
         "step_roofline": {"bytes_per_update": step_bytes, "achieved": step_achieved,
-                          "peak": peak, "unit": "GB/s", "frac": step_achieved / peak},
+                          "peak": peak, "unit": "GB/s", "frac": step_achieved / peak,
+                          "frac_nominal_8000": step_achieved / 8000.0},
         "stages_ms_per_step": stage,
+        "stages_gbs": {n: {"algorithmic_bytes_per_particle": bpp,
+                           "achieved": bpp * np_ / (stage[n] * 1e-3) / 1e9,
+                           "frac_measured": bpp * np_ / (stage[n] * 1e-3) / 1e9 / peak,
+                           "frac_nominal_8000": bpp * np_ / (stage[n] * 1e-3) / 1e9 / 8000.0}
+                       for n, bpp in (("advance", ADV_BYTES[1]),
+                                      ("statistics_binning", BIN_BYTES[1]))},
         "gpu_launches": r32["launches"],
         "e2e": {"value": np_ * world * args.steps / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h},
@@ -605,6 +619,15 @@ def main():
                 "C_fp32_sde_compensated_fp32_accumulation": {
                     "value": value, "unit": UNIT,
                     "errors": precision_study(r32["nodal"], r64["nodal"])}}}
+    if rs8 is not None:
+        line["bins_sweep"] = {
+            "what": "FP32 form with (2, 2, 2) conditioning bins against the default (4, 4, 4)",
+            "bins_2_2_2": {"value": rs8["np"] * world * args.steps / (rs8["ms"] * 1e-3),
+                           "ms_per_step": rs8["ms"] / args.steps,
+                           "binning_ms_per_step": rs8["stage_ms"][STAGES.index("statistics_binning")]
+                           / max(rs8["stage_n"][STAGES.index("statistics_binning")], 1)},
+            "bins_4_4_4": {"value": value, "ms_per_step": r32["ms"] / args.steps,
+                           "binning_ms_per_step": stage["statistics_binning"]}}
     if rr is not None:
         line["redistribution_error"] = rr
     if rs is not None:

@@ -112,3 +112,50 @@ def test_full_size_sampled_parity(precision):
     check_states(sg, so, ~diff & same_cp)
     assert c.check() == 0
     print("largest relative state errors (quantity, thin cell):", worst)
+
+
+def test_canyon_full_size_sampled_parity_f64():
+    """The street canyon at full size (about 200,000 triangles graded to y+ = 1 at the floor,
+    the cavity walls and corners; 100 particles per element, about 20M), FP64 form: the
+    oracle follows sampled elements (8 at walls, the free-slip top or corners) from the same
+    initialisation through the statistics and one step: states within 1e-12, element
+    indices and conditioning pointers exact."""
+    w = synth.canyon_workload("canyon_200k")
+    g = w["grid"]
+    P = dict(w["params"], minnpel=0)           # particle-number control is global: off
+    c = B.Context(dict(P, precision=0, sort_every=8))
+    c.set_grid(g)
+    c.set_fields(w["fields"])
+    c.init_particles(w["ppe"])
+    elems = _sample_elements(g, n_wall=8, n_inner=8, seed=12)
+    o = oracle.Oracle(g, P, w["fields"])
+    o.init_elements(w["ppe"], elems)
+    ids = o.pids().astype(np.int64)
+    sg, so = c.get_particles(), o.get_particles()
+    assert np.array_equal(sg["elem"][ids], so["elem"])
+    assert np.abs(period_diff(sg["x"][ids], so["x"], g.period_x)).max() <= 1e-12 * g.period_x
+    for k in ("y", "u", "v", "w", "om", "psi"):
+        r = _rel(sg[k][ids], so[k], np.sqrt(np.mean(so[k] ** 2)) or 1.0).max()
+        assert r <= 1e-12, (k, float(r))
+    assert np.array_equal(sg["cp"][ids], so["cp"])
+    eg, cg = c.element_stats()
+    eo, co = o.element_stats()
+    assert np.array_equal(cg[elems], co[elems])
+    sc = np.sqrt(np.mean(eo[elems] ** 2, axis=0)) + 1e-300
+    assert _rel(eg[elems], eo[elems], sc).max() <= 1e-10
+    c.autotune(w["dt"])
+    c.step(w["dt"])
+    o.step(w["dt"])
+    sg, so = c.get_particles(), o.get_particles()
+    diff = sg["elem"][ids] != so["elem"]
+    for i in np.where(diff)[0]:          # a particle on a shared edge may sit in either element
+        assert o.lam(int(sg["elem"][ids][i]), so["x"][i], so["y"][i]).min() > -1e-12
+    assert diff.sum() <= 2
+    m = ~diff
+    assert np.abs(period_diff(sg["x"][ids][m], so["x"][m], g.period_x)).max() <= 1e-12 * g.period_x
+    for k in ("y", "u", "v", "w", "om", "psi"):
+        r = _rel(sg[k][ids][m], so[k][m], np.sqrt(np.mean(so[k] ** 2)) or 1.0).max()
+        assert r <= 1e-12, (k, float(r))
+    d = o.diag()
+    assert d["wall_hits"] > 0 or d["freeslip_hits"] > 0
+    assert c.check() == 0
