@@ -941,3 +941,40 @@ def test_scalar_stats_conditional_means_balance_on_a_real_state():
     np.testing.assert_allclose(mean_from_phit[N > 0], em[N > 0, 11], rtol=1e-12, atol=1e-14)
     np.testing.assert_allclose(s["mom"][N > 0, 0], em[N > 0, 11], rtol=1e-12, atol=1e-14)
     np.testing.assert_allclose(s["mom"][N > 0, 1], em[N > 0, 12], rtol=1e-9, atol=1e-14)
+
+
+def test_free_slip_reflection_beyond_the_start_element():
+    """Sect. 4.2 with the walk's reflection: a particle starting in an element with no
+    boundary line (second row of the stretched grid) that crosses the whole boundary row in
+    one step ends at the mirror image of X + U dt across y = 0 (Eq. 46 moves it with U^n,
+    without noise), in an element that contains it, counted once as a free-slip hit."""
+    w = synth.redistribution_workload("redist_tiny")
+    g = w["grid"]
+    ys = np.sort(np.unique(np.round(g.node_xy[:, 1], 12)))
+    row1 = ys[1]
+    y_of = g.node_xy[g.tri, 1]                                     # [ne, 3]
+    start = [e for e in range(g.ne) if y_of[e].min() > 0.5 * row1 and y_of[e].max() < 0.5]
+    e0 = min(start, key=lambda e: y_of[e].min())                   # lowest such element
+    lam = np.array([1.0, 1.0, 1.0]) / 3.0
+    xy = g.node_xy[g.tri[e0]].copy()
+    for k in (1, 2):
+        d = xy[k, 0] - xy[0, 0]
+        if abs(d) > g.period_x / 2:
+            xy[k, 0] -= np.sign(d) * g.period_x
+    x0, y0 = lam @ xy
+    x0 %= g.period_x
+    dt = w["dt"]
+    target = -0.3 * row1                                          # below y = 0 before reflection
+    st = dict(x=np.array([x0]), y=np.array([y0]), u=np.array([0.1]),
+              v=np.array([(target - y0) / dt]), w=np.array([0.0]), om=np.array([1.0]),
+              psi=np.array([0.0]), elem=np.array([e0], dtype=np.int32))
+    P = dict(w["params"], minnpel=0)
+    o = oracle.Oracle(g, P, w["fields"])
+    o.set_particles(st, 0)
+    o.step(dt)
+    s = o.get_particles()
+    assert abs(s["y"][0] - (-target)) <= 1e-14
+    assert abs(((s["x"][0] - (x0 + 0.1 * dt)) + 0.5) % 1.0 - 0.5) <= 1e-14
+    assert o.lam(int(s["elem"][0]), s["x"][0], s["y"][0]).min() >= -1e-12
+    d = o.diag()
+    assert d["freeslip_hits"] == 1 and d["lost"] == 0
