@@ -1265,7 +1265,7 @@ int pdfx_scalar_stats(void* ctx, int32_t n, const int32_t* elems, int32_t nb, in
     else
       launch_scalar_stats<double>(carve<double>(c->pbuf[c->cur], c->np), c->np, dprobe, c->vcce,
                                   c->G, n, nb, acc, out, c->num_sms, s);
-    c->launches += 3;
+    c->launches += c->np > 0 ? 3 : 1;
     PDFX_CUDA(cudaGetLastError());
     PDFX_TRY(copy_out(count, out.count, 4 * B, on_device, s));
     PDFX_TRY(copy_out(phit, out.phit, 8 * B, on_device, s));
