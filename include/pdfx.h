@@ -10,7 +10,10 @@
  * scalar source (Sect. 4.1.2), tracks the particle to its new element (Sect. 3.6),
  * redistributes particles to keep every element above a minimum count (Sect. 3.7,
  * Appendix B), and recomputes the element and nodal statistics (Sect. 3.3, Eqs. 34-36)
- * and the velocity-conditioned scalar means used by the next step (Sect. 3.5, Appendix A).
+ * and the velocity-conditioned scalar means used by the next step (Sect. 3.5, Appendix A,
+ * or Fox's projection, Eqs. 64-66).  Also: batches of independent grids stepped together,
+ * the simplified model of the particle-redistribution test (Eqs. 46-47), and scalar
+ * post-processing of probe elements (Eqs. 67-69).
  *
  * Conventions for every call:
  *  - Return value: PDFX_OK (0) or a negative PDFX_ERR_* code.  No exception crosses this

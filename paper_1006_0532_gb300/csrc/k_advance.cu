@@ -7,6 +7,8 @@
 //   position (Eq. 7), frequency (Eq. 19), scalar (Eq. 24); wall conditions (Eqs. 53-58)
 //   and free-slip reflection; periodic wrap; source disc (Sect. 4.1.2); neighbour walk to
 //   the new host element (Sect. 3.6).  Counts per new element are aggregated per warp.
+// The simplified model of the particle-redistribution test (Eqs. 46-47, model 1) has its
+// own kernel and shares the end of the update (reflection, wrap, walk, store, counts).
 #include "pdfx_internal.h"
 
 namespace pdfx {
