@@ -978,3 +978,57 @@ def test_free_slip_reflection_beyond_the_start_element():
     assert o.lam(int(s["elem"][0]), s["x"][0], s["y"][0]).min() >= -1e-12
     d = o.diag()
     assert d["freeslip_hits"] == 1 and d["lost"] == 0
+
+
+# ----------------------------------------------------------------------------------------
+# Corner walls of the street canyon (reading of Sect. 3.8 for corners)
+# ----------------------------------------------------------------------------------------
+
+def _one_particle_step(g, F, params, x, y, u, v, e=None):
+    o = oracle.Oracle(g, params, F)
+    if e is None:
+        e = next(f for f in range(g.ne) if o.lam(f, x, y).min() >= 0.0)
+    st = dict(x=np.array([x]), y=np.array([y]), u=np.array([u]), v=np.array([v]),
+              w=np.array([0.0]), om=np.array([1.0]), psi=np.array([0.0]),
+              elem=np.array([e], dtype=np.int32))
+    o.set_particles(st, 0)
+    return o
+
+
+def test_concave_corner_reflects_across_both_walls():
+    """Cavity floor y = 0 meets the cavity wall x = 1.5.  With nu = 0 Eq. 7 moves the
+    particle by U dt alone; a particle driven across both wall lines is reflected across
+    each (the second from the first's image), ending at the double mirror image; Eq. 56
+    stops it and the hit counts once."""
+    w = synth.canyon_workload("canyon_2k")
+    g = w["grid"]
+    P = dict(w["params"], nu=0.0, minnpel=0, source_on=0)
+    h, dt = 0.004, 1e-3
+    x0, y0 = 1.5 + 0.3 * h, 0.3 * h
+    o = _one_particle_step(g, w["fields"], P, x0, y0, -0.8 * h / dt, -0.8 * h / dt)
+    o.step(dt)
+    s = o.get_particles()
+    assert abs(s["x"][0] - (1.5 + 0.5 * h)) <= 1e-13 and abs(s["y"][0] - 0.5 * h) <= 1e-13
+    assert s["u"][0] == 0.0 and s["v"][0] == 0.0 and s["w"][0] == 0.0
+    assert o.lam(int(s["elem"][0]), s["x"][0], s["y"][0]).min() >= -1e-12
+    d = o.diag()
+    assert d["wall_hits"] == 1 and d["lost"] == 0
+
+
+def test_convex_corner_applies_only_the_wall_in_front():
+    """The channel floor y = 1 meets the cavity wall x = 1.5 at a convex corner.  A particle
+    just left of the corner moving down crosses the floor line and is reflected across it
+    alone: the cavity wall's line, oriented into the cavity, has the particle's element
+    behind it and is not applied."""
+    w = synth.canyon_workload("canyon_2k")
+    g = w["grid"]
+    P = dict(w["params"], nu=0.0, minnpel=0, source_on=0)
+    h, dt = 0.004, 1e-3
+    x0, y0 = 1.5 - 0.3 * h, 1.0 + 0.3 * h
+    o = _one_particle_step(g, w["fields"], P, x0, y0, 0.0, -0.8 * h / dt)
+    o.step(dt)
+    s = o.get_particles()
+    assert abs(s["x"][0] - x0) <= 1e-13 and abs(s["y"][0] - (1.0 + 0.5 * h)) <= 1e-13
+    assert s["v"][0] == 0.0
+    d = o.diag()
+    assert d["wall_hits"] == 1 and d["lost"] == 0
