@@ -1032,3 +1032,58 @@ def test_convex_corner_applies_only_the_wall_in_front():
     assert s["v"][0] == 0.0
     d = o.diag()
     assert d["wall_hits"] == 1 and d["lost"] == 0
+
+
+def _in_canyon_domain(x, y, tol=1e-12):
+    """The street-canyon domain: channel [0, 4] x [1, 2] over cavity [1.5, 2.5] x [0, 1]."""
+    chan = (y >= 1.0 - tol) & (y <= 2.0 + tol)
+    cav = (x >= 1.5 - tol) & (x <= 2.5 + tol) & (y >= -tol) & (y <= 1.0 + tol)
+    return chan | cav
+
+
+def test_walk_equals_brute_force_on_the_canyon():
+    """Sect. 3.6 on the street canyon: from random elements to random points of the domain
+    a few elements away (through the periodic seam and around the cavity's re-entrant
+    corners), the walk with its fall-back finds the element brute force finds."""
+    w = synth.canyon_workload("canyon_2k")
+    g = w["grid"]
+    o = oracle.Oracle(g, w["params"], w["fields"])
+    rng = np.random.default_rng(8)
+    n = 0
+    while n < 3000:
+        e0 = int(rng.integers(0, g.ne))
+        xy = _unwrapped_vertices(g, e0)
+        p = xy.mean(0) + rng.normal(0, 0.08, 2)
+        x = p[0] % g.period_x
+        if not _in_canyon_domain(np.array([x]), np.array([p[1]]), -1e-9)[0]:
+            continue
+        n += 1
+        e, hops = o.walk(e0, x, p[1])
+        b = o.brute(x, p[1])
+        assert b >= 0 and e >= 0, (e0, x, p[1])
+        if e != b:
+            assert o.lam(e, x, p[1]).min() > -1e-12
+            assert o.lam(b, x, p[1]).min() > -1e-12
+
+
+def test_canyon_steps_keep_particles_in_the_domain():
+    """P12 on the street canyon (walls, corners, free-slip top, particle-number control):
+    after 10 steps every particle lies in the domain and in its element, none is lost, and
+    the particle count is unchanged."""
+    w = synth.canyon_workload("canyon_2k")
+    P = dict(w["params"], minnpel=w["ppe"] - 2)
+    o = oracle.Oracle(w["grid"], P, w["fields"])
+    o.init_particles(w["ppe"])
+    n0 = o.np_
+    for _ in range(10):
+        o.step(5e-4)
+    s = o.get_particles()
+    assert s["x"].size == n0
+    assert np.all(_in_canyon_domain(s["x"], s["y"]))
+    rng = np.random.default_rng(6)
+    for p in rng.integers(0, n0, 3000):
+        assert o.lam(int(s["elem"][p]), s["x"][p], s["y"][p]).min() >= -1e-12
+    d = o.diag()
+    assert d["lost"] == 0 and d["wall_hits"] > 0 and d["moves"] > 0
+    for k in ("u", "v", "w", "om", "psi"):
+        assert np.all(np.isfinite(s[k]))
