@@ -48,6 +48,7 @@ class Params(C.Structure):
         ("interp_mode", C.c_int), ("source_on", C.c_int),
         ("seed", C.c_uint64), ("instance", C.c_uint32), ("period_x", C.c_double),
         ("cond_mode", C.c_int), ("fox_bins", C.c_int), ("model", C.c_int), ("alpha", C.c_double),
+        ("cfl", C.c_double),
     ]
 
 
@@ -62,7 +63,7 @@ _DEFAULTS = dict(C1=1.85, C2=0.63, C3=5.0, C4=0.25, CT=6.0, CL=0.134, Ceta=72.0,
                  gamma5=0.1, Cw1=0.5, Cw2=0.73, nu=1e-4, c0_mode=0, C0=0.0, tm_mode=0,
                  Cs=0.02, Ct=0.7, Cphi=2.0, src_x=0.5, src_y=0.5, src_r=0.02, bins=(4, 4, 4),
                  min_per_bin=2, minnpel=0, interp_mode=0, source_on=1, seed=1, instance=0,
-                 period_x=0.0, cond_mode=0, fox_bins=5, model=0, alpha=0.5)
+                 period_x=0.0, cond_mode=0, fox_bins=5, model=0, alpha=0.5, cfl=0.7)
 
 
 def make_params(d: dict) -> Params:
@@ -123,6 +124,9 @@ def lib():
             L.orc_get_nodal_stats.argtypes = [C.c_void_p, dp]
             L.orc_get_bins.argtypes = [C.c_void_p, dp, ip]
             L.orc_scalar_stats.argtypes = [C.c_void_p, C.c_int, ip, C.c_int, ip, dp, dp, dp, dp]
+            L.orc_cfl_dt.argtypes = [C.c_void_p, dp]
+            L.orc_last_dt.argtypes = [C.c_void_p]
+            L.orc_last_dt.restype = C.c_double
             L.orc_get_diag.argtypes = [C.c_void_p, C.POINTER(Diag)]
             L.orc_reset_diag.argtypes = [C.c_void_p]
             L.orc_redistribution_counts.argtypes = [ip, C.c_int, C.c_int, ip]
@@ -295,6 +299,17 @@ class Oracle:
         rc = lib().orc_step(self.h, float(dt))
         if rc:
             raise RuntimeError("orc_step failed: %d" % rc)
+
+    def cfl_dt(self) -> float:
+        """The time step of Eq. 26 from the current nodal means."""
+        v = C.c_double()
+        if lib().orc_cfl_dt(self.h, C.byref(v)):
+            raise RuntimeError("orc_cfl_dt: every nodal mean vector is zero")
+        return v.value
+
+    @property
+    def last_dt(self) -> float:
+        return float(lib().orc_last_dt(self.h))
 
     def advance(self, dt):
         return lib().orc_advance(self.h, float(dt))

@@ -65,6 +65,7 @@ struct orc_ctx {
     uint32_t *pid;        /* particle ids (ascending), NULL: the index is the id */
     double *uphi;         /* [ne][3] element <u_a phi'> (Fox's projection, Eq. 66) */
     uint32_t step;
+    double last_dt;       /* the time step of the last orc_step */
     /* statistics */
     int32_t *count;       /* [ne] */
     double *emom;         /* [ne][13] */
@@ -274,6 +275,7 @@ static int params_valid(const orc_params *p)
     if (p->cond_mode == 1 && (p->fox_bins < 1 || p->fox_bins > 256)) return 0;
     if (p->model != 0 && p->model != 1) return 0;
     if (!isfinite(p->alpha)) return 0;
+    if (!(p->cfl > 0.0) || !isfinite(p->cfl)) return 0;
     return 1;
 }
 
@@ -1298,10 +1300,42 @@ int orc_get_particles(const orc_ctx *c, double *x, double *y, double *u, double 
 int orc_num_particles(const orc_ctx *c) { return c->np; }
 uint32_t orc_step_index(const orc_ctx *c) { return c->step; }
 
+/* Eq. 26: dt = CFL min_n sqrt(A_n) / max_n ||<Z>_n||_2, A_n the average area of the
+ * elements around node n and <Z>_n = (<U>, <V>, <W>, <omega>, <psi>) the nodal means of the
+ * last statistics pass.  Reading: the norm is taken literally, omega and psi included;
+ * nodes that no element holding particles surrounds have zero means and take part; the
+ * step cannot be derived (returns -1) when every nodal mean vector is zero. */
+int orc_cfl_dt(const orc_ctx *c, double *dt)
+{
+    double min_sqrt_a = INFINITY, max_norm = 0.0;
+    for (int n = 0; n < c->nn; ++n) {
+        const int m = c->ne_off[n + 1] - c->ne_off[n];
+        if (m > 0) {
+            double a = 0.0;
+            for (int i = c->ne_off[n]; i < c->ne_off[n + 1]; ++i) a += 0.5 * fabs(c->area2[c->ne_list[i]]);
+            const double s = sqrt(a / m);
+            if (s < min_sqrt_a) min_sqrt_a = s;
+        }
+        const double *z = c->nmom + (size_t)NS * n;
+        const double norm = sqrt(z[1] * z[1] + z[2] * z[2] + z[3] * z[3] + z[10] * z[10] + z[11] * z[11]);
+        if (norm > max_norm) max_norm = norm;
+    }
+    if (!(max_norm > 0.0) || !isfinite(min_sqrt_a)) return -1;
+    *dt = c->p.cfl * min_sqrt_a / max_norm;
+    return 0;
+}
+
+double orc_last_dt(const orc_ctx *c) { return c->last_dt; }
+
 /* One timestep (Table 1 order restricted to the particle path): advance and track,
- * particle-number control, then statistics and conditional means for the next step. */
+ * particle-number control, then statistics and conditional means for the next step; with
+ * dt <= 0 the step of Eq. 26 from the current nodal means. */
 int orc_step(orc_ctx *c, double dt)
 {
+    if (!(dt > 0.0)) {
+        if (orc_cfl_dt(c, &dt)) return -1;
+    }
+    c->last_dt = dt;
     int rc = orc_advance(c, dt);
     if (rc) return rc;
     orc_redistribute(c);

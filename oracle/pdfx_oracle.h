@@ -40,6 +40,7 @@ typedef struct orc_params {
     int    model;              /* 0: the full model; 1: the simplified model of Eqs. 46-47
                                   (particle-redistribution test, Sect. 3.7; no no-slip walls) */
     double alpha;              /* Eq. 47 */
+    double cfl;                /* Eq. 26 CFL constant (a step with dt <= 0 takes Eq. 26's dt) */
 } orc_params;
 
 typedef struct orc_diag {
@@ -90,7 +91,9 @@ int  orc_num_particles(const orc_ctx *c);
 uint32_t orc_step_index(const orc_ctx *c);
 
 /* One timestep and its stages (Table 1 order restricted to the particle path). */
-int  orc_step(orc_ctx *c, double dt);
+int  orc_step(orc_ctx *c, double dt);   /* dt <= 0: the time step of Eq. 26 */
+int  orc_cfl_dt(const orc_ctx *c, double *dt);
+double orc_last_dt(const orc_ctx *c);
 int  orc_advance(orc_ctx *c, double dt);      /* Eqs. 7, 27, 19, 24, Sect. 3.8, 3.6 */
 int  orc_redistribute(orc_ctx *c);            /* Sect. 3.7, Appendix B */
 int  orc_statistics(orc_ctx *c);              /* Sect. 3.3 and 3.5, Appendix A */

@@ -1087,3 +1087,27 @@ def test_canyon_steps_keep_particles_in_the_domain():
     assert d["lost"] == 0 and d["wall_hits"] > 0 and d["moves"] > 0
     for k in ("u", "v", "w", "om", "psi"):
         assert np.all(np.isfinite(s[k]))
+
+
+def test_cfl_time_step_closed_form():
+    """Eq. 26 on an unjittered lattice, where every triangle has area dx dy / 2 and so
+    every A_n does: with all particles at U = (2, 0, 0), omega = psi = 0 the nodal mean
+    vectors have norm 2 and dt = CFL sqrt(dx dy / 2) / 2; with psi = 1 the literal norm of
+    Z = (V, omega, psi) is sqrt(5).  A step with dt <= 0 takes that dt."""
+    nx, ny = 8, 6
+    g = synth.channel_grid(nx, ny, lx=2.0, jitter_x=0.0, jitter_y=0.0, seed=1)
+    dx, dy = 2.0 / nx, 1.0 / (ny - 1)
+    F = synth.uniform_fields(g.nn, U=(2.0, 0.0, 0.0))
+    P = base_params(period_x=g.period_x, source_on=0, cfl=0.7)
+    st = _element_state(g, list(range(g.ne)), 6, np.random.default_rng(3),
+                        lambda u, v, w_: np.zeros(u.shape))
+    for k, val in (("u", 2.0), ("v", 0.0), ("w", 0.0), ("om", 0.0)):
+        st[k] = np.full(st["u"].shape, val)
+    for psi, norm in ((0.0, 2.0), (1.0, math.sqrt(5.0))):
+        st["psi"] = np.full(st["u"].shape, psi)
+        o = oracle.Oracle(g, P, F)
+        o.set_particles(st, 0)
+        expect = 0.7 * math.sqrt(0.5 * dx * dy) / norm
+        assert abs(o.cfl_dt() / expect - 1.0) < 1e-14
+        o.step(0.0)
+        assert abs(o.last_dt / expect - 1.0) < 1e-14
