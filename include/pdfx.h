@@ -104,6 +104,8 @@ typedef struct pdfx_params {
                                  moves with the velocity, omega and psi are kept; the grid may
                                  have free-slip boundaries but no no-slip walls */
     double alpha;             /* Eq. 47 (model 1), finite */
+    double cfl;               /* Eq. 26 CFL constant (default 0.7), > 0: a step with dt <= 0
+                                 takes dt = cfl min_n sqrt(A_n) / max_n ||<Z>_n||_2 */
 } pdfx_params;
 
 typedef struct pdfx_allocator {
@@ -213,11 +215,19 @@ int64_t pdfx_num_particles(const void *ctx);
 /* Step counter (the Philox counter word of the next step). */
 uint32_t pdfx_step_index(const void *ctx);
 
-/* One timestep of fixed size dt > 0 (Table 1 order restricted to the particle path):
- * advance and track every particle, particle-number control, statistics and conditional
- * means.  Asynchronous on stream.  PDFX_ERR_ORDER without particles and fields;
- * PDFX_ERR_ARG for model 1 on a grid with no-slip walls (Eqs. 46-47 define none). */
+/* One timestep (Table 1 order restricted to the particle path): advance and track every
+ * particle, particle-number control, statistics and conditional means.  Asynchronous on
+ * stream for dt > 0.  dt <= 0 takes the step of Eq. 26 from the nodal means of the last
+ * statistics pass: dt = cfl min_n sqrt(A_n) / max_n ||<Z>_n||_2, A_n the mean area of the
+ * elements around node n and <Z>_n = (<U>, <V>, <W>, <omega>, <psi>) (the norm as the paper
+ * prints it, omega and psi included); this reads one number back and synchronises the
+ * stream, and is for a single instance (PDFX_ERR_ARG in a batch, or when every nodal mean
+ * vector is zero).  PDFX_ERR_ORDER without particles and fields; PDFX_ERR_ARG for model 1
+ * on a grid with no-slip walls (Eqs. 46-47 define none). */
 int  pdfx_step(void *ctx, double dt, void *stream);
+
+/* The time step of the last pdfx_step (host, 0 before the first step). */
+int  pdfx_last_dt(const void *ctx, double *dt);
 
 /* One timestep of each of n independent contexts (distinct, each with its own grid,
  * parameters and particles), in array order on one stream: the same work and results as n
@@ -226,7 +236,8 @@ int  pdfx_step(void *ctx, double dt, void *stream);
  * code; PDFX_ERR_ARG for n < 1, a NULL or repeated context. */
 int  pdfx_batch_step(void *const *ctxs, int32_t n, double dt, void *stream);
 
-/* nsteps calls of pdfx_step with the same dt.  With use_graph != 0 the steps of whole
+/* nsteps calls of pdfx_step with the same dt (dt <= 0: each step takes Eq. 26's step, and
+ * no graph is used).  With use_graph != 0 the steps of whole
  * re-order cycles (2 sort_every steps, or 1 without re-ordering) are replayed from a CUDA
  * graph captured on the first such call (steps before the next cycle start and after the
  * last whole cycle run as plain launches); the results are those of plain steps.  The

@@ -40,6 +40,7 @@ class Params(C.Structure):
         ("seed", C.c_uint64), ("instance", C.c_uint32), ("period_x", C.c_double),
         ("precision", C.c_int), ("sort_every", C.c_int), ("acc64", C.c_int),
         ("cond_mode", C.c_int), ("fox_bins", C.c_int), ("model", C.c_int), ("alpha", C.c_double),
+        ("cfl", C.c_double),
     ]
 
 
@@ -94,6 +95,7 @@ def lib():
                 "pdfx_num_particles": (i64, [vp]),
                 "pdfx_step_index": (u32, [vp]),
                 "pdfx_step": (C.c_int, [vp, dp, vp]),
+                "pdfx_last_dt": (C.c_int, [vp, C.POINTER(dp)]),
                 "pdfx_batch_step": (C.c_int, [vp, i32, dp, vp]),
                 "pdfx_set_instances": (C.c_int, [vp, i32, C.POINTER(Params), vp]),
                 "pdfx_step_many": (C.c_int, [vp, dp, i32, C.c_int, vp]),
@@ -295,7 +297,14 @@ class Context:
         return out
 
     def step(self, dt: float, stream=None):
+        """One step of dt (dt <= 0: the step of Eq. 26 from the current nodal means)."""
         self._check(lib().pdfx_step(self.h, float(dt), _stream(stream)), "pdfx_step")
+
+    @property
+    def last_dt(self) -> float:
+        v = C.c_double()
+        self._check(lib().pdfx_last_dt(self.h, C.byref(v)), "pdfx_last_dt")
+        return v.value
 
     def autotune(self, dt: float, stream=None) -> dict:
         blk, se = C.c_int32(0), C.c_int32(0)

@@ -70,6 +70,7 @@ bool params_valid(const pdfx_params& p) {
   if (p.cond_mode == 1 && (p.fox_bins < 1 || p.fox_bins > 256)) return false;
   if (p.model != 0 && p.model != 1) return false;
   if (!std::isfinite(p.alpha)) return false;
+  if (!(p.cfl > 0.0) || !std::isfinite(p.cfl)) return false;
   return true;
 }
 
@@ -336,6 +337,7 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
 
 template <typename T>
 int do_step(Ctx& c, double dt, cudaStream_t s) {
+  c.last_dt = dt;
   Particles<T> p = carve<T>(c.pbuf[c.cur], c.np);
   PDFX_CUDA(cudaMemsetAsync(c.plan.cnt, 0, sizeof(int32_t) * c.ne, s));
   {
@@ -674,6 +676,22 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
                                 : upload_grid<double>(c, g, topo, walls, fsl, fse);
   if (rc) return rc;
   PDFX_TRY(alloc_into(c, c.wall2, wall2.size()));
+  PDFX_TRY(alloc_into(c, c.dnorm, static_cast<size_t>(1)));
+  {
+    // Eq. 26's numerator: min over nodes of sqrt(A_n), A_n the mean area of its elements
+    double m = 0.0;
+    bool any = false;
+    for (int32_t n = 0; n < nn; ++n) {
+      const int32_t k = off[n + 1] - off[n];
+      if (k <= 0) continue;
+      double a = 0.0;
+      for (int32_t i = off[n]; i < off[n + 1]; ++i) a += 0.5 * std::fabs(g.area2[lst[i]]);
+      const double r = std::sqrt(a / k);
+      if (!any || r < m) m = r;
+      any = true;
+    }
+    c.min_sqrt_an = m;
+  }
   PDFX_CUDA(cudaMemcpy(c.wall2, wall2.data(), sizeof(int32_t) * wall2.size(), cudaMemcpyHostToDevice));
   PDFX_TRY(alloc_into(c, c.ne_off, off.size()));
   PDFX_TRY(alloc_into(c, c.ne_list, lst.size()));
@@ -897,6 +915,19 @@ Ctx* as_ctx(void* p) { return static_cast<Ctx*>(p); }
 // walls (free-slip boundaries and a periodic direction only).
 bool model_fits_grid(const Ctx& c) { return c.prm.model != 1 || c.n_wall_lines == 0; }
 
+// Eq. 26 from the nodal means of the last statistics pass (synchronises the stream).
+int cfl_dt(Ctx& c, cudaStream_t s, double* dt) {
+  if (c.K > 1 || !c.dnorm || c.nn <= 0) return PDFX_ERR_ARG;
+  launch_cfl_norm(c.nmom, c.nn, c.dnorm, s);
+  c.launches++;
+  double norm = 0.0;
+  PDFX_CUDA(cudaMemcpyAsync(&norm, c.dnorm, sizeof(double), cudaMemcpyDeviceToHost, s));
+  PDFX_CUDA(cudaStreamSynchronize(s));
+  if (!(norm > 0.0) || !std::isfinite(norm)) return PDFX_ERR_ARG;
+  *dt = c.prm.cfl * c.min_sqrt_an / norm;
+  return (*dt > 0.0 && std::isfinite(*dt)) ? PDFX_OK : PDFX_ERR_ARG;
+}
+
 }  // namespace
 }  // namespace pdfx
 
@@ -919,6 +950,7 @@ void pdfx_default_params(pdfx_params* p) {
   p->fox_bins = 5;
   p->model = 0;
   p->alpha = 0.5;
+  p->cfl = 0.7;
   p->min_per_bin = 2;
   p->minnpel = 0;
   p->interp_mode = 0;
@@ -1128,6 +1160,13 @@ int pdfx_get_particles(void* ctx, pdfx_soa* s, int on_device, void* stream) {
                                : do_get_particles<double>(*c, s, on_device, as_stream(stream));
 }
 
+int pdfx_last_dt(const void* ctx, double* dt) {
+  const Ctx* c = static_cast<const Ctx*>(ctx);
+  if (!c || !dt) return PDFX_ERR_ARG;
+  *dt = c->last_dt;
+  return PDFX_OK;
+}
+
 int64_t pdfx_num_particles(const void* ctx) {
   const Ctx* c = static_cast<const Ctx*>(ctx);
   return c ? c->np : 0;
@@ -1140,8 +1179,12 @@ uint32_t pdfx_step_index(const void* ctx) {
 
 int pdfx_step_many(void* ctx, double dt, int32_t nsteps, int use_graph, void* stream) {
   Ctx* c = as_ctx(ctx);
-  if (!c || !(dt > 0.0) || nsteps < 0 || !model_fits_grid(*c)) return PDFX_ERR_ARG;
+  if (!c || nsteps < 0 || !model_fits_grid(*c) || std::isnan(dt)) return PDFX_ERR_ARG;
   if (!c->pbuf[0] || !c->have_fields) return PDFX_ERR_ORDER;
+  if (!(dt > 0.0)) {   // Eq. 26 at every step: plain steps
+    for (int32_t i = 0; i < nsteps; ++i) PDFX_TRY(pdfx_step(ctx, dt, stream));
+    return PDFX_OK;
+  }
   return c->prm.precision == 1 ? do_step_many<float>(*c, dt, nsteps, use_graph, as_stream(stream))
                                : do_step_many<double>(*c, dt, nsteps, use_graph, as_stream(stream));
 }
@@ -1156,8 +1199,9 @@ int pdfx_autotune(void* ctx, double dt, int32_t* adv_block, int32_t* sort_every,
 
 int pdfx_step(void* ctx, double dt, void* stream) {
   Ctx* c = as_ctx(ctx);
-  if (!c || !(dt > 0.0) || !model_fits_grid(*c)) return PDFX_ERR_ARG;
+  if (!c || !model_fits_grid(*c) || std::isnan(dt)) return PDFX_ERR_ARG;
   if (!c->pbuf[0] || !c->have_fields) return PDFX_ERR_ORDER;
+  if (!(dt > 0.0)) PDFX_TRY(cfl_dt(*c, as_stream(stream), &dt));
   return c->prm.precision == 1 ? do_step<float>(*c, dt, as_stream(stream))
                                : do_step<double>(*c, dt, as_stream(stream));
 }

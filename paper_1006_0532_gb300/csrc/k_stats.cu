@@ -804,6 +804,34 @@ void launch_node_average(const double* emom, const int32_t* ne_off, const int32_
   node_average_kernel<<<(nn + 127) / 128, 128, 0, s>>>(emom, ne_off, ne_list, nn, nmom);
 }
 
+namespace {
+
+// Eq. 26's denominator: the largest ||(<U>, <V>, <W>, <omega>, <psi>)||_2 over the nodes.
+__global__ void __launch_bounds__(256) cfl_norm_kernel(const double* __restrict__ nmom, int32_t nn,
+                                                      double* out) {
+  __shared__ double red[8];
+  double m = 0.0;
+  for (int32_t n = threadIdx.x; n < nn; n += blockDim.x) {
+    const double* z = nmom + static_cast<size_t>(kNS) * n;
+    const double v = sqrt(z[1] * z[1] + z[2] * z[2] + z[3] * z[3] + z[10] * z[10] + z[11] * z[11]);
+    m = fmax(m, v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(kFull, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int w = 1; w < static_cast<int>(blockDim.x >> 5); ++w) m = fmax(m, red[w]);
+    out[0] = m;
+  }
+}
+
+}  // namespace
+
+void launch_cfl_norm(const double* nmom, int32_t nn, double* out, cudaStream_t s) {
+  cfl_norm_kernel<<<1, 256, 0, s>>>(nmom, nn, out);
+}
+
 #define PDFX_INSTANTIATE(T)                                                                    \
   template void launch_redistribute<T>(Particles<T>, Plan&, int, const InstDev<T>*, int32_t,   \
                                        int64_t, const ElemGeo<T>*, const ElemTopo*,            \

@@ -164,6 +164,9 @@ struct Ctx {
   void* walls = nullptr;        // Line<T>[n_walls]
   void* fsedges = nullptr;      // Line<T>[]: each free-slip boundary edge's own line
   int n_wall_lines = 0;         // no-slip wall lines of the grid
+  double min_sqrt_an = 0.0;     // min over nodes of sqrt(mean area of the elements around it)
+  double last_dt = 0.0;         // the time step of the last step
+  double* dnorm = nullptr;      // device scalar: max nodal ||<Z>|| (Eq. 26)
   void* fslines = nullptr;      // Line<T>[n_fs]
   int32_t* ne_off = nullptr;    // [nn + 1]
   int32_t* ne_list = nullptr;   // [3 ne]
@@ -257,6 +260,8 @@ template <typename T>
 void launch_stats_tiles(const StatsArgs<T>& a, int num_sms, cudaStream_t s);   // k_bins_f32.cu / k_bins_f64.cu
 void launch_node_average(const double* emom, const int32_t* ne_off, const int32_t* ne_list,
                          int32_t nn, double* nmom, cudaStream_t s);
+// Eq. 26: max over nodes of ||(<U>, <V>, <W>, <omega>, <psi>)||_2 into out[0] (one block).
+void launch_cfl_norm(const double* nmom, int32_t nn, double* out, cudaStream_t s);
 
 // Accumulators of the scalar statistics of n probe elements over nb psi bins (fixed-point
 // sums in two's complement; lo and hi hold order-preserving images of doubles).

@@ -485,3 +485,24 @@ def test_fox_projection_large_and_degenerate_elements(precision):
         rank = np.argsort(np.argsort(pids, kind="stable"), kind="stable")
         assert np.array_equal(co[sel], (nc * rank) // n)
     assert c.check() == 0
+
+
+def test_cfl_steps_match_oracle_f64():
+    """Steps with dt <= 0 take Eq. 26's step from the nodal means of the last statistics
+    pass, on both sides: the step sizes agree to 1e-12 and the states as in the fixed-step
+    parity."""
+    w, g, o, c, ppe = both("channel_2k")
+    o.init_particles(ppe)
+    c.init_particles(ppe)
+    for _ in range(5):
+        o.step(0.0)
+        c.step(0.0)
+        assert abs(c.last_dt / o.last_dt - 1.0) <= 1e-12
+        assert 0.0 < o.last_dt < 1.0
+    so, sg = o.get_particles(), c.get_particles()
+    diff = sg["elem"] != so["elem"]
+    for p in np.where(diff)[0]:
+        assert o.lam(sg["elem"][p], sg["x"][p], sg["y"][p]).min() > -1e-12
+    assert diff.sum() <= 2
+    compare_state(sg, so, g.period_x, 1e-12)
+    assert c.check() == 0
