@@ -125,6 +125,9 @@ def lib():
             L.orc_get_bins.argtypes = [C.c_void_p, dp, ip]
             L.orc_scalar_stats.argtypes = [C.c_void_p, C.c_int, ip, C.c_int, ip, dp, dp, dp, dp]
             L.orc_cfl_dt.argtypes = [C.c_void_p, dp]
+            L.orc_node_gradient.argtypes = [C.c_void_p, dp, dp]
+            L.orc_derive_fields.argtypes = [C.c_void_p]
+            L.orc_get_fields.argtypes = [C.c_void_p, dp]
             L.orc_last_dt.argtypes = [C.c_void_p]
             L.orc_last_dt.restype = C.c_double
             L.orc_get_diag.argtypes = [C.c_void_p, C.POINTER(Diag)]
@@ -310,6 +313,23 @@ class Oracle:
     @property
     def last_dt(self) -> float:
         return float(lib().orc_last_dt(self.h))
+
+    def node_gradient(self, q):
+        """Node-transferred gradient (Eqs. 39-40) of a nodal quantity: [nn][2]."""
+        qq = np.ascontiguousarray(q, dtype=np.float64)
+        out = np.zeros((qq.size, 2))
+        lib().orc_node_gradient(self.h, _dp(qq), _dp(out))
+        return out
+
+    def fields(self):
+        out = np.zeros((self.nn, 32))
+        lib().orc_get_fields(self.h, _dp(out))
+        return out
+
+    def derive_fields(self):
+        """Overwrite the nodal fields the particles' statistics provide (slots 0-2, 5-13,
+        23-29) from the current nodal statistics."""
+        lib().orc_derive_fields(self.h)
 
     def advance(self, dt):
         return lib().orc_advance(self.h, float(dt))

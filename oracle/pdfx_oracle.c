@@ -1327,6 +1327,80 @@ int orc_cfl_dt(const orc_ctx *c, double *dt)
 
 double orc_last_dt(const orc_ctx *c) { return c->last_dt; }
 
+/* Sect. 3.4.  Eq. 39 with the shapefunction derivatives of Eq. 40 (constant over the
+ * element, from its vertices in the element's frame, x_CA = x_C - x_A and so on, and twice
+ * its area): dQ/dx = sum_j dN^j/dx Q_j.  The element values are then transferred to the
+ * nodes as the plain mean over the elements around each node. */
+void orc_node_gradient(const orc_ctx *c, const double *q, double *grad)
+{
+    for (int n = 0; n < c->nn; ++n) {
+        double gx = 0.0, gy = 0.0;
+        const int m = c->ne_off[n + 1] - c->ne_off[n];
+        for (int i = c->ne_off[n]; i < c->ne_off[n + 1]; ++i) {
+            const int e = c->ne_list[i];
+            const double *vx = c->vx + 3 * e, *vy = c->vy + 3 * e;
+            const double xBA = vx[1] - vx[0], yBA = vy[1] - vy[0];
+            const double xCA = vx[2] - vx[0], yCA = vy[2] - vy[0];
+            const double inv = 1.0 / c->area2[e];
+            const double dNx[3] = {(-yCA + yBA) * inv, yCA * inv, -yBA * inv};
+            const double dNy[3] = {(xCA - xBA) * inv, -xCA * inv, xBA * inv};
+            const int32_t *t = c->tri + 3 * e;
+            gx += dNx[0] * q[t[0]] + dNx[1] * q[t[1]] + dNx[2] * q[t[2]];
+            gy += dNy[0] * q[t[0]] + dNy[1] * q[t[1]] + dNy[2] * q[t[2]];
+        }
+        grad[2 * n] = m > 0 ? gx / m : 0.0;
+        grad[2 * n + 1] = m > 0 ? gy / m : 0.0;
+    }
+}
+
+/* The nodal fields that the particles' own statistics provide (the non-hybrid coupling of
+ * Sect. 3.3-3.4): <U_i> (slots 0-2) = the nodal means; d<U_i>/dx_j (slots 5-10, i-major)
+ * = their node-transferred gradients; the laplacian of <U_i> (slots 11-13) =
+ * d/dx (d<U_i>/dx) + d/dy (d<U_i>/dy) by the same procedure applied to the nodal first
+ * derivatives (the two-pass second derivatives of Sect. 3.4); <u_i u_j> (slots 23-28) and
+ * <omega> (slot 29) = the nodal moments.  The mean-pressure gradient, the
+ * elliptic-relaxation tensor and the wall frequency (slots 3-4, 14-22, 30) come from the
+ * Eulerian solves and are kept. */
+int orc_get_fields(const orc_ctx *c, double *out)
+{
+    memcpy(out, c->fields, sizeof(double) * (size_t)NF * c->nn);
+    return 0;
+}
+
+int orc_derive_fields(orc_ctx *c)
+{
+    const int nn = c->nn;
+    double *q = (double *)malloc(sizeof(double) * (size_t)nn);
+    double *g1 = (double *)malloc(sizeof(double) * 2 * (size_t)nn);
+    double *g2 = (double *)malloc(sizeof(double) * 2 * (size_t)nn);
+    double *first = (double *)malloc(sizeof(double) * 6 * (size_t)nn);
+    double *lap = (double *)calloc(3 * (size_t)nn, sizeof(double));
+    for (int i = 0; i < 3; ++i) {
+        for (int n = 0; n < nn; ++n) q[n] = c->nmom[(size_t)NS * n + 1 + i];
+        orc_node_gradient(c, q, g1);
+        for (int n = 0; n < nn; ++n) {
+            first[6 * n + 2 * i] = g1[2 * n];
+            first[6 * n + 2 * i + 1] = g1[2 * n + 1];
+        }
+        for (int j = 0; j < 2; ++j) {
+            for (int n = 0; n < nn; ++n) q[n] = g1[2 * n + j];
+            orc_node_gradient(c, q, g2);
+            for (int n = 0; n < nn; ++n) lap[3 * n + i] += g2[2 * n + j];
+        }
+    }
+    for (int n = 0; n < nn; ++n) {
+        double *f = c->fields + (size_t)NF * n;
+        const double *m = c->nmom + (size_t)NS * n;
+        for (int i = 0; i < 3; ++i) f[i] = m[1 + i];
+        for (int k = 0; k < 6; ++k) f[5 + k] = first[6 * n + k];
+        for (int i = 0; i < 3; ++i) f[11 + i] = lap[3 * n + i];
+        for (int k = 0; k < 6; ++k) f[23 + k] = m[4 + k];
+        f[29] = m[10];
+    }
+    free(q); free(g1); free(g2); free(first); free(lap);
+    return 0;
+}
+
 /* One timestep (Table 1 order restricted to the particle path): advance and track,
  * particle-number control, then statistics and conditional means for the next step; with
  * dt <= 0 the step of Eq. 26 from the current nodal means. */

@@ -93,6 +93,12 @@ uint32_t orc_step_index(const orc_ctx *c);
 /* One timestep and its stages (Table 1 order restricted to the particle path). */
 int  orc_step(orc_ctx *c, double dt);   /* dt <= 0: the time step of Eq. 26 */
 int  orc_cfl_dt(const orc_ctx *c, double *dt);
+/* Sect. 3.4: node-transferred gradient of a nodal quantity q[nn] (Eqs. 39-40, then the mean
+ * over the elements around each node): grad[nn][2]. */
+void orc_node_gradient(const orc_ctx *c, const double *q, double *grad);
+/* Nodal fields from the particles' nodal statistics (slots 0-2, 5-13, 23-29). */
+int  orc_derive_fields(orc_ctx *c);
+int  orc_get_fields(const orc_ctx *c, double *out /* [nn][32] */);
 double orc_last_dt(const orc_ctx *c);
 int  orc_advance(orc_ctx *c, double dt);      /* Eqs. 7, 27, 19, 24, Sect. 3.8, 3.6 */
 int  orc_redistribute(orc_ctx *c);            /* Sect. 3.7, Appendix B */

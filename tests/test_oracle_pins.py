@@ -1111,3 +1111,74 @@ def test_cfl_time_step_closed_form():
         assert abs(o.cfl_dt() / expect - 1.0) < 1e-14
         o.step(0.0)
         assert abs(o.last_dt / expect - 1.0) < 1e-14
+
+
+# ----------------------------------------------------------------------------------------
+# Eulerian derivatives from nodal values (Sect. 3.4, Eqs. 39-40)
+# ----------------------------------------------------------------------------------------
+
+def _same_diagonal_lattice(nx, ny, lx=2.0):
+    """A periodic lattice on [0, lx] x [0, 1] with every quad split along the same diagonal
+    (so every interior node's star has as many elements above as below), walls at y = 0, 1."""
+    xs, ys = np.arange(nx) * (lx / nx), np.linspace(0.0, 1.0, ny)
+    X, Y = np.meshgrid(xs, ys)
+    xy = np.stack([X.ravel(), Y.ravel()], 1)
+    tri = []
+    for j in range(ny - 1):
+        for i in range(nx):
+            a, b = j * nx + i, j * nx + (i + 1) % nx
+            c, d = (j + 1) * nx + (i + 1) % nx, (j + 1) * nx + i
+            tri += [[a, b, c], [a, c, d]]
+    tri = np.array(tri, dtype=np.int32)
+    y = xy[:, 1]
+    tag = np.zeros(tri.shape, dtype=np.int8)
+    for k in range(3):
+        p, q = tri[:, (k + 1) % 3], tri[:, (k + 2) % 3]
+        tag[:, k] = (((y[p] == 0) & (y[q] == 0)) | ((y[p] == 1) & (y[q] == 1))).astype(np.int8)
+    return synth.Grid(node_xy=xy, tri=tri, edge_tag=tag, period_x=lx)
+
+
+def test_node_gradient_linear_and_quadratic():
+    """Eqs. 39-40 with the node transfer: a field linear in y has the exact gradient at every
+    node of a jittered periodic grid (element gradients are exact, their means too); y^2 on
+    a lattice whose interior nodes see as many elements above as below gets 2y at the
+    interior nodes, and the second pass gets the exact second derivative 2 at nodes two rows
+    or more from the boundaries."""
+    g = synth.channel_grid(12, 9, jitter_x=0.2, jitter_y=0.1, seed=6)
+    o = oracle.Oracle(g, base_params(period_x=g.period_x), synth.uniform_fields(g.nn))
+    y = g.node_xy[:, 1]
+    gr = o.node_gradient(1.0 + 2.0 * y)
+    assert np.abs(gr[:, 0]).max() < 1e-12 and np.abs(gr[:, 1] - 2.0).max() < 1e-12
+    g = _same_diagonal_lattice(12, 9)
+    o = oracle.Oracle(g, base_params(period_x=g.period_x), synth.uniform_fields(g.nn))
+    y = g.node_xy[:, 1]
+    h = 1.0 / 8
+    g1 = o.node_gradient(y * y)
+    inner = (y > 0.5 * h) & (y < 1 - 0.5 * h)
+    assert np.abs(g1[inner, 1] - 2 * y[inner]).max() < 1e-12 and np.abs(g1[:, 0]).max() < 1e-12
+    g2 = o.node_gradient(g1[:, 1])
+    deep = (y > 1.5 * h) & (y < 1 - 1.5 * h)
+    assert np.abs(g2[deep, 1] - 2.0).max() < 1e-12
+
+
+def test_derived_fields_from_statistics():
+    """The fields the particles' statistics provide: <U_i>, <u_i u_j> and <omega> are the
+    nodal moments; the gradient and laplacian slots are the node transfers of Eqs. 39-40
+    applied once and twice; the slots of the Eulerian solves are kept."""
+    w = synth.workload("channel_tiny")
+    o = oracle.Oracle(w["grid"], w["params"], w["fields"])
+    o.init_particles(60)
+    o.step(w["dt"])
+    before = o.fields()
+    o.derive_fields()
+    f, m = o.fields(), o.nodal_stats()
+    np.testing.assert_array_equal(f[:, 0:3], m[:, 1:4])
+    np.testing.assert_array_equal(f[:, 23:29], m[:, 4:10])
+    np.testing.assert_array_equal(f[:, 29], m[:, 10])
+    for i in range(3):
+        g1 = o.node_gradient(m[:, 1 + i])
+        np.testing.assert_array_equal(f[:, 5 + 2 * i:7 + 2 * i], g1)
+        lap = o.node_gradient(g1[:, 0])[:, 0] + o.node_gradient(g1[:, 1])[:, 1]
+        np.testing.assert_allclose(f[:, 11 + i], lap, rtol=0, atol=1e-12 * max(1.0, np.abs(lap).max()))
+    for k in (3, 4, 14, 15, 16, 17, 18, 19, 20, 21, 22, 30):
+        np.testing.assert_array_equal(f[:, k], before[:, k])
