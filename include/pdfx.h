@@ -229,6 +229,21 @@ int  pdfx_step(void *ctx, double dt, void *stream);
 /* The time step of the last pdfx_step (host, 0 before the first step). */
 int  pdfx_last_dt(const void *ctx, double *dt);
 
+/* The nodal fields the particles' own statistics provide (the non-hybrid coupling of Sect.
+ * 3.3-3.4), from the nodal statistics of the last statistics pass, written into the
+ * context's fields: <U_i> (slots 0-2), d<U_i>/dx_j (slots 5-10) = the node transfer (mean
+ * over the elements around a node) of Eq. 39's element gradients with Eq. 40's
+ * shapefunction derivatives, the laplacian of <U_i> (slots 11-13) by the same procedure
+ * applied to the first derivatives (Sect. 3.4's two passes), <u_i u_j> (slots 23-28) and
+ * <omega> (slot 29).  The slots the Eulerian solves provide (mean-pressure gradient 3-4,
+ * elliptic-relaxation tensor 14-22, wall frequency 30) keep the values of pdfx_set_fields.
+ * Asynchronous on stream (a scratch block of 18 (ne + nn) doubles is allocated and freed).
+ * PDFX_ERR_ORDER before fields and statistics exist. */
+int  pdfx_derive_fields(void *ctx, void *stream);
+
+/* The context's nodal fields [nn][32] in FP64 (host; the FP32 form's are widened). */
+int  pdfx_get_fields(void *ctx, double *out, void *stream);
+
 /* One timestep of each of n independent contexts (distinct, each with its own grid,
  * parameters and particles), in array order on one stream: the same work and results as n
  * calls of pdfx_step.  A set of instances stepped with one launch per stage is a single

@@ -96,6 +96,8 @@ def lib():
                 "pdfx_step_index": (u32, [vp]),
                 "pdfx_step": (C.c_int, [vp, dp, vp]),
                 "pdfx_last_dt": (C.c_int, [vp, C.POINTER(dp)]),
+                "pdfx_derive_fields": (C.c_int, [vp, vp]),
+                "pdfx_get_fields": (C.c_int, [vp, vp, vp]),
                 "pdfx_batch_step": (C.c_int, [vp, i32, dp, vp]),
                 "pdfx_set_instances": (C.c_int, [vp, i32, C.POINTER(Params), vp]),
                 "pdfx_step_many": (C.c_int, [vp, dp, i32, C.c_int, vp]),
@@ -299,6 +301,15 @@ class Context:
     def step(self, dt: float, stream=None):
         """One step of dt (dt <= 0: the step of Eq. 26 from the current nodal means)."""
         self._check(lib().pdfx_step(self.h, float(dt), _stream(stream)), "pdfx_step")
+
+    def derive_fields(self, stream=None):
+        """Overwrite the fields the particles' statistics provide (pdfx_derive_fields)."""
+        self._check(lib().pdfx_derive_fields(self.h, _stream(stream)), "pdfx_derive_fields")
+
+    def fields(self, stream=None):
+        out = np.zeros((self.nn, 32))
+        self._check(lib().pdfx_get_fields(self.h, out.ctypes.data, _stream(stream)), "pdfx_get_fields")
+        return out
 
     @property
     def last_dt(self) -> float:

@@ -1234,6 +1234,48 @@ int pdfx_get_nodal_stats(void* ctx, double* out, int on_device, void* stream) {
   return copy_out(out, c->nmom, sizeof(double) * kNS * c->nn, on_device, as_stream(stream));
 }
 
+int pdfx_derive_fields(void* ctx, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c) return PDFX_ERR_ARG;
+  if (!c->have_grid || !c->have_fields || !c->pbuf[0]) return PDFX_ERR_ORDER;
+  const cudaStream_t s = as_stream(stream);
+  const size_t n = 18 * (static_cast<size_t>(c->ne) + static_cast<size_t>(c->nn));
+  auto* scratch = static_cast<double*>(dev_alloc(*c, sizeof(double) * n));
+  if (!scratch) return PDFX_ERR_ALLOC;
+  const int32_t* einst = c->K > 1 ? c->einst : nullptr;
+  if (c->prm.precision == 1)
+    launch_derive_fields<float>(static_cast<const ElemGeo<float>*>(c->geo), c->topo, c->ne,
+                                c->prm.period_x, einst, static_cast<const InstDev<float>*>(c->inst),
+                                c->ne_off, c->ne_list, c->nn, c->nmom, scratch,
+                                static_cast<float*>(c->fields), s);
+  else
+    launch_derive_fields<double>(static_cast<const ElemGeo<double>*>(c->geo), c->topo, c->ne,
+                                 c->prm.period_x, einst, static_cast<const InstDev<double>*>(c->inst),
+                                 c->ne_off, c->ne_list, c->nn, c->nmom, scratch,
+                                 static_cast<double*>(c->fields), s);
+  c->launches += 5;
+  int rc = cerr(cudaGetLastError());
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == PDFX_OK) rc = PDFX_ERR_CUDA;
+  dev_free(*c, scratch);
+  drop_graph(*c);
+  return rc;
+}
+
+int pdfx_get_fields(void* ctx, double* out, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !out) return PDFX_ERR_ARG;
+  if (!c->have_fields) return PDFX_ERR_ORDER;
+  const size_t n = static_cast<size_t>(kNF) * c->nn;
+  const cudaStream_t s = as_stream(stream);
+  if (c->prm.precision == 1) {
+    std::vector<float> h(n);
+    PDFX_TRY(copy_out(h.data(), c->fields, sizeof(float) * n, 0, s));
+    for (size_t i = 0; i < n; ++i) out[i] = static_cast<double>(h[i]);
+    return PDFX_OK;
+  }
+  return copy_out(out, c->fields, sizeof(double) * n, 0, s);
+}
+
 int pdfx_get_element_stats(void* ctx, double* out, int32_t* counts, int on_device, void* stream) {
   Ctx* c = as_ctx(ctx);
   if (!c) return PDFX_ERR_ARG;

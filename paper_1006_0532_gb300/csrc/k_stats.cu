@@ -832,6 +832,99 @@ void launch_cfl_norm(const double* nmom, int32_t nn, double* out, cudaStream_t s
   cfl_norm_kernel<<<1, 256, 0, s>>>(nmom, nn, out);
 }
 
+namespace {
+
+// Eq. 39 with Eq. 40's shapefunction derivatives, per element, for nq nodal quantities
+// q[n * stride + off + i]: out[e][2 i + 0/1] = (dQ_i/dx, dQ_i/dy).  The stored node x are the
+// canonical images: x differences are taken as minimum images of the element's period (its
+// instance's in a batch, einst and inst non-null).
+template <typename T>
+__global__ void elem_gradient_kernel(const ElemGeo<T>* __restrict__ geo, const ElemTopo* __restrict__ topo,
+                                     int32_t ne, double L0, const int32_t* __restrict__ einst,
+                                     const InstDev<T>* __restrict__ inst, const double* __restrict__ q,
+                                     int stride, int off, int nq, double* __restrict__ out) {
+  const int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  const ElemGeo<T> g = geo[e];
+  const ElemTopo t = topo[e];
+  const double L = einst ? static_cast<double>(inst[einst[e]].m.period_x) : L0;
+  const double xBA = min_image(static_cast<double>(g.x1) - static_cast<double>(g.x0), L);
+  const double yBA = static_cast<double>(g.y1) - static_cast<double>(g.y0);
+  const double xCA = min_image(static_cast<double>(g.x2) - static_cast<double>(g.x0), L);
+  const double yCA = static_cast<double>(g.y2) - static_cast<double>(g.y0);
+  const double inv = static_cast<double>(g.inv2a);
+  const double dNx0 = (-yCA + yBA) * inv, dNx1 = yCA * inv, dNx2 = -yBA * inv;
+  const double dNy0 = (xCA - xBA) * inv, dNy1 = -xCA * inv, dNy2 = xBA * inv;
+  for (int i = 0; i < nq; ++i) {
+    const double q0 = q[static_cast<size_t>(stride) * t.n0 + off + i];
+    const double q1 = q[static_cast<size_t>(stride) * t.n1 + off + i];
+    const double q2 = q[static_cast<size_t>(stride) * t.n2 + off + i];
+    out[static_cast<size_t>(2 * nq) * e + 2 * i] = dNx0 * q0 + dNx1 * q1 + dNx2 * q2;
+    out[static_cast<size_t>(2 * nq) * e + 2 * i + 1] = dNy0 * q0 + dNy1 * q1 + dNy2 * q2;
+  }
+}
+
+// Transfer to nodes: the mean of w element values over the elements around each node
+// (ascending element id).
+__global__ void node_mean_kernel(const int32_t* __restrict__ ne_off, const int32_t* __restrict__ ne_list,
+                                 int32_t nn, const double* __restrict__ ev, int w, double* __restrict__ out) {
+  const int32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  const int32_t a = ne_off[n], b = ne_off[n + 1];
+  for (int k = 0; k < w; ++k) {
+    double s = 0.0;
+    for (int32_t i = a; i < b; ++i) s += ev[static_cast<size_t>(w) * ne_list[i] + k];
+    out[static_cast<size_t>(w) * n + k] = b > a ? s / (b - a) : 0.0;
+  }
+}
+
+// The nodal fields the statistics provide: <U_i>, d<U_i>/dx_j, laplacians, <u_i u_j>, <omega>.
+template <typename T>
+__global__ void write_fields_kernel(int32_t nn, const double* __restrict__ nmom,
+                                    const double* __restrict__ g1, const double* __restrict__ g2,
+                                    T* __restrict__ F) {
+  const int32_t n = blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= nn) return;
+  const double* m = nmom + static_cast<size_t>(kNS) * n;
+  T* f = F + static_cast<size_t>(kNF) * n;
+  for (int i = 0; i < 3; ++i) f[i] = static_cast<T>(m[1 + i]);
+  for (int k = 0; k < 6; ++k) f[5 + k] = static_cast<T>(g1[6 * static_cast<size_t>(n) + k]);
+  // g2[n][12]: (d/dx, d/dy) of each of the 6 first derivatives, (dU_i/dx at 2i, dU_i/dy at 2i+1)
+  for (int i = 0; i < 3; ++i)
+    f[11 + i] = static_cast<T>(g2[12 * static_cast<size_t>(n) + 4 * i] + g2[12 * static_cast<size_t>(n) + 4 * i + 3]);
+  for (int k = 0; k < 6; ++k) f[23 + k] = static_cast<T>(m[4 + k]);
+  f[29] = static_cast<T>(m[10]);
+}
+
+}  // namespace
+
+template <typename T>
+void launch_derive_fields(const ElemGeo<T>* geo, const ElemTopo* topo, int32_t ne, double period_x,
+                          const int32_t* einst, const InstDev<T>* inst, const int32_t* ne_off,
+                          const int32_t* ne_list, int32_t nn, const double* nmom, double* scratch,
+                          T* fields, cudaStream_t s) {
+  if (ne <= 0 || nn <= 0) return;
+  double* eg1 = scratch;                                   // [ne][6]
+  double* ng1 = eg1 + 6 * static_cast<size_t>(ne);         // [nn][6]
+  double* eg2 = ng1 + 6 * static_cast<size_t>(nn);         // [ne][12]
+  double* ng2 = eg2 + 12 * static_cast<size_t>(ne);        // [nn][12]
+  const unsigned be = static_cast<unsigned>((ne + 127) / 128), bn = static_cast<unsigned>((nn + 127) / 128);
+  elem_gradient_kernel<T><<<be, 128, 0, s>>>(geo, topo, ne, period_x, einst, inst, nmom, kNS, 1, 3, eg1);
+  node_mean_kernel<<<bn, 128, 0, s>>>(ne_off, ne_list, nn, eg1, 6, ng1);
+  elem_gradient_kernel<T><<<be, 128, 0, s>>>(geo, topo, ne, period_x, einst, inst, ng1, 6, 0, 6, eg2);
+  node_mean_kernel<<<bn, 128, 0, s>>>(ne_off, ne_list, nn, eg2, 12, ng2);
+  write_fields_kernel<T><<<bn, 128, 0, s>>>(nn, nmom, ng1, ng2, fields);
+}
+
+template void launch_derive_fields<float>(const ElemGeo<float>*, const ElemTopo*, int32_t, double,
+                                          const int32_t*, const InstDev<float>*, const int32_t*,
+                                          const int32_t*, int32_t, const double*, double*, float*,
+                                          cudaStream_t);
+template void launch_derive_fields<double>(const ElemGeo<double>*, const ElemTopo*, int32_t, double,
+                                           const int32_t*, const InstDev<double>*, const int32_t*,
+                                           const int32_t*, int32_t, const double*, double*, double*,
+                                           cudaStream_t);
+
 #define PDFX_INSTANTIATE(T)                                                                    \
   template void launch_redistribute<T>(Particles<T>, Plan&, int, const InstDev<T>*, int32_t,   \
                                        int64_t, const ElemGeo<T>*, const ElemTopo*,            \

@@ -506,3 +506,36 @@ def test_cfl_steps_match_oracle_f64():
     assert diff.sum() <= 2
     compare_state(sg, so, g.period_x, 1e-12)
     assert c.check() == 0
+
+
+def test_derived_fields_match_oracle_f64():
+    """The fields the particles' statistics provide (Sect. 3.3-3.4, Eqs. 39-40): after two
+    steps both sides derive them from their nodal statistics; the derived slots agree within
+    1e-10 of each slot's RMS (they carry the statistics' summation-order rounding), the
+    slots of the Eulerian solves are the values set; a step with the derived fields then
+    gives states within 1e-10."""
+    w, g, o, c, ppe = both("channel_2k")
+    o.init_particles(ppe)
+    c.init_particles(ppe)
+    for _ in range(2):
+        o.step(w["dt"])
+        c.step(w["dt"])
+    o.derive_fields()
+    c.derive_fields()
+    fo, fg = o.fields(), c.fields()
+    derived = list(range(0, 3)) + list(range(5, 14)) + list(range(23, 30))
+    for k in range(31):
+        if k in derived:
+            sc = max(float(np.sqrt(np.mean(fo[:, k] ** 2))), 1e-300)
+            r = float(np.abs(fg[:, k] - fo[:, k]).max()) / sc
+            assert r <= 1e-10, (k, r)
+        else:
+            assert np.array_equal(fg[:, k], w["fields"][:, k]), k
+    assert np.abs(fo[:, 11:14]).max() > 0.0 and np.abs(fo[:, 5:11]).max() > 0.0
+    o.step(w["dt"])
+    c.step(w["dt"])
+    so, sg = o.get_particles(), c.get_particles()
+    diff = sg["elem"] != so["elem"]
+    assert diff.sum() <= 2
+    compare_state(sg, so, g.period_x, 1e-10, skip=diff)
+    assert c.check() == 0
