@@ -128,6 +128,7 @@ def lib():
             L.orc_node_gradient.argtypes = [C.c_void_p, dp, dp]
             L.orc_derive_fields.argtypes = [C.c_void_p]
             L.orc_get_fields.argtypes = [C.c_void_p, dp]
+            L.orc_correct_velocity.argtypes = [C.c_void_p, dp, C.c_double]
             L.orc_last_dt.argtypes = [C.c_void_p]
             L.orc_last_dt.restype = C.c_double
             L.orc_get_diag.argtypes = [C.c_void_p, C.POINTER(Diag)]
@@ -325,6 +326,12 @@ class Oracle:
         out = np.zeros((self.nn, 32))
         lib().orc_get_fields(self.h, _dp(out))
         return out
+
+    def correct_velocity(self, dp, dt: float):
+        """Eq. 31 applied to the particles with the nodal pressure change dp[nn]."""
+        d = np.ascontiguousarray(dp, dtype=np.float64)
+        if lib().orc_correct_velocity(self.h, _dp(d), float(dt)):
+            raise RuntimeError("orc_correct_velocity: no particles")
 
     def derive_fields(self):
         """Overwrite the nodal fields the particles' statistics provide (slots 0-2, 5-13,

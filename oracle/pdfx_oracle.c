@@ -1361,6 +1361,29 @@ void orc_node_gradient(const orc_ctx *c, const double *q, double *grad)
  * <omega> (slot 29) = the nodal moments.  The mean-pressure gradient, the
  * elliptic-relaxation tensor and the wall frequency (slots 3-4, 14-22, 30) come from the
  * Eulerian solves and are kept. */
+/* Sect. 3.2, Eq. 31: the mean-velocity correction <U>^{n+1} = <U>* - dt grad(<P>^{n+1} -
+ * <P>^n) / rho applied to every particle (the velocity field is the particles', rho = 1),
+ * the gradient of the nodal pressure change being constant over the particle's element
+ * (Eq. 39 with Eq. 40's derivatives).  The third velocity component has no gradient in the
+ * plane and is unchanged. */
+int orc_correct_velocity(orc_ctx *c, const double *dp, double dt)
+{
+    if (!c->x) return -1;
+    for (int p = 0; p < c->np; ++p) {
+        const int e = c->elem[p];
+        const double *vx = c->vx + 3 * e, *vy = c->vy + 3 * e;
+        const double xBA = vx[1] - vx[0], yBA = vy[1] - vy[0];
+        const double xCA = vx[2] - vx[0], yCA = vy[2] - vy[0];
+        const double inv = 1.0 / c->area2[e];
+        const int32_t *t = c->tri + 3 * e;
+        const double gx = (-yCA + yBA) * inv * dp[t[0]] + yCA * inv * dp[t[1]] - yBA * inv * dp[t[2]];
+        const double gy = (xCA - xBA) * inv * dp[t[0]] - xCA * inv * dp[t[1]] + xBA * inv * dp[t[2]];
+        c->u[p] -= dt * gx;
+        c->v[p] -= dt * gy;
+    }
+    return 0;
+}
+
 int orc_get_fields(const orc_ctx *c, double *out)
 {
     memcpy(out, c->fields, sizeof(double) * (size_t)NF * c->nn);

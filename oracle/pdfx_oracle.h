@@ -99,6 +99,9 @@ void orc_node_gradient(const orc_ctx *c, const double *q, double *grad);
 /* Nodal fields from the particles' nodal statistics (slots 0-2, 5-13, 23-29). */
 int  orc_derive_fields(orc_ctx *c);
 int  orc_get_fields(const orc_ctx *c, double *out /* [nn][32] */);
+/* Eq. 31 (rho = 1) applied to the particles: U_i -= dt d(dP)/dx_i with the element-constant
+ * gradient (Eqs. 39-40) of the nodal pressure change dP[nn] of the particle's element. */
+int  orc_correct_velocity(orc_ctx *c, const double *dp, double dt);
 double orc_last_dt(const orc_ctx *c);
 int  orc_advance(orc_ctx *c, double dt);      /* Eqs. 7, 27, 19, 24, Sect. 3.8, 3.6 */
 int  orc_redistribute(orc_ctx *c);            /* Sect. 3.7, Appendix B */
