@@ -241,6 +241,14 @@ int  pdfx_last_dt(const void *ctx, double *dt);
  * PDFX_ERR_ORDER before fields and statistics exist. */
 int  pdfx_derive_fields(void *ctx, void *stream);
 
+/* The mean-velocity correction of Eq. 31 applied to the particles (rho = 1; the velocity
+ * field is the particles'): U_i -= dt d(dP)/dx_i, with the gradient of the nodal pressure
+ * change dP = <P>^{n+1} - <P>^n (host array [nn], from the caller's solution of Eq. 33)
+ * constant over each particle's element (Eq. 39 with Eq. 40's derivatives); W is unchanged.
+ * dt > 0.  Complete on return (a scratch block of nn + 2 ne doubles is allocated and
+ * freed).  PDFX_ERR_ORDER before particles exist. */
+int  pdfx_correct_velocity(void *ctx, const double *dp, double dt, void *stream);
+
 /* The context's nodal fields [nn][32] in FP64 (host; the FP32 form's are widened). */
 int  pdfx_get_fields(void *ctx, double *out, void *stream);
 

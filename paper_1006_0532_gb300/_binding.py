@@ -97,6 +97,7 @@ def lib():
                 "pdfx_step": (C.c_int, [vp, dp, vp]),
                 "pdfx_last_dt": (C.c_int, [vp, C.POINTER(dp)]),
                 "pdfx_derive_fields": (C.c_int, [vp, vp]),
+                "pdfx_correct_velocity": (C.c_int, [vp, vp, dp, vp]),
                 "pdfx_get_fields": (C.c_int, [vp, vp, vp]),
                 "pdfx_batch_step": (C.c_int, [vp, i32, dp, vp]),
                 "pdfx_set_instances": (C.c_int, [vp, i32, C.POINTER(Params), vp]),
@@ -305,6 +306,12 @@ class Context:
     def derive_fields(self, stream=None):
         """Overwrite the fields the particles' statistics provide (pdfx_derive_fields)."""
         self._check(lib().pdfx_derive_fields(self.h, _stream(stream)), "pdfx_derive_fields")
+
+    def correct_velocity(self, dp, dt: float, stream=None):
+        """Eq. 31 applied to the particles with the nodal pressure change dp[nn]."""
+        d = np.ascontiguousarray(dp, dtype=np.float64)
+        self._check(lib().pdfx_correct_velocity(self.h, d.ctypes.data, float(dt), _stream(stream)),
+                    "pdfx_correct_velocity")
 
     def fields(self, stream=None):
         out = np.zeros((self.nn, 32))

@@ -1261,6 +1261,35 @@ int pdfx_derive_fields(void* ctx, void* stream) {
   return rc;
 }
 
+int pdfx_correct_velocity(void* ctx, const double* dp, double dt, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !dp || !(dt > 0.0) || !std::isfinite(dt)) return PDFX_ERR_ARG;
+  if (!c->have_grid || !c->pbuf[0]) return PDFX_ERR_ORDER;
+  const cudaStream_t s = as_stream(stream);
+  const size_t nn = static_cast<size_t>(c->nn), ne = static_cast<size_t>(c->ne);
+  auto* scratch = static_cast<double*>(dev_alloc(*c, sizeof(double) * (nn + 2 * ne)));
+  if (!scratch) return PDFX_ERR_ALLOC;
+  const int32_t* einst = c->K > 1 ? c->einst : nullptr;
+  int rc = cerr(cudaMemcpyAsync(scratch, dp, sizeof(double) * nn, cudaMemcpyHostToDevice, s));
+  if (rc == PDFX_OK) {
+    if (c->prm.precision == 1)
+      launch_correct_velocity<float>(static_cast<const ElemGeo<float>*>(c->geo), c->topo, c->ne,
+                                     c->prm.period_x, einst, static_cast<const InstDev<float>*>(c->inst),
+                                     scratch, scratch + nn, carve<float>(c->pbuf[c->cur], c->np), c->np,
+                                     dt, s);
+    else
+      launch_correct_velocity<double>(static_cast<const ElemGeo<double>*>(c->geo), c->topo, c->ne,
+                                      c->prm.period_x, einst,
+                                      static_cast<const InstDev<double>*>(c->inst), scratch,
+                                      scratch + nn, carve<double>(c->pbuf[c->cur], c->np), c->np, dt, s);
+    c->launches += 2;
+    rc = cerr(cudaGetLastError());
+  }
+  if (cudaStreamSynchronize(s) != cudaSuccess && rc == PDFX_OK) rc = PDFX_ERR_CUDA;
+  dev_free(*c, scratch);
+  return rc;
+}
+
 int pdfx_get_fields(void* ctx, double* out, void* stream) {
   Ctx* c = as_ctx(ctx);
   if (!c || !out) return PDFX_ERR_ARG;

@@ -916,6 +916,39 @@ void launch_derive_fields(const ElemGeo<T>* geo, const ElemTopo* topo, int32_t n
   write_fields_kernel<T><<<bn, 128, 0, s>>>(nn, nmom, ng1, ng2, fields);
 }
 
+namespace {
+
+// Eq. 31 (rho = 1) on each particle: U -= dt grad(dP) of its element (egrad[e][2]).
+template <typename T>
+__global__ void correct_velocity_kernel(Particles<T> p, int64_t np, const double* __restrict__ egrad,
+                                        double dt) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= np) return;
+  const int e = p.elem[i];
+  p.u[i] = static_cast<T>(static_cast<double>(p.u[i]) - dt * egrad[2 * static_cast<size_t>(e)]);
+  p.v[i] = static_cast<T>(static_cast<double>(p.v[i]) - dt * egrad[2 * static_cast<size_t>(e) + 1]);
+}
+
+}  // namespace
+
+template <typename T>
+void launch_correct_velocity(const ElemGeo<T>* geo, const ElemTopo* topo, int32_t ne, double period_x,
+                             const int32_t* einst, const InstDev<T>* inst, const double* dp,
+                             double* egrad, Particles<T> p, int64_t np, double dt, cudaStream_t s) {
+  if (ne <= 0) return;
+  elem_gradient_kernel<T><<<static_cast<unsigned>((ne + 127) / 128), 128, 0, s>>>(
+      geo, topo, ne, period_x, einst, inst, dp, 1, 0, 1, egrad);
+  if (np > 0)
+    correct_velocity_kernel<T><<<static_cast<unsigned>((np + 255) / 256), 256, 0, s>>>(p, np, egrad, dt);
+}
+
+template void launch_correct_velocity<float>(const ElemGeo<float>*, const ElemTopo*, int32_t, double,
+                                             const int32_t*, const InstDev<float>*, const double*,
+                                             double*, Particles<float>, int64_t, double, cudaStream_t);
+template void launch_correct_velocity<double>(const ElemGeo<double>*, const ElemTopo*, int32_t, double,
+                                              const int32_t*, const InstDev<double>*, const double*,
+                                              double*, Particles<double>, int64_t, double, cudaStream_t);
+
 template void launch_derive_fields<float>(const ElemGeo<float>*, const ElemTopo*, int32_t, double,
                                           const int32_t*, const InstDev<float>*, const int32_t*,
                                           const int32_t*, int32_t, const double*, double*, float*,

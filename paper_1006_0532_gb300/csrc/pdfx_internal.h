@@ -262,6 +262,12 @@ void launch_node_average(const double* emom, const int32_t* ne_off, const int32_
                          int32_t nn, double* nmom, cudaStream_t s);
 // Eq. 26: max over nodes of ||(<U>, <V>, <W>, <omega>, <psi>)||_2 into out[0] (one block).
 void launch_cfl_norm(const double* nmom, int32_t nn, double* out, cudaStream_t s);
+// Eq. 31 (rho = 1): U -= dt grad(dP) with the element-constant gradient of the nodal dP[nn];
+// egrad is scratch of 2 ne doubles.
+template <typename T>
+void launch_correct_velocity(const ElemGeo<T>* geo, const ElemTopo* topo, int32_t ne, double period_x,
+                             const int32_t* einst, const InstDev<T>* inst, const double* dp,
+                             double* egrad, Particles<T> p, int64_t np, double dt, cudaStream_t s);
 // Sect. 3.4: the nodal fields the statistics provide (slots 0-2, 5-13, 23-29) from nmom;
 // scratch holds 18 (ne + nn) doubles.
 template <typename T>

@@ -539,3 +539,22 @@ def test_derived_fields_match_oracle_f64():
     assert diff.sum() <= 2
     compare_state(sg, so, g.period_x, 1e-10, skip=diff)
     assert c.check() == 0
+
+
+def test_velocity_correction_matches_oracle_f64():
+    """Eq. 31 applied to the particles with a random nodal pressure change (the periodic
+    seam's elements included), then a step: states within 1e-12 of the oracle's."""
+    w, g, o, c, ppe = both("channel_2k", ppe=40)
+    o.init_particles(ppe)
+    c.init_particles(ppe)
+    dp = np.random.default_rng(17).normal(0.0, 1.0, g.nn)
+    o.correct_velocity(dp, w["dt"])
+    c.correct_velocity(dp, w["dt"])
+    compare_state(c.get_particles(), o.get_particles(), g.period_x, 1e-12)
+    o.step(w["dt"])
+    c.step(w["dt"])
+    so, sg = o.get_particles(), c.get_particles()
+    diff = sg["elem"] != so["elem"]
+    assert diff.sum() <= 2
+    compare_state(sg, so, g.period_x, 1e-12, skip=diff)
+    assert c.check() == 0
