@@ -46,3 +46,22 @@ def test_host_only_calls(lib):
     lib.pdfx_strerror.restype = ctypes.c_char_p
     assert lib.pdfx_strerror(0) == b"ok"
     assert b"element" in lib.pdfx_strerror(-6)
+
+
+def test_host_only_argument_checks(lib):
+    """Entry points refuse a null context or bad arguments before touching the device, and
+    the defaults of the newer parameters are those documented (model 0, alpha 0.5 for Eq.
+    47, CFL 0.7 for Eq. 26)."""
+    from paper_1006_0532_gb300 import _binding as B
+    p = B.make_params({})
+    assert p.model == 0 and abs(p.alpha - 0.5) < 1e-15 and abs(p.cfl - 0.7) < 1e-15
+    assert p.cond_mode == 0 and p.fox_bins == 5 and p.acc64 == 0
+    ERR_ARG = -1
+    L = B.lib()
+    d = ctypes.c_double()
+    assert L.pdfx_last_dt(None, ctypes.byref(d)) == ERR_ARG
+    assert L.pdfx_batch_step(None, 0, 1e-3, None) == ERR_ARG
+    assert L.pdfx_derive_fields(None, None) == ERR_ARG
+    assert L.pdfx_get_fields(None, None, None) == ERR_ARG
+    assert L.pdfx_correct_velocity(None, None, 1e-3, None) == ERR_ARG
+    assert L.pdfx_scalar_stats(None, 1, None, 10, None, None, None, None, None, 0, None) == ERR_ARG
