@@ -22,6 +22,14 @@
  *   Eqs. 53-58         wall crossing probability, reflection, no-slip, wall frequency
  *   Sect. 3.9          six Gaussians per particle per step, plus one uniform for Eq. 55
  *   Sect. 4.1.2        source disc with psi = 1
+ *   Sect. 4.2          free-slip reflection (also beyond the start element, in the walk)
+ *   Eq. 26             CFL time step for steps with dt <= 0
+ *   Eq. 31             mean-velocity correction applied to the particles
+ *   Eqs. 39-40         element gradients and their node transfer (Sect. 3.4)
+ *   Eqs. 46-47         simplified model of the particle-redistribution test (Sect. 3.7)
+ *   Eqs. 64-66         Fox's projection conditioning
+ *   Eqs. 67-69         scalar statistics of probe elements (PDF, conditional diffusion and
+ *                      dissipation, moments)
  *
  * Readings where the paper is silent, ambiguous or garbled are marked "Reading:".
  */
