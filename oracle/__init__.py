@@ -131,6 +131,9 @@ def lib():
             L.orc_correct_velocity.argtypes = [C.c_void_p, dp, C.c_double]
             L.orc_last_dt.argtypes = [C.c_void_p]
             L.orc_last_dt.restype = C.c_double
+            L.orc_wp_rhs.argtypes = [C.c_void_p, dp, dp]
+            L.orc_wp_solve.argtypes = [C.c_void_p, dp, dp, dp, C.c_double, C.c_int, ip]
+            L.orc_update_wp.argtypes = [C.c_void_p, C.c_double, C.c_int, ip]
             L.orc_get_diag.argtypes = [C.c_void_p, C.POINTER(Diag)]
             L.orc_reset_diag.argtypes = [C.c_void_p]
             L.orc_redistribution_counts.argtypes = [ip, C.c_int, C.c_int, ip]
@@ -337,6 +340,36 @@ class Oracle:
         """Overwrite the nodal fields the particles' statistics provide (slots 0-2, 5-13,
         23-29) from the current nodal statistics."""
         lib().orc_derive_fields(self.h)
+
+    def wp_rhs(self):
+        """Eqs. 12-18 at every node from the current fields: (rhs[nn][3][3], L[nn])."""
+        rhs = np.zeros((self.nn, 9))
+        L = np.zeros(self.nn)
+        if lib().orc_wp_rhs(self.h, _dp(rhs), _dp(L)):
+            raise RuntimeError("orc_wp_rhs: a node has eps <= 0")
+        return rhs.reshape(self.nn, 3, 3), L
+
+    def wp_solve(self, rhs, L, wp0=None, tol: float = 1e-13, max_iter: int = 100000):
+        """Eq. 12 by Galerkin FEM and Jacobi-PCG (Eq. 59 and the symmetry conditions at the
+        boundaries): returns (wp[nn][3][3], iterations)."""
+        r = np.ascontiguousarray(np.asarray(rhs, dtype=np.float64).reshape(self.nn, 9))
+        LL = np.ascontiguousarray(L, dtype=np.float64)
+        wp = (np.zeros((self.nn, 9)) if wp0 is None
+              else np.array(np.asarray(wp0, dtype=np.float64).reshape(self.nn, 9)))
+        it = C.c_int()
+        rc = lib().orc_wp_solve(self.h, _dp(r), _dp(LL), _dp(wp), float(tol), int(max_iter),
+                                C.byref(it))
+        if rc:
+            raise RuntimeError("orc_wp_solve failed: %d" % rc)
+        return wp.reshape(self.nn, 3, 3), it.value
+
+    def update_wp(self, tol: float = 1e-13, max_iter: int = 100000) -> int:
+        """Eq. 12's update of the fields' wp_ij (slots 14-22); returns the iterations."""
+        it = C.c_int()
+        rc = lib().orc_update_wp(self.h, float(tol), int(max_iter), C.byref(it))
+        if rc:
+            raise RuntimeError("orc_update_wp failed: %d" % rc)
+        return it.value
 
     def advance(self, dt):
         return lib().orc_advance(self.h, float(dt))

@@ -30,6 +30,9 @@
  *   Eqs. 64-66         Fox's projection conditioning
  *   Eqs. 67-69         scalar statistics of probe elements (PDF, conditional diffusion and
  *                      dissipation, moments)
+ *   Eqs. 12-18         local right-hand side and length scale of the elliptic relaxation
+ *   Sect. 3.2, Eq. 59  Galerkin FEM and Jacobi-PCG solve of Eq. 12, its wall condition and
+ *                      the symmetry conditions of Sect. 4.1 at free-slip boundaries
  *
  * Readings where the paper is silent, ambiguous or garbled are marked "Reading:".
  */
@@ -1430,6 +1433,295 @@ int orc_derive_fields(orc_ctx *c)
     }
     free(q); free(g1); free(g2); free(first); free(lap);
     return 0;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Elliptic relaxation (Sect. 2, Eqs. 12-18; Sect. 3.2; Eq. 59).                          */
+/* ------------------------------------------------------------------------------------ */
+
+/* Boundary class of every node: 1 where a no-slip edge (tag 1) ends, else 2 where a
+ * free-slip edge (tag 2) ends, else 0.  For class-1 nodes (onx, ony) is the unit outward
+ * normal: the normalised sum of the outward unit normals of the node's no-slip edges (one
+ * edge's normal on a straight wall; the bisector at a corner). */
+static void node_boundary(const orc_ctx *c, int8_t *cls, double *onx, double *ony)
+{
+    for (int n = 0; n < c->nn; ++n) { cls[n] = 0; onx[n] = 0.0; ony[n] = 0.0; }
+    for (int e = 0; e < c->ne; ++e) {
+        for (int k = 0; k < 3; ++k) {
+            const int t = c->tag[3 * e + k];
+            if (t != 1 && t != 2) continue;
+            double px, py, mx, my;
+            edge_line(c, e, k, &px, &py, &mx, &my);   /* (mx, my) points into the domain */
+            const int ends[2] = {c->tri[3 * e + (k + 1) % 3], c->tri[3 * e + (k + 2) % 3]};
+            for (int s = 0; s < 2; ++s) {
+                const int n = ends[s];
+                if (t == 1) {
+                    cls[n] = 1;
+                    onx[n] -= mx;
+                    ony[n] -= my;
+                } else if (cls[n] == 0) {
+                    cls[n] = 2;
+                }
+            }
+        }
+    }
+    for (int n = 0; n < c->nn; ++n) {
+        if (cls[n] != 1) continue;
+        const double len = sqrt(onx[n] * onx[n] + ony[n] * ony[n]);
+        if (len > 0.0) { onx[n] /= len; ony[n] /= len; }
+    }
+}
+
+/* Eq. 17's n_i: the unit outward normal of the no-slip edge nearest to the point (x, y)
+ * (point-to-segment distance, minimum image in x; the first edge in element and local edge
+ * order wins a tie).  Returns 0 and n = 0 when the grid has no no-slip edge. */
+static int nearest_wall_normal(const orc_ctx *c, double x, double y, double *nx, double *ny)
+{
+    double best = INFINITY;
+    *nx = 0.0; *ny = 0.0;
+    for (int e = 0; e < c->ne; ++e) {
+        for (int k = 0; k < 3; ++k) {
+            if (c->tag[3 * e + k] != 1) continue;
+            const double *vx = c->vx + 3 * e, *vy = c->vy + 3 * e;
+            const int a = (k + 1) % 3, b = (k + 2) % 3;
+            /* segment in the frame of the point */
+            const double ax = x + min_image(vx[a] - x, c->p.period_x), ay = vy[a];
+            const double bx = ax + (vx[b] - vx[a]), by = vy[b];
+            const double tx = bx - ax, ty = by - ay;
+            double s = ((x - ax) * tx + (y - ay) * ty) / (tx * tx + ty * ty);
+            s = s < 0.0 ? 0.0 : (s > 1.0 ? 1.0 : s);
+            const double dx = x - (ax + s * tx), dy = y - (ay + s * ty);
+            const double d = sqrt(dx * dx + dy * dy);
+            if (d < best) {
+                double px, py, mx, my;
+                edge_line(c, e, k, &px, &py, &mx, &my);
+                best = d;
+                *nx = -mx;
+                *ny = -my;
+            }
+        }
+    }
+    return isfinite(best);
+}
+
+/* Eqs. 12-18 at every node, from the context's nodal fields: the local right-hand side of
+ * Eq. 12,
+ *     rhs_ij = (1 - C1)/2 k <omega> delta_ij + k H_ijkl d<U_k>/dx_l,
+ * with H_ijkl of Eq. 13, A_v of Eq. 14 and b_ij of Eq. 15, and the length scale L of
+ * Eq. 16 with C_xi of Eq. 17 and eps of Eq. 18.  Inputs: d<U_k>/dx_l (slots 5-10, k-major,
+ * l = x, y; d/dz = 0 in the plane), <u_i u_j> (slots 23-28), <omega> (slot 29); nu and the
+ * constants of Table 4 from the parameters.  Readings: b_ij = 0 where <u_k u_k> = 0 and
+ * A_v = 0 where k = 0 (every term of the right-hand side carries the factor k there, so
+ * neither choice shows); A_v is min[1, .] as printed, with no lower bound; C_xi takes the
+ * printed n_i n_i of a unit normal, which is 1 wherever a no-slip wall exists (C_xi = 2.3)
+ * and 0 on a grid without one (C_xi = 1).  A node with eps <= 0 has no length scale:
+ * the call fails.  rhs[nn][9] is row-major (i, j); L[nn]. */
+int orc_wp_rhs(const orc_ctx *c, double *rhs, double *L)
+{
+    const orc_params *p = &c->p;
+    for (int n = 0; n < c->nn; ++n) {
+        const double *f = c->fields + (size_t)NF * n;
+        const double R[3][3] = {{f[23], f[26], f[27]}, {f[26], f[24], f[28]}, {f[27], f[28], f[25]}};
+        const double G[3][3] = {{f[5], f[6], 0.0}, {f[7], f[8], 0.0}, {f[9], f[10], 0.0}};
+        const double om = f[29];
+        const double ukuk = R[0][0] + R[1][1] + R[2][2];
+        const double k = 0.5 * ukuk;
+        double b[3][3];
+        for (int i = 0; i < 3; ++i)
+            for (int j = 0; j < 3; ++j)
+                b[i][j] = ukuk > 0.0 ? R[i][j] / ukuk - (i == j ? 1.0 / 3.0 : 0.0) : 0.0;   /* Eq. 15 */
+        const double det = R[0][0] * (R[1][1] * R[2][2] - R[1][2] * R[2][1])
+                         - R[0][1] * (R[1][0] * R[2][2] - R[1][2] * R[2][0])
+                         + R[0][2] * (R[1][0] * R[2][1] - R[1][1] * R[2][0]);
+        const double k23 = 2.0 * k / 3.0;
+        const double Av = k > 0.0 ? fmin(1.0, p->Cv * det / (k23 * k23 * k23)) : 0.0;   /* Eq. 14 */
+        for (int i = 0; i < 3; ++i) {
+            for (int j = 0; j < 3; ++j) {
+                double s = 0.0;
+                for (int kk = 0; kk < 3; ++kk) {
+                    for (int l = 0; l < 3; ++l) {
+                        const double d_ik = i == kk, d_jl = j == l, d_il = i == l, d_jk = j == kk;
+                        const double H = (p->C2 * Av + p->gamma5 / 3.0) * d_ik * d_jl       /* Eq. 13 */
+                                       - (p->gamma5 / 3.0) * d_il * d_jk
+                                       + p->gamma5 * b[i][kk] * d_jl
+                                       - p->gamma5 * b[i][l] * d_jk;
+                        s += H * G[kk][l];
+                    }
+                }
+                rhs[(size_t)9 * n + 3 * i + j] =
+                    (i == j ? 0.5 * (1.0 - p->C1) * k * om : 0.0) + k * s;            /* Eq. 12 */
+            }
+        }
+        const double eps = om * (k + p->nu * p->CT * p->CT * om);                    /* Eq. 18 */
+        if (!(eps > 0.0)) return -1;
+        double nx, ny;
+        nearest_wall_normal(c, c->node_xy[2 * n], c->node_xy[2 * n + 1], &nx, &ny);
+        const double Cxi = 1.0 + 1.3 * (nx * nx + ny * ny);                           /* Eq. 17 */
+        L[n] = p->CL * fmax(Cxi * pow(k, 1.5) / eps,
+                            p->Ceta * pow(p->nu * p->nu * p->nu / eps, 0.25));         /* Eq. 16 */
+    }
+    return 0;
+}
+
+/* y = (M + K) x for one component: the Galerkin matrices of Eq. 12's operator with linear
+ * triangles (Sect. 3.2), the consistent mass matrix M_e = A_e/12 (1 + delta_ab) and the
+ * stiffness K_e = L_e^2 A_e grad N_a . grad N_b with Eq. 40's derivatives; L_e^2 is the mean
+ * of the element's three nodal L^2.  Reading: the paper solves Eq. 12 by conjugate
+ * gradients, whose matrix must be symmetric, so the operator is div(L_e^2 grad) with L^2
+ * constant over each element (the L^2 grad(N_a) . grad(wp) weak form without the
+ * non-symmetric N_a grad(L^2) . grad(wp) term).  Elements use their vertices in the
+ * element's frame, so a periodic seam needs nothing else. */
+static void wp_operator(const orc_ctx *c, const double *L, const double *x, double *y, double *diag)
+{
+    for (int n = 0; n < c->nn; ++n) y[n] = 0.0;
+    if (diag) for (int n = 0; n < c->nn; ++n) diag[n] = 0.0;
+    for (int e = 0; e < c->ne; ++e) {
+        const double *vx = c->vx + 3 * e, *vy = c->vy + 3 * e;
+        const double xBA = vx[1] - vx[0], yBA = vy[1] - vy[0];
+        const double xCA = vx[2] - vx[0], yCA = vy[2] - vy[0];
+        const double A = 0.5 * c->area2[e];
+        const double inv = 1.0 / c->area2[e];
+        const double dNx[3] = {(-yCA + yBA) * inv, yCA * inv, -yBA * inv};   /* Eq. 40 */
+        const double dNy[3] = {(xCA - xBA) * inv, -xCA * inv, xBA * inv};
+        const int32_t *t = c->tri + 3 * e;
+        const double L2 = (L[t[0]] * L[t[0]] + L[t[1]] * L[t[1]] + L[t[2]] * L[t[2]]) / 3.0;
+        for (int a = 0; a < 3; ++a) {
+            for (int b = 0; b < 3; ++b) {
+                const double m = A / 12.0 * (a == b ? 2.0 : 1.0);
+                const double kab = L2 * A * (dNx[a] * dNx[b] + dNy[a] * dNy[b]);
+                y[t[a]] += (m + kab) * x[t[b]];
+                if (diag && a == b) diag[t[a]] += m + kab;
+            }
+        }
+    }
+}
+
+/* y = M x with the consistent mass matrix (the Galerkin load of a linearly interpolated
+ * right-hand side). */
+static void mass_apply(const orc_ctx *c, const double *x, double *y)
+{
+    for (int n = 0; n < c->nn; ++n) y[n] = 0.0;
+    for (int e = 0; e < c->ne; ++e) {
+        const double A = 0.5 * c->area2[e];
+        const int32_t *t = c->tri + 3 * e;
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) y[t[a]] += A / 12.0 * (a == b ? 2.0 : 1.0) * x[t[b]];
+    }
+}
+
+static double dot_free(const double *a, const double *b, const int8_t *fixed, int n)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; ++i)
+        if (!fixed[i]) s += a[i] * b[i];
+    return s;
+}
+
+/* Eq. 12 solved for the nine components of wp_ij (Sect. 3.2: Galerkin FEM with linear
+ * triangles, conjugate gradients with a Jacobi preconditioner started from the previous
+ * solution).  Boundary conditions: at no-slip nodes wp_ij = -4.5 eps n_i n_j (Eq. 59; eps of
+ * Eq. 18 from the node's fields, n the node's outward unit normal, n_z = 0); at free-slip
+ * nodes the symmetry conditions of Sect. 4.1, homogeneous Dirichlet for i != j and the
+ * natural (zero normal derivative) condition for i == j; a node on both kinds takes the
+ * no-slip condition.  rhs[nn][9], L[nn]; wp[nn][9] holds the initial guess on entry and the
+ * solution on exit.  Each component iterates until the preconditioned residual's
+ * 2-norm over the free nodes is at most tol times that of its reduced load (the load minus
+ * the Dirichlet columns); *iters returns the largest count.  Fails (-2) if a component
+ * needs more than max_iter iterations, (-1) if an eps needed at a wall is not positive. */
+int orc_wp_solve(const orc_ctx *c, const double *rhs, const double *L, double *wp, double tol,
+                 int max_iter, int *iters)
+{
+    const int nn = c->nn;
+    int8_t *cls = (int8_t *)malloc((size_t)nn);
+    int8_t *fixed = (int8_t *)malloc((size_t)nn);
+    double *onx = (double *)malloc(sizeof(double) * nn), *ony = (double *)malloc(sizeof(double) * nn);
+    double *f = (double *)malloc(sizeof(double) * nn), *bl = (double *)malloc(sizeof(double) * nn);
+    double *x = (double *)malloc(sizeof(double) * nn), *r = (double *)malloc(sizeof(double) * nn);
+    double *z = (double *)malloc(sizeof(double) * nn), *d = (double *)malloc(sizeof(double) * nn);
+    double *q = (double *)malloc(sizeof(double) * nn), *dg = (double *)malloc(sizeof(double) * nn);
+    double *x0 = (double *)malloc(sizeof(double) * nn);
+    int rc = 0, worst = 0;
+    node_boundary(c, cls, onx, ony);
+    for (int comp = 0; comp < 9 && rc == 0; ++comp) {
+        const int i = comp / 3, j = comp % 3;
+        for (int n = 0; n < nn; ++n) {
+            f[n] = rhs[(size_t)9 * n + comp];
+            x[n] = wp[(size_t)9 * n + comp];
+            fixed[n] = 0;
+            if (cls[n] == 1) {
+                const double *fl = c->fields + (size_t)NF * n;
+                const double k = 0.5 * (fl[23] + fl[24] + fl[25]), om = fl[29];
+                const double eps = om * (k + c->p.nu * c->p.CT * c->p.CT * om);
+                if (!(eps > 0.0)) { rc = -1; break; }
+                const double nv[3] = {onx[n], ony[n], 0.0};
+                x[n] = -4.5 * eps * nv[i] * nv[j];                                      /* Eq. 59 */
+                fixed[n] = 1;
+            } else if (cls[n] == 2 && i != j) {
+                x[n] = 0.0;
+                fixed[n] = 1;
+            }
+        }
+        if (rc) break;
+        mass_apply(c, f, bl);
+        /* reduced load: bl - A (Dirichlet values, zero elsewhere), on the free nodes */
+        for (int n = 0; n < nn; ++n) x0[n] = fixed[n] ? x[n] : 0.0;
+        wp_operator(c, L, x0, q, dg);
+        for (int n = 0; n < nn; ++n) q[n] = bl[n] - q[n];
+        for (int n = 0; n < nn; ++n) z[n] = fixed[n] ? 0.0 : q[n] / dg[n];
+        const double bnorm = sqrt(dot_free(z, z, fixed, nn));
+        /* r = bl - A x on the free nodes */
+        wp_operator(c, L, x, q, NULL);
+        for (int n = 0; n < nn; ++n) r[n] = fixed[n] ? 0.0 : bl[n] - q[n];
+        for (int n = 0; n < nn; ++n) z[n] = fixed[n] ? 0.0 : r[n] / dg[n];
+        for (int n = 0; n < nn; ++n) d[n] = z[n];
+        double rz = dot_free(r, z, fixed, nn);
+        int it = 0;
+        while (sqrt(dot_free(z, z, fixed, nn)) > tol * bnorm) {
+            if (it == max_iter) { rc = -2; break; }
+            wp_operator(c, L, d, q, NULL);
+            for (int n = 0; n < nn; ++n) if (fixed[n]) q[n] = 0.0;
+            const double alpha = rz / dot_free(d, q, fixed, nn);
+            for (int n = 0; n < nn; ++n) {
+                if (fixed[n]) continue;
+                x[n] += alpha * d[n];
+                r[n] -= alpha * q[n];
+                z[n] = r[n] / dg[n];
+            }
+            const double rz1 = dot_free(r, z, fixed, nn);
+            const double beta = rz1 / rz;
+            rz = rz1;
+            for (int n = 0; n < nn; ++n) d[n] = fixed[n] ? 0.0 : z[n] + beta * d[n];
+            ++it;
+        }
+        if (it > worst) worst = it;
+        for (int n = 0; n < nn; ++n) wp[(size_t)9 * n + comp] = x[n];
+    }
+    if (iters) *iters = worst;
+    free(cls); free(fixed); free(onx); free(ony); free(f); free(bl); free(x); free(r);
+    free(z); free(d); free(q); free(dg); free(x0);
+    return rc;
+}
+
+/* The elliptic-relaxation update of the coupled loop: Eq. 12's right-hand side and length
+ * scale from the current nodal fields, solved from the fields' wp_ij (slots 14-22) as the
+ * initial guess, the solution written back to slots 14-22. */
+int orc_update_wp(orc_ctx *c, double tol, int max_iter, int *iters)
+{
+    const int nn = c->nn;
+    double *rhs = (double *)malloc(sizeof(double) * 9 * (size_t)nn);
+    double *L = (double *)malloc(sizeof(double) * (size_t)nn);
+    double *wp = (double *)malloc(sizeof(double) * 9 * (size_t)nn);
+    int rc = orc_wp_rhs(c, rhs, L);
+    if (rc == 0) {
+        for (int n = 0; n < nn; ++n)
+            for (int m = 0; m < 9; ++m) wp[(size_t)9 * n + m] = c->fields[(size_t)NF * n + 14 + m];
+        rc = orc_wp_solve(c, rhs, L, wp, tol, max_iter, iters);
+        if (rc == 0)
+            for (int n = 0; n < nn; ++n)
+                for (int m = 0; m < 9; ++m) c->fields[(size_t)NF * n + 14 + m] = wp[(size_t)9 * n + m];
+    }
+    free(rhs); free(L); free(wp);
+    return rc;
 }
 
 /* One timestep (Table 1 order restricted to the particle path): advance and track,

@@ -103,6 +103,15 @@ int  orc_get_fields(const orc_ctx *c, double *out /* [nn][32] */);
  * gradient (Eqs. 39-40) of the nodal pressure change dP[nn] of the particle's element. */
 int  orc_correct_velocity(orc_ctx *c, const double *dp, double dt);
 double orc_last_dt(const orc_ctx *c);
+/* Eqs. 12-18: the local right-hand side of Eq. 12 (rhs[nn][9], row-major i, j) and its
+ * length scale L[nn] at every node from the nodal fields. */
+int  orc_wp_rhs(const orc_ctx *c, double *rhs, double *L);
+/* Eq. 12 solved by Galerkin FEM and Jacobi-PCG with the conditions of Eq. 59 and Sect. 4.1;
+ * wp[nn][9]: initial guess in, solution out. */
+int  orc_wp_solve(const orc_ctx *c, const double *rhs, const double *L, double *wp, double tol,
+                  int max_iter, int *iters);
+/* orc_wp_rhs, then orc_wp_solve from the fields' wp_ij (slots 14-22), written back there. */
+int  orc_update_wp(orc_ctx *c, double tol, int max_iter, int *iters);
 int  orc_advance(orc_ctx *c, double dt);      /* Eqs. 7, 27, 19, 24, Sect. 3.8, 3.6 */
 int  orc_redistribute(orc_ctx *c);            /* Sect. 3.7, Appendix B */
 int  orc_statistics(orc_ctx *c);              /* Sect. 3.3 and 3.5, Appendix A */
