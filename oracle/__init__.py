@@ -134,6 +134,10 @@ def lib():
             L.orc_wp_rhs.argtypes = [C.c_void_p, dp, dp]
             L.orc_wp_solve.argtypes = [C.c_void_p, dp, dp, dp, C.c_double, C.c_int, ip]
             L.orc_update_wp.argtypes = [C.c_void_p, C.c_double, C.c_int, ip]
+            L.orc_pressure_rhs.argtypes = [C.c_void_p, dp, dp, C.c_double, C.c_double, dp, dp]
+            L.orc_pressure_solve.argtypes = [C.c_void_p, dp, dp, dp, C.c_double, C.c_int, ip]
+            L.orc_coupled_step.argtypes = [C.c_void_p, C.c_double, C.c_double, dp, dp, C.c_double,
+                                           C.c_int, ip, ip]
             L.orc_get_diag.argtypes = [C.c_void_p, C.POINTER(Diag)]
             L.orc_reset_diag.argtypes = [C.c_void_p]
             L.orc_redistribution_counts.argtypes = [ip, C.c_int, C.c_int, ip]
@@ -370,6 +374,40 @@ class Oracle:
         if rc:
             raise RuntimeError("orc_update_wp failed: %d" % rc)
         return it.value
+
+    def pressure_rhs(self, ustar, P, dt: float, Cp: float = 1e-3):
+        """Eq. 33's nodal right-hand side and Eq. 61's increment flux: (src[nn], flux[nn])."""
+        u = np.ascontiguousarray(np.asarray(ustar, dtype=np.float64).reshape(self.nn, 3))
+        p = np.ascontiguousarray(P, dtype=np.float64)
+        src, flux = np.zeros(self.nn), np.zeros(self.nn)
+        if lib().orc_pressure_rhs(self.h, _dp(u), _dp(p), float(dt), float(Cp), _dp(src), _dp(flux)):
+            raise RuntimeError("orc_pressure_rhs: dt must be positive")
+        return src, flux
+
+    def pressure_solve(self, src, flux, dP0=None, tol: float = 1e-13, max_iter: int = 100000):
+        """Eq. 33 by Galerkin FEM and Jacobi-PCG: (zero-mean dP[nn], iterations)."""
+        s = np.ascontiguousarray(src, dtype=np.float64)
+        f = np.ascontiguousarray(flux, dtype=np.float64)
+        d = np.zeros(self.nn) if dP0 is None else np.array(dP0, dtype=np.float64)
+        it = C.c_int()
+        rc = lib().orc_pressure_solve(self.h, _dp(s), _dp(f), _dp(d), float(tol), int(max_iter),
+                                      C.byref(it))
+        if rc:
+            raise RuntimeError("orc_pressure_solve failed: %d" % rc)
+        return d, it.value
+
+    def coupled_step(self, dt, P, dP=None, Cp: float = 1e-3, tol: float = 1e-13,
+                     max_iter: int = 100000):
+        """One step of the coupled loop (Table 1 order).  P[nn] is updated in place; returns
+        (dP, wp iterations, pressure iterations)."""
+        assert P.dtype == np.float64 and P.flags.c_contiguous and P.size == self.nn
+        d = np.zeros(self.nn) if dP is None else np.array(dP, dtype=np.float64)
+        wi, pi = C.c_int(), C.c_int()
+        rc = lib().orc_coupled_step(self.h, float(dt), float(Cp), _dp(P), _dp(d), float(tol),
+                                    int(max_iter), C.byref(wi), C.byref(pi))
+        if rc:
+            raise RuntimeError("orc_coupled_step failed: %d" % rc)
+        return d, wi.value, pi.value
 
     def advance(self, dt):
         return lib().orc_advance(self.h, float(dt))

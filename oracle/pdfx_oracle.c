@@ -33,6 +33,9 @@
  *   Eqs. 12-18         local right-hand side and length scale of the elliptic relaxation
  *   Sect. 3.2, Eq. 59  Galerkin FEM and Jacobi-PCG solve of Eq. 12, its wall condition and
  *                      the symmetry conditions of Sect. 4.1 at free-slip boundaries
+ *   Eqs. 30-33, 61     pressure projection by Galerkin FEM with the Neumann condition of Eq. 61
+ *   Table 1            order of the coupled step (time step, elliptic relaxation, advance,
+ *                      pressure projection, mean-velocity correction, statistics)
  *
  * Readings where the paper is silent, ambiguous or garbled are marked "Reading:".
  */
@@ -1721,6 +1724,210 @@ int orc_update_wp(orc_ctx *c, double tol, int max_iter, int *iters)
                 for (int m = 0; m < 9; ++m) c->fields[(size_t)NF * n + 14 + m] = wp[(size_t)9 * n + m];
     }
     free(rhs); free(L); free(wp);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------------------ */
+/* Pressure projection (Sect. 3.2, Eqs. 28-33; Eqs. 60-61) and the coupled step.          */
+/* ------------------------------------------------------------------------------------ */
+
+/* The nodal right-hand side of Eq. 33 with rho = 1,
+ *     src = (div <U>* - C_p lap <P>^n) / dt,
+ * with div <U>* from the node-transferred gradients of the nodal means ustar[nn][3] and
+ * lap <P>^n by the two passes of Sect. 3.4 applied to P[nn]; and the normal derivative of
+ * the pressure increment at no-slip nodes (zero elsewhere), flux[nn].  Reading: Eq. 61
+ * fixes the outward normal derivative of <P>^{n+1}; with the current nodal fields (the
+ * laplacian of <U_i>, slots 11-12, and the node-transferred gradients of <u_i u_j>, slots
+ * 23, 24 and 26) it is nu lap<U_i> n_i - d<u_i u_j>/dx_j n_i, and the increment's is that
+ * value minus n . grad <P>^n (the node-transferred gradient of P); n is the node's outward
+ * unit normal (the bisector at a corner).  Free-slip rows are symmetry lines, where the
+ * normal derivative is zero. */
+int orc_pressure_rhs(const orc_ctx *c, const double *ustar, const double *P, double dt, double Cp,
+                     double *src, double *flux)
+{
+    const int nn = c->nn;
+    if (!(dt > 0.0)) return -1;
+    double *q = (double *)calloc((size_t)nn, sizeof(double));
+    double *gu = (double *)malloc(sizeof(double) * 2 * nn), *gv = (double *)malloc(sizeof(double) * 2 * nn);
+    double *gp = (double *)malloc(sizeof(double) * 2 * nn), *g2 = (double *)malloc(sizeof(double) * 2 * nn);
+    double *lapP = (double *)calloc((size_t)nn, sizeof(double));
+    double *guu = (double *)malloc(sizeof(double) * 2 * nn), *gvv = (double *)malloc(sizeof(double) * 2 * nn);
+    double *guv = (double *)malloc(sizeof(double) * 2 * nn);
+    double *onx = (double *)malloc(sizeof(double) * nn), *ony = (double *)malloc(sizeof(double) * nn);
+    int8_t *cls = (int8_t *)malloc((size_t)nn);
+    for (int n = 0; n < nn; ++n) q[n] = ustar[3 * n];
+    orc_node_gradient(c, q, gu);
+    for (int n = 0; n < nn; ++n) q[n] = ustar[3 * n + 1];
+    orc_node_gradient(c, q, gv);
+    orc_node_gradient(c, P, gp);
+    for (int j = 0; j < 2; ++j) {
+        for (int n = 0; n < nn; ++n) q[n] = gp[2 * n + j];
+        orc_node_gradient(c, q, g2);
+        for (int n = 0; n < nn; ++n) lapP[n] += g2[2 * n + j];
+    }
+    for (int n = 0; n < nn; ++n) src[n] = (gu[2 * n] + gv[2 * n + 1] - Cp * lapP[n]) / dt;   /* Eq. 33 */
+    const int slots[3] = {23, 24, 26};                 /* <uu>, <vv>, <uv> */
+    double *gs[3] = {guu, gvv, guv};
+    for (int s = 0; s < 3; ++s) {
+        for (int n = 0; n < nn; ++n) q[n] = c->fields[(size_t)NF * n + slots[s]];
+        orc_node_gradient(c, q, gs[s]);
+    }
+    node_boundary(c, cls, onx, ony);
+    for (int n = 0; n < nn; ++n) {
+        flux[n] = 0.0;
+        if (cls[n] != 1) continue;
+        const double *f = c->fields + (size_t)NF * n;
+        const double divx = guu[2 * n] + guv[2 * n + 1];   /* d<u u_j>/dx_j */
+        const double divy = guv[2 * n] + gvv[2 * n + 1];   /* d<v u_j>/dx_j */
+        const double eq61 = c->p.nu * (f[11] * onx[n] + f[12] * ony[n]) - (divx * onx[n] + divy * ony[n]);
+        flux[n] = eq61 - (gp[2 * n] * onx[n] + gp[2 * n + 1] * ony[n]);
+    }
+    free(q); free(gu); free(gv); free(gp); free(g2); free(lapP); free(guu); free(gvv); free(guv);
+    free(onx); free(ony); free(cls);
+    return 0;
+}
+
+/* y = K x, the Galerkin stiffness of the laplacian with linear triangles (Eq. 40). */
+static void stiffness_apply(const orc_ctx *c, const double *x, double *y, double *diag)
+{
+    for (int n = 0; n < c->nn; ++n) y[n] = 0.0;
+    if (diag) for (int n = 0; n < c->nn; ++n) diag[n] = 0.0;
+    for (int e = 0; e < c->ne; ++e) {
+        const double *vx = c->vx + 3 * e, *vy = c->vy + 3 * e;
+        const double xBA = vx[1] - vx[0], yBA = vy[1] - vy[0];
+        const double xCA = vx[2] - vx[0], yCA = vy[2] - vy[0];
+        const double A = 0.5 * c->area2[e];
+        const double inv = 1.0 / c->area2[e];
+        const double dNx[3] = {(-yCA + yBA) * inv, yCA * inv, -yBA * inv};
+        const double dNy[3] = {(xCA - xBA) * inv, -xCA * inv, xBA * inv};
+        const int32_t *t = c->tri + 3 * e;
+        for (int a = 0; a < 3; ++a) {
+            for (int b = 0; b < 3; ++b) {
+                const double kab = A * (dNx[a] * dNx[b] + dNy[a] * dNy[b]);
+                y[t[a]] += kab * x[t[b]];
+                if (diag && a == b) diag[t[a]] += kab;
+            }
+        }
+    }
+}
+
+/* Eq. 33 by Galerkin FEM with linear triangles (Sect. 3.2): the weak form
+ *     int grad N_a . grad dP = int_boundary N_a dP/dn - int N_a src
+ * with src[nn] interpolated linearly (consistent mass matrix) and the normal derivative
+ * flux[nn] interpolated linearly along each no-slip edge (edge length l: l/6 (2 g_a + g_b)
+ * to node a).  The matrix is singular (periodic and Neumann boundaries only: constants
+ * are its null space).  Readings: the load's component along the constants (the
+ * statistical defect of the compatibility condition) is removed by subtracting its nodal
+ * mean; conjugate gradients with the Jacobi preconditioner, started from dP, then solve
+ * the consistent system, and the solution is shifted to zero integral over the domain.
+ * Stopping rule and iteration limit as in orc_wp_solve. */
+int orc_pressure_solve(const orc_ctx *c, const double *src, const double *flux, double *dP,
+                       double tol, int max_iter, int *iters)
+{
+    const int nn = c->nn;
+    double *b = (double *)malloc(sizeof(double) * nn), *r = (double *)malloc(sizeof(double) * nn);
+    double *z = (double *)malloc(sizeof(double) * nn), *d = (double *)malloc(sizeof(double) * nn);
+    double *q = (double *)malloc(sizeof(double) * nn), *dg = (double *)malloc(sizeof(double) * nn);
+    int8_t *none = (int8_t *)calloc((size_t)nn, 1);
+    int rc = 0;
+    mass_apply(c, src, b);
+    for (int n = 0; n < nn; ++n) b[n] = -b[n];
+    for (int e = 0; e < c->ne; ++e) {
+        for (int k = 0; k < 3; ++k) {
+            if (c->tag[3 * e + k] != 1) continue;
+            const int ia = (k + 1) % 3, ib = (k + 2) % 3;
+            const int na = c->tri[3 * e + ia], nb = c->tri[3 * e + ib];
+            const double ex = c->vx[3 * e + ib] - c->vx[3 * e + ia], ey = c->vy[3 * e + ib] - c->vy[3 * e + ia];
+            const double l = sqrt(ex * ex + ey * ey);
+            b[na] += l / 6.0 * (2.0 * flux[na] + flux[nb]);
+            b[nb] += l / 6.0 * (flux[na] + 2.0 * flux[nb]);
+        }
+    }
+    double mean = 0.0;
+    for (int n = 0; n < nn; ++n) mean += b[n];
+    mean /= nn;
+    for (int n = 0; n < nn; ++n) b[n] -= mean;
+    stiffness_apply(c, dP, q, dg);
+    for (int n = 0; n < nn; ++n) r[n] = b[n] - q[n];
+    for (int n = 0; n < nn; ++n) z[n] = b[n] / dg[n];
+    const double bnorm = sqrt(dot_free(z, z, none, nn));
+    for (int n = 0; n < nn; ++n) { z[n] = r[n] / dg[n]; d[n] = z[n]; }
+    double rz = dot_free(r, z, none, nn);
+    int it = 0;
+    while (sqrt(dot_free(z, z, none, nn)) > tol * bnorm) {
+        if (it == max_iter) { rc = -2; break; }
+        stiffness_apply(c, d, q, NULL);
+        const double alpha = rz / dot_free(d, q, none, nn);
+        for (int n = 0; n < nn; ++n) {
+            dP[n] += alpha * d[n];
+            r[n] -= alpha * q[n];
+            z[n] = r[n] / dg[n];
+        }
+        const double rz1 = dot_free(r, z, none, nn);
+        const double beta = rz1 / rz;
+        rz = rz1;
+        for (int n = 0; n < nn; ++n) d[n] = z[n] + beta * d[n];
+        ++it;
+    }
+    /* zero integral: the integral of the linear interpolant is sum_a dP_a (sum_e A_e / 3) */
+    double num = 0.0, den = 0.0;
+    for (int e = 0; e < c->ne; ++e) {
+        const double A3 = 0.5 * c->area2[e] / 3.0;
+        for (int a = 0; a < 3; ++a) { num += A3 * dP[c->tri[3 * e + a]]; den += A3; }
+    }
+    for (int n = 0; n < nn; ++n) dP[n] -= num / den;
+    if (iters) *iters = it;
+    free(b); free(r); free(z); free(d); free(q); free(dg); free(none);
+    return rc;
+}
+
+/* One timestep of the coupled loop in the order of Table 1: the time step (Eq. 26, for
+ * dt <= 0), the elliptic relaxation (Eq. 12, slots 14-22), the particle advance (velocity
+ * prediction, Eq. 27, with the other particle equations, walls and tracking) and the
+ * particle-number control, the pressure projection (Eq. 33 from the nodal means <U>* of
+ * the predicted particles, two-pass as in Sect. 3.3) and the mean-velocity correction
+ * (Eq. 31), then the statistics.  P[nn] (the nodal mean pressure, rho = 1) is advanced by
+ * the increment, which dP[nn] returns (its value on entry is the initial guess); the
+ * fields the particles provide and the pressure gradient (slots 3-4, Sect. 3.4) are then
+ * derived from the new state.  Reading: the redistribution of Appendix B, which Table 1
+ * does not list, follows the advance as in the particle-path step. */
+int orc_coupled_step(orc_ctx *c, double dt, double Cp, double *P, double *dP, double tol,
+                     int max_iter, int *wp_iters, int *p_iters)
+{
+    const int nn = c->nn;
+    if (!(dt > 0.0)) {
+        if (orc_cfl_dt(c, &dt)) return -1;
+    }
+    c->last_dt = dt;
+    int rc = orc_update_wp(c, tol, max_iter, wp_iters);
+    if (rc) return rc;
+    rc = orc_advance(c, dt);
+    if (rc) return rc;
+    orc_redistribute(c);
+    rc = orc_statistics(c);
+    if (rc) return rc;
+    double *ustar = (double *)malloc(sizeof(double) * 3 * nn);
+    double *src = (double *)malloc(sizeof(double) * nn), *flux = (double *)malloc(sizeof(double) * nn);
+    double *gp = (double *)malloc(sizeof(double) * 2 * nn);
+    for (int n = 0; n < nn; ++n)
+        for (int i = 0; i < 3; ++i) ustar[3 * n + i] = c->nmom[(size_t)NS * n + 1 + i];
+    rc = orc_pressure_rhs(c, ustar, P, dt, Cp, src, flux);
+    if (rc == 0) rc = orc_pressure_solve(c, src, flux, dP, tol, max_iter, p_iters);
+    if (rc == 0) {
+        orc_correct_velocity(c, dP, dt);
+        rc = orc_statistics(c);
+    }
+    if (rc == 0) {
+        for (int n = 0; n < nn; ++n) P[n] += dP[n];
+        orc_derive_fields(c);
+        orc_node_gradient(c, P, gp);
+        for (int n = 0; n < nn; ++n) {
+            c->fields[(size_t)NF * n + 3] = gp[2 * n];
+            c->fields[(size_t)NF * n + 4] = gp[2 * n + 1];
+        }
+        orc_finish_step(c);
+    }
+    free(ustar); free(src); free(flux); free(gp);
     return rc;
 }
 

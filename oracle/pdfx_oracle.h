@@ -112,6 +112,17 @@ int  orc_wp_solve(const orc_ctx *c, const double *rhs, const double *L, double *
                   int max_iter, int *iters);
 /* orc_wp_rhs, then orc_wp_solve from the fields' wp_ij (slots 14-22), written back there. */
 int  orc_update_wp(orc_ctx *c, double tol, int max_iter, int *iters);
+/* Eq. 33's nodal right-hand side src[nn] from the nodal means ustar[nn][3] and the nodal
+ * pressure P[nn] (rho = 1), and the increment's normal derivative flux[nn] at no-slip nodes
+ * from Eq. 61. */
+int  orc_pressure_rhs(const orc_ctx *c, const double *ustar, const double *P, double dt, double Cp,
+                      double *src, double *flux);
+/* Eq. 33 by Galerkin FEM and Jacobi-PCG; dP[nn]: initial guess in, zero-mean solution out. */
+int  orc_pressure_solve(const orc_ctx *c, const double *src, const double *flux, double *dP,
+                        double tol, int max_iter, int *iters);
+/* One step of the coupled loop in Table 1's order (see pdfx_oracle.c). */
+int  orc_coupled_step(orc_ctx *c, double dt, double Cp, double *P, double *dP, double tol,
+                      int max_iter, int *wp_iters, int *p_iters);
 int  orc_advance(orc_ctx *c, double dt);      /* Eqs. 7, 27, 19, 24, Sect. 3.8, 3.6 */
 int  orc_redistribute(orc_ctx *c);            /* Sect. 3.7, Appendix B */
 int  orc_statistics(orc_ctx *c);              /* Sect. 3.3 and 3.5, Appendix A */

@@ -359,3 +359,164 @@ def test_solve_free_slip_symmetry_conditions():
         assert np.abs(off[edge]).max() == 0.0
         errs.append(np.abs(off - prof[:, None]).max())
     assert errs[2] < 4e-3 and errs[0] / errs[2] > 10.0
+
+
+# --------------------------------------------------------------------------------------
+# The pressure projection (Eq. 33 with Eq. 61) and the coupled step
+# --------------------------------------------------------------------------------------
+
+def _unwrapped(g):
+    """Element vertex coordinates with x taken as the image nearest to vertex A."""
+    x = g.node_xy[g.tri, 0].copy()
+    for k in (1, 2):
+        x[:, k] -= g.period_x * np.round((x[:, k] - x[:, 0]) / g.period_x)
+    return x, g.node_xy[g.tri, 1]
+
+
+def _areas(g):
+    x, y = _unwrapped(g)
+    return 0.5 * ((x[:, 1] - x[:, 0]) * (y[:, 2] - y[:, 0]) - (x[:, 2] - x[:, 0]) * (y[:, 1] - y[:, 0]))
+
+
+def test_pressure_solve_periodic_mode_converges_at_second_order():
+    """lap dP = -5 pi^2 cos(2 pi x) cos(pi y) on the periodic strip with zero normal
+    derivative at the free-slip rows: the zero-mean solution is cos(2 pi x) cos(pi y), which
+    the Galerkin solution approaches at second order; its integral is zero."""
+    errs = []
+    for n in (8, 16, 32):
+        g = _freeslip_grid(n, n + 1, seed=3)
+        o = oracle.Oracle(g, base_params(period_x=g.period_x), synth.uniform_fields(g.nn))
+        x, y = g.node_xy.T
+        exact = np.cos(2 * np.pi * x) * np.cos(np.pi * y)
+        dP, _ = o.pressure_solve(-5 * np.pi ** 2 * exact, np.zeros(g.nn))
+        errs.append(np.abs(dP - exact).max())
+        assert abs(np.sum(_areas(g)[:, None] / 3 * dP[g.tri])) < 1e-13
+    assert errs[2] < 0.01 and errs[0] / errs[2] > 10.0
+
+
+def test_pressure_solve_wall_flux_converges_at_second_order():
+    """lap dP = 1 in the walled channel with outward normal derivative 1 on the wall y = 1
+    and 0 on y = 0 (compatible: the source integrates to the boundary flux) has the
+    zero-mean solution y^2/2 - 1/6; the flux enters through the edge integrals of the weak
+    form."""
+    errs = []
+    for n in (8, 16, 32):
+        g = synth.channel_grid(n, n + 1, lx=1.0, seed=3)
+        o = oracle.Oracle(g, base_params(period_x=g.period_x), synth.uniform_fields(g.nn))
+        y = g.node_xy[:, 1]
+        dP, _ = o.pressure_solve(np.ones(g.nn), np.where(y == 1.0, 1.0, 0.0))
+        errs.append(np.abs(dP - (y * y / 2 - 1.0 / 6.0)).max())
+    assert errs[2] < 3e-4 and errs[0] / errs[2] > 10.0
+
+
+def test_pressure_rhs_linear_fields_closed_form():
+    """Eq. 33's source and Eq. 61's increment flux for fields linear in y, for which every
+    node-transferred derivative is exact: <U>* = (a y, b y, 0) has divergence b; P = c y has
+    zero laplacian; with laplacian slots (lx, ly) and <uu>, <vv>, <uv> with y-slopes s1, s2,
+    s3, the wall y = 0 (n = (0, -1)) gets -nu ly + s2 + c and the wall y = 1 (n = (0, 1))
+    gets nu ly - s2 - c; other nodes get 0."""
+    g = synth.channel_grid(10, 9, lx=1.0, seed=6)
+    nu = 3e-3
+    y = g.node_xy[:, 1]
+    F = synth.uniform_fields(g.nn, lap=(0.4, -0.7, 0.0))
+    s1, s2, s3 = 0.3, -0.5, 0.8
+    F[:, 23] = 0.5 + s1 * y
+    F[:, 24] = 0.6 + s2 * y
+    F[:, 26] = 0.1 + s3 * y
+    o = oracle.Oracle(g, base_params(period_x=g.period_x, nu=nu), F)
+    a, b, c, dt, Cp = 1.3, 0.25, -2.0, 1e-3, 1e-3
+    ustar = np.stack([a * y, b * y, np.zeros(g.nn)], 1)
+    src, flux = o.pressure_rhs(ustar, c * y, dt, Cp)
+    np.testing.assert_allclose(src, b / dt, rtol=1e-10)
+    want = np.where(y == 0.0, -nu * (-0.7) + s2 + c, np.where(y == 1.0, nu * (-0.7) - s2 - c, 0.0))
+    np.testing.assert_allclose(flux, want, rtol=1e-10, atol=1e-12)
+
+
+def test_pressure_rhs_stabilisation_term():
+    """Eq. 33's C_p term with P = y^2 on a lattice whose node transfers give the exact
+    second derivative 2 two rows from the walls: src = (div <U>* - 2 C_p) / dt there."""
+    from test_oracle_pins import _same_diagonal_lattice
+    g = _same_diagonal_lattice(12, 9)
+    o = oracle.Oracle(g, base_params(period_x=g.period_x), synth.uniform_fields(g.nn))
+    y = g.node_xy[:, 1]
+    dt, Cp = 2e-3, 0.05
+    src, _ = o.pressure_rhs(np.stack([0 * y, 0.5 * y, 0 * y], 1), y * y, dt, Cp)
+    deep = (y > 1.5 / 8) & (y < 1 - 1.5 / 8)
+    np.testing.assert_allclose(src[deep], (0.5 - 2 * Cp) / dt, rtol=1e-10)
+
+
+def _elem_grad(g, q):
+    """Element gradients of a nodal field (shapefunction derivatives in the element frame)."""
+    x, yv = _unwrapped(g)
+    t = g.tri
+    A2 = (x[:, 1] - x[:, 0]) * (yv[:, 2] - yv[:, 0]) - (x[:, 2] - x[:, 0]) * (yv[:, 1] - yv[:, 0])
+    qv = q[t]
+    gx = (qv[:, 0] * (yv[:, 1] - yv[:, 2]) + qv[:, 1] * (yv[:, 2] - yv[:, 0]) + qv[:, 2] * (yv[:, 0] - yv[:, 1])) / A2
+    gy = (qv[:, 0] * (x[:, 2] - x[:, 1]) + qv[:, 1] * (x[:, 0] - x[:, 2]) + qv[:, 2] * (x[:, 1] - x[:, 0])) / A2
+    return gx, gy
+
+
+def test_coupled_step_against_the_particle_step():
+    """The coupled step of Table 1 moves the particles exactly as the particle-path step does
+    after the same elliptic-relaxation update (positions, frequency, scalar and element are
+    untouched by the projection), and differs only by Eq. 31's correction: each particle's
+    u, v drop by dt times its element's gradient of the pressure increment.  The increment
+    has zero integral, P advances by it, the pressure-gradient slots hold its node-transferred
+    gradient and the elliptic-relaxation slots the solution."""
+    w = synth.workload("channel_tiny")
+    g = w["grid"]
+    dt = w["dt"]
+    o1 = oracle.Oracle(g, w["params"], w["fields"])
+    o2 = oracle.Oracle(g, w["params"], w["fields"])
+    o1.init_particles(60)
+    o2.init_particles(60)
+    P0 = 0.2 * g.node_xy[:, 1] ** 2
+    P = P0.copy()
+    dP, wi, pi = o1.coupled_step(dt, P)
+    assert wi > 0 and pi > 0
+    o2.update_wp()
+    o2.step(dt)
+    s1, s2 = o1.get_particles(), o2.get_particles()
+    for k in ("x", "y", "w", "om", "psi", "elem"):
+        np.testing.assert_array_equal(s1[k], s2[k])
+    gx, gy = _elem_grad(g, dP)
+    e = s1["elem"]
+    np.testing.assert_allclose(s1["u"], s2["u"] - dt * gx[e], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(s1["v"], s2["v"] - dt * gy[e], rtol=0, atol=1e-13)
+    assert np.abs(dt * gy).max() > 1e-6
+    np.testing.assert_array_equal(P, P0 + dP)
+    f1, f2 = o1.fields(), o2.fields()
+    np.testing.assert_array_equal(f1[:, 14:23], f2[:, 14:23])
+    np.testing.assert_allclose(f1[:, 3:5], o1.node_gradient(P), rtol=0, atol=1e-14)
+    assert abs(np.sum(_areas(g)[:, None] / 3 * dP[g.tri])) < 1e-12 * np.abs(dP).max()
+
+
+def test_coupled_step_statistics_shift_with_the_correction():
+    """Eq. 31 shifts every particle of an element by the same vector, so the element means
+    shift by it, while the central moments, the velocity ordering and with it the bins and
+    their conditional scalar means stay as they were before the correction."""
+    w = synth.workload("channel_tiny")
+    g = w["grid"]
+    dt = w["dt"]
+    o1 = oracle.Oracle(g, w["params"], w["fields"])
+    o2 = oracle.Oracle(g, w["params"], w["fields"])
+    o1.init_particles(60)
+    o2.init_particles(60)
+    P = 0.2 * g.node_xy[:, 1] ** 2
+    dP, _, _ = o1.coupled_step(dt, P)
+    o2.update_wp()
+    o2.step(dt)
+    (m1, c1), (m2, c2) = o1.element_stats(), o2.element_stats()
+    np.testing.assert_array_equal(c1, c2)
+    gx, gy = _elem_grad(g, dP)
+    has = c1 > 0
+    np.testing.assert_allclose(m1[has, 1], m2[has, 1] - dt * gx[has], rtol=0, atol=1e-13)
+    np.testing.assert_allclose(m1[has, 2], m2[has, 2] - dt * gy[has], rtol=0, atol=1e-13)
+    np.testing.assert_array_equal(m1[:, 3], m2[:, 3])
+    scale = np.abs(m2[:, 4:10]).max()
+    np.testing.assert_allclose(m1[:, 4:10], m2[:, 4:10], rtol=0, atol=1e-12 * scale)
+    np.testing.assert_array_equal(m1[:, 10:], m2[:, 10:])
+    (v1, g1), (v2, g2) = o1.bins(), o2.bins()
+    np.testing.assert_array_equal(g1, g2)
+    np.testing.assert_array_equal(v1, v2)
+    np.testing.assert_array_equal(o1.get_particles()["cp"], o2.get_particles()["cp"])
