@@ -520,3 +520,49 @@ def test_coupled_step_statistics_shift_with_the_correction():
     np.testing.assert_array_equal(g1, g2)
     np.testing.assert_array_equal(v1, v2)
     np.testing.assert_array_equal(o1.get_particles()["cp"], o2.get_particles()["cp"])
+
+
+def test_pressure_stabilisation_factor():
+    """Eq. 33 with a divergence-free <U>* and no wall flux leaves lap dP = -(C_p / dt) lap P^n,
+    so dP = -(C_p / dt) P^n for a zero-mean P^n: P^{n+1} = (1 - C_p / dt) P^n, which is
+    stable only for C_p < 2 dt.  On a smooth mode the Galerkin solution of the two-pass
+    laplacian's load approaches that factor as h falls (slower than second order on the
+    coarse grids: the node-transferred second derivatives are one-sided at the boundary
+    rows)."""
+    errs = []
+    dt, Cp = 1e-3, 4e-4
+    for n in (8, 16, 32):
+        g = _freeslip_grid(n, n + 1, seed=6)
+        o = oracle.Oracle(g, base_params(period_x=g.period_x), synth.uniform_fields(g.nn))
+        x, y = g.node_xy.T
+        P = np.cos(2 * np.pi * x) * np.cos(np.pi * y)
+        src, flux = o.pressure_rhs(np.zeros((g.nn, 3)), P, dt, Cp)
+        assert np.abs(flux).max() == 0.0
+        dP, _ = o.pressure_solve(src, flux)
+        errs.append(np.abs(dP + (Cp / dt) * P).max() / (Cp / dt))
+    assert errs[2] < 0.04 and errs[0] / errs[2] > 8.0
+
+
+@pytest.mark.parametrize("name", ["channel_tiny", "canyon_2k"])
+def test_coupled_steps_stay_bounded(name):
+    """Six coupled steps (C_p = dt/2) on the channel (walls) and on the street canyon
+    (walls, cavity corners, free-slip top): states stay finite, every particle stays in the
+    domain and is found by the walk, the solves converge every step and the pressure
+    increment does not grow from step to step."""
+    w = synth.workload(name) if name == "channel_tiny" else synth.canyon_workload(name)
+    g = w["grid"]
+    o = oracle.Oracle(g, w["params"], w["fields"])
+    o.init_particles(20 if name == "canyon_2k" else 60)
+    o.derive_fields()
+    P = np.zeros(g.nn)
+    dP, peak = None, []
+    for _ in range(6):
+        dP, wi, pi = o.coupled_step(w["dt"], P, dP, Cp=0.5 * w["dt"], tol=1e-10)
+        peak.append(np.abs(dP).max())
+    st = o.get_particles()
+    for k in ("x", "y", "u", "v", "w", "om", "psi"):
+        assert np.isfinite(st[k]).all()
+    d = o.diag()
+    assert d["lost"] == 0 and d["walk_brute"] == 0
+    assert max(peak[1:]) < 2.0 * peak[0]
+    assert np.isfinite(P).all()
