@@ -49,6 +49,7 @@ extern "C" {
 #define PDFX_ERR_LOST_PARTICLE -6   /* a particle was found in no element (device word) */
 #define PDFX_ERR_CAPACITY      -7   /* an element exceeded PDFX_MAX_PER_ELEMENT (device word) */
 #define PDFX_ERR_NONFINITE     -8   /* a particle state became NaN or infinite (device word) */
+#define PDFX_ERR_SOLVE         -9   /* an iterative solve did not converge within its limit */
 
 #define PDFX_NF 32                  /* nodal field slots, layout below */
 #define PDFX_NSTAT 13               /* statistics per element or node, layout below */
@@ -349,6 +350,84 @@ int  pdfx_element_stats_noalloc(void *ctx, int64_t np, const double *u, const do
                                 const double *w, const double *om, const double *psi,
                                 const int32_t *elem, double *emom, double *vcce, int32_t *gbin,
                                 uint8_t *cp, double *nmom, void *stream);
+
+/* ---------------------------------------------------------------------------------------
+ * Eulerian solves of the coupled loop (Sect. 3.2), FP64 on the device for both forms.
+ * Single grids only (PDFX_ERR_ARG for a batch).  The first of these calls after
+ * pdfx_set_grid builds the grid's Galerkin matrices for linear triangles in CSR: the
+ * consistent mass matrix and the laplacian stiffness, from Eq. 40's derivatives.  It also
+ * classifies the nodes: a node on a no-slip edge (tag 1), with its outward unit normal
+ * (the normalised sum of its wall edges' normals), else a node on a free-slip edge (tag
+ * 2), else interior.  The linear systems are solved by conjugate gradients with the
+ * Jacobi preconditioner, started from the given initial guess.  Each system iterates
+ * until the 2-norm of its preconditioned residual over the free nodes is at most tol
+ * times that of its preconditioned reduced load (the load minus the Dirichlet columns;
+ * a zero reduced load gives the zero solution on the free nodes).  More than max_iter
+ * iterations is PDFX_ERR_SOLVE.  *iters (may be NULL) receives the largest iteration
+ * count.  Host arrays; every call returns after its results are on the host (or in the
+ * context).
+ * ------------------------------------------------------------------------------------- */
+
+/* Eqs. 12-18 at every node from the context's nodal fields: the local right-hand side
+ *     rhs_ij = (1 - C1)/2 k <omega> delta_ij + k H_ijkl d<U_k>/dx_l
+ * (H of Eq. 13, A_v of Eq. 14, b of Eq. 15; d/dz = 0) into rhs[nn][9] (row-major i, j), and
+ * the length scale L of Eq. 16 (C_xi of Eq. 17 = 2.3 when the grid has a no-slip edge,
+ * else 1; eps of Eq. 18) into L[nn].  Inputs: d<U_i>/dx_j (slots 5-10), <u_i u_j>
+ * (23-28), <omega> (29).  A node with eps <= 0 gives PDFX_ERR_ARG. */
+int  pdfx_wp_rhs(void *ctx, double *rhs, double *L, void *stream);
+
+/* Eq. 12, wp - div(L_e^2 grad wp) = rhs, by Galerkin FEM.  The nine components share the
+ * matrix M + L_e^2 K, where L_e^2 is the mean of the element's nodal L^2; the load is M rhs.
+ * Conditions: wp_ij = -4.5 eps n_i n_j at no-slip nodes (Eq. 59, eps from the node's
+ * fields); at free-slip nodes wp_ij = 0 for i != j and the natural condition for i == j
+ * (the symmetry conditions of Sect. 4.1).  rhs[nn][9], L[nn]; wp[nn][9] holds the initial
+ * guess on entry and the solution on exit. */
+int  pdfx_wp_solve(void *ctx, const double *rhs, const double *L, double *wp, double tol,
+                   int32_t max_iter, int32_t *iters, void *stream);
+
+/* The elliptic-relaxation update of the coupled loop: pdfx_wp_rhs and pdfx_wp_solve on the
+ * context's own fields, from their wp_ij (slots 14-22) as the initial guess, the solution
+ * written back to slots 14-22. */
+int  pdfx_update_wp(void *ctx, double tol, int32_t max_iter, int32_t *iters, void *stream);
+
+/* Eq. 33's nodal source with rho = 1, src = (div <U>* - Cp lap P) / dt, into src[nn]:
+ * div <U>* from the node-transferred gradients (Sect. 3.4) of ustar[nn][3] (the nodal
+ * means of the predicted velocities), and lap P by Sect. 3.4's two passes applied to
+ * P[nn].  Also, into flux[nn], the outward normal derivative of the pressure increment at
+ * no-slip nodes (0 elsewhere).  That is Eq. 61's value from the fields, nu lap<U_i> n_i
+ * (slots 11-12) - d<u_i u_j>/dx_j n_i (node-transferred gradients of slots 23, 24, 26),
+ * minus n . grad P.  dt > 0. */
+int  pdfx_pressure_rhs(void *ctx, const double *ustar, const double *P, double dt, double Cp,
+                       double *src, double *flux, void *stream);
+
+/* Eq. 33 by Galerkin FEM: the laplacian stiffness K against the load -M src plus the edge
+ * integrals of flux along no-slip edges (flux linear along the edge).  The matrix is
+ * singular (periodic and natural boundaries), so the load's nodal mean is removed, and the
+ * solution is shifted to zero integral over the domain.  src[nn], flux[nn]; dP[nn] holds
+ * the initial guess on entry and the solution on exit. */
+int  pdfx_pressure_solve(void *ctx, const double *src, const double *flux, double *dP, double tol,
+                         int32_t max_iter, int32_t *iters, void *stream);
+
+/* The context's nodal mean pressure P[nn] (rho = 1; zero after the FEM data is built) and
+ * the last pressure increment dP[nn] (the next step's initial guess; set_pressure clears
+ * it).  get_pressure writes whichever pointer is not NULL. */
+int  pdfx_set_pressure(void *ctx, const double *P, void *stream);
+int  pdfx_get_pressure(void *ctx, double *P, double *dP, void *stream);
+
+/* One step of the coupled loop, in the order of Table 1:
+ *   1. the time step (Eq. 26 when dt <= 0);
+ *   2. the elliptic-relaxation update (pdfx_update_wp);
+ *   3. the particle step of pdfx_step (velocity prediction of Eq. 27 with the other
+ *      particle equations, walls, tracking, particle-number control, statistics);
+ *   4. the pressure projection: pdfx_pressure_rhs with the predicted nodal means and the
+ *      context's P, then pdfx_pressure_solve from the last increment;
+ *   5. the correction of Eq. 31 on the particles and the statistics of the corrected state;
+ *   6. P += dP; the fields the statistics provide (pdfx_derive_fields) and the pressure
+ *      gradient (slots 3-4: the node-transferred gradient of P) from the new state.
+ * Eq. 33 is stable only for Cp < 2 dt.  iters[2] (may be NULL) receives the iteration
+ * counts of the two solves. */
+int  pdfx_coupled_step(void *ctx, double dt, double Cp, double tol, int32_t max_iter,
+                       int32_t *iters, void *stream);
 
 /* Number of kernel launches the library issued since creation. */
 int64_t pdfx_kernel_launches(const void *ctx);

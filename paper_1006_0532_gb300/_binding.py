@@ -117,6 +117,14 @@ def lib():
                 "pdfx_stage_times": (C.c_int, [vp, C.POINTER(dp), C.POINTER(i64), C.c_int, vp]),
                 "pdfx_kernel_launches": (i64, [vp]),
                 "pdfx_element_stats_noalloc": (C.c_int, [vp, i64] + [vp] * 11 + [vp]),
+                "pdfx_wp_rhs": (C.c_int, [vp, vp, vp, vp]),
+                "pdfx_wp_solve": (C.c_int, [vp, vp, vp, vp, dp, i32, C.POINTER(i32), vp]),
+                "pdfx_update_wp": (C.c_int, [vp, dp, i32, C.POINTER(i32), vp]),
+                "pdfx_pressure_rhs": (C.c_int, [vp, vp, vp, dp, dp, vp, vp, vp]),
+                "pdfx_pressure_solve": (C.c_int, [vp, vp, vp, vp, dp, i32, C.POINTER(i32), vp]),
+                "pdfx_set_pressure": (C.c_int, [vp, vp, vp]),
+                "pdfx_get_pressure": (C.c_int, [vp, vp, vp, vp]),
+                "pdfx_coupled_step": (C.c_int, [vp, dp, dp, dp, i32, vp, vp]),
                 "pdfx_strerror": (C.c_char_p, [C.c_int]),
             }
             for name, (res, args) in sig.items():
@@ -312,6 +320,73 @@ class Context:
         d = np.ascontiguousarray(dp, dtype=np.float64)
         self._check(lib().pdfx_correct_velocity(self.h, d.ctypes.data, float(dt), _stream(stream)),
                     "pdfx_correct_velocity")
+
+    # Eulerian solves of the coupled loop (FP64 on the device; host arrays).
+    def wp_rhs(self, stream=None):
+        """Eqs. 12-18 at every node from the fields: (rhs[nn][3][3], L[nn])."""
+        rhs, L = np.zeros((self.nn, 9)), np.zeros(self.nn)
+        self._check(lib().pdfx_wp_rhs(self.h, rhs.ctypes.data, L.ctypes.data, _stream(stream)),
+                    "pdfx_wp_rhs")
+        return rhs.reshape(self.nn, 3, 3), L
+
+    def wp_solve(self, rhs, L, wp0=None, tol: float = 1e-13, max_iter: int = 100000, stream=None):
+        """Eq. 12 by Galerkin FEM and Jacobi-PCG: (wp[nn][3][3], iterations)."""
+        r = np.ascontiguousarray(np.asarray(rhs, dtype=np.float64).reshape(self.nn, 9))
+        LL = np.ascontiguousarray(L, dtype=np.float64)
+        wp = (np.zeros((self.nn, 9)) if wp0 is None
+              else np.array(np.asarray(wp0, dtype=np.float64).reshape(self.nn, 9)))
+        it = C.c_int32()
+        self._check(lib().pdfx_wp_solve(self.h, r.ctypes.data, LL.ctypes.data, wp.ctypes.data, float(tol),
+                                        int(max_iter), C.byref(it), _stream(stream)), "pdfx_wp_solve")
+        return wp.reshape(self.nn, 3, 3), it.value
+
+    def update_wp(self, tol: float = 1e-13, max_iter: int = 100000, stream=None) -> int:
+        """Eq. 12's update of the fields' wp_ij (slots 14-22); returns the iterations."""
+        it = C.c_int32()
+        self._check(lib().pdfx_update_wp(self.h, float(tol), int(max_iter), C.byref(it), _stream(stream)),
+                    "pdfx_update_wp")
+        return it.value
+
+    def pressure_rhs(self, ustar, P, dt: float, Cp: float = 1e-3, stream=None):
+        """Eq. 33's nodal source and Eq. 61's increment flux: (src[nn], flux[nn])."""
+        u = np.ascontiguousarray(np.asarray(ustar, dtype=np.float64).reshape(self.nn, 3))
+        p = np.ascontiguousarray(P, dtype=np.float64)
+        src, flux = np.zeros(self.nn), np.zeros(self.nn)
+        self._check(lib().pdfx_pressure_rhs(self.h, u.ctypes.data, p.ctypes.data, float(dt), float(Cp),
+                                            src.ctypes.data, flux.ctypes.data, _stream(stream)),
+                    "pdfx_pressure_rhs")
+        return src, flux
+
+    def pressure_solve(self, src, flux, dP0=None, tol: float = 1e-13, max_iter: int = 100000,
+                       stream=None):
+        """Eq. 33 by Galerkin FEM and Jacobi-PCG: (zero-mean dP[nn], iterations)."""
+        s_ = np.ascontiguousarray(src, dtype=np.float64)
+        f = np.ascontiguousarray(flux, dtype=np.float64)
+        d = np.zeros(self.nn) if dP0 is None else np.array(dP0, dtype=np.float64)
+        it = C.c_int32()
+        self._check(lib().pdfx_pressure_solve(self.h, s_.ctypes.data, f.ctypes.data, d.ctypes.data,
+                                              float(tol), int(max_iter), C.byref(it), _stream(stream)),
+                    "pdfx_pressure_solve")
+        return d, it.value
+
+    def set_pressure(self, P, stream=None):
+        p = np.ascontiguousarray(P, dtype=np.float64)
+        self._check(lib().pdfx_set_pressure(self.h, p.ctypes.data, _stream(stream)), "pdfx_set_pressure")
+
+    def pressure(self, stream=None):
+        """(P[nn], last dP[nn])."""
+        P, dP = np.zeros(self.nn), np.zeros(self.nn)
+        self._check(lib().pdfx_get_pressure(self.h, P.ctypes.data, dP.ctypes.data, _stream(stream)),
+                    "pdfx_get_pressure")
+        return P, dP
+
+    def coupled_step(self, dt: float, Cp: float = 1e-3, tol: float = 1e-13, max_iter: int = 100000,
+                     stream=None):
+        """One step of the coupled loop in Table 1's order; returns the two solves' iterations."""
+        it = (C.c_int32 * 2)()
+        self._check(lib().pdfx_coupled_step(self.h, float(dt), float(Cp), float(tol), int(max_iter), it,
+                                            _stream(stream)), "pdfx_coupled_step")
+        return it[0], it[1]
 
     def fields(self, stream=None):
         out = np.zeros((self.nn, 32))

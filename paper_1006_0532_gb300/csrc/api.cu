@@ -742,6 +742,12 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
   if (!c.fields || (c.prm.precision == 1 && !c.fields64)) return PDFX_ERR_ALLOC;
   for (int b = 0; b < 2; ++b) { dev_free(c, c.pbuf[b]); c.pbuf[b] = nullptr; }
   c.np = 0;
+  c.h_tri.assign(tri, tri + 3 * E);
+  c.h_tag.assign(tag, tag + 3 * E);
+  c.h_vx = g.vx;
+  c.h_vy = g.vy;
+  c.h_area2 = g.area2;
+  c.fem_ready = false;   // the Eulerian calls rebuild their FEM data for this grid
   c.have_grid = true;
   c.have_fields = false;
   return PDFX_OK;
@@ -926,6 +932,365 @@ int cfl_dt(Ctx& c, cudaStream_t s, double* dt) {
   if (!(norm > 0.0) || !std::isfinite(norm)) return PDFX_ERR_ARG;
   *dt = c.prm.cfl * c.min_sqrt_an / norm;
   return (*dt > 0.0 && std::isfinite(*dt)) ? PDFX_OK : PDFX_ERR_ARG;
+}
+
+
+// ---------------------------------------------------------------------------------------
+// Eulerian solves of the coupled loop (Sect. 3.2): FEM data, Jacobi-PCG, the elliptic
+// relaxation (Eqs. 12-18, 59), the pressure projection (Eqs. 33, 61) and the coupled step
+// in the order of Table 1.  Single grids only (a batch's instances would each need their
+// own pressure null space).
+// ---------------------------------------------------------------------------------------
+
+template <typename P>
+int upload_vec(Ctx& c, P*& dst, const std::vector<P>& src) {
+  PDFX_TRY(alloc_into(c, dst, src.size()));
+  if (!src.empty()) PDFX_CUDA(cudaMemcpy(dst, src.data(), sizeof(P) * src.size(), cudaMemcpyHostToDevice));
+  return PDFX_OK;
+}
+
+// Work arrays of the Eulerian calls, carved from c.ew.
+struct EWork {
+  double *x, *b, *r, *z, *d, *q;   // [9][nn] solver vectors
+  double *rhs;                     // [9][nn] right-hand side of Eq. 12
+  double *L;                       // [nn] length scale of Eq. 16
+  double *aval, *adiag;            // [nnz], [nn] elliptic-relaxation matrix
+  double *src, *flux;              // [nn] Eq. 33 source, increment normal derivative
+  double *pcg;                     // PCG partial sums and scalars
+  double *prs;                     // derivative passes of the pressure source
+  double *big;                     // 18 (ne + nn): derived fields, element gradients
+  double *red;                     // 72: reductions
+};
+
+size_t ework_doubles(const Ctx& c) {
+  const size_t N = static_cast<size_t>(c.nn), E = static_cast<size_t>(c.ne);
+  return 7 * 9 * N + N + static_cast<size_t>(c.fem.nnz) + N + 2 * N + pcg_scratch_doubles(c.nn, 9) +
+         pressure_rhs_scratch_doubles(c.nn, c.ne) + 18 * (E + N) + 72;
+}
+
+EWork ework(Ctx& c) {
+  const size_t N = static_cast<size_t>(c.nn), N9 = 9 * N, E = static_cast<size_t>(c.ne);
+  double* p = c.ew;
+  EWork w{};
+  w.x = p; p += N9;
+  w.b = p; p += N9;
+  w.r = p; p += N9;
+  w.z = p; p += N9;
+  w.d = p; p += N9;
+  w.q = p; p += N9;
+  w.rhs = p; p += N9;
+  w.L = p; p += N;
+  w.aval = p; p += static_cast<size_t>(c.fem.nnz);
+  w.adiag = p; p += N;
+  w.src = p; p += N;
+  w.flux = p; p += N;
+  w.pcg = p; p += pcg_scratch_doubles(c.nn, 9);
+  w.prs = p; p += pressure_rhs_scratch_doubles(c.nn, c.ne);
+  w.big = p; p += 18 * (E + N);
+  w.red = p;
+  return w;
+}
+
+// The FEM data of the current grid (host, FP64) and the device work arrays.
+int ensure_fem(Ctx& c) {
+  if (c.fem_ready) return PDFX_OK;
+  if (!c.have_grid || c.K > 1) return PDFX_ERR_ARG;
+  const int nn = c.nn, ne = c.ne;
+  const std::vector<int32_t>& tri = c.h_tri;
+  FemDev& m = c.fem;
+  // element data: Eq. 40's derivatives in the element's frame, and the area
+  std::vector<double> fe(7 * static_cast<size_t>(ne)), mlump(static_cast<size_t>(nn), 0.0);
+  double area = 0.0;
+  for (int e = 0; e < ne; ++e) {
+    const double* vx = &c.h_vx[3 * static_cast<size_t>(e)];
+    const double* vy = &c.h_vy[3 * static_cast<size_t>(e)];
+    const double xBA = vx[1] - vx[0], yBA = vy[1] - vy[0];
+    const double xCA = vx[2] - vx[0], yCA = vy[2] - vy[0];
+    const double a2 = c.h_area2[e], inv = 1.0 / a2;
+    double* g = &fe[7 * static_cast<size_t>(e)];
+    g[0] = (-yCA + yBA) * inv; g[1] = yCA * inv; g[2] = -yBA * inv;
+    g[3] = (xCA - xBA) * inv;  g[4] = -xCA * inv; g[5] = xBA * inv;
+    g[6] = 0.5 * a2;
+    area += g[6];
+    for (int a = 0; a < 3; ++a) mlump[tri[3 * e + a]] += g[6] / 3.0;
+  }
+  // CSR pattern of the node graph (each node with its neighbours and itself)
+  std::vector<std::vector<int32_t>> adj(static_cast<size_t>(nn));
+  for (int e = 0; e < ne; ++e)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) adj[tri[3 * e + a]].push_back(tri[3 * e + b]);
+  std::vector<int32_t> row(static_cast<size_t>(nn) + 1, 0), col;
+  for (int n = 0; n < nn; ++n) {
+    std::sort(adj[n].begin(), adj[n].end());
+    adj[n].erase(std::unique(adj[n].begin(), adj[n].end()), adj[n].end());
+    row[n + 1] = row[n] + static_cast<int32_t>(adj[n].size());
+  }
+  const int nnz = row[nn];
+  col.reserve(static_cast<size_t>(nnz));
+  for (int n = 0; n < nn; ++n) col.insert(col.end(), adj[n].begin(), adj[n].end());
+  auto entry = [&](int r, int cc) {
+    return static_cast<int32_t>(std::lower_bound(col.begin() + row[r], col.begin() + row[r + 1], cc) - col.begin());
+  };
+  std::vector<int32_t> dpos(static_cast<size_t>(nn));
+  for (int n = 0; n < nn; ++n) dpos[n] = entry(n, n);
+  // contributions of each entry, ascending element
+  std::vector<int32_t> cptr(static_cast<size_t>(nnz) + 1, 0), clist(9 * static_cast<size_t>(ne));
+  std::vector<int32_t> epos(9 * static_cast<size_t>(ne));
+  for (int e = 0; e < ne; ++e)
+    for (int a = 0; a < 3; ++a)
+      for (int b = 0; b < 3; ++b) {
+        const int32_t k = entry(tri[3 * e + a], tri[3 * e + b]);
+        epos[9 * static_cast<size_t>(e) + 3 * a + b] = k;
+        cptr[k + 1]++;
+      }
+  for (int k = 0; k < nnz; ++k) cptr[k + 1] += cptr[k];
+  {
+    std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
+    for (int e = 0; e < ne; ++e)
+      for (int ab = 0; ab < 9; ++ab) clist[fill[epos[9 * static_cast<size_t>(e) + ab]]++] = 9 * e + ab;
+  }
+  // the fixed matrices: consistent mass and laplacian stiffness
+  std::vector<double> mval(static_cast<size_t>(nnz), 0.0), kval(static_cast<size_t>(nnz), 0.0);
+  for (int k = 0; k < nnz; ++k)
+    for (int j = cptr[k]; j < cptr[k + 1]; ++j) {
+      const int e = clist[j] / 9, a = (clist[j] % 9) / 3, b = clist[j] % 3;
+      const double* g = &fe[7 * static_cast<size_t>(e)];
+      mval[k] += g[6] / 12.0 * (a == b ? 2.0 : 1.0);
+      kval[k] += g[6] * (g[a] * g[b] + g[3 + a] * g[3 + b]);
+    }
+  std::vector<double> kdiag(static_cast<size_t>(nn));
+  for (int n = 0; n < nn; ++n) kdiag[n] = kval[dpos[n]];
+  // boundary classes, outward normals of no-slip nodes, no-slip edges at each node
+  std::vector<int8_t> cls(static_cast<size_t>(nn), 0);
+  std::vector<double> nrm(2 * static_cast<size_t>(nn), 0.0);
+  std::vector<std::vector<std::pair<int32_t, double>>> bed(static_cast<size_t>(nn));
+  bool wall = false;
+  for (int e = 0; e < ne; ++e) {
+    const double* vx = &c.h_vx[3 * static_cast<size_t>(e)];
+    const double* vy = &c.h_vy[3 * static_cast<size_t>(e)];
+    for (int k = 0; k < 3; ++k) {
+      const int t = c.h_tag[3 * static_cast<size_t>(e) + k];
+      if (t != 1 && t != 2) continue;
+      const int ia = (k + 1) % 3, ib = (k + 2) % 3;
+      const int32_t na = tri[3 * e + ia], nb = tri[3 * e + ib];
+      const double tx = vx[ib] - vx[ia], ty = vy[ib] - vy[ia];
+      const double len = std::sqrt(tx * tx + ty * ty);
+      double mx = -ty / len, my = tx / len;   // toward vertex k: into the domain
+      if ((vx[k] - vx[ia]) * mx + (vy[k] - vy[ia]) * my < 0.0) { mx = -mx; my = -my; }
+      for (const int32_t n : {na, nb}) {
+        if (t == 1) {
+          cls[n] = 1;
+          nrm[2 * static_cast<size_t>(n)] -= mx;
+          nrm[2 * static_cast<size_t>(n) + 1] -= my;
+        } else if (cls[n] == 0) {
+          cls[n] = 2;
+        }
+      }
+      if (t == 1) {
+        wall = true;
+        bed[na].push_back({nb, len});
+        bed[nb].push_back({na, len});
+      }
+    }
+  }
+  for (int n = 0; n < nn; ++n) {
+    if (cls[n] != 1) continue;
+    const double l = std::hypot(nrm[2 * static_cast<size_t>(n)], nrm[2 * static_cast<size_t>(n) + 1]);
+    if (l > 0.0) { nrm[2 * static_cast<size_t>(n)] /= l; nrm[2 * static_cast<size_t>(n) + 1] /= l; }
+  }
+  std::vector<int32_t> boff(static_cast<size_t>(nn) + 1, 0), bnb;
+  std::vector<double> blen;
+  for (int n = 0; n < nn; ++n) {
+    for (const auto& pr : bed[n]) { bnb.push_back(pr.first); blen.push_back(pr.second); }
+    boff[n + 1] = static_cast<int32_t>(bnb.size());
+  }
+  m.nn = nn;
+  m.ne = ne;
+  m.nnz = nnz;
+  m.area = area;
+  m.cxi = 1.0 + 1.3 * (wall ? 1.0 : 0.0);   // Eq. 17 with n_i n_i of a unit normal
+  PDFX_TRY(upload_vec(c, m.row, row));
+  PDFX_TRY(upload_vec(c, m.col, col));
+  PDFX_TRY(upload_vec(c, m.dpos, dpos));
+  PDFX_TRY(upload_vec(c, m.cptr, cptr));
+  PDFX_TRY(upload_vec(c, m.clist, clist));
+  PDFX_TRY(upload_vec(c, m.tri, tri));
+  PDFX_TRY(upload_vec(c, m.fe, fe));
+  PDFX_TRY(upload_vec(c, m.mval, mval));
+  PDFX_TRY(upload_vec(c, m.kval, kval));
+  PDFX_TRY(upload_vec(c, m.kdiag, kdiag));
+  PDFX_TRY(upload_vec(c, m.mlump, mlump));
+  PDFX_TRY(upload_vec(c, m.ncls, cls));
+  PDFX_TRY(upload_vec(c, m.nrm, nrm));
+  PDFX_TRY(upload_vec(c, m.boff, boff));
+  PDFX_TRY(upload_vec(c, m.bnb, bnb));
+  PDFX_TRY(upload_vec(c, m.blen, blen));
+  PDFX_TRY(alloc_into(c, c.ew, ework_doubles(c)));
+  PDFX_TRY(alloc_into(c, c.efixed, 9 * static_cast<size_t>(nn)));
+  PDFX_TRY(alloc_into(c, c.eflag, 1));
+  PDFX_TRY(alloc_into(c, c.P, static_cast<size_t>(nn)));
+  PDFX_TRY(alloc_into(c, c.dP, static_cast<size_t>(nn)));
+  PDFX_CUDA(cudaMemset(c.P, 0, sizeof(double) * nn));
+  PDFX_CUDA(cudaMemset(c.dP, 0, sizeof(double) * nn));
+  c.fem_ready = true;
+  return PDFX_OK;
+}
+
+WpConst wp_const(const Ctx& c) {
+  const pdfx_params& p = c.prm;
+  WpConst k{};
+  k.C1 = p.C1; k.C2 = p.C2; k.Cv = p.Cv; k.gamma5 = p.gamma5; k.CL = p.CL; k.Ceta = p.Ceta;
+  k.CT = p.CT; k.nu = p.nu; k.cxi = c.fem.cxi;
+  return k;
+}
+
+// Iterates until every component meets its stopping rule (checked on the host every 16
+// iterations; a component that has converged stops changing), or fails after max_iter.
+int run_pcg(Ctx& c, const PcgArgs& a, int32_t max_iter, int32_t* iters, cudaStream_t s) {
+  launch_pcg_setup(c.fem, a, s);
+  c.launches += 8;
+  const double* sc = pcg_scalars(a, c.nn);
+  std::vector<double> h(static_cast<size_t>(a.C) * kPcgScalars);
+  int32_t done = 0;
+  for (;;) {
+    PDFX_CUDA(cudaMemcpyAsync(h.data(), sc, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
+    PDFX_CUDA(cudaStreamSynchronize(s));
+    bool any = false;
+    for (int j = 0; j < a.C; ++j) any |= h[static_cast<size_t>(j) * kPcgScalars + kPcgActive] != 0.0;
+    if (!any) break;
+    if (done >= max_iter) return PDFX_ERR_SOLVE;
+    const int32_t chunk = std::min<int32_t>(16, max_iter - done);
+    for (int32_t j = 0; j < chunk; ++j) launch_pcg_iteration(c.fem, a, s);
+    c.launches += 6 * static_cast<int64_t>(chunk);
+    done += chunk;
+  }
+  int32_t most = 0;
+  for (int j = 0; j < a.C; ++j)
+    most = std::max(most, static_cast<int32_t>(h[static_cast<size_t>(j) * kPcgScalars + kPcgIters]));
+  if (iters) *iters = most;
+  return PDFX_OK;
+}
+
+int read_flag(Ctx& c, cudaStream_t s) {
+  int flag = 0;
+  PDFX_CUDA(cudaMemcpyAsync(&flag, c.eflag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  PDFX_CUDA(cudaStreamSynchronize(s));
+  return flag ? PDFX_ERR_ARG : PDFX_OK;
+}
+
+// Eq. 12 from w.rhs, w.L and the initial guess in w.x (Dirichlet values set here).
+template <typename T>
+int wp_solve_dev(Ctx& c, const EWork& w, double tol, int32_t max_iter, int32_t* iters, cudaStream_t s) {
+  const WpConst k = wp_const(c);
+  PDFX_CUDA(cudaMemsetAsync(c.eflag, 0, sizeof(int), s));
+  launch_wp_bc<T>(static_cast<const T*>(c.fields), c.nn, k, c.fem.ncls, c.fem.nrm, c.efixed, w.x, c.eflag, s);
+  launch_assemble_wp(c.fem, w.L, w.aval, w.adiag, s);
+  launch_spmv(c.fem, c.fem.mval, 9, w.rhs, w.b, s);
+  c.launches += 4;
+  PDFX_TRY(read_flag(c, s));
+  PcgArgs a;
+  a.C = 9; a.val = w.aval; a.diag = w.adiag; a.fixed = c.efixed; a.b = w.b;
+  a.x = w.x; a.r = w.r; a.z = w.z; a.d = w.d; a.q = w.q; a.scratch = w.pcg; a.tol = tol;
+  return run_pcg(c, a, max_iter, iters, s);
+}
+
+template <typename T>
+int wp_rhs_dev(Ctx& c, const EWork& w, cudaStream_t s) {
+  PDFX_CUDA(cudaMemsetAsync(c.eflag, 0, sizeof(int), s));
+  launch_wp_rhs<T>(static_cast<const T*>(c.fields), c.nn, wp_const(c), w.rhs, w.L, c.eflag, s);
+  c.launches++;
+  return read_flag(c, s);
+}
+
+// The fields' wp_ij: right-hand side and length scale from the fields, solved from slots
+// 14-22 and written back there.
+template <typename T>
+int update_wp_dev(Ctx& c, const EWork& w, double tol, int32_t max_iter, int32_t* iters, cudaStream_t s) {
+  PDFX_TRY(wp_rhs_dev<T>(c, w, s));
+  launch_read_wp<T>(c.nn, static_cast<const T*>(c.fields), w.x, s);
+  c.launches++;
+  PDFX_TRY(wp_solve_dev<T>(c, w, tol, max_iter, iters, s));
+  launch_write_wp<T>(c.nn, w.x, static_cast<T*>(c.fields), s);
+  c.launches++;
+  return cerr(cudaGetLastError());
+}
+
+// Eq. 33 from w.src and w.flux into x (initial guess in), zero integral.
+int pressure_dev(Ctx& c, const EWork& w, double* x, double tol, int32_t max_iter, int32_t* iters,
+                 cudaStream_t s) {
+  launch_pressure_load(c.fem, w.src, w.flux, w.b, w.red, s);
+  c.launches += 4;
+  PcgArgs a;
+  a.C = 1; a.val = c.fem.kval; a.diag = c.fem.kdiag; a.fixed = nullptr; a.b = w.b;
+  a.x = x; a.r = w.r; a.z = w.z; a.d = w.d; a.q = w.q; a.scratch = w.pcg; a.tol = tol;
+  PDFX_TRY(run_pcg(c, a, max_iter, iters, s));
+  launch_zero_mean(c.fem, x, w.red, s);
+  c.launches += 3;
+  return cerr(cudaGetLastError());
+}
+
+template <typename T>
+int do_coupled_step(Ctx& c, double dt, double Cp, double tol, int32_t max_iter, int32_t* iters, cudaStream_t s) {
+  const EWork w = ework(c);
+  int32_t iw = 0, ip = 0;
+  PDFX_TRY(update_wp_dev<T>(c, w, tol, max_iter, &iw, s));
+  PDFX_TRY(do_step<T>(c, dt, s));   // prediction (Eq. 27 and the other equations), control, statistics
+  T* fields = static_cast<T*>(c.fields);
+  launch_pressure_rhs<T>(c.fem, c.ne_off, c.ne_list, c.nmom, kNS, 1, c.P, fields, c.prm.nu, dt, Cp, w.prs,
+                         w.src, w.flux, s);
+  c.launches += 7;
+  PDFX_TRY(pressure_dev(c, w, c.dP, tol, max_iter, &ip, s));
+  const ElemGeo<T>* geo = static_cast<const ElemGeo<T>*>(c.geo);
+  launch_correct_velocity<T>(geo, c.topo, c.ne, c.prm.period_x, nullptr, nullptr, c.dP, w.big,
+                             carve<T>(c.pbuf[c.cur], c.np), c.np, dt, s);
+  c.launches += 2;
+  PDFX_TRY(run_statistics<T>(c, false, false, false, s));
+  launch_add(c.nn, c.dP, c.P, s);
+  launch_derive_fields<T>(geo, c.topo, c.ne, c.prm.period_x, nullptr, nullptr, c.ne_off, c.ne_list, c.nn,
+                          c.nmom, w.big, fields, s);
+  launch_write_pgrad<T>(c.fem, c.ne_off, c.ne_list, c.P, w.big, w.big + 2 * static_cast<size_t>(c.ne),
+                        fields, s);
+  c.launches += 9;
+  drop_graph(c);
+  if (iters) { iters[0] = iw; iters[1] = ip; }
+  return cerr(cudaGetLastError());
+}
+
+// [nn][9] host <-> [9][nn] device.
+int upload_9(const double* h, double* d, int nn, cudaStream_t s) {
+  std::vector<double> t(9 * static_cast<size_t>(nn));
+  for (int n = 0; n < nn; ++n)
+    for (int j = 0; j < 9; ++j) t[static_cast<size_t>(j) * nn + n] = h[9 * static_cast<size_t>(n) + j];
+  PDFX_CUDA(cudaMemcpyAsync(d, t.data(), sizeof(double) * t.size(), cudaMemcpyHostToDevice, s));
+  return cerr(cudaStreamSynchronize(s));
+}
+int download_9(const double* d, double* h, int nn, cudaStream_t s) {
+  std::vector<double> t(9 * static_cast<size_t>(nn));
+  PDFX_CUDA(cudaMemcpyAsync(t.data(), d, sizeof(double) * t.size(), cudaMemcpyDeviceToHost, s));
+  PDFX_CUDA(cudaStreamSynchronize(s));
+  for (int n = 0; n < nn; ++n)
+    for (int j = 0; j < 9; ++j) h[9 * static_cast<size_t>(n) + j] = t[static_cast<size_t>(j) * nn + n];
+  return PDFX_OK;
+}
+int upload_n(const double* h, double* d, size_t n, cudaStream_t s) {
+  PDFX_CUDA(cudaMemcpyAsync(d, h, sizeof(double) * n, cudaMemcpyHostToDevice, s));
+  return cerr(cudaStreamSynchronize(s));
+}
+int download_n(const double* d, double* h, size_t n, cudaStream_t s) {
+  PDFX_CUDA(cudaMemcpyAsync(h, d, sizeof(double) * n, cudaMemcpyDeviceToHost, s));
+  return cerr(cudaStreamSynchronize(s));
+}
+
+// Common checks of the Eulerian entry points.
+int eulerian_ready(Ctx* c, bool need_fields) {
+  if (!c) return PDFX_ERR_ARG;
+  if (!c->have_grid || (need_fields && !c->have_fields)) return PDFX_ERR_ORDER;
+  if (c->K > 1) return PDFX_ERR_ARG;
+  return ensure_fem(*c);
+}
+
+bool solve_args_ok(double tol, int32_t max_iter) {
+  return tol > 0.0 && std::isfinite(tol) && max_iter >= 0;
 }
 
 }  // namespace
@@ -1484,6 +1849,114 @@ int64_t pdfx_kernel_launches(const void* ctx) {
   return c ? c->launches : 0;
 }
 
+int pdfx_wp_rhs(void* ctx, double* rhs, double* L, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !rhs || !L) return PDFX_ERR_ARG;
+  PDFX_TRY(eulerian_ready(c, true));
+  const cudaStream_t s = as_stream(stream);
+  const EWork w = ework(*c);
+  PDFX_TRY(c->prm.precision == 1 ? wp_rhs_dev<float>(*c, w, s) : wp_rhs_dev<double>(*c, w, s));
+  PDFX_TRY(download_9(w.rhs, rhs, c->nn, s));
+  return download_n(w.L, L, static_cast<size_t>(c->nn), s);
+}
+
+int pdfx_wp_solve(void* ctx, const double* rhs, const double* L, double* wp, double tol, int32_t max_iter,
+                  int32_t* iters, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !rhs || !L || !wp || !solve_args_ok(tol, max_iter)) return PDFX_ERR_ARG;
+  PDFX_TRY(eulerian_ready(c, true));
+  const cudaStream_t s = as_stream(stream);
+  const EWork w = ework(*c);
+  PDFX_TRY(upload_9(rhs, w.rhs, c->nn, s));
+  PDFX_TRY(upload_9(wp, w.x, c->nn, s));
+  PDFX_TRY(upload_n(L, w.L, static_cast<size_t>(c->nn), s));
+  PDFX_TRY(c->prm.precision == 1 ? wp_solve_dev<float>(*c, w, tol, max_iter, iters, s)
+                                 : wp_solve_dev<double>(*c, w, tol, max_iter, iters, s));
+  return download_9(w.x, wp, c->nn, s);
+}
+
+int pdfx_update_wp(void* ctx, double tol, int32_t max_iter, int32_t* iters, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !solve_args_ok(tol, max_iter)) return PDFX_ERR_ARG;
+  PDFX_TRY(eulerian_ready(c, true));
+  const cudaStream_t s = as_stream(stream);
+  const EWork w = ework(*c);
+  drop_graph(*c);
+  return c->prm.precision == 1 ? update_wp_dev<float>(*c, w, tol, max_iter, iters, s)
+                               : update_wp_dev<double>(*c, w, tol, max_iter, iters, s);
+}
+
+int pdfx_pressure_rhs(void* ctx, const double* ustar, const double* P, double dt, double Cp, double* src,
+                      double* flux, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !ustar || !P || !src || !flux || !(dt > 0.0) || !std::isfinite(dt) || !std::isfinite(Cp))
+    return PDFX_ERR_ARG;
+  PDFX_TRY(eulerian_ready(c, true));
+  const cudaStream_t s = as_stream(stream);
+  const EWork w = ework(*c);
+  const size_t nn = static_cast<size_t>(c->nn);
+  PDFX_TRY(upload_n(ustar, w.q, 3 * nn, s));
+  PDFX_TRY(upload_n(P, w.r, nn, s));
+  if (c->prm.precision == 1)
+    launch_pressure_rhs<float>(c->fem, c->ne_off, c->ne_list, w.q, 3, 0, w.r,
+                               static_cast<const float*>(c->fields), c->prm.nu, dt, Cp, w.prs, w.src, w.flux, s);
+  else
+    launch_pressure_rhs<double>(c->fem, c->ne_off, c->ne_list, w.q, 3, 0, w.r,
+                                static_cast<const double*>(c->fields), c->prm.nu, dt, Cp, w.prs, w.src, w.flux, s);
+  c->launches += 7;
+  PDFX_TRY(cerr(cudaGetLastError()));
+  PDFX_TRY(download_n(w.src, src, nn, s));
+  return download_n(w.flux, flux, nn, s);
+}
+
+int pdfx_pressure_solve(void* ctx, const double* src, const double* flux, double* dP, double tol,
+                        int32_t max_iter, int32_t* iters, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !src || !flux || !dP || !solve_args_ok(tol, max_iter)) return PDFX_ERR_ARG;
+  PDFX_TRY(eulerian_ready(c, false));
+  const cudaStream_t s = as_stream(stream);
+  const EWork w = ework(*c);
+  const size_t nn = static_cast<size_t>(c->nn);
+  PDFX_TRY(upload_n(src, w.src, nn, s));
+  PDFX_TRY(upload_n(flux, w.flux, nn, s));
+  PDFX_TRY(upload_n(dP, w.x, nn, s));
+  PDFX_TRY(pressure_dev(*c, w, w.x, tol, max_iter, iters, s));
+  return download_n(w.x, dP, nn, s);
+}
+
+int pdfx_set_pressure(void* ctx, const double* P, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || !P) return PDFX_ERR_ARG;
+  PDFX_TRY(eulerian_ready(c, false));
+  const cudaStream_t s = as_stream(stream);
+  PDFX_TRY(upload_n(P, c->P, static_cast<size_t>(c->nn), s));
+  PDFX_CUDA(cudaMemsetAsync(c->dP, 0, sizeof(double) * c->nn, s));
+  return cerr(cudaStreamSynchronize(s));
+}
+
+int pdfx_get_pressure(void* ctx, double* P, double* dP, void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || (!P && !dP)) return PDFX_ERR_ARG;
+  PDFX_TRY(eulerian_ready(c, false));
+  const cudaStream_t s = as_stream(stream);
+  if (P) PDFX_TRY(download_n(c->P, P, static_cast<size_t>(c->nn), s));
+  if (dP) PDFX_TRY(download_n(c->dP, dP, static_cast<size_t>(c->nn), s));
+  return PDFX_OK;
+}
+
+int pdfx_coupled_step(void* ctx, double dt, double Cp, double tol, int32_t max_iter, int32_t* iters,
+                      void* stream) {
+  Ctx* c = as_ctx(ctx);
+  if (!c || std::isnan(dt) || !std::isfinite(Cp) || !solve_args_ok(tol, max_iter)) return PDFX_ERR_ARG;
+  if (!model_fits_grid(*c)) return PDFX_ERR_ARG;
+  if (!c->pbuf[0] || !c->have_fields) return PDFX_ERR_ORDER;
+  PDFX_TRY(eulerian_ready(c, true));
+  const cudaStream_t s = as_stream(stream);
+  if (!(dt > 0.0)) PDFX_TRY(cfl_dt(*c, s, &dt));
+  return c->prm.precision == 1 ? do_coupled_step<float>(*c, dt, Cp, tol, max_iter, iters, s)
+                               : do_coupled_step<double>(*c, dt, Cp, tol, max_iter, iters, s);
+}
+
 const char* pdfx_strerror(int code) {
   switch (code) {
     case PDFX_OK: return "ok";
@@ -1495,6 +1968,7 @@ const char* pdfx_strerror(int code) {
     case PDFX_ERR_LOST_PARTICLE: return "a particle was found in no element";
     case PDFX_ERR_CAPACITY: return "an element exceeded the per-element capacity";
     case PDFX_ERR_NONFINITE: return "a particle state became non-finite";
+    case PDFX_ERR_SOLVE: return "an iterative solve did not converge within its iteration limit";
     default: return "unknown error";
   }
 }

@@ -150,6 +150,52 @@ constexpr int64_t kMaxParticles = int64_t(1) << 28;   // particle ids fit the 28
 constexpr int64_t kMaxSlots = (int64_t(1) << 31) - 1;  // particle slots of a batch (int32 lists)
 constexpr int kBigCap = 4096;       // binning capacity of the large-element kernel
 
+// Eulerian solves of the coupled loop (k_eulerian.cu), FP64.
+struct WpConst {             // constants of Eqs. 12-18 and Eq. 59
+  double C1, C2, Cv, gamma5, CL, Ceta, CT, nu;
+  double cxi;                // Eq. 17: 1 + 1.3 n_i n_i (2.3 with a no-slip wall, else 1)
+};
+// Galerkin FEM data of a grid with linear triangles (Sect. 3.2), built on the host once.
+struct FemDev {
+  int32_t nn = 0, ne = 0, nnz = 0;
+  int32_t* row = nullptr;    // [nn + 1] CSR rows: each node's neighbours and itself
+  int32_t* col = nullptr;    // [nnz] ascending within a row
+  int32_t* dpos = nullptr;   // [nn] position of each row's diagonal entry
+  int32_t* cptr = nullptr;   // [nnz + 1] element contributions of each entry
+  int32_t* clist = nullptr;  // [9 ne] 9 e + 3 a + b (local row a, column b), ascending e
+  int32_t* tri = nullptr;    // [ne][3]
+  double* fe = nullptr;      // [ne][7] dN/dx (3), dN/dy (3), area (Eq. 40, element frame)
+  double* mval = nullptr;    // [nnz] consistent mass matrix
+  double* kval = nullptr;    // [nnz] stiffness of the laplacian
+  double* kdiag = nullptr;   // [nn] its diagonal
+  double* mlump = nullptr;   // [nn] integral of each shapefunction
+  double area = 0.0;         // domain area
+  int8_t* ncls = nullptr;    // [nn] 0 interior, 1 no-slip, 2 free-slip (no-slip wins)
+  double* nrm = nullptr;     // [nn][2] outward unit normal of no-slip nodes (corner: bisector)
+  int32_t* boff = nullptr;   // [nn + 1] no-slip edges at each node
+  int32_t* bnb = nullptr;    // [.] the edge's other node
+  double* blen = nullptr;    // [.] the edge's length
+  double cxi = 1.0;
+};
+// Jacobi-PCG over C systems sharing one matrix; vectors [C][nn].
+struct PcgArgs {
+  int C = 1;
+  const double* val = nullptr;     // [nnz]
+  const double* diag = nullptr;    // [nn]
+  const uint8_t* fixed = nullptr;  // [C][nn] Dirichlet mask (NULL: none)
+  const double* b = nullptr;       // [C][nn] load
+  double* x = nullptr;             // [C][nn] initial guess (Dirichlet values set) in, solution out
+  double* r = nullptr;
+  double* z = nullptr;
+  double* d = nullptr;
+  double* q = nullptr;
+  double* scratch = nullptr;       // pcg_scratch_doubles(nn, C)
+  double tol = 0.0;
+};
+constexpr int kPcgScalars = 8;     // per component: rz, |b|, zz, alpha, beta, active, iterations
+constexpr int kPcgActive = 5;
+constexpr int kPcgIters = 6;
+
 struct Ctx {
   pdfx_params prm{};
   pdfx_allocator alloc{};
@@ -228,6 +274,18 @@ struct Ctx {
   std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> ev_pending;
   double stage_ms[kStages] = {0};
   int64_t stage_n[kStages] = {0};
+  // Eulerian solves of the coupled loop: host copies of the grid, the FEM data (built on
+  // the first Eulerian call after pdfx_set_grid) and their device work arrays
+  std::vector<int32_t> h_tri;
+  std::vector<int8_t> h_tag;
+  std::vector<double> h_vx, h_vy, h_area2;   // [ne][3] vertices unwrapped toward vertex A
+  FemDev fem;
+  bool fem_ready = false;
+  double* ew = nullptr;         // work: 7 [9][nn] vectors, rhs, L, matrix, scratch
+  uint8_t* efixed = nullptr;    // [9][nn] Dirichlet masks
+  int* eflag = nullptr;         // [1] eps <= 0 at a node
+  double* P = nullptr;          // [nn] nodal mean pressure (rho = 1)
+  double* dP = nullptr;         // [nn] last pressure increment (the next initial guess)
   // allocations to release
   std::vector<std::pair<void*, size_t>> owned;
 };
@@ -275,6 +333,38 @@ void launch_derive_fields(const ElemGeo<T>* geo, const ElemTopo* topo, int32_t n
                           const int32_t* einst, const InstDev<T>* inst, const int32_t* ne_off,
                           const int32_t* ne_list, int32_t nn, const double* nmom, double* scratch,
                           T* fields, cudaStream_t s);
+
+// Eulerian solves of the coupled loop (k_eulerian.cu): launchers.
+int pcg_blocks(int nn);
+size_t pcg_scratch_doubles(int nn, int C);
+const double* pcg_scalars(const PcgArgs& a, int nn);   // [C][kPcgScalars], device
+template <typename T>
+void launch_wp_rhs(const T* fields, int nn, const WpConst& k, double* rhs, double* L, int* err, cudaStream_t s);
+template <typename T>
+void launch_read_wp(int nn, const T* fields, double* x, cudaStream_t s);
+template <typename T>
+void launch_wp_bc(const T* fields, int nn, const WpConst& k, const int8_t* ncls, const double* nrm,
+                  uint8_t* fixed, double* x, int* err, cudaStream_t s);
+void launch_assemble_wp(const FemDev& m, const double* L, double* aval, double* adiag, cudaStream_t s);
+void launch_spmv(const FemDev& m, const double* val, int C, const double* x, double* y, cudaStream_t s);
+void launch_pcg_setup(const FemDev& m, const PcgArgs& a, cudaStream_t s);
+void launch_pcg_iteration(const FemDev& m, const PcgArgs& a, cudaStream_t s);
+void launch_node_gradients(const FemDev& m, const int32_t* ne_off, const int32_t* ne_list, int nq,
+                           const double* q, double* eg, double* gn, cudaStream_t s);
+size_t pressure_rhs_scratch_doubles(int nn, int ne);
+template <typename T>
+void launch_pressure_rhs(const FemDev& m, const int32_t* ne_off, const int32_t* ne_list, const double* ustar,
+                         int ustride, int uoff, const double* P, const T* fields, double nu, double dt,
+                         double Cp, double* work, double* src, double* flux, cudaStream_t s);
+void launch_pressure_load(const FemDev& m, const double* src, const double* flux, double* b, double* red,
+                          cudaStream_t s);
+void launch_zero_mean(const FemDev& m, double* x, double* red, cudaStream_t s);
+template <typename T>
+void launch_write_wp(int nn, const double* x, T* fields, cudaStream_t s);
+template <typename T>
+void launch_write_pgrad(const FemDev& m, const int32_t* ne_off, const int32_t* ne_list, const double* P,
+                        double* eg, double* gp, T* fields, cudaStream_t s);
+void launch_add(int nn, const double* a, double* b, cudaStream_t s);
 
 // Accumulators of the scalar statistics of n probe elements over nb psi bins (fixed-point
 // sums in two's complement; lo and hi hold order-preserving images of doubles).

@@ -65,3 +65,21 @@ def test_host_only_argument_checks(lib):
     assert L.pdfx_get_fields(None, None, None) == ERR_ARG
     assert L.pdfx_correct_velocity(None, None, 1e-3, None) == ERR_ARG
     assert L.pdfx_scalar_stats(None, 1, None, 10, None, None, None, None, None, 0, None) == ERR_ARG
+
+
+def test_host_only_argument_checks_of_the_eulerian_calls(lib):
+    """The coupled loop's entry points refuse a null context, null arrays or a bad
+    tolerance before touching the device; the new error code has its own message."""
+    from paper_1006_0532_gb300 import _binding as B
+    ERR_ARG = -1
+    L = B.lib()
+    it = ctypes.c_int32()
+    assert L.pdfx_wp_rhs(None, None, None, None) == ERR_ARG
+    assert L.pdfx_wp_solve(None, None, None, None, 1e-10, 10, ctypes.byref(it), None) == ERR_ARG
+    assert L.pdfx_update_wp(None, 1e-10, 10, ctypes.byref(it), None) == ERR_ARG
+    assert L.pdfx_pressure_rhs(None, None, None, 1e-3, 1e-3, None, None, None) == ERR_ARG
+    assert L.pdfx_pressure_solve(None, None, None, None, 1e-10, 10, ctypes.byref(it), None) == ERR_ARG
+    assert L.pdfx_set_pressure(None, None, None) == ERR_ARG
+    assert L.pdfx_get_pressure(None, None, None, None) == ERR_ARG
+    assert L.pdfx_coupled_step(None, 1e-3, 1e-3, 1e-10, 10, None, None) == ERR_ARG
+    assert L.pdfx_strerror(-9) == b"an iterative solve did not converge within its iteration limit"
