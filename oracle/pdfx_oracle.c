@@ -1629,7 +1629,8 @@ static double dot_free(const double *a, const double *b, const int8_t *fixed, in
  * no-slip condition.  rhs[nn][9], L[nn]; wp[nn][9] holds the initial guess on entry and the
  * solution on exit.  Each component iterates until the preconditioned residual's
  * 2-norm over the free nodes is at most tol times that of its reduced load (the load minus
- * the Dirichlet columns); *iters returns the largest count.  Fails (-2) if a component
+ * the Dirichlet columns), a zero reduced load giving the zero solution on the free nodes
+ * at once; *iters returns the largest count.  Fails (-2) if a component
  * needs more than max_iter iterations, (-1) if an eps needed at a wall is not positive. */
 int orc_wp_solve(const orc_ctx *c, const double *rhs, const double *L, double *wp, double tol,
                  int max_iter, int *iters)
@@ -1672,6 +1673,9 @@ int orc_wp_solve(const orc_ctx *c, const double *rhs, const double *L, double *w
         for (int n = 0; n < nn; ++n) q[n] = bl[n] - q[n];
         for (int n = 0; n < nn; ++n) z[n] = fixed[n] ? 0.0 : q[n] / dg[n];
         const double bnorm = sqrt(dot_free(z, z, fixed, nn));
+        if (bnorm == 0.0)   /* a zero reduced load: the free nodes' solution is zero */
+            for (int n = 0; n < nn; ++n)
+                if (!fixed[n]) x[n] = 0.0;
         /* r = bl - A x on the free nodes */
         wp_operator(c, L, x, q, NULL);
         for (int n = 0; n < nn; ++n) r[n] = fixed[n] ? 0.0 : bl[n] - q[n];
@@ -1848,9 +1852,11 @@ int orc_pressure_solve(const orc_ctx *c, const double *src, const double *flux, 
     mean /= nn;
     for (int n = 0; n < nn; ++n) b[n] -= mean;
     stiffness_apply(c, dP, q, dg);
-    for (int n = 0; n < nn; ++n) r[n] = b[n] - q[n];
     for (int n = 0; n < nn; ++n) z[n] = b[n] / dg[n];
     const double bnorm = sqrt(dot_free(z, z, none, nn));
+    if (bnorm == 0.0)   /* a zero load: the solution is zero */
+        for (int n = 0; n < nn; ++n) { dP[n] = 0.0; q[n] = 0.0; }
+    for (int n = 0; n < nn; ++n) r[n] = b[n] - q[n];
     for (int n = 0; n < nn; ++n) { z[n] = r[n] / dg[n]; d[n] = z[n]; }
     double rz = dot_free(r, z, none, nn);
     int it = 0;

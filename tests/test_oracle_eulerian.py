@@ -566,3 +566,16 @@ def test_coupled_steps_stay_bounded(name):
     assert d["lost"] == 0 and d["walk_brute"] == 0
     assert max(peak[1:]) < 2.0 * peak[0]
     assert np.isfinite(P).all()
+
+
+def test_solves_with_a_zero_load_return_zero_at_once():
+    """A zero right-hand side with zero boundary values has the zero solution; both solves
+    return it from any initial guess without iterating (a stopping rule relative to a zero
+    load could never be met)."""
+    g = _freeslip_grid(8, 9, seed=2)
+    o = oracle.Oracle(g, base_params(period_x=g.period_x), synth.uniform_fields(g.nn))
+    rng = np.random.default_rng(10)
+    wp, it = o.wp_solve(np.zeros((g.nn, 3, 3)), np.full(g.nn, 0.2), rng.normal(size=(g.nn, 3, 3)))
+    assert it == 0 and np.abs(wp).max() == 0.0
+    dP, it = o.pressure_solve(np.zeros(g.nn), np.zeros(g.nn), rng.normal(size=g.nn))
+    assert it == 0 and np.abs(dP).max() == 0.0
