@@ -358,7 +358,8 @@ int  pdfx_element_stats_noalloc(void *ctx, int64_t np, const double *u, const do
  * consistent mass matrix and the laplacian stiffness, from Eq. 40's derivatives.  It also
  * classifies the nodes: a node on a no-slip edge (tag 1), with its outward unit normal
  * (the normalised sum of its wall edges' normals), else a node on a free-slip edge (tag
- * 2), else interior.  The linear systems are solved by conjugate gradients with the
+ * 2), else interior; a node that belongs to no element gives PDFX_ERR_MESH.  The linear
+ * systems are solved by conjugate gradients with the
  * Jacobi preconditioner, started from the given initial guess.  Each system iterates
  * until the 2-norm of its preconditioned residual over the free nodes is at most tol
  * times that of its preconditioned reduced load (the load minus the Dirichlet columns;

@@ -1021,6 +1021,7 @@ int ensure_fem(Ctx& c) {
       for (int b = 0; b < 3; ++b) adj[tri[3 * e + a]].push_back(tri[3 * e + b]);
   std::vector<int32_t> row(static_cast<size_t>(nn) + 1, 0), col;
   for (int n = 0; n < nn; ++n) {
+    if (adj[n].empty()) return PDFX_ERR_MESH;   // a node of no element has no equation
     std::sort(adj[n].begin(), adj[n].end());
     adj[n].erase(std::unique(adj[n].begin(), adj[n].end()), adj[n].end());
     row[n + 1] = row[n] + static_cast<int32_t>(adj[n].size());
