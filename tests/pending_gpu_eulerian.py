@@ -188,3 +188,25 @@ def test_coupled_steps_fp32_stay_bounded(channel):
         assert np.isfinite(st[k]).all()
     assert max(peaks[1:]) < 2.0 * peaks[0]
     assert c.check() == 0
+
+
+def test_canyon_solves_match_oracle():
+    """The street canyon: walls with re-entrant and convex corners (bisector normals in Eq.
+    59), a free-slip top and the periodic seam, for both solves."""
+    w = synth.canyon_workload("canyon_2k")
+    g = w["grid"]
+    o, c = both(g, w["params"], w["fields"])
+    rhs, L = o.wp_rhs()
+    rg, Lg = c.wp_rhs()
+    assert rel(rg, rhs) < 1e-13 and rel(Lg, L) < 1e-13
+    wo, _ = o.wp_solve(rhs, L, tol=1e-13)
+    wg, _ = c.wp_solve(rhs, L, tol=1e-13)
+    assert rel(wg, wo) < 1e-9
+    rng = np.random.default_rng(6)
+    ustar, P = rng.normal(size=(g.nn, 3)), rng.normal(size=g.nn)
+    so, fo = o.pressure_rhs(ustar, P, 1e-4, 5e-5)
+    sg, fg = c.pressure_rhs(ustar, P, 1e-4, 5e-5)
+    assert rel(sg, so) < 1e-12 and rel(fg, fo) < 1e-12
+    do, _ = o.pressure_solve(so, fo, tol=1e-13)
+    dg, _ = c.pressure_solve(so, fo, tol=1e-13)
+    assert rel(dg, do) < 1e-8
