@@ -12,8 +12,10 @@
  * Appendix B), and recomputes the element and nodal statistics (Sect. 3.3, Eqs. 34-36)
  * and the velocity-conditioned scalar means used by the next step (Sect. 3.5, Appendix A,
  * or Fox's projection, Eqs. 64-66).  Also: batches of independent grids stepped together,
- * the simplified model of the particle-redistribution test (Eqs. 46-47), and scalar
- * post-processing of probe elements (Eqs. 67-69).
+ * the simplified model of the particle-redistribution test (Eqs. 46-47), scalar
+ * post-processing of probe elements (Eqs. 67-69), and the Eulerian solves of the coupled
+ * loop (elliptic relaxation, Eqs. 12-18 and 59; pressure projection, Eqs. 33 and 61; one
+ * coupled step in the order of Table 1).
  *
  * Conventions for every call:
  *  - Return value: PDFX_OK (0) or a negative PDFX_ERR_* code.  No exception crosses this
