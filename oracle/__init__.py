@@ -134,6 +134,7 @@ def lib():
             L.orc_wp_rhs.argtypes = [C.c_void_p, dp, dp]
             L.orc_wp_solve.argtypes = [C.c_void_p, dp, dp, dp, C.c_double, C.c_int, ip]
             L.orc_update_wp.argtypes = [C.c_void_p, C.c_double, C.c_int, ip]
+            L.orc_fem_apply.argtypes = [C.c_void_p, C.c_int, dp, dp]
             L.orc_pressure_rhs.argtypes = [C.c_void_p, dp, dp, C.c_double, C.c_double, dp, dp]
             L.orc_pressure_solve.argtypes = [C.c_void_p, dp, dp, dp, C.c_double, C.c_int, ip]
             L.orc_coupled_step.argtypes = [C.c_void_p, C.c_double, C.c_double, dp, dp, C.c_double,
@@ -374,6 +375,13 @@ class Oracle:
         if rc:
             raise RuntimeError("orc_update_wp failed: %d" % rc)
         return it.value
+
+    def fem_apply(self, which: int, x):
+        """The Galerkin mass (which = 0) or laplacian stiffness (1) applied to x[nn]."""
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.zeros(self.nn)
+        lib().orc_fem_apply(self.h, int(which), _dp(xx), _dp(y))
+        return y
 
     def pressure_rhs(self, ustar, P, dt: float, Cp: float = 1e-3):
         """Eq. 33's nodal right-hand side and Eq. 61's increment flux: (src[nn], flux[nn])."""

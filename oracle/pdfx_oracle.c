@@ -1612,6 +1612,15 @@ static void mass_apply(const orc_ctx *c, const double *x, double *y)
     }
 }
 
+/* The Galerkin operators as plain functions (test access): which = 0 the consistent mass
+ * matrix, 1 the laplacian stiffness. */
+static void stiffness_apply(const orc_ctx *c, const double *x, double *y, double *diag);
+void orc_fem_apply(const orc_ctx *c, int which, const double *x, double *y)
+{
+    if (which == 0) mass_apply(c, x, y);
+    else stiffness_apply(c, x, y, NULL);
+}
+
 static double dot_free(const double *a, const double *b, const int8_t *fixed, int n)
 {
     double s = 0.0;

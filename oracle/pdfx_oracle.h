@@ -120,6 +120,8 @@ int  orc_pressure_rhs(const orc_ctx *c, const double *ustar, const double *P, do
 /* Eq. 33 by Galerkin FEM and Jacobi-PCG; dP[nn]: initial guess in, zero-mean solution out. */
 int  orc_pressure_solve(const orc_ctx *c, const double *src, const double *flux, double *dP,
                         double tol, int max_iter, int *iters);
+/* y = M x (which = 0, consistent mass matrix) or K x (which = 1, laplacian stiffness). */
+void orc_fem_apply(const orc_ctx *c, int which, const double *x, double *y);
 /* One step of the coupled loop in Table 1's order (see pdfx_oracle.c). */
 int  orc_coupled_step(orc_ctx *c, double dt, double Cp, double *P, double *dP, double tol,
                       int max_iter, int *wp_iters, int *p_iters);

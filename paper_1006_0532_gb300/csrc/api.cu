@@ -5,6 +5,7 @@
 #include <new>
 #include <vector>
 
+#include "fem_host.h"
 #include "pdfx_internal.h"
 
 namespace pdfx {
@@ -995,142 +996,36 @@ EWork ework(Ctx& c) {
 int ensure_fem(Ctx& c) {
   if (c.fem_ready) return PDFX_OK;
   if (!c.have_grid || c.K > 1) return PDFX_ERR_ARG;
-  const int nn = c.nn, ne = c.ne;
-  const std::vector<int32_t>& tri = c.h_tri;
+  FemHost h;
+  if (!build_fem_host(c.nn, c.ne, c.h_tri, c.h_tag, c.h_vx, c.h_vy, c.h_area2, h)) return PDFX_ERR_MESH;
   FemDev& m = c.fem;
-  // element data: Eq. 40's derivatives in the element's frame, and the area
-  std::vector<double> fe(7 * static_cast<size_t>(ne)), mlump(static_cast<size_t>(nn), 0.0);
-  double area = 0.0;
-  for (int e = 0; e < ne; ++e) {
-    const double* vx = &c.h_vx[3 * static_cast<size_t>(e)];
-    const double* vy = &c.h_vy[3 * static_cast<size_t>(e)];
-    const double xBA = vx[1] - vx[0], yBA = vy[1] - vy[0];
-    const double xCA = vx[2] - vx[0], yCA = vy[2] - vy[0];
-    const double a2 = c.h_area2[e], inv = 1.0 / a2;
-    double* g = &fe[7 * static_cast<size_t>(e)];
-    g[0] = (-yCA + yBA) * inv; g[1] = yCA * inv; g[2] = -yBA * inv;
-    g[3] = (xCA - xBA) * inv;  g[4] = -xCA * inv; g[5] = xBA * inv;
-    g[6] = 0.5 * a2;
-    area += g[6];
-    for (int a = 0; a < 3; ++a) mlump[tri[3 * e + a]] += g[6] / 3.0;
-  }
-  // CSR pattern of the node graph (each node with its neighbours and itself)
-  std::vector<std::vector<int32_t>> adj(static_cast<size_t>(nn));
-  for (int e = 0; e < ne; ++e)
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) adj[tri[3 * e + a]].push_back(tri[3 * e + b]);
-  std::vector<int32_t> row(static_cast<size_t>(nn) + 1, 0), col;
-  for (int n = 0; n < nn; ++n) {
-    if (adj[n].empty()) return PDFX_ERR_MESH;   // a node of no element has no equation
-    std::sort(adj[n].begin(), adj[n].end());
-    adj[n].erase(std::unique(adj[n].begin(), adj[n].end()), adj[n].end());
-    row[n + 1] = row[n] + static_cast<int32_t>(adj[n].size());
-  }
-  const int nnz = row[nn];
-  col.reserve(static_cast<size_t>(nnz));
-  for (int n = 0; n < nn; ++n) col.insert(col.end(), adj[n].begin(), adj[n].end());
-  auto entry = [&](int r, int cc) {
-    return static_cast<int32_t>(std::lower_bound(col.begin() + row[r], col.begin() + row[r + 1], cc) - col.begin());
-  };
-  std::vector<int32_t> dpos(static_cast<size_t>(nn));
-  for (int n = 0; n < nn; ++n) dpos[n] = entry(n, n);
-  // contributions of each entry, ascending element
-  std::vector<int32_t> cptr(static_cast<size_t>(nnz) + 1, 0), clist(9 * static_cast<size_t>(ne));
-  std::vector<int32_t> epos(9 * static_cast<size_t>(ne));
-  for (int e = 0; e < ne; ++e)
-    for (int a = 0; a < 3; ++a)
-      for (int b = 0; b < 3; ++b) {
-        const int32_t k = entry(tri[3 * e + a], tri[3 * e + b]);
-        epos[9 * static_cast<size_t>(e) + 3 * a + b] = k;
-        cptr[k + 1]++;
-      }
-  for (int k = 0; k < nnz; ++k) cptr[k + 1] += cptr[k];
-  {
-    std::vector<int32_t> fill(cptr.begin(), cptr.end() - 1);
-    for (int e = 0; e < ne; ++e)
-      for (int ab = 0; ab < 9; ++ab) clist[fill[epos[9 * static_cast<size_t>(e) + ab]]++] = 9 * e + ab;
-  }
-  // the fixed matrices: consistent mass and laplacian stiffness
-  std::vector<double> mval(static_cast<size_t>(nnz), 0.0), kval(static_cast<size_t>(nnz), 0.0);
-  for (int k = 0; k < nnz; ++k)
-    for (int j = cptr[k]; j < cptr[k + 1]; ++j) {
-      const int e = clist[j] / 9, a = (clist[j] % 9) / 3, b = clist[j] % 3;
-      const double* g = &fe[7 * static_cast<size_t>(e)];
-      mval[k] += g[6] / 12.0 * (a == b ? 2.0 : 1.0);
-      kval[k] += g[6] * (g[a] * g[b] + g[3 + a] * g[3 + b]);
-    }
-  std::vector<double> kdiag(static_cast<size_t>(nn));
-  for (int n = 0; n < nn; ++n) kdiag[n] = kval[dpos[n]];
-  // boundary classes, outward normals of no-slip nodes, no-slip edges at each node
-  std::vector<int8_t> cls(static_cast<size_t>(nn), 0);
-  std::vector<double> nrm(2 * static_cast<size_t>(nn), 0.0);
-  std::vector<std::vector<std::pair<int32_t, double>>> bed(static_cast<size_t>(nn));
-  bool wall = false;
-  for (int e = 0; e < ne; ++e) {
-    const double* vx = &c.h_vx[3 * static_cast<size_t>(e)];
-    const double* vy = &c.h_vy[3 * static_cast<size_t>(e)];
-    for (int k = 0; k < 3; ++k) {
-      const int t = c.h_tag[3 * static_cast<size_t>(e) + k];
-      if (t != 1 && t != 2) continue;
-      const int ia = (k + 1) % 3, ib = (k + 2) % 3;
-      const int32_t na = tri[3 * e + ia], nb = tri[3 * e + ib];
-      const double tx = vx[ib] - vx[ia], ty = vy[ib] - vy[ia];
-      const double len = std::sqrt(tx * tx + ty * ty);
-      double mx = -ty / len, my = tx / len;   // toward vertex k: into the domain
-      if ((vx[k] - vx[ia]) * mx + (vy[k] - vy[ia]) * my < 0.0) { mx = -mx; my = -my; }
-      for (const int32_t n : {na, nb}) {
-        if (t == 1) {
-          cls[n] = 1;
-          nrm[2 * static_cast<size_t>(n)] -= mx;
-          nrm[2 * static_cast<size_t>(n) + 1] -= my;
-        } else if (cls[n] == 0) {
-          cls[n] = 2;
-        }
-      }
-      if (t == 1) {
-        wall = true;
-        bed[na].push_back({nb, len});
-        bed[nb].push_back({na, len});
-      }
-    }
-  }
-  for (int n = 0; n < nn; ++n) {
-    if (cls[n] != 1) continue;
-    const double l = std::hypot(nrm[2 * static_cast<size_t>(n)], nrm[2 * static_cast<size_t>(n) + 1]);
-    if (l > 0.0) { nrm[2 * static_cast<size_t>(n)] /= l; nrm[2 * static_cast<size_t>(n) + 1] /= l; }
-  }
-  std::vector<int32_t> boff(static_cast<size_t>(nn) + 1, 0), bnb;
-  std::vector<double> blen;
-  for (int n = 0; n < nn; ++n) {
-    for (const auto& pr : bed[n]) { bnb.push_back(pr.first); blen.push_back(pr.second); }
-    boff[n + 1] = static_cast<int32_t>(bnb.size());
-  }
-  m.nn = nn;
-  m.ne = ne;
-  m.nnz = nnz;
-  m.area = area;
-  m.cxi = 1.0 + 1.3 * (wall ? 1.0 : 0.0);   // Eq. 17 with n_i n_i of a unit normal
-  PDFX_TRY(upload_vec(c, m.row, row));
-  PDFX_TRY(upload_vec(c, m.col, col));
-  PDFX_TRY(upload_vec(c, m.dpos, dpos));
-  PDFX_TRY(upload_vec(c, m.cptr, cptr));
-  PDFX_TRY(upload_vec(c, m.clist, clist));
-  PDFX_TRY(upload_vec(c, m.tri, tri));
-  PDFX_TRY(upload_vec(c, m.fe, fe));
-  PDFX_TRY(upload_vec(c, m.mval, mval));
-  PDFX_TRY(upload_vec(c, m.kval, kval));
-  PDFX_TRY(upload_vec(c, m.kdiag, kdiag));
-  PDFX_TRY(upload_vec(c, m.mlump, mlump));
-  PDFX_TRY(upload_vec(c, m.ncls, cls));
-  PDFX_TRY(upload_vec(c, m.nrm, nrm));
-  PDFX_TRY(upload_vec(c, m.boff, boff));
-  PDFX_TRY(upload_vec(c, m.bnb, bnb));
-  PDFX_TRY(upload_vec(c, m.blen, blen));
+  m.nn = c.nn;
+  m.ne = c.ne;
+  m.nnz = h.row[c.nn];
+  m.area = h.area;
+  m.cxi = h.cxi;
+  const size_t nn = static_cast<size_t>(c.nn);
+  PDFX_TRY(upload_vec(c, m.row, h.row));
+  PDFX_TRY(upload_vec(c, m.col, h.col));
+  PDFX_TRY(upload_vec(c, m.dpos, h.dpos));
+  PDFX_TRY(upload_vec(c, m.cptr, h.cptr));
+  PDFX_TRY(upload_vec(c, m.clist, h.clist));
+  PDFX_TRY(upload_vec(c, m.tri, c.h_tri));
+  PDFX_TRY(upload_vec(c, m.fe, h.fe));
+  PDFX_TRY(upload_vec(c, m.mval, h.mval));
+  PDFX_TRY(upload_vec(c, m.kval, h.kval));
+  PDFX_TRY(upload_vec(c, m.kdiag, h.kdiag));
+  PDFX_TRY(upload_vec(c, m.mlump, h.mlump));
+  PDFX_TRY(upload_vec(c, m.ncls, h.cls));
+  PDFX_TRY(upload_vec(c, m.nrm, h.nrm));
+  PDFX_TRY(upload_vec(c, m.boff, h.boff));
+  PDFX_TRY(upload_vec(c, m.bnb, h.bnb));
+  PDFX_TRY(upload_vec(c, m.blen, h.blen));
   PDFX_TRY(alloc_into(c, c.ew, ework_doubles(c)));
-  PDFX_TRY(alloc_into(c, c.efixed, 9 * static_cast<size_t>(nn)));
+  PDFX_TRY(alloc_into(c, c.efixed, 9 * nn));
   PDFX_TRY(alloc_into(c, c.eflag, 1));
-  PDFX_TRY(alloc_into(c, c.P, static_cast<size_t>(nn)));
-  PDFX_TRY(alloc_into(c, c.dP, static_cast<size_t>(nn)));
+  PDFX_TRY(alloc_into(c, c.P, nn));
+  PDFX_TRY(alloc_into(c, c.dP, nn));
   PDFX_CUDA(cudaMemset(c.P, 0, sizeof(double) * nn));
   PDFX_CUDA(cudaMemset(c.dP, 0, sizeof(double) * nn));
   c.fem_ready = true;
