@@ -311,6 +311,40 @@ def redistribution_study(torch, B, synth, args):
     return out
 
 
+def coupled_form(torch, B, w, args):
+    """The full coupled step of Table 1 (CG solves included) on the same workload, FP32 state
+    with FP64 solves: C_p = dt/2 (Eq. 33 is stable only for C_p < 2 dt), solver tolerance
+    1e-6 relative to the load.  Device time of K coupled steps after W, CUDA events on the
+    library's stream; the solves read their convergence flags on the host every 16
+    iterations, so the time includes those round trips."""
+    c = make_ctx(B, w, 1, 0, args.sort_every)
+    dt, Cp, tol = w["dt"], 0.5 * w["dt"], 1e-6
+    for _ in range(args.warmup):
+        c.coupled_step(dt, Cp=Cp, tol=tol)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    iters = []
+    steps = args.coupled_steps
+    ev0.record(stream)
+    for _ in range(steps):
+        iters.append(c.coupled_step(dt, Cp=Cp, tol=tol))
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    ms = ev0.elapsed_time(ev1) / steps
+    np_ = c.np_
+    err = c.check()
+    c.close()
+    return {"what": "full coupled step (Table 1: elliptic relaxation, particle step, pressure "
+                    "projection, Eq. 31 correction, statistics), FP32 state, FP64 CG solves",
+            "ms_per_step": ms, "value": np_ / (ms * 1e-3), "unit": UNIT, "steps": steps,
+            "Cp": Cp, "tol": tol,
+            "wp_iterations": [int(a) for a, _ in iters],
+            "pressure_iterations": [int(b) for _, b in iters],
+            "device_errors": err}
+
+
 def scalar_post(torch, c, w):
     """Scalar post-processing of Sect. 4.1.2 (Eqs. 67-69) through the C ABI with host
     outputs: the wall time of one call for 64 probe elements at 200 psi bins (the paper's
@@ -478,6 +512,9 @@ def main():
     ap.add_argument("--no-fox", action="store_true")
     ap.add_argument("--no-redist", action="store_true")
     ap.add_argument("--no-sweep", action="store_true")
+    ap.add_argument("--coupled", action="store_true",
+                    help="also time the full coupled step (its kernels await a first GPU run)")
+    ap.add_argument("--coupled-steps", type=int, default=5)
     ap.add_argument("--batch-instances", type=int, default=64)
     ap.add_argument("--batch-steps", type=int, default=16)
     ap.add_argument("--ppe", type=int, default=None,
@@ -538,6 +575,9 @@ def main():
     rc = None
     if not args.no_canyon:
         rc = canyon_form(torch, B, synth, args)
+    rcs = None
+    if args.coupled and rank == 0:
+        rcs = coupled_form(torch, B, w, args)
     e2e_s = max_over_ranks(torch, dist, e2e_s)
     if rank != 0:
         if dist is not None:
@@ -630,6 +670,9 @@ def main():
                            "binning_ms_per_step": stage["statistics_binning"]}}
     if rr is not None:
         line["redistribution_error"] = rr
+    line["coupled_step"] = rcs if rcs is not None else {
+        "unavailable": "not timed by default: the coupled loop's kernels have not yet had their "
+                       "first GPU run and parity check (--coupled times them)"}
     if rs is not None:
         line["scalar_statistics"] = rs
     if rf is not None:
