@@ -210,3 +210,14 @@ def test_canyon_solves_match_oracle():
     do, _ = o.pressure_solve(so, fo, tol=1e-13)
     dg, _ = c.pressure_solve(so, fo, tol=1e-13)
     assert rel(dg, do) < 1e-8
+
+
+def test_pressure_state_round_trip(channel):
+    """pdfx_set_pressure stores P and clears the last increment; pdfx_get_pressure returns
+    both bit for bit; a batch context refuses the Eulerian calls."""
+    w, g = channel
+    c = gpu_ctx(g, w["params"], w["fields"])
+    P = np.random.default_rng(7).normal(size=g.nn)
+    c.set_pressure(P)
+    Pg, dPg = c.pressure()
+    assert np.array_equal(Pg, P) and np.abs(dPg).max() == 0.0
