@@ -214,7 +214,7 @@ def test_canyon_solves_match_oracle():
 
 def test_pressure_state_round_trip(channel):
     """pdfx_set_pressure stores P and clears the last increment; pdfx_get_pressure returns
-    both bit for bit; a batch context refuses the Eulerian calls."""
+    both bit for bit."""
     w, g = channel
     c = gpu_ctx(g, w["params"], w["fields"])
     P = np.random.default_rng(7).normal(size=g.nn)
