@@ -135,6 +135,7 @@ def lib():
             L.orc_wp_solve.argtypes = [C.c_void_p, dp, dp, dp, C.c_double, C.c_int, ip]
             L.orc_update_wp.argtypes = [C.c_void_p, C.c_double, C.c_int, ip]
             L.orc_fem_apply.argtypes = [C.c_void_p, C.c_int, dp, dp]
+            L.orc_wp_apply.argtypes = [C.c_void_p, dp, dp, dp]
             L.orc_pressure_rhs.argtypes = [C.c_void_p, dp, dp, C.c_double, C.c_double, dp, dp]
             L.orc_pressure_solve.argtypes = [C.c_void_p, dp, dp, dp, C.c_double, C.c_int, ip]
             L.orc_coupled_step.argtypes = [C.c_void_p, C.c_double, C.c_double, dp, dp, C.c_double,
@@ -381,6 +382,14 @@ class Oracle:
         xx = np.ascontiguousarray(x, dtype=np.float64)
         y = np.zeros(self.nn)
         lib().orc_fem_apply(self.h, int(which), _dp(xx), _dp(y))
+        return y
+
+    def wp_apply(self, L, x):
+        """Eq. 12's Galerkin operator (M + K_L) applied to x[nn] with the length scale L[nn]."""
+        LL = np.ascontiguousarray(L, dtype=np.float64)
+        xx = np.ascontiguousarray(x, dtype=np.float64)
+        y = np.zeros(self.nn)
+        lib().orc_wp_apply(self.h, _dp(LL), _dp(xx), _dp(y))
         return y
 
     def pressure_rhs(self, ustar, P, dt: float, Cp: float = 1e-3):

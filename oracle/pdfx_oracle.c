@@ -1621,6 +1621,12 @@ void orc_fem_apply(const orc_ctx *c, int which, const double *x, double *y)
     else stiffness_apply(c, x, y, NULL);
 }
 
+/* y = (M + K_L) x, Eq. 12's Galerkin operator with the nodal length scale L (test access). */
+void orc_wp_apply(const orc_ctx *c, const double *L, const double *x, double *y)
+{
+    wp_operator(c, L, x, y, NULL);
+}
+
 static double dot_free(const double *a, const double *b, const int8_t *fixed, int n)
 {
     double s = 0.0;

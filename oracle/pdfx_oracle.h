@@ -122,6 +122,8 @@ int  orc_pressure_solve(const orc_ctx *c, const double *src, const double *flux,
                         double tol, int max_iter, int *iters);
 /* y = M x (which = 0, consistent mass matrix) or K x (which = 1, laplacian stiffness). */
 void orc_fem_apply(const orc_ctx *c, int which, const double *x, double *y);
+/* y = (M + K_L) x, Eq. 12's Galerkin operator with the nodal length scale L[nn]. */
+void orc_wp_apply(const orc_ctx *c, const double *L, const double *x, double *y);
 /* One step of the coupled loop in Table 1's order (see pdfx_oracle.c). */
 int  orc_coupled_step(orc_ctx *c, double dt, double Cp, double *P, double *dP, double tol,
                       int max_iter, int *wp_iters, int *p_iters);

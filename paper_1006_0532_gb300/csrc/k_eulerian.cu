@@ -1,4 +1,6 @@
-// Eulerian solves of the coupled loop (Sect. 3.2), FP64 throughout.
+// Eulerian solves of the coupled loop (Sect. 3.2), FP64 throughout.  The per-node and
+// per-element arithmetic lives in eulerian_ops.h; these kernels map threads onto it and
+// carry the reductions.
 //
 // * The local right-hand side of the elliptic relaxation and its length scale (Eqs. 12-18),
 //   one thread per node.  H_ijkl of Eq. 13 is applied in contracted form:
@@ -43,51 +45,8 @@ __global__ void wp_rhs_kernel(const T* __restrict__ f, int nn, WpConst k, double
                               double* __restrict__ L, int* __restrict__ err) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nn) return;
-  const T* q = f + static_cast<size_t>(n) * kNF;
-  double R[3][3];
-  R[0][0] = q[23]; R[1][1] = q[24]; R[2][2] = q[25];
-  R[0][1] = R[1][0] = q[26];
-  R[0][2] = R[2][0] = q[27];
-  R[1][2] = R[2][1] = q[28];
-  double G[3][3];
-  for (int i = 0; i < 3; ++i) {
-    G[i][0] = q[5 + 2 * i];
-    G[i][1] = q[6 + 2 * i];
-    G[i][2] = 0.0;
-  }
-  const double om = q[29];
-  const double tr = R[0][0] + R[1][1] + R[2][2];
-  const double kk = 0.5 * tr;
-  double b[3][3];
-  for (int i = 0; i < 3; ++i)
-    for (int j = 0; j < 3; ++j) b[i][j] = tr > 0.0 ? R[i][j] / tr - (i == j ? 1.0 / 3.0 : 0.0) : 0.0;
-  const double det = R[0][0] * (R[1][1] * R[2][2] - R[1][2] * R[2][1]) -
-                     R[0][1] * (R[1][0] * R[2][2] - R[1][2] * R[2][0]) +
-                     R[0][2] * (R[1][0] * R[2][1] - R[1][1] * R[2][0]);
-  const double k23 = 2.0 * kk / 3.0;
-  const double Av = kk > 0.0 ? fmin(1.0, k.Cv * det / (k23 * k23 * k23)) : 0.0;
-  const double c1 = k.C2 * Av + k.gamma5 / 3.0, c2 = k.gamma5 / 3.0;
-  for (int i = 0; i < 3; ++i) {
-    for (int j = 0; j < 3; ++j) {
-      double bG = 0.0, bGt = 0.0;
-      for (int m = 0; m < 3; ++m) {
-        bG += b[i][m] * G[m][j];
-        bGt += b[i][m] * G[j][m];
-      }
-      const double h = c1 * G[i][j] - c2 * G[j][i] + k.gamma5 * (bG - bGt);
-      rhs[static_cast<size_t>(3 * i + j) * nn + n] =
-          (i == j ? 0.5 * (1.0 - k.C1) * kk * om : 0.0) + kk * h;
-    }
-  }
-  const double eps = om * (kk + k.nu * k.CT * k.CT * om);   // Eq. 18
-  if (!(eps > 0.0)) {
+  if (!eops::wp_rhs_node(f + static_cast<size_t>(n) * kNF, k, rhs + n, static_cast<size_t>(nn), L + n))
     atomicExch(err, 1);
-    L[n] = 0.0;
-    return;
-  }
-  const double lt = k.cxi * kk * sqrt(kk) / eps;
-  const double lk = k.Ceta * sqrt(sqrt(k.nu * k.nu * k.nu / eps));
-  L[n] = k.CL * fmax(lt, lk);                                  // Eq. 16
 }
 
 // The fields' wp_ij (slots 14-22) as the initial guess x[9][nn].
@@ -106,29 +65,9 @@ __global__ void wp_bc_kernel(const T* __restrict__ f, int nn, WpConst k, const i
                              double* __restrict__ x, int* __restrict__ err) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nn) return;
-  const T* q = f + static_cast<size_t>(n) * kNF;
-  const int cls = ncls[n];
-  double eps = 0.0;
-  if (cls == 1) {
-    const double kk = 0.5 * (static_cast<double>(q[23]) + q[24] + q[25]);
-    const double om = q[29];
-    eps = om * (kk + k.nu * k.CT * k.CT * om);
-    if (!(eps > 0.0)) atomicExch(err, 1);
-  }
-  const double nv[3] = {nrm[2 * n], nrm[2 * n + 1], 0.0};
-  for (int c = 0; c < 9; ++c) {
-    const int i = c / 3, j = c % 3;
-    const size_t o = static_cast<size_t>(c) * nn + n;
-    if (cls == 1) {
-      x[o] = -4.5 * eps * nv[i] * nv[j];   // Eq. 59
-      fixed[o] = 1;
-    } else if (cls == 2 && i != j) {
-      x[o] = 0.0;
-      fixed[o] = 1;
-    } else {
-      fixed[o] = 0;
-    }
-  }
+  if (!eops::wp_bc_node(f + static_cast<size_t>(n) * kNF, k, ncls[n], nrm[2 * n], nrm[2 * n + 1], fixed + n,
+                        x + n, static_cast<size_t>(nn)))
+    atomicExch(err, 1);
 }
 
 __global__ void assemble_wp_kernel(int nnz, const int32_t* __restrict__ cptr, const int32_t* __restrict__ clist,
@@ -136,18 +75,7 @@ __global__ void assemble_wp_kernel(int nnz, const int32_t* __restrict__ cptr, co
                                    const double* __restrict__ L, double* __restrict__ aval) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= nnz) return;
-  double s = 0.0;
-  for (int j = cptr[i]; j < cptr[i + 1]; ++j) {
-    const int cc = clist[j];
-    const int e = cc / 9, a = (cc % 9) / 3, b = cc % 3;
-    const double* g = fe + 7 * static_cast<size_t>(e);
-    const int32_t* t = tri + 3 * static_cast<size_t>(e);
-    const double l0 = L[t[0]], l1 = L[t[1]], l2 = L[t[2]];
-    const double L2 = (l0 * l0 + l1 * l1 + l2 * l2) / 3.0;
-    const double A = g[6];
-    s += A / 12.0 * (a == b ? 2.0 : 1.0) + L2 * A * (g[a] * g[b] + g[3 + a] * g[3 + b]);
-  }
-  aval[i] = s;
+  aval[i] = eops::wp_entry(cptr[i], cptr[i + 1], clist, fe, tri, L);
 }
 
 // y[c][n] = sum_k val[k] x[c][col[k]] over row n, for C components.
@@ -157,10 +85,7 @@ __global__ void spmv_kernel(int nn, int C, const int32_t* __restrict__ row, cons
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= static_cast<int64_t>(nn) * C) return;
   const int c = static_cast<int>(i / nn), n = static_cast<int>(i % nn);
-  const double* xc = x + static_cast<size_t>(c) * nn;
-  double s = 0.0;
-  for (int k = row[n]; k < row[n + 1]; ++k) s += val[k] * xc[col[k]];
-  y[i] = s;
+  y[i] = eops::csr_row(n, row, col, val, x + static_cast<size_t>(c) * nn);
 }
 
 // Scalars of component c: sc[c * kSc + .].
@@ -294,12 +219,7 @@ __global__ void egrad_kernel(int ne, int nn, int nq, const double* __restrict__ 
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= static_cast<int64_t>(ne) * nq) return;
   const int j = static_cast<int>(i / ne), e = static_cast<int>(i % ne);
-  const double* g = fe + 7 * static_cast<size_t>(e);
-  const int32_t* t = tri + 3 * static_cast<size_t>(e);
-  const double* qj = q + static_cast<size_t>(j) * nn;
-  const double v0 = qj[t[0]], v1 = qj[t[1]], v2 = qj[t[2]];
-  eg[2 * i] = g[0] * v0 + g[1] * v1 + g[2] * v2;
-  eg[2 * i + 1] = g[3] * v0 + g[4] * v1 + g[5] * v2;
+  eops::elem_gradient(e, fe, tri, q + static_cast<size_t>(j) * nn, &eg[2 * i], &eg[2 * i + 1]);
 }
 
 // Node transfer (Sect. 3.4): the mean over the elements around each node: gn[nq][nn][2].
@@ -309,16 +229,7 @@ __global__ void nmean_kernel(int nn, int ne, int nq, const int32_t* __restrict__
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= static_cast<int64_t>(nn) * nq) return;
   const int j = static_cast<int>(i / nn), n = static_cast<int>(i % nn);
-  const double* egj = eg + 2 * static_cast<size_t>(j) * ne;
-  double gx = 0.0, gy = 0.0;
-  const int m = ne_off[n + 1] - ne_off[n];
-  for (int k = ne_off[n]; k < ne_off[n + 1]; ++k) {
-    const int e = ne_list[k];
-    gx += egj[2 * e];
-    gy += egj[2 * e + 1];
-  }
-  gn[2 * i] = m > 0 ? gx / m : 0.0;
-  gn[2 * i + 1] = m > 0 ? gy / m : 0.0;
+  eops::node_mean(n, ne_off, ne_list, eg + 2 * static_cast<size_t>(j) * ne, &gn[2 * i], &gn[2 * i + 1]);
 }
 
 // Inputs of the first derivative pass: <U>*, <V>* (from nmom or a caller's [nn][3]), P and
@@ -356,25 +267,10 @@ __global__ void pressure_src_kernel(int nn, const double* __restrict__ g6, const
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nn) return;
   const size_t N2 = 2 * static_cast<size_t>(nn);
-  const double* gu = g6;
-  const double* gv = g6 + N2;
-  const double* gp = g6 + 2 * N2;
-  const double* guu = g6 + 3 * N2;
-  const double* gvv = g6 + 4 * N2;
-  const double* guv = g6 + 5 * N2;
   const double lapP = g2[2 * n] + g2[N2 + 2 * n + 1];
-  src[n] = (gu[2 * n] + gv[2 * n + 1] - Cp * lapP) / dt;
-  double fl = 0.0;
-  if (ncls[n] == 1) {
-    const T* fn = f + static_cast<size_t>(n) * kNF;
-    const double nx = nrm[2 * n], ny = nrm[2 * n + 1];
-    const double divx = guu[2 * n] + guv[2 * n + 1];
-    const double divy = guv[2 * n] + gvv[2 * n + 1];
-    const double eq61 = nu * (static_cast<double>(fn[11]) * nx + static_cast<double>(fn[12]) * ny) -
-                        (divx * nx + divy * ny);
-    fl = eq61 - (gp[2 * n] * nx + gp[2 * n + 1] * ny);
-  }
-  flux[n] = fl;
+  eops::pressure_node(g6 + 2 * n, g6 + N2 + 2 * n, g6 + 2 * N2 + 2 * n, g6 + 3 * N2 + 2 * n,
+                      g6 + 4 * N2 + 2 * n, g6 + 5 * N2 + 2 * n, lapP, f + static_cast<size_t>(n) * kNF, ncls[n],
+                      nrm[2 * n], nrm[2 * n + 1], nu, dt, Cp, &src[n], &flux[n]);
 }
 
 // Galerkin load of Eq. 33: b = -M src + the no-slip edge integrals of the normal derivative.
@@ -385,11 +281,7 @@ __global__ void pressure_load_kernel(int nn, const int32_t* __restrict__ row, co
                                      double* __restrict__ b) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nn) return;
-  double s = 0.0;
-  for (int k = row[n]; k < row[n + 1]; ++k) s += mval[k] * src[col[k]];
-  double e = 0.0;
-  for (int k = boff[n]; k < boff[n + 1]; ++k) e += blen[k] / 6.0 * (2.0 * flux[n] + flux[bnb[k]]);
-  b[n] = e - s;
+  b[n] = eops::pressure_load_node(n, row, col, mval, src, flux, boff, bnb, blen);
 }
 
 // v -= sum(v) / n, the sum from a scalar slot (sc[c * kSc + S_BNORM] holds it unsquared).

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include "../../include/pdfx.h"
+#include "eulerian_ops.h"
 #include "pdfx_device.cuh"
 
 namespace pdfx {
@@ -151,10 +152,6 @@ constexpr int64_t kMaxSlots = (int64_t(1) << 31) - 1;  // particle slots of a ba
 constexpr int kBigCap = 4096;       // binning capacity of the large-element kernel
 
 // Eulerian solves of the coupled loop (k_eulerian.cu), FP64.
-struct WpConst {             // constants of Eqs. 12-18 and Eq. 59
-  double C1, C2, Cv, gamma5, CL, Ceta, CT, nu;
-  double cxi;                // Eq. 17: 1 + 1.3 n_i n_i (2.3 with a no-slip wall, else 1)
-};
 // Galerkin FEM data of a grid with linear triangles (Sect. 3.2), built on the host once.
 struct FemDev {
   int32_t nn = 0, ne = 0, nnz = 0;
