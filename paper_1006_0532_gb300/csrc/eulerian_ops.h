@@ -23,8 +23,6 @@ struct WpConst {             // constants of Eqs. 12-18 and Eq. 59
 
 namespace eops {
 
-constexpr int kFieldSlots = 32;
-
 // Eqs. 12-18 at one node from its 32 field slots f: the right-hand side of Eq. 12 into
 // rhs[c * stride] (c = 3 i + j) and the length scale of Eq. 16 into *L.  H_ijkl of Eq. 13
 // is applied in contracted form,
@@ -188,6 +186,84 @@ PDFX_HD double pressure_load_node(int n, const int32_t* row, const int32_t* col,
   double e = 0.0;
   for (int k = boff[n]; k < boff[n + 1]; ++k) e += blen[k] / 6.0 * (2.0 * flux[n] + flux[bnb[k]]);
   return e - s;
+}
+
+// Conjugate gradients with the Jacobi preconditioner over C systems (Sect. 3.2): the work
+// of one free or fixed node per pass, and the scalars of one component.  Scalars of a
+// component: s[kPcgScalars] = rz, |b|, zz, alpha, beta, active, iterations.
+constexpr int kPcgScalars = 8;
+enum { S_RZ = 0, S_BNORM = 1, S_ZZ = 2, S_ALPHA = 3, S_BETA = 4, S_ACTIVE = 5, S_ITERS = 6 };
+
+// One node of a pass (fr: the node is free for this component; q holds A times the vector
+// the pass needs).  mode 0: the preconditioned reduced load, sums zb^2; mode 1: initial
+// residual r = b - q, z = r / diag, d = z, sums r z and z z; mode 2: q masked, sums d q;
+// mode 3: x += alpha d, r -= alpha q, z = r / diag, sums r z and z z.
+PDFX_HD void pcg_node(int mode, bool fr, double diag, double alpha, const double* b, double* x, double* r,
+                      double* z, double* d, double* q, double* s0, double* s1) {
+  if (mode == 0) {
+    const double zb = fr ? (*b - *q) / diag : 0.0;
+    *s0 += zb * zb;
+  } else if (mode == 1) {
+    const double rr = fr ? *b - *q : 0.0;
+    const double zz = fr ? rr / diag : 0.0;
+    *r = rr;
+    *z = zz;
+    *d = zz;
+    *s0 += rr * zz;
+    *s1 += zz * zz;
+  } else if (mode == 2) {
+    const double qq = fr ? *q : 0.0;
+    *q = qq;
+    *s0 += *d * qq;
+  } else {
+    if (fr) {
+      *x += alpha * *d;
+      *r -= alpha * *q;
+    }
+    const double zz = fr ? *r / diag : 0.0;
+    *z = zz;
+    *s0 += *r * zz;
+    *s1 += zz * zz;
+  }
+}
+
+// The scalars of one component from a pass's sums t0, t1.  step 0: |b|; step 1: rz, zz,
+// the stopping test, iterations = 0; step 2: alpha (0 once converged); step 3: beta, rz, zz,
+// iterations + 1 and the stopping test, for a component still iterating.
+PDFX_HD void pcg_scalars(int step, double t0, double t1, double tol, double* s) {
+  if (step == 0) {
+    s[S_BNORM] = sqrt(t0);
+  } else if (step == 1) {
+    s[S_RZ] = t0;
+    s[S_ZZ] = t1;
+    s[S_ITERS] = 0.0;
+    s[S_ACTIVE] = sqrt(t1) > tol * s[S_BNORM] ? 1.0 : 0.0;
+    s[S_ALPHA] = 0.0;
+    s[S_BETA] = 0.0;
+  } else if (step == 2) {
+    s[S_ALPHA] = s[S_ACTIVE] != 0.0 ? s[S_RZ] / t0 : 0.0;
+  } else {
+    if (s[S_ACTIVE] != 0.0) {
+      s[S_BETA] = t0 / s[S_RZ];
+      s[S_RZ] = t0;
+      s[S_ZZ] = t1;
+      s[S_ITERS] += 1.0;
+      s[S_ACTIVE] = sqrt(t1) > tol * s[S_BNORM] ? 1.0 : 0.0;
+    } else {
+      s[S_BETA] = 0.0;
+    }
+  }
+}
+
+// The new direction d = z + beta d of a free node of a component still iterating.
+PDFX_HD void pcg_direction(bool fr, const double* s, double z, double* d) {
+  if (s[S_ACTIVE] == 0.0) return;
+  *d = fr ? z + s[S_BETA] * *d : 0.0;
+}
+
+// A component with a zero reduced load has the zero solution on its free nodes.
+PDFX_HD void pcg_trivial(bool fr, const double* s, double* x) {
+  if (s[S_BNORM] == 0.0 && fr) *x = 0.0;
 }
 
 }  // namespace eops

@@ -90,8 +90,7 @@ __global__ void spmv_kernel(int nn, int C, const int32_t* __restrict__ row, cons
 
 // Scalars of component c: sc[c * kSc + .].
 constexpr int kSc = kPcgScalars;
-enum { S_RZ = 0, S_BNORM = 1, S_ZZ = 2, S_ALPHA = 3, S_BETA = 4, S_ACTIVE = 5, S_ITERS = 6 };
-static_assert(S_ACTIVE == kPcgActive && S_ITERS == kPcgIters, "scalar layout");
+using eops::S_ALPHA;
 
 // Sums over nodes of the block's slice: grid (nblk, C); part[(c * nblk + blk) * 2 + m].
 // mode 0: zb = free ? (b - q) / diag : 0, sums zb^2 (the reduced load's norm)
@@ -110,31 +109,7 @@ __global__ void pcg_pass_kernel(int mode, int nn, const uint8_t* __restrict__ fi
   for (int n = blockIdx.x * kEB + threadIdx.x; n < nn; n += nblk * kEB) {
     const size_t o = base + n;
     const bool fr = !fixed || !fixed[o];
-    if (mode == 0) {
-      const double zb = fr ? (b[o] - q[o]) / diag[n] : 0.0;
-      s0 += zb * zb;
-    } else if (mode == 1) {
-      const double rr = fr ? b[o] - q[o] : 0.0;
-      const double zz = fr ? rr / diag[n] : 0.0;
-      r[o] = rr;
-      z[o] = zz;
-      d[o] = zz;
-      s0 += rr * zz;
-      s1 += zz * zz;
-    } else if (mode == 2) {
-      const double qq = fr ? q[o] : 0.0;
-      q[o] = qq;
-      s0 += d[o] * qq;
-    } else {
-      if (fr) {
-        x[o] += alpha * d[o];
-        r[o] -= alpha * q[o];
-      }
-      const double zz = fr ? r[o] / diag[n] : 0.0;
-      z[o] = zz;
-      s0 += r[o] * zz;
-      s1 += zz * zz;
-    }
+    eops::pcg_node(mode, fr, diag[n], alpha, b + o, x + o, r + o, z + o, d + o, q + o, &s0, &s1);
   }
   const double t0 = block_sum(s0, sh);
   const double t1 = block_sum(s1, sh);
@@ -158,30 +133,7 @@ __global__ void pcg_scalar_kernel(int step, int nblk, const double* __restrict__
   }
   const double t0 = block_sum(a0, sh);
   const double t1 = block_sum(a1, sh);
-  if (threadIdx.x != 0) return;
-  double* s = sc + c * kSc;
-  if (step == 0) {
-    s[S_BNORM] = sqrt(t0);
-  } else if (step == 1) {
-    s[S_RZ] = t0;
-    s[S_ZZ] = t1;
-    s[S_ITERS] = 0.0;
-    s[S_ACTIVE] = sqrt(t1) > tol * s[S_BNORM] ? 1.0 : 0.0;
-    s[S_ALPHA] = 0.0;
-    s[S_BETA] = 0.0;
-  } else if (step == 2) {
-    s[S_ALPHA] = s[S_ACTIVE] != 0.0 ? s[S_RZ] / t0 : 0.0;
-  } else {
-    if (s[S_ACTIVE] != 0.0) {
-      s[S_BETA] = t0 / s[S_RZ];
-      s[S_RZ] = t0;
-      s[S_ZZ] = t1;
-      s[S_ITERS] += 1.0;
-      s[S_ACTIVE] = sqrt(t1) > tol * s[S_BNORM] ? 1.0 : 0.0;
-    } else {
-      s[S_BETA] = 0.0;
-    }
-  }
+  if (threadIdx.x == 0) eops::pcg_scalars(step, t0, t1, tol, sc + c * kSc);
 }
 
 // d = free ? z + beta d : 0 for the components still iterating.
@@ -190,9 +142,7 @@ __global__ void pcg_direction_kernel(int nn, int C, const uint8_t* __restrict__ 
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= static_cast<int64_t>(nn) * C) return;
   const int c = static_cast<int>(i / nn);
-  if (sc[c * kSc + S_ACTIVE] == 0.0) return;
-  const bool fr = !fixed || !fixed[i];
-  d[i] = fr ? z[i] + sc[c * kSc + S_BETA] * d[i] : 0.0;
+  eops::pcg_direction(!fixed || !fixed[i], sc + c * kSc, z[i], d + i);
 }
 
 // xD = fixed ? x : 0 (the Dirichlet columns of the reduced load).
@@ -209,7 +159,7 @@ __global__ void trivial_kernel(int nn, int C, const uint8_t* __restrict__ fixed,
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= static_cast<int64_t>(nn) * C) return;
   const int c = static_cast<int>(i / nn);
-  if (sc[c * kSc + S_BNORM] == 0.0 && !(fixed && fixed[i])) x[i] = 0.0;
+  eops::pcg_trivial(!(fixed && fixed[i]), sc + c * kSc, x + i);
 }
 
 // Element gradients (Eq. 39 with Eq. 40's derivatives) of nq nodal quantities q[nq][nn]:
@@ -284,7 +234,7 @@ __global__ void pressure_load_kernel(int nn, const int32_t* __restrict__ row, co
   b[n] = eops::pressure_load_node(n, row, col, mval, src, flux, boff, bnb, blen);
 }
 
-// v -= sum(v) / n, the sum from a scalar slot (sc[c * kSc + S_BNORM] holds it unsquared).
+// v -= sum[0] / div (a sum the dot kernels left in device memory).
 __global__ void sub_mean_kernel(int nn, const double* __restrict__ sum, double div, double* __restrict__ v) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= nn) return;

@@ -189,9 +189,9 @@ struct PcgArgs {
   double* scratch = nullptr;       // pcg_scratch_doubles(nn, C)
   double tol = 0.0;
 };
-constexpr int kPcgScalars = 8;     // per component: rz, |b|, zz, alpha, beta, active, iterations
-constexpr int kPcgActive = 5;
-constexpr int kPcgIters = 6;
+constexpr int kPcgScalars = eops::kPcgScalars;   // per component: rz, |b|, zz, alpha, beta, active, iterations
+constexpr int kPcgActive = eops::S_ACTIVE;
+constexpr int kPcgIters = eops::S_ITERS;
 
 struct Ctx {
   pdfx_params prm{};

@@ -46,6 +46,63 @@ void node_gradients(const pdfx::FemHost& m, const std::vector<int32_t>& tri, con
   }
 }
 
+// Conjugate gradients over C systems [C][nn] with the library's per-node and per-component
+// functions, in the order of its kernels: the reduced load's norm, the zero solution of a
+// zero load, the initial residual, then iterations (A d, alpha, update, beta, direction)
+// until every component meets its stopping rule.  Returns the largest iteration count, or
+// -1 after max_iter.
+int pcg(const pdfx::FemHost& m, const std::vector<double>& val, const std::vector<double>& diag, int C, int nn,
+        const std::vector<uint8_t>* fixed, const std::vector<double>& b, std::vector<double>& x, double tol,
+        int max_iter) {
+  using namespace pdfx::eops;
+  const size_t N = static_cast<size_t>(C) * nn;
+  std::vector<double> r(N), z(N), d(N), q(N), sc(static_cast<size_t>(C) * kPcgScalars, 0.0);
+  auto fr = [&](size_t o) { return !fixed || !(*fixed)[o]; };
+  auto spmv = [&](const std::vector<double>& v) {
+    for (int c = 0; c < C; ++c)
+      for (int n = 0; n < nn; ++n)
+        q[static_cast<size_t>(c) * nn + n] = csr_row(n, m.row.data(), m.col.data(), val.data(), v.data() + static_cast<size_t>(c) * nn);
+  };
+  auto pass = [&](int mode, int step) {
+    for (int c = 0; c < C; ++c) {
+      double s0 = 0.0, s1 = 0.0;
+      double* s = &sc[static_cast<size_t>(c) * kPcgScalars];
+      for (int n = 0; n < nn; ++n) {
+        const size_t o = static_cast<size_t>(c) * nn + n;
+        pcg_node(mode, fr(o), diag[n], s[S_ALPHA], &b[o], &x[o], &r[o], &z[o], &d[o], &q[o], &s0, &s1);
+      }
+      pcg_scalars(step, s0, s1, tol, s);
+    }
+  };
+  for (size_t o = 0; o < N; ++o) d[o] = fr(o) ? 0.0 : x[o];
+  spmv(d);
+  pass(0, 0);
+  for (size_t o = 0; o < N; ++o) pcg_trivial(fr(o), &sc[(o / nn) * kPcgScalars], &x[o]);
+  spmv(x);
+  pass(1, 1);
+  int done = 0;
+  for (;;) {
+    bool any = false;
+    for (int c = 0; c < C; ++c) any |= sc[static_cast<size_t>(c) * kPcgScalars + S_ACTIVE] != 0.0;
+    if (!any) break;
+    if (done >= max_iter) return -1;
+    const int chunk = max_iter - done < 16 ? max_iter - done : 16;
+    for (int j = 0; j < chunk; ++j) {
+      spmv(d);
+      pass(2, 2);
+      pass(3, 3);
+      for (size_t o = 0; o < N; ++o) pcg_direction(fr(o), &sc[(o / nn) * kPcgScalars], z[o], &d[o]);
+    }
+    done += chunk;
+  }
+  int most = 0;
+  for (int c = 0; c < C; ++c) {
+    const int it = static_cast<int>(sc[static_cast<size_t>(c) * kPcgScalars + S_ITERS]);
+    most = it > most ? it : most;
+  }
+  return most;
+}
+
 }  // namespace
 
 int main(int argc, char** argv) {
@@ -115,6 +172,26 @@ int main(int argc, char** argv) {
   for (int n = 0; n < nn; ++n)
     b[n] = pdfx::eops::pressure_load_node(n, m.row.data(), m.col.data(), m.mval.data(), src.data(), flux.data(),
                                           m.boff.data(), m.bnb.data(), m.blen.data());
+  // Eq. 12 solved from the zero initial guess (Dirichlet values set above): the load M rhs
+  std::vector<double> bw(9 * static_cast<size_t>(nn)), adiag(nn), wp = x;
+  for (int c = 0; c < 9; ++c)
+    for (int n = 0; n < nn; ++n)
+      bw[static_cast<size_t>(c) * nn + n] = pdfx::eops::csr_row(n, m.row.data(), m.col.data(), m.mval.data(),
+                                                                 rhs.data() + static_cast<size_t>(c) * nn);
+  for (int n = 0; n < nn; ++n) adiag[n] = aval[m.dpos[n]];
+  const double tol = kc[10];
+  std::vector<int32_t> iters(2, 0);
+  iters[0] = pcg(m, aval, adiag, 9, nn, &fixed, bw, wp, tol, 100000);
+  // Eq. 33 from the zero initial guess: load with its nodal mean removed, zero integral
+  std::vector<double> dP(nn, 0.0), bl = b;
+  double mean = 0.0;
+  for (int n = 0; n < nn; ++n) mean += bl[n];
+  for (int n = 0; n < nn; ++n) bl[n] -= mean / nn;
+  iters[1] = pcg(m, m.kval, m.kdiag, 1, nn, nullptr, bl, dP, tol, 100000);
+  double num = 0.0;
+  for (int n = 0; n < nn; ++n) num += m.mlump[n] * dP[n];
+  for (int n = 0; n < nn; ++n) dP[n] -= num / m.area;
+  save("wp", wp); save("dP", dP); save("iters", iters);
   save("rhs", rhs); save("L", L); save("x", x); save("fixed", fixed); save("bad", bad);
   save("row", m.row); save("col", m.col); save("aval", aval);
   save("src", src); save("flux", flux); save("b", b);

@@ -4,8 +4,9 @@ Every kernel of the coupled loop maps its threads onto one inline function per n
 element.  The test compiles those functions with g++ into a harness that applies them over
 a whole grid in the kernels' order.  It compares the results with the oracle: Eq. 12's
 right-hand side and length scale, Eq. 59's wall values, the assembled matrix M + L_e^2 K,
-Eq. 33's source and Eq. 61's flux, and the Galerkin load.  What this leaves to the GPU
-tests is the launch and reduction structure around these functions.
+Eq. 33's source and Eq. 61's flux, the Galerkin load, and both solves driven through the
+library's per-node conjugate-gradient functions.  What this leaves to the GPU tests is the
+launch structure and the two-stage sums around these functions.
 """
 import os
 import shutil
@@ -55,13 +56,14 @@ def run(harness, g, F, params, ustar, P, dt, Cp, d):
     files = dict(tri=g.tri.astype(np.int32), tag=g.edge_tag.astype(np.int8), vx=x, vy=y, area2=a2,
                  fields=np.ascontiguousarray(F, dtype=np.float64),
                  consts=np.array([params[k] for k in ("C1", "C2", "Cv", "gamma5", "CL", "Ceta", "CT", "nu")]
-                                 + [dt, Cp, 0.0, 0.0]),
+                                 + [dt, Cp, 1e-13, 0.0]),
                  ustar=np.ascontiguousarray(ustar, dtype=np.float64), P=np.ascontiguousarray(P, dtype=np.float64))
     for k, v in files.items():
         v.tofile(os.path.join(d, k))
     subprocess.run([harness, d, str(g.nn), str(g.tri.shape[0])], check=True)
     rd = lambda n, t: np.fromfile(os.path.join(d, n), t)
-    out = {n: rd(n, np.float64) for n in ("rhs", "L", "x", "aval", "src", "flux", "b")}
+    out = {n: rd(n, np.float64) for n in ("rhs", "L", "x", "aval", "src", "flux", "b", "wp", "dP")}
+    out["iters"] = rd("iters", np.int32)
     out.update(fixed=rd("fixed", np.uint8), bad=rd("bad", np.int32), row=rd("row", np.int32),
                col=rd("col", np.int32))
     return out
@@ -119,3 +121,25 @@ def test_kernel_arithmetic_matches_oracle(harness, tmp_path, name, g, params):
         wall[g.tri[msk, (kk + 2) % 3]] = True
     assert np.abs(edge[~wall]).max() <= 1e-12 * np.abs(r["b"]).max()
     assert np.abs(edge[wall]).max() > 0.0
+
+
+@pytest.mark.parametrize("name,g,params", cases())
+def test_solves_through_the_kernel_functions_match_oracle(harness, tmp_path, name, g, params):
+    """Both solves driven through pcg_node, pcg_scalars, pcg_direction and pcg_trivial
+    (tolerance 1e-13, zero initial guess) reproduce the oracle's solutions and iteration
+    counts: the same stopping rule, masks and zero-load rule."""
+    F = random_fields(g, 4)
+    p = base_params(**{k: params[k] for k in ("nu",)}, period_x=g.period_x)
+    o = oracle.Oracle(g, p, F)
+    rng = np.random.default_rng(6)
+    ustar, P = rng.normal(size=(g.nn, 3)), rng.normal(size=g.nn)
+    r = run(harness, g, F, p, ustar, P, 1e-4, 5e-5, str(tmp_path))
+    ro, Lo = o.wp_rhs()
+    wo, io = o.wp_solve(ro, Lo, tol=1e-13)
+    wg = r["wp"].reshape(9, g.nn).T.reshape(g.nn, 3, 3)
+    assert np.abs(wg - wo).max() <= 1e-10 * np.abs(wo).max()
+    assert abs(int(r["iters"][0]) - io) <= 1
+    so, fo = o.pressure_rhs(ustar, P, 1e-4, 5e-5)
+    do, ip = o.pressure_solve(so, fo, tol=1e-13)
+    assert np.abs(r["dP"] - do).max() <= 1e-9 * np.abs(do).max()
+    assert abs(int(r["iters"][1]) - ip) <= 1
