@@ -52,6 +52,7 @@ extern "C" {
 #define PDFX_ERR_CAPACITY      -7   /* an element exceeded PDFX_MAX_PER_ELEMENT (device word) */
 #define PDFX_ERR_NONFINITE     -8   /* a particle state became NaN or infinite (device word) */
 #define PDFX_ERR_SOLVE         -9   /* an iterative solve did not converge within its limit */
+#define PDFX_ERR_ELEMENT      -10   /* a particle's element id lies outside the grid (device word) */
 
 #define PDFX_NF 32                  /* nodal field slots, layout below */
 #define PDFX_NSTAT 13               /* statistics per element or node, layout below */
@@ -133,6 +134,8 @@ typedef struct pdfx_diag {
     int32_t error;            /* first device error code seen (PDFX_ERR_*), 0 if none */
     int32_t lost_records;     /* entries of lost[] in use */
     double  lost_xy[4][4];    /* first lost particles: x, y, old element, particle id */
+    int64_t bad_element;      /* particles whose element id, given in device memory, lay
+                                 outside 0 .. ne - 1 (PDFX_ERR_ELEMENT) */
 } pdfx_diag;
 
 /* Defaults: Table 4 constants, Cs = 0.02, Ct = 0.7 (Sect. 4.1.2), C0 from Eq. 11,
@@ -203,8 +206,11 @@ int  pdfx_init_particles_batch(void *ctx, const int32_t *ppe, void *stream);
 /* Replaces the particle state by np particles with ids 0..np-1 (FP64 arrays of s, host
  * or device per on_device; cp is ignored) and sets the step counter.  In a batch, host
  * arrays only, ordered by instance (ids restart at 0 in each instance; PDFX_ERR_ARG
- * otherwise).  Computes the
- * statistics and conditional means of that state.  Synchronous for host input. */
+ * otherwise).  Computes the statistics and conditional means of that state.  Element ids
+ * outside 0 .. ne - 1 are PDFX_ERR_ARG for host input; for device input the device checks
+ * them: such a particle is placed in element 0 (the next step's walk relocates it), counted
+ * (pdfx_diag.bad_element), and the device error word and the return value become
+ * PDFX_ERR_ELEMENT.  Synchronous. */
 int  pdfx_set_particles(void *ctx, int64_t np, const pdfx_soa *s, uint32_t step,
                         int on_device, void *stream);
 
@@ -340,7 +346,11 @@ int  pdfx_stage_times(void *ctx, double *ms, int64_t *launches, int n, void *str
  *   Outputs, device memory written on stream: emom [ne][13], vcce [ne][G], gbin [ne][3],
  *   cp [np] (conditioning pointers), nmom [nn][13] (may be NULL to skip).
  * The results equal those the context computes for the same state (pdfx_set_particles
- * followed by pdfx_get_element_stats / pdfx_get_bins / pdfx_get_nodal_stats), in FP64.
+ * followed by pdfx_get_element_stats / pdfx_get_bins / pdfx_get_nodal_stats), in FP64,
+ * with the context's conditioning (hierarchical bins or Fox's projection).  A particle whose
+ * element id lies outside 0 .. ne - 1 is left out of every element (its cp is not written),
+ * counted (pdfx_diag.bad_element) and sets the context's device error word to
+ * PDFX_ERR_ELEMENT (read by pdfx_check).
  * Scratch is one fixed device array of the library (about 10 MB) that every GPU loading
  * the library reserves until exit; the first call on a device looks up its address with
  * cudaGetSymbolAddress, so make that first call before any stream capture.  Every call

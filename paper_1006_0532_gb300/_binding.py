@@ -65,7 +65,8 @@ class Diag(C.Structure):
     _fields_ = [(n, C.c_int64) for n in DIAG_NAMES] + [("hop_hist", C.c_int64 * 8),
                                                         ("error", C.c_int32),
                                                         ("lost_records", C.c_int32),
-                                                        ("lost_xy", C.c_double * 16)]
+                                                        ("lost_xy", C.c_double * 16),
+                                                        ("bad_element", C.c_int64)]
 
 
 def library_path() -> str:
@@ -454,6 +455,7 @@ class Context:
         out["hop_hist"] = [int(v) for v in d.hop_hist]
         out["error"] = int(d.error)
         out["lost_records"] = [list(d.lost_xy[4 * i:4 * i + 4]) for i in range(d.lost_records)]
+        out["bad_element"] = int(d.bad_element)
         return out
 
     def reset_diag(self, stream=None):

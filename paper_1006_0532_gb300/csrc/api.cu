@@ -262,7 +262,7 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
   Particles<T> p = carve<T>(c.pbuf[c.cur], c.np);
   if (!counts_ready) {
     PDFX_CUDA(cudaMemsetAsync(c.plan.cnt, 0, sizeof(int32_t) * c.ne, s));
-    launch_count(p.elem, c.np, c.plan.cnt, s);
+    launch_count(p.elem, c.np, c.ne, c.plan.cnt, c.diag, c.err, s);
     c.launches++;
   }
   {
@@ -272,7 +272,7 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
   }
   {
     StageTimer t(c, 2, s);
-    launch_scatter(p.elem, c.np, c.plan, s);
+    launch_scatter(p.elem, c.np, c.ne, c.plan, s);
     c.launches++;
   }
   bool any_minnpel = false;
@@ -431,16 +431,23 @@ int do_set_particles(Ctx& c, int64_t np, const pdfx_soa* soa, uint32_t step, int
     el = tel;
   }
   launch_load_state<T>(p, np, c.K > 1 ? c.einst : nullptr, c.K > 1 ? c.ip0 : nullptr, src[0],
-                       src[1], src[2], src[3], src[4], src[5], src[6], el, s);
+                       src[1], src[2], src[3], src[4], src[5], src[6], el, c.ne, c.diag, c.err, s);
   c.launches++;
   c.step = step;
   PDFX_CUDA(cudaMemcpyAsync(c.dstep, &step, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
   c.steps_since_sort = 0;
-  const int rc = run_statistics<T>(c, false, false, true, s);
+  int rc = run_statistics<T>(c, false, false, true, s);
   if (tmp) {
     cudaStreamSynchronize(s);
     dev_free(c, tmp);
     dev_free(c, tel);
+  }
+  if (rc == PDFX_OK && on_device) {
+    // device element ids are range-checked by the load kernel: report a bad one now
+    int err = 0;
+    PDFX_CUDA(cudaMemcpyAsync(&err, c.err, sizeof(int), cudaMemcpyDeviceToHost, s));
+    PDFX_CUDA(cudaStreamSynchronize(s));
+    if (err == PDFX_ERR_ELEMENT) rc = err;
   }
   return rc;
 }
@@ -1697,6 +1704,7 @@ int pdfx_get_diag(void* ctx, pdfx_diag* d, void* stream) {
     PDFX_CUDA(cudaMemcpy(d->lost_xy, c->lost_rec, sizeof(double) * 4 * nrec, cudaMemcpyDeviceToHost));
   }
   d->lost_records = nrec;
+  d->bad_element = static_cast<int64_t>(h[kDiagBadElement]);
   return PDFX_OK;
 }
 
@@ -1865,6 +1873,7 @@ const char* pdfx_strerror(int code) {
     case PDFX_ERR_CAPACITY: return "an element exceeded the per-element capacity";
     case PDFX_ERR_NONFINITE: return "a particle state became non-finite";
     case PDFX_ERR_SOLVE: return "an iterative solve did not converge within its iteration limit";
+    case PDFX_ERR_ELEMENT: return "a particle's element id lies outside the grid";
     default: return "unknown error";
   }
 }

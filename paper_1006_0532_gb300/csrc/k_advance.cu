@@ -567,14 +567,23 @@ __global__ void init_batch_kernel(Particles<T> p, int64_t np, int K, const InstD
   warp_count(diag, kDiagGammaExhausted, c_gex);
 }
 
-__global__ void count_kernel(const int32_t* __restrict__ elem, int64_t np, int32_t* cnt) {
+// Counts per element of a state whose element ids may come from the caller: an id outside
+// 0 .. ne - 1 is not counted (the particle is in no element list), is counted in the
+// diagnostics and sets the error word to PDFX_ERR_ELEMENT.
+__global__ void count_kernel(const int32_t* __restrict__ elem, int64_t np, int32_t ne, int32_t* cnt,
+                             unsigned long long* diag, int* err) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const bool valid = i < np;
-  const int e = valid ? elem[i] : -1;
+  const int e = i < np ? elem[i] : -1;
+  const bool bad = i < np && (e < 0 || e >= ne);
+  const bool valid = i < np && !bad;
   const unsigned active = __ballot_sync(kFull, valid);
   if (valid) {
     const unsigned peers = __match_any_sync(active, e);
     if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(cnt + e, __popc(peers));
+  }
+  if (__any_sync(kFull, bad)) {
+    warp_count(diag, kDiagBadElement, bad ? 1 : 0);
+    if ((threadIdx.x & 31) == 0) atomicCAS(err, 0, PDFX_ERR_ELEMENT);
   }
 }
 
@@ -601,7 +610,8 @@ template <typename T>
 __global__ void load_state_kernel(Particles<T> p, int64_t np, const int32_t* einst,
                                   const int64_t* ip0, const double* x, const double* y,
                                   const double* u, const double* v, const double* w,
-                                  const double* om, const double* psi, const int32_t* elem) {
+                                  const double* om, const double* psi, const int32_t* elem,
+                                  int32_t ne, unsigned long long* diag, int* err) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= np) return;
   p.x[i] = static_cast<T>(x[i]);
@@ -611,8 +621,17 @@ __global__ void load_state_kernel(Particles<T> p, int64_t np, const int32_t* ein
   p.w[i] = static_cast<T>(w[i]);
   p.om[i] = static_cast<T>(om[i]);
   p.psi[i] = static_cast<T>(psi[i]);
-  p.elem[i] = elem[i];
-  p.pid[i] = static_cast<uint32_t>(i - (einst ? ip0[einst[elem[i]]] : 0));
+  // an element id outside the grid (device input is not checked on the host) is replaced
+  // by element 0, whose walk relocates the particle at the next step, and raises
+  // PDFX_ERR_ELEMENT; every later index stays within the grid
+  int32_t e = elem[i];
+  if (e < 0 || e >= ne) {
+    atomicAdd(diag + kDiagBadElement, 1ull);
+    atomicCAS(err, 0, PDFX_ERR_ELEMENT);
+    e = 0;
+  }
+  p.elem[i] = e;
+  p.pid[i] = static_cast<uint32_t>(i - (einst ? ip0[einst[e]] : 0));
   p.cp[i] = 0;
 }
 
@@ -661,9 +680,10 @@ void launch_init_batch(Particles<T> p, int64_t np, int K, const InstDev<T>* inst
   init_batch_kernel<T><<<blocks_for(np, 256), 256, 0, s>>>(p, np, K, inst, ip0, geo, topo, fields, diag);
 }
 
-void launch_count(const int32_t* elem, int64_t np, int32_t* cnt, cudaStream_t s) {
+void launch_count(const int32_t* elem, int64_t np, int32_t ne, int32_t* cnt, unsigned long long* diag,
+                  int* err, cudaStream_t s) {
   if (np <= 0) return;
-  count_kernel<<<blocks_for(np, 256), 256, 0, s>>>(elem, np, cnt);
+  count_kernel<<<blocks_for(np, 256), 256, 0, s>>>(elem, np, ne, cnt, diag, err);
 }
 
 template <typename T>
@@ -679,10 +699,10 @@ template <typename T>
 void launch_load_state(Particles<T> p, int64_t np, const int32_t* einst, const int64_t* ip0,
                        const double* x, const double* y, const double* u, const double* v,
                        const double* w, const double* om, const double* psi, const int32_t* elem,
-                       cudaStream_t s) {
+                       int32_t ne, unsigned long long* diag, int* err, cudaStream_t s) {
   if (np <= 0) return;
   load_state_kernel<T><<<blocks_for(np, 256), 256, 0, s>>>(p, np, einst, ip0, x, y, u, v, w, om,
-                                                           psi, elem);
+                                                           psi, elem, ne, diag, err);
 }
 
 void launch_convert_fields(const double* in, float* out, int64_t n, cudaStream_t s) {
@@ -704,7 +724,8 @@ void launch_convert_fields(const double* in, float* out, int64_t n, cudaStream_t
   template void launch_load_state<T>(Particles<T>, int64_t, const int32_t*, const int64_t*,    \
                                      const double*, const double*, const double*,              \
                                      const double*, const double*, const double*,              \
-                                     const double*, const int32_t*, cudaStream_t);
+                                     const double*, const int32_t*, int32_t,                   \
+                                     unsigned long long*, int*, cudaStream_t);
 PDFX_INSTANTIATE(double)
 PDFX_INSTANTIATE(float)
 #undef PDFX_INSTANTIATE

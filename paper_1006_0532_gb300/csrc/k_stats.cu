@@ -278,11 +278,13 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne_
 }
 
 // Element lists: idx[off[e] .. off[e] + cnt[e]) holds the slots of the particles in e.
-__global__ void scatter_kernel(const int32_t* __restrict__ elem, int64_t np, int32_t* cursor,
+// An element id outside 0 .. ne - 1 (a caller's state) is skipped: the count kernel has
+// left it out of the counts and reported it.
+__global__ void scatter_kernel(const int32_t* __restrict__ elem, int64_t np, int32_t ne, int32_t* cursor,
                                int32_t* idx) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const bool valid = i < np;
-  const int e = valid ? elem[i] : -1;
+  const int e = i < np ? elem[i] : -1;
+  const bool valid = i < np && e >= 0 && e < ne;
   const unsigned active = __ballot_sync(kFull, valid);
   if (!valid) return;
   const unsigned peers = __match_any_sync(active, e);
@@ -756,15 +758,28 @@ __global__ void node_average_kernel(const double* __restrict__ emom, const int32
   for (int s = 0; s < kNS; ++s) out[s] = c > 0 ? acc[s] / c : 0.0;
 }
 
+// Kernel attributes are per device: a flag per device records that a kernel's attributes
+// were set on it (setting them twice from racing host threads is harmless).
+constexpr int kMaxDevices = 64;
+template <typename T> bool redist_configured[kMaxDevices];
+template <typename T> bool stats_configured[kMaxDevices];
+bool first_use_on_device(bool (&flags)[kMaxDevices]) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return true;
+  if (flags[dev]) return false;
+  flags[dev] = true;
+  return true;
+}
+
 }  // namespace
 
 void launch_plan(Plan& pl, int32_t ne, int K, int minnpel, int allow_moves, cudaStream_t s) {
   plan_kernel<<<static_cast<unsigned>(K > 0 ? K : 1), kPlanThreads, 0, s>>>(pl, ne, minnpel, allow_moves);
 }
 
-void launch_scatter(const int32_t* elem, int64_t np, Plan& pl, cudaStream_t s) {
+void launch_scatter(const int32_t* elem, int64_t np, int32_t ne, Plan& pl, cudaStream_t s) {
   if (np <= 0) return;
-  scatter_kernel<<<static_cast<unsigned>((np + 255) / 256), 256, 0, s>>>(elem, np, pl.cursor, pl.idx);
+  scatter_kernel<<<static_cast<unsigned>((np + 255) / 256), 256, 0, s>>>(elem, np, ne, pl.cursor, pl.idx);
 }
 
 template <typename T>
@@ -772,12 +787,10 @@ void launch_redistribute(Particles<T> p, Plan& pl, int K, const InstDev<T>* inst
                          int64_t np, const ElemGeo<T>* geo, const ElemTopo* topo, const uint32_t* stepc,
                          int num_sms, unsigned long long* diag, int* err, cudaStream_t s) {
   const unsigned grid = static_cast<unsigned>(num_sms > 0 ? num_sms : 1);
-  static bool configured = false;
   const size_t apply_smem = 12 * static_cast<size_t>(kRedistCap);
-  if (!configured) {
+  if (first_use_on_device(redist_configured<T>)) {
     cudaFuncSetAttribute(apply_moves_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(apply_smem));
-    configured = true;
   }
   select_donors_kernel<T><<<grid, kRedistThreads, 0, s>>>(p, pl, K);
   apply_moves_kernel<T><<<grid, kRedistThreads, apply_smem, s>>>(p, pl, K, inst, np, geo, topo, stepc);
@@ -786,13 +799,11 @@ void launch_redistribute(Particles<T> p, Plan& pl, int K, const InstDev<T>* inst
 
 template <typename T>
 void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s) {
-  static bool configured = false;
   const size_t big = stats_smem_bytes<T>(kBigCap);
   static_assert(5 * 8 * kBigCap + 11 * kBigCap <= 227 * 1024, "large-element tile exceeds shared memory");
-  if (!configured) {
+  if (first_use_on_device(stats_configured<T>)) {
     cudaFuncSetAttribute(stats_big_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(big));
-    configured = true;
   }
   launch_stats_tiles<T>(a, num_sms, s);
   stats_big_kernel<T><<<static_cast<unsigned>(num_sms > 0 ? num_sms : 1), kStatsThreads, big, s>>>(a);

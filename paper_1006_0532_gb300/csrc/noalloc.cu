@@ -91,10 +91,10 @@ int element_stats_noalloc(Ctx& c, int64_t np, const double* u, const double* v, 
   if (cudaMemsetAsync(pl.cnt, 0, sizeof(int32_t) * c.ne, s) != cudaSuccess) return PDFX_ERR_CUDA;
   if (np > 0) {
     iota_kernel<<<static_cast<unsigned>((np + 255) / 256), 256, 0, s>>>(pid, np);
-    launch_count(elem, np, pl.cnt, s);
+    launch_count(elem, np, c.ne, pl.cnt, c.diag, c.err, s);
   }
   launch_plan(pl, c.ne, 1, 0, 0, s);
-  launch_scatter(elem, np, pl, s);
+  launch_scatter(elem, np, c.ne, pl, s);
   StatsArgs<double> a{};
   a.p.u = const_cast<double*>(u);
   a.p.v = const_cast<double*>(v);
@@ -126,6 +126,9 @@ int element_stats_noalloc(Ctx& c, int64_t np, const double* u, const double* v, 
   a.bins[2] = c.prm.bins[2];
   a.min_per_bin = c.prm.min_per_bin;
   a.G = c.G;
+  a.acc64 = 0;                      // FP64 throughout
+  a.cond_mode = c.prm.cond_mode;    // the context's conditioning: bins or Fox's projection
+  a.fox_bins = c.prm.fox_bins;
   a.emom = emom;
   a.vcce = vcce;
   a.gbin = gbin;

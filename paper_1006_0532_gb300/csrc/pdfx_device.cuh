@@ -21,7 +21,7 @@ enum Diag : int {
   kDiagHops = 0, kDiagFallback, kDiagBrute, kDiagLost, kDiagWall, kDiagFreeSlip,
   kDiagOmegaReflect, kDiagC0Clamp, kDiagGammaExhausted, kDiagMoves, kDiagSource,
   kDiagCapacity, kDiagNonFinite, kDiagHopHist0, kDiagLostRecord = kDiagHopHist0 + 8,
-  kDiagCount
+  kDiagBadElement, kDiagCount
 };
 constexpr int kLostRecords = 4;    // (x, y, old element, particle id) of the first lost particles
 constexpr int kBruteCap = 4096;    // particles per step that may need the brute-force search

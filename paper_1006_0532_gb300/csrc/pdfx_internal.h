@@ -302,9 +302,12 @@ template <typename T>
 void launch_init_batch(Particles<T> p, int64_t np, int K, const InstDev<T>* inst,
                        const int64_t* ip0, const ElemGeo<T>* geo, const ElemTopo* topo,
                        const T* fields, unsigned long long* diag, cudaStream_t s);
-void launch_count(const int32_t* elem, int64_t np, int32_t* cnt, cudaStream_t s);
+// Counts per element; ids outside 0 .. ne - 1 are skipped, counted and raise PDFX_ERR_ELEMENT.
+void launch_count(const int32_t* elem, int64_t np, int32_t ne, int32_t* cnt, unsigned long long* diag,
+                  int* err, cudaStream_t s);
 void launch_plan(Plan& pl, int32_t ne, int K, int minnpel, int allow_moves, cudaStream_t s);
-void launch_scatter(const int32_t* elem, int64_t np, Plan& pl, cudaStream_t s);
+// Element lists (ids outside 0 .. ne - 1 are skipped; launch_count reports them).
+void launch_scatter(const int32_t* elem, int64_t np, int32_t ne, Plan& pl, cudaStream_t s);
 template <typename T>
 void launch_redistribute(Particles<T> p, Plan& pl, int K, const InstDev<T>* inst, int32_t ne,
                          int64_t np, const ElemGeo<T>* geo, const ElemTopo* topo, const uint32_t* stepc,
@@ -397,7 +400,7 @@ template <typename T>
 void launch_load_state(Particles<T> p, int64_t np, const int32_t* einst, const int64_t* ip0,
                        const double* x, const double* y, const double* u, const double* v,
                        const double* w, const double* om, const double* psi, const int32_t* elem,
-                       cudaStream_t s);
+                       int32_t ne, unsigned long long* diag, int* err, cudaStream_t s);
 void launch_convert_fields(const double* in, float* out, int64_t n, cudaStream_t s);
 template <typename T>
 void launch_check_finite(Particles<T> p, int64_t np, unsigned long long* diag, int* err,

@@ -558,3 +558,36 @@ def test_velocity_correction_matches_oracle_f64():
     assert diff.sum() <= 2
     compare_state(sg, so, g.period_x, 1e-12, skip=diff)
     assert c.check() == 0
+
+
+# ----------------------------------------------------------------------------------------
+# Element ids from the caller's device memory
+# ----------------------------------------------------------------------------------------
+
+def test_device_state_with_out_of_range_elements_is_refused_without_a_fault():
+    """Element ids handed over in device memory are range-checked on the device: the load
+    replaces an id outside the grid by element 0, counts it and raises PDFX_ERR_ELEMENT,
+    which pdfx_set_particles returns.  Every later kernel sees ids inside the grid, so the
+    state can still be stepped and its particles are relocated by the walk."""
+    w = synth.workload("channel_tiny")
+    g = w["grid"]
+    c = gpu_ctx(g, w["params"], w["fields"])
+    c.init_particles(w["ppe"])
+    st = c.get_particles()
+    dev = torch.device("cuda")
+    d = {k: torch.from_numpy(np.ascontiguousarray(st[k])).to(dev) for k in STATE_KEYS}
+    el = st["elem"].astype(np.int32).copy()
+    el[3] = -1
+    el[7] = g.ne
+    d["elem"] = torch.from_numpy(el).to(dev)
+    with pytest.raises(B.PdfxError) as exc:
+        c.set_particles(d, 0)
+    assert exc.value.code == -10
+    diag = c.diag()
+    assert diag["bad_element"] == 2 and diag["error"] == -10
+    c.step(w["dt"])
+    torch.cuda.synchronize()
+    after = c.get_particles()
+    assert np.all((after["elem"] >= 0) & (after["elem"] < g.ne))
+    assert c.check() == -10
+    c.close()

@@ -63,6 +63,56 @@ def test_noalloc_statistics_match_regular_entry_points():
     c.close()
 
 
+def test_noalloc_follows_the_contexts_fox_projection():
+    """A context conditioned on Fox's projected velocity (cond_mode 1) gets Fox's intervals
+    from the no-allocation entry point too, not the hierarchical bins."""
+    w = synth.workload("channel_2k")
+    p = dict(w["params"], precision=0, sort_every=4, period_x=w["grid"].period_x, cond_mode=1,
+             fox_bins=16)
+    c = B.Context(p)
+    c.set_grid(w["grid"])
+    c.set_fields(w["fields"])
+    c.init_particles(w["ppe"])
+    c.step(w["dt"])
+    st = c.get_particles()
+    em_ref, _ = c.element_stats()
+    v_ref, g_ref = c.bins()
+    em, v, g, cp, nm = _noalloc(c, st)
+    assert np.array_equal(g, g_ref)
+    assert np.all(g_ref[:, 1] == 1) and np.any(g_ref[:, 0] > 4)
+    assert _rel(v, v_ref) <= 1e-10
+    assert np.array_equal(cp, st["cp"])
+    assert _rel(em, em_ref) <= 1e-10
+    assert c.check() == 0
+    c.close()
+
+
+def test_noalloc_skips_and_reports_element_ids_outside_the_grid():
+    """An element id outside the grid is left out of every element (no write outside the
+    scratch) and raises PDFX_ERR_ELEMENT in the context's error word; the other elements'
+    statistics are those of the regular entry points."""
+    w = synth.workload("channel_2k")
+    p = dict(w["params"], precision=0, sort_every=4, period_x=w["grid"].period_x)
+    c = B.Context(p)
+    c.set_grid(w["grid"])
+    c.set_fields(w["fields"])
+    c.init_particles(w["ppe"])
+    st = c.get_particles()
+    em_ref, _ = c.element_stats()
+    k = 12345
+    home = int(st["elem"][k])
+    bad = dict(st)
+    bad["elem"] = st["elem"].astype(np.int32).copy()
+    bad["elem"][k] = c.ne + 7
+    em, v, g, cp, nm = _noalloc(c, bad)
+    others = np.arange(c.ne) != home
+    assert np.array_equal(em[others], em_ref[others])
+    assert int(em[home, 0]) == int(em_ref[home, 0]) - 1
+    assert c.check() == -10
+    assert c.diag()["bad_element"] == 1
+    c.close()
+
+
 def test_noalloc_rejects_sizes_beyond_its_limits():
     w = synth.workload("channel_tiny")
     c = B.Context(dict(w["params"], period_x=w["grid"].period_x))
