@@ -758,18 +758,8 @@ __global__ void node_average_kernel(const double* __restrict__ emom, const int32
   for (int s = 0; s < kNS; ++s) out[s] = c > 0 ? acc[s] / c : 0.0;
 }
 
-// Kernel attributes are per device: a flag per device records that a kernel's attributes
-// were set on it (setting them twice from racing host threads is harmless).
-constexpr int kMaxDevices = 64;
 template <typename T> bool redist_configured[kMaxDevices];
 template <typename T> bool stats_configured[kMaxDevices];
-bool first_use_on_device(bool (&flags)[kMaxDevices]) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return true;
-  if (flags[dev]) return false;
-  flags[dev] = true;
-  return true;
-}
 
 }  // namespace
 

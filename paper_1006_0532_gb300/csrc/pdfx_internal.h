@@ -290,6 +290,18 @@ struct Ctx {
 template <typename T>
 Particles<T> particles_of(Ctx& c, int which);
 
+// Kernel attributes are per device: a flag per device records that a kernel's attributes
+// were set on it (setting them twice from racing host threads is harmless).  True on the
+// first call for the current device (and whenever the device cannot be told).
+constexpr int kMaxDevices = 64;
+inline bool first_use_on_device(bool (&flags)[kMaxDevices]) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return true;
+  if (flags[dev]) return false;
+  flags[dev] = true;
+  return true;
+}
+
 // Kernel launchers (defined in the .cu files).
 template <typename T>
 void launch_advance(const AdvanceArgs<T>& a, int num_sms, int block, cudaStream_t s);   // block <= 256

@@ -1,10 +1,8 @@
 """GPU parity of the coupled loop's CUDA path (Eqs. 12-18, 33, 59, 61; Table 1).
 
-This module is not collected yet (its name does not match test_*.py): its kernels have not
-had a first run on a GPU.  After that run it becomes test_gpu_eulerian.py.  Each test
-compares the CUDA path with the oracle on the same inputs in FP64; the solves use the same
-stopping rule on both sides, so their results differ by the solver tolerance times the
-conditioning, not by rounding alone.
+Each test compares the CUDA path with the oracle on the same inputs in FP64; the solves use
+the same stopping rule on both sides, so their results differ by the solver tolerance times
+the conditioning, not by rounding alone.
 """
 import numpy as np
 import pytest
