@@ -315,6 +315,7 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
     a.gbin = c.gbin;
     a.step_inc = allow_moves ? c.dstep : nullptr;   // only a step advances the counter
     a.acc64 = c.prm.acc64;
+    a.prior = 1;
     a.cond_mode = c.prm.cond_mode;
     a.fox_bins = c.prm.fox_bins;
     a.diag = c.diag;

@@ -176,6 +176,7 @@ struct Acc<float> {
     s = t;
   }
   __device__ __forceinline__ float value() const { return s - c; }
+  __device__ __forceinline__ static float err(const Acc& a) { return a.c; }
   // value/error pairs: an exact two-sum of the leading parts, errors added, renormalised
   __device__ __forceinline__ void warp_pair(float& hv, float& lv) const {
     float h = s, l = -c;
@@ -198,6 +199,7 @@ struct Acc<double> {
   double s = 0.0;
   __device__ __forceinline__ void add(double x) { s += x; }
   __device__ __forceinline__ double value() const { return s; }
+  __device__ __forceinline__ static double err(const Acc&) { return 0.0; }
   __device__ __forceinline__ void warp_pair(double& hv, double& lv) const {
     double v = s;
 #pragma unroll
@@ -461,16 +463,16 @@ struct ProjVal {
 // outputs are formed in FP64, one per lane.  Inlined: as an out-of-line call it measured
 // slower (its spills and the call outweigh the spills it saves in the sorting loops).
 // FOX: also the sums of d_a d_phi, then <u_a phi'> and the factors of Eqs. 65-66.
-template <typename A, bool FOX, typename T, int CAP>
+template <typename A, bool FOX, typename T, typename TileT, typename I>
 __device__ __forceinline__ void element_moments(const T* __restrict__ pu, const T* __restrict__ pv,
                                                 const T* __restrict__ pw, const T* __restrict__ pom,
                                                 const T* __restrict__ ppsi, double* emom_e,
-                                                int32_t* gbin_e, Tile<T, CAP, FOX>& t,
-                                                const int32_t* cur, int n, int g0, int g1, int g2) {
+                                                int32_t* gbin_e, TileT& t,
+                                                const I* cur, int n, int g0, int g1, int g2) {
   const int lane = threadIdx.x & 31;
   A sh[5] = {A(0), A(0), A(0), A(0), A(0)};
   if (n > 0) {
-    const int32_t q0 = cur[0];
+    const int q0 = cur[0];
     sh[0] = A(pu[q0]); sh[1] = A(pv[q0]); sh[2] = A(pw[q0]);
     sh[3] = A(pom[q0]); sh[4] = A(ppsi[q0]);
   }
@@ -478,7 +480,7 @@ __device__ __forceinline__ void element_moments(const T* __restrict__ pu, const 
   Acc<A> mx[3];   // FOX only
 #pragma unroll 2
   for (int p = lane; p < n; p += 32) {
-    const int32_t q = cur[p];
+    const int q = cur[p];
     const A du = A(pu[q]) - sh[0], dv = A(pv[q]) - sh[1], dw = A(pw[q]) - sh[2];
     const A dom = A(pom[q]) - sh[3], dp = A(ppsi[q]) - sh[4];
     m[0].add(du); m[1].add(dv); m[2].add(dw); m[3].add(dom); m[4].add(dp);
@@ -750,6 +752,598 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP, FOX>& t, int e,
   }
 }
 
+// ---------------------------------------------------------------------------------------
+// Hierarchical bins by per-level bucket ranks (the default conditioning, Sect. 3.5 and
+// Appendix A).  A level needs each particle's rank by (key, id) inside its group of the
+// previous level; it is found without sorting:
+//   1. each group's smallest and largest key (as FP32, shared-memory atomics);
+//   2. a bucket per particle, floor((key - min) NB_g / (max - min)) with NB_g buckets per
+//      group, computed in FP32 from the key rounded to FP32: rounding, subtraction of the
+//      group minimum and scaling are all monotone, so the bucket never decreases with the
+//      key and equal keys share a bucket;
+//   3. bucket counts (atomics), their exclusive scan (the first position of every bucket:
+//      the groups lie in group order, so a bucket's first position is its group's first
+//      position plus the particles of the group's lower buckets), the particles listed by
+//      bucket;
+//   4. a particle's position is its bucket's first position plus the number of particles of
+//      its bucket that come before it by (key, id), counted directly (buckets hold a few
+//      particles).
+// The positions are a permutation, the order of an exact sort within the groups, so every
+// level, the final order, the moment sums taken in it, the bins and the conditioning
+// pointers are those of a full sort by (key, id).  The element's values, ids and slots are
+// staged in shared memory once.
+// ---------------------------------------------------------------------------------------
+template <typename T, int CAP, int THREADS>
+struct RankTile {
+  static constexpr int kNB = CAP;   // buckets of one level over all of its groups
+  using A = double;                 // moment combination and outputs
+  double mh[12], ml[12], msh[5];    // moment sums (value/error pairs) and shift values
+  T u[CAP], v[CAP], w[CAP], om[CAP], psi[CAP];
+  uint32_t pid[CAP];
+  int32_t slot[CAP];
+  union {
+    struct {
+      int32_t start[kNB + 1];       // bucket counts, then each bucket's first position
+      uint32_t glo[256], gsc[256];  // each group's key range, then its bucket origin and scale
+    } b;
+    float2 combf[12 * 32];          // per-lane moment sums, sum-major: compensated FP32
+    double combd[12 * 32];          // or FP64
+  } x;
+  int16_t ord[CAP];                 // position -> particle (staging index), final level
+  int16_t pos[CAP];                 // particle -> position, final level
+  int16_t mem[CAP];                 // particles by bucket
+  uint8_t grp[CAP];                 // particle -> group of the last level done
+  int32_t wsum[THREADS / 32];
+  int n_gathered;
+};
+
+// Order-preserving 32-bit image of an FP32 value and its inverse (-0 folded onto +0).
+__device__ __forceinline__ uint32_t ord32(float x) { return ord_bits(x); }
+__device__ __forceinline__ float unord32(uint32_t o) {
+  return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+__device__ __forceinline__ float bucket_key(float x) { return x; }
+__device__ __forceinline__ float bucket_key(double x) { return __double2float_rn(x); }
+
+// (a, ia) before (b, ib): value first, then particle id (the order of the FP32 and FP64
+// keys of the sort-based levels; -0 equals +0).
+__device__ __forceinline__ bool rank_before(float a, uint32_t ia, float b, uint32_t ib) {
+  return (a < b) | ((a == b) & (ia < ib));
+}
+__device__ __forceinline__ bool rank_before(double a, uint32_t ia, double b, uint32_t ib) {
+  const uint64_t oa = ord_bits(a), ob = ord_bits(b);
+  return (oa < ob) | ((oa == ob) & (ia < ib));
+}
+
+// In-place exclusive scan of c[0, N) (N a multiple of THREADS), c[N] = the total.
+template <int N, int THREADS>
+__device__ __forceinline__ void block_scan_counts(int32_t* c, int32_t* wsum) {
+  constexpr int E = N / THREADS;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  int v[E];
+  int sum = 0;
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    v[i] = c[tid * E + i];
+    sum += v[i];
+  }
+  int incl = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, incl, o);
+    if (lane >= o) incl += y;
+  }
+  if (lane == 31) wsum[warp] = incl;
+  __syncthreads();
+  int before = incl - sum;
+  int total = 0;
+#pragma unroll
+  for (int w = 0; w < THREADS / 32; ++w) {
+    const int ws = wsum[w];
+    if (w < warp) before += ws;
+    total += ws;
+  }
+#pragma unroll
+  for (int i = 0; i < E; ++i) {
+    c[tid * E + i] = before;
+    before += v[i];
+  }
+  if (tid == 0) c[N] = total;
+}
+
+// Bucket tables of one level: each particle's bucket within its group (t.grp, or one group
+// when Gprev is 1) and the bucket's arrival index; t.x.b.start ends as the first position of
+// every bucket.  The bucket of key x is floor((x - lo) scale) clamped to the group's NB_g
+// buckets.  With a prior (mean m and standard deviation s of the key over the element, from
+// the previous statistics pass) every group takes lo = m - 3 s and scale = NB_g / (6 s);
+// otherwise each group's own smallest and largest key set them.  Either way the bucket never
+// decreases with the key, which is all the ranks need.
+template <typename T, int CAP, int THREADS>
+__device__ __forceinline__ void bucket_level(RankTile<T, CAP, THREADS>& t, const T* key, int n, int Gprev,
+                                             float prior_m, float prior_s, int (&bin)[CAP / THREADS],
+                                             int (&arr)[CAP / THREADS]) {
+  constexpr int KPT = CAP / THREADS, NB = RankTile<T, CAP, THREADS>::kNB;
+  const int tid = threadIdx.x;
+  const int NBg = NB / Gprev;                  // Gprev <= 256 <= NB / 2
+  const float fNBg = static_cast<float>(NBg);
+  const bool prior = prior_s > 0.0f;           // false for NaN
+  if (!prior) {
+    for (int g = tid; g < Gprev; g += THREADS) {
+      t.x.b.glo[g] = 0xffffffffu;
+      t.x.b.gsc[g] = 0u;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k <= KPT; ++k) {
+    const int b = tid + k * THREADS;
+    if (b <= NB) t.x.b.start[b] = 0;
+  }
+  int grp[KPT];
+  float fk[KPT];
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    const int j = tid + k * THREADS;
+    grp[k] = 0;
+    fk[k] = 0.0f;
+    if (j < n) {
+      if (Gprev > 1) grp[k] = t.grp[j];
+      fk[k] = bucket_key(key[j]);
+    }
+  }
+  float plo = 0.0f, pscale = 0.0f;
+  if (prior) {
+    plo = prior_m - 3.0f * prior_s;
+    pscale = fNBg / (6.0f * prior_s);
+    __syncthreads();
+  } else {
+    __syncthreads();
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int j = tid + k * THREADS;
+      if (j < n) {
+        const uint32_t o = ord32(fk[k]);
+        atomicMin(&t.x.b.glo[grp[k]], o);
+        atomicMax(&t.x.b.gsc[grp[k]], o);
+      }
+    }
+    __syncthreads();
+    // per group: the bucket origin (its smallest key) and scale NB_g / (largest - smallest)
+    for (int g = tid; g < Gprev; g += THREADS) {
+      const float lo = unord32(t.x.b.glo[g]), hi = unord32(t.x.b.gsc[g]);
+      const float span = hi - lo;
+      t.x.b.glo[g] = __float_as_uint(lo);
+      t.x.b.gsc[g] = __float_as_uint(span > 0.0f ? fNBg / span : 0.0f);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    const int j = tid + k * THREADS;
+    bin[k] = 0;
+    arr[k] = 0;
+    if (j < n) {
+      const float lo = prior ? plo : __uint_as_float(t.x.b.glo[grp[k]]);
+      const float scale = prior ? pscale : __uint_as_float(t.x.b.gsc[grp[k]]);
+      const float q = (fk[k] - lo) * scale;
+      // q is non-decreasing in the key; NaN (a non-finite state) falls into bucket 0
+      const int b = q >= fNBg ? NBg - 1 : (q > 0.0f ? static_cast<int>(q) : 0);
+      bin[k] = grp[k] * NBg + b;
+      arr[k] = atomicAdd(&t.x.b.start[bin[k]], 1);
+    }
+  }
+  __syncthreads();
+  block_scan_counts<NB, THREADS>(t.x.b.start, t.wsum);
+  __syncthreads();
+}
+
+// Position of particle j in its bucket's order by (key, id), from the bucket's first
+// position s0 and its members t.mem[s0, s1).
+template <typename T, int CAP, int THREADS>
+__device__ __forceinline__ int bucket_position(const RankTile<T, CAP, THREADS>& t, const T* key, int j,
+                                               int s0, int s1) {
+  const T kv = key[j];
+  const uint32_t kid = t.pid[j];
+  int r = 0;
+#pragma unroll 1
+  for (int m = s0; m < s1; ++m) {
+    const int o = t.mem[m];
+    r += rank_before(key[o], t.pid[o], kv, kid) ? 1 : 0;
+  }
+  return s0 + r;
+}
+
+// A level before the last: only each particle's new group floor(Gl p / n) is needed.  It
+// follows from the bucket's position range unless the range straddles a group boundary;
+// only the particles of such buckets are ranked inside their bucket.
+template <typename T, int CAP, int THREADS>
+__device__ void group_level(RankTile<T, CAP, THREADS>& t, const T* key, int n, int Gprev, int Gl,
+                            float prior_m, float prior_s) {
+  constexpr int KPT = CAP / THREADS;
+  const int tid = threadIdx.x;
+  const float inv_n = 1.0f / static_cast<float>(n);
+  int bin[KPT], arr[KPT];
+  bucket_level(t, key, n, Gprev, prior_m, prior_s, bin, arr);
+  bool cut[KPT];
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    const int j = tid + k * THREADS;
+    cut[k] = false;
+    if (j < n) {
+      const int s0 = t.x.b.start[bin[k]], s1 = t.x.b.start[bin[k] + 1];
+      const int g0 = fdiv(Gl * s0, inv_n), g1 = fdiv(Gl * (s1 - 1), inv_n);
+      if (g0 == g1) t.grp[j] = static_cast<uint8_t>(g0);
+      else { cut[k] = true; t.mem[s0 + arr[k]] = static_cast<int16_t>(j); }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    const int j = tid + k * THREADS;
+    if (cut[k]) {
+      const int p = bucket_position(t, key, j, t.x.b.start[bin[k]], t.x.b.start[bin[k] + 1]);
+      t.grp[j] = static_cast<uint8_t>(fdiv(Gl * p, inv_n));
+    }
+  }
+  __syncthreads();
+}
+
+// The last level: every particle's position in the final order (t.pos, t.ord).
+template <typename T, int CAP, int THREADS>
+__device__ void order_level(RankTile<T, CAP, THREADS>& t, const T* key, int n, int Gprev, float prior_m,
+                            float prior_s) {
+  constexpr int KPT = CAP / THREADS;
+  const int tid = threadIdx.x;
+  int bin[KPT], arr[KPT];
+  bucket_level(t, key, n, Gprev, prior_m, prior_s, bin, arr);
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    const int j = tid + k * THREADS;
+    if (j < n) {
+      t.mem[t.x.b.start[bin[k]] + arr[k]] = static_cast<int16_t>(j);
+      t.ord[j] = static_cast<int16_t>(j);   // every position holds a valid index
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < KPT; ++k) {
+    const int j = tid + k * THREADS;
+    if (j < n) {
+      const int p = bucket_position(t, key, j, t.x.b.start[bin[k]], t.x.b.start[bin[k] + 1]);
+      t.pos[j] = static_cast<int16_t>(p);
+      t.ord[p] = static_cast<int16_t>(j);
+    }
+  }
+  __syncthreads();
+}
+
+// Sect. 3.3, Eqs. 35-36 in the final order.  Sums 0..4: d = x - x_0 of u, v, w, omega, psi;
+// 5..11: uu, vv, ww, uv, uw, vw, psi psi (products of d; x_0 the first particle of the
+// order).  Warp w < 4 takes three of the twelve sums over all particles, lane l the
+// positions l, l + 32, ... (compensated FP32 per lane, or FP64); lane c < 3 then adds the
+// 32 lanes' value/error pairs of its sum in lane order.  Called by every thread.
+template <typename A, typename T, int CAP, int THREADS>
+__device__ __forceinline__ void rank_moments(RankTile<T, CAP, THREADS>& t, int n) {
+  static_assert(THREADS >= 128, "four warps take the moment sums");
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (warp < 4) {
+    // warp 0: d_u, d_u d_u, d_u d_v; 1: d_v, d_v d_v, d_v d_w; 2: d_w, d_w d_w, d_u d_w;
+    // 3: d_omega, d_psi, d_psi d_psi
+    const T* xa = warp == 0 ? t.u : warp == 1 ? t.v : warp == 2 ? t.w : t.om;
+    const T* xb = warp == 0 ? t.v : warp == 1 ? t.w : warp == 2 ? t.u : t.psi;
+    A sa = A(0), sb = A(0);
+    if (n > 0) {
+      const int q0 = t.ord[0];
+      sa = A(xa[q0]);
+      sb = A(xb[q0]);
+    }
+    Acc<A> m0, m1, m2;
+#pragma unroll 2
+    for (int p = lane; p < n; p += 32) {
+      const int q = t.ord[p];
+      const A da = A(xa[q]) - sa, db = A(xb[q]) - sb;
+      if (warp < 3) {
+        m0.add(da);
+        m1.add(da * da);
+        m2.add(da * db);
+      } else {
+        m0.add(da);
+        m1.add(db);
+        m2.add(db * db);
+      }
+    }
+    // sum index of each accumulator
+    const int c0 = warp < 3 ? warp : 3;
+    const int c1 = warp < 3 ? 5 + warp : 4;
+    const int c2 = warp == 0 ? 8 : warp == 1 ? 10 : warp == 2 ? 9 : 11;
+    if constexpr (sizeof(A) == 4) {
+      t.x.combf[32 * c0 + lane] = make_float2(m0.s, -Acc<A>::err(m0));
+      t.x.combf[32 * c1 + lane] = make_float2(m1.s, -Acc<A>::err(m1));
+      t.x.combf[32 * c2 + lane] = make_float2(m2.s, -Acc<A>::err(m2));
+    } else {
+      t.x.combd[32 * c0 + lane] = m0.s;
+      t.x.combd[32 * c1 + lane] = m1.s;
+      t.x.combd[32 * c2 + lane] = m2.s;
+    }
+    if (lane == 0) {
+      if (warp < 3) t.msh[warp] = static_cast<double>(sa);
+      else { t.msh[3] = static_cast<double>(sa); t.msh[4] = static_cast<double>(sb); }
+    }
+    __syncwarp();
+    if (lane < 3) {
+      const int c = lane == 0 ? c0 : lane == 1 ? c1 : c2;
+      if constexpr (sizeof(A) == 4) {
+        // the 32 lanes' (value, error) pairs in lane order: exact two-sums of the values,
+        // the errors added
+        float h = 0.0f, l = 0.0f;
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) {
+          const float2 pv = t.x.combf[32 * c + i];
+          const float sh = h + pv.x;
+          const float bb = sh - h;
+          const float se = (h - (sh - bb)) + (pv.x - bb);
+          l += se + pv.y;
+          h = sh;
+        }
+        t.mh[c] = h;
+        t.ml[c] = l;
+      } else {
+        double h = 0.0;
+#pragma unroll 4
+        for (int i = 0; i < 32; ++i) h += t.x.combd[32 * c + i];
+        t.mh[c] = h;
+        t.ml[c] = 0.0;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// One element of N <= CAP particles by a block of THREADS (hierarchical bins).
+template <typename T, int CAP, int THREADS>
+__device__ void element_rank_tile(const StatsArgs<T>& a, RankTile<T, CAP, THREADS>& t, int e, int N,
+                                  int moves) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const unsigned below = (1u << lane) - 1u;
+  constexpr int KPT = CAP / THREADS;
+  // gather: the element's list minus particles moved out, plus those moved in.  The list
+  // entries (and the moved-out test) of a thread's first KPT rounds are loaded before any is
+  // used, so that they are in flight together.
+  if (threadIdx.x == 0) t.n_gathered = 0;
+  __syncthreads();
+  {
+    const int32_t o = a.off[e], c = a.cnt[e];
+    int32_t qk[KPT];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int j = warp * 32 + k * THREADS + lane;
+      qk[k] = j < c ? __ldg(a.idx + o + j) : -1;
+    }
+    if (moves) {
+      int32_t ek[KPT];
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) ek[k] = qk[k] >= 0 ? __ldg(a.p.elem + qk[k]) : e;
+#pragma unroll
+      for (int k = 0; k < KPT; ++k)
+        if (ek[k] != e) qk[k] = -1;
+    }
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int32_t q = qk[k];
+      const unsigned keep = __ballot_sync(kFull, q >= 0);
+      int base = 0;
+      if (lane == 0 && keep) base = atomicAdd(&t.n_gathered, __popc(keep));
+      base = __shfl_sync(kFull, base, 0);
+      const int at = base + __popc(keep & below);
+      if (q >= 0 && at < CAP) t.slot[at] = q;
+    }
+    // a list longer than the capacity (particles leave it by moves) continues one round at
+    // a time
+#pragma unroll 1
+    for (int j0 = warp * 32 + KPT * THREADS; j0 < c; j0 += THREADS) {
+      const int j = j0 + lane;
+      int32_t q = -1;
+      if (j < c) {
+        q = a.idx[o + j];
+        if (moves && a.p.elem[q] != e) q = -1;
+      }
+      const unsigned keep = __ballot_sync(kFull, q >= 0);
+      int base = 0;
+      if (lane == 0 && keep) base = atomicAdd(&t.n_gathered, __popc(keep));
+      base = __shfl_sync(kFull, base, 0);
+      const int at = base + __popc(keep & below);
+      if (q >= 0 && at < CAP) t.slot[at] = q;
+    }
+    if (moves) {
+      const int32_t gn = a.gain[e], g0 = a.goff[e];
+#pragma unroll 1
+      for (int j0 = warp * 32; j0 < gn; j0 += THREADS) {
+        const int j = j0 + lane;
+        int32_t q = j < gn ? a.movers[g0 + j] : -1;
+        if (q >= a.np) q = -1;
+        const unsigned keep = __ballot_sync(kFull, q >= 0);
+        int base = 0;
+        if (lane == 0 && keep) base = atomicAdd(&t.n_gathered, __popc(keep));
+        base = __shfl_sync(kFull, base, 0);
+        const int at = base + __popc(keep & below);
+        if (q >= 0 && at < CAP) t.slot[at] = q;
+      }
+    }
+  }
+  __syncthreads();
+  int n = t.n_gathered;
+  if (n != N && threadIdx.x == 0) atomicCAS(a.err, 0, PDFX_ERR_CAPACITY);
+  n = min(min(n, N), CAP);
+  // stage the element's values and ids: every load of a thread before any store (the
+  // particle arrays are read only here), so that they are in flight together
+  {
+    T vu[KPT], vv[KPT], vw[KPT], vo[KPT], vp[KPT];
+    uint32_t vi[KPT];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int j = threadIdx.x + k * THREADS;
+      if (j < n) {
+        const int32_t q = t.slot[j];
+        vu[k] = __ldg(a.p.u + q);
+        vv[k] = __ldg(a.p.v + q);
+        vw[k] = __ldg(a.p.w + q);
+        vo[k] = __ldg(a.p.om + q);
+        vp[k] = __ldg(a.p.psi + q);
+        vi[k] = __ldg(a.p.pid + q);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int j = threadIdx.x + k * THREADS;
+      if (j < n) {
+        t.u[j] = vu[k];
+        t.v[j] = vv[k];
+        t.w[j] = vw[k];
+        t.om[j] = vo[k];
+        t.psi[j] = vp[k];
+        t.pid[j] = vi[k];
+      }
+    }
+  }
+  // effective bins (reading of Sect. 3.5): g_l = max(1, min(b_l, n / (g_1..g_{l-1} min_per_bin)))
+  int g[3];
+  {
+    int Gp = 1;
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      const int capl = n / (Gp * a.min_per_bin);
+      int gl = a.bins[l] < capl ? a.bins[l] : capl;
+      if (gl < 1) gl = 1;
+      g[l] = gl;
+      Gp *= gl;
+    }
+  }
+  __syncthreads();
+  // levels by (u, id), (v, id), (w, id) within the groups of the previous level; the levels
+  // before the last need only the groups, the last gives the final order
+  if (n > 0) {
+    int last = 0;
+    for (int l = 1; l < 3; ++l)
+      if (g[l] > 1) last = l;
+    int Gprev = 1;
+#pragma unroll 1
+    for (int l = 0; l <= last; ++l) {
+      if (l > 0 && g[l] <= 1) continue;
+      const T* key = l == 0 ? t.u : (l == 1 ? t.v : t.w);
+      float pm = 0.0f, ps = 0.0f;   // the key's mean and standard deviation of the last pass
+      if (a.prior) {
+        const double* em = a.emom + static_cast<size_t>(kNS) * e;
+        const double m = em[1 + l], var = em[4 + l];
+        if (em[0] >= 2.0 && var > 0.0 && fabs(m) < 1e30 && var < 1e60) {
+          pm = static_cast<float>(m);
+          ps = static_cast<float>(sqrt(var));
+        }
+      }
+      if (l == last) order_level<T, CAP, THREADS>(t, key, n, Gprev, pm, ps);
+      else group_level<T, CAP, THREADS>(t, key, n, Gprev, Gprev * g[l], pm, ps);
+      Gprev *= g[l];
+    }
+  }
+  const int G = g[0] * g[1] * g[2];
+  // moments in the final order, then the 13 outputs in FP64 (one per lane of warp 0)
+  if (sizeof(T) == 4 && a.acc64) rank_moments<double>(t, n);
+  else rank_moments<T>(t, n);
+  if (warp == 0) {
+    if (lane < kNS) {
+      const double inv = n > 0 ? 1.0 / n : 0.0;
+      const int ix = mom_nib(kMomX, lane), iy = mom_nib(kMomY, lane);
+      const int iz = mom_nib(kMomZ, lane), iw = mom_nib(kMomW, lane);
+      double v = ix < 15 ? t.msh[ix] : 0.0;
+      if (iy < 15) v += (t.mh[iy] + t.ml[iy]) * inv;
+      if (iz < 15) {
+        const double z = (t.mh[iz] + t.ml[iz]) * inv;
+        const double wv = (t.mh[iw] + t.ml[iw]) * inv;
+        v -= z * wv;
+      }
+      if (lane == 0) v = static_cast<double>(n);
+      else if (n == 0) v = 0.0;
+      a.emom[static_cast<size_t>(kNS) * e + lane] = v;
+    }
+    if (lane < 3) a.gbin[3 * e + lane] = g[lane];
+  }
+  // Appendix A bins: conditional scalar means over the final order's bins
+  double* vc = a.vcce + static_cast<size_t>(a.G) * e;
+  const float invGb = 1.0f / static_cast<float>(G);
+  for (int i = threadIdx.x; i < a.G; i += THREADS) {
+    double mval = 0.0;
+    if (i < G && n > 0) {
+      const int b0 = group_start(i, n, G, invGb), b1 = group_start(i + 1, n, G, invGb);
+      if (sizeof(T) == 4 && a.acc64) {
+        double sum = 0.0;
+#pragma unroll 1
+        for (int p = b0; p < b1; ++p) sum += static_cast<double>(t.psi[t.ord[p]]);
+        mval = sum / static_cast<double>(b1 - b0);
+      } else {
+        Acc<T> sum;
+#pragma unroll 1
+        for (int p = b0; p < b1; ++p) sum.add(t.psi[t.ord[p]]);
+        mval = static_cast<double>(sum.value() / static_cast<T>(b1 - b0));
+      }
+    }
+    vc[i] = mval;
+  }
+  // conditioning pointers (and the element-ordered copy of the state every few steps)
+  const float inv_n = n > 0 ? 1.0f / static_cast<float>(n) : 0.0f;
+  if (a.resort) {
+    const int32_t fo = a.foff[e];
+    T vx[KPT], vy[KPT];
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int p = threadIdx.x + k * THREADS;
+      if (p < n) {
+        const int32_t q = t.slot[t.ord[p]];
+        vx[k] = __ldg(a.p.x + q);
+        vy[k] = __ldg(a.p.y + q);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < KPT; ++k) {
+      const int p = threadIdx.x + k * THREADS;
+      const int32_t d = fo + p;
+      if (p >= n || d >= a.np) break;
+      const int j = t.ord[p];
+      a.out.x[d] = vx[k];
+      a.out.y[d] = vy[k];
+      a.out.u[d] = t.u[j];
+      a.out.v[d] = t.v[j];
+      a.out.w[d] = t.w[j];
+      a.out.om[d] = t.om[j];
+      a.out.psi[d] = t.psi[j];
+      a.out.pid[d] = t.pid[j];
+      a.out.elem[d] = e;
+      a.out.cp[d] = static_cast<uint8_t>(fdiv(G * p, inv_n));
+    }
+  } else {
+    for (int j = threadIdx.x; j < n; j += THREADS)
+      a.p.cp[t.slot[j]] = static_cast<uint8_t>(fdiv(G * t.pos[j], inv_n));
+  }
+}
+
+// Residency: the FP32 tiles (21 KB per 128 threads) fit 1280 threads per SM, the FP64
+// tiles 896; the register cap matches.
+template <typename T, int CAP, int THREADS, bool FRONT>
+__global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1280 : 1024) / THREADS)
+    rank_tile_kernel(const StatsArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char rank_smem[];
+  RankTile<T, CAP, THREADS>& t = *reinterpret_cast<RankTile<T, CAP, THREADS>*>(rank_smem);
+  const int b = blockIdx.x;
+  if (FRONT && b == 0 && threadIdx.x == 0 && a.step_inc) atomicAdd(a.step_inc, 1u);
+  const int inst = a.einst ? a.einst[b] : 0;
+  const int eb = a.einst ? a.ielem[inst] : 0, ee = a.einst ? a.ielem[inst + 1] : a.ne;
+  const int32_t* sc = a.scal + 16 * inst;
+  if (FRONT ? (b - eb >= sc[6]) : (ee - 1 - b >= sc[7])) return;
+  const int moves = sc[0] > 0;
+  const int e = a.tiles[b];
+  const int N = moves ? a.fin[e] : a.cnt[e];
+  element_rank_tile<T, CAP, THREADS>(a, t, e, min(N, CAP), moves);
+}
+
+template <typename T> bool rank_configured[kMaxDevices];
+
 // One block per entry of one size class of the plan's tile lists: the elements of up to
 // kTileSplit particles (FRONT) or of kTileSplit + 1 .. kSmallCap (the back of each
 // instance's list).  The grid covers every element; blocks past the class count return.  The register cap
@@ -785,8 +1379,16 @@ void launch_stats_tiles_impl(const StatsArgs<T>& a, int num_sms, cudaStream_t s)
     stats_tile_kernel<T, 512, 128, true, true><<<grid, 128, 0, s>>>(a);
     stats_tile_kernel<T, 1024, 256, false, true><<<grid, 256, 0, s>>>(a);
   } else {
-    stats_tile_kernel<T, 512, 128, true, false><<<grid, 128, 0, s>>>(a);
-    stats_tile_kernel<T, 1024, 256, false, false><<<grid, 256, 0, s>>>(a);
+    constexpr size_t small = sizeof(RankTile<T, 512, 128>), large = sizeof(RankTile<T, 1024, 256>);
+    static_assert(large <= 227 * 1024, "rank tile exceeds shared memory");
+    if (first_use_on_device(rank_configured<T>)) {
+      cudaFuncSetAttribute(rank_tile_kernel<T, 512, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(small));
+      cudaFuncSetAttribute(rank_tile_kernel<T, 1024, 256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(large));
+    }
+    rank_tile_kernel<T, 512, 128, true><<<grid, 128, small, s>>>(a);
+    rank_tile_kernel<T, 1024, 256, false><<<grid, 256, large, s>>>(a);
   }
 }
 

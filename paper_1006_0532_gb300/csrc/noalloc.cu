@@ -127,6 +127,7 @@ int element_stats_noalloc(Ctx& c, int64_t np, const double* u, const double* v, 
   a.min_per_bin = c.prm.min_per_bin;
   a.G = c.G;
   a.acc64 = 0;                      // FP64 throughout
+  a.prior = 0;                      // the caller's emom holds no previous statistics
   a.cond_mode = c.prm.cond_mode;    // the context's conditioning: bins or Fox's projection
   a.fox_bins = c.prm.fox_bins;
   a.emom = emom;

@@ -109,6 +109,9 @@ struct StatsArgs {
   int32_t* gbin;
   uint32_t* step_inc;    // stepping: the step counter, advanced once after this step's reads
   int acc64;             // FP32 form: accumulate moments and conditional means in FP64
+  int prior;             // emom holds the previous statistics pass of the same grid (the
+                         // binning takes its bucket scales from them; results do not depend
+                         // on it)
   int cond_mode;         // 0 hierarchical bins (Sect. 3.5); 1 Fox's projection (Eqs. 64-66)
   int fox_bins;          // intervals of the projected velocity (cond_mode 1)
   unsigned long long* diag;
