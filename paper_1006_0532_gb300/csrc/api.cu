@@ -82,6 +82,9 @@ Model<T> model_of(const pdfx_params& p) {
   m.Cw1 = T(p.Cw1); m.Cw2 = T(p.Cw2); m.nu = T(p.nu); m.C0 = T(p.C0); m.Cs = T(p.Cs);
   m.Ct = T(p.Ct); m.Cphi = T(p.Cphi); m.src_x = T(p.src_x); m.src_y = T(p.src_y);
   m.src_r = T(p.src_r); m.period_x = T(p.period_x);
+  // FP32 form: the source centre as hi + lo pairs (the particle positions are pairs)
+  m.src_xl = T(p.src_x - static_cast<double>(m.src_x));
+  m.src_yl = T(p.src_y - static_cast<double>(m.src_y));
   m.nuCT2 = T(p.nu * p.CT * p.CT);
   m.s2nu = T(std::sqrt(2.0 * p.nu));
   m.cs_r2 = T(p.Cs * std::cbrt(p.src_r * p.src_r));
@@ -180,6 +183,10 @@ Particles<T> carve(void* base, int64_t np) {
   p.pid = reinterpret_cast<uint32_t*>(step(4 * n));
   p.elem = reinterpret_cast<int32_t*>(step(4 * n));
   p.cp = reinterpret_cast<uint8_t*>(step(n));
+  if (sizeof(T) == 4) {   // the positions' trailing parts
+    p.xl = reinterpret_cast<T*>(step(sizeof(T) * n));
+    p.yl = reinterpret_cast<T*>(step(sizeof(T) * n));
+  }
   return p;
 }
 
@@ -187,7 +194,7 @@ template <typename T>
 size_t particle_bytes(int64_t np) {
   const size_t n = static_cast<size_t>(np > 0 ? np : 1);
   auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
-  return 7 * r(sizeof(T) * n) + r(4 * n) + r(4 * n) + r(n);
+  return (sizeof(T) == 4 ? 9 : 7) * r(sizeof(T) * n) + r(4 * n) + r(4 * n) + r(n);
 }
 
 // ---- profiling ----------------------------------------------------------------------------
@@ -485,19 +492,42 @@ int do_get_particles(Ctx& c, pdfx_soa* soa, int on_device, cudaStream_t s) {
   return rc;
 }
 
+// Element geometry in the working precision: node coordinates (canonical x) and 1 / (2 A_e);
+// the FP32 form stores each coordinate as an FP32 pair.
+void geo_of(const HostGeo& g, int32_t e, ElemGeo<double>& o) {
+  for (int k = 0; k < 3; ++k) {
+    o.x[k] = g.nx[3 * e + k];
+    o.y[k] = g.vy[3 * e + k];
+  }
+  o.inv2a = 1.0 / g.area2[e];
+  o.pad = 0.0;
+}
+void geo_of(const HostGeo& g, int32_t e, ElemGeo<float>& o) {
+  for (int k = 0; k < 3; ++k) {
+    pair_of(g.nx[3 * e + k], o.xh[k], o.xl[k]);
+    pair_of(g.vy[3 * e + k], o.yh[k], o.yl[k]);
+  }
+  o.inv2a = static_cast<float>(1.0 / g.area2[e]);
+  o.pad[0] = o.pad[1] = o.pad[2] = 0.0f;
+}
+void line_of(const double* src, Line<double>& o) {
+  o.px = src[0]; o.py = src[1]; o.nx = src[2]; o.ny = src[3];
+}
+void line_of(const double* src, Line<float>& o) {
+  pair_of(src[0], o.px, o.pxl);
+  pair_of(src[1], o.py, o.pyl);
+  o.nx = static_cast<float>(src[2]);
+  o.ny = static_cast<float>(src[3]);
+  o.pad0 = o.pad1 = 0.0f;
+}
+
 template <typename T>
 int upload_grid(Ctx& c, const HostGeo& g, const std::vector<ElemTopo>& topo,
                 const std::vector<double>& walls, const std::vector<double>& fsl,
                 const std::vector<double>& fse) {
   const int32_t ne = c.ne;
   std::vector<ElemGeo<T>> hg(static_cast<size_t>(ne));
-  for (int32_t e = 0; e < ne; ++e) {
-    hg[e].x0 = T(g.nx[3 * e]); hg[e].y0 = T(g.vy[3 * e]);
-    hg[e].x1 = T(g.nx[3 * e + 1]); hg[e].y1 = T(g.vy[3 * e + 1]);
-    hg[e].x2 = T(g.nx[3 * e + 2]); hg[e].y2 = T(g.vy[3 * e + 2]);
-    hg[e].inv2a = T(1.0 / g.area2[e]);
-    hg[e].pad = T(0);
-  }
+  for (int32_t e = 0; e < ne; ++e) geo_of(g, e, hg[e]);
   dev_free(c, c.geo);
   c.geo = dev_alloc(c, sizeof(ElemGeo<T>) * ne);
   if (!c.geo) return PDFX_ERR_ALLOC;
@@ -510,10 +540,7 @@ int upload_grid(Ctx& c, const HostGeo& g, const std::vector<ElemTopo>& topo,
     const size_t nl = src.size() / 4;
     if (which == 0) c.n_wall_lines = static_cast<int>(nl);
     std::vector<Line<T>> hl(nl ? nl : 1);
-    for (size_t i = 0; i < nl; ++i) {
-      hl[i].px = T(src[4 * i]); hl[i].py = T(src[4 * i + 1]);
-      hl[i].nx = T(src[4 * i + 2]); hl[i].ny = T(src[4 * i + 3]);
-    }
+    for (size_t i = 0; i < nl; ++i) line_of(&src[4 * i], hl[i]);
     dev_free(c, dst);
     dst = dev_alloc(c, sizeof(Line<T>) * hl.size());
     if (!dst) return PDFX_ERR_ALLOC;

@@ -735,8 +735,7 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP, FOX>& t, int e,
       const int32_t d = fo + p;
       if (d >= a.np) break;
       const int32_t q = cur[p];
-      a.out.x[d] = a.p.x[q];
-      a.out.y[d] = a.p.y[q];
+      store_pos(a.out, d, load_pos(a.p, q));
       a.out.u[d] = a.p.u[q];
       a.out.v[d] = a.p.v[q];
       a.out.w[d] = a.p.w[q];
@@ -1290,15 +1289,11 @@ __device__ void element_rank_tile(const StatsArgs<T>& a, RankTile<T, CAP, THREAD
   const float inv_n = n > 0 ? 1.0f / static_cast<float>(n) : 0.0f;
   if (a.resort) {
     const int32_t fo = a.foff[e];
-    T vx[KPT], vy[KPT];
+    Pos<T> vx[KPT];
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
       const int p = threadIdx.x + k * THREADS;
-      if (p < n) {
-        const int32_t q = t.slot[t.ord[p]];
-        vx[k] = __ldg(a.p.x + q);
-        vy[k] = __ldg(a.p.y + q);
-      }
+      if (p < n) vx[k] = load_pos(a.p, t.slot[t.ord[p]]);
     }
 #pragma unroll
     for (int k = 0; k < KPT; ++k) {
@@ -1306,8 +1301,7 @@ __device__ void element_rank_tile(const StatsArgs<T>& a, RankTile<T, CAP, THREAD
       const int32_t d = fo + p;
       if (p >= n || d >= a.np) break;
       const int j = t.ord[p];
-      a.out.x[d] = vx[k];
-      a.out.y[d] = vy[k];
+      store_pos(a.out, d, vx[k]);
       a.out.u[d] = t.u[j];
       a.out.v[d] = t.v[j];
       a.out.w[d] = t.w[j];

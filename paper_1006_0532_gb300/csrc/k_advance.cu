@@ -18,9 +18,9 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 
 template <typename T>
-__device__ __forceinline__ bool inside(const ElemGeo<T>& g, const ElemTopo& t, T x, T y, T L) {
+__device__ __forceinline__ bool inside(const ElemGeo<T>& g, const ElemTopo& t, const Pos<T>& P, T L) {
   T na, nb, nc;
-  area_cross(g, t.n0, t.n1, t.n2, x, y, L, na, nb, nc);
+  area_cross(g, t.n0, t.n1, t.n2, P, L, na, nb, nc);
   return na >= T(0) && nb >= T(0) && nc >= T(0);
 }
 
@@ -32,7 +32,7 @@ __device__ __forceinline__ bool inside(const ElemGeo<T>& g, const ElemTopo& t, T
 // elements around the nodes of the old host element (lowest containing id), then all
 // elements.
 template <typename T>
-__device__ int walk(const AdvanceArgs<T>& a, int e0, T& x, T& y, T (&U)[3], T L, int& hops,
+__device__ int walk(const AdvanceArgs<T>& a, int e0, Pos<T>& P, T (&U)[3], T L, int& hops,
                     int& fb, int& brute, int& refl) {
   int e = e0;
   hops = 0;
@@ -40,7 +40,7 @@ __device__ int walk(const AdvanceArgs<T>& a, int e0, T& x, T& y, T (&U)[3], T L,
     const ElemGeo<T> g = a.geo[e];
     const ElemTopo t = a.topo[e];
     T la, lb, lc;   // 2 N^k: signs and order of the area coordinates
-    area_cross(g, t.n0, t.n1, t.n2, x, y, L, la, lb, lc);
+    area_cross(g, t.n0, t.n1, t.n2, P, L, la, lb, lc);
     if (la >= T(0) && lb >= T(0) && lc >= T(0)) return e;
     if (hops >= kHopLimit) break;
     int k = 0;
@@ -51,10 +51,9 @@ __device__ int walk(const AdvanceArgs<T>& a, int e0, T& x, T& y, T (&U)[3], T L,
     if (nb < 0) {
       if (nb == -1) break;
       const Line<T> ln = a.fsedges[-2 - nb];
-      const T d = min_image(x - ln.px, L) * ln.nx + (y - ln.py) * ln.ny;
+      const T d = line_dist(ln, P, L);
       if (!(d < T(0))) break;
-      x -= T(2) * d * ln.nx;
-      y -= T(2) * d * ln.ny;
+      pos_reflect(P, d, ln.nx, ln.ny);
       const T un = U[0] * ln.nx + U[1] * ln.ny;
       U[0] -= T(2) * un * ln.nx;
       U[1] -= T(2) * un * ln.ny;
@@ -74,7 +73,7 @@ __device__ int walk(const AdvanceArgs<T>& a, int e0, T& x, T& y, T (&U)[3], T L,
     for (int i = a.ne_off[nd]; i < a.ne_off[nd + 1]; ++i) {
       const int f = a.ne_list[i];
       if (best >= 0 && f >= best) continue;
-      if (inside(a.geo[f], a.topo[f], x, y, L)) best = f;
+      if (inside(a.geo[f], a.topo[f], P, L)) best = f;
     }
   }
   if (best >= 0) return best;
@@ -117,6 +116,8 @@ __device__ __forceinline__ float texp(float x) { return expf(x); }
 
 template <typename T>
 __device__ __forceinline__ bool finite(T v) { return isfinite(v); }
+__device__ __forceinline__ double pos_lead(const Pos<double>& P) { return P.x + P.y; }
+__device__ __forceinline__ float pos_lead(const Pos<float>& P) { return P.xh + P.yh; }
 
 __device__ __forceinline__ void warp_count(unsigned long long* diag, int slot, int v) {
   const unsigned s = __reduce_add_sync(kFull, static_cast<unsigned>(v));
@@ -137,37 +138,36 @@ struct StepFlags {
 // element.
 template <typename T>
 __device__ __forceinline__ int finish_update(const AdvanceArgs<T>& a, const Model<T>& M, int64_t i,
-                                             int e, const ElemTopo& tp, T Xn, T Yn, T (&Un)[3],
+                                             int e, const ElemTopo& tp, Pos<T> Pn, T (&Un)[3],
                                              T wn, T psin, StepFlags& f) {
   const T L = M.period_x;
   if (tp.fslip >= 0) {
     const Line<T> ln = a.fslines[tp.fslip];
-    const T d1 = min_image(Xn - ln.px, L) * ln.nx + (Yn - ln.py) * ln.ny;
+    const T d1 = line_dist(ln, Pn, L);
     if (d1 < T(0)) {
       f.fs = 1;
-      Xn -= T(2) * d1 * ln.nx;
-      Yn -= T(2) * d1 * ln.ny;
+      pos_reflect(Pn, d1, ln.nx, ln.ny);
       const T un = Un[0] * ln.nx + Un[1] * ln.ny;
       Un[0] -= T(2) * un * ln.nx;
       Un[1] -= T(2) * un * ln.ny;
     }
   }
-  Xn = wrap_period(Xn, L);
+  pos_wrap(Pn, L);
   // a sum of finite terms of this size is finite; a NaN or infinity anywhere is not
-  if (!finite(Xn + Yn + Un[0] + Un[1] + Un[2] + wn + psin)) f.nf = 1;
+  if (!finite(pos_lead(Pn) + Un[0] + Un[1] + Un[2] + wn + psin)) f.nf = 1;
 
   int hops = 0, fb = 0, brute = 0, refl = 0;
-  int e_new = walk(a, e, Xn, Yn, Un, L, hops, fb, brute, refl);
+  int e_new = walk(a, e, Pn, Un, L, hops, fb, brute, refl);
   f.hops = hops;
   f.fb = fb;
   f.brute = brute;
   f.hop_bin = hops < 7 ? hops : 7;
   if (refl) {
     f.fs = 1;
-    Xn = wrap_period(Xn, L);
+    pos_wrap(Pn, L);
   }
   if (M.source_on) {
-    const T sx = min_image(Xn - M.src_x, L), sy = Yn - M.src_y;
+    const T sx = rel_x(Pn, M.src_x, M.src_xl, L), sy = rel_y(Pn, M.src_y, M.src_yl);
     if (sx * sx + sy * sy <= M.src_r * M.src_r) { psin = T(1); f.src = 1; }
   }
   if (e_new < 0) {
@@ -178,8 +178,7 @@ __device__ __forceinline__ int finish_update(const AdvanceArgs<T>& a, const Mode
     else f.lost = 1;
   }
 
-  a.p.x[i] = Xn;
-  a.p.y[i] = Yn;
+  store_pos(a.p, i, Pn);
   a.p.u[i] = Un[0];
   a.p.v[i] = Un[1];
   a.p.w[i] = Un[2];
@@ -236,7 +235,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
     const Model<T>& M = BATCH ? a.inst[ki].m : a.m;
     const uint32_t k0 = BATCH ? a.inst[ki].k0 : a.k0, k1 = BATCH ? a.inst[ki].k1 : a.k1;
     const T L = M.period_x;
-    const T X0 = a.p.x[i], Y0 = a.p.y[i];
+    const Pos<T> P0 = load_pos(a.p, i);
     const T U0[3] = {a.p.u[i], a.p.v[i], a.p.w[i]};
     const T w0 = a.p.om[i], psi0 = a.p.psi[i];
     const uint32_t pid = a.p.pid[i];
@@ -249,7 +248,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
     if (M.interp_mode == 1) {
       la = lb = lc = T(1) / T(3);
     } else {
-      area_coords(g, tp.n0, tp.n1, tp.n2, X0, Y0, L, la, lb, lc);
+      area_coords(g, tp.n0, tp.n1, tp.n2, P0, L, la, lb, lc);
     }
     T q[kNF];
     interp_fields(a.fields, tp.n0, tp.n1, tp.n2, la, lb, lc, q);
@@ -294,7 +293,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
     } else {
       const T kt = k * ieps, kol = M.CT * sqrt(M.nu * ieps);
       const T a2 = kt > kol ? kt : kol;
-      const T ddx = min_image(X0 - M.src_x, L), ddy = Y0 - M.src_y;
+      const T ddx = rel_x(P0, M.src_x, M.src_xl, L), ddy = rel_y(P0, M.src_y, M.src_yl);
       const T Uc2 = Um[0] * Um[0] + Um[1] * Um[1] + Um[2] * Um[2];
       T tm = a2;
       if (Uc2 > T(0)) {
@@ -336,8 +335,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
       Un[r] = base + gsum * ik * dt + sc0e * xi[2 + r];
     }
     // Eq. 7 (same dW as Eq. 27)
-    T Xn = X0 + U0[0] * dt + s2nu * dWx;
-    T Yn = Y0 + U0[1] * dt + s2nu * dWy;
+    Pos<T> Pn = P0;
+    pos_move(Pn, U0[0], U0[1], dt, s2nu, dWx, dWy);
     // Eq. 19, reflected at zero
     const T wpos = w0 > T(0) ? w0 : T(0);
     T wn = w0 - M.C3 * Om * (w0 - Om) * dt - Somega * Om * w0 * dt +
@@ -356,8 +355,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
       for (int j = 0; j < 2; ++j) {
         if (lines[j] < 0) break;
         const Line<T> ln = a.walls[lines[j]];
-        const T d0 = min_image(X0 - ln.px, L) * ln.nx + (Y0 - ln.py) * ln.ny;
-        const T d1 = min_image(Xn - ln.px, L) * ln.nx + (Yn - ln.py) * ln.ny;
+        const T d0 = line_dist(ln, P0, L);
+        const T d1 = line_dist(ln, Pn, L);
         bool hit;
         if (d1 < T(0)) {
           hit = true;
@@ -367,7 +366,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
         }
         if (hit) {
           any_hit = true;
-          if (d1 < T(0)) { Xn -= T(2) * d1 * ln.nx; Yn -= T(2) * d1 * ln.ny; }
+          if (d1 < T(0)) pos_reflect(Pn, d1, ln.nx, ln.ny);
         }
       }
       if (any_hit) {
@@ -378,7 +377,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
         f.gex = ex;
       }
     }
-    e_new = finish_update(a, M, i, e, tp, Xn, Yn, Un, wn, psin, f);
+    e_new = finish_update(a, M, i, e, tp, Pn, Un, wn, psin, f);
   }
   count_update(a, valid, e_new, f);
 }
@@ -400,14 +399,14 @@ __global__ void __launch_bounds__(256) simple_advance_kernel(const AdvanceArgs<T
     const int ki = BATCH ? a.einst[e] : 0;
     const Model<T>& M = BATCH ? a.inst[ki].m : a.m;
     const uint32_t k0 = BATCH ? a.inst[ki].k0 : a.k0, k1 = BATCH ? a.inst[ki].k1 : a.k1;
-    const T X0 = a.p.x[i], Y0 = a.p.y[i];
+    const Pos<T> P0 = load_pos(a.p, i);
     const T U0[3] = {a.p.u[i], a.p.v[i], a.p.w[i]};
     const ElemTopo tp = a.topo[e];
     T la, lb, lc;
     if (M.interp_mode == 1) {
       la = lb = lc = T(1) / T(3);
     } else {
-      area_coords(a.geo[e], tp.n0, tp.n1, tp.n2, X0, Y0, M.period_x, la, lb, lc);
+      area_coords(a.geo[e], tp.n0, tp.n1, tp.n2, P0, M.period_x, la, lb, lc);
     }
     const double* m0 = a.nmom + static_cast<size_t>(kNS) * tp.n0;
     const double* m1 = a.nmom + static_cast<size_t>(kNS) * tp.n1;
@@ -424,9 +423,9 @@ __global__ void __launch_bounds__(256) simple_advance_kernel(const AdvanceArgs<T
       const T Um = la * T(m0[1 + r]) + lb * T(m1[1 + r]) + lc * T(m2[1 + r]);
       Un[r] = U0[r] - (U0[r] - M.alpha * Um) * dt + s2dt * xi[r];
     }
-    const T Xn = X0 + U0[0] * dt;
-    const T Yn = Y0 + U0[1] * dt;
-    e_new = finish_update(a, M, i, e, tp, Xn, Yn, Un, a.p.om[i], a.p.psi[i], f);
+    Pos<T> Pn = P0;
+    pos_add(Pn, U0[0] * dt, U0[1] * dt);
+    e_new = finish_update(a, M, i, e, tp, Pn, Un, a.p.om[i], a.p.psi[i], f);
   }
   count_update(a, valid, e_new, f);
 }
@@ -441,13 +440,13 @@ __global__ void __launch_bounds__(256) brute_search_kernel(AdvanceArgs<T> a) {
   const int n = min(*a.brute_count, a.brute_cap);
   for (int j = blockIdx.x; j < n; j += gridDim.x) {
     const int32_t i = a.brute_list[j];
-    const T x = a.p.x[i], y = a.p.y[i];
+    const Pos<T> P = load_pos(a.p, i);
     const int ki = BATCH ? a.einst[a.p.elem[i]] : 0;
     const int f0 = BATCH ? a.inst[ki].e0 : 0, f1 = BATCH ? a.inst[ki].e1 : a.ne;
     const T L = BATCH ? a.inst[ki].m.period_x : a.m.period_x;
     int best = 0x7fffffff;
     for (int f = f0 + threadIdx.x; f < f1; f += blockDim.x)
-      if (f < best && inside(a.geo[f], a.topo[f], x, y, L)) best = f;
+      if (f < best && inside(a.geo[f], a.topo[f], P, L)) best = f;
     for (int o = 16; o > 0; o >>= 1) best = min(best, __shfl_xor_sync(kFull, best, o));
     if ((threadIdx.x & 31) == 0) best_s[threadIdx.x >> 5] = best;
     __syncthreads();
@@ -466,8 +465,8 @@ __global__ void __launch_bounds__(256) brute_search_kernel(AdvanceArgs<T> a) {
         const unsigned long long k = atomicAdd(a.diag + kDiagLostRecord, 1ull);
         if (k < kLostRecords) {
           double* rec = a.lost_rec + 4 * k;
-          rec[0] = static_cast<double>(x);
-          rec[1] = static_cast<double>(y);
+          rec[0] = pos_x(P);
+          rec[1] = pos_y(P);
           rec[2] = static_cast<double>(e0);
           rec[3] = static_cast<double>(a.p.pid[i]);
         }
@@ -493,13 +492,12 @@ __device__ __forceinline__ int init_one(Particles<T> p, int64_t i, int e, uint32
     const ElemTopo tp = topo[e];
     const T s = sqrt(uniform01(r0.x, T(0)));
     const T t = uniform01(r0.y, T(0));
-    T px, py;
-    triangle_point(g, s, t, m.period_x, px, py);
+    Pos<T> P = triangle_point(g, s, t, m.period_x);
     T la, lb, lc;
     if (m.interp_mode == 1) {
       la = lb = lc = T(1) / T(3);
     } else {
-      area_coords(g, tp.n0, tp.n1, tp.n2, px, py, m.period_x, la, lb, lc);
+      area_coords(g, tp.n0, tp.n1, tp.n2, P, m.period_x, la, lb, lc);
     }
     T q[kNF];
     interp_fields(fields, tp.n0, tp.n1, tp.n2, la, lb, lc, q);
@@ -512,14 +510,13 @@ __device__ __forceinline__ int init_one(Particles<T> p, int64_t i, int e, uint32
     int ex = 0;
     const T om = gamma_draw<T>(k0, k1, pid, 0u, kPurInitGamma, T(1) / m.C4, m.C4 * q[29], &ex);
     c_gex = ex;
-    px = wrap_period(px, m.period_x);
+    pos_wrap(P, m.period_x);
     bool src = false;
     if (m.source_on) {
-      const T sx = min_image(px - m.src_x, m.period_x), sy = py - m.src_y;
+      const T sx = rel_x(P, m.src_x, m.src_xl, m.period_x), sy = rel_y(P, m.src_y, m.src_yl);
       src = sx * sx + sy * sy <= m.src_r * m.src_r;
     }
-    p.x[i] = px;
-    p.y[i] = py;
+    store_pos(p, i, P);
     p.u[i] = q[0] + sd * g0;
     p.v[i] = q[1] + sd * g1;
     p.w[i] = q[2] + sd * g2;
@@ -595,8 +592,9 @@ __global__ void gather_by_pid_kernel(Particles<T> p, int64_t np, const int32_t* 
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= np) return;
   const int64_t id = (einst ? ip0[einst[p.elem[i]]] : 0) + p.pid[i];
-  if (x) x[id] = p.x[i];
-  if (y) y[id] = p.y[i];
+  const Pos<T> P = load_pos(p, i);
+  if (x) x[id] = pos_x(P);
+  if (y) y[id] = pos_y(P);
   if (u) u[id] = p.u[i];
   if (v) v[id] = p.v[i];
   if (w) w[id] = p.w[i];
@@ -614,8 +612,7 @@ __global__ void load_state_kernel(Particles<T> p, int64_t np, const int32_t* ein
                                   int32_t ne, unsigned long long* diag, int* err) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= np) return;
-  p.x[i] = static_cast<T>(x[i]);
-  p.y[i] = static_cast<T>(y[i]);
+  store_pos(p, i, pos_of(x[i], y[i], T(0)));
   p.u[i] = static_cast<T>(u[i]);
   p.v[i] = static_cast<T>(v[i]);
   p.w[i] = static_cast<T>(w[i]);

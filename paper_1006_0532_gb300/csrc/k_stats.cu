@@ -350,7 +350,7 @@ __global__ void __launch_bounds__(kRedistThreads) apply_moves_kernel(
   const int32_t eb = pl.ielem ? pl.ielem[inst] : 0;
   const int32_t nrec = sc[0] > 0 ? sc[1] : 0;
   const Model<T>& mi = inst_tab[inst].m;
-  const T period_x = mi.period_x, sx = mi.src_x, sy = mi.src_y, sr = mi.src_r;
+  const T period_x = mi.period_x, sr = mi.src_r;
   const int source_on = mi.source_on;
   const uint32_t k0 = inst_tab[inst].k0, k1 = inst_tab[inst].k1;
   for (int32_t ri = blockIdx.x; ri < nrec; ri += gridDim.x) {
@@ -390,9 +390,8 @@ __global__ void __launch_bounds__(kRedistThreads) apply_moves_kernel(
       const uint4 rw = philox(make_uint4(pid, step, kPurRedist, 0u), k0, k1);
       const T s = sqrt(uniform01(rw.x, T(0)));
       const T t = uniform01(rw.y, T(0));
-      T px, py;
-      triangle_point(g, s, t, period_x, px, py);
-      px = wrap_period(px, period_x);
+      Pos<T> P = triangle_point(g, s, t, period_x);
+      pos_wrap(P, period_x);
       int32_t from = q;
       if (n > 0) {
         const double uu = uniform01(rw.z, 0.0);   // rank choice in double in both forms
@@ -401,15 +400,15 @@ __global__ void __launch_bounds__(kRedistThreads) apply_moves_kernel(
         from = sorted[jj];
       }
       double* mv = pl.mvals + static_cast<size_t>(k) * 7;
-      mv[0] = static_cast<double>(px);
-      mv[1] = static_cast<double>(py);
+      mv[0] = pos_x(P);
+      mv[1] = pos_y(P);
       mv[2] = static_cast<double>(p.u[from]);
       mv[3] = static_cast<double>(p.v[from]);
       mv[4] = static_cast<double>(p.w[from]);
       mv[5] = static_cast<double>(p.om[from]);
       bool insrc = false;
       if (source_on) {
-        const T ddx = min_image(px - sx, period_x), ddy = py - sy;
+        const T ddx = rel_x(P, mi.src_x, mi.src_xl, period_x), ddy = rel_y(P, mi.src_y, mi.src_yl);
         insrc = ddx * ddx + ddy * ddy <= sr * sr;
       }
       mv[6] = insrc ? 1.0 : static_cast<double>(p.psi[from]);
@@ -435,8 +434,7 @@ __global__ void commit_moves_kernel(Particles<T> p, Plan pl, int K, int64_t np, 
       continue;
     }
     const double* mv = pl.mvals + static_cast<size_t>(k) * 7;
-    p.x[q] = static_cast<T>(mv[0]);
-    p.y[q] = static_cast<T>(mv[1]);
+    store_pos(p, q, pos_of(mv[0], mv[1], T(0)));
     p.u[q] = static_cast<T>(mv[2]);
     p.v[q] = static_cast<T>(mv[3]);
     p.w[q] = static_cast<T>(mv[4]);
@@ -691,8 +689,7 @@ __device__ void process_element(const StatsArgs<T>& a, int e, int N, int cap, un
       const int32_t d = fo + j;
       if (d >= a.np) break;
       const int32_t src = s.slot[q];
-      a.out.x[d] = a.p.x[src];
-      a.out.y[d] = a.p.y[src];
+      store_pos(a.out, d, load_pos(a.p, src));
       a.out.u[d] = s.u[q];
       a.out.v[d] = s.v[q];
       a.out.w[d] = s.w[q];
@@ -849,10 +846,10 @@ __global__ void elem_gradient_kernel(const ElemGeo<T>* __restrict__ geo, const E
   const ElemGeo<T> g = geo[e];
   const ElemTopo t = topo[e];
   const double L = einst ? static_cast<double>(inst[einst[e]].m.period_x) : L0;
-  const double xBA = min_image(static_cast<double>(g.x1) - static_cast<double>(g.x0), L);
-  const double yBA = static_cast<double>(g.y1) - static_cast<double>(g.y0);
-  const double xCA = min_image(static_cast<double>(g.x2) - static_cast<double>(g.x0), L);
-  const double yCA = static_cast<double>(g.y2) - static_cast<double>(g.y0);
+  const double xBA = min_image(node_x(g, 1) - node_x(g, 0), L);
+  const double yBA = node_y(g, 1) - node_y(g, 0);
+  const double xCA = min_image(node_x(g, 2) - node_x(g, 0), L);
+  const double yCA = node_y(g, 2) - node_y(g, 0);
   const double inv = static_cast<double>(g.inv2a);
   const double dNx0 = (-yCA + yBA) * inv, dNx1 = yCA * inv, dNx2 = -yBA * inv;
   const double dNy0 = (xCA - xBA) * inv, dNy1 = -xCA * inv, dNy2 = xBA * inv;

@@ -26,11 +26,21 @@ enum Diag : int {
 constexpr int kLostRecords = 4;    // (x, y, old element, particle id) of the first lost particles
 constexpr int kBruteCap = 4096;    // particles per step that may need the brute-force search
 
-// Per-element geometry: the coordinates of the three nodes (x in [0, period)) and
-// 1 / (2 A_e).
+// Per-element geometry: the coordinates of the three nodes (x in [0, period), the canonical
+// image) and 1 / (2 A_e).  FP64 form: plain FP64.  FP32 form: each coordinate as an
+// unevaluated sum hi + lo of two FP32 numbers (about 48 significant bits), so that a
+// particle's offset from a node, and with it the area coordinates, keep FP32 precision
+// relative to the cell rather than to the domain (a first cell 4.6e-5 high at y = 1 is 770
+// FP32 spacings of y).
 template <typename T>
-struct __align__(sizeof(T) * 8) ElemGeo {
-  T x0, y0, x1, y1, x2, y2, inv2a, pad;
+struct ElemGeo;
+template <>
+struct __align__(64) ElemGeo<double> {
+  double x[3], y[3], inv2a, pad;
+};
+template <>
+struct __align__(16) ElemGeo<float> {
+  float xh[3], yh[3], xl[3], yl[3], inv2a, pad[3];
 };
 
 // Per-element topology: node ids, neighbour across the edge opposite each vertex (-1 = a
@@ -41,10 +51,29 @@ struct __align__(16) ElemTopo {
   int nb0, nb1, nb2, fslip;
 };
 
-// A boundary line: a point on it and the unit normal pointing into the domain.
+// A boundary line: a point on it and the unit normal pointing into the domain (FP32 form:
+// the point as hi + lo pairs).
 template <typename T>
-struct __align__(sizeof(T) * 4) Line {
-  T px, py, nx, ny;
+struct Line;
+template <>
+struct __align__(32) Line<double> {
+  double px, py, nx, ny;
+};
+template <>
+struct __align__(16) Line<float> {
+  float px, py, nx, ny, pxl, pyl, pad0, pad1;
+};
+
+// A particle position: FP64, or (FP32 form) each coordinate as hi + lo.
+template <typename T>
+struct Pos;
+template <>
+struct Pos<double> {
+  double x, y;
+};
+template <>
+struct Pos<float> {
+  float xh, xl, yh, yl;
 };
 
 // ---------------------------------------------------------------------------------------
@@ -121,7 +150,7 @@ __device__ T gamma_draw(uint32_t k0, uint32_t k1, uint32_t pid, uint32_t step, u
 }
 
 template <typename T>
-__device__ __forceinline__ T min_image(T d, T L) {
+__host__ __device__ __forceinline__ T min_image(T d, T L) {
   if (L > T(0)) {
     if (d > T(0.5) * L) return d - L;
     if (d < T(-0.5) * L) return d + L;
@@ -138,6 +167,125 @@ __device__ __forceinline__ T wrap_period(T x, T L) {
   return x;
 }
 
+// (h, l) += d for an FP32 pair: an exact two-sum of the leading parts (Knuth), the error
+// added to the trailing part, then renormalised (Dekker's fast two-sum), every operation
+// rounded on its own.
+__device__ __forceinline__ void pair_add(float& h, float& l, float d) {
+  const float s = __fadd_rn(h, d);
+  const float bb = __fsub_rn(s, h);
+  const float e = __fadd_rn(__fsub_rn(h, __fsub_rn(s, bb)), __fsub_rn(d, bb));
+  const float t = __fadd_rn(l, e);
+  h = __fadd_rn(s, t);
+  l = __fsub_rn(t, __fsub_rn(h, s));
+}
+// The FP32 pair nearest a double (hi = its FP32 rounding, lo = the FP32 rounding of the rest).
+__host__ __device__ __forceinline__ void pair_of(double v, float& h, float& l) {
+  h = static_cast<float>(v);
+  l = static_cast<float>(v - static_cast<double>(h));
+}
+__host__ __device__ __forceinline__ double pair_value(float h, float l) {
+  return static_cast<double>(h) + static_cast<double>(l);
+}
+
+// Node k's coordinates as FP64 (the FP32 form's pairs summed).
+__device__ __forceinline__ double node_x(const ElemGeo<double>& g, int k) { return g.x[k]; }
+__device__ __forceinline__ double node_y(const ElemGeo<double>& g, int k) { return g.y[k]; }
+__device__ __forceinline__ double node_x(const ElemGeo<float>& g, int k) { return pair_value(g.xh[k], g.xl[k]); }
+__device__ __forceinline__ double node_y(const ElemGeo<float>& g, int k) { return pair_value(g.yh[k], g.yl[k]); }
+
+// Node m minus node k (minimum image in x), in the working precision.
+__device__ __forceinline__ void node_vec(const ElemGeo<double>& g, int k, int m, double L, double& ex,
+                                         double& ey) {
+  ex = min_image(g.x[m] - g.x[k], L);
+  ey = g.y[m] - g.y[k];
+}
+__device__ __forceinline__ void node_vec(const ElemGeo<float>& g, int k, int m, float L, float& ex,
+                                         float& ey) {
+  ex = __fadd_rn(min_image(__fsub_rn(g.xh[m], g.xh[k]), L), __fsub_rn(g.xl[m], g.xl[k]));
+  ey = __fadd_rn(__fsub_rn(g.yh[m], g.yh[k]), __fsub_rn(g.yl[m], g.yl[k]));
+}
+// Particle minus node k (minimum image in x), in the working precision.
+__device__ __forceinline__ void node_rel(const ElemGeo<double>& g, int k, const Pos<double>& P, double L,
+                                         double& dx, double& dy) {
+  dx = min_image(P.x - g.x[k], L);
+  dy = P.y - g.y[k];
+}
+__device__ __forceinline__ void node_rel(const ElemGeo<float>& g, int k, const Pos<float>& P, float L,
+                                         float& dx, float& dy) {
+  dx = __fadd_rn(min_image(__fsub_rn(P.xh, g.xh[k]), L), __fsub_rn(P.xl, g.xl[k]));
+  dy = __fadd_rn(__fsub_rn(P.yh, g.yh[k]), __fsub_rn(P.yl, g.yl[k]));
+}
+
+// Particle minus a point given in FP64 (FP32 form: as the pair (ph, pl)), minimum image in x.
+__device__ __forceinline__ double rel_x(const Pos<double>& P, double px, double, double L) {
+  return min_image(P.x - px, L);
+}
+__device__ __forceinline__ double rel_y(const Pos<double>& P, double py, double) { return P.y - py; }
+__device__ __forceinline__ float rel_x(const Pos<float>& P, float ph, float pl, float L) {
+  return __fadd_rn(min_image(__fsub_rn(P.xh, ph), L), __fsub_rn(P.xl, pl));
+}
+__device__ __forceinline__ float rel_y(const Pos<float>& P, float ph, float pl) {
+  return __fadd_rn(__fsub_rn(P.yh, ph), __fsub_rn(P.yl, pl));
+}
+
+// Signed distance of a particle from a boundary line (positive on the domain side).
+__device__ __forceinline__ double line_dist(const Line<double>& ln, const Pos<double>& P, double L) {
+  return min_image(P.x - ln.px, L) * ln.nx + (P.y - ln.py) * ln.ny;
+}
+__device__ __forceinline__ float line_dist(const Line<float>& ln, const Pos<float>& P, float L) {
+  return rel_x(P, ln.px, ln.pxl, L) * ln.nx + rel_y(P, ln.py, ln.pyl) * ln.ny;
+}
+
+// P += (dx, dy): plain FP64, or pair additions.
+__device__ __forceinline__ void pos_add(Pos<double>& P, double dx, double dy) {
+  P.x += dx;
+  P.y += dy;
+}
+__device__ __forceinline__ void pos_add(Pos<float>& P, float dx, float dy) {
+  pair_add(P.xh, P.xl, dx);
+  pair_add(P.yh, P.yl, dy);
+}
+// Eq. 7's move X + U dt + sqrt(2 nu) dW per coordinate (FP64: one expression, as the
+// oracle writes it; FP32: the increment added to the pair).
+__device__ __forceinline__ void pos_move(Pos<double>& P, double ux, double uy, double dt, double s2nu,
+                                         double dWx, double dWy) {
+  P.x = P.x + ux * dt + s2nu * dWx;
+  P.y = P.y + uy * dt + s2nu * dWy;
+}
+__device__ __forceinline__ void pos_move(Pos<float>& P, float ux, float uy, float dt, float s2nu,
+                                         float dWx, float dWy) {
+  pair_add(P.xh, P.xl, ux * dt + s2nu * dWx);
+  pair_add(P.yh, P.yl, uy * dt + s2nu * dWy);
+}
+// Reflection across a line at signed distance d < 0: P -= 2 d n.
+__device__ __forceinline__ void pos_reflect(Pos<double>& P, double d, double nx, double ny) {
+  P.x -= 2.0 * d * nx;
+  P.y -= 2.0 * d * ny;
+}
+__device__ __forceinline__ void pos_reflect(Pos<float>& P, float d, float nx, float ny) {
+  pair_add(P.xh, P.xl, -(2.0f * d * nx));
+  pair_add(P.yh, P.yl, -(2.0f * d * ny));
+}
+// Periodic wrap of x into [0, L).
+__device__ __forceinline__ void pos_wrap(Pos<double>& P, double L) { P.x = wrap_period(P.x, L); }
+__device__ __forceinline__ void pos_wrap(Pos<float>& P, float L) {
+  if (L > 0.0f) {
+    if (P.xh < 0.0f) pair_add(P.xh, P.xl, L);
+    if (P.xh >= L) pair_add(P.xh, P.xl, -L);
+  }
+}
+__device__ __forceinline__ double pos_x(const Pos<double>& P) { return P.x; }
+__device__ __forceinline__ double pos_y(const Pos<double>& P) { return P.y; }
+__device__ __forceinline__ double pos_x(const Pos<float>& P) { return pair_value(P.xh, P.xl); }
+__device__ __forceinline__ double pos_y(const Pos<float>& P) { return pair_value(P.yh, P.yl); }
+__device__ __forceinline__ Pos<double> pos_of(double x, double y, double) { return {x, y}; }
+__device__ __forceinline__ Pos<float> pos_of(double x, double y, float) {
+  Pos<float> P;
+  pair_of(x, P.xh, P.xl);
+  pair_of(y, P.yh, P.yl);
+  return P;
+}
+
 // Separately rounded products (no fused multiply-add).  Every evaluation of an edge's
 // cross product then rounds identically, whichever element and slot it is computed for,
 // so the two elements sharing an edge always see exactly opposite values (a point on the
@@ -145,10 +293,15 @@ __device__ __forceinline__ T wrap_period(T x, T L) {
 __device__ __forceinline__ double xmul(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ float xmul(float a, float b) { return __fmul_rn(a, b); }
 
-// (r_b - r_a) x (r_P - r_a) for the edge a -> b (minimum image in x).
+// (r_b - r_a) x (r_P - r_a) for the edge from local node a to local node b.  Its inputs are
+// node b - node a and P - node a, formed from the nodes' own coordinates and the particle's
+// alone, so both elements of the edge compute the same value.
 template <typename T>
-__device__ __forceinline__ T edge_cross(T xa, T ya, T xb, T yb, T x, T y, T L) {
-  return xmul(min_image(xb - xa, L), y - ya) - xmul(yb - ya, min_image(x - xa, L));
+__device__ __forceinline__ T edge_cross(const ElemGeo<T>& g, int a, int b, const Pos<T>& P, T L) {
+  T ex, ey, dx, dy;
+  node_vec(g, a, b, L, ex, ey);
+  node_rel(g, a, P, L, dx, dy);
+  return xmul(ex, dy) - xmul(ey, dx);
 }
 
 // Twice the signed areas N^A, N^B, N^C (Eqs. 44-45, Fig. 1): for each vertex, the cross
@@ -156,34 +309,37 @@ __device__ __forceinline__ T edge_cross(T xa, T ya, T xb, T yb, T x, T y, T L) {
 // Each edge is pivoted at its lower-numbered node, so the two elements sharing an edge
 // evaluate it with identical rounding and opposite signs (watertight point location).
 template <typename T>
-__device__ __forceinline__ void area_cross(const ElemGeo<T>& g, int na, int nb, int nc, T x, T y,
+__device__ __forceinline__ void area_cross(const ElemGeo<T>& g, int na, int nb, int nc, const Pos<T>& P,
                                            T L, T& n0, T& n1, T& n2) {
-  // edge opposite A: B -> C
-  n0 = nb < nc ? edge_cross(g.x1, g.y1, g.x2, g.y2, x, y, L)
-               : -edge_cross(g.x2, g.y2, g.x1, g.y1, x, y, L);
-  // edge opposite B: C -> A
-  n1 = nc < na ? edge_cross(g.x2, g.y2, g.x0, g.y0, x, y, L)
-               : -edge_cross(g.x0, g.y0, g.x2, g.y2, x, y, L);
-  // edge opposite C: A -> B
-  n2 = na < nb ? edge_cross(g.x0, g.y0, g.x1, g.y1, x, y, L)
-               : -edge_cross(g.x1, g.y1, g.x0, g.y0, x, y, L);
+  n0 = nb < nc ? edge_cross(g, 1, 2, P, L) : -edge_cross(g, 2, 1, P, L);   // edge B -> C
+  n1 = nc < na ? edge_cross(g, 2, 0, P, L) : -edge_cross(g, 0, 2, P, L);   // edge C -> A
+  n2 = na < nb ? edge_cross(g, 0, 1, P, L) : -edge_cross(g, 1, 0, P, L);   // edge A -> B
 }
 
 // Area coordinates lambda_k = N^k / A_e (Eqs. 37-38 shapefunction values at the particle).
 template <typename T>
-__device__ __forceinline__ void area_coords(const ElemGeo<T>& g, int na, int nb, int nc, T x, T y,
+__device__ __forceinline__ void area_coords(const ElemGeo<T>& g, int na, int nb, int nc, const Pos<T>& P,
                                             T L, T& la, T& lb, T& lc) {
-  area_cross(g, na, nb, nc, x, y, L, la, lb, lc);
+  area_cross(g, na, nb, nc, P, L, la, lb, lc);
   la *= g.inv2a;
   lb *= g.inv2a;
   lc *= g.inv2a;
 }
 
 // Point in the triangle with weights (1 - s) A + s (1 - t) B + s t C (Osada et al.).
-template <typename T>
-__device__ __forceinline__ void triangle_point(const ElemGeo<T>& g, T s, T t, T L, T& px, T& py) {
-  px = g.x0 + s * (T(1) - t) * min_image(g.x1 - g.x0, L) + s * t * min_image(g.x2 - g.x0, L);
-  py = g.y0 + s * (T(1) - t) * (g.y1 - g.y0) + s * t * (g.y2 - g.y0);
+__device__ __forceinline__ Pos<double> triangle_point(const ElemGeo<double>& g, double s, double t, double L) {
+  Pos<double> P;
+  P.x = g.x[0] + s * (1.0 - t) * min_image(g.x[1] - g.x[0], L) + s * t * min_image(g.x[2] - g.x[0], L);
+  P.y = g.y[0] + s * (1.0 - t) * (g.y[1] - g.y[0]) + s * t * (g.y[2] - g.y[0]);
+  return P;
+}
+__device__ __forceinline__ Pos<float> triangle_point(const ElemGeo<float>& g, float s, float t, float L) {
+  float bx, by, cx, cy;
+  node_vec(g, 0, 1, L, bx, by);
+  node_vec(g, 0, 2, L, cx, cy);
+  Pos<float> P{g.xh[0], g.xl[0], g.yh[0], g.yl[0]};
+  pos_add(P, s * (1.0f - t) * bx + s * t * cx, s * (1.0f - t) * by + s * t * cy);
+  return P;
 }
 
 }  // namespace pdfx

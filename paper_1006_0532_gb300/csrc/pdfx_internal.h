@@ -16,6 +16,7 @@ namespace pdfx {
 template <typename T>
 struct Model {
   T C1, C2, C3, C4, CT, Cw1, Cw2, nu, C0, Cs, Ct, Cphi, src_x, src_y, src_r, period_x;
+  T src_xl, src_yl;  // FP32 form: the source centre's trailing parts (hi + lo pairs)
   T nuCT2;      // nu C_T^2 (Eq. 18)
   T s2nu;       // sqrt(2 nu) (Eqs. 7, 27)
   T cs_r2;      // C_s r0^(2/3) (Eq. 25)
@@ -35,7 +36,9 @@ struct InstDev {
   int32_t ppe, minnpel;
 };
 
-// Particle storage (structure of arrays) in the working precision.
+// Particle storage (structure of arrays) in the working precision.  The FP32 form holds the
+// position as hi + lo pairs: x, y the leading parts, xl, yl the trailing ones (nullptr in
+// the FP64 form).
 template <typename T>
 struct Particles {
   T *x = nullptr, *y = nullptr, *u = nullptr, *v = nullptr, *w = nullptr, *om = nullptr,
@@ -43,7 +46,25 @@ struct Particles {
   uint32_t* pid = nullptr;
   int32_t* elem = nullptr;
   uint8_t* cp = nullptr;
+  T *xl = nullptr, *yl = nullptr;
 };
+
+__device__ __forceinline__ Pos<double> load_pos(const Particles<double>& p, int64_t i) {
+  return {p.x[i], p.y[i]};
+}
+__device__ __forceinline__ Pos<float> load_pos(const Particles<float>& p, int64_t i) {
+  return {p.x[i], p.xl[i], p.y[i], p.yl[i]};
+}
+__device__ __forceinline__ void store_pos(const Particles<double>& p, int64_t i, const Pos<double>& P) {
+  p.x[i] = P.x;
+  p.y[i] = P.y;
+}
+__device__ __forceinline__ void store_pos(const Particles<float>& p, int64_t i, const Pos<float>& P) {
+  p.x[i] = P.xh;
+  p.xl[i] = P.xl;
+  p.y[i] = P.yh;
+  p.yl[i] = P.yl;
+}
 
 // Arguments of the advance kernel (Eqs. 7, 27, 19, 24; Sect. 3.8; Sect. 3.6).
 template <typename T>
