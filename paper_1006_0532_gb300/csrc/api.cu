@@ -502,14 +502,26 @@ void geo_of(const HostGeo& g, int32_t e, ElemGeo<double>& o) {
   o.inv2a = 1.0 / g.area2[e];
   o.pad = 0.0;
 }
-void geo_of(const HostGeo& g, int32_t e, ElemGeo<float>& o) {
+void geo_of(const HostGeo& g, int32_t e, const int32_t* tri, double L, ElemGeo<float>& o) {
   for (int k = 0; k < 3; ++k) {
     pair_of(g.nx[3 * e + k], o.xh[k], o.xl[k]);
     pair_of(g.vy[3 * e + k], o.yh[k], o.yl[k]);
   }
+  // edge opposite vertex k: counter-clockwise from a = k + 1 to b = k + 2; pivot at the
+  // lower node id, vector from the pivot to the other node (minimum image in x)
+  o.code = 0u;
+  for (int k = 0; k < 3; ++k) {
+    const int a = (k + 1) % 3, b = (k + 2) % 3;
+    const bool flip = tri[3 * e + b] < tri[3 * e + a];
+    const int p = flip ? b : a, q = flip ? a : b;
+    o.ex[k] = static_cast<float>(min_image(g.nx[3 * e + q] - g.nx[3 * e + p], L));
+    o.ey[k] = static_cast<float>(g.vy[3 * e + q] - g.vy[3 * e + p]);
+    o.code |= (static_cast<uint32_t>(p) | (flip ? 4u : 0u)) << (3 * k);
+  }
   o.inv2a = static_cast<float>(1.0 / g.area2[e]);
-  o.pad[0] = o.pad[1] = o.pad[2] = 0.0f;
+  o.pad[0] = o.pad[1] = 0.0f;
 }
+void geo_of(const HostGeo& g, int32_t e, const int32_t*, double, ElemGeo<double>& o) { geo_of(g, e, o); }
 void line_of(const double* src, Line<double>& o) {
   o.px = src[0]; o.py = src[1]; o.nx = src[2]; o.ny = src[3];
 }
@@ -524,10 +536,10 @@ void line_of(const double* src, Line<float>& o) {
 template <typename T>
 int upload_grid(Ctx& c, const HostGeo& g, const std::vector<ElemTopo>& topo,
                 const std::vector<double>& walls, const std::vector<double>& fsl,
-                const std::vector<double>& fse) {
+                const std::vector<double>& fse, const int32_t* tri, const std::vector<double>& period) {
   const int32_t ne = c.ne;
   std::vector<ElemGeo<T>> hg(static_cast<size_t>(ne));
-  for (int32_t e = 0; e < ne; ++e) geo_of(g, e, hg[e]);
+  for (int32_t e = 0; e < ne; ++e) geo_of(g, e, tri, period[e], hg[e]);
   dev_free(c, c.geo);
   c.geo = dev_alloc(c, sizeof(ElemGeo<T>) * ne);
   if (!c.geo) return PDFX_ERR_ALLOC;
@@ -708,8 +720,10 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
   }
   c.nn = nn;
   c.ne = ne;
-  int rc = c.prm.precision == 1 ? upload_grid<float>(c, g, topo, walls, fsl, fse)
-                                : upload_grid<double>(c, g, topo, walls, fsl, fse);
+  std::vector<double> eperiod(static_cast<size_t>(ne));
+  for (int32_t e = 0; e < ne; ++e) eperiod[e] = period_of(e);
+  int rc = c.prm.precision == 1 ? upload_grid<float>(c, g, topo, walls, fsl, fse, tri, eperiod)
+                                : upload_grid<double>(c, g, topo, walls, fsl, fse, tri, eperiod);
   if (rc) return rc;
   PDFX_TRY(alloc_into(c, c.wall2, wall2.size()));
   PDFX_TRY(alloc_into(c, c.dnorm, static_cast<size_t>(1)));

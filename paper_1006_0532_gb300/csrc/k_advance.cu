@@ -109,8 +109,32 @@ __device__ __forceinline__ void interp_fields(const float* __restrict__ F, int n
   }
 }
 
+// Reciprocal, square root and cube root of the closure (Eqs. 11, 18, 25).  FP64 form: the
+// correctly rounded functions.  FP32 form: the hardware approximations (a few units in the
+// last place; the state tolerance of this form is 1e-5) called through CUDA's intrinsics;
+// arguments are positive or zero.
+__device__ __forceinline__ double trcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float trcp(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double tsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float tsqrt(float x) { return x > 0.0f ? x * rsqrtf(x) : 0.0f; }
+__device__ __forceinline__ double tsqrt_ratio(double a, double b) { return sqrt(a / b); }
+__device__ __forceinline__ float tsqrt_ratio(float a, float b) { return tsqrt(a * trcp(b)); }
 __device__ __forceinline__ double tcbrt(double x) { return cbrt(x); }
-__device__ __forceinline__ float tcbrt(float x) { return cbrtf(x); }
+__device__ __forceinline__ float tcbrt(float x) { return exp2f(__log2f(x) * (1.0f / 3.0f)); }
+
+// Box & Muller (1958) for the step's six Gaussians: FP64 form as everywhere; FP32 form with
+// the hardware logarithm, square root and sine/cosine (CUDA intrinsics), the angle taken in
+// (-pi, pi) where they are most accurate: (cos, sin)(2 pi u) = -(cos, sin)(2 pi (u - 1/2)).
+__device__ __forceinline__ void step_gaussians(uint32_t w1, uint32_t w2, double& g1, double& g2) {
+  box_muller(w1, w2, g1, g2);
+}
+__device__ __forceinline__ void step_gaussians(uint32_t w1, uint32_t w2, float& g1, float& g2) {
+  const float r = tsqrt(-2.0f * __logf(uniform01(w1, 0.0f)));
+  float sn, cs;
+  __sincosf(6.2831853071795865f * (uniform01(w2, 0.0f) - 0.5f), &sn, &cs);
+  g1 = -r * cs;
+  g2 = -r * sn;
+}
 __device__ __forceinline__ double texp(double x) { return exp(x); }
 __device__ __forceinline__ float texp(float x) { return expf(x); }
 
@@ -122,6 +146,22 @@ __device__ __forceinline__ float pos_lead(const Pos<float>& P) { return P.xh + P
 __device__ __forceinline__ void warp_count(unsigned long long* diag, int slot, int v) {
   const unsigned s = __reduce_add_sync(kFull, static_cast<unsigned>(v));
   if ((threadIdx.x & 31) == 0 && s) atomicAdd(diag + slot, static_cast<unsigned long long>(s));
+}
+// The same per warp into the block's counters in shared memory.
+__device__ __forceinline__ void warp_count(unsigned* bc, int slot, int v) {
+  const unsigned s = __reduce_add_sync(kFull, static_cast<unsigned>(v));
+  if ((threadIdx.x & 31) == 0 && s) atomicAdd(bc + slot, s);
+}
+// Block counters: cleared at the start of a kernel, added to the diagnostics at its end (one
+// global atomic per block and counter instead of one per warp on the same address).
+__device__ __forceinline__ void block_counts_clear(unsigned* bc) {
+  for (int k = threadIdx.x; k < kDiagCount; k += blockDim.x) bc[k] = 0u;
+  __syncthreads();
+}
+__device__ __forceinline__ void block_counts_flush(unsigned* bc, unsigned long long* diag) {
+  __syncthreads();
+  for (int k = threadIdx.x; k < kDiagCount; k += blockDim.x)
+    if (bc[k]) atomicAdd(diag + k, static_cast<unsigned long long>(bc[k]));
 }
 
 // Per-particle event flags of one update, summed per warp into the diagnostics.
@@ -188,36 +228,44 @@ __device__ __forceinline__ int finish_update(const AdvanceArgs<T>& a, const Mode
   return e_new;
 }
 
-// Counts per new element, aggregated over the lanes of a warp that share it, and the
-// diagnostics counters and error word.  Every lane of the warp takes part.
+// Counts per new element, aggregated over the lanes of a warp that share it (one atomic when
+// the whole warp shares one element, the common case in element-ordered storage), and the
+// diagnostics counters (into the block's counters bc) and error word.  Every lane of the
+// warp takes part.
 template <typename T>
 __device__ __forceinline__ void count_update(const AdvanceArgs<T>& a, bool valid, int e_new,
-                                             const StepFlags& f) {
+                                             const StepFlags& f, unsigned* bc) {
   const unsigned active = __ballot_sync(kFull, valid);
   if (valid) {
-    const unsigned peers = __match_any_sync(active, e_new);
-    if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(a.cnt + e_new, __popc(peers));
+    const int lead = __ffs(active) - 1;
+    const int e_lead = __shfl_sync(active, e_new, lead);
+    if (__all_sync(active, e_new == e_lead)) {
+      if ((threadIdx.x & 31) == lead) atomicAdd(a.cnt + e_lead, __popc(active));
+    } else {
+      const unsigned peers = __match_any_sync(active, e_new);
+      if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(a.cnt + e_new, __popc(peers));
+    }
   }
-  warp_count(a.diag, kDiagHops, f.hops);
+  warp_count(bc, kDiagHops, f.hops);
   if (__any_sync(kFull, f.fb | f.brute | f.lost | f.nf | f.gex | f.c0)) {
-    warp_count(a.diag, kDiagFallback, f.fb);
-    warp_count(a.diag, kDiagBrute, f.brute);
-    warp_count(a.diag, kDiagLost, f.lost);
-    warp_count(a.diag, kDiagNonFinite, f.nf);
-    warp_count(a.diag, kDiagGammaExhausted, f.gex);
-    warp_count(a.diag, kDiagC0Clamp, f.c0);
+    warp_count(bc, kDiagFallback, f.fb);
+    warp_count(bc, kDiagBrute, f.brute);
+    warp_count(bc, kDiagLost, f.lost);
+    warp_count(bc, kDiagNonFinite, f.nf);
+    warp_count(bc, kDiagGammaExhausted, f.gex);
+    warp_count(bc, kDiagC0Clamp, f.c0);
   }
   if (__any_sync(kFull, f.lost) && (threadIdx.x & 31) == 0) atomicCAS(a.err, 0, PDFX_ERR_LOST_PARTICLE);
   if (__any_sync(kFull, f.nf) && (threadIdx.x & 31) == 0) atomicCAS(a.err, 0, PDFX_ERR_NONFINITE);
   if (__any_sync(kFull, f.wall | f.fs | f.oref | f.src)) {
-    warp_count(a.diag, kDiagWall, f.wall);
-    warp_count(a.diag, kDiagFreeSlip, f.fs);
-    warp_count(a.diag, kDiagOmegaReflect, f.oref);
-    warp_count(a.diag, kDiagSource, f.src);
+    warp_count(bc, kDiagWall, f.wall);
+    warp_count(bc, kDiagFreeSlip, f.fs);
+    warp_count(bc, kDiagOmegaReflect, f.oref);
+    warp_count(bc, kDiagSource, f.src);
   }
   if (__any_sync(kFull, f.hop_bin > 0)) {
 #pragma unroll
-    for (int b = 1; b < 8; ++b) warp_count(a.diag, kDiagHopHist0 + b, f.hop_bin == b);
+    for (int b = 1; b < 8; ++b) warp_count(bc, kDiagHopHist0 + b, f.hop_bin == b);
   }
 }
 
@@ -225,6 +273,8 @@ __device__ __forceinline__ void count_update(const AdvanceArgs<T>& a, bool valid
 // Philox key of the particle's instance (that of its element) instead of a.m, a.k0, a.k1.
 template <typename T, bool BATCH>
 __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(const AdvanceArgs<T> a) {
+  __shared__ unsigned bc[kDiagCount];
+  block_counts_clear(bc);
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool valid = i < a.np;
   StepFlags f;
@@ -266,7 +316,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
     if (k < T(1e-30)) k = T(1e-30);
     T eps = Om * (k + M.nuCT2 * Om);
     if (eps < T(1e-30)) eps = T(1e-30);
-    const T ik = T(1) / k, ieps = T(1) / eps;
+    const T ik = trcp(k), ieps = trcp(eps);
     // Eq. 11
     T C0;
     if (M.c0_mode == 1) {
@@ -291,16 +341,16 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
     if (M.tm_mode == 1) {
       itm = T(0.5) * M.Cphi * eps * ik;
     } else {
-      const T kt = k * ieps, kol = M.CT * sqrt(M.nu * ieps);
+      const T kt = k * ieps, kol = M.CT * tsqrt(M.nu * ieps);
       const T a2 = kt > kol ? kt : kol;
       const T ddx = rel_x(P0, M.src_x, M.src_xl, L), ddy = rel_y(P0, M.src_y, M.src_yl);
       const T Uc2 = Um[0] * Um[0] + Um[1] * Um[1] + Um[2] * Um[2];
       T tm = a2;
       if (Uc2 > T(0)) {
-        const T a1 = M.cs_r2 * tcbrt(ieps) + M.Ct * sqrt((ddx * ddx + ddy * ddy) / Uc2);
+        const T a1 = M.cs_r2 * tcbrt(ieps) + M.Ct * tsqrt_ratio(ddx * ddx + ddy * ddy, Uc2);
         tm = a1 < a2 ? a1 : a2;
       }
-      itm = T(1) / tm;
+      itm = trcp(tm);
     }
 
     // Sect. 3.9: six Gaussians and eta
@@ -308,9 +358,9 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
     const uint4 r0 = philox(make_uint4(pid, step, kPurStep, 0u), k0, k1);
     const uint4 r1 = philox(make_uint4(pid, step, kPurStep, 1u), k0, k1);
     T xi[6];
-    box_muller(r0.x, r0.y, xi[0], xi[1]);
-    box_muller(r0.z, r0.w, xi[2], xi[3]);
-    box_muller(r1.x, r1.y, xi[4], xi[5]);
+    step_gaussians(r0.x, r0.y, xi[0], xi[1]);
+    step_gaussians(r0.z, r0.w, xi[2], xi[3]);
+    step_gaussians(r1.x, r1.y, xi[4], xi[5]);
     const T eta = uniform01(r1.z, T(0));     // first wall line
     const T eta2 = uniform01(r1.w, T(0));    // second wall line (a corner element)
     const T dt = a.dt;
@@ -322,7 +372,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
     // G_ij (U_j - <U_j>) = (wp_ij (U_j - <U_j>) - eps/2 (U_i - <U_i>)) / k  (Eq. 11)
     T c0e = C0 * eps;
     if (c0e < T(0)) { c0e = T(0); f.c0 = 1; }
-    const T sc0e = sqrt(c0e) * sdt;
+    const T sc0e = tsqrt(c0e) * sdt;
     const T dU[3] = {U0[0] - Um[0], U0[1] - Um[1], U0[2] - Um[2]};
     T Un[3];
 #pragma unroll
@@ -340,7 +390,7 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
     // Eq. 19, reflected at zero
     const T wpos = w0 > T(0) ? w0 : T(0);
     T wn = w0 - M.C3 * Om * (w0 - Om) * dt - Somega * Om * w0 * dt +
-           sqrt(T(2) * M.C3 * M.C4 * Om * Om * wpos) * (sdt * xi[5]);
+           tsqrt(T(2) * M.C3 * M.C4 * Om * Om * wpos) * (sdt * xi[5]);
     if (wn < T(0)) { wn = -wn; f.oref = 1; }
     // Eq. 24 with the conditional mean of the particle's bin
     const T phic = static_cast<T>(a.vcce[(size_t)e * a.G + cpi]);
@@ -379,7 +429,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
     }
     e_new = finish_update(a, M, i, e, tp, Pn, Un, wn, psin, f);
   }
-  count_update(a, valid, e_new, f);
+  count_update(a, valid, e_new, f, bc);
+  block_counts_flush(bc, a.diag);
 }
 
 // Eqs. 46-47 (model 1), the particle-redistribution test of Sect. 3.7: one thread per
@@ -390,6 +441,8 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
 // no-slip walls; free-slip reflection, wrap, source and walk as in the full model.
 template <typename T, bool BATCH>
 __global__ void __launch_bounds__(256) simple_advance_kernel(const AdvanceArgs<T> a) {
+  __shared__ unsigned bc[kDiagCount];
+  block_counts_clear(bc);
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   const bool valid = i < a.np;
   StepFlags f;
@@ -427,7 +480,8 @@ __global__ void __launch_bounds__(256) simple_advance_kernel(const AdvanceArgs<T
     pos_add(Pn, U0[0] * dt, U0[1] * dt);
     e_new = finish_update(a, M, i, e, tp, Pn, Un, a.p.om[i], a.p.psi[i], f);
   }
-  count_update(a, valid, e_new, f);
+  count_update(a, valid, e_new, f, bc);
+  block_counts_flush(bc, a.diag);
 }
 
 // Last resort of Sect. 3.6 for particles neither the walk nor the fall-back located: one

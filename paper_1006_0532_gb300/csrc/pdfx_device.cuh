@@ -38,9 +38,18 @@ template <>
 struct __align__(64) ElemGeo<double> {
   double x[3], y[3], inv2a, pad;
 };
+// The FP32 form also keeps each edge's vector in FP32, from the edge's lower-numbered node
+// (its pivot) to the other, computed once in FP64 from the nodes' coordinates: the same
+// numbers for both elements of the edge.  code holds, for the edge opposite local vertex k,
+// the pivot's local index (bits 3k, 3k + 1) and whether the pivot is the edge's second
+// node in counter-clockwise order (bit 3k + 2, the cross product's sign flips).
 template <>
 struct __align__(16) ElemGeo<float> {
-  float xh[3], yh[3], xl[3], yl[3], inv2a, pad[3];
+  float xh[3], yh[3], xl[3], yl[3];
+  float ex[3], ey[3];
+  float inv2a;
+  uint32_t code;
+  float pad[2];
 };
 
 // Per-element topology: node ids, neighbour across the edge opposite each vertex (-1 = a
@@ -308,12 +317,33 @@ __device__ __forceinline__ T edge_cross(const ElemGeo<T>& g, int a, int b, const
 // product of the opposite edge with the vector from one end of that edge to the particle.
 // Each edge is pivoted at its lower-numbered node, so the two elements sharing an edge
 // evaluate it with identical rounding and opposite signs (watertight point location).
-template <typename T>
-__device__ __forceinline__ void area_cross(const ElemGeo<T>& g, int na, int nb, int nc, const Pos<T>& P,
-                                           T L, T& n0, T& n1, T& n2) {
+__device__ __forceinline__ void area_cross(const ElemGeo<double>& g, int na, int nb, int nc,
+                                           const Pos<double>& P, double L, double& n0, double& n1,
+                                           double& n2) {
   n0 = nb < nc ? edge_cross(g, 1, 2, P, L) : -edge_cross(g, 2, 1, P, L);   // edge B -> C
   n1 = nc < na ? edge_cross(g, 2, 0, P, L) : -edge_cross(g, 0, 2, P, L);   // edge C -> A
   n2 = na < nb ? edge_cross(g, 0, 1, P, L) : -edge_cross(g, 1, 0, P, L);   // edge A -> B
+}
+// FP32 form: the particle's offsets from the three nodes, then each edge's stored vector
+// crossed with the offset from its pivot.
+__device__ __forceinline__ void area_cross(const ElemGeo<float>& g, int, int, int, const Pos<float>& P,
+                                           float L, float& n0, float& n1, float& n2) {
+  float dx[3], dy[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) node_rel(g, m, P, L, dx[m], dy[m]);
+  float n[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const uint32_t c = g.code >> (3 * k);
+    const int pv = static_cast<int>(c & 3u);
+    const float px = pv == 0 ? dx[0] : (pv == 1 ? dx[1] : dx[2]);
+    const float py = pv == 0 ? dy[0] : (pv == 1 ? dy[1] : dy[2]);
+    const float cr = xmul(g.ex[k], py) - xmul(g.ey[k], px);
+    n[k] = (c & 4u) ? -cr : cr;
+  }
+  n0 = n[0];
+  n1 = n[1];
+  n2 = n[2];
 }
 
 // Area coordinates lambda_k = N^k / A_e (Eqs. 37-38 shapefunction values at the particle).
