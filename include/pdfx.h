@@ -434,7 +434,14 @@ int  pdfx_get_pressure(void *ctx, double *P, double *dP, void *stream);
  *      particle equations, walls, tracking, particle-number control, statistics);
  *   4. the pressure projection: pdfx_pressure_rhs with the predicted nodal means and the
  *      context's P, then pdfx_pressure_solve from the last increment;
- *   5. the correction of Eq. 31 on the particles and the statistics of the corrected state;
+ *   5. the correction of Eq. 31 and the statistics of the corrected state.  The correction
+ *      is one vector per element (dt times its pressure-increment gradient), so the
+ *      corrected statistics are the step's own with each element's mean U and V shifted
+ *      by it (central moments, conditioning pointers and conditional means unchanged) and
+ *      averaged at the nodes again.  The particles' velocities take the correction as the
+ *      next advance (pdfx_step, pdfx_batch_step, pdfx_coupled_step) reads them, or before
+ *      any other call that reads or replaces them (pdfx_get_particles,
+ *      pdfx_correct_velocity, pdfx_step_many, pdfx_autotune);
  *   6. P += dP; the fields the statistics provide (pdfx_derive_fields) and the pressure
  *      gradient (slots 3-4: the node-transferred gradient of P) from the new state.
  * Eq. 33 is stable only for Cp < 2 dt.  iters[2] (may be NULL) receives the iteration

@@ -378,17 +378,33 @@ int do_step(Ctx& c, double dt, cudaStream_t s) {
     a.dt = T(dt);
     a.sdt = T(std::sqrt(dt));
     a.stepc = c.dstep;
+    a.corr = c.corr_pending ? c.corr : nullptr;   // consumed by this advance
     a.k0 = key0(c.prm);
     a.k1 = key1(c.prm);
     a.inst = c.K > 1 ? static_cast<const InstDev<T>*>(c.inst) : nullptr;
     a.einst = c.K > 1 ? c.einst : nullptr;
     launch_advance<T>(a, c.num_sms, c.adv_block, s);
     c.launches++;
+    c.corr_pending = false;
   }
   PDFX_TRY(run_statistics<T>(c, true, true, false, s));
   c.step++;
   c.steps_done++;
   return cerr(cudaGetLastError());
+}
+
+// Applies a pending Eq. 31 correction to the particles now (before a caller reads them, or
+// before steps are captured into a graph).
+template <typename T>
+void apply_pending_correction(Ctx& c, cudaStream_t s) {
+  if (!c.corr_pending) return;
+  launch_apply_correction<T>(carve<T>(c.pbuf[c.cur], c.np), c.np, c.corr, s);
+  c.launches++;
+  c.corr_pending = false;
+}
+void apply_pending_correction_any(Ctx& c, cudaStream_t s) {
+  if (c.prm.precision == 1) apply_pending_correction<float>(c, s);
+  else apply_pending_correction<double>(c, s);
 }
 
 template <typename T>
@@ -413,6 +429,7 @@ int do_init(Ctx& c, const int32_t* ppe, cudaStream_t s) {
   c.step = 0;
   PDFX_CUDA(cudaMemsetAsync(c.dstep, 0, sizeof(uint32_t), s));
   c.steps_since_sort = 0;
+  c.corr_pending = false;
   return run_statistics<T>(c, false, false, false, s);
 }
 
@@ -444,6 +461,7 @@ int do_set_particles(Ctx& c, int64_t np, const pdfx_soa* soa, uint32_t step, int
   c.step = step;
   PDFX_CUDA(cudaMemcpyAsync(c.dstep, &step, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
   c.steps_since_sort = 0;
+  c.corr_pending = false;
   int rc = run_statistics<T>(c, false, false, true, s);
   if (tmp) {
     cudaStreamSynchronize(s);
@@ -462,6 +480,7 @@ int do_set_particles(Ctx& c, int64_t np, const pdfx_soa* soa, uint32_t step, int
 
 template <typename T>
 int do_get_particles(Ctx& c, pdfx_soa* soa, int on_device, cudaStream_t s) {
+  apply_pending_correction<T>(c, s);
   Particles<T> p = carve<T>(c.pbuf[c.cur], c.np);
   const size_t n = static_cast<size_t>(c.np);
   if (on_device) {
@@ -798,6 +817,7 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
   c.h_vy = g.vy;
   c.h_area2 = g.area2;
   c.fem_ready = false;   // the Eulerian calls rebuild their FEM data for this grid
+  c.corr_pending = false;
   c.have_grid = true;
   c.have_fields = false;
   return PDFX_OK;
@@ -852,6 +872,7 @@ int capture_cycle(Ctx& c, double dt, int nsteps) {
 
 template <typename T>
 int do_step_many(Ctx& c, double dt, int32_t nsteps, int use_graph, cudaStream_t s) {
+  apply_pending_correction<T>(c, s);   // a captured step must not carry it
   const int cycle = c.prm.sort_every > 0 ? 2 * c.prm.sort_every : 1;
   int32_t left = nsteps;
   if (use_graph) {
@@ -880,6 +901,7 @@ int do_step_many(Ctx& c, double dt, int32_t nsteps, int use_graph, cudaStream_t 
 // diagnostics are restored afterwards.
 template <typename T>
 int do_autotune(Ctx& c, double dt, cudaStream_t s, int32_t* best_block, int32_t* best_se) {
+  apply_pending_correction<T>(c, s);
   const size_t pb = c.pbuf_bytes;
   const size_t vb = sizeof(double) * static_cast<size_t>(c.ne) * c.G;
   const size_t eb = sizeof(double) * static_cast<size_t>(c.ne) * kNS;
@@ -1075,6 +1097,7 @@ int ensure_fem(Ctx& c) {
   PDFX_TRY(alloc_into(c, c.eflag, 1));
   PDFX_TRY(alloc_into(c, c.P, nn));
   PDFX_TRY(alloc_into(c, c.dP, nn));
+  PDFX_TRY(alloc_into(c, c.corr, 2 * static_cast<size_t>(c.ne)));
   PDFX_CUDA(cudaMemset(c.P, 0, sizeof(double) * nn));
   PDFX_CUDA(cudaMemset(c.dP, 0, sizeof(double) * nn));
   c.fem_ready = true;
@@ -1186,10 +1209,15 @@ int do_coupled_step(Ctx& c, double dt, double Cp, double tol, int32_t max_iter, 
   c.launches += 7;
   PDFX_TRY(pressure_dev(c, w, c.dP, tol, max_iter, &ip, s));
   const ElemGeo<T>* geo = static_cast<const ElemGeo<T>*>(c.geo);
-  launch_correct_velocity<T>(geo, c.topo, c.ne, c.prm.period_x, nullptr, nullptr, c.dP, w.big,
-                             carve<T>(c.pbuf[c.cur], c.np), c.np, dt, s);
-  c.launches += 2;
-  PDFX_TRY(run_statistics<T>(c, false, false, false, s));
+  // Eq. 31: U -= dt grad(dP), one vector per element.  It shifts the particles of an element
+  // together, so the statistics follow by shifting the element means (central moments,
+  // conditioning order and conditional means stay) and averaging at the nodes; the
+  // particles take it as the next advance reads them (or before any other reader).
+  launch_correction_field<T>(geo, c.topo, c.ne, c.prm.period_x, nullptr, nullptr, c.dP, dt, c.corr, s);
+  launch_shift_means(c.ne, c.corr, c.emom, s);
+  launch_node_average(c.emom, c.ne_off, c.ne_list, c.nn, c.nmom, s);
+  c.corr_pending = true;
+  c.launches += 4;
   launch_add(c.nn, c.dP, c.P, s);
   launch_derive_fields<T>(geo, c.topo, c.ne, c.prm.period_x, nullptr, nullptr, c.ne_off, c.ne_list, c.nn,
                           c.nmom, w.big, fields, s);
@@ -1580,6 +1608,7 @@ int pdfx_correct_velocity(void* ctx, const double* dp, double dt, void* stream) 
   auto* scratch = static_cast<double*>(dev_alloc(*c, sizeof(double) * (nn + 2 * ne)));
   if (!scratch) return PDFX_ERR_ALLOC;
   const int32_t* einst = c->K > 1 ? c->einst : nullptr;
+  apply_pending_correction_any(*c, s);
   int rc = cerr(cudaMemcpyAsync(scratch, dp, sizeof(double) * nn, cudaMemcpyHostToDevice, s));
   if (rc == PDFX_OK) {
     if (c->prm.precision == 1)

@@ -286,7 +286,11 @@ __global__ void __launch_bounds__(256, sizeof(T) == 4 ? 4 : 2) advance_kernel(co
     const uint32_t k0 = BATCH ? a.inst[ki].k0 : a.k0, k1 = BATCH ? a.inst[ki].k1 : a.k1;
     const T L = M.period_x;
     const Pos<T> P0 = load_pos(a.p, i);
-    const T U0[3] = {a.p.u[i], a.p.v[i], a.p.w[i]};
+    T U0[3] = {a.p.u[i], a.p.v[i], a.p.w[i]};
+    if (a.corr) {   // Eq. 31 of the last coupled step, applied as the velocity is read
+      U0[0] = static_cast<T>(static_cast<double>(U0[0]) - a.corr[2 * static_cast<size_t>(e)]);
+      U0[1] = static_cast<T>(static_cast<double>(U0[1]) - a.corr[2 * static_cast<size_t>(e) + 1]);
+    }
     const T w0 = a.p.om[i], psi0 = a.p.psi[i];
     const uint32_t pid = a.p.pid[i];
     const int cpi = a.p.cp[i];
@@ -453,7 +457,11 @@ __global__ void __launch_bounds__(256) simple_advance_kernel(const AdvanceArgs<T
     const Model<T>& M = BATCH ? a.inst[ki].m : a.m;
     const uint32_t k0 = BATCH ? a.inst[ki].k0 : a.k0, k1 = BATCH ? a.inst[ki].k1 : a.k1;
     const Pos<T> P0 = load_pos(a.p, i);
-    const T U0[3] = {a.p.u[i], a.p.v[i], a.p.w[i]};
+    T U0[3] = {a.p.u[i], a.p.v[i], a.p.w[i]};
+    if (a.corr) {
+      U0[0] = static_cast<T>(static_cast<double>(U0[0]) - a.corr[2 * static_cast<size_t>(e)]);
+      U0[1] = static_cast<T>(static_cast<double>(U0[1]) - a.corr[2 * static_cast<size_t>(e) + 1]);
+    }
     const ElemTopo tp = a.topo[e];
     T la, lb, lc;
     if (M.interp_mode == 1) {

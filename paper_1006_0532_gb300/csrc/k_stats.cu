@@ -916,29 +916,72 @@ void launch_derive_fields(const ElemGeo<T>* geo, const ElemTopo* topo, int32_t n
 
 namespace {
 
-// Eq. 31 (rho = 1) on each particle: U -= dt grad(dP) of its element (egrad[e][2]).
+// Eq. 31 (rho = 1) on each particle: U -= corr of its element, corr[e][2] = dt grad(dP).
 template <typename T>
-__global__ void correct_velocity_kernel(Particles<T> p, int64_t np, const double* __restrict__ egrad,
-                                        double dt) {
+__global__ void correct_velocity_kernel(Particles<T> p, int64_t np, const double* __restrict__ corr) {
   const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (i >= np) return;
   const int e = p.elem[i];
-  p.u[i] = static_cast<T>(static_cast<double>(p.u[i]) - dt * egrad[2 * static_cast<size_t>(e)]);
-  p.v[i] = static_cast<T>(static_cast<double>(p.v[i]) - dt * egrad[2 * static_cast<size_t>(e) + 1]);
+  p.u[i] = static_cast<T>(static_cast<double>(p.u[i]) - corr[2 * static_cast<size_t>(e)]);
+  p.v[i] = static_cast<T>(static_cast<double>(p.v[i]) - corr[2 * static_cast<size_t>(e) + 1]);
+}
+
+__global__ void scale_kernel(int64_t n, double f, double* __restrict__ v) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i < n) v[i] *= f;
+}
+
+// Eq. 31 shifts every particle of an element by the same vector, so the element's mean
+// velocity moves by it and its central moments and conditioning order stay: emom means of
+// U and V of the elements that hold particles -= corr.
+__global__ void shift_means_kernel(int32_t ne, const double* __restrict__ corr, double* __restrict__ emom) {
+  const int32_t e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= ne) return;
+  double* em = emom + static_cast<size_t>(kNS) * e;
+  if (em[0] < 1.0) return;
+  em[1] -= corr[2 * static_cast<size_t>(e)];
+  em[2] -= corr[2 * static_cast<size_t>(e) + 1];
 }
 
 }  // namespace
 
 template <typename T>
+void launch_correction_field(const ElemGeo<T>* geo, const ElemTopo* topo, int32_t ne, double period_x,
+                             const int32_t* einst, const InstDev<T>* inst, const double* dp, double dt,
+                             double* corr, cudaStream_t s) {
+  if (ne <= 0) return;
+  elem_gradient_kernel<T><<<static_cast<unsigned>((ne + 127) / 128), 128, 0, s>>>(
+      geo, topo, ne, period_x, einst, inst, dp, 1, 0, 1, corr);
+  const int64_t n = 2 * static_cast<int64_t>(ne);
+  scale_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, s>>>(n, dt, corr);
+}
+
+template <typename T>
+void launch_apply_correction(Particles<T> p, int64_t np, const double* corr, cudaStream_t s) {
+  if (np > 0)
+    correct_velocity_kernel<T><<<static_cast<unsigned>((np + 255) / 256), 256, 0, s>>>(p, np, corr);
+}
+
+void launch_shift_means(int32_t ne, const double* corr, double* emom, cudaStream_t s) {
+  if (ne > 0) shift_means_kernel<<<static_cast<unsigned>((ne + 127) / 128), 128, 0, s>>>(ne, corr, emom);
+}
+
+template <typename T>
 void launch_correct_velocity(const ElemGeo<T>* geo, const ElemTopo* topo, int32_t ne, double period_x,
                              const int32_t* einst, const InstDev<T>* inst, const double* dp,
                              double* egrad, Particles<T> p, int64_t np, double dt, cudaStream_t s) {
-  if (ne <= 0) return;
-  elem_gradient_kernel<T><<<static_cast<unsigned>((ne + 127) / 128), 128, 0, s>>>(
-      geo, topo, ne, period_x, einst, inst, dp, 1, 0, 1, egrad);
-  if (np > 0)
-    correct_velocity_kernel<T><<<static_cast<unsigned>((np + 255) / 256), 256, 0, s>>>(p, np, egrad, dt);
+  launch_correction_field<T>(geo, topo, ne, period_x, einst, inst, dp, dt, egrad, s);
+  launch_apply_correction<T>(p, np, egrad, s);
 }
+
+template void launch_correction_field<float>(const ElemGeo<float>*, const ElemTopo*, int32_t, double,
+                                             const int32_t*, const InstDev<float>*, const double*, double,
+                                             double*, cudaStream_t);
+template void launch_correction_field<double>(const ElemGeo<double>*, const ElemTopo*, int32_t, double,
+                                              const int32_t*, const InstDev<double>*, const double*, double,
+                                              double*, cudaStream_t);
+template void launch_apply_correction<float>(Particles<float>, int64_t, const double*, cudaStream_t);
+template void launch_apply_correction<double>(Particles<double>, int64_t, const double*, cudaStream_t);
 
 template void launch_correct_velocity<float>(const ElemGeo<float>*, const ElemTopo*, int32_t, double,
                                              const int32_t*, const InstDev<float>*, const double*,

@@ -94,6 +94,8 @@ struct AdvanceArgs {
   Model<T> m;
   T dt, sdt;    // time step and its square root
   const uint32_t* stepc;   // step counter (Philox counter word) in device memory
+  const double* corr;      // [ne][2] Eq. 31 correction of the last coupled step still to be
+                           // applied to the velocities as they are read (nullptr: none)
   uint32_t k0, k1;
   // batches: per-instance parameters (m, k0, k1 above are unused) and element -> instance
   const InstDev<T>* inst;
@@ -306,6 +308,8 @@ struct Ctx {
   uint8_t* efixed = nullptr;    // [9][nn] Dirichlet masks
   int* eflag = nullptr;         // [1] eps <= 0 at a node
   double* P = nullptr;          // [nn] nodal mean pressure (rho = 1)
+  double* corr = nullptr;       // [ne][2] Eq. 31: dt grad(dP) per element of the last coupled step
+  bool corr_pending = false;    // corr not yet applied to the particles (the next advance does)
   double* dP = nullptr;         // [nn] last pressure increment (the next initial guess)
   // allocations to release
   std::vector<std::pair<void*, size_t>> owned;
@@ -362,6 +366,15 @@ template <typename T>
 void launch_correct_velocity(const ElemGeo<T>* geo, const ElemTopo* topo, int32_t ne, double period_x,
                              const int32_t* einst, const InstDev<T>* inst, const double* dp,
                              double* egrad, Particles<T> p, int64_t np, double dt, cudaStream_t s);
+// The same in parts: corr[ne][2] = dt grad(dP) per element; U -= corr on each particle;
+// the element means of U and V shifted by corr (elements that hold particles).
+template <typename T>
+void launch_correction_field(const ElemGeo<T>* geo, const ElemTopo* topo, int32_t ne, double period_x,
+                             const int32_t* einst, const InstDev<T>* inst, const double* dp, double dt,
+                             double* corr, cudaStream_t s);
+template <typename T>
+void launch_apply_correction(Particles<T> p, int64_t np, const double* corr, cudaStream_t s);
+void launch_shift_means(int32_t ne, const double* corr, double* emom, cudaStream_t s);
 // Sect. 3.4: the nodal fields the statistics provide (slots 0-2, 5-13, 23-29) from nmom;
 // scratch holds 18 (ne + nn) doubles.
 template <typename T>
