@@ -28,20 +28,34 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-updates/sec per full PDF timestep, FP32/batched vs FP64, same GPU"
 UNIT = "particle-updates/s"
 # Algorithmic bytes per particle-update (keys: 1 FP32 form, 0 FP64 form).
-# advance (pass 1): read x, y, u, v, w, omega, psi, elem, cp; write x, y, u, v, w, omega,
-#   psi, elem: 4*7+4+1+4*7+4 in FP32, 8*7+4+1+8*7+4 in FP64.
+# advance (pass 1): read the position, u, v, w, omega, psi, elem, cp; write the position,
+#   u, v, w, omega, psi, elem.  The FP32 form holds each coordinate as an FP32 pair (hi +
+#   lo, 8 B): 4*9+4+1+4*9+4 = 81 B; the FP64 form 8*7+4+1+8*7+4 = 121 B.
 # binning (pass 2): read u, v, w, psi, elem; write cp: 4*4+4+1, 8*4+4+1.
-ADV_BYTES = {1: 65, 0: 121}
+# With single FP32 positions the FP32 step would be 65 + 21 = 86 B; the pairs add 16 B.
+ADV_BYTES = {1: 81, 0: 121}
 BIN_BYTES = {1: 21, 0: 37}
-# DRAM bytes per particle measured by ncu (dram__bytes_read.sum + dram__bytes_write.sum)
-# for the current kernels, FP32 form: profiles/advance_kernel_channel_50k_ppe100_f32.md and
-# profiles/stats_tile_kernel_channel_50k_ppe500_f32.md.  None once a kernel changes.
-TRAFFIC_PER_PARTICLE = {"advance": 64.4, "statistics_binning": 35.9}
-# What bounds each kernel instead of HBM, from the same ncu captures.
-LIMITER = {"advance": "instruction issue (issue active 66%, long-scoreboard stalls; DRAM 15% of peak)",
-           "statistics_binning": "integer ALU issue (ALU pipe 74%, issue active 74% in the <= 512 class; "
-                                 "DRAM 6% of peak)"}
+SINGLE_POSITION_STEP_BYTES = 86
+# Figures from ncu captures of the kernels (DRAM bytes per particle and launch,
+# dram__bytes_read.sum + dram__bytes_write.sum; FP64 instructions per particle of the FP64
+# form's advance; the bound each capture shows), keyed by the SHA-256 of the CUDA sources
+# they were taken from: a capture describes only the kernels it measured, so after any
+# change of the sources the bench reports traffic as null until the next capture.
+NCU_RECORDS = {}
 STAGES = ["advance", "plan", "lists", "redistribute", "statistics_binning", "node_average"]
+
+
+def kernel_sources_hash() -> str:
+    """SHA-256 over the CUDA sources of the library (file names and contents, sorted)."""
+    import hashlib
+    d = os.path.join(ROOT, "paper_1006_0532_gb300", "csrc")
+    h = hashlib.sha256()
+    for name in sorted(os.listdir(d)):
+        if name.endswith((".cu", ".cuh", ".h")):
+            h.update(name.encode())
+            with open(os.path.join(d, name), "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()
 
 
 def peaks():
@@ -123,7 +137,8 @@ def oracle_sample(workload_name: str, steps: int, ppe: int):
     from paper_1006_0532_gb300 import synth
 
     w = synth.workload(workload_name)
-    o = oracle.Oracle(w["grid"], w["params"], w["fields"])
+    # MINNPEL follows the particle count of the sample (one tenth, the workloads' ratio)
+    o = oracle.Oracle(w["grid"], dict(w["params"], minnpel=max(1, ppe // 10)), w["fields"])
     o.init_particles(ppe)
     n = o.np_
     t0 = time.perf_counter()
@@ -133,31 +148,84 @@ def oracle_sample(workload_name: str, steps: int, ppe: int):
     return n, steps, dt, w
 
 
+def _oracle_part(job):
+    """One host process of the all-core oracle timing: the oracle as it stands (one thread)
+    stepping the particles of its share of the elements; waits at the barrier, then times
+    its steps (it returns its particle count and time)."""
+    workload, ppe, elems, warmup, steps, barrier = job
+    import numpy as np
+    import oracle
+    from paper_1006_0532_gb300 import synth
+    w = synth.workload(workload)
+    o = oracle.Oracle(w["grid"], dict(w["params"], minnpel=0), w["fields"])
+    o.init_elements(ppe, np.asarray(elems, dtype=np.int64))
+    for _ in range(warmup):
+        o.step(w["dt"])
+    barrier.wait()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        o.step(w["dt"])
+    return o.np_, time.perf_counter() - t0
+
+
+def oracle_parallel(workload: str, ppe: int, warmup: int, steps: int, procs: int):
+    """The oracle on all host cores: procs processes (spawned), each stepping the particles of
+    a contiguous share of the elements with the unchanged one-thread oracle (particle-number
+    control off: it couples all elements).  Throughput = all particles x steps / the slowest
+    process's time."""
+    import multiprocessing as mp
+    import numpy as np
+    from paper_1006_0532_gb300 import synth
+    ne = synth.workload(workload)["grid"].ne
+    procs = max(1, min(procs, ne))
+    parts = np.array_split(np.arange(ne), procs)
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as mgr:
+        barrier = mgr.Barrier(procs)
+        with ctx.Pool(procs) as pool:
+            res = pool.map(_oracle_part, [(workload, ppe, p.tolist(), warmup, steps, barrier)
+                                          for p in parts])
+    n = sum(r[0] for r in res)
+    el = max(r[1] for r in res)
+    return n, el
+
+
+def host_cores():
+    """Host cores this process may use, and the CPU model (lscpu) for the record."""
+    try:
+        cores = len(os.sched_getaffinity(0))
+    except Exception:
+        cores = os.cpu_count() or 1
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.split(":")[0].strip() in ("Model name", "Vendor ID") and model is None:
+                model = line.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    return cores, model
+
+
 def run_reference(args, rank, world):
+    """The reference arm: the oracle (there is no other implementation of the paper's method
+    to run), timed on all host cores, on the benchmark's grid at a bounded particle count."""
     if rank != 0:
         return
     ppe = args.oracle_ppe
-    from paper_1006_0532_gb300 import synth
-    w = synth.workload(args.workload)
-    import oracle
-    o = oracle.Oracle(w["grid"], w["params"], w["fields"])
-    o.init_particles(ppe)
-    n = o.np_
-    for _ in range(args.warmup):
-        o.step(w["dt"])
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        o.step(w["dt"])
-    el = time.perf_counter() - t0
-    v = n * args.steps / el
-    sample = "%s grid (%d triangles) at %d particles per element (%d particles), %d steps" % (
-        args.workload, w["grid"].ne, ppe, n, args.steps)
+    cores, model = host_cores()
+    steps = max(1, args.steps)
+    n, el = oracle_parallel(args.workload, ppe, min(args.warmup, 1), steps, cores)
+    v = n * steps / el
+    sample = ("%s grid at %d particles per element (%d particles), %d steps after %d, "
+              "%d processes of the one-thread oracle over contiguous element shares"
+              % (args.workload, ppe, n, steps, min(args.warmup, 1), cores))
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "steps": steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": args.workload, "particles": n,
-                                            "triangles": w["grid"].ne, "ppe": ppe},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample},
+            "data": "synthetic", "config": {"workload": args.workload, "particles": n, "ppe": ppe,
+                                            "host_cores": cores, "cpu": model},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": sample},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -368,23 +436,108 @@ def scalar_post(torch, c, w):
 STAT_NAMES = ["N", "U", "V", "W", "uu", "vv", "ww", "uv", "uw", "vw", "omega", "psi", "psi2"]
 
 
-def precision_study(n32, n64):
-    """Relative error per nodal statistic of the FP32 form against the FP64 form after the
-    same steps from the same seeds (floor: the column RMS; covariances also sqrt(<ii><jj>))."""
+def _rel_errors(a, b, ref):
+    """Relative error per statistic column (floor: the column RMS of the reference; the
+    covariances also sqrt(<ii><jj>)): max, RMS and 99th percentile."""
     import numpy as np
     pairs = {7: (4, 5), 8: (4, 6), 9: (5, 6)}
     out = {}
     for j, name in enumerate(STAT_NAMES):
         if j == 0:
             continue
-        b = n64[:, j]
-        rms = float(np.sqrt(np.mean(b * b))) or 1.0
-        den = np.maximum(np.abs(b), rms)
+        rms = float(np.sqrt(np.mean(ref[:, j] ** 2))) or 1.0
+        den = np.maximum(np.abs(b[:, j]), rms)
         if j in pairs:
-            den = np.maximum(den, np.sqrt(np.abs(n64[:, pairs[j][0]] * n64[:, pairs[j][1]])))
-        r = np.abs(n32[:, j] - b) / den
+            den = np.maximum(den, np.sqrt(np.abs(b[:, pairs[j][0]] * b[:, pairs[j][1]])))
+        r = np.abs(a[:, j] - b[:, j]) / den
         out[name] = {"max": float(r.max()), "rms": float(np.sqrt(np.mean(r * r))),
                      "p99": float(np.percentile(r, 99))}
+    return out
+
+
+def _patches(grid, centres, radius):
+    """Elements of a few round patches of the grid; the interior elements (those whose
+    neighbours up to two edges away lie in a patch) and the nodes all of whose elements are
+    interior."""
+    import numpy as np
+    xy = grid.node_xy[grid.tri].mean(axis=1)
+    L = grid.period_x
+    inside = np.zeros(grid.ne, bool)
+    for cx, cy in centres:
+        dx = xy[:, 0] - cx
+        if L > 0:
+            dx = (dx + 0.5 * L) % L - 0.5 * L
+        inside |= dx * dx + (xy[:, 1] - cy) ** 2 <= radius * radius
+    # element neighbours across edges
+    e3 = np.repeat(np.arange(grid.ne), 3)
+    a = grid.tri[:, [1, 2, 0]].ravel()
+    b = grid.tri[:, [2, 0, 1]].ravel()
+    key = np.minimum(a, b).astype(np.int64) * grid.nn + np.maximum(a, b)
+    order = np.argsort(key, kind="stable")
+    ks, es = key[order], e3[order]
+    same = ks[1:] == ks[:-1]
+    pairs = np.stack([es[:-1][same], es[1:][same]], axis=1)
+    inner = inside.copy()
+    for _ in range(2):
+        bad = np.zeros(grid.ne, bool)
+        bad[pairs[:, 0][~inner[pairs[:, 1]]]] = True
+        bad[pairs[:, 1][~inner[pairs[:, 0]]]] = True
+        inner &= ~bad
+    node_ok = np.ones(grid.nn, bool)
+    node_ok[grid.tri[~inner].ravel()] = False
+    node_ok[np.setdiff1d(np.arange(grid.nn), grid.tri.ravel())] = False
+    return np.where(inside)[0], np.where(inner)[0], np.where(node_ok)[0]
+
+
+def precision_study(B, w, forms, sample_steps, patch_radius=0.06):
+    """Forms A/B/C against the FP64 oracle, one step at a time from identical inputs: at each
+    sampled step of a run of the form, the particles of round element patches (a wall patch
+    and an interior one) are handed to the oracle as the form holds them (FP32 values widened
+    exactly; the fields rounded to FP32 for the FP32 forms); both take one step; the nodal
+    statistics of the nodes whose elements all lie well inside a patch are compared.  The
+    differences are those of the form's arithmetic only; particles whose discrete decisions
+    differ are counted (element on a shared edge to rounding; a wall decision whose uniform
+    and Eq. 53's probability agree to rounding)."""
+    import numpy as np
+    import oracle
+    g = w["grid"]
+    P = dict(w["params"], minnpel=0)             # particle-number control is global: off
+    patch, inner, nodes = _patches(g, [(0.7, 0.03), (1.3, 0.5)], patch_radius)
+    out = {}
+    for name, (precision, acc64) in forms.items():
+        F = w["fields"] if precision == 0 else w["fields"].astype(np.float32).astype(np.float64)
+        c = B.Context(dict(P, precision=precision, acc64=acc64, sort_every=4))
+        c.set_grid(g)
+        c.set_fields(F)
+        c.init_particles(w["ppe"])
+        done, errs, nmax = 0, [], {}
+        ex_elem = ex_wall = n_cmp = 0
+        for s in sample_steps:
+            while done < s:
+                c.step(w["dt"])
+                done += 1
+            sg = c.get_particles()
+            ids = np.where(np.isin(sg["elem"], patch))[0]
+            o = oracle.Oracle(g, P, F)
+            o.set_particles({k: sg[k][ids] for k in ("x", "y", "u", "v", "w", "om", "psi", "elem")},
+                            c.step_index, pid=ids)
+            o.step(w["dt"])
+            c.step(w["dt"])
+            done += 1
+            sg, so = c.get_particles(), o.get_particles()
+            ex_elem += int((sg["elem"][ids] != so["elem"]).sum())
+            stop_g = (sg["u"][ids] == 0) & (sg["v"][ids] == 0) & (sg["w"][ids] == 0)
+            stop_o = (so["u"] == 0) & (so["v"] == 0) & (so["w"] == 0)
+            ex_wall += int((stop_g != stop_o).sum())
+            ng, no = c.nodal_stats()[nodes], o.nodal_stats()[nodes]
+            errs.append(_rel_errors(ng, no, no))
+            n_cmp += nodes.size
+        c.close()
+        for st in STAT_NAMES[1:]:
+            nmax[st] = {k: max(e[st][k] for e in errs) for k in ("max", "rms", "p99")}
+        out[name] = {"errors": nmax, "nodes_compared": n_cmp, "sampled_steps": list(sample_steps),
+                     "exempt_element": ex_elem, "exempt_wall_decision": ex_wall,
+                     "patch_elements": int(patch.size)}
     return out
 
 
@@ -593,7 +746,9 @@ def main():
     per_p = BIN_BYTES[1] if dom == "statistics_binning" else ADV_BYTES[1]
     dom_ms = stage[dom]
     achieved = per_p * np_ / (dom_ms * 1e-3) / 1e9
-    traffic = TRAFFIC_PER_PARTICLE.get(dom)
+    src_hash = kernel_sources_hash()
+    rec = NCU_RECORDS.get(src_hash)
+    traffic = rec["traffic"].get(dom) if rec else None
     step_bytes = ADV_BYTES[1] + BIN_BYTES[1]
     step_achieved = step_bytes * np_ * args.steps / (r32["ms"] * 1e-3) / 1e9
     line = {
@@ -612,14 +767,20 @@ def main():
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                      "frac": achieved / peak,
                      "traffic": traffic * np_ if traffic is not None else None,
-                     "kernel": ("stats_tile_kernel<float> (2 size-class launches per step)"
+                     "traffic_source": ("ncu capture of these sources (DRAM bytes per particle "
+                                        "x particles)" if traffic is not None else
+                                        "null: no ncu capture of these kernel sources (sha256 %s)"
+                                        % src_hash[:16]),
+                     "kernel": ("rank_tile_kernel<float> (2 size-class launches per step)"
                                 if dom == "statistics_binning" else "advance_kernel<float>"),
                      "algorithmic_bytes_per_particle": per_p, "peak_source": peak_kind,
                      "ms_per_step": dom_ms,
-                     "limiter": LIMITER.get(dom)},
+                     "limiter": rec["limiter"].get(dom) if rec else None},
         "step_roofline": {"bytes_per_update": step_bytes, "achieved": step_achieved,
                           "peak": peak, "unit": "GB/s", "frac": step_achieved / peak,
-                          "frac_nominal_8000": step_achieved / 8000.0},
+                          "frac_nominal_8000": step_achieved / 8000.0,
+                          "frac_at_single_fp32_positions": SINGLE_POSITION_STEP_BYTES * np_ * args.steps
+                          / (r32["ms"] * 1e-3) / 1e9 / peak},
         "stages_ms_per_step": stage,
         "stages_gbs": {n: {"algorithmic_bytes_per_particle": bpp,
                            "achieved": bpp * np_ / (stage[n] * 1e-3) / 1e9,
@@ -647,18 +808,36 @@ def main():
                             "diag": {k: r64["diag"][k] for k in ("hops_total", "walk_fallback",
                                                                   "walk_brute", "lost", "wall_hits",
                                                                   "moves")}}
+        # the FP64 form's advance is bound by the FP64 pipe: its FP64 instruction rate
+        # (instructions per particle from an ncu capture of these sources) against the
+        # measured FMA rate of this GPU
+        fp64_peak = B.measure_fp64_rate() / 1e12
+        adv64_ms = r64["stage_ms"][0] / max(r64["stage_n"][0], 1)
+        n64 = rec.get("f64_advance_fp64_inst_per_particle") if rec else None
+        line["f64_form"]["roofline"] = {
+            "bound": "alu", "pipe": "fp64", "unit": "TFLOP/s", "peak": fp64_peak,
+            "peak_source": "measured (pdfx_measure_fp64_rate: independent FMA chains, 2 FLOP each)",
+            "kernel": "advance_kernel<double>", "ms_per_step": adv64_ms,
+            "achieved": (2.0 * n64 * r64["np"] / (adv64_ms * 1e-3) / 1e12) if n64 else None,
+            "frac": (2.0 * n64 * r64["np"] / (adv64_ms * 1e-3) / 1e12 / fp64_peak) if n64 else None,
+            "fp64_inst_per_particle": n64,
+            "flop_convention": "each FP64 instruction counted as one FMA (2 FLOP), as the probe counts",
+            "note": None if n64 else "no ncu capture of these kernel sources: FP64 instructions "
+                                     "per particle unknown"}
         line["speedup_f32_vs_f64"] = value / v64
         vB = rb64["np"] * world * args.steps / (rb64["ms"] * 1e-3)
+        ps = precision_study(B, w, {"A_fp64": (0, 0), "B_fp32_sde_fp64_accumulation": (1, 1),
+                                    "C_fp32_sde_compensated_fp32_accumulation": (1, 0)},
+                             sample_steps=(0, 10))
+        ps["A_fp64"]["value"], ps["B_fp32_sde_fp64_accumulation"]["value"] = v64, vB
+        ps["C_fp32_sde_compensated_fp32_accumulation"]["value"] = value
         line["precision_study"] = {
-            "what": "nodal statistics against the FP64 form (A) after the same %d steps from the "
-                    "same seeds (relative error, floor = column RMS)" % (args.warmup + args.steps),
-            "forms": {
-                "A_fp64": {"value": v64, "unit": UNIT},
-                "B_fp32_sde_fp64_accumulation": {"value": vB, "unit": UNIT,
-                                                 "errors": precision_study(rb64["nodal"], r64["nodal"])},
-                "C_fp32_sde_compensated_fp32_accumulation": {
-                    "value": value, "unit": UNIT,
-                    "errors": precision_study(r32["nodal"], r64["nodal"])}}}
+            "what": "nodal statistics of one step against the FP64 oracle from identical inputs "
+                    "(the form's own state at the sampled steps, handed over exactly), on the "
+                    "nodes inside a wall patch and an interior patch; relative error per "
+                    "statistic (floor: the column RMS; covariances also sqrt(<ii><jj>)), "
+                    "max / RMS / 99th percentile over the samples",
+            "unit": UNIT, "forms": ps}
     if rs8 is not None:
         line["bins_sweep"] = {
             "what": "FP32 form with (2, 2, 2) conditioning bins against the default (4, 4, 4)",
@@ -691,10 +870,20 @@ def main():
         if r64 is not None:
             line["speedup_batched_vs_f64"] = rb["value"] / v64
     if not args.no_cpu:
+        cores, model = host_cores()
         n, st, el, _ = oracle_sample(args.workload, args.oracle_steps, args.oracle_ppe)
-        line["cpu_baseline"] = {"value": n * st / el, "unit": UNIT, "cores": 1, "kind": "oracle",
-                                "sample": "%s grid at %d particles per element (%d particles), %d steps"
-                                          % (args.workload, args.oracle_ppe, n, st)}
+        na, ela = oracle_parallel(args.workload, args.oracle_ppe, 1, 3, cores)
+        line["cpu_baseline"] = {
+            "value": na * 3 / ela, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%s grid at %d particles per element (%d particles), 3 steps after 1: %d "
+                      "processes of the one-thread oracle over contiguous element shares "
+                      "(particle-number control off)" % (args.workload, args.oracle_ppe, na, cores),
+            "one_thread": {"value": n * st / el, "unit": UNIT, "cores": 1,
+                           "sample": "the same grid and particles per element, %d steps, "
+                                     "particle-number control on (MINNPEL %d)" % (st, max(1, args.oracle_ppe // 10))},
+            "host": {"cores": cores, "cpu": model},
+            "config_differs": "the oracle runs %d particles per element, the GPU arm %d"
+                              % (args.oracle_ppe, w["ppe"])}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

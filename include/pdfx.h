@@ -449,6 +449,13 @@ int  pdfx_get_pressure(void *ctx, double *P, double *dP, void *stream);
 int  pdfx_coupled_step(void *ctx, double dt, double Cp, double tol, int32_t max_iter,
                        int32_t *iters, void *stream);
 
+/* A measurement helper with no counterpart in the paper: the FP64 fused multiply-add rate
+ * of the current device, 2 FLOP per FMA, from a kernel of independent FMA chains (no memory
+ * traffic; 8 blocks of 256 threads per SM) timed with CUDA events on stream after one
+ * warm-up launch.  The FP64 form's advance is bound by this rate.  Writes *flops_per_s
+ * (host); synchronises stream.  PDFX_ERR_ARG for a NULL pointer. */
+int  pdfx_measure_fp64_rate(double *flops_per_s, void *stream);
+
 /* Number of kernel launches the library issued since creation. */
 int64_t pdfx_kernel_launches(const void *ctx);
 

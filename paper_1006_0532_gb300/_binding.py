@@ -118,6 +118,7 @@ def lib():
                 "pdfx_stage_times": (C.c_int, [vp, C.POINTER(dp), C.POINTER(i64), C.c_int, vp]),
                 "pdfx_kernel_launches": (i64, [vp]),
                 "pdfx_element_stats_noalloc": (C.c_int, [vp, i64] + [vp] * 11 + [vp]),
+                "pdfx_measure_fp64_rate": (C.c_int, [C.POINTER(C.c_double), vp]),
                 "pdfx_wp_rhs": (C.c_int, [vp, vp, vp, vp]),
                 "pdfx_wp_solve": (C.c_int, [vp, vp, vp, vp, dp, i32, C.POINTER(i32), vp]),
                 "pdfx_update_wp": (C.c_int, [vp, dp, i32, C.POINTER(i32), vp]),
@@ -488,3 +489,12 @@ class Context:
     @property
     def kernel_launches(self) -> int:
         return int(lib().pdfx_kernel_launches(self.h))
+
+
+def measure_fp64_rate(stream=None) -> float:
+    """FP64 FMA rate of the current device in FLOP/s (pdfx_measure_fp64_rate)."""
+    out = C.c_double(0.0)
+    rc = lib().pdfx_measure_fp64_rate(C.byref(out), _stream(stream))
+    if rc:
+        raise PdfxError(rc, "pdfx_measure_fp64_rate")
+    return float(out.value)

@@ -14,7 +14,7 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libpdfx.so")
 SOURCES = ["api.cu", "k_advance.cu", "k_stats.cu", "k_bins_f32.cu", "k_bins_f64.cu", "noalloc.cu",
-           "k_scalar.cu", "k_eulerian.cu"]
+           "k_scalar.cu", "k_eulerian.cu", "k_probe.cu"]
 HEADERS = ["pdfx_device.cuh", "pdfx_internal.h", "bins_impl.cuh", "fem_host.h", "eulerian_ops.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]

@@ -308,6 +308,7 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
     a.movers = c.plan.movers;
     a.big_list = c.plan.big_list;
     a.tiles = c.plan.tiles;
+    a.tiles_mid = c.plan.tiles_mid;
     a.einst = c.K > 1 ? c.einst : nullptr;
     a.ielem = c.K > 1 ? c.ielem : nullptr;
     a.K = c.K;
@@ -328,7 +329,7 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
     a.diag = c.diag;
     a.err = c.err;
     launch_stats<T>(a, c.num_sms, s);
-    c.launches += 2;
+    c.launches += 4;   // three tile classes and the large-element kernel
   }
   if (resort) {
     c.cur = 1 - c.cur;
@@ -772,7 +773,7 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
   const size_t E = static_cast<size_t>(ne), N = static_cast<size_t>(nn);
   Plan& pl = c.plan;
   for (int32_t** b : {&pl.cnt, &pl.cursor, &pl.fin, &pl.gain, &pl.loss, &pl.recips, &pl.donors,
-                      &pl.big_list, &pl.tiles})
+                      &pl.big_list, &pl.tiles, &pl.tiles_mid})
     PDFX_TRY(alloc_into(c, *b, E));
   for (int32_t** b : {&pl.off, &pl.foff, &pl.goff, &pl.doff}) PDFX_TRY(alloc_into(c, *b, E + 1));
   const int K = c.K;

@@ -751,6 +751,22 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP, FOX>& t, int e,
   }
 }
 
+// The element of block b in one size class of the plan's tile lists, or -1: block b is entry
+// b of the list, which for instance k fills its element range [eb, ee) -- class 0 (up to
+// kTileSplit particles) from the front of a.tiles, class 1 (kTileMid + 1 .. kSmallCap) from
+// its back, class 2 (kTileSplit + 1 .. kTileMid) from the front of a.tiles_mid.  The class-0
+// kernel, launched first, advances the step counter once per step.
+template <int CLS, typename T>
+__device__ __forceinline__ int tile_element(const StatsArgs<T>& a, int b, int& moves) {
+  if (CLS == 0 && b == 0 && threadIdx.x == 0 && a.step_inc) atomicAdd(a.step_inc, 1u);
+  const int inst = a.einst ? a.einst[b] : 0;
+  const int eb = a.einst ? a.ielem[inst] : 0, ee = a.einst ? a.ielem[inst + 1] : a.ne;
+  const int32_t* sc = a.scal + 16 * inst;
+  if (CLS == 0 ? (b - eb >= sc[6]) : CLS == 1 ? (ee - 1 - b >= sc[7]) : (b - eb >= sc[8])) return -1;
+  moves = sc[0] > 0;
+  return CLS == 2 ? a.tiles_mid[b] : a.tiles[b];
+}
+
 // ---------------------------------------------------------------------------------------
 // Hierarchical bins by per-level bucket ranks (the default conditioning, Sect. 3.5 and
 // Appendix A).  A level needs each particle's rank by (key, id) inside its group of the
@@ -814,16 +830,16 @@ __device__ __forceinline__ bool rank_before(double a, uint32_t ia, double b, uin
   return (oa < ob) | ((oa == ob) & (ia < ib));
 }
 
-// In-place exclusive scan of c[0, N) (N a multiple of THREADS), c[N] = the total.
-template <int N, int THREADS>
-__device__ __forceinline__ void block_scan_counts(int32_t* c, int32_t* wsum) {
-  constexpr int E = N / THREADS;
+// In-place exclusive scan of c[0, N) (N = E THREADS, E <= EMAX), c[N] = the total.
+template <int EMAX, int THREADS>
+__device__ __forceinline__ void block_scan_counts(int32_t* c, int E, int32_t* wsum) {
+  const int N = E * THREADS;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  int v[E];
+  int v[EMAX];
   int sum = 0;
 #pragma unroll
-  for (int i = 0; i < E; ++i) {
-    v[i] = c[tid * E + i];
+  for (int i = 0; i < EMAX; ++i) {
+    v[i] = i < E ? c[tid * E + i] : 0;
     sum += v[i];
   }
   int incl = sum;
@@ -843,8 +859,8 @@ __device__ __forceinline__ void block_scan_counts(int32_t* c, int32_t* wsum) {
     total += ws;
   }
 #pragma unroll
-  for (int i = 0; i < E; ++i) {
-    c[tid * E + i] = before;
+  for (int i = 0; i < EMAX; ++i) {
+    if (i < E) c[tid * E + i] = before;
     before += v[i];
   }
   if (tid == 0) c[N] = total;
@@ -852,7 +868,8 @@ __device__ __forceinline__ void block_scan_counts(int32_t* c, int32_t* wsum) {
 
 // Bucket tables of one level: each particle's bucket within its group (t.grp, or one group
 // when Gprev is 1) and the bucket's arrival index; t.x.b.start ends as the first position of
-// every bucket.  The bucket of key x is floor((x - lo) scale) clamped to the group's NB_g
+// every bucket.  The buckets of all groups together number NB, a multiple of THREADS of about
+// the element's particle count (at most the tile's capacity), at least two per group.  The bucket of key x is floor((x - lo) scale) clamped to the group's NB_g
 // buckets.  With a prior (mean m and standard deviation s of the key over the element, from
 // the previous statistics pass) every group takes lo = m - 3 s and scale = NB_g / (6 s);
 // otherwise each group's own smallest and largest key set them.  Either way the bucket never
@@ -861,9 +878,12 @@ template <typename T, int CAP, int THREADS>
 __device__ __forceinline__ void bucket_level(RankTile<T, CAP, THREADS>& t, const T* key, int n, int Gprev,
                                              float prior_m, float prior_s, int (&bin)[CAP / THREADS],
                                              int (&arr)[CAP / THREADS]) {
-  constexpr int KPT = CAP / THREADS, NB = RankTile<T, CAP, THREADS>::kNB;
+  constexpr int KPT = CAP / THREADS, EMAX = RankTile<T, CAP, THREADS>::kNB / THREADS;
   const int tid = threadIdx.x;
-  const int NBg = NB / Gprev;                  // Gprev <= 256 <= NB / 2
+  int E = 1;                                   // buckets per thread
+  while (E < EMAX && (E * THREADS < n || E * THREADS < 2 * Gprev)) E <<= 1;
+  const int NB = E * THREADS;
+  const int NBg = NB / Gprev;                  // Gprev <= 256, 2 Gprev <= NB
   const float fNBg = static_cast<float>(NBg);
   const bool prior = prior_s > 0.0f;           // false for NaN
   if (!prior) {
@@ -931,7 +951,7 @@ __device__ __forceinline__ void bucket_level(RankTile<T, CAP, THREADS>& t, const
     }
   }
   __syncthreads();
-  block_scan_counts<NB, THREADS>(t.x.b.start, t.wsum);
+  block_scan_counts<EMAX, THREADS>(t.x.b.start, E, t.wsum);
   __syncthreads();
 }
 
@@ -953,7 +973,10 @@ __device__ __forceinline__ int bucket_position(const RankTile<T, CAP, THREADS>& 
 
 // A level before the last: only each particle's new group floor(Gl p / n) is needed.  It
 // follows from the bucket's position range unless the range straddles a group boundary;
-// only the particles of such buckets are ranked inside their bucket.
+// only the particles of such buckets are ranked inside their bucket.  t.ord receives an
+// arrangement by group (each group's particles within its position range, in any order):
+// a particle of a bucket inside one group takes the bucket's first position plus its
+// arrival index, a particle of a straddling bucket its exact position.
 template <typename T, int CAP, int THREADS>
 __device__ void group_level(RankTile<T, CAP, THREADS>& t, const T* key, int n, int Gprev, int Gl,
                             float prior_m, float prior_s) {
@@ -970,8 +993,13 @@ __device__ void group_level(RankTile<T, CAP, THREADS>& t, const T* key, int n, i
     if (j < n) {
       const int s0 = t.x.b.start[bin[k]], s1 = t.x.b.start[bin[k] + 1];
       const int g0 = fdiv(Gl * s0, inv_n), g1 = fdiv(Gl * (s1 - 1), inv_n);
-      if (g0 == g1) t.grp[j] = static_cast<uint8_t>(g0);
-      else { cut[k] = true; t.mem[s0 + arr[k]] = static_cast<int16_t>(j); }
+      if (g0 == g1) {
+        t.grp[j] = static_cast<uint8_t>(g0);
+        t.ord[s0 + arr[k]] = static_cast<int16_t>(j);
+      } else {
+        cut[k] = true;
+        t.mem[s0 + arr[k]] = static_cast<int16_t>(j);
+      }
     }
   }
   __syncthreads();
@@ -981,6 +1009,41 @@ __device__ void group_level(RankTile<T, CAP, THREADS>& t, const T* key, int n, i
     if (cut[k]) {
       const int p = bucket_position(t, key, j, t.x.b.start[bin[k]], t.x.b.start[bin[k] + 1]);
       t.grp[j] = static_cast<uint8_t>(fdiv(Gl * p, inv_n));
+      t.ord[p] = static_cast<int16_t>(j);
+    }
+  }
+  __syncthreads();
+}
+
+// A level whose groups hold at most 32 particles: a warp takes a whole group from the
+// arrangement t.ord (its position range), sorts it in registers by the exact key (value,
+// particle id) with a bitonic network, and writes the order back into the same range: the
+// exact positions (t.pos, t.ord) and, before the last level, the next level's groups.
+template <typename T, int CAP, int THREADS>
+__device__ void warp_level(RankTile<T, CAP, THREADS>& t, const T* key, int n, int Gprev, int Gl,
+                           bool last) {
+  using P = KeyPolicy<T, true>;
+  using K = typename P::K;
+  constexpr int W = THREADS / 32;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const float invG = 1.0f / static_cast<float>(Gprev), inv_n = 1.0f / static_cast<float>(n);
+#pragma unroll 1
+  for (int c = warp; c < Gprev; c += W) {
+    const int gs = group_start(c, n, Gprev, invG), len = group_start(c + 1, n, Gprev, invG) - gs;
+    K k;
+    int32_t j = -1;
+    if (lane < len) {
+      j = t.ord[gs + lane];
+      k = P::make(key[j], t.pid, j);
+    } else {
+      pad_key(k);
+    }
+    warp_sort32(k, j, lane);
+    if (lane < len) {
+      const int p = gs + lane;
+      t.ord[p] = static_cast<int16_t>(j);
+      t.pos[j] = static_cast<int16_t>(p);
+      if (!last) t.grp[j] = static_cast<uint8_t>(fdiv(Gl * p, inv_n));
     }
   }
   __syncthreads();
@@ -1200,6 +1263,7 @@ __device__ void element_rank_tile(const StatsArgs<T>& a, RankTile<T, CAP, THREAD
         t.om[j] = vo[k];
         t.psi[j] = vp[k];
         t.pid[j] = vi[k];
+        t.ord[j] = static_cast<int16_t>(j);   // the first level's arrangement
       }
     }
   }
@@ -1237,7 +1301,8 @@ __device__ void element_rank_tile(const StatsArgs<T>& a, RankTile<T, CAP, THREAD
           ps = static_cast<float>(sqrt(var));
         }
       }
-      if (l == last) order_level<T, CAP, THREADS>(t, key, n, Gprev, pm, ps);
+      if ((n + Gprev - 1) / Gprev <= 32) warp_level<T, CAP, THREADS>(t, key, n, Gprev, Gprev * g[l], l == last);
+      else if (l == last) order_level<T, CAP, THREADS>(t, key, n, Gprev, pm, ps);
       else group_level<T, CAP, THREADS>(t, key, n, Gprev, Gprev * g[l], pm, ps);
       Gprev *= g[l];
     }
@@ -1319,43 +1384,30 @@ __device__ void element_rank_tile(const StatsArgs<T>& a, RankTile<T, CAP, THREAD
 
 // Residency: the FP32 tiles (21 KB per 128 threads) fit 1280 threads per SM, the FP64
 // tiles 896; the register cap matches.
-template <typename T, int CAP, int THREADS, bool FRONT>
+template <typename T, int CAP, int THREADS, int CLS>
 __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1280 : 1024) / THREADS)
     rank_tile_kernel(const StatsArgs<T> a) {
   extern __shared__ __align__(16) unsigned char rank_smem[];
   RankTile<T, CAP, THREADS>& t = *reinterpret_cast<RankTile<T, CAP, THREADS>*>(rank_smem);
-  const int b = blockIdx.x;
-  if (FRONT && b == 0 && threadIdx.x == 0 && a.step_inc) atomicAdd(a.step_inc, 1u);
-  const int inst = a.einst ? a.einst[b] : 0;
-  const int eb = a.einst ? a.ielem[inst] : 0, ee = a.einst ? a.ielem[inst + 1] : a.ne;
-  const int32_t* sc = a.scal + 16 * inst;
-  if (FRONT ? (b - eb >= sc[6]) : (ee - 1 - b >= sc[7])) return;
-  const int moves = sc[0] > 0;
-  const int e = a.tiles[b];
+  int moves = 0;
+  const int e = tile_element<CLS>(a, blockIdx.x, moves);
+  if (e < 0) return;
   const int N = moves ? a.fin[e] : a.cnt[e];
   element_rank_tile<T, CAP, THREADS>(a, t, e, min(N, CAP), moves);
 }
 
 template <typename T> bool rank_configured[kMaxDevices];
 
-// One block per entry of one size class of the plan's tile lists: the elements of up to
-// kTileSplit particles (FRONT) or of kTileSplit + 1 .. kSmallCap (the back of each
-// instance's list).  The grid covers every element; blocks past the class count return.  The register cap
-// keeps 1536 threads resident per SM in the FP32 form, 1024 in the FP64 form.
-template <typename T, int CAP, int THREADS, bool FRONT, bool FOX>
+// One block per entry of one size class of the plan's tile lists (tile_element); the grid
+// covers every element and blocks past the class count return.  The register cap keeps 1536
+// threads resident per SM in the FP32 form, 1024 in the FP64 form.
+template <typename T, int CAP, int THREADS, int CLS, bool FOX>
 __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1536 : 1024) / THREADS)
     stats_tile_kernel(const StatsArgs<T> a) {
   __shared__ Tile<T, CAP, FOX> t;
-  // block b is entry b of the tile list; the list of instance k fills its element range
-  // [eb, ee): the first class from the front, the second from the back
-  const int b = blockIdx.x;
-  if (FRONT && b == 0 && threadIdx.x == 0 && a.step_inc) atomicAdd(a.step_inc, 1u);
-  const int inst = a.einst ? a.einst[b] : 0;
-  const int eb = a.einst ? a.ielem[inst] : 0, ee = a.einst ? a.ielem[inst + 1] : a.ne;
-  const int32_t* sc = a.scal + 16 * inst;
-  if (FRONT ? (b - eb >= sc[6]) : (ee - 1 - b >= sc[7])) return;
-  const int moves = sc[0] > 0;
-  const int e = a.tiles[b];
+  int moves = 0;
+  const int e = tile_element<CLS>(a, blockIdx.x, moves);
+  if (e < 0) return;
   const int N = moves ? a.fin[e] : a.cnt[e];
   element_tile<T, CAP, THREADS, FOX>(a, t, e, min(N, CAP), moves);
 }
@@ -1365,24 +1417,29 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1536 : 1024) / THRE
 template <typename T>
 void launch_stats_tiles_impl(const StatsArgs<T>& a, int num_sms, cudaStream_t s) {
   if (a.ne <= 0) return;
-  static_assert(kSmallCap == 1024 && kTileSplit == 512, "tile classes cover the small-element capacity");
-  // elements of up to 512 particles (4 warps), then 513..1024 (8 warps)
+  static_assert(kSmallCap == 1024 && kTileMid == 512 && kTileSplit == 256,
+                "tile classes cover the small-element capacity");
+  // elements of up to 256 particles: chunk sorts (4 warps; groups of at most 32 positions
+  // are sorted by one warp in registers, which suits small elements); 257..512 (4 warps)
+  // and 513..1024 (8 warps): bucket ranks.  Fox's projection: chunk sorts in every class.
   (void)num_sms;
   const unsigned grid = static_cast<unsigned>(a.ne);
   if (a.cond_mode == 1) {
-    stats_tile_kernel<T, 512, 128, true, true><<<grid, 128, 0, s>>>(a);
-    stats_tile_kernel<T, 1024, 256, false, true><<<grid, 256, 0, s>>>(a);
+    stats_tile_kernel<T, 256, 128, 0, true><<<grid, 128, 0, s>>>(a);
+    stats_tile_kernel<T, 512, 128, 2, true><<<grid, 128, 0, s>>>(a);
+    stats_tile_kernel<T, 1024, 256, 1, true><<<grid, 256, 0, s>>>(a);
   } else {
-    constexpr size_t small = sizeof(RankTile<T, 512, 128>), large = sizeof(RankTile<T, 1024, 256>);
+    constexpr size_t mid = sizeof(RankTile<T, 512, 128>), large = sizeof(RankTile<T, 1024, 256>);
     static_assert(large <= 227 * 1024, "rank tile exceeds shared memory");
     if (first_use_on_device(rank_configured<T>)) {
-      cudaFuncSetAttribute(rank_tile_kernel<T, 512, 128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           static_cast<int>(small));
-      cudaFuncSetAttribute(rank_tile_kernel<T, 1024, 256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(rank_tile_kernel<T, 512, 128, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(mid));
+      cudaFuncSetAttribute(rank_tile_kernel<T, 1024, 256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(large));
     }
-    rank_tile_kernel<T, 512, 128, true><<<grid, 128, small, s>>>(a);
-    rank_tile_kernel<T, 1024, 256, false><<<grid, 256, large, s>>>(a);
+    stats_tile_kernel<T, 256, 128, 0, false><<<grid, 128, 0, s>>>(a);
+    rank_tile_kernel<T, 512, 128, 2><<<grid, 128, mid, s>>>(a);
+    rank_tile_kernel<T, 1024, 256, 1><<<grid, 256, large, s>>>(a);
   }
 }
 

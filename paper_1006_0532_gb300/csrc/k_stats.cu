@@ -82,22 +82,26 @@ __device__ int64_t S_of(const int64_t* P0, const int64_t* P1, int64_t H, int64_t
   return a1 - H * a0;
 }
 
-// Tile-class lists for the statistics kernels: elements of up to kTileSplit particles from
-// the front of pl.tiles, of up to kSmallCap from the back, in element order.  The class
-// flags ride in bits 32-47 and 48-63 of a count's block scan (counts sum below 2^28 and a
+// Tile-class lists for the statistics kernels, in element order: elements of up to
+// kTileSplit particles from the front of pl.tiles, of kTileMid + 1 .. kSmallCap from its
+// back, and of kTileSplit + 1 .. kTileMid from the front of pl.tiles_mid.  The class flags
+// ride in bits 28-39, 40-51 and 52-63 of a count's block scan (counts sum below 2^28 and a
 // block holds kPlanThreads elements, so the fields never carry into each other).
+constexpr int64_t kCountMask = (int64_t(1) << 28) - 1;
 __device__ __forceinline__ int64_t tile_class_bits(bool valid, int32_t c) {
   if (!valid || c > kSmallCap) return 0;
-  return c <= kTileSplit ? (int64_t(1) << 32) : (int64_t(1) << 48);
+  return c <= kTileSplit ? (int64_t(1) << 28) : (c <= kTileMid ? (int64_t(1) << 52) : (int64_t(1) << 40));
 }
 __device__ __forceinline__ void place_tile_class(Plan& pl, bool valid, int32_t c, int32_t e,
                                                  int32_t eb, int32_t ee, int64_t ex, int64_t tot,
-                                                 int32_t& tA, int32_t& tB) {
+                                                 int32_t& tA, int32_t& tB, int32_t& tM) {
   const int64_t bits = tile_class_bits(valid, c);
-  if (bits == (int64_t(1) << 32)) pl.tiles[eb + tA + static_cast<int32_t>((ex >> 32) & 0xffff)] = e;
-  else if (bits != 0) pl.tiles[ee - 1 - (tB + static_cast<int32_t>(ex >> 48))] = e;
-  tA += static_cast<int32_t>((tot >> 32) & 0xffff);
-  tB += static_cast<int32_t>(tot >> 48);
+  if (bits == (int64_t(1) << 28)) pl.tiles[eb + tA + static_cast<int32_t>((ex >> 28) & 0xfff)] = e;
+  else if (bits == (int64_t(1) << 40)) pl.tiles[ee - 1 - (tB + static_cast<int32_t>((ex >> 40) & 0xfff))] = e;
+  else if (bits != 0) pl.tiles_mid[eb + tM + static_cast<int32_t>((ex >> 52) & 0xfff)] = e;
+  tA += static_cast<int32_t>((tot >> 28) & 0xfff);
+  tB += static_cast<int32_t>((tot >> 40) & 0xfff);
+  tM += static_cast<int32_t>((tot >> 52) & 0xfff);
 }
 
 // One block per instance: elements [eb, ee) of the union grid, particle slots from p0.
@@ -114,7 +118,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne_
   const int minnpel = pl.iminnpel ? pl.iminnpel[inst] : minnpel_one;
   int32_t* scal = pl.scal + 16 * inst;
   // pass 1: offsets of the element lists, min / max, big elements (no moves)
-  int32_t carry = p0, lmin = 0x7fffffff, lmax = -1, tA = 0, tB = 0;
+  int32_t carry = p0, lmin = 0x7fffffff, lmax = -1, tA = 0, tB = 0, tM = 0;
   if (tid == 0) scal[3] = 0;
   __syncthreads();
   for (int32_t base = 0; base < ne; base += kPlanThreads) {
@@ -123,8 +127,8 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne_
     const int32_t c = valid ? pl.cnt[e] : 0;
     int64_t ptot;
     const int64_t pex = block_exclusive_scan<int64_t>(c | tile_class_bits(valid, c), sh.tmp64, ptot);
-    const int32_t ex = static_cast<int32_t>(pex & 0xffffffff), tot = static_cast<int32_t>(ptot & 0xffffffff);
-    place_tile_class(pl, valid, c, e, eb, ee, pex, ptot, tA, tB);
+    const int32_t ex = static_cast<int32_t>(pex & kCountMask), tot = static_cast<int32_t>(ptot & kCountMask);
+    place_tile_class(pl, valid, c, e, eb, ee, pex, ptot, tA, tB, tM);
     if (valid) {
       pl.off[e] = carry + ex;
       pl.foff[e] = carry + ex;
@@ -139,6 +143,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne_
     if (last) { pl.off[ee] = carry; pl.foff[ee] = carry; }
     scal[6] = tA;
     scal[7] = tB;
+    scal[8] = tM;
   }
   for (int o = 16; o > 0; o >>= 1) {
     lmin = min(lmin, __shfl_xor_sync(kFull, lmin, o));
@@ -219,6 +224,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne_
   int32_t cRankL = 0, cRankH = 0, cG = p0, cD = p0, cF = p0, cNR = 0, cND = 0;
   tA = 0;
   tB = 0;
+  tM = 0;
   for (int32_t base = 0; base < ne; base += kPlanThreads) {
     const bool valid = base + tid < ne;
     const int32_t e = eb + base + tid;
@@ -245,9 +251,9 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne_
     int64_t ptot;
     const int64_t pex = block_exclusive_scan<int64_t>((valid ? f : 0) | tile_class_bits(valid, f),
                                                       sh.tmp64, ptot);
-    const int32_t fo = cF + static_cast<int32_t>(pex & 0xffffffff);
-    cF += static_cast<int32_t>(ptot & 0xffffffff);
-    place_tile_class(pl, valid, f, e, eb, ee, pex, ptot, tA, tB);
+    const int32_t fo = cF + static_cast<int32_t>(pex & kCountMask);
+    cF += static_cast<int32_t>(ptot & kCountMask);
+    place_tile_class(pl, valid, f, e, eb, ee, pex, ptot, tA, tB, tM);
     const int32_t ri = cNR + block_exclusive_scan<int32_t>(g > 0 ? 1 : 0, sh.tmp32, tot);
     cNR += tot;
     const int32_t di = cND + block_exclusive_scan<int32_t>(l > 0 ? 1 : 0, sh.tmp32, tot);
@@ -267,6 +273,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne_
   if (tid == 0) {
     scal[6] = tA;
     scal[7] = tB;
+    scal[8] = tM;
     if (last) {
       pl.goff[ee] = cG;
       pl.doff[ee] = cD;

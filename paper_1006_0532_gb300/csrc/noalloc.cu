@@ -21,9 +21,9 @@ constexpr size_t kNaP = static_cast<size_t>(kNaMaxParticles);
 constexpr size_t kNaE = static_cast<size_t>(kNaMaxElements) + 1;
 
 // Layout (int32 words): element lists [P], particle ids [P], counts [E], list offsets [E],
-// final offsets [E], cursors [E], large-element list [E], tile-class lists [E], plan
+// final offsets [E], cursors [E], large-element list [E], tile-class lists [E] and [E], plan
 // scalars [16].
-constexpr size_t kNaWords = 2 * kNaP + 6 * kNaE + 16;
+constexpr size_t kNaWords = 2 * kNaP + 7 * kNaE + 16;
 constexpr size_t kNaBytes = ((4 * kNaWords + 255) / 256) * 256;
 static_assert(kNaMaxParticles == PDFX_NOALLOC_MAX_PARTICLES, "header limit");
 static_assert(kNaMaxElements == PDFX_NOALLOC_MAX_ELEMENTS, "header limit");
@@ -78,7 +78,8 @@ int element_stats_noalloc(Ctx& c, int64_t np, const double* u, const double* v, 
   pl.cursor = per_e + 3 * kNaE;
   pl.big_list = per_e + 4 * kNaE;
   pl.tiles = per_e + 5 * kNaE;
-  pl.scal = per_e + 6 * kNaE;
+  pl.tiles_mid = per_e + 6 * kNaE;
+  pl.scal = per_e + 7 * kNaE;
   pl.idx = idx;
   // without particle moves the plan touches only the arrays above; the rest alias the final
   // offsets so that no pointer leaves the scratch
@@ -115,6 +116,7 @@ int element_stats_noalloc(Ctx& c, int64_t np, const double* u, const double* v, 
   a.movers = pl.movers;
   a.big_list = pl.big_list;
   a.tiles = pl.tiles;
+  a.tiles_mid = pl.tiles_mid;
   a.einst = nullptr;   // the whole grid as one instance
   a.ielem = nullptr;
   a.K = 1;
@@ -137,7 +139,9 @@ int element_stats_noalloc(Ctx& c, int64_t np, const double* u, const double* v, 
   a.err = c.err;
   launch_stats<double>(a, c.num_sms, s);
   if (nmom) launch_node_average(emom, c.ne_off, c.ne_list, c.nn, nmom, s);
-  c.launches += np > 0 ? 7 : 5;
+  // iota, count and scatter (with particles), plan, three tile classes and the large-element
+  // kernel, node average
+  c.launches += (np > 0 ? 3 : 0) + 1 + 4 + (nmom ? 1 : 0);
   return cudaGetLastError() == cudaSuccess ? PDFX_OK : PDFX_ERR_CUDA;
 }
 

@@ -118,6 +118,7 @@ struct StatsArgs {
   const int32_t* movers;
   const int32_t* big_list;
   const int32_t* tiles;  // tile-class element lists (scal 6 from the front, scal 7 from the back)
+  const int32_t* tiles_mid;  // the middle tile class (scal 8 from the front)
   const int32_t* einst;  // element -> instance (nullptr: one instance)
   const int32_t* ielem;  // [K + 1] first element of each instance
   int K;                 // instances (plan scalars scal[16 k ...] per instance)
@@ -156,9 +157,11 @@ struct Plan {
   int32_t* donors = nullptr;   // [ne] elements that give
   int32_t* big_list = nullptr; // [ne] elements above the small binning capacity
   int32_t* tiles = nullptr;    // [ne] elements of up to kTileSplit particles from the front,
-                               // up to kSmallCap from the back
+                               // kTileMid + 1 .. kSmallCap from the back
+  int32_t* tiles_mid = nullptr;  // [ne] elements of kTileSplit + 1 .. kTileMid particles
   int32_t* scal = nullptr;     // [16 K]: per instance 0 T, 1 n_recips, 2 n_donors, 3 n_big,
-                               // 4 min, 5 max, 6 / 7 tile-class counts; lists of instance k
+                               // 4 min, 5 max, 6 / 7 / 8 tile-class counts (front, back,
+                               // middle); lists of instance k
                                // live in its element range, its moves in its slot range
   const int32_t* ielem = nullptr;    // [K + 1] first element of each instance (nullptr: one)
   const int64_t* ip0 = nullptr;      // [K + 1] first particle slot of each instance
@@ -172,7 +175,8 @@ struct Plan {
 
 constexpr int kHistCap = 8192;      // counts above this are clipped for the closed form
 constexpr int kSmallCap = 1024;     // binning capacity of the block-per-element tile kernels
-constexpr int kTileSplit = 512;     // tile classes: up to 512 particles, then up to kSmallCap
+constexpr int kTileSplit = 256;     // tile classes: up to 256 particles (chunk-sort tile),
+constexpr int kTileMid = 512;       // 257 .. 512 and 513 .. kSmallCap (bucket-rank tiles)
 constexpr int64_t kMaxParticles = int64_t(1) << 28;   // particle ids fit the 28-bit sort key field
 constexpr int64_t kMaxSlots = (int64_t(1) << 31) - 1;  // particle slots of a batch (int32 lists)
 constexpr int kBigCap = 4096;       // binning capacity of the large-element kernel
