@@ -796,14 +796,10 @@ struct RankTile {
   T u[CAP], v[CAP], w[CAP], om[CAP], psi[CAP];
   uint32_t pid[CAP];
   int32_t slot[CAP];
-  union {
-    struct {
-      int32_t start[kNB + 1];       // bucket counts, then each bucket's first position
-      uint32_t glo[256], gsc[256];  // each group's key range, then its bucket origin and scale
-    } b;
-    float2 combf[12 * 32];          // per-lane moment sums, sum-major: compensated FP32
-    double combd[12 * 32];          // or FP64
-  } x;
+  struct {
+    int32_t start[kNB + 1];         // bucket counts, then each bucket's first position
+    uint32_t glo[256], gsc[256];    // each group's key range, then its bucket origin and scale
+  } x_b;
   int16_t ord[CAP];                 // position -> particle (staging index), final level
   int16_t pos[CAP];                 // particle -> position, final level
   int16_t mem[CAP];                 // particles by bucket
@@ -867,35 +863,35 @@ __device__ __forceinline__ void block_scan_counts(int32_t* c, int E, int32_t* ws
 }
 
 // Bucket tables of one level: each particle's bucket within its group (t.grp, or one group
-// when Gprev is 1) and the bucket's arrival index; t.x.b.start ends as the first position of
-// every bucket.  The buckets of all groups together number NB, a multiple of THREADS of about
-// the element's particle count (at most the tile's capacity), at least two per group.  The bucket of key x is floor((x - lo) scale) clamped to the group's NB_g
+// when Gprev is 1) and the bucket's arrival index; t.x_b.start ends as the first position of
+// every bucket.  The buckets of all groups together number NB, a multiple of THREADS of at
+// least nb_min (at most the tile's capacity), at least two per group.  The bucket of key x is floor((x - lo) scale) clamped to the group's NB_g
 // buckets.  With a prior (mean m and standard deviation s of the key over the element, from
 // the previous statistics pass) every group takes lo = m - 3 s and scale = NB_g / (6 s);
 // otherwise each group's own smallest and largest key set them.  Either way the bucket never
 // decreases with the key, which is all the ranks need.
 template <typename T, int CAP, int THREADS>
 __device__ __forceinline__ void bucket_level(RankTile<T, CAP, THREADS>& t, const T* key, int n, int Gprev,
-                                             float prior_m, float prior_s, int (&bin)[CAP / THREADS],
-                                             int (&arr)[CAP / THREADS]) {
+                                             int nb_min, float prior_m, float prior_s,
+                                             int (&bin)[CAP / THREADS], int (&arr)[CAP / THREADS]) {
   constexpr int KPT = CAP / THREADS, EMAX = RankTile<T, CAP, THREADS>::kNB / THREADS;
   const int tid = threadIdx.x;
   int E = 1;                                   // buckets per thread
-  while (E < EMAX && (E * THREADS < n || E * THREADS < 2 * Gprev)) E <<= 1;
+  while (E < EMAX && (E * THREADS < nb_min || E * THREADS < 2 * Gprev)) E <<= 1;
   const int NB = E * THREADS;
   const int NBg = NB / Gprev;                  // Gprev <= 256, 2 Gprev <= NB
   const float fNBg = static_cast<float>(NBg);
   const bool prior = prior_s > 0.0f;           // false for NaN
   if (!prior) {
     for (int g = tid; g < Gprev; g += THREADS) {
-      t.x.b.glo[g] = 0xffffffffu;
-      t.x.b.gsc[g] = 0u;
+      t.x_b.glo[g] = 0xffffffffu;
+      t.x_b.gsc[g] = 0u;
     }
   }
 #pragma unroll
   for (int k = 0; k <= KPT; ++k) {
     const int b = tid + k * THREADS;
-    if (b <= NB) t.x.b.start[b] = 0;
+    if (b <= NB) t.x_b.start[b] = 0;
   }
   int grp[KPT];
   float fk[KPT];
@@ -921,17 +917,17 @@ __device__ __forceinline__ void bucket_level(RankTile<T, CAP, THREADS>& t, const
       const int j = tid + k * THREADS;
       if (j < n) {
         const uint32_t o = ord32(fk[k]);
-        atomicMin(&t.x.b.glo[grp[k]], o);
-        atomicMax(&t.x.b.gsc[grp[k]], o);
+        atomicMin(&t.x_b.glo[grp[k]], o);
+        atomicMax(&t.x_b.gsc[grp[k]], o);
       }
     }
     __syncthreads();
     // per group: the bucket origin (its smallest key) and scale NB_g / (largest - smallest)
     for (int g = tid; g < Gprev; g += THREADS) {
-      const float lo = unord32(t.x.b.glo[g]), hi = unord32(t.x.b.gsc[g]);
+      const float lo = unord32(t.x_b.glo[g]), hi = unord32(t.x_b.gsc[g]);
       const float span = hi - lo;
-      t.x.b.glo[g] = __float_as_uint(lo);
-      t.x.b.gsc[g] = __float_as_uint(span > 0.0f ? fNBg / span : 0.0f);
+      t.x_b.glo[g] = __float_as_uint(lo);
+      t.x_b.gsc[g] = __float_as_uint(span > 0.0f ? fNBg / span : 0.0f);
     }
     __syncthreads();
   }
@@ -941,17 +937,17 @@ __device__ __forceinline__ void bucket_level(RankTile<T, CAP, THREADS>& t, const
     bin[k] = 0;
     arr[k] = 0;
     if (j < n) {
-      const float lo = prior ? plo : __uint_as_float(t.x.b.glo[grp[k]]);
-      const float scale = prior ? pscale : __uint_as_float(t.x.b.gsc[grp[k]]);
+      const float lo = prior ? plo : __uint_as_float(t.x_b.glo[grp[k]]);
+      const float scale = prior ? pscale : __uint_as_float(t.x_b.gsc[grp[k]]);
       const float q = (fk[k] - lo) * scale;
       // q is non-decreasing in the key; NaN (a non-finite state) falls into bucket 0
       const int b = q >= fNBg ? NBg - 1 : (q > 0.0f ? static_cast<int>(q) : 0);
       bin[k] = grp[k] * NBg + b;
-      arr[k] = atomicAdd(&t.x.b.start[bin[k]], 1);
+      arr[k] = atomicAdd(&t.x_b.start[bin[k]], 1);
     }
   }
   __syncthreads();
-  block_scan_counts<EMAX, THREADS>(t.x.b.start, E, t.wsum);
+  block_scan_counts<EMAX, THREADS>(t.x_b.start, E, t.wsum);
   __syncthreads();
 }
 
@@ -984,14 +980,14 @@ __device__ void group_level(RankTile<T, CAP, THREADS>& t, const T* key, int n, i
   const int tid = threadIdx.x;
   const float inv_n = 1.0f / static_cast<float>(n);
   int bin[KPT], arr[KPT];
-  bucket_level(t, key, n, Gprev, prior_m, prior_s, bin, arr);
+  bucket_level(t, key, n, Gprev, n, prior_m, prior_s, bin, arr);
   bool cut[KPT];
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
     const int j = tid + k * THREADS;
     cut[k] = false;
     if (j < n) {
-      const int s0 = t.x.b.start[bin[k]], s1 = t.x.b.start[bin[k] + 1];
+      const int s0 = t.x_b.start[bin[k]], s1 = t.x_b.start[bin[k] + 1];
       const int g0 = fdiv(Gl * s0, inv_n), g1 = fdiv(Gl * (s1 - 1), inv_n);
       if (g0 == g1) {
         t.grp[j] = static_cast<uint8_t>(g0);
@@ -1007,7 +1003,7 @@ __device__ void group_level(RankTile<T, CAP, THREADS>& t, const T* key, int n, i
   for (int k = 0; k < KPT; ++k) {
     const int j = tid + k * THREADS;
     if (cut[k]) {
-      const int p = bucket_position(t, key, j, t.x.b.start[bin[k]], t.x.b.start[bin[k] + 1]);
+      const int p = bucket_position(t, key, j, t.x_b.start[bin[k]], t.x_b.start[bin[k] + 1]);
       t.grp[j] = static_cast<uint8_t>(fdiv(Gl * p, inv_n));
       t.ord[p] = static_cast<int16_t>(j);
     }
@@ -1056,12 +1052,12 @@ __device__ void order_level(RankTile<T, CAP, THREADS>& t, const T* key, int n, i
   constexpr int KPT = CAP / THREADS;
   const int tid = threadIdx.x;
   int bin[KPT], arr[KPT];
-  bucket_level(t, key, n, Gprev, prior_m, prior_s, bin, arr);
+  bucket_level(t, key, n, Gprev, n, prior_m, prior_s, bin, arr);
 #pragma unroll
   for (int k = 0; k < KPT; ++k) {
     const int j = tid + k * THREADS;
     if (j < n) {
-      t.mem[t.x.b.start[bin[k]] + arr[k]] = static_cast<int16_t>(j);
+      t.mem[t.x_b.start[bin[k]] + arr[k]] = static_cast<int16_t>(j);
       t.ord[j] = static_cast<int16_t>(j);   // every position holds a valid index
     }
   }
@@ -1070,7 +1066,7 @@ __device__ void order_level(RankTile<T, CAP, THREADS>& t, const T* key, int n, i
   for (int k = 0; k < KPT; ++k) {
     const int j = tid + k * THREADS;
     if (j < n) {
-      const int p = bucket_position(t, key, j, t.x.b.start[bin[k]], t.x.b.start[bin[k] + 1]);
+      const int p = bucket_position(t, key, j, t.x_b.start[bin[k]], t.x_b.start[bin[k] + 1]);
       t.pos[j] = static_cast<int16_t>(p);
       t.ord[p] = static_cast<int16_t>(j);
     }
@@ -1081,8 +1077,8 @@ __device__ void order_level(RankTile<T, CAP, THREADS>& t, const T* key, int n, i
 // Sect. 3.3, Eqs. 35-36 in the final order.  Sums 0..4: d = x - x_0 of u, v, w, omega, psi;
 // 5..11: uu, vv, ww, uv, uw, vw, psi psi (products of d; x_0 the first particle of the
 // order).  Warp w < 4 takes three of the twelve sums over all particles, lane l the
-// positions l, l + 32, ... (compensated FP32 per lane, or FP64); lane c < 3 then adds the
-// 32 lanes' value/error pairs of its sum in lane order.  Called by every thread.
+// positions l, l + 32, ... (compensated FP32 per lane, or FP64); the lanes then combine by
+// a shuffle tree in a fixed order (value/error pairs in FP32).  Called by every thread.
 template <typename A, typename T, int CAP, int THREADS>
 __device__ __forceinline__ void rank_moments(RankTile<T, CAP, THREADS>& t, int n) {
   static_assert(THREADS >= 128, "four warps take the moment sums");
@@ -1117,44 +1113,16 @@ __device__ __forceinline__ void rank_moments(RankTile<T, CAP, THREADS>& t, int n
     const int c0 = warp < 3 ? warp : 3;
     const int c1 = warp < 3 ? 5 + warp : 4;
     const int c2 = warp == 0 ? 8 : warp == 1 ? 10 : warp == 2 ? 9 : 11;
-    if constexpr (sizeof(A) == 4) {
-      t.x.combf[32 * c0 + lane] = make_float2(m0.s, -Acc<A>::err(m0));
-      t.x.combf[32 * c1 + lane] = make_float2(m1.s, -Acc<A>::err(m1));
-      t.x.combf[32 * c2 + lane] = make_float2(m2.s, -Acc<A>::err(m2));
-    } else {
-      t.x.combd[32 * c0 + lane] = m0.s;
-      t.x.combd[32 * c1 + lane] = m1.s;
-      t.x.combd[32 * c2 + lane] = m2.s;
-    }
+    A h0, l0, h1, l1, h2, l2;
+    m0.warp_pair(h0, l0);
+    m1.warp_pair(h1, l1);
+    m2.warp_pair(h2, l2);
     if (lane == 0) {
+      t.mh[c0] = h0; t.ml[c0] = l0;
+      t.mh[c1] = h1; t.ml[c1] = l1;
+      t.mh[c2] = h2; t.ml[c2] = l2;
       if (warp < 3) t.msh[warp] = static_cast<double>(sa);
       else { t.msh[3] = static_cast<double>(sa); t.msh[4] = static_cast<double>(sb); }
-    }
-    __syncwarp();
-    if (lane < 3) {
-      const int c = lane == 0 ? c0 : lane == 1 ? c1 : c2;
-      if constexpr (sizeof(A) == 4) {
-        // the 32 lanes' (value, error) pairs in lane order: exact two-sums of the values,
-        // the errors added
-        float h = 0.0f, l = 0.0f;
-#pragma unroll 4
-        for (int i = 0; i < 32; ++i) {
-          const float2 pv = t.x.combf[32 * c + i];
-          const float sh = h + pv.x;
-          const float bb = sh - h;
-          const float se = (h - (sh - bb)) + (pv.x - bb);
-          l += se + pv.y;
-          h = sh;
-        }
-        t.mh[c] = h;
-        t.ml[c] = l;
-      } else {
-        double h = 0.0;
-#pragma unroll 4
-        for (int i = 0; i < 32; ++i) h += t.x.combd[32 * c + i];
-        t.mh[c] = h;
-        t.ml[c] = 0.0;
-      }
     }
   }
   __syncthreads();
