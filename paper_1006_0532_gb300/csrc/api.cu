@@ -581,6 +581,8 @@ int upload_grid(Ctx& c, const HostGeo& g, const std::vector<ElemTopo>& topo,
   return PDFX_OK;
 }
 
+void drop_pcg_graphs(Ctx& c);
+
 int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tri, const int8_t* tag) {
   if (nn <= 0 || ne <= 0 || !xy || !tri || !tag) return PDFX_ERR_ARG;
   if (c.K > 1 && c.h_ielem.back() != ne) return PDFX_ERR_ARG;
@@ -818,6 +820,7 @@ int set_grid(Ctx& c, int32_t nn, const double* xy, int32_t ne, const int32_t* tr
   c.h_vy = g.vy;
   c.h_area2 = g.area2;
   c.fem_ready = false;   // the Eulerian calls rebuild their FEM data for this grid
+  drop_pcg_graphs(c);
   c.corr_pending = false;
   c.have_grid = true;
   c.have_fields = false;
@@ -1024,7 +1027,7 @@ int upload_vec(Ctx& c, P*& dst, const std::vector<P>& src) {
 
 // Work arrays of the Eulerian calls, carved from c.ew.
 struct EWork {
-  double *x, *b, *r, *z, *d, *q;   // [9][nn] solver vectors
+  double *x, *b, *r, *z, *d, *q, *d2;   // [9][nn] solver vectors (d2: second direction)
   double *rhs;                     // [9][nn] right-hand side of Eq. 12
   double *L;                       // [nn] length scale of Eq. 16
   double *aval, *adiag;            // [nnz], [nn] elliptic-relaxation matrix
@@ -1032,13 +1035,14 @@ struct EWork {
   double *pcg;                     // PCG partial sums and scalars
   double *prs;                     // derivative passes of the pressure source
   double *big;                     // 18 (ne + nn): derived fields, element gradients
-  double *red;                     // 72: reductions
+  double *red;                     // kRedBlocks + 8: reductions
+  unsigned *ticket;                // [9] last-block counters (zeroed once)
 };
 
 size_t ework_doubles(const Ctx& c) {
   const size_t N = static_cast<size_t>(c.nn), E = static_cast<size_t>(c.ne);
-  return 7 * 9 * N + N + static_cast<size_t>(c.fem.nnz) + N + 2 * N + pcg_scratch_doubles(c.nn, 9) +
-         pressure_rhs_scratch_doubles(c.nn, c.ne) + 18 * (E + N) + 72;
+  return 8 * 9 * N + N + static_cast<size_t>(c.fem.nnz) + N + 2 * N + pcg_scratch_doubles(c.nn, 9) +
+         pressure_rhs_scratch_doubles(c.nn, c.ne) + 18 * (E + N) + (kRedBlocks + 8) + 8;
 }
 
 EWork ework(Ctx& c) {
@@ -1051,6 +1055,7 @@ EWork ework(Ctx& c) {
   w.z = p; p += N9;
   w.d = p; p += N9;
   w.q = p; p += N9;
+  w.d2 = p; p += N9;
   w.rhs = p; p += N9;
   w.L = p; p += N;
   w.aval = p; p += static_cast<size_t>(c.fem.nnz);
@@ -1060,7 +1065,8 @@ EWork ework(Ctx& c) {
   w.pcg = p; p += pcg_scratch_doubles(c.nn, 9);
   w.prs = p; p += pressure_rhs_scratch_doubles(c.nn, c.ne);
   w.big = p; p += 18 * (E + N);
-  w.red = p;
+  w.red = p; p += kRedBlocks + 8;
+  w.ticket = reinterpret_cast<unsigned*>(p);
   return w;
 }
 
@@ -1094,6 +1100,7 @@ int ensure_fem(Ctx& c) {
   PDFX_TRY(upload_vec(c, m.bnb, h.bnb));
   PDFX_TRY(upload_vec(c, m.blen, h.blen));
   PDFX_TRY(alloc_into(c, c.ew, ework_doubles(c)));
+  PDFX_CUDA(cudaMemset(ework(c).ticket, 0, 8 * sizeof(double)));
   PDFX_TRY(alloc_into(c, c.efixed, 9 * nn));
   PDFX_TRY(alloc_into(c, c.eflag, 1));
   PDFX_TRY(alloc_into(c, c.P, nn));
@@ -1113,13 +1120,60 @@ WpConst wp_const(const Ctx& c) {
   return k;
 }
 
-// Iterates until every component meets its stopping rule (checked on the host every 16
-// iterations; a component that has converged stops changing), or fails after max_iter.
+// 16 conjugate-gradient iterations (two kernels each) as a CUDA graph for this solve
+// configuration, captured on the library's stream the first time and kept until the grid
+// changes (the arrays are the grid's work arrays).
+constexpr int kPcgChunk = 16;
+int pcg_graph(Ctx& c, const PcgArgs& a, cudaGraphExec_t* out) {
+  const void* key[4] = {a.val, a.x, a.b, a.fixed};
+  Ctx::PcgGraph* free_slot = nullptr;
+  for (Ctx::PcgGraph& g : c.pcg_graphs) {
+    if (g.exec && g.C == a.C && g.tol == a.tol && std::equal(key, key + 4, g.key)) {
+      *out = g.exec;
+      return PDFX_OK;
+    }
+    if (!g.exec && !free_slot) free_slot = &g;
+  }
+  if (!free_slot) {                      // all in use: replace the first
+    free_slot = &c.pcg_graphs[0];
+    cudaGraphExecDestroy(free_slot->exec);
+    free_slot->exec = nullptr;
+  }
+  if (!c.gstream && cudaStreamCreateWithFlags(&c.gstream, cudaStreamNonBlocking) != cudaSuccess)
+    return PDFX_ERR_CUDA;
+  PDFX_CUDA(cudaStreamBeginCapture(c.gstream, cudaStreamCaptureModeThreadLocal));
+  for (int j = 0; j < kPcgChunk / 2; ++j) launch_pcg_two_iterations(c.fem, a, c.gstream);
+  cudaGraph_t g = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(c.gstream, &g);
+  if (ec != cudaSuccess || !g) {
+    if (g) cudaGraphDestroy(g);
+    return PDFX_ERR_CUDA;
+  }
+  const cudaError_t ei = cudaGraphInstantiate(&free_slot->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (ei != cudaSuccess) { free_slot->exec = nullptr; return PDFX_ERR_CUDA; }
+  free_slot->C = a.C;
+  free_slot->tol = a.tol;
+  std::copy(key, key + 4, free_slot->key);
+  *out = free_slot->exec;
+  return PDFX_OK;
+}
+void drop_pcg_graphs(Ctx& c) {
+  for (Ctx::PcgGraph& g : c.pcg_graphs) {
+    if (g.exec) cudaGraphExecDestroy(g.exec);
+    g = Ctx::PcgGraph{};
+  }
+}
+
+// Iterates until every component meets its stopping rule, in chunks of 16 iterations
+// replayed from a graph and checked on the host after each chunk (a component that has
+// converged stops changing); more than max_iter iterations of a component is an error.
 int run_pcg(Ctx& c, const PcgArgs& a, int32_t max_iter, int32_t* iters, cudaStream_t s) {
   launch_pcg_setup(c.fem, a, s);
   c.launches += 8;
   const double* sc = pcg_scalars(a, c.nn);
   std::vector<double> h(static_cast<size_t>(a.C) * kPcgScalars);
+  cudaGraphExec_t chunk = nullptr;
   int32_t done = 0;
   for (;;) {
     PDFX_CUDA(cudaMemcpyAsync(h.data(), sc, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, s));
@@ -1128,14 +1182,15 @@ int run_pcg(Ctx& c, const PcgArgs& a, int32_t max_iter, int32_t* iters, cudaStre
     for (int j = 0; j < a.C; ++j) any |= h[static_cast<size_t>(j) * kPcgScalars + kPcgActive] != 0.0;
     if (!any) break;
     if (done >= max_iter) return PDFX_ERR_SOLVE;
-    const int32_t chunk = std::min<int32_t>(16, max_iter - done);
-    for (int32_t j = 0; j < chunk; ++j) launch_pcg_iteration(c.fem, a, s);
-    c.launches += 6 * static_cast<int64_t>(chunk);
-    done += chunk;
+    if (!chunk) PDFX_TRY(pcg_graph(c, a, &chunk));
+    PDFX_CUDA(cudaGraphLaunch(chunk, s));
+    c.launches += 2 * kPcgChunk;
+    done += kPcgChunk;
   }
   int32_t most = 0;
   for (int j = 0; j < a.C; ++j)
     most = std::max(most, static_cast<int32_t>(h[static_cast<size_t>(j) * kPcgScalars + kPcgIters]));
+  if (most > max_iter) return PDFX_ERR_SOLVE;
   if (iters) *iters = most;
   return PDFX_OK;
 }
@@ -1159,7 +1214,8 @@ int wp_solve_dev(Ctx& c, const EWork& w, double tol, int32_t max_iter, int32_t* 
   PDFX_TRY(read_flag(c, s));
   PcgArgs a;
   a.C = 9; a.val = w.aval; a.diag = w.adiag; a.fixed = c.efixed; a.b = w.b;
-  a.x = w.x; a.r = w.r; a.z = w.z; a.d = w.d; a.q = w.q; a.scratch = w.pcg; a.tol = tol;
+  a.x = w.x; a.r = w.r; a.z = w.z; a.d = w.d; a.q = w.q; a.d2 = w.d2; a.ticket = w.ticket;
+  a.scratch = w.pcg; a.tol = tol;
   return run_pcg(c, a, max_iter, iters, s);
 }
 
@@ -1191,7 +1247,8 @@ int pressure_dev(Ctx& c, const EWork& w, double* x, double tol, int32_t max_iter
   c.launches += 4;
   PcgArgs a;
   a.C = 1; a.val = c.fem.kval; a.diag = c.fem.kdiag; a.fixed = nullptr; a.b = w.b;
-  a.x = x; a.r = w.r; a.z = w.z; a.d = w.d; a.q = w.q; a.scratch = w.pcg; a.tol = tol;
+  a.x = x; a.r = w.r; a.z = w.z; a.d = w.d; a.q = w.q; a.d2 = w.d2; a.ticket = w.ticket;
+  a.scratch = w.pcg; a.tol = tol;
   PDFX_TRY(run_pcg(c, a, max_iter, iters, s));
   launch_zero_mean(c.fem, x, w.red, s);
   c.launches += 3;
@@ -1342,6 +1399,8 @@ void pdfx_destroy(void* ctx) {
   if (!c) return;
   cudaDeviceSynchronize();
   if (c->gexec) cudaGraphExecDestroy(c->gexec);
+  for (Ctx::PcgGraph& g : c->pcg_graphs)
+    if (g.exec) cudaGraphExecDestroy(g.exec);
   if (c->gstream) cudaStreamDestroy(c->gstream);
   for (auto& o : c->owned) {
     if (c->has_alloc) c->alloc.release(o.first, o.second, c->alloc.user);

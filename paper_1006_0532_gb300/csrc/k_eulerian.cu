@@ -145,6 +145,110 @@ __global__ void pcg_direction_kernel(int nn, int C, const uint8_t* __restrict__ 
   eops::pcg_direction(!fixed || !fixed[i], sc + c * kSc, z[i], d + i);
 }
 
+// ---------------------------------------------------------------------------------------
+// Two kernels per conjugate-gradient iteration.  Each ends with a block sum per block and,
+// in the last block of a component to finish (an atomic ticket after a memory fence), the
+// component's scalars from the blocks' partial sums in block order: the sums and scalars
+// of the three-kernel passes above, bit for bit.
+//   direction_spmv: d1 = the new direction (z + beta d0 on free nodes of a component still
+//     iterating; d0 otherwise), q = A d1 masked to the free nodes, sums d1 q; then alpha.
+//     A row needs the new direction at its neighbours: it forms z + beta d0 there itself, so
+//     the old direction d0 stays untouched and d1 is a second buffer.
+//   update: x += alpha d1, r -= alpha q, z = r / diag, sums r z and z z; then beta, the
+//     stopping test, the iteration count.
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ double new_direction(bool fr, const double* sc, double z, double d0) {
+  double d = d0;
+  eops::pcg_direction(fr, sc, z, &d);
+  return d;
+}
+
+// The last block of component c (grid.x blocks) to arrive returns true, after a fence that
+// makes the other blocks' partial sums visible; it resets the ticket for the next use.
+__device__ __forceinline__ bool last_block(unsigned* ticket, int c) {
+  __shared__ bool last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned k = atomicAdd(ticket + c, 1u);
+    last = k == gridDim.x - 1;
+    if (last) ticket[c] = 0u;
+  }
+  __syncthreads();
+  if (last) __threadfence();
+  return last;
+}
+
+// Sums the component's partials part[(c nblk + j) 2 + m] over j in the order of the scalar
+// kernel and applies scalar step `step` (called by a whole block).
+__device__ __forceinline__ void finish_scalars(int step, int c, int nblk, const double* part, double tol,
+                                               double* sc, double* sh) {
+  double a0 = 0.0, a1 = 0.0;
+  for (int j = threadIdx.x; j < nblk; j += kEB) {   // other blocks' sums: read past the L1
+    a0 += __ldcg(part + (static_cast<size_t>(c) * nblk + j) * 2);
+    a1 += __ldcg(part + (static_cast<size_t>(c) * nblk + j) * 2 + 1);
+  }
+  const double t0 = block_sum(a0, sh);
+  const double t1 = block_sum(a1, sh);
+  if (threadIdx.x == 0) eops::pcg_scalars(step, t0, t1, tol, sc + c * kSc);
+}
+
+__global__ void pcg_direction_spmv_kernel(int nn, const int32_t* __restrict__ row, const int32_t* __restrict__ col,
+                                          const double* __restrict__ val, const uint8_t* __restrict__ fixed,
+                                          const double* __restrict__ z, const double* __restrict__ d0,
+                                          double* __restrict__ d1, double* __restrict__ q, double tol,
+                                          double* __restrict__ sc, double* __restrict__ part,
+                                          unsigned* __restrict__ ticket) {
+  __shared__ double sh[kEB];
+  const int c = blockIdx.y, nblk = gridDim.x;
+  const size_t base = static_cast<size_t>(c) * nn;
+  const double* scc = sc + c * kSc;
+  double s0 = 0.0;
+  for (int n = blockIdx.x * kEB + threadIdx.x; n < nn; n += nblk * kEB) {
+    double acc = 0.0;
+    for (int k = row[n]; k < row[n + 1]; ++k) {
+      const size_t oj = base + col[k];
+      acc += val[k] * new_direction(!fixed || !fixed[oj], scc, z[oj], d0[oj]);
+    }
+    const size_t o = base + n;
+    const bool fr = !fixed || !fixed[o];
+    const double dn = new_direction(fr, scc, z[o], d0[o]);
+    double qn = acc, dummy = 0.0;
+    d1[o] = dn;
+    eops::pcg_node(2, fr, 1.0, 0.0, nullptr, nullptr, nullptr, nullptr, &d1[o], &qn, &s0, &dummy);
+    q[o] = qn;
+  }
+  const double t0 = block_sum(s0, sh);
+  if (threadIdx.x == 0) {
+    part[(static_cast<size_t>(c) * nblk + blockIdx.x) * 2] = t0;
+    part[(static_cast<size_t>(c) * nblk + blockIdx.x) * 2 + 1] = 0.0;
+  }
+  if (last_block(ticket, c)) finish_scalars(2, c, nblk, part, tol, sc, sh);
+}
+
+__global__ void pcg_update_kernel(int nn, const uint8_t* __restrict__ fixed, const double* __restrict__ diag,
+                                  double* __restrict__ x, double* __restrict__ r, double* __restrict__ z,
+                                  double* __restrict__ d1, double* __restrict__ q, double tol,
+                                  double* __restrict__ sc, double* __restrict__ part, unsigned* __restrict__ ticket) {
+  __shared__ double sh[kEB];
+  const int c = blockIdx.y, nblk = gridDim.x;
+  const size_t base = static_cast<size_t>(c) * nn;
+  const double alpha = sc[c * kSc + S_ALPHA];
+  double s0 = 0.0, s1 = 0.0;
+  for (int n = blockIdx.x * kEB + threadIdx.x; n < nn; n += nblk * kEB) {
+    const size_t o = base + n;
+    const bool fr = !fixed || !fixed[o];
+    eops::pcg_node(3, fr, diag[n], alpha, nullptr, x + o, r + o, z + o, d1 + o, q + o, &s0, &s1);
+  }
+  const double t0 = block_sum(s0, sh);
+  const double t1 = block_sum(s1, sh);
+  if (threadIdx.x == 0) {
+    part[(static_cast<size_t>(c) * nblk + blockIdx.x) * 2] = t0;
+    part[(static_cast<size_t>(c) * nblk + blockIdx.x) * 2 + 1] = t1;
+  }
+  if (last_block(ticket, c)) finish_scalars(3, c, nblk, part, tol, sc, sh);
+}
+
 // xD = fixed ? x : 0 (the Dirichlet columns of the reduced load).
 __global__ void dirichlet_part_kernel(int64_t n, const uint8_t* __restrict__ fixed, const double* __restrict__ x,
                                       double* __restrict__ xd) {
@@ -287,9 +391,11 @@ __global__ void add_kernel(int nn, const double* __restrict__ a, double* __restr
 
 }  // namespace
 
+// Blocks of the reduction passes: one node per thread up to kRedBlocks blocks (the passes
+// are latency-bound at these sizes, so every SM should take part).
 int pcg_blocks(int nn) {
   const int nb = static_cast<int>(blocks_for(nn));
-  return nb < 64 ? nb : 64;
+  return nb < kRedBlocks ? nb : kRedBlocks;
 }
 
 size_t pcg_scratch_doubles(int nn, int C) {
@@ -359,6 +465,23 @@ const double* pcg_scalars(const PcgArgs& a, int nn) {
   return a.scratch + 2 * static_cast<size_t>(a.C) * pcg_blocks(nn);
 }
 
+// Two iterations of every component still iterating, in two kernels each; the direction
+// alternates between a.d and a.q2 (a second direction buffer), so that after an even number
+// of iterations it is back in a.d.  a.ticket: C zeroed counters.
+void launch_pcg_two_iterations(const FemDev& m, const PcgArgs& a, cudaStream_t s) {
+  const int nn = m.nn, C = a.C, nblk = pcg_blocks(nn);
+  double* part = a.scratch;
+  double* sc = a.scratch + 2 * static_cast<size_t>(C) * nblk;
+  const dim3 grid(static_cast<unsigned>(nblk), static_cast<unsigned>(C));
+  double* dirs[2] = {a.d, a.d2};
+  for (int it = 0; it < 2; ++it) {
+    pcg_direction_spmv_kernel<<<grid, kEB, 0, s>>>(nn, m.row, m.col, a.val, a.fixed, a.z, dirs[it],
+                                                   dirs[1 - it], a.q, a.tol, sc, part, a.ticket);
+    pcg_update_kernel<<<grid, kEB, 0, s>>>(nn, a.fixed, a.diag, a.x, a.r, a.z, dirs[1 - it], a.q, a.tol,
+                                           sc, part, a.ticket);
+  }
+}
+
 // Node-transferred gradients (Sect. 3.4) of nq quantities q[nq][nn] into gn[nq][nn][2];
 // eg is scratch of 2 nq ne doubles.
 void launch_node_gradients(const FemDev& m, const int32_t* ne_off, const int32_t* ne_list, int nq,
@@ -389,23 +512,23 @@ size_t pressure_rhs_scratch_doubles(int nn, int ne) {
   return 24 * static_cast<size_t>(nn) + 12 * static_cast<size_t>(ne);
 }
 
-// The Galerkin load of Eq. 33 with its nodal mean removed; red holds 64 + 1 doubles.
+// The Galerkin load of Eq. 33 with its nodal mean removed; red holds kRedBlocks + 1 doubles.
 void launch_pressure_load(const FemDev& m, const double* src, const double* flux, double* b, double* red,
                           cudaStream_t s) {
   pressure_load_kernel<<<blocks_for(m.nn), kEB, 0, s>>>(m.nn, m.row, m.col, m.mval, src, flux, m.boff, m.bnb,
                                                         m.blen, b);
   const int nblk = pcg_blocks(m.nn);
   dot_part_kernel<<<nblk, kEB, 0, s>>>(m.nn, nullptr, b, red);
-  dot_finish_kernel<<<1, kEB, 0, s>>>(nblk, red, red + 64);
-  sub_mean_kernel<<<blocks_for(m.nn), kEB, 0, s>>>(m.nn, red + 64, static_cast<double>(m.nn), b);
+  dot_finish_kernel<<<1, kEB, 0, s>>>(nblk, red, red + kRedBlocks);
+  sub_mean_kernel<<<blocks_for(m.nn), kEB, 0, s>>>(m.nn, red + kRedBlocks, static_cast<double>(m.nn), b);
 }
 
 // Zero integral: x -= (sum_n mlump_n x_n) / (domain area).
 void launch_zero_mean(const FemDev& m, double* x, double* red, cudaStream_t s) {
   const int nblk = pcg_blocks(m.nn);
   dot_part_kernel<<<nblk, kEB, 0, s>>>(m.nn, m.mlump, x, red);
-  dot_finish_kernel<<<1, kEB, 0, s>>>(nblk, red, red + 64);
-  sub_mean_kernel<<<blocks_for(m.nn), kEB, 0, s>>>(m.nn, red + 64, m.area, x);
+  dot_finish_kernel<<<1, kEB, 0, s>>>(nblk, red, red + kRedBlocks);
+  sub_mean_kernel<<<blocks_for(m.nn), kEB, 0, s>>>(m.nn, red + kRedBlocks, m.area, x);
 }
 
 template <typename T>

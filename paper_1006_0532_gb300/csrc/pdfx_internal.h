@@ -216,10 +216,13 @@ struct PcgArgs {
   double* z = nullptr;
   double* d = nullptr;
   double* q = nullptr;
+  double* d2 = nullptr;            // [C][nn] the second direction buffer (two-kernel iterations)
+  unsigned* ticket = nullptr;      // [C] zeroed counters of the last-block reductions
   double* scratch = nullptr;       // pcg_scratch_doubles(nn, C)
   double tol = 0.0;
 };
 constexpr int kPcgScalars = eops::kPcgScalars;   // per component: rz, |b|, zz, alpha, beta, active, iterations
+constexpr int kRedBlocks = 256;                  // blocks of the solvers' reduction passes, at most
 constexpr int kPcgActive = eops::S_ACTIVE;
 constexpr int kPcgIters = eops::S_ITERS;
 
@@ -313,6 +316,15 @@ struct Ctx {
   int* eflag = nullptr;         // [1] eps <= 0 at a node
   double* P = nullptr;          // [nn] nodal mean pressure (rho = 1)
   double* corr = nullptr;       // [ne][2] Eq. 31: dt grad(dP) per element of the last coupled step
+  // conjugate-gradient iterations replayed from CUDA graphs (16 iterations each), one per
+  // solve configuration (components, arrays, tolerance)
+  struct PcgGraph {
+    cudaGraphExec_t exec = nullptr;
+    int C = 0;
+    const void* key[4] = {nullptr, nullptr, nullptr, nullptr};
+    double tol = 0.0;
+  };
+  PcgGraph pcg_graphs[4];
   bool corr_pending = false;    // corr not yet applied to the particles (the next advance does)
   double* dP = nullptr;         // [nn] last pressure increment (the next initial guess)
   // allocations to release
@@ -402,6 +414,7 @@ void launch_assemble_wp(const FemDev& m, const double* L, double* aval, double* 
 void launch_spmv(const FemDev& m, const double* val, int C, const double* x, double* y, cudaStream_t s);
 void launch_pcg_setup(const FemDev& m, const PcgArgs& a, cudaStream_t s);
 void launch_pcg_iteration(const FemDev& m, const PcgArgs& a, cudaStream_t s);
+void launch_pcg_two_iterations(const FemDev& m, const PcgArgs& a, cudaStream_t s);
 void launch_node_gradients(const FemDev& m, const int32_t* ne_off, const int32_t* ne_list, int nq,
                            const double* q, double* eg, double* gn, cudaStream_t s);
 size_t pressure_rhs_scratch_doubles(int nn, int ne);
