@@ -762,6 +762,7 @@ def main():
                          % (np_ * 37 / 1e9),
                    "sort_every": (r32["tuned"] or {}).get("sort_every", args.sort_every),
                    "advance_block": (r32["tuned"] or {}).get("adv_block", 256),
+                   "binning_tile_split": (r32["tuned"] or {}).get("tile_split", 256),
                    "autotuned": r32["tuned"] is not None,
                    "parallelism": "independent instance per GPU"},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -771,7 +772,8 @@ def main():
                                         "x particles)" if traffic is not None else
                                         "null: no ncu capture of these kernel sources (sha256 %s)"
                                         % src_hash[:16]),
-                     "kernel": ("rank_tile_kernel<float> (2 size-class launches per step)"
+                     "kernel": ("binning: stats_tile_kernel<float> and rank_tile_kernel<float> "
+                                 "(three size-class launches per step)"
                                 if dom == "statistics_binning" else "advance_kernel<float>"),
                      "algorithmic_bytes_per_particle": per_p, "peak_source": peak_kind,
                      "ms_per_step": dom_ms,

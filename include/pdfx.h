@@ -279,12 +279,24 @@ int  pdfx_step_many(void *ctx, double dt, int32_t nsteps, int use_graph, void *s
 
 /* Picks the launch shapes that do not change any result: the advance kernel's block size
  * (128 or 256 threads) and the re-order period sort_every (4, 8 or 16 steps; results do
- * not depend on the slots' order).  Each candidate runs one re-order cycle of dt steps from
- * a snapshot of the current state, which is restored afterwards (particles, statistics,
- * step counter and diagnostics as before the call).  Writes the choice to adv_block and
- * sort_every where not NULL.  Needs temporary device memory of one particle buffer plus
- * the statistics.  Synchronous on stream. */
+ * not depend on the slots' order), then, with those, the binning's size-class split (the
+ * largest element, 0, 128, 192 or 256 particles, taken by the chunk-sort tile; larger ones
+ * up to 512 take the bucket-rank tile; both give the same order).  Each candidate runs one
+ * re-order cycle of dt steps from a snapshot of the current state, which is restored
+ * afterwards (particles, statistics, step counter and diagnostics as before the call).
+ * Writes the block size and period to adv_block and sort_every where not NULL (all three
+ * shapes: pdfx_get_launch_shapes).  Needs temporary device memory of one particle buffer
+ * plus the statistics.  Synchronous on stream. */
 int  pdfx_autotune(void *ctx, double dt, int32_t *adv_block, int32_t *sort_every, void *stream);
+
+/* The launch shapes in use (host outputs, any may be NULL): the advance block size, the
+ * re-order period and the binning's size-class split. */
+int  pdfx_get_launch_shapes(const void *ctx, int32_t *adv_block, int32_t *sort_every, int32_t *tile_split);
+
+/* Sets the launch shapes (a negative value keeps the current one): the advance block size
+ * (128 or 256), the re-order period (0 = never) and the binning's size-class split (0 to
+ * 256 particles).  None of them changes a result.  PDFX_ERR_ARG for any other value. */
+int  pdfx_set_launch_shapes(void *ctx, int32_t adv_block, int32_t sort_every, int32_t tile_split);
 
 /* Nodal statistics [nn][13] and element statistics [ne][13] with counts [ne] of the last
  * step (or initialisation), into host or device memory.  Synchronous for host output. */

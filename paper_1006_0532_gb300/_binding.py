@@ -119,6 +119,8 @@ def lib():
                 "pdfx_kernel_launches": (i64, [vp]),
                 "pdfx_element_stats_noalloc": (C.c_int, [vp, i64] + [vp] * 11 + [vp]),
                 "pdfx_measure_fp64_rate": (C.c_int, [C.POINTER(C.c_double), vp]),
+                "pdfx_get_launch_shapes": (C.c_int, [vp, vp, vp, vp]),
+                "pdfx_set_launch_shapes": (C.c_int, [vp, i32, i32, i32]),
                 "pdfx_wp_rhs": (C.c_int, [vp, vp, vp, vp]),
                 "pdfx_wp_solve": (C.c_int, [vp, vp, vp, vp, dp, i32, C.POINTER(i32), vp]),
                 "pdfx_update_wp": (C.c_int, [vp, dp, i32, C.POINTER(i32), vp]),
@@ -405,7 +407,19 @@ class Context:
         blk, se = C.c_int32(0), C.c_int32(0)
         self._check(lib().pdfx_autotune(self.h, float(dt), C.byref(blk), C.byref(se),
                                         _stream(stream)), "pdfx_autotune")
-        return {"adv_block": int(blk.value), "sort_every": int(se.value)}
+        return self.launch_shapes()
+
+    def launch_shapes(self) -> dict:
+        """The advance block size, the re-order period and the binning's size-class split."""
+        blk, se, sp = C.c_int32(0), C.c_int32(0), C.c_int32(0)
+        self._check(lib().pdfx_get_launch_shapes(self.h, C.byref(blk), C.byref(se), C.byref(sp)),
+                    "pdfx_get_launch_shapes")
+        return {"adv_block": int(blk.value), "sort_every": int(se.value), "tile_split": int(sp.value)}
+
+    def set_launch_shapes(self, adv_block: int = -1, sort_every: int = -1, tile_split: int = -1):
+        """Sets the launch shapes that change no result (-1 keeps the current one)."""
+        self._check(lib().pdfx_set_launch_shapes(self.h, int(adv_block), int(sort_every),
+                                                 int(tile_split)), "pdfx_set_launch_shapes")
 
     def step_many(self, dt: float, nsteps: int, use_graph: bool = True, stream=None):
         self._check(lib().pdfx_step_many(self.h, float(dt), int(nsteps), int(bool(use_graph)),

@@ -274,6 +274,7 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
   }
   {
     StageTimer t(c, 1, s);
+    c.plan.tile_split = c.tile_split;
     launch_plan(c.plan, c.ne, c.K, c.prm.minnpel, allow_moves ? 1 : 0, s);
     c.launches++;
   }
@@ -952,26 +953,40 @@ int do_autotune(Ctx& c, double dt, cudaStream_t s, int32_t* best_block, int32_t*
   }
   const int blocks[] = {128, 256};
   const int periods[] = {4, 8, 16};
+  const int splits[] = {0, 128, 192, 256};
+  const int split0 = c.tile_split;
+  // one re-order cycle from the snapshot with the given shapes: milliseconds per step
+  auto time_cycle = [&](int blk, int se, int split, double* ms_step) -> int {
+    PDFX_TRY(restore());
+    c.adv_block = blk;
+    c.prm.sort_every = se;
+    c.tile_split = split;
+    PDFX_TRY(do_step<T>(c, dt, s));                    // warm-up
+    const int n = 2 * se;
+    PDFX_CUDA(cudaEventRecord(e0, s));
+    for (int k = 0; k < n; ++k) PDFX_TRY(do_step<T>(c, dt, s));
+    PDFX_CUDA(cudaEventRecord(e1, s));
+    PDFX_CUDA(cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    PDFX_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    *ms_step = ms / n;
+    return PDFX_OK;
+  };
   double best = 1e300;
-  int bb = block0, bs = se0;
+  int bb = block0, bs = se0, bsp = split0;
   int rc = PDFX_OK;
-  for (int blk : blocks) {
+  for (int blk : blocks)
     for (int se : periods) {
-      if (rc != PDFX_OK) break;
-      rc = restore();
-      if (rc != PDFX_OK) break;
-      c.adv_block = blk;
-      c.prm.sort_every = se;
-      rc = do_step<T>(c, dt, s);                    // warm-up
-      const int n = 2 * se;
-      if (rc == PDFX_OK) rc = cerr(cudaEventRecord(e0, s));
-      for (int k = 0; k < n && rc == PDFX_OK; ++k) rc = do_step<T>(c, dt, s);
-      if (rc == PDFX_OK) rc = cerr(cudaEventRecord(e1, s));
-      if (rc == PDFX_OK) rc = cerr(cudaEventSynchronize(e1));
-      float ms = 0.0f;
-      if (rc == PDFX_OK) rc = cerr(cudaEventElapsedTime(&ms, e0, e1));
-      if (rc == PDFX_OK && ms / n < best) { best = ms / n; bb = blk; bs = se; }
+      double ms = 0.0;
+      if (rc == PDFX_OK) rc = time_cycle(blk, se, split0, &ms);
+      if (rc == PDFX_OK && ms < best) { best = ms; bb = blk; bs = se; }
     }
+  // then the binning's size-class split with the chosen block size and period
+  for (int sp : splits) {
+    double ms = 0.0;
+    if (rc == PDFX_OK && sp != split0) rc = time_cycle(bb, bs, sp, &ms);
+    else continue;
+    if (rc == PDFX_OK && ms < best) { best = ms; bsp = sp; }
   }
   const int rr = restore();
   cudaEventDestroy(e0);
@@ -981,10 +996,12 @@ int do_autotune(Ctx& c, double dt, cudaStream_t s, int32_t* best_block, int32_t*
   if (rc != PDFX_OK || rr != PDFX_OK) {
     c.adv_block = block0;
     c.prm.sort_every = se0;
+    c.tile_split = split0;
     return rc != PDFX_OK ? rc : rr;
   }
   c.adv_block = bb;
   c.prm.sort_every = bs;
+  c.tile_split = bsp;
   drop_graph(c);
   if (best_block) *best_block = bb;
   if (best_se) *best_se = bs;
@@ -1593,6 +1610,27 @@ int pdfx_autotune(void* ctx, double dt, int32_t* adv_block, int32_t* sort_every,
   if (!c->pbuf[0] || !c->have_fields || c->np <= 0) return PDFX_ERR_ORDER;
   return c->prm.precision == 1 ? do_autotune<float>(*c, dt, as_stream(stream), adv_block, sort_every)
                                : do_autotune<double>(*c, dt, as_stream(stream), adv_block, sort_every);
+}
+
+int pdfx_get_launch_shapes(const void* ctx, int32_t* adv_block, int32_t* sort_every, int32_t* tile_split) {
+  const Ctx* c = static_cast<const Ctx*>(ctx);
+  if (!c) return PDFX_ERR_ARG;
+  if (adv_block) *adv_block = c->adv_block;
+  if (sort_every) *sort_every = c->prm.sort_every;
+  if (tile_split) *tile_split = c->tile_split;
+  return PDFX_OK;
+}
+
+int pdfx_set_launch_shapes(void* ctx, int32_t adv_block, int32_t sort_every, int32_t tile_split) {
+  Ctx* c = as_ctx(ctx);
+  if (!c) return PDFX_ERR_ARG;
+  if (adv_block >= 0 && adv_block != 128 && adv_block != 256) return PDFX_ERR_ARG;
+  if (tile_split > kTileSplit) return PDFX_ERR_ARG;
+  if (adv_block >= 0) c->adv_block = adv_block;
+  if (sort_every >= 0) c->prm.sort_every = sort_every;
+  if (tile_split >= 0) c->tile_split = tile_split;
+  drop_graph(*c);
+  return PDFX_OK;
 }
 
 int pdfx_step(void* ctx, double dt, void* stream) {

@@ -177,16 +177,22 @@ struct Acc<float> {
   }
   __device__ __forceinline__ float value() const { return s - c; }
   __device__ __forceinline__ static float err(const Acc& a) { return a.c; }
-  // value/error pairs: an exact two-sum of the leading parts, errors added, renormalised
+  // value/error pairs: an exact two-sum of the leading parts, errors added, renormalised.
+  // Both lanes of a pair take the lower lane's pair as the first operand, so every lane ends
+  // with the same bits.
   __device__ __forceinline__ void warp_pair(float& hv, float& lv) const {
     float h = s, l = -c;
+    const int lane = threadIdx.x & 31;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       const float oh = __shfl_xor_sync(kFull, h, o), ol = __shfl_xor_sync(kFull, l, o);
-      const float sh = h + oh;
-      const float bb = sh - h;
-      const float se = (h - (sh - bb)) + (oh - bb);
-      const float lo = se + (l + ol);
+      const bool first = (lane & o) == 0;
+      const float ah = first ? h : oh, bh = first ? oh : h;
+      const float al = first ? l : ol, bl = first ? ol : l;
+      const float sh = ah + bh;
+      const float bb = sh - ah;
+      const float se = (ah - (sh - bb)) + (bh - bb);
+      const float lo = se + (al + bl);
       h = sh + lo;
       l = lo - (h - sh);
     }
@@ -458,7 +464,8 @@ struct ProjVal {
 };
 
 // Sect. 3.3, Eqs. 35-36, by warp 0 in the order cur: sums of d = x - x_0 and of products of
-// d in precision A, x_0 the first particle of the order; mean = x_0 + S1/N, central =
+// d in precision A (each product rounded on its own, never fused into the sum, so that every
+// tile kernel forms the same sums bit for bit), x_0 the first particle of the order; mean = x_0 + S1/N, central =
 // S2/N - (S1/N)^2; lanes combine as value/error pairs (FP32) or in FP64, then the 13
 // outputs are formed in FP64, one per lane.  Inlined: as an out-of-line call it measured
 // slower (its spills and the call outweigh the spills it saves in the sorting loops).
@@ -484,10 +491,10 @@ __device__ __forceinline__ void element_moments(const T* __restrict__ pu, const 
     const A du = A(pu[q]) - sh[0], dv = A(pv[q]) - sh[1], dw = A(pw[q]) - sh[2];
     const A dom = A(pom[q]) - sh[3], dp = A(ppsi[q]) - sh[4];
     m[0].add(du); m[1].add(dv); m[2].add(dw); m[3].add(dom); m[4].add(dp);
-    m[5].add(du * du); m[6].add(dv * dv); m[7].add(dw * dw);
-    m[8].add(du * dv); m[9].add(du * dw); m[10].add(dv * dw);
-    m[11].add(dp * dp);
-    if constexpr (FOX) { mx[0].add(du * dp); mx[1].add(dv * dp); mx[2].add(dw * dp); }
+    m[5].add(xmul(du, du)); m[6].add(xmul(dv, dv)); m[7].add(xmul(dw, dw));
+    m[8].add(xmul(du, dv)); m[9].add(xmul(du, dw)); m[10].add(xmul(dv, dw));
+    m[11].add(xmul(dp, dp));
+    if constexpr (FOX) { mx[0].add(xmul(du, dp)); mx[1].add(xmul(dv, dp)); mx[2].add(xmul(dw, dp)); }
   }
 #pragma unroll
   for (int c = 0; c < 12; ++c) {
@@ -1077,7 +1084,8 @@ __device__ void order_level(RankTile<T, CAP, THREADS>& t, const T* key, int n, i
 // Sect. 3.3, Eqs. 35-36 in the final order.  Sums 0..4: d = x - x_0 of u, v, w, omega, psi;
 // 5..11: uu, vv, ww, uv, uw, vw, psi psi (products of d; x_0 the first particle of the
 // order).  Warp w < 4 takes three of the twelve sums over all particles, lane l the
-// positions l, l + 32, ... (compensated FP32 per lane, or FP64); the lanes then combine by
+// positions l, l + 32, ... (compensated FP32 per lane, or FP64; products rounded on their
+// own as in element_moments, whose sums these equal bit for bit); the lanes then combine by
 // a shuffle tree in a fixed order (value/error pairs in FP32).  Called by every thread.
 template <typename A, typename T, int CAP, int THREADS>
 __device__ __forceinline__ void rank_moments(RankTile<T, CAP, THREADS>& t, int n) {
@@ -1101,12 +1109,12 @@ __device__ __forceinline__ void rank_moments(RankTile<T, CAP, THREADS>& t, int n
       const A da = A(xa[q]) - sa, db = A(xb[q]) - sb;
       if (warp < 3) {
         m0.add(da);
-        m1.add(da * da);
-        m2.add(da * db);
+        m1.add(xmul(da, da));
+        m2.add(xmul(da, db));
       } else {
         m0.add(da);
         m1.add(db);
-        m2.add(db * db);
+        m2.add(xmul(db, db));
       }
     }
     // sum index of each accumulator

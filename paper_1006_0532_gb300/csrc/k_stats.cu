@@ -88,14 +88,14 @@ __device__ int64_t S_of(const int64_t* P0, const int64_t* P1, int64_t H, int64_t
 // ride in bits 28-39, 40-51 and 52-63 of a count's block scan (counts sum below 2^28 and a
 // block holds kPlanThreads elements, so the fields never carry into each other).
 constexpr int64_t kCountMask = (int64_t(1) << 28) - 1;
-__device__ __forceinline__ int64_t tile_class_bits(bool valid, int32_t c) {
+__device__ __forceinline__ int64_t tile_class_bits(bool valid, int32_t c, int split) {
   if (!valid || c > kSmallCap) return 0;
-  return c <= kTileSplit ? (int64_t(1) << 28) : (c <= kTileMid ? (int64_t(1) << 52) : (int64_t(1) << 40));
+  return c <= split ? (int64_t(1) << 28) : (c <= kTileMid ? (int64_t(1) << 52) : (int64_t(1) << 40));
 }
 __device__ __forceinline__ void place_tile_class(Plan& pl, bool valid, int32_t c, int32_t e,
                                                  int32_t eb, int32_t ee, int64_t ex, int64_t tot,
                                                  int32_t& tA, int32_t& tB, int32_t& tM) {
-  const int64_t bits = tile_class_bits(valid, c);
+  const int64_t bits = tile_class_bits(valid, c, pl.tile_split);
   if (bits == (int64_t(1) << 28)) pl.tiles[eb + tA + static_cast<int32_t>((ex >> 28) & 0xfff)] = e;
   else if (bits == (int64_t(1) << 40)) pl.tiles[ee - 1 - (tB + static_cast<int32_t>((ex >> 40) & 0xfff))] = e;
   else if (bits != 0) pl.tiles_mid[eb + tM + static_cast<int32_t>((ex >> 52) & 0xfff)] = e;
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne_
     const int32_t e = eb + base + tid;
     const int32_t c = valid ? pl.cnt[e] : 0;
     int64_t ptot;
-    const int64_t pex = block_exclusive_scan<int64_t>(c | tile_class_bits(valid, c), sh.tmp64, ptot);
+    const int64_t pex = block_exclusive_scan<int64_t>(c | tile_class_bits(valid, c, pl.tile_split), sh.tmp64, ptot);
     const int32_t ex = static_cast<int32_t>(pex & kCountMask), tot = static_cast<int32_t>(ptot & kCountMask);
     place_tile_class(pl, valid, c, e, eb, ee, pex, ptot, tA, tB, tM);
     if (valid) {
@@ -249,7 +249,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne_
     const int32_t dof = cD + block_exclusive_scan<int32_t>(l, sh.tmp32, tot);
     cD += tot;
     int64_t ptot;
-    const int64_t pex = block_exclusive_scan<int64_t>((valid ? f : 0) | tile_class_bits(valid, f),
+    const int64_t pex = block_exclusive_scan<int64_t>((valid ? f : 0) | tile_class_bits(valid, f, pl.tile_split),
                                                       sh.tmp64, ptot);
     const int32_t fo = cF + static_cast<int32_t>(pex & kCountMask);
     cF += static_cast<int32_t>(ptot & kCountMask);

@@ -81,6 +81,7 @@ int element_stats_noalloc(Ctx& c, int64_t np, const double* u, const double* v, 
   pl.tiles_mid = per_e + 6 * kNaE;
   pl.scal = per_e + 7 * kNaE;
   pl.idx = idx;
+  pl.tile_split = c.tile_split;
   // without particle moves the plan touches only the arrays above; the rest alias the final
   // offsets so that no pointer leaves the scratch
   pl.fin = pl.gain = pl.goff = pl.loss = pl.doff = pl.recips = pl.donors = pl.foff;

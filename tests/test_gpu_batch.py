@@ -166,8 +166,8 @@ def test_batch_graph_equals_instances_run_alone():
 
 @pytest.mark.parametrize("precision", [0, 1])
 def test_autotune_changes_no_result(precision):
-    """The tuned launch shapes (advance block size, re-order period) leave every result as
-    it was, and tuning leaves the state where it found it."""
+    """The tuned launch shapes (advance block size, re-order period, binning split) leave
+    every result as it was, and tuning leaves the state where it found it."""
     it = _instances()[2]
     a = _single(it, precision, 8)
     b = _single(it, precision, 8)
@@ -177,6 +177,8 @@ def test_autotune_changes_no_result(precision):
     x_before = b.get_particles()["x"]
     tuned = b.autotune(dt)
     assert tuned["adv_block"] in (128, 256) and tuned["sort_every"] in (4, 8, 16)
+    assert tuned["tile_split"] in (0, 128, 192, 256)
+    assert b.launch_shapes() == tuned
     assert b.step_index == a.step_index
     assert np.array_equal(b.get_particles()["x"], x_before)
     assert b.diag()["steps"] == a.diag()["steps"]
@@ -209,3 +211,4 @@ def test_batch_step_of_separate_contexts_equals_single_steps():
         assert ca.check() == 0
     with pytest.raises(B.PdfxError):
         B.batch_step([a[0], a[1], a[0]], dt)
+

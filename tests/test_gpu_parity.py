@@ -226,6 +226,49 @@ def test_large_element_path_and_empty_elements():
     compare_stats(vg, vo, 1e-10, stats_layout=False)
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_binning_split_changes_no_result(precision):
+    """Every size-class split of the binning (chunk-sort tile for elements up to the split,
+    bucket-rank tiles above it, up to 512 and up to 1024, the large-element kernel beyond)
+    gives the same pointers, bins and statistics bit for bit; in FP64 they are the oracle's.
+    Out-of-range shapes are refused."""
+    w = synth.workload("channel_tiny")
+    g = w["grid"]
+    rng = np.random.default_rng(17)
+    counts = rng.integers(1, 60, g.ne)
+    counts[rng.choice(g.ne, 24, replace=False)] = np.concatenate(
+        [rng.integers(100, 257, 8), rng.integers(257, 513, 8), rng.integers(513, 1025, 6),
+         [1200, 2000]])
+    st = _imbalanced_state(g, counts, 8)
+    ref = None
+    for split in (256, 0, 100, 192):
+        c = gpu_ctx(g, w["params"], w["fields"], precision=precision)
+        c.set_launch_shapes(tile_split=split)
+        assert c.launch_shapes()["tile_split"] == split
+        c.set_particles(st, 0)
+        out = (c.get_particles()["cp"], c.element_stats()[0], *c.bins(), c.nodal_stats())
+        if ref is None:
+            ref = out
+        else:
+            for a, b in zip(out, ref):
+                assert np.array_equal(a, b)
+        assert c.check() == 0
+        c.close()
+    if precision == 0:
+        o = oracle.Oracle(g, w["params"], w["fields"])
+        o.set_particles(st, 0)
+        assert np.array_equal(ref[0], o.get_particles()["cp"])
+        vo, go = o.bins()
+        assert np.array_equal(ref[3], go)
+        compare_stats(ref[2], vo, 1e-10, stats_layout=False)
+        compare_stats(ref[1], o.element_stats()[0], 1e-10)
+    c = gpu_ctx(g, w["params"], w["fields"], precision=precision)
+    for bad in (dict(tile_split=300), dict(adv_block=96)):
+        with pytest.raises(B.PdfxError):
+            c.set_launch_shapes(**bad)
+    c.close()
+
+
 def test_empty_state():
     w = synth.workload("channel_tiny")
     g = w["grid"]
