@@ -1019,29 +1019,42 @@ __device__ void group_level(RankTile<T, CAP, THREADS>& t, const T* key, int n, i
 }
 
 // A level whose groups hold at most 32 particles: a warp takes a whole group from the
-// arrangement t.ord (its position range), sorts it in registers by the exact key (value,
-// particle id) with a bitonic network, and writes the order back into the same range: the
-// exact positions (t.pos, t.ord) and, before the last level, the next level's groups.
+// arrangement t.ord (its position range), sorts it in registers with a bitonic network and
+// writes the order back into the same range: the exact positions (t.pos, t.ord) and, before
+// the last level, the next level's groups.  The sort takes the value bits alone; only a
+// group in which two sorted neighbours have equal values is sorted again by the exact key
+// (value, particle id).  Either way the order is that of (value, id).
 template <typename T, int CAP, int THREADS>
 __device__ void warp_level(RankTile<T, CAP, THREADS>& t, const T* key, int n, int Gprev, int Gl,
                            bool last) {
-  using P = KeyPolicy<T, true>;
-  using K = typename P::K;
+  using PF = KeyPolicy<T, false>;
+  using PE = KeyPolicy<T, true>;
   constexpr int W = THREADS / 32;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const float invG = 1.0f / static_cast<float>(Gprev), inv_n = 1.0f / static_cast<float>(n);
 #pragma unroll 1
   for (int c = warp; c < Gprev; c += W) {
     const int gs = group_start(c, n, Gprev, invG), len = group_start(c + 1, n, Gprev, invG) - gs;
-    K k;
-    int32_t j = -1;
-    if (lane < len) {
-      j = t.ord[gs + lane];
-      k = P::make(key[j], t.pid, j);
-    } else {
-      pad_key(k);
+    const int32_t j0 = lane < len ? t.ord[gs + lane] : -1;
+    int32_t j = j0;
+    {
+      typename PF::K k;
+      if (lane < len) k = PF::make(key[j0], t.pid, j0);
+      else pad_key(k);
+      warp_sort32(k, j, lane);
+      // a tie, or a real value equal to the padding key (a non-finite state), takes the
+      // exact pass, whose keys always sort below the padding
+      typename PF::K pad;
+      pad_key(pad);
+      const typename PF::K up = kdown(k);
+      if (__any_sync(kFull, (lane + 1 < len && keq(k, up)) || (lane < len && keq(k, pad)))) {
+        typename PE::K ke;
+        j = j0;
+        if (lane < len) ke = PE::make(key[j0], t.pid, j0);
+        else pad_key(ke);
+        warp_sort32(ke, j, lane);
+      }
     }
-    warp_sort32(k, j, lane);
     if (lane < len) {
       const int p = gs + lane;
       t.ord[p] = static_cast<int16_t>(j);
