@@ -812,6 +812,8 @@ struct RankTile {
   int16_t mem[CAP];                 // particles by bucket
   uint8_t grp[CAP];                 // particle -> group of the last level done
   int32_t wsum[THREADS / 32];
+  float prior[6];                   // per level: the key's mean and standard deviation of the
+                                    // last statistics pass (0, 0: none)
   int n_gathered;
 };
 
@@ -1269,6 +1271,24 @@ __device__ void element_rank_tile(const StatsArgs<T>& a, RankTile<T, CAP, THREAD
       Gp *= gl;
     }
   }
+  // the bucket mapping's prior, once per element (FP64 arithmetic runs at a small fraction
+  // of the FP32 rate on this GPU, so no thread but one touches it)
+  if (threadIdx.x == 0) {
+#pragma unroll 1
+    for (int l = 0; l < 3; ++l) {
+      float pm = 0.0f, ps = 0.0f;
+      if (a.prior) {
+        const double* em = a.emom + static_cast<size_t>(kNS) * e;
+        const double m = em[1 + l], var = em[4 + l];
+        if (em[0] >= 2.0 && var > 0.0 && fabs(m) < 1e30 && var < 1e60) {
+          pm = static_cast<float>(m);
+          ps = static_cast<float>(sqrt(var));
+        }
+      }
+      t.prior[2 * l] = pm;
+      t.prior[2 * l + 1] = ps;
+    }
+  }
   __syncthreads();
   // levels by (u, id), (v, id), (w, id) within the groups of the previous level; the levels
   // before the last need only the groups, the last gives the final order
@@ -1281,15 +1301,7 @@ __device__ void element_rank_tile(const StatsArgs<T>& a, RankTile<T, CAP, THREAD
     for (int l = 0; l <= last; ++l) {
       if (l > 0 && g[l] <= 1) continue;
       const T* key = l == 0 ? t.u : (l == 1 ? t.v : t.w);
-      float pm = 0.0f, ps = 0.0f;   // the key's mean and standard deviation of the last pass
-      if (a.prior) {
-        const double* em = a.emom + static_cast<size_t>(kNS) * e;
-        const double m = em[1 + l], var = em[4 + l];
-        if (em[0] >= 2.0 && var > 0.0 && fabs(m) < 1e30 && var < 1e60) {
-          pm = static_cast<float>(m);
-          ps = static_cast<float>(sqrt(var));
-        }
-      }
+      const float pm = t.prior[2 * l], ps = t.prior[2 * l + 1];
       if ((n + Gprev - 1) / Gprev <= 32) warp_level<T, CAP, THREADS>(t, key, n, Gprev, Gprev * g[l], l == last);
       else if (l == last) order_level<T, CAP, THREADS>(t, key, n, Gprev, pm, ps);
       else group_level<T, CAP, THREADS>(t, key, n, Gprev, Gprev * g[l], pm, ps);
