@@ -28,20 +28,36 @@ sys.path.insert(0, ROOT)
 METRIC = "particle-updates/sec per full PDF timestep, FP32/batched vs FP64, same GPU"
 UNIT = "particle-updates/s"
 # Algorithmic bytes per particle-update (keys: 1 FP32 form, 0 FP64 form).
-# advance (pass 1): read the position, u, v, w, omega, psi, elem, cp; write the position,
-#   u, v, w, omega, psi, elem.  The FP32 form holds each coordinate as an FP32 pair (hi +
-#   lo, 8 B): 4*9+4+1+4*9+4 = 81 B; the FP64 form 8*7+4+1+8*7+4 = 121 B.
-# binning (pass 2): read u, v, w, psi, elem; write cp: 4*4+4+1, 8*4+4+1.
-# With single FP32 positions the FP32 step would be 65 + 21 = 86 B; the pairs add 16 B.
-ADV_BYTES = {1: 81, 0: 121}
-BIN_BYTES = {1: 21, 0: 37}
-SINGLE_POSITION_STEP_BYTES = 86
+# advance (pass 1): read the position, u, v, w, omega, psi, the particle id (Philox
+#   counter), elem, cp; write the position, u, v, w, omega, psi, elem.  The FP32 form holds
+#   each coordinate as an FP32 pair (hi + lo, 8 B): 4*9+4+4+1+4*9+4 = 85 B; the FP64 form
+#   8*7+4+4+1+8*7+4 = 125 B.
+# binning (pass 2): read u, v, w, omega, psi (the moments of Eqs. 35-36), the particle id
+#   (the (value, id) order of the bins), the element; write cp: 4*5+4+4+1 = 29 B,
+#   8*5+4+4+1 = 49 B.
+# With single FP32 positions the FP32 step would be 69 + 29 = 98 B; the pairs add 16 B.
+ADV_BYTES = {1: 85, 0: 125}
+BIN_BYTES = {1: 29, 0: 49}
+SINGLE_POSITION_STEP_BYTES = 98
 # Figures from ncu captures of the kernels (DRAM bytes per particle and launch,
 # dram__bytes_read.sum + dram__bytes_write.sum; FP64 instructions per particle of the FP64
 # form's advance; the bound each capture shows), keyed by the SHA-256 of the CUDA sources
 # they were taken from: a capture describes only the kernels it measured, so after any
 # change of the sources the bench reports traffic as null until the next capture.
-NCU_RECORDS = {}
+NCU_RECORDS = {
+    # channel_50k, 25.0M particles (FP32) and 5.0M (FP64 form), one GB300
+    "28612f92c7a38c546113feeb260b4f9dbf67d22a23361d2cbbcd97b0942d4dee": {
+        "traffic": {"advance": 2102.473e6 / 25.0e6,
+                    "statistics_binning": (0.066048e6 + 738.736896e6 + 245.224704e6) / 25.0e6},
+        "limiter": {"advance": "instruction issue: 65% issue-active at 48% warps active "
+                               "(64 registers cap 4 blocks of 256), long-scoreboard stalls "
+                               "first; DRAM 21% of peak",
+                    "statistics_binning": "instruction issue and shared-memory latency: 66% "
+                                          "issue-active (<= 512 class), short-scoreboard and "
+                                          "barrier stalls first; DRAM 11% of peak"},
+        "f64_advance_fp64_inst_per_particle": (1407568787 + 454038118 + 836638858) / 5.0e6,
+    },
+}
 STAGES = ["advance", "plan", "lists", "redistribute", "statistics_binning", "node_average"]
 
 
@@ -491,8 +507,8 @@ def _patches(grid, centres, radius):
 
 def precision_study(B, w, forms, sample_steps, patch_radius=0.06):
     """Forms A/B/C against the FP64 oracle, one step at a time from identical inputs: at each
-    sampled step of a run of the form, the particles of round element patches (a wall patch
-    and an interior one) are handed to the oracle as the form holds them (FP32 values widened
+    sampled step of a run of the form, the particles of round element patches (a wall patch,
+    an interior one and one around the scalar source, where psi varies) are handed to the oracle as the form holds them (FP32 values widened
     exactly; the fields rounded to FP32 for the FP32 forms); both take one step; the nodal
     statistics of the nodes whose elements all lie well inside a patch are compared.  The
     differences are those of the form's arithmetic only; particles whose discrete decisions
@@ -502,7 +518,8 @@ def precision_study(B, w, forms, sample_steps, patch_radius=0.06):
     import oracle
     g = w["grid"]
     P = dict(w["params"], minnpel=0)             # particle-number control is global: off
-    patch, inner, nodes = _patches(g, [(0.7, 0.03), (1.3, 0.5)], patch_radius)
+    src = (w["params"]["src_x"], w["params"]["src_y"])
+    patch, inner, nodes = _patches(g, [(0.7, 0.03), (1.3, 0.5), src], patch_radius)
     out = {}
     for name, (precision, acc64) in forms.items():
         F = w["fields"] if precision == 0 else w["fields"].astype(np.float32).astype(np.float64)
@@ -839,7 +856,8 @@ def main():
         line["precision_study"] = {
             "what": "nodal statistics of one step against the FP64 oracle from identical inputs "
                     "(the form's own state at the sampled steps, handed over exactly), on the "
-                    "nodes inside a wall patch and an interior patch; relative error per "
+                    "nodes inside a wall patch, an interior patch and a patch around the "
+                    "scalar source; relative error per "
                     "statistic (floor: the column RMS; covariances also sqrt(<ii><jj>)), "
                     "max / RMS / 99th percentile over the samples",
             "unit": UNIT, "forms": ps}
