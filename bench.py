@@ -471,15 +471,15 @@ def _rel_errors(a, b, ref):
     return out
 
 
-def _patches(grid, centres, radius):
-    """Elements of a few round patches of the grid; the interior elements (those whose
-    neighbours up to two edges away lie in a patch) and the nodes all of whose elements are
-    interior."""
+def _patches(grid, centres):
+    """Elements of a few round patches of the grid, centres[k] = (x, y, radius); the interior
+    elements (those whose neighbours up to two edges away lie in a patch) and the nodes all
+    of whose elements are interior."""
     import numpy as np
     xy = grid.node_xy[grid.tri].mean(axis=1)
     L = grid.period_x
     inside = np.zeros(grid.ne, bool)
-    for cx, cy in centres:
+    for cx, cy, radius in centres:
         dx = xy[:, 0] - cx
         if L > 0:
             dx = (dx + 0.5 * L) % L - 0.5 * L
@@ -505,7 +505,7 @@ def _patches(grid, centres, radius):
     return np.where(inside)[0], np.where(inner)[0], np.where(node_ok)[0]
 
 
-def precision_study(B, w, forms, sample_steps, patch_radius=0.06):
+def precision_study(B, w, forms, sample_steps):
     """Forms A/B/C against the FP64 oracle, one step at a time from identical inputs: at each
     sampled step of a run of the form, the particles of round element patches (a wall patch,
     an interior one and one around the scalar source, where psi varies) are handed to the oracle as the form holds them (FP32 values widened
@@ -518,8 +518,10 @@ def precision_study(B, w, forms, sample_steps, patch_radius=0.06):
     import oracle
     g = w["grid"]
     P = dict(w["params"], minnpel=0)             # particle-number control is global: off
-    src = (w["params"]["src_x"], w["params"]["src_y"])
-    patch, inner, nodes = _patches(g, [(0.7, 0.03), (1.3, 0.5), src], patch_radius)
+    # radii that leave about 300, 30 and 30 nodes inside: the graded wall cells are small,
+    # the interior ones large
+    src = (w["params"]["src_x"], w["params"]["src_y"], 0.1)
+    patch, inner, nodes = _patches(g, [(0.7, 0.03, 0.06), (1.3, 0.5, 0.1), src])
     out = {}
     for name, (precision, acc64) in forms.items():
         F = w["fields"] if precision == 0 else w["fields"].astype(np.float32).astype(np.float64)

@@ -215,6 +215,18 @@ struct Acc<double> {
   }
 };
 
+// 1/n in FP64 for the element sizes of the tiles (n <= 1024), correctly rounded at compile
+// time: the same bits as a run-time FP64 division, without its long dependent sequence on
+// this GPU's narrow FP64 pipe.
+struct RecipTable {
+  double v[1025];
+  constexpr RecipTable() : v() {
+    for (int i = 1; i <= 1024; ++i) v[i] = 1.0 / i;
+  }
+};
+__constant__ RecipTable c_recip = RecipTable();
+__device__ __forceinline__ double recip_n(int n) { return n > 0 ? c_recip.v[n] : 0.0; }
+
 // floor(x / d) for 0 <= x < 2^18 + 2^8 and 1 <= d <= 1024 with inv = 1/d in FP32: the
 // quotient is at most 1025, so the two roundings of (x + 1/2) inv err by at most
 // 1025 * 2^-23 < 2^-12 < 1/(2d), the distance from (x + 1/2)/d to the nearest integer.
@@ -514,7 +526,7 @@ __device__ __forceinline__ void element_moments(const T* __restrict__ pu, const 
     t.msh[lane] = lane == 0 ? sh[0] : lane == 1 ? sh[1] : lane == 2 ? sh[2] : lane == 3 ? sh[3] : sh[4];
   __syncwarp();
   if (lane < kNS) {
-    const double inv = n > 0 ? 1.0 / n : 0.0;
+    const double inv = recip_n(n);
     const int ix = mom_nib(kMomX, lane), iy = mom_nib(kMomY, lane);
     const int iz = mom_nib(kMomZ, lane), iw = mom_nib(kMomW, lane);
     double v = ix < 15 ? t.msh[ix] : 0.0;
@@ -534,7 +546,7 @@ __device__ __forceinline__ void element_moments(const T* __restrict__ pu, const 
     __syncwarp();
     if (lane == 0) {
       // <u_a phi'> = S(d_a d_phi)/N - (S d_a/N)(S d_phi/N); then Eqs. 65-66
-      const double inv = n > 0 ? 1.0 / n : 0.0;
+      const double inv = recip_n(n);
       const double sp = (t.mh[4] + t.ml[4]) * inv;
       double uphi[3], f[3];
       for (int k = 0; k < 3; ++k)
@@ -1162,6 +1174,14 @@ __device__ void element_rank_tile(const StatsArgs<T>& a, RankTile<T, CAP, THREAD
   // entries (and the moved-out test) of a thread's first KPT rounds are loaded before any is
   // used, so that they are in flight together.
   if (threadIdx.x == 0) t.n_gathered = 0;
+  // the bucket mapping's prior: the previous pass's count, means and variances of u, v, w,
+  // loaded by one thread now and used after the gather (FP32 arithmetic from here on)
+  double pri[7];
+  if (threadIdx.x == 0 && a.prior) {
+    const double* em = a.emom + static_cast<size_t>(kNS) * e;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) pri[k] = __ldg(em + k);
+  }
   __syncthreads();
   {
     const int32_t o = a.off[e], c = a.cnt[e];
@@ -1271,18 +1291,18 @@ __device__ void element_rank_tile(const StatsArgs<T>& a, RankTile<T, CAP, THREAD
       Gp *= gl;
     }
   }
-  // the bucket mapping's prior, once per element (FP64 arithmetic runs at a small fraction
-  // of the FP32 rate on this GPU, so no thread but one touches it)
+  // the prior per level, by one thread in FP32 (FP64 arithmetic runs at a small fraction of
+  // the FP32 rate on this GPU); any monotone bucket mapping gives the same ranks
   if (threadIdx.x == 0) {
-#pragma unroll 1
+    const bool have = a.prior && static_cast<float>(pri[0]) >= 2.0f;
+#pragma unroll
     for (int l = 0; l < 3; ++l) {
       float pm = 0.0f, ps = 0.0f;
-      if (a.prior) {
-        const double* em = a.emom + static_cast<size_t>(kNS) * e;
-        const double m = em[1 + l], var = em[4 + l];
-        if (em[0] >= 2.0 && var > 0.0 && fabs(m) < 1e30 && var < 1e60) {
-          pm = static_cast<float>(m);
-          ps = static_cast<float>(sqrt(var));
+      if (have) {
+        const float m = static_cast<float>(pri[1 + l]), var = static_cast<float>(pri[4 + l]);
+        if (var > 0.0f && fabsf(m) < 1e30f && var < 1e30f) {
+          pm = m;
+          ps = sqrtf(var);
         }
       }
       t.prior[2 * l] = pm;
@@ -1314,7 +1334,7 @@ __device__ void element_rank_tile(const StatsArgs<T>& a, RankTile<T, CAP, THREAD
   else rank_moments<T>(t, n);
   if (warp == 0) {
     if (lane < kNS) {
-      const double inv = n > 0 ? 1.0 / n : 0.0;
+      const double inv = recip_n(n);
       const int ix = mom_nib(kMomX, lane), iy = mom_nib(kMomY, lane);
       const int iz = mom_nib(kMomZ, lane), iw = mom_nib(kMomW, lane);
       double v = ix < 15 ? t.msh[ix] : 0.0;
