@@ -264,8 +264,19 @@ __device__ __forceinline__ void count_update(const AdvanceArgs<T>& a, bool valid
     warp_count(bc, kDiagSource, f.src);
   }
   if (__any_sync(kFull, f.hop_bin > 0)) {
+    // the warp's hop histogram in two packed sums (8-bit fields: bins 1-4, then 5-7; a field
+    // counts at most 32 lanes)
+    const int b = f.hop_bin;
+    const unsigned lo = (b >= 1 && b <= 4) ? 1u << (8 * (b - 1)) : 0u;
+    const unsigned hi = b >= 5 ? 1u << (8 * (b - 5)) : 0u;
+    const unsigned slo = __reduce_add_sync(kFull, lo), shi = __reduce_add_sync(kFull, hi);
+    if ((threadIdx.x & 31) == 0) {
 #pragma unroll
-    for (int b = 1; b < 8; ++b) warp_count(bc, kDiagHopHist0 + b, f.hop_bin == b);
+      for (int k = 0; k < 7; ++k) {
+        const unsigned c = ((k < 4 ? slo : shi) >> (8 * (k < 4 ? k : k - 4))) & 0xffu;
+        if (c) atomicAdd(bc + kDiagHopHist0 + 1 + k, c);
+      }
+    }
   }
 }
 

@@ -140,6 +140,9 @@ def test_steps_match_oracle_f64(name, steps):
     assert dg["error"] == 0 and dg["lost"] == 0
     assert dg["wall_hits"] == do["wall_hits"]
     assert dg["hops_total"] == do["hops_total"]
+    assert dg["hop_hist"] == do["hop_hist"]            # particles per number of walk hops
+    if name == "channel_2k":
+        assert sum(dg["hop_hist"][1:]) > 0
 
 
 def _imbalanced_state(g, counts, seed):
