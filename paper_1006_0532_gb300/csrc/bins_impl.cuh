@@ -465,13 +465,20 @@ struct ArrVal {
   const T* v;
   __device__ __forceinline__ T operator()(int32_t q) const { return v[q]; }
 };
+// Eq. 64's projected velocity from the factors f_a and the means m_a, summed left to right
+// with every operation rounded on its own (no fused multiply-add): in FP64 the oracle's bits.
+template <typename T>
+__device__ __forceinline__ T fox_key(const double* f, const double* m, T u, T v, T w) {
+  const double a = __dmul_rn(f[0], __dsub_rn(static_cast<double>(u), m[0]));
+  const double b = __dmul_rn(f[1], __dsub_rn(static_cast<double>(v), m[1]));
+  const double c = __dmul_rn(f[2], __dsub_rn(static_cast<double>(w), m[2]));
+  return static_cast<T>(__dadd_rn(__dadd_rn(a, b), c));
+}
 template <typename T>
 struct ProjVal {
   const ProjSrc<T>* s;
   __device__ __forceinline__ T operator()(int32_t q) const {
-    return static_cast<T>(s->f[0] * (static_cast<double>(s->c[0][q]) - s->m[0]) +
-                          s->f[1] * (static_cast<double>(s->c[1][q]) - s->m[1]) +
-                          s->f[2] * (static_cast<double>(s->c[2][q]) - s->m[2]));
+    return fox_key<T>(s->f, s->m, s->c[0][q], s->c[1][q], s->c[2][q]);
   }
 };
 

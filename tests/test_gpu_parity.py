@@ -229,13 +229,16 @@ def test_large_element_path_and_empty_elements():
     compare_stats(vg, vo, 1e-10, stats_layout=False)
 
 
+@pytest.mark.parametrize("fox", [False, True])
 @pytest.mark.parametrize("precision", [0, 1])
-def test_binning_split_changes_no_result(precision):
+def test_binning_split_changes_no_result(precision, fox):
     """Every size-class split of the binning (chunk-sort tile for elements up to the split,
     bucket-rank tiles above it, up to 512 and up to 1024, the large-element kernel beyond)
-    gives the same pointers, bins and statistics bit for bit; in FP64 they are the oracle's.
-    Out-of-range shapes are refused."""
+    gives the same pointers, bins and statistics bit for bit, with the hierarchical bins and
+    with Fox's projection; in FP64 they are the oracle's, and the re-ordered state keeps
+    every particle's values.  Out-of-range shapes are refused."""
     w = synth.workload("channel_tiny")
+    w = dict(w, params=dict(w["params"], cond_mode=1, fox_bins=16) if fox else w["params"])
     g = w["grid"]
     rng = np.random.default_rng(17)
     counts = rng.integers(1, 60, g.ne)
@@ -249,7 +252,11 @@ def test_binning_split_changes_no_result(precision):
         c.set_launch_shapes(tile_split=split)
         assert c.launch_shapes()["tile_split"] == split
         c.set_particles(st, 0)
-        out = (c.get_particles()["cp"], c.element_stats()[0], *c.bins(), c.nodal_stats())
+        sg = c.get_particles()
+        if precision == 0:
+            for k in ("u", "v", "w", "om", "psi"):
+                assert np.array_equal(sg[k], st[k]), k
+        out = (sg["cp"], c.element_stats()[0], *c.bins(), c.nodal_stats())
         if ref is None:
             ref = out
         else:
