@@ -246,7 +246,8 @@ __device__ __forceinline__ void count_update(const AdvanceArgs<T>& a, bool valid
       if ((threadIdx.x & 31) == __ffs(peers) - 1) atomicAdd(a.cnt + e_new, __popc(peers));
     }
   }
-  warp_count(bc, kDiagHops, f.hops);
+  // hops: the few lanes that hopped add to the block's counters themselves
+  if (f.hops > 0) atomicAdd(bc + kDiagHops, static_cast<unsigned>(f.hops));
   if (__any_sync(kFull, f.fb | f.brute | f.lost | f.nf | f.gex | f.c0)) {
     warp_count(bc, kDiagFallback, f.fb);
     warp_count(bc, kDiagBrute, f.brute);
@@ -263,21 +264,7 @@ __device__ __forceinline__ void count_update(const AdvanceArgs<T>& a, bool valid
     warp_count(bc, kDiagOmegaReflect, f.oref);
     warp_count(bc, kDiagSource, f.src);
   }
-  if (__any_sync(kFull, f.hop_bin > 0)) {
-    // the warp's hop histogram in two packed sums (8-bit fields: bins 1-4, then 5-7; a field
-    // counts at most 32 lanes)
-    const int b = f.hop_bin;
-    const unsigned lo = (b >= 1 && b <= 4) ? 1u << (8 * (b - 1)) : 0u;
-    const unsigned hi = b >= 5 ? 1u << (8 * (b - 5)) : 0u;
-    const unsigned slo = __reduce_add_sync(kFull, lo), shi = __reduce_add_sync(kFull, hi);
-    if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-      for (int k = 0; k < 7; ++k) {
-        const unsigned c = ((k < 4 ? slo : shi) >> (8 * (k < 4 ? k : k - 4))) & 0xffu;
-        if (c) atomicAdd(bc + kDiagHopHist0 + 1 + k, c);
-      }
-    }
-  }
+  if (f.hop_bin > 0) atomicAdd(bc + kDiagHopHist0 + f.hop_bin, 1u);
 }
 
 // FP32: 4 blocks of 256 per SM (64 registers); FP64: 2 blocks.  BATCH: model constants and
