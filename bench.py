@@ -46,15 +46,16 @@ SINGLE_POSITION_STEP_BYTES = 98
 # change of the sources the bench reports traffic as null until the next capture.
 NCU_RECORDS = {
     # channel_50k, 25.0M particles (FP32) and 5.0M (FP64 form), one GB300
-    "28612f92c7a38c546113feeb260b4f9dbf67d22a23361d2cbbcd97b0942d4dee": {
-        "traffic": {"advance": 2102.473e6 / 25.0e6,
-                    "statistics_binning": (0.066048e6 + 738.736896e6 + 245.224704e6) / 25.0e6},
-        "limiter": {"advance": "instruction issue: 65% issue-active at 48% warps active "
-                               "(64 registers cap 4 blocks of 256), long-scoreboard stalls "
-                               "first; DRAM 21% of peak",
-                    "statistics_binning": "instruction issue and shared-memory latency: 66% "
-                                          "issue-active (<= 512 class), short-scoreboard and "
-                                          "barrier stalls first; DRAM 11% of peak"},
+    "0879a78330f4f2ec94bffd52990fb9ad2359439b4f6d2eb4e70a84746016fd13": {
+        "traffic": {"advance": (1161.091e6 + 941.431296e6) / 25.0e6,
+                    "statistics_binning": (0.065792e6 + 688.83712e6 + 50.196736e6 + 233.807104e6
+                                           + 11.623168e6) / 25.0e6},
+        "limiter": {"advance": "instruction issue and memory latency: 65% issue-active at 48% "
+                               "warps active (64 registers cap 4 blocks of 256), long-scoreboard "
+                               "stalls first; DRAM 22% of peak",
+                    "statistics_binning": "instruction issue and shared-memory latency: 69% "
+                                          "issue-active (<= 512 class), short-scoreboard stalls "
+                                          "first; DRAM 12% of peak"},
         "f64_advance_fp64_inst_per_particle": (1407568787 + 454038118 + 836638858) / 5.0e6,
     },
 }
