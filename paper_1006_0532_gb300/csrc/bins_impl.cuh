@@ -474,6 +474,22 @@ __device__ __forceinline__ T fox_key(const double* f, const double* m, T u, T v,
   const double c = __dmul_rn(f[2], __dsub_rn(static_cast<double>(w), m[2]));
   return static_cast<T>(__dadd_rn(__dadd_rn(a, b), c));
 }
+// The sort value of a particle id: a positive normal number whose bits are 2^23 (FP32) or
+// 2^52 (FP64) plus the id, so that values are distinct and ordered as the ids.
+template <typename T>
+struct PidVal;
+template <>
+struct PidVal<float> {
+  const uint32_t* pid;
+  __device__ __forceinline__ float operator()(int32_t q) const { return __uint_as_float(0x00800000u + pid[q]); }
+};
+template <>
+struct PidVal<double> {
+  const uint32_t* pid;
+  __device__ __forceinline__ double operator()(int32_t q) const {
+    return __longlong_as_double(static_cast<long long>(0x0010000000000000ull + pid[q]));
+  }
+};
 template <typename T>
 struct ProjVal {
   const ProjSrc<T>* s;
@@ -727,7 +743,10 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP, FOX>& t, int e,
         t.proj.c[k] = k == 0 ? a.p.u : (k == 1 ? a.p.v : a.p.w);
       }
       __syncthreads();
-      whole_level(ProjVal<T>{&t.proj}, 1);
+      // all factors zero (a constant scalar, or a degenerate correlation system): every
+      // U_rho is 0 and the order of (U_rho, id) is that of the ids, sorted directly
+      if (t.fox[0] == 0.0 && t.fox[1] == 0.0 && t.fox[2] == 0.0) whole_level(PidVal<T>{a.p.pid}, 1);
+      else whole_level(ProjVal<T>{&t.proj}, 1);
     }
   }
   const int G = g[0] * g[1] * g[2];
