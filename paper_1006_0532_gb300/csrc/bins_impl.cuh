@@ -1,6 +1,8 @@
 // Per-element statistics and conditional means for elements of up to 1024 particles, one
-// thread block per entry of the plan's tile lists (two size classes, launched one after the
-// other; larger elements go through the block kernel in k_stats.cu).
+// thread block per entry of the plan's tile lists (three size classes, launched one after
+// the other; larger elements go through the block kernel in k_stats.cu).  The chunk-sort
+// tile below serves elements up to the split and, for Fox's projection, every class; the
+// bucket-rank tile further down serves the larger classes of the hierarchical bins.
 //
 // Sect. 3.5 / Appendix A: the element's particles are sorted by (u, id); the level-1 groups
 // (positions with equal floor(g1 p / N)) are sorted by (v, id), the level-2 groups by
@@ -19,10 +21,11 @@
 // lane and combines lanes as FP32 value/error pairs, the FP64 form sums in FP64.  The 13
 // outputs are then formed in FP64 one per lane.
 // Fox's projection (Eqs. 64-66, cond_mode 1) is a compile-time variant of the kernel: the
-// (u, id) order fixes the order of the moment sums, the moments give the projection
+// particle-id order fixes the order of the moment sums, the moments give the projection
 // factors, and one more level orders the whole element by the projected velocity (pairwise
-// merge rounds of sorted runs rank these whole-element levels).  The hierarchical variant
-// carries none of its members or code.
+// merge rounds of sorted runs rank these whole-element levels); an element whose factors
+// are all zero keeps the id order, which is then its (U_rho, id) order.  The hierarchical
+// variant carries none of its members or code.
 #pragma once
 #include <initializer_list>
 
@@ -715,8 +718,8 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP, FOX>& t, int e,
     // moments (warp 0) in the final order
     if (warp == 0) element_moments_of(a, t, cur, n, e, g);
   } else {
-    // Fox's projection (Eqs. 64-66): the (u, id) order fixes the order of the moment sums;
-    // the moments give the factors; then one level over the whole element by U_rho
+    // Fox's projection (Eqs. 64-66): the particle-id order fixes the order of the moment
+    // sums; the moments give the factors; then one level over the whole element by U_rho
     auto whole_level = [&](const auto& val, int ti) {
       const float invG = 1.0f;
       if (n > 32 && warp == 0) chunk_tables(t, n, 1, invG, lane);
@@ -733,7 +736,7 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP, FOX>& t, int e,
       cur = nxt;
       nxt = tmp;
     };
-    if (n > 0) whole_level(ArrVal<T>{a.p.u}, 0);
+    if (n > 0) whole_level(PidVal<T>{a.p.pid}, 0);
     if (warp == 0) element_moments_of(a, t, cur, n, e, g);   // an empty element writes zeros
     if (n > 0) {
       if (threadIdx.x < 3) {
@@ -744,9 +747,8 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP, FOX>& t, int e,
       }
       __syncthreads();
       // all factors zero (a constant scalar, or a degenerate correlation system): every
-      // U_rho is 0 and the order of (U_rho, id) is that of the ids, sorted directly
-      if (t.fox[0] == 0.0 && t.fox[1] == 0.0 && t.fox[2] == 0.0) whole_level(PidVal<T>{a.p.pid}, 1);
-      else whole_level(ProjVal<T>{&t.proj}, 1);
+      // U_rho is 0 and the order of (U_rho, id) is the id order the element already has
+      if (!(t.fox[0] == 0.0 && t.fox[1] == 0.0 && t.fox[2] == 0.0)) whole_level(ProjVal<T>{&t.proj}, 1);
     }
   }
   const int G = g[0] * g[1] * g[2];
