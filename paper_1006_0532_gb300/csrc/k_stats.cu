@@ -121,10 +121,13 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne_
   int32_t carry = p0, lmin = 0x7fffffff, lmax = -1, tA = 0, tB = 0, tM = 0;
   if (tid == 0) scal[3] = 0;
   __syncthreads();
+  // each pass's counts are loaded one pass ahead, so that the load overlaps the scan
+  int32_t c_next = tid < ne ? pl.cnt[eb + tid] : 0;
   for (int32_t base = 0; base < ne; base += kPlanThreads) {
     const bool valid = base + tid < ne;
     const int32_t e = eb + base + tid;
-    const int32_t c = valid ? pl.cnt[e] : 0;
+    const int32_t c = c_next;
+    c_next = base + kPlanThreads + tid < ne ? pl.cnt[e + kPlanThreads] : 0;
     int64_t ptot;
     const int64_t pex = block_exclusive_scan<int64_t>(c | tile_class_bits(valid, c, pl.tile_split), sh.tmp64, ptot);
     const int32_t ex = static_cast<int32_t>(pex & kCountMask), tot = static_cast<int32_t>(ptot & kCountMask);
