@@ -46,10 +46,10 @@ SINGLE_POSITION_STEP_BYTES = 98
 # change of the sources the bench reports traffic as null until the next capture.
 NCU_RECORDS = {
     # channel_50k, 25.0M particles (FP32) and 5.0M (FP64 form), one GB300
-    "1e7506cc44b58a84597b4a773cc52e18ddce2c389ccb1c94e2acf61c1019045a": {
-        "traffic": {"advance": (1160.577e6 + 942.027264e6) / 25.0e6,
-                    "statistics_binning": (0.066048e6 + 688.635904e6 + 49.738496e6 + 233.79584e6
-                                           + 11.924736e6) / 25.0e6},
+    "013b670569e217261573ce1c69b284fb413726ce86f75411d20da99b9ae6b51c": {
+        "traffic": {"advance": (1161.118e6 + 941.98656e6) / 25.0e6,
+                    "statistics_binning": (0.065792e6 + 688.991232e6 + 49.92896e6 + 233.8048e6
+                                           + 11.673088e6) / 25.0e6},
         "limiter": {"advance": "instruction issue and memory latency: 65% issue-active at 48% "
                                "warps active (64 registers cap 4 blocks of 256), long-scoreboard "
                                "stalls first; DRAM 22% of peak",
