@@ -289,21 +289,42 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne_
 
 // Element lists: idx[off[e] .. off[e] + cnt[e]) holds the slots of the particles in e.
 // An element id outside 0 .. ne - 1 (a caller's state) is skipped: the count kernel has
-// left it out of the counts and reported it.
+// left it out of the counts and reported it.  A thread takes kScatterPer particles, blockDim.x
+// apart, and issues all their loads, then all their cursor atomics (one per run of lanes
+// sharing an element), then all their stores, so that each kind is in flight together.
+constexpr int kScatterPer = 8;
 __global__ void scatter_kernel(const int32_t* __restrict__ elem, int64_t np, int32_t ne, int32_t* cursor,
                                int32_t* idx) {
-  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-  const int e = i < np ? elem[i] : -1;
-  const bool valid = i < np && e >= 0 && e < ne;
-  const unsigned active = __ballot_sync(kFull, valid);
-  if (!valid) return;
-  const unsigned peers = __match_any_sync(active, e);
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * blockDim.x * kScatterPer + threadIdx.x;
   const int lane = threadIdx.x & 31;
-  const int leader = __ffs(peers) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(cursor + e, __popc(peers));
-  base = __shfl_sync(peers, base, leader);
-  idx[base + __popc(peers & ((1u << lane) - 1u))] = static_cast<int32_t>(i);
+  int e[kScatterPer];
+  bool valid[kScatterPer];
+#pragma unroll
+  for (int k = 0; k < kScatterPer; ++k) {
+    const int64_t i = i0 + static_cast<int64_t>(k) * blockDim.x;
+    e[k] = i < np ? elem[i] : -1;
+    valid[k] = i < np && e[k] >= 0 && e[k] < ne;
+  }
+  unsigned peers[kScatterPer];
+  int base[kScatterPer];
+#pragma unroll
+  for (int k = 0; k < kScatterPer; ++k) {
+    const unsigned active = __ballot_sync(kFull, valid[k]);
+    peers[k] = 0u;
+    base[k] = 0;
+    if (valid[k]) {
+      peers[k] = __match_any_sync(active, e[k]);
+      if (lane == __ffs(peers[k]) - 1) base[k] = atomicAdd(cursor + e[k], __popc(peers[k]));
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < kScatterPer; ++k) {
+    if (valid[k]) {
+      const int b = __shfl_sync(peers[k], base[k], __ffs(peers[k]) - 1);
+      idx[b + __popc(peers[k] & ((1u << lane) - 1u))] =
+          static_cast<int32_t>(i0 + static_cast<int64_t>(k) * blockDim.x);
+    }
+  }
 }
 
 // ---------------------------------------------------------------------------------------
@@ -776,7 +797,9 @@ void launch_plan(Plan& pl, int32_t ne, int K, int minnpel, int allow_moves, cuda
 
 void launch_scatter(const int32_t* elem, int64_t np, int32_t ne, Plan& pl, cudaStream_t s) {
   if (np <= 0) return;
-  scatter_kernel<<<static_cast<unsigned>((np + 255) / 256), 256, 0, s>>>(elem, np, ne, pl.cursor, pl.idx);
+  const int64_t per_block = 256 * kScatterPer;
+  scatter_kernel<<<static_cast<unsigned>((np + per_block - 1) / per_block), 256, 0, s>>>(elem, np, ne, pl.cursor,
+                                                                                          pl.idx);
 }
 
 template <typename T>
