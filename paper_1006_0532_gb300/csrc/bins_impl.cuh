@@ -839,14 +839,20 @@ template <typename T, int CAP, int THREADS>
 struct RankTile {
   static constexpr int kNB = CAP;   // buckets of one level over all of its groups
   using A = double;                 // moment combination and outputs
-  double mh[12], ml[12], msh[5];    // moment sums (value/error pairs) and shift values
   T u[CAP], v[CAP], w[CAP], om[CAP], psi[CAP];
   uint32_t pid[CAP];
   int32_t slot[CAP];
-  struct {
-    int32_t start[kNB + 1];         // bucket counts, then each bucket's first position
-    uint32_t glo[256], gsc[256];    // each group's key range, then its bucket origin and scale
-  } x_b;
+  // the levels' bucket tables, and after the last level the moment sums in the same bytes
+  // (the FP32 mid-size tile then fits 10 blocks per SM instead of 9)
+  union {
+    struct {
+      int32_t start[kNB + 1];       // bucket counts, then each bucket's first position
+      uint32_t glo[256], gsc[256];  // each group's key range, then its bucket origin and scale
+    } x_b;
+    struct {
+      double mh[12], ml[12], msh[5];   // moment sums (value/error pairs) and shift values
+    } x_m;
+  };
   int16_t ord[CAP];                 // position -> particle (staging index), final level
   int16_t pos[CAP];                 // particle -> position, final level
   int16_t mem[CAP];                 // particles by bucket
@@ -1181,11 +1187,11 @@ __device__ __forceinline__ void rank_moments(RankTile<T, CAP, THREADS>& t, int n
     m1.warp_pair(h1, l1);
     m2.warp_pair(h2, l2);
     if (lane == 0) {
-      t.mh[c0] = h0; t.ml[c0] = l0;
-      t.mh[c1] = h1; t.ml[c1] = l1;
-      t.mh[c2] = h2; t.ml[c2] = l2;
-      if (warp < 3) t.msh[warp] = static_cast<double>(sa);
-      else { t.msh[3] = static_cast<double>(sa); t.msh[4] = static_cast<double>(sb); }
+      t.x_m.mh[c0] = h0; t.x_m.ml[c0] = l0;
+      t.x_m.mh[c1] = h1; t.x_m.ml[c1] = l1;
+      t.x_m.mh[c2] = h2; t.x_m.ml[c2] = l2;
+      if (warp < 3) t.x_m.msh[warp] = static_cast<double>(sa);
+      else { t.x_m.msh[3] = static_cast<double>(sa); t.x_m.msh[4] = static_cast<double>(sb); }
     }
   }
   __syncthreads();
@@ -1365,11 +1371,11 @@ __device__ void element_rank_tile(const StatsArgs<T>& a, RankTile<T, CAP, THREAD
       const double inv = recip_n(n);
       const int ix = mom_nib(kMomX, lane), iy = mom_nib(kMomY, lane);
       const int iz = mom_nib(kMomZ, lane), iw = mom_nib(kMomW, lane);
-      double v = ix < 15 ? t.msh[ix] : 0.0;
-      if (iy < 15) v += (t.mh[iy] + t.ml[iy]) * inv;
+      double v = ix < 15 ? t.x_m.msh[ix] : 0.0;
+      if (iy < 15) v += (t.x_m.mh[iy] + t.x_m.ml[iy]) * inv;
       if (iz < 15) {
-        const double z = (t.mh[iz] + t.ml[iz]) * inv;
-        const double wv = (t.mh[iw] + t.ml[iw]) * inv;
+        const double z = (t.x_m.mh[iz] + t.x_m.ml[iz]) * inv;
+        const double wv = (t.x_m.mh[iw] + t.x_m.ml[iw]) * inv;
         v -= z * wv;
       }
       if (lane == 0) v = static_cast<double>(n);
