@@ -329,7 +329,7 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
     a.fox_bins = c.prm.fox_bins;
     a.diag = c.diag;
     a.err = c.err;
-    launch_stats<T>(a, c.num_sms, s);
+    launch_stats<T>(a, c.num_sms, s, &c.side);
     c.launches += 4;   // three tile classes and the large-element kernel
   }
   if (resort) {
@@ -1392,6 +1392,14 @@ int pdfx_create(const pdfx_params* p, const pdfx_allocator* alloc, void** out) {
     delete c;
     return PDFX_ERR_CUDA;
   }
+  {
+    bool ok = true;
+    for (cudaStream_t& st : c->side.side)
+      ok = ok && cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t& e : c->side.ev)
+      ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+    c->side.ok = ok;
+  }
   c->diag = static_cast<unsigned long long*>(dev_alloc(*c, sizeof(unsigned long long) * kDiagCount));
   c->err = static_cast<int*>(dev_alloc(*c, sizeof(int) * 4));
   c->brute_list = static_cast<int32_t*>(dev_alloc(*c, sizeof(int32_t) * kBruteCap));
@@ -1419,6 +1427,10 @@ void pdfx_destroy(void* ctx) {
   for (Ctx::PcgGraph& g : c->pcg_graphs)
     if (g.exec) cudaGraphExecDestroy(g.exec);
   if (c->gstream) cudaStreamDestroy(c->gstream);
+  for (cudaStream_t st : c->side.side)
+    if (st) cudaStreamDestroy(st);
+  for (cudaEvent_t e : c->side.ev)
+    if (e) cudaEventDestroy(e);
   for (auto& o : c->owned) {
     if (c->has_alloc) c->alloc.release(o.first, o.second, c->alloc.user);
     else cudaFree(o.first);

@@ -802,7 +802,7 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP, FOX>& t, int e,
 // b of the list, which for instance k fills its element range [eb, ee) -- class 0 (up to
 // kTileSplit particles) from the front of a.tiles, class 1 (kTileMid + 1 .. kSmallCap) from
 // its back, class 2 (kTileSplit + 1 .. kTileMid) from the front of a.tiles_mid.  The class-0
-// kernel, launched first, advances the step counter once per step.
+// kernel advances the step counter once per step (no kernel of the statistics reads it).
 template <int CLS, typename T>
 __device__ __forceinline__ int tile_element(const StatsArgs<T>& a, int b, int& moves) {
   if (CLS == 0 && b == 0 && threadIdx.x == 0 && a.step_inc) atomicAdd(a.step_inc, 1u);
@@ -1470,19 +1470,32 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1536 : 1024) / THRE
 }  // namespace
 
 template <typename T>
-void launch_stats_tiles_impl(const StatsArgs<T>& a, int num_sms, cudaStream_t s) {
+void launch_stats_tiles_impl(const StatsArgs<T>& a, int num_sms, cudaStream_t s, const SideStreams* side) {
   if (a.ne <= 0) return;
   static_assert(kSmallCap == 1024 && kTileMid == 512 && kTileSplit == 256,
                 "tile classes cover the small-element capacity");
   // elements of up to 256 particles: chunk sorts (4 warps; groups of at most 32 positions
   // are sorted by one warp in registers, which suits small elements); 257..512 (4 warps)
   // and 513..1024 (8 warps): bucket ranks.  Fox's projection: chunk sorts in every class.
+  // The classes take disjoint elements and write disjoint outputs: with the context's side
+  // streams they run as parallel branches (the large class on side[0], the small on side[1],
+  // the mid-size on s), so that each one's last wave and its blocks of other classes, which
+  // return at once, overlap the others' work; s then waits for both branches.
   (void)num_sms;
   const unsigned grid = static_cast<unsigned>(a.ne);
+  const bool fork = side && side->ok;
+  cudaStream_t s_large = s, s_small = s;
+  if (fork) {
+    cudaEventRecord(side->ev[0], s);
+    cudaStreamWaitEvent(side->side[0], side->ev[0], 0);
+    cudaStreamWaitEvent(side->side[1], side->ev[0], 0);
+    s_large = side->side[0];
+    s_small = side->side[1];
+  }
   if (a.cond_mode == 1) {
-    stats_tile_kernel<T, 256, 128, 0, true><<<grid, 128, 0, s>>>(a);
+    stats_tile_kernel<T, 1024, 256, 1, true><<<grid, 256, 0, s_large>>>(a);
+    stats_tile_kernel<T, 256, 128, 0, true><<<grid, 128, 0, s_small>>>(a);
     stats_tile_kernel<T, 512, 128, 2, true><<<grid, 128, 0, s>>>(a);
-    stats_tile_kernel<T, 1024, 256, 1, true><<<grid, 256, 0, s>>>(a);
   } else {
     constexpr size_t mid = sizeof(RankTile<T, 512, 128>), large = sizeof(RankTile<T, 1024, 256>);
     static_assert(large <= 227 * 1024, "rank tile exceeds shared memory");
@@ -1492,9 +1505,15 @@ void launch_stats_tiles_impl(const StatsArgs<T>& a, int num_sms, cudaStream_t s)
       cudaFuncSetAttribute(rank_tile_kernel<T, 1024, 256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(large));
     }
-    stats_tile_kernel<T, 256, 128, 0, false><<<grid, 128, 0, s>>>(a);
+    rank_tile_kernel<T, 1024, 256, 1><<<grid, 256, large, s_large>>>(a);
+    stats_tile_kernel<T, 256, 128, 0, false><<<grid, 128, 0, s_small>>>(a);
     rank_tile_kernel<T, 512, 128, 2><<<grid, 128, mid, s>>>(a);
-    rank_tile_kernel<T, 1024, 256, 1><<<grid, 256, large, s>>>(a);
+  }
+  if (fork) {
+    cudaEventRecord(side->ev[1], side->side[0]);
+    cudaEventRecord(side->ev[2], side->side[1]);
+    cudaStreamWaitEvent(s, side->ev[1], 0);
+    cudaStreamWaitEvent(s, side->ev[2], 0);
   }
 }
 

@@ -4,8 +4,9 @@
 namespace pdfx {
 
 template <>
-void launch_stats_tiles<float>(const StatsArgs<float>& a, int num_sms, cudaStream_t s) {
-  launch_stats_tiles_impl<float>(a, num_sms, s);
+void launch_stats_tiles<float>(const StatsArgs<float>& a, int num_sms, cudaStream_t s,
+                               const SideStreams* side) {
+  launch_stats_tiles_impl<float>(a, num_sms, s, side);
 }
 
 }  // namespace pdfx

@@ -818,14 +818,14 @@ void launch_redistribute(Particles<T> p, Plan& pl, int K, const InstDev<T>* inst
 }
 
 template <typename T>
-void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s) {
+void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s, const SideStreams* side) {
   const size_t big = stats_smem_bytes<T>(kBigCap);
   static_assert(5 * 8 * kBigCap + 11 * kBigCap <= 227 * 1024, "large-element tile exceeds shared memory");
   if (first_use_on_device(stats_configured<T>)) {
     cudaFuncSetAttribute(stats_big_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(big));
   }
-  launch_stats_tiles<T>(a, num_sms, s);
+  launch_stats_tiles<T>(a, num_sms, s, side);
   stats_big_kernel<T><<<static_cast<unsigned>(num_sms > 0 ? num_sms : 1), kStatsThreads, big, s>>>(a);
 }
 
@@ -1037,7 +1037,7 @@ template void launch_derive_fields<double>(const ElemGeo<double>*, const ElemTop
                                        int64_t, const ElemGeo<T>*, const ElemTopo*,            \
                                        const uint32_t*,                                        \
                                        int, unsigned long long*, int*, cudaStream_t);          \
-  template void launch_stats<T>(const StatsArgs<T>&, int, cudaStream_t);
+  template void launch_stats<T>(const StatsArgs<T>&, int, cudaStream_t, const SideStreams*);
 PDFX_INSTANTIATE(double)
 PDFX_INSTANTIATE(float)
 #undef PDFX_INSTANTIATE

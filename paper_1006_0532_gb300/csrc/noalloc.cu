@@ -138,7 +138,7 @@ int element_stats_noalloc(Ctx& c, int64_t np, const double* u, const double* v, 
   a.gbin = gbin;
   a.diag = c.diag;
   a.err = c.err;
-  launch_stats<double>(a, c.num_sms, s);
+  launch_stats<double>(a, c.num_sms, s, &c.side);
   if (nmom) launch_node_average(emom, c.ne_off, c.ne_list, c.nn, nmom, s);
   // iota, count and scatter (with particles), plan, three tile classes and the large-element
   // kernel, node average

@@ -229,6 +229,17 @@ constexpr int kRedBlocks = 256;                  // blocks of the solvers' reduc
 constexpr int kPcgActive = eops::S_ACTIVE;
 constexpr int kPcgIters = eops::S_ITERS;
 
+// Two streams and three events for the statistics tiles' size classes, which are independent
+// (disjoint elements and outputs) and run as parallel branches of the step: fork after the
+// lists, join before the large-element kernel.  Captured into a graph they become parallel
+// nodes.  Created with the context, outside any capture; ok is false when creation failed
+// (the classes then run one after another on the caller's stream).
+struct SideStreams {
+  cudaStream_t side[2] = {nullptr, nullptr};
+  cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+  bool ok = false;
+};
+
 struct Ctx {
   pdfx_params prm{};
   pdfx_allocator alloc{};
@@ -266,6 +277,7 @@ struct Ctx {
   // CUDA graph of a cycle of steps (2 sort_every steps, so the buffer roles repeat)
   cudaStream_t gstream = nullptr;
   cudaGraphExec_t gexec = nullptr;
+  SideStreams side;               // branches of the statistics tiles
   double g_dt = 0.0;
   int g_steps = 0;
   const void* g_buf = nullptr;
@@ -373,9 +385,10 @@ void launch_redistribute(Particles<T> p, Plan& pl, int K, const InstDev<T>* inst
                          int64_t np, const ElemGeo<T>* geo, const ElemTopo* topo, const uint32_t* stepc,
                          int num_sms, unsigned long long* diag, int* err, cudaStream_t s);
 template <typename T>
-void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s);
+void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s, const SideStreams* side);
 template <typename T>
-void launch_stats_tiles(const StatsArgs<T>& a, int num_sms, cudaStream_t s);   // k_bins_f32.cu / k_bins_f64.cu
+void launch_stats_tiles(const StatsArgs<T>& a, int num_sms, cudaStream_t s,
+                        const SideStreams* side);   // k_bins_f32.cu / k_bins_f64.cu
 void launch_node_average(const double* emom, const int32_t* ne_off, const int32_t* ne_list,
                          int32_t nn, double* nmom, cudaStream_t s);
 // Eq. 26: max over nodes of ||(<U>, <V>, <W>, <omega>, <psi>)||_2 into out[0] (one block).
