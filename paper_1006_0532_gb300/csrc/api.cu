@@ -275,8 +275,7 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
   {
     StageTimer t(c, 1, s);
     c.plan.tile_split = c.tile_split;
-    launch_plan(c.plan, c.ne, c.K, c.prm.minnpel, allow_moves ? 1 : 0, s);
-    c.launches++;
+    c.launches += launch_plan(c.plan, c.ne, c.K, c.prm.minnpel, allow_moves ? 1 : 0, s);
   }
   {
     StageTimer t(c, 2, s);

@@ -104,9 +104,111 @@ __device__ __forceinline__ void place_tile_class(Plan& pl, bool valid, int32_t c
   tM += static_cast<int32_t>((tot >> 52) & 0xfff);
 }
 
+// Pass 1 for a single instance over many blocks: chunk k holds elements [k kPlanThreads,
+// (k + 1) kPlanThreads).  plan_chunk_totals leaves each chunk's count sum with its tile-class
+// counts packed above it (as pass 1's scan packs them; a chunk holds at most kPlanThreads
+// elements) in tot[2 k], and its smallest and largest count in the two words of tot[2 k + 1].
+__global__ void __launch_bounds__(kPlanThreads) plan_chunk_totals(Plan pl, int32_t ne, int64_t* tot) {
+  __shared__ PlanShared sh;
+  const int tid = threadIdx.x;
+  const int32_t e = static_cast<int32_t>(blockIdx.x) * kPlanThreads + tid;
+  const bool valid = e < ne;
+  const int32_t c = valid ? pl.cnt[e] : 0;
+  if (blockIdx.x == 0 && tid == 0) pl.scal[3] = 0;
+  int64_t ptot;
+  block_exclusive_scan<int64_t>(c | tile_class_bits(valid, c, pl.tile_split), sh.tmp64, ptot);
+  int32_t lmin = valid ? c : 0x7fffffff, lmax = valid ? c : -1;
+  for (int o = 16; o > 0; o >>= 1) {
+    lmin = min(lmin, __shfl_xor_sync(kFull, lmin, o));
+    lmax = max(lmax, __shfl_xor_sync(kFull, lmax, o));
+  }
+  if ((tid & 31) == 0) { sh.vmin[tid >> 5] = lmin; sh.vmax[tid >> 5] = lmax; }
+  __syncthreads();
+  if (tid == 0) {
+    int32_t a = 0x7fffffff, b = -1;
+    for (int w = 0; w < kPlanThreads / 32; ++w) { a = min(a, sh.vmin[w]); b = max(b, sh.vmax[w]); }
+    tot[2 * blockIdx.x] = ptot;
+    int32_t* mm = reinterpret_cast<int32_t*>(tot + 2 * blockIdx.x + 1);
+    mm[0] = a;
+    mm[1] = b;
+  }
+}
+
+// plan_chunk_offsets: chunk k's offsets and tile-class entries, from the totals of the
+// chunks before it; the last chunk also writes the end offset, the class counts and the
+// minimum and maximum count (scal 4, 5).  The same values as the one-block pass 1.
+__global__ void __launch_bounds__(kPlanThreads) plan_chunk_offsets(Plan pl, int32_t ne, int nchunks,
+                                                                    const int64_t* tot) {
+  __shared__ PlanShared sh;
+  const int tid = threadIdx.x;
+  const int k = static_cast<int>(blockIdx.x);
+  const bool last = k == nchunks - 1;
+  if (tid < 32) {
+    // counts and class counts of the chunks before k (all chunks for the last one's totals)
+    int32_t cnt = 0, a = 0, b = 0, m = 0, mn = 0x7fffffff, mx = -1;
+    for (int j = tid; j < nchunks; j += 32) {
+      const int64_t t = tot[2 * j];
+      if (j < k) {
+        cnt += static_cast<int32_t>(t & kCountMask);
+        a += static_cast<int32_t>((t >> 28) & 0xfff);
+        b += static_cast<int32_t>((t >> 40) & 0xfff);
+        m += static_cast<int32_t>((t >> 52) & 0xfff);
+      }
+      const int32_t* mm = reinterpret_cast<const int32_t*>(tot + 2 * j + 1);
+      mn = min(mn, mm[0]);
+      mx = max(mx, mm[1]);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      cnt += __shfl_xor_sync(kFull, cnt, o);
+      a += __shfl_xor_sync(kFull, a, o);
+      b += __shfl_xor_sync(kFull, b, o);
+      m += __shfl_xor_sync(kFull, m, o);
+      mn = min(mn, __shfl_xor_sync(kFull, mn, o));
+      mx = max(mx, __shfl_xor_sync(kFull, mx, o));
+    }
+    if (tid == 0) {
+      sh.carry[0] = cnt;
+      sh.carry[1] = a;
+      sh.carry[2] = b;
+      sh.carry[3] = m;
+      sh.carry[4] = mn;
+      sh.carry[5] = mx;
+    }
+  }
+  __syncthreads();
+  const int32_t p0 = pl.ip0 ? static_cast<int32_t>(pl.ip0[0]) : 0;
+  const int32_t carry = p0 + sh.carry[0];
+  int32_t tA = sh.carry[1], tB = sh.carry[2], tM = sh.carry[3];
+  const int32_t e = k * kPlanThreads + tid;
+  const bool valid = e < ne;
+  const int32_t c = valid ? pl.cnt[e] : 0;
+  int64_t ptot;
+  const int64_t pex = block_exclusive_scan<int64_t>(c | tile_class_bits(valid, c, pl.tile_split), sh.tmp64, ptot);
+  place_tile_class(pl, valid, c, e, 0, ne, pex, ptot, tA, tB, tM);
+  if (valid) {
+    const int32_t o = carry + static_cast<int32_t>(pex & kCountMask);
+    pl.off[e] = o;
+    pl.foff[e] = o;
+    pl.cursor[e] = o;
+    if (c > kSmallCap) pl.big_list[atomicAdd(pl.scal + 3, 1)] = e;
+  }
+  if (last && tid == 0) {
+    const int32_t end = carry + static_cast<int32_t>(ptot & kCountMask);
+    pl.off[ne] = end;
+    pl.foff[ne] = end;
+    pl.scal[4] = sh.carry[4];
+    pl.scal[5] = sh.carry[5];
+    pl.scal[6] = tA;
+    pl.scal[7] = tB;
+    pl.scal[8] = tM;
+  }
+}
+
 // One block per instance: elements [eb, ee) of the union grid, particle slots from p0.
+// pass1_done: pass 1 (offsets, tile classes, min / max) was taken by plan_chunk_totals and
+// plan_chunk_offsets; this block reads the minimum and maximum count they left in scal.
 __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne_all, int minnpel_one,
-                                                             int allow_moves) {
+                                                             int allow_moves, int pass1_done) {
   __shared__ PlanShared sh;
   __shared__ int32_t hist[kHistCap + 1];
   const int tid = threadIdx.x;
@@ -119,11 +221,11 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne_
   int32_t* scal = pl.scal + 16 * inst;
   // pass 1: offsets of the element lists, min / max, big elements (no moves)
   int32_t carry = p0, lmin = 0x7fffffff, lmax = -1, tA = 0, tB = 0, tM = 0;
-  if (tid == 0) scal[3] = 0;
+  if (tid == 0 && !pass1_done) scal[3] = 0;
   __syncthreads();
   // each pass's counts are loaded one pass ahead, so that the load overlaps the scan
-  int32_t c_next = tid < ne ? pl.cnt[eb + tid] : 0;
-  for (int32_t base = 0; base < ne; base += kPlanThreads) {
+  int32_t c_next = tid < ne && !pass1_done ? pl.cnt[eb + tid] : 0;
+  for (int32_t base = 0; base < ne && !pass1_done; base += kPlanThreads) {
     const bool valid = base + tid < ne;
     const int32_t e = eb + base + tid;
     const int32_t c = c_next;
@@ -142,7 +244,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne_
     }
     carry += tot;
   }
-  if (tid == 0) {
+  if (tid == 0 && !pass1_done) {
     if (last) { pl.off[ee] = carry; pl.foff[ee] = carry; }
     scal[6] = tA;
     scal[7] = tB;
@@ -157,6 +259,7 @@ __global__ void __launch_bounds__(kPlanThreads) plan_kernel(Plan pl, int32_t ne_
   if (tid == 0) {
     int32_t a = 0x7fffffff, b = -1;
     for (int w = 0; w < kPlanThreads / 32; ++w) { a = min(a, sh.vmin[w]); b = max(b, sh.vmax[w]); }
+    if (pass1_done) { a = scal[4]; b = scal[5]; }
     sh.cmin = a;
     sh.cmax = b;
     sh.need = allow_moves && minnpel > 0 && a < minnpel && (b - a) >= 2;
@@ -791,8 +894,19 @@ template <typename T> bool stats_configured[kMaxDevices];
 
 }  // namespace
 
-void launch_plan(Plan& pl, int32_t ne, int K, int minnpel, int allow_moves, cudaStream_t s) {
-  plan_kernel<<<static_cast<unsigned>(K > 0 ? K : 1), kPlanThreads, 0, s>>>(pl, ne, minnpel, allow_moves);
+int launch_plan(Plan& pl, int32_t ne, int K, int minnpel, int allow_moves, cudaStream_t s) {
+  // one instance with its histogram scratch: pass 1 over many blocks (the chunk totals live
+  // in the histogram, which only the later passes of the particle-number control use), then
+  // the one-block kernel for those passes, which returns at once when no particle moves
+  const int nchunks = ne > 0 ? (ne + kPlanThreads - 1) / kPlanThreads : 1;
+  if (K <= 1 && pl.hist && nchunks <= kHistCap) {
+    plan_chunk_totals<<<static_cast<unsigned>(nchunks), kPlanThreads, 0, s>>>(pl, ne, pl.hist);
+    plan_chunk_offsets<<<static_cast<unsigned>(nchunks), kPlanThreads, 0, s>>>(pl, ne, nchunks, pl.hist);
+    plan_kernel<<<1, kPlanThreads, 0, s>>>(pl, ne, minnpel, allow_moves, 1);
+    return 3;
+  }
+  plan_kernel<<<static_cast<unsigned>(K > 0 ? K : 1), kPlanThreads, 0, s>>>(pl, ne, minnpel, allow_moves, 0);
+  return 1;
 }
 
 void launch_scatter(const int32_t* elem, int64_t np, int32_t ne, Plan& pl, cudaStream_t s) {

@@ -95,7 +95,7 @@ int element_stats_noalloc(Ctx& c, int64_t np, const double* u, const double* v, 
     iota_kernel<<<static_cast<unsigned>((np + 255) / 256), 256, 0, s>>>(pid, np);
     launch_count(elem, np, c.ne, pl.cnt, c.diag, c.err, s);
   }
-  launch_plan(pl, c.ne, 1, 0, 0, s);
+  const int plan_launches = launch_plan(pl, c.ne, 1, 0, 0, s);
   launch_scatter(elem, np, c.ne, pl, s);
   StatsArgs<double> a{};
   a.p.u = const_cast<double*>(u);
@@ -142,7 +142,7 @@ int element_stats_noalloc(Ctx& c, int64_t np, const double* u, const double* v, 
   if (nmom) launch_node_average(emom, c.ne_off, c.ne_list, c.nn, nmom, s);
   // iota, count and scatter (with particles), plan, three tile classes and the large-element
   // kernel, node average
-  c.launches += (np > 0 ? 3 : 0) + 1 + 4 + (nmom ? 1 : 0);
+  c.launches += (np > 0 ? 3 : 0) + plan_launches + 4 + (nmom ? 1 : 0);
   return cudaGetLastError() == cudaSuccess ? PDFX_OK : PDFX_ERR_CUDA;
 }
 

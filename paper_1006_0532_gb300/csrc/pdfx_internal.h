@@ -377,7 +377,7 @@ void launch_init_batch(Particles<T> p, int64_t np, int K, const InstDev<T>* inst
 // Counts per element; ids outside 0 .. ne - 1 are skipped, counted and raise PDFX_ERR_ELEMENT.
 void launch_count(const int32_t* elem, int64_t np, int32_t ne, int32_t* cnt, unsigned long long* diag,
                   int* err, cudaStream_t s);
-void launch_plan(Plan& pl, int32_t ne, int K, int minnpel, int allow_moves, cudaStream_t s);
+int launch_plan(Plan& pl, int32_t ne, int K, int minnpel, int allow_moves, cudaStream_t s);   // kernels launched
 // Element lists (ids outside 0 .. ne - 1 are skipped; launch_count reports them).
 void launch_scatter(const int32_t* elem, int64_t np, int32_t ne, Plan& pl, cudaStream_t s);
 template <typename T>
