@@ -631,20 +631,27 @@ __device__ void element_tile(const StatsArgs<T>& a, Tile<T, CAP, FOX>& t, int e,
   __syncthreads();
   {
     const int32_t o = a.off[e], c = a.cnt[e];
+    if (!moves) {
+      // no particle moved: every list entry is the element's, entry j goes to position j
 #pragma unroll 1
-    for (int j0 = warp * 32; j0 < c; j0 += THREADS) {
-      const int j = j0 + lane;
-      int32_t q = -1;
-      if (j < c) {
-        q = a.idx[o + j];
-        if (moves && a.p.elem[q] != e) q = -1;
+      for (int j = threadIdx.x; j < c && j < CAP; j += THREADS) t.ord[j] = a.idx[o + j];
+      if (threadIdx.x == 0) t.n_gathered = c;
+    } else {
+#pragma unroll 1
+      for (int j0 = warp * 32; j0 < c; j0 += THREADS) {
+        const int j = j0 + lane;
+        int32_t q = -1;
+        if (j < c) {
+          q = a.idx[o + j];
+          if (a.p.elem[q] != e) q = -1;
+        }
+        const unsigned keep = __ballot_sync(kFull, q >= 0);
+        int base = 0;
+        if (lane == 0 && keep) base = atomicAdd(&t.n_gathered, __popc(keep));
+        base = __shfl_sync(kFull, base, 0);
+        const int at = base + __popc(keep & below);
+        if (q >= 0 && at < CAP) t.ord[at] = q;
       }
-      const unsigned keep = __ballot_sync(kFull, q >= 0);
-      int base = 0;
-      if (lane == 0 && keep) base = atomicAdd(&t.n_gathered, __popc(keep));
-      base = __shfl_sync(kFull, base, 0);
-      const int at = base + __popc(keep & below);
-      if (q >= 0 && at < CAP) t.ord[at] = q;
     }
     if (moves) {
       const int32_t gn = a.gain[e], g0 = a.goff[e];
@@ -1233,15 +1240,25 @@ __device__ void element_rank_tile(const StatsArgs<T>& a, RankTile<T, CAP, THREAD
       for (int k = 0; k < KPT; ++k)
         if (ek[k] != e) qk[k] = -1;
     }
+    if (!moves && c <= KPT * THREADS) {
+      // no particle moved: every list entry is the element's, entry j goes to position j
 #pragma unroll
-    for (int k = 0; k < KPT; ++k) {
-      const int32_t q = qk[k];
-      const unsigned keep = __ballot_sync(kFull, q >= 0);
-      int base = 0;
-      if (lane == 0 && keep) base = atomicAdd(&t.n_gathered, __popc(keep));
-      base = __shfl_sync(kFull, base, 0);
-      const int at = base + __popc(keep & below);
-      if (q >= 0 && at < CAP) t.slot[at] = q;
+      for (int k = 0; k < KPT; ++k) {
+        const int j = warp * 32 + k * THREADS + lane;
+        if (j < c) t.slot[j] = qk[k];
+      }
+      if (threadIdx.x == 0) atomicAdd(&t.n_gathered, c);
+    } else {
+#pragma unroll
+      for (int k = 0; k < KPT; ++k) {
+        const int32_t q = qk[k];
+        const unsigned keep = __ballot_sync(kFull, q >= 0);
+        int base = 0;
+        if (lane == 0 && keep) base = atomicAdd(&t.n_gathered, __popc(keep));
+        base = __shfl_sync(kFull, base, 0);
+        const int at = base + __popc(keep & below);
+        if (q >= 0 && at < CAP) t.slot[at] = q;
+      }
     }
     // a list longer than the capacity (particles leave it by moves) continues one round at
     // a time
@@ -1470,32 +1487,18 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1536 : 1024) / THRE
 }  // namespace
 
 template <typename T>
-void launch_stats_tiles_impl(const StatsArgs<T>& a, int num_sms, cudaStream_t s, const SideStreams* side) {
+void launch_stats_tiles_impl(const StatsArgs<T>& a, cudaStream_t s_small, cudaStream_t s_mid, cudaStream_t s_large) {
   if (a.ne <= 0) return;
   static_assert(kSmallCap == 1024 && kTileMid == 512 && kTileSplit == 256,
                 "tile classes cover the small-element capacity");
   // elements of up to 256 particles: chunk sorts (4 warps; groups of at most 32 positions
   // are sorted by one warp in registers, which suits small elements); 257..512 (4 warps)
   // and 513..1024 (8 warps): bucket ranks.  Fox's projection: chunk sorts in every class.
-  // The classes take disjoint elements and write disjoint outputs: with the context's side
-  // streams they run as parallel branches (the large class on side[0], the small on side[1],
-  // the mid-size on s), so that each one's last wave and its blocks of other classes, which
-  // return at once, overlap the others' work; s then waits for both branches.
-  (void)num_sms;
   const unsigned grid = static_cast<unsigned>(a.ne);
-  const bool fork = side && side->ok;
-  cudaStream_t s_large = s, s_small = s;
-  if (fork) {
-    cudaEventRecord(side->ev[0], s);
-    cudaStreamWaitEvent(side->side[0], side->ev[0], 0);
-    cudaStreamWaitEvent(side->side[1], side->ev[0], 0);
-    s_large = side->side[0];
-    s_small = side->side[1];
-  }
   if (a.cond_mode == 1) {
     stats_tile_kernel<T, 1024, 256, 1, true><<<grid, 256, 0, s_large>>>(a);
     stats_tile_kernel<T, 256, 128, 0, true><<<grid, 128, 0, s_small>>>(a);
-    stats_tile_kernel<T, 512, 128, 2, true><<<grid, 128, 0, s>>>(a);
+    stats_tile_kernel<T, 512, 128, 2, true><<<grid, 128, 0, s_mid>>>(a);
   } else {
     constexpr size_t mid = sizeof(RankTile<T, 512, 128>), large = sizeof(RankTile<T, 1024, 256>);
     static_assert(large <= 227 * 1024, "rank tile exceeds shared memory");
@@ -1507,13 +1510,7 @@ void launch_stats_tiles_impl(const StatsArgs<T>& a, int num_sms, cudaStream_t s,
     }
     rank_tile_kernel<T, 1024, 256, 1><<<grid, 256, large, s_large>>>(a);
     stats_tile_kernel<T, 256, 128, 0, false><<<grid, 128, 0, s_small>>>(a);
-    rank_tile_kernel<T, 512, 128, 2><<<grid, 128, mid, s>>>(a);
-  }
-  if (fork) {
-    cudaEventRecord(side->ev[1], side->side[0]);
-    cudaEventRecord(side->ev[2], side->side[1]);
-    cudaStreamWaitEvent(s, side->ev[1], 0);
-    cudaStreamWaitEvent(s, side->ev[2], 0);
+    rank_tile_kernel<T, 512, 128, 2><<<grid, 128, mid, s_mid>>>(a);
   }
 }
 

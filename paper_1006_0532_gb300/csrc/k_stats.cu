@@ -869,24 +869,38 @@ size_t stats_smem_bytes(int cap) {
   return 5 * r(sizeof(T) * cap) + r(4 * cap) + r(4 * cap) + r(2 * cap) + r(cap);
 }
 
+// The nodal moments: the mean of each element statistic over the node's elements that hold
+// particles (the count, statistic 0, at least one), summed in the order of the node's element
+// list.  One thread per node and statistic (k = kNS n + s), so that the FP64 additions spread
+// over every SM and the stores are contiguous.  The count is tested on its bits (for a
+// non-negative or NaN double, x >= 1 exactly when its bits as a signed integer are at least
+// those of 1.0), which keeps the test off the FP64 pipe; the mean is the sum times 1/c from a
+// table of correctly rounded reciprocals (within one rounding of the quotient), since an FP64
+// division per output would make this kernel FP64-bound on this GPU.
+struct NodeRecip {
+  double v[65];
+  constexpr NodeRecip() : v() {
+    for (int i = 1; i < 65; ++i) v[i] = 1.0 / i;
+  }
+};
+__device__ const NodeRecip g_node_recip{};
+
 __global__ void node_average_kernel(const double* __restrict__ emom, const int32_t* __restrict__ ne_off,
                                     const int32_t* __restrict__ ne_list, int32_t nn, double* nmom) {
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n >= nn) return;
-  double acc[kNS];
-#pragma unroll
-  for (int s = 0; s < kNS; ++s) acc[s] = 0.0;
+  const int64_t k = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= static_cast<int64_t>(nn) * kNS) return;
+  const int32_t n = static_cast<int32_t>(k / kNS);
+  const int s = static_cast<int>(k - static_cast<int64_t>(n) * kNS);
+  double acc = 0.0;
   int c = 0;
   for (int i = ne_off[n]; i < ne_off[n + 1]; ++i) {
     const double* em = emom + static_cast<size_t>(kNS) * ne_list[i];
-    if (em[0] < 1.0) continue;
-#pragma unroll
-    for (int s = 0; s < kNS; ++s) acc[s] += em[s];
+    if (__double_as_longlong(em[0]) < 0x3FF0000000000000LL) continue;
+    acc += em[s];
     ++c;
   }
-  double* out = nmom + static_cast<size_t>(kNS) * n;
-#pragma unroll
-  for (int s = 0; s < kNS; ++s) out[s] = c > 0 ? acc[s] / c : 0.0;
+  const double r = c <= 0 ? 0.0 : (c < 65 ? g_node_recip.v[c] : 1.0 / c);
+  nmom[k] = acc * r;
 }
 
 template <typename T> bool redist_configured[kMaxDevices];
@@ -939,14 +953,35 @@ void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s, const Side
     cudaFuncSetAttribute(stats_big_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          static_cast<int>(big));
   }
-  launch_stats_tiles<T>(a, num_sms, s, side);
-  stats_big_kernel<T><<<static_cast<unsigned>(num_sms > 0 ? num_sms : 1), kStatsThreads, big, s>>>(a);
+  // The tile classes and the large-element kernel take disjoint elements and write disjoint
+  // outputs: with the context's side streams they run as parallel branches (the 513..1024
+  // class on side[0]; the class of up to 256 and the large-element kernel on side[1]; the
+  // 257..512 class on s), so that each one's last wave, and its blocks of other classes,
+  // which return at once, overlap the others' work; s then waits for both branches.
+  const bool fork = side && side->ok;
+  cudaStream_t s_large = s, s_small = s;
+  if (fork) {
+    cudaEventRecord(side->ev[0], s);
+    cudaStreamWaitEvent(side->side[0], side->ev[0], 0);
+    cudaStreamWaitEvent(side->side[1], side->ev[0], 0);
+    s_large = side->side[0];
+    s_small = side->side[1];
+  }
+  launch_stats_tiles<T>(a, s_small, s, s_large);
+  stats_big_kernel<T><<<static_cast<unsigned>(num_sms > 0 ? num_sms : 1), kStatsThreads, big, s_small>>>(a);
+  if (fork) {
+    cudaEventRecord(side->ev[1], side->side[0]);
+    cudaEventRecord(side->ev[2], side->side[1]);
+    cudaStreamWaitEvent(s, side->ev[1], 0);
+    cudaStreamWaitEvent(s, side->ev[2], 0);
+  }
 }
 
 void launch_node_average(const double* emom, const int32_t* ne_off, const int32_t* ne_list,
                          int32_t nn, double* nmom, cudaStream_t s) {
   if (nn <= 0) return;
-  node_average_kernel<<<(nn + 127) / 128, 128, 0, s>>>(emom, ne_off, ne_list, nn, nmom);
+  const int64_t work = static_cast<int64_t>(nn) * kNS;
+  node_average_kernel<<<static_cast<unsigned>((work + 255) / 256), 256, 0, s>>>(emom, ne_off, ne_list, nn, nmom);
 }
 
 namespace {

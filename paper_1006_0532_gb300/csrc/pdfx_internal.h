@@ -386,9 +386,10 @@ void launch_redistribute(Particles<T> p, Plan& pl, int K, const InstDev<T>* inst
                          int num_sms, unsigned long long* diag, int* err, cudaStream_t s);
 template <typename T>
 void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s, const SideStreams* side);
+// The tile classes of up to 256, 257..512 and 513..1024 particles on s_small, s_mid and
+// s_large (k_bins_f32.cu / k_bins_f64.cu).
 template <typename T>
-void launch_stats_tiles(const StatsArgs<T>& a, int num_sms, cudaStream_t s,
-                        const SideStreams* side);   // k_bins_f32.cu / k_bins_f64.cu
+void launch_stats_tiles(const StatsArgs<T>& a, cudaStream_t s_small, cudaStream_t s_mid, cudaStream_t s_large);
 void launch_node_average(const double* emom, const int32_t* ne_off, const int32_t* ne_list,
                          int32_t nn, double* nmom, cudaStream_t s);
 // Eq. 26: max over nodes of ||(<U>, <V>, <W>, <omega>, <psi>)||_2 into out[0] (one block).
