@@ -46,16 +46,16 @@ SINGLE_POSITION_STEP_BYTES = 98
 # change of the sources the bench reports traffic as null until the next capture.
 NCU_RECORDS = {
     # channel_50k, 25.0M particles (FP32) and 5.0M (FP64 form), one GB300
-    "013b670569e217261573ce1c69b284fb413726ce86f75411d20da99b9ae6b51c": {
-        "traffic": {"advance": (1161.118e6 + 941.98656e6) / 25.0e6,
-                    "statistics_binning": (0.065792e6 + 688.991232e6 + 49.92896e6 + 233.8048e6
-                                           + 11.673088e6) / 25.0e6},
-        "limiter": {"advance": "instruction issue and memory latency: 65% issue-active at 48% "
-                               "warps active (64 registers cap 4 blocks of 256), long-scoreboard "
-                               "stalls first; DRAM 22% of peak",
-                    "statistics_binning": "instruction issue and shared-memory latency: 69% "
+    "77dbc2eb6a5ebf7e3fee035bb3ef2ac7b225775af85201c9f2d70cb85e466bf4": {
+        "traffic": {"advance": (1162.683e6 + 948.889856e6) / 25.0e6,
+                    "statistics_binning": (0.066048e6 + 688.425984e6 + 49.146112e6 + 233.91744e6
+                                           + 11.202048e6) / 25.0e6},
+        "limiter": {"advance": "instruction issue: 76% issue-active at 49% warps active (64 "
+                               "registers cap 4 blocks of 256), long-scoreboard stalls first; "
+                               "DRAM 26% of peak",
+                    "statistics_binning": "instruction issue and shared-memory latency: 71% "
                                           "issue-active (<= 512 class), short-scoreboard stalls "
-                                          "first; DRAM 12% of peak"},
+                                          "first; DRAM 13% of peak"},
         "f64_advance_fp64_inst_per_particle": (1407568787 + 454038118 + 836638858) / 5.0e6,
     },
 }
