@@ -1,6 +1,6 @@
-// Per-element statistics and conditional means for elements of up to 1024 particles, one
-// thread block per entry of the plan's tile lists (three size classes, launched one after
-// the other; larger elements go through the block kernel in k_stats.cu).  The chunk-sort
+// Per-element statistics and conditional means for elements of up to 768 particles, one
+// thread block per entry of the plan's tile lists (three size classes, launched as parallel
+// stream branches; larger elements go through the block kernel in k_stats.cu).  The chunk-sort
 // tile below serves elements up to the split and, for Fox's projection, every class; the
 // bucket-rank tile further down serves the larger classes of the hierarchical bins.
 //
@@ -1454,10 +1454,10 @@ __device__ void element_rank_tile(const StatsArgs<T>& a, RankTile<T, CAP, THREAD
   }
 }
 
-// Residency: the FP32 tiles (21 KB per 128 threads) fit 1280 threads per SM, the FP64
-// tiles 896; the register cap matches.
+// Residency: the FP32 tiles fit 10 blocks of 128 threads (22 KB each) or 7 of 192 (32 KB)
+// per SM, the FP64 tiles fewer; the register cap matches.
 template <typename T, int CAP, int THREADS, int CLS>
-__global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1280 : 1024) / THREADS)
+__global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? (THREADS == 192 ? 1344 : 1280) : 1024) / THREADS)
     rank_tile_kernel(const StatsArgs<T> a) {
   extern __shared__ __align__(16) unsigned char rank_smem[];
   RankTile<T, CAP, THREADS>& t = *reinterpret_cast<RankTile<T, CAP, THREADS>*>(rank_smem);
@@ -1489,26 +1489,27 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1536 : 1024) / THRE
 template <typename T>
 void launch_stats_tiles_impl(const StatsArgs<T>& a, cudaStream_t s_small, cudaStream_t s_mid, cudaStream_t s_large) {
   if (a.ne <= 0) return;
-  static_assert(kSmallCap == 1024 && kTileMid == 512 && kTileSplit == 256,
+  static_assert(kSmallCap == 768 && kTileMid == 512 && kTileSplit == 256,
                 "tile classes cover the small-element capacity");
   // elements of up to 256 particles: chunk sorts (4 warps; groups of at most 32 positions
   // are sorted by one warp in registers, which suits small elements); 257..512 (4 warps)
-  // and 513..1024 (8 warps): bucket ranks.  Fox's projection: chunk sorts in every class.
+  // and 513..768 (6 warps): bucket ranks.  Fox's projection: chunk sorts in every class
+  // (the largest class in a tile of 1,024).
   const unsigned grid = static_cast<unsigned>(a.ne);
   if (a.cond_mode == 1) {
     stats_tile_kernel<T, 1024, 256, 1, true><<<grid, 256, 0, s_large>>>(a);
     stats_tile_kernel<T, 256, 128, 0, true><<<grid, 128, 0, s_small>>>(a);
     stats_tile_kernel<T, 512, 128, 2, true><<<grid, 128, 0, s_mid>>>(a);
   } else {
-    constexpr size_t mid = sizeof(RankTile<T, 512, 128>), large = sizeof(RankTile<T, 1024, 256>);
+    constexpr size_t mid = sizeof(RankTile<T, 512, 128>), large = sizeof(RankTile<T, 768, 192>);
     static_assert(large <= 227 * 1024, "rank tile exceeds shared memory");
     if (first_use_on_device(rank_configured<T>)) {
       cudaFuncSetAttribute(rank_tile_kernel<T, 512, 128, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(mid));
-      cudaFuncSetAttribute(rank_tile_kernel<T, 1024, 256, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+      cudaFuncSetAttribute(rank_tile_kernel<T, 768, 192, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(large));
     }
-    rank_tile_kernel<T, 1024, 256, 1><<<grid, 256, large, s_large>>>(a);
+    rank_tile_kernel<T, 768, 192, 1><<<grid, 192, large, s_large>>>(a);
     stats_tile_kernel<T, 256, 128, 0, false><<<grid, 128, 0, s_small>>>(a);
     rank_tile_kernel<T, 512, 128, 2><<<grid, 128, mid, s_mid>>>(a);
   }

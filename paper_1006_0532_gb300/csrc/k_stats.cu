@@ -954,7 +954,7 @@ void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s, const Side
                          static_cast<int>(big));
   }
   // The tile classes and the large-element kernel take disjoint elements and write disjoint
-  // outputs: with the context's side streams they run as parallel branches (the 513..1024
+  // outputs: with the context's side streams they run as parallel branches (the 513..768
   // class on side[0]; the class of up to 256 and the large-element kernel on side[1]; the
   // 257..512 class on s), so that each one's last wave, and its blocks of other classes,
   // which return at once, overlap the others' work; s then waits for both branches.

@@ -177,7 +177,7 @@ struct Plan {
 };
 
 constexpr int kHistCap = 8192;      // counts above this are clipped for the closed form
-constexpr int kSmallCap = 1024;     // binning capacity of the block-per-element tile kernels
+constexpr int kSmallCap = 768;      // binning capacity of the block-per-element tile kernels
 constexpr int kTileSplit = 256;     // tile classes: up to 256 particles at most (chunk-sort tile),
 constexpr int kTileMid = 512;       // 257 .. 512 and 513 .. kSmallCap (bucket-rank tiles)
 constexpr int64_t kMaxParticles = int64_t(1) << 28;   // particle ids fit the 28-bit sort key field
@@ -386,7 +386,7 @@ void launch_redistribute(Particles<T> p, Plan& pl, int K, const InstDev<T>* inst
                          int num_sms, unsigned long long* diag, int* err, cudaStream_t s);
 template <typename T>
 void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s, const SideStreams* side);
-// The tile classes of up to 256, 257..512 and 513..1024 particles on s_small, s_mid and
+// The tile classes of up to 256, 257..512 and 513..768 particles on s_small, s_mid and
 // s_large (k_bins_f32.cu / k_bins_f64.cu).
 template <typename T>
 void launch_stats_tiles(const StatsArgs<T>& a, cudaStream_t s_small, cudaStream_t s_mid, cudaStream_t s_large);

@@ -200,7 +200,7 @@ def test_redistribution_matches_oracle_f64(seed):
 
 
 def test_large_element_path_and_empty_elements():
-    """Elements above the 1024-particle binning tile go through the large-element kernel."""
+    """Elements above the 768-particle binning tiles go through the large-element kernel."""
     w = synth.workload("channel_tiny")
     g = w["grid"]
     counts = np.full(g.ne, 30)
@@ -233,7 +233,7 @@ def test_large_element_path_and_empty_elements():
 @pytest.mark.parametrize("precision", [0, 1])
 def test_binning_split_changes_no_result(precision, fox):
     """Every size-class split of the binning (chunk-sort tile for elements up to the split,
-    bucket-rank tiles above it, up to 512 and up to 1024, the large-element kernel beyond)
+    bucket-rank tiles above it, up to 512 and up to 768, the large-element kernel beyond)
     gives the same pointers, bins and statistics bit for bit, with the hierarchical bins and
     with Fox's projection; in FP64 they are the oracle's, and the re-ordered state keeps
     every particle's values.  Out-of-range shapes are refused."""
@@ -243,8 +243,8 @@ def test_binning_split_changes_no_result(precision, fox):
     rng = np.random.default_rng(17)
     counts = rng.integers(1, 60, g.ne)
     counts[rng.choice(g.ne, 24, replace=False)] = np.concatenate(
-        [rng.integers(100, 257, 8), rng.integers(257, 513, 8), rng.integers(513, 1025, 6),
-         [1200, 2000]])
+        [rng.integers(100, 257, 8), rng.integers(257, 513, 8), rng.integers(513, 1025, 4),
+         [768, 769, 1200, 2000]])
     st = _imbalanced_state(g, counts, 8)
     ref = None
     for split in (256, 0, 100, 192):
