@@ -329,7 +329,9 @@ int run_statistics(Ctx& c, bool counts_ready, bool allow_moves, bool force_resor
     a.diag = c.diag;
     a.err = c.err;
     launch_stats<T>(a, c.num_sms, s, &c.side);
-    c.launches += 4;   // three tile classes and the large-element kernel
+    // three tile classes, the large-element kernel and (hierarchical bins) the bucket-rank
+    // tile over the large-element list
+    c.launches += a.cond_mode == 1 ? 4 : 5;
   }
   if (resort) {
     c.cur = 1 - c.cur;

@@ -1,6 +1,7 @@
 // Per-element statistics and conditional means for elements of up to 768 particles, one
 // thread block per entry of the plan's tile lists (three size classes, launched as parallel
-// stream branches; larger elements go through the block kernel in k_stats.cu).  The chunk-sort
+// stream branches), and of 769..1024 from the plan's large-element list; larger elements go
+// through the block kernel in k_stats.cu.  The chunk-sort
 // tile below serves elements up to the split and, for Fox's projection, every class; the
 // bucket-rank tile further down serves the larger classes of the hierarchical bins.
 //
@@ -1468,6 +1469,30 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? (THREADS == 192 ? 1
   element_rank_tile<T, CAP, THREADS>(a, t, e, min(N, CAP), moves);
 }
 
+// The plan's large-element lists (every instance's), entries of up to kTileBig particles, on
+// the bucket-rank tile of kTileBig: a few blocks per SM, each over entries gridDim.x apart;
+// stats_big_kernel takes the larger ones.
+template <typename T>
+__global__ void __launch_bounds__(256, (sizeof(T) == 4 ? 1280 : 1024) / 256) rank_big_kernel(const StatsArgs<T> a) {
+  extern __shared__ __align__(16) unsigned char rank_smem[];
+  RankTile<T, kTileBig, 256>& t = *reinterpret_cast<RankTile<T, kTileBig, 256>*>(rank_smem);
+  bool used = false;
+  for (int inst = 0; inst < a.K; ++inst) {
+    const int32_t* sc = a.scal + 16 * inst;
+    const int eb = a.ielem ? a.ielem[inst] : 0;
+    const int moves = sc[0] > 0;
+    const int nbig = sc[3];
+    for (int b = blockIdx.x; b < nbig; b += gridDim.x) {
+      const int e = a.big_list[eb + b];
+      const int N = moves ? a.fin[e] : a.cnt[e];
+      if (N > kTileBig) continue;
+      if (used) __syncthreads();   // the tile's previous element is done with the shared memory
+      used = true;
+      element_rank_tile<T, kTileBig, 256>(a, t, e, N, moves);
+    }
+  }
+}
+
 template <typename T> bool rank_configured[kMaxDevices];
 
 // One block per entry of one size class of the plan's tile lists (tile_element); the grid
@@ -1487,7 +1512,8 @@ __global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? 1536 : 1024) / THRE
 }  // namespace
 
 template <typename T>
-void launch_stats_tiles_impl(const StatsArgs<T>& a, cudaStream_t s_small, cudaStream_t s_mid, cudaStream_t s_large) {
+void launch_stats_tiles_impl(const StatsArgs<T>& a, int num_sms, cudaStream_t s_small, cudaStream_t s_mid,
+                             cudaStream_t s_large) {
   if (a.ne <= 0) return;
   static_assert(kSmallCap == 768 && kTileMid == 512 && kTileSplit == 256,
                 "tile classes cover the small-element capacity");
@@ -1502,14 +1528,18 @@ void launch_stats_tiles_impl(const StatsArgs<T>& a, cudaStream_t s_small, cudaSt
     stats_tile_kernel<T, 512, 128, 2, true><<<grid, 128, 0, s_mid>>>(a);
   } else {
     constexpr size_t mid = sizeof(RankTile<T, 512, 128>), large = sizeof(RankTile<T, 768, 192>);
-    static_assert(large <= 227 * 1024, "rank tile exceeds shared memory");
+    constexpr size_t big = sizeof(RankTile<T, kTileBig, 256>);
+    static_assert(big <= 227 * 1024, "rank tile exceeds shared memory");
     if (first_use_on_device(rank_configured<T>)) {
       cudaFuncSetAttribute(rank_tile_kernel<T, 512, 128, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(mid));
       cudaFuncSetAttribute(rank_tile_kernel<T, 768, 192, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(large));
+      cudaFuncSetAttribute(rank_big_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(big));
     }
     rank_tile_kernel<T, 768, 192, 1><<<grid, 192, large, s_large>>>(a);
+    // 769..1024 from the large-element list: 4 blocks per SM
+    rank_big_kernel<T><<<static_cast<unsigned>(4 * (num_sms > 0 ? num_sms : 1)), 256, big, s_large>>>(a);
     stats_tile_kernel<T, 256, 128, 0, false><<<grid, 128, 0, s_small>>>(a);
     rank_tile_kernel<T, 512, 128, 2><<<grid, 128, mid, s_mid>>>(a);
   }

@@ -4,9 +4,9 @@
 namespace pdfx {
 
 template <>
-void launch_stats_tiles<double>(const StatsArgs<double>& a, cudaStream_t s_small, cudaStream_t s_mid,
+void launch_stats_tiles<double>(const StatsArgs<double>& a, int num_sms, cudaStream_t s_small, cudaStream_t s_mid,
                                cudaStream_t s_large) {
-  launch_stats_tiles_impl<double>(a, s_small, s_mid, s_large);
+  launch_stats_tiles_impl<double>(a, num_sms, s_small, s_mid, s_large);
 }
 
 }  // namespace pdfx

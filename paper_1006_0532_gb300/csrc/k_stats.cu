@@ -851,6 +851,7 @@ __global__ void __launch_bounds__(kStatsThreads) stats_big_kernel(const StatsArg
   for (int b = blockIdx.x; b < nbig; b += gridDim.x) {
     const int e = a.big_list[eb + b];
     const int N = moves ? a.fin[e] : a.cnt[e];
+    if (N <= kTileBig && a.cond_mode != 1) continue;   // rank_big_kernel's (hierarchical bins)
     if (N > kBigCap) {
       if (threadIdx.x == 0) {
         atomicAdd(a.diag + kDiagCapacity, 1ull);
@@ -955,7 +956,8 @@ void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s, const Side
   }
   // The tile classes and the large-element kernel take disjoint elements and write disjoint
   // outputs: with the context's side streams they run as parallel branches (the 513..768
-  // class on side[0]; the class of up to 256 and the large-element kernel on side[1]; the
+  // class and the large-element list's 769..1024 on side[0]; the class of up to 256 and the
+  // large-element kernel on side[1]; the
   // 257..512 class on s), so that each one's last wave, and its blocks of other classes,
   // which return at once, overlap the others' work; s then waits for both branches.
   const bool fork = side && side->ok;
@@ -967,7 +969,7 @@ void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s, const Side
     s_large = side->side[0];
     s_small = side->side[1];
   }
-  launch_stats_tiles<T>(a, s_small, s, s_large);
+  launch_stats_tiles<T>(a, num_sms, s_small, s, s_large);
   stats_big_kernel<T><<<static_cast<unsigned>(num_sms > 0 ? num_sms : 1), kStatsThreads, big, s_small>>>(a);
   if (fork) {
     cudaEventRecord(side->ev[1], side->side[0]);

@@ -140,9 +140,10 @@ int element_stats_noalloc(Ctx& c, int64_t np, const double* u, const double* v, 
   a.err = c.err;
   launch_stats<double>(a, c.num_sms, s, &c.side);
   if (nmom) launch_node_average(emom, c.ne_off, c.ne_list, c.nn, nmom, s);
-  // iota, count and scatter (with particles), plan, three tile classes and the large-element
-  // kernel, node average
-  c.launches += (np > 0 ? 3 : 0) + plan_launches + 4 + (nmom ? 1 : 0);
+  // iota, count and scatter (with particles), plan, three tile classes, the large-element
+  // kernel and (hierarchical bins) the bucket-rank tile over the large-element list, node
+  // average
+  c.launches += (np > 0 ? 3 : 0) + plan_launches + (a.cond_mode == 1 ? 4 : 5) + (nmom ? 1 : 0);
   return cudaGetLastError() == cudaSuccess ? PDFX_OK : PDFX_ERR_CUDA;
 }
 

@@ -178,6 +178,7 @@ struct Plan {
 
 constexpr int kHistCap = 8192;      // counts above this are clipped for the closed form
 constexpr int kSmallCap = 768;      // binning capacity of the block-per-element tile kernels
+constexpr int kTileBig = 1024;      // the large-element list's entries up to this size take a bucket-rank tile
 constexpr int kTileSplit = 256;     // tile classes: up to 256 particles at most (chunk-sort tile),
 constexpr int kTileMid = 512;       // 257 .. 512 and 513 .. kSmallCap (bucket-rank tiles)
 constexpr int64_t kMaxParticles = int64_t(1) << 28;   // particle ids fit the 28-bit sort key field
@@ -389,7 +390,8 @@ void launch_stats(const StatsArgs<T>& a, int num_sms, cudaStream_t s, const Side
 // The tile classes of up to 256, 257..512 and 513..768 particles on s_small, s_mid and
 // s_large (k_bins_f32.cu / k_bins_f64.cu).
 template <typename T>
-void launch_stats_tiles(const StatsArgs<T>& a, cudaStream_t s_small, cudaStream_t s_mid, cudaStream_t s_large);
+void launch_stats_tiles(const StatsArgs<T>& a, int num_sms, cudaStream_t s_small, cudaStream_t s_mid,
+                        cudaStream_t s_large);
 void launch_node_average(const double* emom, const int32_t* ne_off, const int32_t* ne_list,
                          int32_t nn, double* nmom, cudaStream_t s);
 // Eq. 26: max over nodes of ||(<U>, <V>, <W>, <omega>, <psi>)||_2 into out[0] (one block).
