@@ -46,13 +46,13 @@ SINGLE_POSITION_STEP_BYTES = 98
 # change of the sources the bench reports traffic as null until the next capture.
 NCU_RECORDS = {
     # channel_50k, 25.0M particles (FP32) and 5.0M (FP64 form), one GB300
-    "77dbc2eb6a5ebf7e3fee035bb3ef2ac7b225775af85201c9f2d70cb85e466bf4": {
-        "traffic": {"advance": (1162.683e6 + 948.889856e6) / 25.0e6,
-                    "statistics_binning": (0.066048e6 + 688.425984e6 + 49.146112e6 + 233.91744e6
-                                           + 11.202048e6) / 25.0e6},
+    "3cdc24831a92467d850719feb4c7e2872f53c238892ddabfd4e268154d8fe39f": {
+        "traffic": {"advance": (1162.174e6 + 949.394432e6) / 25.0e6,
+                    "statistics_binning": (0.065792e6 + 688.448256e6 + 49.588736e6 + 237.700352e6
+                                           + 10.991872e6) / 25.0e6},
         "limiter": {"advance": "instruction issue: 76% issue-active at 49% warps active (64 "
                                "registers cap 4 blocks of 256), long-scoreboard stalls first; "
-                               "DRAM 26% of peak",
+                               "DRAM 25% of peak",
                     "statistics_binning": "instruction issue and shared-memory latency: 71% "
                                           "issue-active (<= 512 class), short-scoreboard stalls "
                                           "first; DRAM 13% of peak"},
