@@ -387,7 +387,7 @@ int do_step(Ctx& c, double dt, cudaStream_t s) {
     a.inst = c.K > 1 ? static_cast<const InstDev<T>*>(c.inst) : nullptr;
     a.einst = c.K > 1 ? c.einst : nullptr;
     launch_advance<T>(a, c.num_sms, c.adv_block, s);
-    c.launches++;
+    c.launches += 2;   // the advance and the brute-force search
     c.corr_pending = false;
   }
   PDFX_TRY(run_statistics<T>(c, true, true, false, s));
