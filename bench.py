@@ -46,10 +46,10 @@ SINGLE_POSITION_STEP_BYTES = 98
 # change of the sources the bench reports traffic as null until the next capture.
 NCU_RECORDS = {
     # channel_50k, 25.0M particles (FP32) and 5.0M (FP64 form), one GB300
-    "3cdc24831a92467d850719feb4c7e2872f53c238892ddabfd4e268154d8fe39f": {
-        "traffic": {"advance": (1162.174e6 + 949.394432e6) / 25.0e6,
-                    "statistics_binning": (0.065792e6 + 688.448256e6 + 49.588736e6 + 237.700352e6
-                                           + 10.991872e6) / 25.0e6},
+    "9b2eb27218f5268a35116fb34c8c5ea35bba4df56ca5a88dac14c24b7910acc1": {
+        "traffic": {"advance": (1162.812e6 + 949.04576e6) / 25.0e6,
+                    "statistics_binning": (0.066048e6 + 688.497152e6 + 49.604096e6 + 237.73184e6
+                                           + 10.911232e6) / 25.0e6},
         "limiter": {"advance": "instruction issue: 76% issue-active at 49% warps active (64 "
                                "registers cap 4 blocks of 256), long-scoreboard stalls first; "
                                "DRAM 25% of peak",
