@@ -585,11 +585,20 @@ def canyon_form(torch, B, synth, args):
     e1.record(stream)
     torch.cuda.synchronize()
     ms = e0.elapsed_time(e1)
+    # where the time goes: one re-order cycle of eager steps with the stage timers on
+    c.set_profiling(True)
+    c.stage_times()
+    for _ in range(cycle):
+        c.step(dt)
+    torch.cuda.synchronize()
+    stage_ms, stage_n = c.stage_times()
+    c.set_profiling(False)
     npart = c.np_
     d = c.diag()
     out = {"value": npart * steps / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms / steps,
            "steps": steps, "particles": npart, "triangles": int(w["grid"].ne), "ppe": w["ppe"],
            "dtype": "f32", "tuned": tuned, "device_errors": c.check(),
+           "stages_ms_per_step": {n: stage_ms[i] / max(stage_n[i], 1) for i, n in enumerate(STAGES)},
            "diag": {k: d[k] for k in ("wall_hits", "freeslip_hits", "moves", "lost", "walk_brute")}}
     c.close()
     torch.cuda.empty_cache()

@@ -1455,10 +1455,11 @@ __device__ void element_rank_tile(const StatsArgs<T>& a, RankTile<T, CAP, THREAD
   }
 }
 
-// Residency: the FP32 tiles fit 10 blocks of 128 threads (22 KB each) or 7 of 192 (32 KB)
-// per SM, the FP64 tiles fewer; the register cap matches.
+// Residency: the FP32 tiles fit 12 blocks of 128 threads up to 256 particles (11 KB each),
+// 10 up to 512 (22 KB) or 7 of 192 up to 768 (32 KB) per SM, the FP64 tiles fewer; the
+// register cap matches.
 template <typename T, int CAP, int THREADS, int CLS>
-__global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? (THREADS == 192 ? 1344 : 1280) : 1024) / THREADS)
+__global__ void __launch_bounds__(THREADS, (sizeof(T) == 4 ? (CAP == 256 ? 1536 : THREADS == 192 ? 1344 : 1280) : 1024) / THREADS)
     rank_tile_kernel(const StatsArgs<T> a) {
   extern __shared__ __align__(16) unsigned char rank_smem[];
   RankTile<T, CAP, THREADS>& t = *reinterpret_cast<RankTile<T, CAP, THREADS>*>(rank_smem);
@@ -1517,20 +1518,22 @@ void launch_stats_tiles_impl(const StatsArgs<T>& a, int num_sms, cudaStream_t s_
   if (a.ne <= 0) return;
   static_assert(kSmallCap == 768 && kTileMid == 512 && kTileSplit == 256,
                 "tile classes cover the small-element capacity");
-  // elements of up to 256 particles: chunk sorts (4 warps; groups of at most 32 positions
-  // are sorted by one warp in registers, which suits small elements); 257..512 (4 warps)
-  // and 513..768 (6 warps): bucket ranks.  Fox's projection: chunk sorts in every class
-  // (the largest class in a tile of 1,024).
+  // hierarchical bins: bucket ranks in every class, up to the split (at most 256
+  // particles) on a tile of 256 (4 warps), then up to 512 (4 warps) and 513..768 (6
+  // warps).  Fox's projection: chunk sorts in every class (groups of at most 32 positions
+  // are sorted by one warp in registers; the largest class in a tile of 1,024).
   const unsigned grid = static_cast<unsigned>(a.ne);
   if (a.cond_mode == 1) {
     stats_tile_kernel<T, 1024, 256, 1, true><<<grid, 256, 0, s_large>>>(a);
     stats_tile_kernel<T, 256, 128, 0, true><<<grid, 128, 0, s_small>>>(a);
     stats_tile_kernel<T, 512, 128, 2, true><<<grid, 128, 0, s_mid>>>(a);
   } else {
-    constexpr size_t mid = sizeof(RankTile<T, 512, 128>), large = sizeof(RankTile<T, 768, 192>);
-    constexpr size_t big = sizeof(RankTile<T, kTileBig, 256>);
+    constexpr size_t small = sizeof(RankTile<T, 256, 128>), mid = sizeof(RankTile<T, 512, 128>);
+    constexpr size_t large = sizeof(RankTile<T, 768, 192>), big = sizeof(RankTile<T, kTileBig, 256>);
     static_assert(big <= 227 * 1024, "rank tile exceeds shared memory");
     if (first_use_on_device(rank_configured<T>)) {
+      cudaFuncSetAttribute(rank_tile_kernel<T, 256, 128, 0>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           static_cast<int>(small));
       cudaFuncSetAttribute(rank_tile_kernel<T, 512, 128, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                            static_cast<int>(mid));
       cudaFuncSetAttribute(rank_tile_kernel<T, 768, 192, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1540,7 +1543,7 @@ void launch_stats_tiles_impl(const StatsArgs<T>& a, int num_sms, cudaStream_t s_
     rank_tile_kernel<T, 768, 192, 1><<<grid, 192, large, s_large>>>(a);
     // 769..1024 from the large-element list: 4 blocks per SM
     rank_big_kernel<T><<<static_cast<unsigned>(4 * (num_sms > 0 ? num_sms : 1)), 256, big, s_large>>>(a);
-    stats_tile_kernel<T, 256, 128, 0, false><<<grid, 128, 0, s_small>>>(a);
+    rank_tile_kernel<T, 256, 128, 0><<<grid, 128, small, s_small>>>(a);
     rank_tile_kernel<T, 512, 128, 2><<<grid, 128, mid, s_mid>>>(a);
   }
 }
