@@ -41,15 +41,16 @@ BIN_BYTES = {1: 29, 0: 49}
 SINGLE_POSITION_STEP_BYTES = 98
 # Figures from ncu captures of the kernels (DRAM bytes per particle and launch,
 # dram__bytes_read.sum + dram__bytes_write.sum; FP64 instructions per particle of the FP64
-# form's advance; the bound each capture shows), keyed by the SHA-256 of the CUDA sources
-# they were taken from: a capture describes only the kernels it measured, so after any
-# change of the sources the bench reports traffic as null until the next capture.
+# form's advance; the bound each capture shows), keyed by the SHA-256 of the CUDA sources'
+# code (comments aside) they were taken from: a capture describes only the kernels it
+# measured, so after any change of the code the bench reports traffic as null until the
+# next capture.
 NCU_RECORDS = {
     # channel_50k, 25.0M particles (FP32) and 5.0M (FP64 form), one GB300
-    "9b2eb27218f5268a35116fb34c8c5ea35bba4df56ca5a88dac14c24b7910acc1": {
-        "traffic": {"advance": (1162.812e6 + 949.04576e6) / 25.0e6,
-                    "statistics_binning": (0.066048e6 + 688.497152e6 + 49.604096e6 + 237.73184e6
-                                           + 10.911232e6) / 25.0e6},
+    "884109f4ef9f937ec8e6c0f340dcb09331d34ffda8b87605775c6a478bbb70d9": {
+        "traffic": {"advance": (1162.113e6 + 949.069312e6) / 25.0e6,
+                    "statistics_binning": (0.066048e6 + 688.4096e6 + 49.580032e6 + 237.703168e6
+                                           + 10.723072e6) / 25.0e6},
         "limiter": {"advance": "instruction issue: 76% issue-active at 49% warps active (64 "
                                "registers cap 4 blocks of 256), long-scoreboard stalls first; "
                                "DRAM 25% of peak",
@@ -62,16 +63,44 @@ NCU_RECORDS = {
 STAGES = ["advance", "plan", "lists", "redistribute", "statistics_binning", "node_average"]
 
 
+def _code_only(text: str) -> str:
+    """C++/CUDA source without its comments and blank lines (string and character literals
+    kept as they are, trailing blanks dropped): what a compiler sees of it."""
+    out = []
+    i, n = 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    lines = (line.rstrip() for line in "".join(out).split("\n"))
+    return "\n".join(line for line in lines if line)
+
+
 def kernel_sources_hash() -> str:
-    """SHA-256 over the CUDA sources of the library (file names and contents, sorted)."""
+    """SHA-256 over the CUDA sources of the library (file names and their code without
+    comments and blank lines, sorted by name): a change of comments alone keeps the hash."""
     import hashlib
     d = os.path.join(ROOT, "paper_1006_0532_gb300", "csrc")
     h = hashlib.sha256()
     for name in sorted(os.listdir(d)):
         if name.endswith((".cu", ".cuh", ".h")):
             h.update(name.encode())
-            with open(os.path.join(d, name), "rb") as f:
-                h.update(f.read())
+            with open(os.path.join(d, name), encoding="utf-8") as f:
+                h.update(_code_only(f.read()).encode())
     return h.hexdigest()
 
 

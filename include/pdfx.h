@@ -280,8 +280,8 @@ int  pdfx_step_many(void *ctx, double dt, int32_t nsteps, int use_graph, void *s
 /* Picks the launch shapes that do not change any result: the advance kernel's block size
  * (128 or 256 threads) and the re-order period sort_every (4, 8 or 16 steps; results do
  * not depend on the slots' order), then, with those, the binning's size-class split (the
- * largest element, 0, 128, 192 or 256 particles, taken by the chunk-sort tile; larger ones
- * up to 512 take the bucket-rank tile; both give the same order).  Each candidate runs one
+ * largest element, 0, 128, 192 or 256 particles, taken by the tile of 256; larger ones up
+ * to 512 take the tile of 512; every tile gives the same order).  Each candidate runs one
  * re-order cycle of dt steps from a snapshot of the current state, which is restored
  * afterwards (particles, statistics, step counter and diagnostics as before the call).
  * Writes the block size and period to adv_block and sort_every where not NULL (all three

@@ -1,9 +1,9 @@
 // Per-element statistics and conditional means for elements of up to 768 particles, one
 // thread block per entry of the plan's tile lists (three size classes, launched as parallel
 // stream branches), and of 769..1024 from the plan's large-element list; larger elements go
-// through the block kernel in k_stats.cu.  The chunk-sort
-// tile below serves elements up to the split and, for Fox's projection, every class; the
-// bucket-rank tile further down serves the larger classes of the hierarchical bins.
+// through the block kernel in k_stats.cu.  The chunk-sort tile below serves every class of
+// Fox's projection; the bucket-rank tile further down every class of the hierarchical
+// bins.
 //
 // Sect. 3.5 / Appendix A: the element's particles are sorted by (u, id); the level-1 groups
 // (positions with equal floor(g1 p / N)) are sorted by (v, id), the level-2 groups by

@@ -171,15 +171,15 @@ struct Plan {
   int32_t* movers = nullptr;   // [np] particle slots that move (by move index)
   int32_t* mrecip = nullptr;   // [np] recipient element per move
   double* mvals = nullptr;     // [np][7] new values per move
-  int tile_split = 256;        // elements of up to this many particles take the chunk-sort
-                               // tile (at most kTileSplit); larger ones up to kTileMid the
-                               // bucket-rank tile of kTileMid
+  int tile_split = 256;        // elements of up to this many particles take the tile of
+                               // kTileSplit (bucket ranks; chunk sorts for Fox's
+                               // projection); larger ones up to kTileMid the tile of kTileMid
 };
 
 constexpr int kHistCap = 8192;      // counts above this are clipped for the closed form
 constexpr int kSmallCap = 768;      // binning capacity of the block-per-element tile kernels
 constexpr int kTileBig = 1024;      // the large-element list's entries up to this size take a bucket-rank tile
-constexpr int kTileSplit = 256;     // tile classes: up to 256 particles at most (chunk-sort tile),
+constexpr int kTileSplit = 256;     // tile classes: up to the split, at most 256 particles,
 constexpr int kTileMid = 512;       // 257 .. 512 and 513 .. kSmallCap (bucket-rank tiles)
 constexpr int64_t kMaxParticles = int64_t(1) << 28;   // particle ids fit the 28-bit sort key field
 constexpr int64_t kMaxSlots = (int64_t(1) << 31) - 1;  // particle slots of a batch (int32 lists)

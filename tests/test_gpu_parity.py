@@ -232,8 +232,9 @@ def test_large_element_path_and_empty_elements():
 @pytest.mark.parametrize("fox", [False, True])
 @pytest.mark.parametrize("precision", [0, 1])
 def test_binning_split_changes_no_result(precision, fox):
-    """Every size-class split of the binning (chunk-sort tile for elements up to the split,
-    bucket-rank tiles above it, up to 512 and up to 768, the large-element kernel beyond)
+    """Every size-class split of the binning (the tile of 256 for elements up to the split,
+    tiles of 512 and 768 above it, the large-element kernels beyond; bucket ranks for the
+    hierarchical bins, chunk sorts for Fox's projection)
     gives the same pointers, bins and statistics bit for bit, with the hierarchical bins and
     with Fox's projection; in FP64 they are the oracle's, and the re-ordered state keeps
     every particle's values.  Out-of-range shapes are refused."""
