@@ -90,7 +90,11 @@ int  orc_get_particles(const orc_ctx *c, double *x, double *y, double *u, double
 int  orc_num_particles(const orc_ctx *c);
 uint32_t orc_step_index(const orc_ctx *c);
 
-/* One timestep and its stages (Table 1 order restricted to the particle path). */
+/* One timestep and its stages (Table 1 order restricted to the particle path).  Parity
+ * unpinned as a whole: the paper prints no worked example of a full step.  Its stages are
+ * pinned one by one, and whole steps run inside the pins that need them (Eq. 24's bin
+ * means and deviation decay across the statistics and the advance, Eq. 11's energy rate,
+ * Eq. 20's frequency source, the walls' reflection principle). */
 int  orc_step(orc_ctx *c, double dt);   /* dt <= 0: the time step of Eq. 26 */
 int  orc_cfl_dt(const orc_ctx *c, double *dt);
 /* Sect. 3.4: node-transferred gradient of a nodal quantity q[nn] (Eqs. 39-40, then the mean
