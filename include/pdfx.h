@@ -22,6 +22,9 @@
  *    boundary.  pdfx_strerror() names a code.
  *  - Device work is enqueued on the caller's CUDA stream (a cudaStream_t passed as void*,
  *    NULL = the legacy default stream) and is asynchronous unless a call says otherwise.
+ *    The statistics of a step fork onto two streams of the context's own and join back
+ *    (events), so that the caller's stream sees every call's work in order, and a stream
+ *    capture of a call records the branches as parallel nodes.
  *    Problems found on the device (a particle found in no element, an element above the
  *    per-element capacity, a non-finite state) set a device error word; it is read by
  *    pdfx_get_diag() and pdfx_check(), which synchronise the stream.
@@ -144,7 +147,9 @@ typedef struct pdfx_diag {
 void pdfx_default_params(pdfx_params *p);
 
 /* Creates a context.  p: host, copied.  alloc: host, copied, may be NULL (cudaMalloc).
- * The current CUDA device is the context's device.  PDFX_ERR_ARG for invalid params. */
+ * The current CUDA device is the context's device; the context also creates two
+ * non-blocking streams and three events there for the statistics' parallel branches
+ * (without them the branches run on the caller's stream).  PDFX_ERR_ARG for invalid params. */
 int  pdfx_create(const pdfx_params *p, const pdfx_allocator *alloc, void **out_ctx);
 
 /* Releases all device memory of the context (synchronises the device first). */
